@@ -1,0 +1,197 @@
+"""ctypes front end of the C oracle (``fc2_oracle.c``).
+
+TEST INFRASTRUCTURE: the oracle computes Delta chi^2 of the truncated Fourier
+model (Palmer 2009, Sec. 1 Eq. "eqtrunc", Sec. 2 Eqs. "eqchigen", "eqchix")
+directly from the samples -- Householder least squares per trial frequency and
+per H', no FFT, no gridding.  The C file's header states each definition used.
+
+``build()`` compiles the C file with gcc into ``oracle/_build``.  The calls here
+only marshal arrays; threads split the trial bins across host cores (ctypes
+releases the GIL during the foreign call, and the C code is re-entrant).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fc2_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "libfc2_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+TAU_R = 1e-10  # rank rule: drop a column whose residual norm < TAU_R * its norm
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def build(force: bool = False) -> str:
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11",
+                               "-fno-fast-math", "-ffp-contract=off", _SRC,
+                               "-o", tmp, "-lm"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            lib.fc2o_moments.argtypes = [_D, _D, _D, i64, _D]
+            lib.fc2o_dchi2_freqs.argtypes = [_D, _D, _D, i64, i32, _D, i64, dbl, _D, _D]
+            lib.fc2o_dchi2_bins.argtypes = [_D, _D, _D, i64, i32, dbl, dbl, _I64, i64, dbl, _D, _D]
+            lib.fc2o_coeffs.argtypes = [_D, _D, _D, i64, i32, dbl, dbl, _D, _D]
+            lib.fc2o_trig_sums.argtypes = [_D, _D, i64, _D, i64, _D, _D]
+            lib.fc2o_normal_eq.argtypes = [_D, _D, _D, i64, i32, dbl, _D, _D]
+            lib.fc2o_grad.argtypes = [_D, _D, _D, i64, i32, dbl, dbl, _D, _D, _D, _D]
+            lib.fc2o_refine.argtypes = [_D, _D, _D, i64, i32, dbl, dbl, dbl, dbl, _D, _D]
+            for fn in ("fc2o_moments", "fc2o_dchi2_freqs", "fc2o_dchi2_bins", "fc2o_coeffs",
+                       "fc2o_trig_sums", "fc2o_normal_eq", "fc2o_grad", "fc2o_refine"):
+                getattr(lib, fn).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def moments(x, sigma):
+    """(W, xbar, chi2_0, sum w (x - xbar)) -- Sec. 3b and 3c definitions."""
+    lib = _load()
+    x, sigma = _f64(x), _f64(sigma)
+    out = np.zeros(4)
+    _check(lib.fc2o_moments(None, _p(x), _p(sigma), x.size, _p(out)), "moments")
+    return tuple(float(v) for v in out)
+
+
+def _threads(threads):
+    if threads is None or threads <= 0:
+        return os.cpu_count() or 1
+    return threads
+
+
+def dchi2_freqs(t, x, sigma, H, freqs, threads=None, tau_r=TAU_R, with_pivots=False):
+    """Delta chi^2_{H'} for H' = 1..H at each frequency: array [len(freqs), H]."""
+    lib = _load()
+    t, x, sigma, freqs = _f64(t), _f64(x), _f64(sigma), _f64(np.atleast_1d(freqs))
+    nf = freqs.size
+    out = np.zeros((nf, H))
+    piv = np.zeros((nf, H))
+    nt = max(1, min(_threads(threads), nf))
+    chunks = np.array_split(np.arange(nf), nt)
+
+    def run(idx):
+        if idx.size == 0:
+            return 0
+        fr = np.ascontiguousarray(freqs[idx])
+        o = np.zeros((idx.size, H))
+        pv = np.zeros((idx.size, H))
+        rc = lib.fc2o_dchi2_freqs(_p(t), _p(x), _p(sigma), t.size, H, _p(fr), idx.size,
+                                  tau_r, _p(o), _p(pv))
+        out[idx] = o
+        piv[idx] = pv
+        return rc
+
+    if nt == 1:
+        rcs = [run(chunks[0])]
+    else:
+        with ThreadPoolExecutor(nt) as ex:
+            rcs = list(ex.map(run, chunks))
+    for rc in rcs:
+        _check(rc, "dchi2")
+    return (out, piv) if with_pivots else out
+
+
+def freq_of(f_min, df, j):
+    """Trial frequency f_j = f_min + j * df, evaluated in double exactly so."""
+    return f_min + np.asarray(j, dtype=np.float64) * df
+
+
+def dchi2_bins(t, x, sigma, H, f_min, df, bins, threads=None, tau_r=TAU_R, with_pivots=False):
+    return dchi2_freqs(t, x, sigma, H, freq_of(f_min, df, np.asarray(bins, dtype=np.int64)),
+                       threads=threads, tau_r=tau_r, with_pivots=with_pivots)
+
+
+def coeffs(t, x, sigma, Hp, f, tau_r=TAU_R):
+    """(A[2Hp+1] absolute frame with xbar added to A0, Delta chi^2)."""
+    lib = _load()
+    t, x, sigma = _f64(t), _f64(x), _f64(sigma)
+    A = np.zeros(2 * Hp + 1)
+    d = np.zeros(1)
+    _check(lib.fc2o_coeffs(_p(t), _p(x), _p(sigma), t.size, Hp, float(f), tau_r, _p(A), _p(d)),
+           "coeffs")
+    return A, float(d[0])
+
+
+def trig_sums(t, c, freqs):
+    """sum_i c_i exp(+i 2 pi f t_i) for each f (Sec. 2, Eq. eqPQ)."""
+    lib = _load()
+    t, c, freqs = _f64(t), _f64(c), _f64(np.atleast_1d(freqs))
+    re = np.zeros(freqs.size)
+    im = np.zeros(freqs.size)
+    _check(lib.fc2o_trig_sums(_p(t), _p(c), t.size, _p(freqs), freqs.size, _p(re), _p(im)),
+           "trig_sums")
+    return re + 1j * im
+
+
+def normal_eq(t, x, sigma, H, f):
+    """(alpha [(2H+1)^2], beta [2H+1]) by direct sums over samples (Sec. 2)."""
+    lib = _load()
+    t, x, sigma = _f64(t), _f64(x), _f64(sigma)
+    m = 2 * H + 1
+    a = np.zeros((m, m))
+    b = np.zeros(m)
+    _check(lib.fc2o_normal_eq(_p(t), _p(x), _p(sigma), t.size, H, float(f), _p(a), _p(b)),
+           "normal_eq")
+    return a, b
+
+
+def grad(t, x, sigma, H, f, tau_r=TAU_R):
+    """(Delta chi^2_H, d/df, d/dx[n], d/dsigma[n]) at fixed f."""
+    lib = _load()
+    t, x, sigma = _f64(t), _f64(x), _f64(sigma)
+    d = np.zeros(1)
+    g = np.zeros(1)
+    gx = np.zeros(t.size)
+    gs = np.zeros(t.size)
+    _check(lib.fc2o_grad(_p(t), _p(x), _p(sigma), t.size, H, float(f), tau_r, _p(d), _p(g),
+                         _p(gx), _p(gs)), "grad")
+    return float(d[0]), float(g[0]), gx, gs
+
+
+def refine(t, x, sigma, H, a, b, tol=1e-12, tau_r=TAU_R):
+    """Brent maximum of the exact Delta chi^2_H(f) on [a, b]: (f*, value)."""
+    lib = _load()
+    t, x, sigma = _f64(t), _f64(x), _f64(sigma)
+    fs = np.zeros(1)
+    v = np.zeros(1)
+    _check(lib.fc2o_refine(_p(t), _p(x), _p(sigma), t.size, H, float(a), float(b), float(tol),
+                           tau_r, _p(fs), _p(v)), "refine")
+    return float(fs[0]), float(v[0])
+
+
+def periodogram(t, x, sigma, H, f_min, df, N, threads=None, tau_r=TAU_R, with_pivots=False):
+    """Full oracle periodogram over all N bins: [N, H] (small cases only)."""
+    return dchi2_bins(t, x, sigma, H, f_min, df, np.arange(N), threads=threads, tau_r=tau_r,
+                      with_pivots=with_pivots)
