@@ -1,0 +1,350 @@
+#!/usr/bin/env python
+"""Benchmark of the Fchi2 periodogram hot path on one GB300 per rank.
+
+Workload (the long single-curve case): n = 100,000 samples over 3000 d with a
+seasonal window and nightly cadence, an 8-harmonic sawtooth signal, H = 6,
+N = 2^22 trial frequencies up to 20 /d, grids oversampled 4x.  Inputs are
+seeded synthetic curves (seed 2 + rank); every grid is larger than L2.
+
+One step = fc2_execute on resident inputs: phase reduction, spreading, FFTs,
+assembly and bordered Cholesky for all H' = 1..H, exact fix-up of sensitive
+bins, peaks and coefficients.  The metric counts one evaluation per
+(trial frequency, H').
+
+--impl reference times the CPU oracle (direct sums + Householder least
+squares per bin) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Delta-chi2 evals/s (freq x H') at 1e-4*chi2_0, mixed vs FP64; % HBM peak"
+UNIT = "evals/s"
+WORKLOAD = "long single curve: n=100000, T=3000 d seasonal+nightly, sawtooth 8 harmonics, " \
+           "H=6, N=2^22 to 20/d, 4x oversampled grids"
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        try:
+            import torch
+            if not torch.cuda.is_available():
+                backend = "gloo"
+        except Exception:
+            backend = "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(ws, v, device=None):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for ln in fh:
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def oracle_sample(c, bins, threads):
+    from oracle import oracle
+    t0 = time.perf_counter()
+    d, piv = oracle.dchi2_bins(c.t, c.x, c.sigma, c.H, c.f_min, c.df, bins, threads=threads,
+                               with_pivots=True)
+    return d, piv, time.perf_counter() - t0
+
+
+def sample_bins_for(c, n_random, seed, extra=()):
+    from tests.parity import sample_bins
+    f0 = c.truth.get("f0", 1.0)
+    cen = [int(round((f0 - c.f_min) / c.df)), int(round((2 * f0 - c.f_min) / c.df)),
+           int(round((f0 / 2 - c.f_min) / c.df)), int(round((1.0 - c.f_min) / c.df))]
+    cen += [int(j) for j in extra]
+    return sample_bins(c.N, n_random, seed, windows=cen, half=8)
+
+
+def run_reference(args):
+    ws, rank, local = dist_init()
+    if rank != 0:
+        return
+    from paper_0901_1913_gb300 import synth
+    c = synth.config2(seed=2)
+    threads = os.cpu_count() or 1
+    per_step = max(threads, args.ref_bins)
+    rng = np.random.default_rng(7)
+    times = []
+    for it in range(args.warmup + args.steps):
+        bins = np.sort(rng.choice(c.N, size=per_step, replace=False))
+        _, _, dt = oracle_sample(c, bins, threads)
+        if it >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * sum(times) / len(times)
+    value = per_step * c.H / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{per_step} random trial frequencies x H'=1..6 per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    ws, rank, local = dist_init()
+    import torch
+    from paper_0901_1913_gb300 import _fc2, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    c = synth.config2(seed=2 + rank)
+    stream = torch.cuda.Stream(device=dev)
+    evals = c.N * c.H
+
+    def make_plan(prec, t=c.t, x=c.x, s=c.sigma):
+        return _fc2.Plan(t, x, s, c.H, c.f_min, c.df, c.N, c.oversample, prec,
+                         stream=stream.cuda_stream, device=local)
+
+    out = torch.empty((c.H, c.N), dtype=torch.float64, device=dev)
+
+    def timed(plan, steps, warmup, sampler=None):
+        for _ in range(warmup):
+            plan.execute(out, want_records=True)
+        barrier(ws)
+        torch.cuda.synchronize()
+        plan.stage_timing(True)
+        if sampler:
+            sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.execute(out, want_records=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        barrier(ws)
+        ms = e0.elapsed_time(e1)
+        stage_ms, nl, fft_bytes = plan.stage_times()
+        plan.stage_timing(False)
+        return ms, stage_ms, nl, fft_bytes, clocks
+
+    # --- mixed (headline) ---
+    pm = make_plan("mixed")
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    ms, stage_ms, nlaunch, fft_bytes, clocks = timed(pm, args.steps, args.warmup, sampler)
+    counts = pm.counts
+    ms_max = allreduce_max(ws, ms, dev if torch.distributed.is_initialized() and
+                           torch.distributed.get_backend() == "nccl" else None) if ws > 1 else ms
+    ms_step = ms_max / args.steps
+    value = ws * evals / (ms_step / 1e3)
+    dm = out.cpu().numpy()
+    _, best, peaks, chi0 = pm.execute(out)
+    pm.close()
+
+    # --- FP64 plain path, same workload ---
+    pf = make_plan("fp64")
+    f_steps = max(2, min(args.steps, args.fp64_steps))
+    ms64, stage64, _, fft_bytes64, _ = timed(pf, f_steps, max(1, min(args.warmup, 2)))
+    ms64_max = allreduce_max(ws, ms64, dev if ws > 1 and torch.distributed.get_backend() == "nccl"
+                             else None) if ws > 1 else ms64
+    d64 = out.cpu().numpy()
+    pf.close()
+    value64 = ws * evals / (ms64_max / f_steps / 1e3)
+
+    # --- end to end through the C ABI with host buffers ---
+    tp = torch.from_numpy(np.ascontiguousarray(c.t)).pin_memory()
+    xp = torch.from_numpy(np.ascontiguousarray(c.x)).pin_memory()
+    sp = torch.from_numpy(np.ascontiguousarray(c.sigma)).pin_memory()
+    hout = torch.empty((c.H, c.N), dtype=torch.float64).pin_memory()
+    e2e_steps = max(2, min(args.steps, args.e2e_steps))
+    for it in range(1 + e2e_steps):
+        if it == 1:
+            torch.cuda.synchronize()
+            barrier(ws)
+            t_e2e = time.perf_counter()
+        p = _fc2.Plan(tp, xp, sp, c.H, c.f_min, c.df, c.N, c.oversample, "mixed",
+                      stream=stream.cuda_stream, device=local)
+        p.execute(hout, want_records=True)
+        p.close()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t_e2e) / e2e_steps
+    e2e_s = allreduce_max(ws, e2e_s) if ws > 1 else e2e_s
+    rec_bytes = (c.H + 8) * _fc2.ctypes.sizeof(_fc2.Best) + 8
+    e2e = {"value": ws * evals / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(3 * c.n * 8), "d2h_bytes_per_step": int(c.H * c.N * 8 + rec_bytes),
+           "ms_per_step": e2e_s * 1e3, "includes": "plan create (H2D, moments, tables) + execute + D2H + destroy"}
+
+    if rank != 0:
+        return
+
+    # --- roofline of the dominant kernel (the FFT passes) ---
+    peak, peak_kind = load_peaks()
+    P = 2  # passes of the 2^24-point transforms at this size
+    fft_ms = stage_ms[1]
+    achieved = (fft_bytes / 1e9) / (fft_ms / 1e3) if fft_ms > 0 else 0.0
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "fft_pass_long_curve_traffic.txt")
+    try:
+        import importlib
+        ver = importlib.import_module("paper_0901_1913_gb300.build").kernel_version()
+        with open(tpath) as fh:
+            kv = dict(ln.strip().split("=", 1) for ln in fh if "=" in ln)
+        if kv.get("kernel_version") == ver:
+            traffic = float(kv["traffic_bytes_per_launch"])
+    except Exception:
+        traffic = None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": "k_fft_pass (2 passes/step)",
+            "algorithmic_bytes_per_launch": fft_bytes / P, "launch_ms": fft_ms / P,
+            "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
+
+    # --- CPU oracle on a bounded sample of the same curve: baseline + parity ---
+    cpu = None
+    parity = None
+    if not args.no_cpu and ws == 1:
+        threads = os.cpu_count() or 1
+        bj = [b["j"] for b in best] + [p["j"] for p in peaks if p["j"] >= 0]
+        probe = sample_bins_for(c, threads, 11)[:threads]
+        _, _, dt = oracle_sample(c, probe, threads)
+        per_bin = dt / len(probe) * threads
+        nbins = int(max(threads, min(20000, args.cpu_seconds * threads / max(per_bin, 1e-6))))
+        bins = sample_bins_for(c, max(0, nbins - 9 * 17), 13, extra=bj)
+        d_or, piv, dt = oracle_sample(c, bins, threads)
+        cpu = {"value": len(bins) * c.H / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{len(bins)} trial frequencies x H'=1..{c.H} (random + windows at f0, "
+                         f"2f0, f0/2, 1/d and the GPU's best bins)", "seconds": dt}
+        from tests.parity import argmax_ok, compare
+        rm = compare(dm[:, bins].T, d_or, piv, chi0)
+        r6 = compare(d64[:, bins].T, d_or, piv, chi0)
+        jo = int(bins[np.argmax(d_or[:, -1])])
+        parity = {"bins": len(bins), "mixed_max_err_rel": rm["max_err_rel"],
+                  "fp64_max_err_rel": r6["max_err_rel"], "near_alias_bins": rm["n_near_alias"],
+                  "ok": bool(rm["ok"] and r6["ok"]),
+                  "argmax_ok": bool(argmax_ok(best[-1]["j"], jo, d_or[:, -1], chi0, bins))}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "mixed", "n": c.n, "N": c.N, "H": c.H,
+                   "oversample": c.oversample, "parallelism": f"{ws} independent curves",
+                   "l2": "inputs larger than L2 (18 grids x 128 MiB)"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(nlaunch * args.steps),
+        "clocks": clocks,
+        "fp64": {"value": value64, "ms_per_step": ms64_max / f_steps, "steps": f_steps,
+                 "stage_ms": [round(v, 4) for v in stage64]},
+        "mixed_over_fp64": value / value64,
+        "stage_ms": {k: round(v, 4) for k, v in zip(["spread", "fft", "assemble", "fixup", "peaks"],
+                                                    stage_ms)},
+        "bins_resolved_double": counts[0], "bins_exact_sums": counts[1],
+        "bins_exact_double": counts[2],
+        "parity": parity,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fchi2", choices=["fchi2", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-bins", type=int, default=48)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

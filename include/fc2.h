@@ -1,0 +1,191 @@
+/*
+ * fc2.h -- C ABI of libfc2, a GB300 (sm_103a) implementation of the Fast
+ * chi-squared (Fchi2) periodogram of D. M. Palmer, "A Fast Chi-squared
+ * Technique For Period Search of Irregularly Sampled Data" (arXiv 0901.1913).
+ *
+ * Model (Sec. 1, Eq. "eqtrunc"): for trial frequency f and H' harmonics,
+ *     Phi(t) = A_0 + sum_{h=1..H'} A_{2h-1} sin(2 pi h f t) + A_{2h} cos(2 pi h f t).
+ * Output (Sec. 2, Eqs. "eqchigen", "eqchix"; Sec. 3c):
+ *     Delta chi^2_{H'}(f) = chi2_0 - min_A sum_i (Phi(t_i) - x_i)^2 / sigma_i^2,
+ *     chi2_0 = sum_i (x_i - xbar)^2 / sigma_i^2,  xbar = weighted mean (Sec. 3b),
+ * for every H' = 1..H at every trial frequency f_j = f_min + j * df,
+ * j = 0..N-1 (evaluated in double exactly as written).
+ *
+ * Path (Sec. 2 "The function p(t) ... P and Q can be efficiently computed by
+ * the application of the FFT", Sec. 3b-3e): the weights w_i = sigma_i^-2 and
+ * the weighted data w_i (x_i - xbar) are spread onto uniform oversampled
+ * grids, one per needed multiple k f (Q at k = 1..2H, P at k = 1..H), FFTs of
+ * those grids give the trigonometric sums P(k f_j), Q(k f_j) (Eq. "eqPQ"), and
+ * each frequency's (2H+1)-square normal equations (Eqs. "eqalphafirst" ..
+ * "eqalpha" and the beta equations) are solved by one bordered Cholesky
+ * factorisation that yields all H' at once.
+ *
+ * Conventions for every call:
+ *   - Return value is an fc2_status; no call throws or aborts across the ABI.
+ *   - Arrays are plain C arrays of the stated element type and length.  A
+ *     pointer is a device pointer when the matching *_on_device option is set,
+ *     otherwise a host pointer (pageable or pinned).
+ *   - The library copies or borrows inputs as stated per call; output buffers
+ *     always belong to the caller.
+ *   - A plan is used from one host thread at a time and runs on one CUDA
+ *     stream (opt->cuda_stream, or a stream the plan creates).
+ *   - Device-side checks never trap: a kernel that finds a problem writes a
+ *     status word that the calling function reads and returns.
+ */
+#ifndef FC2_H
+#define FC2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FC2_MAX_H 16
+
+typedef struct fc2_plan_s* fc2_plan;
+
+typedef enum {
+    FC2_OK = 0,
+    FC2_ERR_INVALID_ARG = 1,   /* argument out of range, NULL, non-finite input, sigma <= 0 */
+    FC2_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+    FC2_ERR_OOM = 3,           /* device allocation failed or the plan exceeds device memory */
+    FC2_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
+    FC2_ERR_UNSUPPORTED = 5,   /* valid request this build does not implement */
+    FC2_ERR_NUMERIC = 6        /* non-finite intermediate (e.g. overflow in the solve) */
+} fc2_status;
+
+typedef enum {
+    FC2_PREC_FP64 = 0,         /* grids, FFTs and solves in double */
+    FC2_PREC_MIXED = 1         /* double phase reduction and moments; float grids and FFTs
+                                  with compensated spreading; float Cholesky with a double
+                                  re-solve of ill-conditioned bins and an exact double
+                                  fix-up of near-singular (aliased) bins */
+} fc2_precision;
+
+typedef struct {
+    fc2_precision prec;        /* default FC2_PREC_FP64 */
+    int kernel_width;          /* spreading-kernel width in grid cells; 0 = default for prec */
+    int top_k;                 /* number of peak records fc2_execute returns; 0 = 8 */
+    double alias_tau;          /* rank-drop threshold on the Cholesky relative pivot
+                                  d_l / alpha_ll; 0 = default (1e-9 FP64) */
+    void* cuda_stream;         /* cudaStream_t to run on; NULL = plan-owned stream */
+    int device;                /* CUDA device ordinal */
+    int inputs_on_device;      /* t, x, sigma are device pointers (borrowed, not copied) */
+    int outputs_on_device;     /* dchi2 (and d_dx, d_dsigma) are device pointers */
+} fc2_options;
+
+/* One selected frequency: bin index, frequency, Delta chi^2 and the
+ * coefficients A[0..2H'] of Eq. "eqcoeffs" in the basis order of Eq. "eqtrunc"
+ * (absolute time frame, xbar added to A_0 as Sec. 3b directs; entries past
+ * 2H' are zero). */
+typedef struct {
+    int64_t j;
+    double f;
+    double dchi2;
+    int32_t H;                 /* number of harmonics of this record's model */
+    int32_t flags;             /* bit 0: bin needed the exact double fix-up */
+    double A[2 * FC2_MAX_H + 1];
+} fc2_best;
+
+/* Fill *opt with defaults. */
+void fc2_options_default(fc2_options* opt);
+
+/*
+ * fc2_plan_create -- bind one light curve and one frequency search.
+ *   t, x, sigma [n]: sample times, values and standard errors (Sec. 2).
+ *     n >= 1; all finite; sigma > 0.  Any order of t.
+ *   H: highest harmonic, 1 <= H <= FC2_MAX_H.
+ *   f_min >= 0, df > 0, N >= 2: trial frequencies f_j = f_min + j df.
+ *   oversample: grid oversampling sigma_g >= 2; the grid length is the
+ *     smallest power of two >= oversample * N.
+ * Inputs are copied to plan-owned device memory unless inputs_on_device, in
+ * which case the device arrays are borrowed and must stay valid and unchanged
+ * for the plan's lifetime.  Creation sorts by time if needed, computes the
+ * moments of Sec. 3b/3c, and allocates every buffer fc2_execute needs.
+ * Errors: FC2_ERR_INVALID_ARG (ranges, NULL, non-finite or sigma <= 0 found
+ * on the device), FC2_ERR_OOM, FC2_ERR_CUDA.  *out is NULL on error.
+ */
+fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma,
+                           int64_t n, int H, double f_min, double df, int64_t N,
+                           int oversample, const fc2_options* opt, fc2_plan* out);
+
+/*
+ * fc2_execute -- run the periodogram.
+ *   dchi2 [H][N] (row H'-1 holds Delta chi^2_{H'}), may be NULL.
+ *   best [H]: best[H'-1] = argmax_j Delta chi^2_{H'} (ties -> lowest j; Sec. 3e
+ *     "The value of f with the largest value of Delta chi^2 ... provides the
+ *     best fit"), with the H'-harmonic coefficients.  May be NULL.
+ *   peaks [top_k]: local maxima of Delta chi^2_H (value > left neighbour,
+ *     >= right neighbour; edges one-sided) in decreasing value, ties by j
+ *     (the multiple candidates of Sec. 3e).  Unused records have j = -1.
+ *     May be NULL.
+ *   chi2_0: scalar, may be NULL.
+ * Synchronous: returns after the outputs are written.
+ */
+fc2_status fc2_execute(fc2_plan p, double* dchi2, fc2_best* best, fc2_best* peaks,
+                       double* chi2_0);
+
+/*
+ * fc2_execute_batched -- many independent light curves (the "many sources"
+ * case of Sec. 4) in one call.
+ *   C curves; offsets [C+1] (host): curve c owns samples offsets[c] ..
+ *   offsets[c+1]-1 of t, x, sigma (host, or device when inputs_on_device).
+ *   H [C], f_min [C], df [C], N [C] (host): per-curve search.
+ *   dchi2: packed float output; curve c's [H_c][N_c] block starts at
+ *     sum_{c' < c} H_c' N_c'.  Host or device per outputs_on_device.  May be NULL.
+ *   peaks [C][top_k] (host): per-curve peak records as fc2_execute.  May be NULL.
+ * Validation as fc2_plan_create for each curve.
+ */
+fc2_status fc2_execute_batched(int64_t C, const int64_t* offsets,
+                               const double* t, const double* x, const double* sigma,
+                               const int* H, const double* f_min, const double* df,
+                               const int64_t* N, int oversample, const fc2_options* opt,
+                               float* dchi2, fc2_best* peaks);
+
+/*
+ * fc2_backward -- exact (ungridded) gradients and Newton refinement at peaks,
+ * the local refinement "using the ungridded data" of Sec. 3e.
+ *   K peaks at bins peak_j [K] (host).  For each k, with f = f_min + peak_j[k] df
+ *   and the H-harmonic model:
+ *     d_df[k]        = g_k * dDelta/df,
+ *     d_dx[k][i]     = g_k * dDelta/dx_i,
+ *     d_dsigma[k][i] = g_k * dDelta/dsigma_i      (i in the caller's sample order),
+ *   with g_k = grad_out[k] (NULL = all ones), Delta = Delta chi^2_H computed by
+ *   direct double sums over the samples.  f_refined[k] is the Newton maximiser
+ *   of the exact Delta chi^2_H within one df of the bin (stopping when the step
+ *   is below 1e-9 /d... or 1e-3 df, whichever is smaller) and dchi2_refined[k]
+ *   its value.  Any output may be NULL; d_dx/d_dsigma follow outputs_on_device.
+ */
+fc2_status fc2_backward(fc2_plan p, int K, const int64_t* peak_j, const double* grad_out,
+                        double* f_refined, double* dchi2_refined, double* d_df,
+                        double* d_dx, double* d_dsigma);
+
+/* Release a plan and its device memory.  NULL is ignored. */
+void fc2_plan_destroy(fc2_plan p);
+
+/* Static description of a status code. */
+const char* fc2_status_string(fc2_status s);
+
+/* Host-only helpers (no GPU needed), exposed for testing the host logic. */
+
+/* Grid length the library uses for (N, oversample): smallest power of two >=
+ * oversample * N, or 0 if out of range. */
+int64_t fc2_grid_size(int64_t N, int oversample);
+
+/* Default spreading-kernel width for a precision and oversampling. */
+int fc2_default_width(fc2_precision prec, int oversample);
+
+/* Fourier transform phihat(xi) = integral phi(z) cos(2 pi xi z) dz of the
+ * spreading kernel of width w cells used for grids oversampled by
+ * `oversample`, at nxi points (host, double).  Returns FC2_OK or
+ * FC2_ERR_INVALID_ARG. */
+fc2_status fc2_kernel_ft(int w, int oversample, const double* xi, int64_t nxi, double* out);
+
+/* Spreading kernel phi(z) at nz points (host, double). */
+fc2_status fc2_kernel_eval(int w, int oversample, const double* z, int64_t nz, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FC2_H */

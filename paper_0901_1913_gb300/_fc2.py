@@ -1,0 +1,239 @@
+"""ctypes binding of libfc2 (the C ABI declared in include/fc2.h).
+
+Argument marshalling only: every step of the periodogram runs in the CUDA
+library.  The library is built in-tree by ``paper_0901_1913_gb300.build``; if
+it is missing this module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfc2.so")
+MAX_H = 16
+
+FC2_OK, FC2_ERR_INVALID_ARG, FC2_ERR_CUDA, FC2_ERR_OOM, FC2_ERR_TIMEOUT, \
+    FC2_ERR_UNSUPPORTED, FC2_ERR_NUMERIC = range(7)
+FC2_PREC_FP64, FC2_PREC_MIXED = 0, 1
+PREC = {"fp64": FC2_PREC_FP64, "mixed": FC2_PREC_MIXED}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("kernel_width", ctypes.c_int), ("top_k", ctypes.c_int),
+                ("alias_tau", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
+                ("device", ctypes.c_int), ("inputs_on_device", ctypes.c_int),
+                ("outputs_on_device", ctypes.c_int)]
+
+
+class Best(ctypes.Structure):
+    _fields_ = [("j", ctypes.c_int64), ("f", ctypes.c_double), ("dchi2", ctypes.c_double),
+                ("H", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("A", ctypes.c_double * (2 * MAX_H + 1))]
+
+    def as_dict(self):
+        m = 2 * self.H + 1
+        return dict(j=int(self.j), f=float(self.f), dchi2=float(self.dchi2), H=int(self.H),
+                    flags=int(self.flags), A=np.array(self.A[:m]))
+
+
+class Fc2Error(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+
+
+_lib = None
+_lock = threading.Lock()
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def load():
+    """Load libfc2.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfc2.so not built ({LIB_PATH}); run paper_0901_1913_gb300.build")
+        lib = ctypes.CDLL(LIB_PATH)
+        i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        lib.fc2_options_default.argtypes = [ctypes.POINTER(Options)]
+        lib.fc2_options_default.restype = None
+        lib.fc2_plan_create.argtypes = [_P, _P, _P, i64, i32, dbl, dbl, i64, i32,
+                                        ctypes.POINTER(Options), ctypes.POINTER(_P)]
+        lib.fc2_plan_create.restype = i32
+        lib.fc2_execute.argtypes = [_P, _P, _P, _P, _P]
+        lib.fc2_execute.restype = i32
+        lib.fc2_execute_batched.argtypes = [i64, _P, _P, _P, _P, _P, _P, _P, _P, i32,
+                                            ctypes.POINTER(Options), _P, _P]
+        lib.fc2_execute_batched.restype = i32
+        lib.fc2_backward.argtypes = [_P, i32, _P, _P, _P, _P, _P, _P, _P]
+        lib.fc2_backward.restype = i32
+        lib.fc2_plan_destroy.argtypes = [_P]
+        lib.fc2_plan_destroy.restype = None
+        lib.fc2_status_string.argtypes = [i32]
+        lib.fc2_status_string.restype = ctypes.c_char_p
+        lib.fc2_grid_size.argtypes = [i64, i32]
+        lib.fc2_grid_size.restype = i64
+        lib.fc2_default_width.argtypes = [i32, i32]
+        lib.fc2_default_width.restype = i32
+        lib.fc2_kernel_ft.argtypes = [i32, i32, _P, i64, _P]
+        lib.fc2_kernel_ft.restype = i32
+        lib.fc2_kernel_eval.argtypes = [i32, i32, _P, i64, _P]
+        lib.fc2_kernel_eval.restype = i32
+        lib.fc2_debug_flag_count.argtypes = [_P]
+        lib.fc2_debug_flag_count.restype = i64
+        lib.fc2_debug_spectra.argtypes = [_P, _P, _P]
+        lib.fc2_debug_spectra.restype = i32
+        lib.fc2_debug_counts.argtypes = [_P, _P]
+        lib.fc2_debug_counts.restype = None
+        lib.fc2_stage_timing.argtypes = [_P, i32]
+        lib.fc2_stage_timing.restype = i32
+        lib.fc2_stage_times.argtypes = [_P, _P, _P, _P]
+        lib.fc2_stage_times.restype = i32
+        lib.fc2_debug_t0.argtypes = [_P]
+        lib.fc2_debug_t0.restype = dbl
+        _lib = lib
+        return lib
+
+
+def status_string(code):
+    return load().fc2_status_string(int(code)).decode()
+
+
+def _check(rc, where):
+    if rc != FC2_OK:
+        raise Fc2Error(rc, where)
+
+
+def _ptr(a):
+    """Address of a numpy array (host) or a torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _is_dev(a):
+    return (not isinstance(a, np.ndarray)) and getattr(a, "is_cuda", False)
+
+
+def make_options(prec="fp64", kernel_width=0, top_k=0, alias_tau=0.0, stream=None, device=0,
+                 inputs_on_device=False, outputs_on_device=False):
+    o = Options()
+    load().fc2_options_default(ctypes.byref(o))
+    o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    o.kernel_width = int(kernel_width)
+    o.top_k = int(top_k)
+    o.alias_tau = float(alias_tau)
+    o.cuda_stream = stream
+    o.device = int(device)
+    o.inputs_on_device = int(bool(inputs_on_device))
+    o.outputs_on_device = int(bool(outputs_on_device))
+    return o
+
+
+class Plan:
+    """Owns an fc2_plan.  t, x, sigma: float64 numpy arrays (copied to the
+    device) or float64 CUDA tensors (borrowed; keep them alive)."""
+
+    def __init__(self, t, x, sigma, H, f_min, df, N, oversample=2, prec="fp64",
+                 kernel_width=0, top_k=8, alias_tau=0.0, stream=None, device=0):
+        lib = load()
+        dev = _is_dev(t)
+        if not dev:
+            t = np.ascontiguousarray(t, dtype=np.float64)
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        self._keep = (t, x, sigma)
+        self.n = int(t.shape[0])
+        self.H, self.N, self.top_k = int(H), int(N), int(top_k or 8)
+        self.f_min, self.df = float(f_min), float(df)
+        self.opt = make_options(prec, kernel_width, self.top_k, alias_tau, stream, device,
+                                inputs_on_device=dev)
+        h = _P()
+        rc = lib.fc2_plan_create(_ptr(t), _ptr(x), _ptr(sigma), self.n, self.H, self.f_min,
+                                 self.df, self.N, int(oversample), ctypes.byref(self.opt),
+                                 ctypes.byref(h))
+        _check(rc, "fc2_plan_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().fc2_plan_destroy(self.h)
+            self.h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def execute(self, dchi2=None, want_records=True):
+        """Run the periodogram.  dchi2: optional preallocated [H, N] float64
+        output (numpy, or CUDA tensor when the plan writes device outputs).
+        Returns (dchi2, best[H], peaks[top_k], chi2_0)."""
+        lib = load()
+        if dchi2 is None:
+            dchi2 = np.empty((self.H, self.N), dtype=np.float64)
+        best = (Best * self.H)()
+        peaks = (Best * self.top_k)()
+        chi0 = ctypes.c_double()
+        rc = self._execute(lib, dchi2, best if want_records else None,
+                           peaks if want_records else None, chi0)
+        _check(rc, "fc2_execute")
+        return dchi2, [b.as_dict() for b in best], [p.as_dict() for p in peaks], chi0.value
+
+    def _execute(self, lib, dchi2, best, peaks, chi0):
+        return lib.fc2_execute(self.h, _ptr(dchi2), ctypes.cast(best, _P) if best else None,
+                               ctypes.cast(peaks, _P) if peaks else None, ctypes.byref(chi0))
+
+    @property
+    def flag_count(self):
+        return int(load().fc2_debug_flag_count(self.h))
+
+    @property
+    def counts(self):
+        """(bins re-solved in double, bins recomputed from exact sums, of which
+        all-double) in the last execute."""
+        c = np.zeros(3, dtype=np.int64)
+        load().fc2_debug_counts(self.h, c.ctypes.data)
+        return tuple(int(v) for v in c)
+
+    def spectra(self):
+        G = 3 * self.H
+        re = np.empty(G * self.N)
+        im = np.empty(G * self.N)
+        _check(load().fc2_debug_spectra(self.h, re.ctypes.data, im.ctypes.data), "spectra")
+        return (re + 1j * im).reshape(G, self.N)
+
+    def stage_timing(self, enable=True):
+        _check(load().fc2_stage_timing(self.h, int(enable)), "fc2_stage_timing")
+
+    def stage_times(self):
+        """(mean ms per execute of [spread, fft, assemble, fix-up, peaks],
+        kernels launched by the last execute, FFT algorithmic bytes)."""
+        ms = np.zeros(5)
+        nl = np.zeros(1, dtype=np.int64)
+        fb = np.zeros(1)
+        _check(load().fc2_stage_times(self.h, ms.ctypes.data, nl.ctypes.data, fb.ctypes.data),
+               "fc2_stage_times")
+        return ms, int(nl[0]), float(fb[0])
+
+    @property
+    def t0(self):
+        return float(load().fc2_debug_t0(self.h))
+
+
+def periodogram(t, x, sigma, H, f_min, df, N, oversample=2, prec="fp64", **kw):
+    """One-shot: Delta chi^2 [H, N], best records, peak records, chi2_0."""
+    with Plan(t, x, sigma, H, f_min, df, N, oversample, prec, **kw) as p:
+        return p.execute()

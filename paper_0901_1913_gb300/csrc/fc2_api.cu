@@ -1,0 +1,452 @@
+// fc2_api.cu -- the C ABI of libfc2: validation, plan lifetime, buffer
+// management and the order of kernel launches.  No kernel arithmetic here.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "fc2_common.cuh"
+#include "fc2_internal.h"
+
+using namespace fc2;
+
+namespace {
+
+struct Guard {  // returns FC2_ERR_CUDA on the first failing runtime call
+    cudaError_t e = cudaSuccess;
+    bool ok(cudaError_t r) {
+        if (r != cudaSuccess && e == cudaSuccess) e = r;
+        return e == cudaSuccess;
+    }
+};
+
+fc2_status map_err(cudaError_t e) {
+    if (e == cudaSuccess) return FC2_OK;
+    if (e == cudaErrorMemoryAllocation) return FC2_ERR_OOM;
+    return FC2_ERR_CUDA;
+}
+
+template <typename P>
+cudaError_t dalloc(P** ptr, size_t bytes, cudaStream_t s) {
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    return cudaMallocAsync((void**)ptr, bytes, s);
+}
+
+template <typename P>
+void dfree(P*& ptr, cudaStream_t s) {
+    if (ptr) cudaFreeAsync((void*)ptr, s);
+    ptr = nullptr;
+}
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+void free_plan_memory(fc2_plan_s* p) {
+    cudaStream_t s = p->stream;
+    if (!p->borrowed) { dfree(p->d_t, s); dfree(p->d_x, s); dfree(p->d_sigma, s); }
+    dfree(p->d_scal, s); dfree(p->d_status, s); dfree(p->d_perm, s);
+    dfree(p->d_tau, s); dfree(p->d_wq, s); dfree(p->d_wp, s);
+    dfree(p->d_key, s); dfree(p->d_dlt, s); dfree(p->d_cs, s);
+    dfree(p->d_grid[0], s); dfree(p->d_grid[1], s); dfree(p->d_spec, s);
+    dfree(p->d_dec, s); dfree(p->d_twlo, s); dfree(p->d_twhi, s); dfree(p->d_twst, s);
+    dfree(p->d_dchi2, s); dfree(p->d_flag_list, s); dfree(p->d_flag_count, s);
+    dfree(p->d_L, s); dfree(p->d_red, s); dfree(p->d_best, s); dfree(p->d_part, s);
+    dfree(p->d_phA, s); dfree(p->d_phB, s); dfree(p->d_wq32, s); dfree(p->d_wp32, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma, int64_t n,
+                           int H, double f_min, double df, int64_t N, int oversample,
+                           const fc2_options* opt_in, fc2_plan* out) {
+    if (!out) return FC2_ERR_INVALID_ARG;
+    *out = nullptr;
+    fc2_options opt;
+    if (opt_in) opt = *opt_in; else fc2_options_default(&opt);
+    if (!t || !x || !sigma || n < 1 || n > (1ll << 31) - 1) return FC2_ERR_INVALID_ARG;
+    if (H < 1 || H > FC2_MAX_H) return FC2_ERR_INVALID_ARG;
+    if (!(isfinite(f_min) && f_min >= 0.0) || !finite_pos(df) || N < 2) return FC2_ERR_INVALID_ARG;
+    if (!isfinite(f_min + (double)(N - 1) * df)) return FC2_ERR_INVALID_ARG;
+    if (oversample < 2 || oversample > 64) return FC2_ERR_INVALID_ARG;
+    if (opt.prec != FC2_PREC_FP64 && opt.prec != FC2_PREC_MIXED) return FC2_ERR_INVALID_ARG;
+    if (opt.kernel_width != 0 && (opt.kernel_width < 2 || opt.kernel_width > 16))
+        return FC2_ERR_INVALID_ARG;
+    if (opt.top_k < 0 || opt.top_k > 64 || opt.alias_tau < 0.0) return FC2_ERR_INVALID_ARG;
+    if (H > 8) return FC2_ERR_UNSUPPORTED;
+    const int64_t M = fc2_grid_size(N, oversample);
+    if (M == 0) return FC2_ERR_INVALID_ARG;
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return FC2_ERR_CUDA;
+    if (opt.device < 0 || opt.device >= ndev) return FC2_ERR_INVALID_ARG;
+    if (cudaSetDevice(opt.device) != cudaSuccess) return FC2_ERR_CUDA;
+
+    fc2_plan_s* p = new (std::nothrow) fc2_plan_s();
+    if (!p) return FC2_ERR_OOM;
+    p->opt = opt;
+    p->device = opt.device;
+    if (opt.cuda_stream) {
+        p->stream = (cudaStream_t)opt.cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete p;
+            return FC2_ERR_CUDA;
+        }
+        p->own_stream = true;
+    }
+    cudaStream_t s = p->stream;
+    p->n = n; p->H = H; p->f_min = f_min; p->df = df; p->N = N; p->oversample = oversample;
+    p->M = M;
+    p->logM = 0;
+    while ((1ll << p->logM) < M) ++p->logM;
+    p->G = 3 * H;
+    p->fp64 = (opt.prec == FC2_PREC_FP64);
+    p->w = opt.kernel_width ? opt.kernel_width : default_width(p->fp64, oversample);
+    const double sig_eff = (double)M / (double)N;
+    p->beta = 0.97 * M_PI * (1.0 - 0.5 / sig_eff) * (double)p->w;
+    p->tau = opt.alias_tau > 0.0 ? opt.alias_tau : (p->fp64 ? 1e-9 : 1e-6);
+    p->top_k = opt.top_k ? opt.top_k : 8;
+    plan_fft_passes(p);
+
+    const size_t tsz = p->fp64 ? 8 : 4;
+    const size_t csz = 2 * tsz;
+    const int G = p->G;
+    // memory estimate
+    size_t need = 0;
+    need += (size_t)n * 8 * 6 + (size_t)n * 4;
+    need += (size_t)G * n * (4 + tsz + csz);
+    need += 2 * (size_t)G * M * csz;
+    need += (size_t)G * N * csz + (size_t)N * tsz + (size_t)H * N * 8 + (size_t)N * 4;
+    size_t freeb = 0, totalb = 0;
+    if (cudaMemGetInfo(&freeb, &totalb) == cudaSuccess && need > freeb) {
+        if (p->own_stream) cudaStreamDestroy(p->stream);
+        delete p;
+        return FC2_ERR_OOM;
+    }
+
+    Guard g;
+    if (opt.inputs_on_device) {
+        p->d_t = (double*)t; p->d_x = (double*)x; p->d_sigma = (double*)sigma;
+        p->borrowed = true;
+    } else {
+        g.ok(dalloc(&p->d_t, n * 8, s)) && g.ok(dalloc(&p->d_x, n * 8, s)) &&
+            g.ok(dalloc(&p->d_sigma, n * 8, s));
+        if (g.e == cudaSuccess) {
+            g.ok(cudaMemcpyAsync(p->d_t, t, n * 8, cudaMemcpyHostToDevice, s));
+            g.ok(cudaMemcpyAsync(p->d_x, x, n * 8, cudaMemcpyHostToDevice, s));
+            g.ok(cudaMemcpyAsync(p->d_sigma, sigma, n * 8, cudaMemcpyHostToDevice, s));
+        }
+    }
+    const size_t grid_bytes = (size_t)G * M * csz;
+    const size_t sort_b = sort_scratch_bytes(n);
+    const size_t keysort_b = (size_t)n * (8 * 2 + 4 * 3 + tsz + csz) + 4096 +
+                             (size_t)((n + 2047) / 2048) * 256 * 4;
+    const size_t red_b = std::max({peaks_scratch_bytes(N, H, p->top_k), sort_b,
+                                   moments_scratch_bytes(n), (size_t)8192});
+    p->red_bytes = red_b;
+    g.ok(dalloc(&p->d_scal, SC_COUNT * 8, s)) && g.ok(dalloc(&p->d_status, 16, s)) &&
+        g.ok(dalloc(&p->d_perm, n * 4, s)) && g.ok(dalloc(&p->d_tau, n * 8, s)) &&
+        g.ok(dalloc(&p->d_wq, n * 8, s)) && g.ok(dalloc(&p->d_wp, n * 8, s)) &&
+        g.ok(dalloc(&p->d_key, (size_t)G * n * 4, s)) &&
+        g.ok(dalloc(&p->d_dlt, (size_t)G * n * tsz, s)) &&
+        g.ok(dalloc(&p->d_cs, (size_t)G * n * csz, s)) &&
+        g.ok(dalloc(&p->d_grid[0], grid_bytes, s)) &&
+        g.ok(dalloc(&p->d_grid[1], std::max(grid_bytes, keysort_b), s)) &&
+        g.ok(dalloc(&p->d_spec, (size_t)G * N * csz, s)) &&
+        g.ok(dalloc(&p->d_dec, (size_t)N * tsz, s)) &&
+        g.ok(dalloc(&p->d_twlo, (size_t)(1ll << ((p->logM + 1) / 2)) * csz, s)) &&
+        g.ok(dalloc(&p->d_twhi, (size_t)(M >> ((p->logM + 1) / 2)) * csz, s)) &&
+        g.ok(dalloc(&p->d_twst, (size_t)(8 * 4096 + 256) * csz, s)) &&
+        g.ok(dalloc(&p->d_dchi2, (size_t)H * N * 8, s)) &&
+        g.ok(dalloc(&p->d_flag_list, (size_t)N * 4 * 2, s)) &&
+        g.ok(dalloc(&p->d_flag_count, 16, s)) && g.ok(dalloc(&p->d_L, (size_t)G * 8, s)) &&
+        g.ok(dalloc(&p->d_red, red_b, s)) &&
+        g.ok(dalloc(&p->d_best, (size_t)(H + p->top_k) * sizeof(fc2_best), s));
+    p->flag_cap = N;
+    p->exact_cap = std::max<int64_t>(2048, H + p->top_k);
+    g.ok(dalloc(&p->d_part, exact_scratch_bytes(n, H, p->exact_cap), s)) &&
+        g.ok(dalloc(&p->d_phA, (size_t)n * 8, s)) && g.ok(dalloc(&p->d_phB, (size_t)n * 8, s)) &&
+        g.ok(dalloc(&p->d_wq32, (size_t)n * 4, s)) && g.ok(dalloc(&p->d_wp32, (size_t)n * 4, s));
+    if (g.e != cudaSuccess) {
+        fc2_status st = map_err(g.e);
+        free_plan_memory(p);
+        cudaStreamSynchronize(s);
+        if (p->own_stream) cudaStreamDestroy(p->stream);
+        delete p;
+        return st;
+    }
+    g.ok(cudaMemsetAsync(p->d_status, 0, 16, s));
+    g.ok(launch_moments_long(p->d_t, p->d_x, p->d_sigma, n, p->d_scal, p->d_status, p->d_red, s));
+    int status = 0;
+    g.ok(cudaMemcpyAsync(p->scal, p->d_scal, sizeof(p->scal), cudaMemcpyDeviceToHost, s));
+    g.ok(cudaMemcpyAsync(&status, p->d_status, 4, cudaMemcpyDeviceToHost, s));
+    g.ok(cudaStreamSynchronize(s));
+    fc2_status st = FC2_OK;
+    if (g.e != cudaSuccess) st = map_err(g.e);
+    else if (status != 0) st = (fc2_status)status;
+    if (st == FC2_OK) {
+        // Time origin: the earliest sample, moved back by (w/2 + 1) cells of
+        // the k = 1 grid so no sample's spreading window reaches below cell 0.
+        const double back = (0.5 * p->w + 1.0) / ((double)M * df);
+        p->scal[SC_T0] -= back;
+        p->scal[SC_TAUMAX] += back;
+        g.ok(cudaMemcpyAsync(p->d_scal, p->scal, sizeof(p->scal), cudaMemcpyHostToDevice, s));
+        const int32_t* perm = nullptr;
+        if (p->scal[SC_SORTED] == 0.0) {
+            g.ok(sort_by_time(p->d_t, n, p->d_perm, p->d_grid[1], std::max(grid_bytes, keysort_b), s));
+            perm = p->d_perm;
+        }
+        p->has_perm = (perm != nullptr);
+        g.ok(launch_gather_sorted(p->d_t, p->d_x, p->d_sigma, perm, n, p->d_scal, p->d_tau,
+                                  p->d_wq, p->d_wp, s));
+        g.ok(launch_phase_fx(p, s));
+        // geometry of each transform
+        const int LOGR1 = p->passes[0].logR;
+        const int64_t S1 = M >> LOGR1;
+        const int64_t tile = (M >= 4096) ? 1024 : 128;
+        const int64_t unit = std::max(S1, tile);
+        p->geom.resize(G);
+        std::vector<int64_t> Lh(G);
+        for (int gi = 0; gi < G; ++gi) {
+            GridGeom& gg = p->geom[gi];
+            if (gi < 2 * H) { gg.k = gi + 1; gg.kind = 0; } else { gg.k = gi - 2 * H + 1; gg.kind = 1; }
+            const double c = (double)gg.k * df;
+            const double pmax = c * p->scal[SC_TAUMAX];
+            const double cells = pmax * (double)M;
+            if (!(pmax < 1.0) || cells + p->w + 2.0 >= (double)M) {
+                gg.wraps = (pmax >= 1.0) ? 1 : 0;
+                gg.L = M;
+            } else {
+                gg.wraps = 0;
+                int64_t L = (int64_t)floor(cells) + p->w + 3;
+                L = ((L + unit - 1) / unit) * unit;
+                gg.L = std::min(L, M);
+            }
+            Lh[gi] = gg.L;
+        }
+        g.ok(cudaMemcpyAsync(p->d_L, Lh.data(), G * 8, cudaMemcpyHostToDevice, s));
+        // Algorithmic bytes of the transform: each pass reads its input once
+        // (the first pass only the rows that hold samples) and writes its output
+        // once (the last pass only the N kept modes).
+        {
+            double fb = 0.0;
+            const int P = (int)p->passes.size();
+            for (int pi = 0; pi < P; ++pi) {
+                const int64_t R = 1ll << p->passes[pi].logR, Sp = M / R;
+                for (int gi = 0; gi < G; ++gi) {
+                    int64_t rd = M;
+                    if (pi == 0) rd = std::min(R, (Lh[gi] + Sp - 1) / Sp) * Sp;
+                    const int64_t wr = (pi == P - 1) ? N : M;
+                    fb += (double)(rd + wr) * (double)csz;
+                }
+            }
+            p->fft_bytes = fb;
+        }
+        g.ok(init_twiddles(p, s));
+        g.ok(init_deconv(p, s));  // synchronises
+        if (g.e != cudaSuccess) st = map_err(g.e);
+    }
+    if (st != FC2_OK) {
+        cudaStreamSynchronize(s);
+        free_plan_memory(p);
+        cudaStreamSynchronize(s);
+        if (p->own_stream) cudaStreamDestroy(p->stream);
+        delete p;
+        return st;
+    }
+    *out = p;
+    return FC2_OK;
+}
+
+// Kernel launches per stage (for the launch count the benchmark reports).
+static int64_t launches_front(const fc2_plan_s* p) {
+    int64_t n = 1 + 1 + (int64_t)p->passes.size() + 1 + (p->fp64 ? 0 : 1);  // phase, spread, fft, assemble(+resolve)
+    int bits = 0;
+    while ((1ll << bits) < p->M + 2 * p->w + 2) ++bits;
+    for (auto& g : p->geom)
+        if (g.wraps) n += 2 + 3 * ((bits + 7) / 8);
+    return n;
+}
+
+static void rec(fc2_plan_s* p, int i) {
+    if (p->timing) cudaEventRecord(p->ev[i], p->stream);
+}
+
+static fc2_status run_pipeline(fc2_plan_s* p) {
+    cudaStream_t s = p->stream;
+    Guard g;
+    rec(p, 0);
+    g.ok(launch_phase(p, s)) && g.ok(launch_spread(p, s));
+    rec(p, 1);
+    g.ok(launch_fft(p, s));
+    rec(p, 2);
+    g.ok(launch_assemble(p, s));
+    rec(p, 3);
+    int32_t fc[2] = {0, 0};
+    g.ok(cudaMemcpyAsync(fc, p->d_flag_count, 8, cudaMemcpyDeviceToHost, s));
+    g.ok(cudaStreamSynchronize(s));
+    if (g.e != cudaSuccess) return map_err(g.e);
+    p->last_flag_count = fc[0];
+    p->last_resolve_count = fc[1];
+    if (fc[1] > p->flag_cap) return FC2_ERR_NUMERIC;
+    const int64_t nfix = fc[0];
+    if (nfix > p->flag_cap) return FC2_ERR_NUMERIC;
+    g.ok(launch_fixup(p, nfix, s));
+    rec(p, 4);
+    g.ok(launch_peaks(p, s));
+    rec(p, 5);
+    const int64_t cap = p->exact_cap;
+    const int64_t r1 = (nfix + cap - 1) / cap, r2 = (p->last_exact2_count + cap - 1) / cap;
+    p->launches = launches_front(p) + 2 * (r1 + r2) + 4;
+    return map_err(g.e);
+}
+
+fc2_status fc2_execute(fc2_plan p, double* dchi2, fc2_best* best, fc2_best* peaks,
+                       double* chi2_0) {
+    if (!p) return FC2_ERR_INVALID_ARG;
+    if (cudaSetDevice(p->device) != cudaSuccess) return FC2_ERR_CUDA;
+    cudaStream_t s = p->stream;
+    // A device output buffer is written in place; otherwise results are copied.
+    double* own = p->d_dchi2;
+    bool direct = false;
+    if (dchi2) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, dchi2) == cudaSuccess && at.type == cudaMemoryTypeDevice &&
+            at.device == p->device) {
+            p->d_dchi2 = dchi2;
+            direct = true;
+        }
+        cudaGetLastError();
+    }
+    fc2_status st = run_pipeline(p);
+    p->d_dchi2 = own;
+    if (st != FC2_OK) return st;
+    Guard g;
+    const size_t bytes = (size_t)p->H * p->N * 8;
+    if (dchi2 && !direct)
+        g.ok(cudaMemcpyAsync(dchi2, p->d_dchi2, bytes, cudaMemcpyDefault, s));
+    std::vector<fc2_best> recs((size_t)(p->H + p->top_k));
+    int status = 0;
+    if (best || peaks)
+        g.ok(cudaMemcpyAsync(recs.data(), p->d_best, recs.size() * sizeof(fc2_best),
+                             cudaMemcpyDeviceToHost, s));
+    g.ok(cudaMemcpyAsync(&status, p->d_status, 4, cudaMemcpyDeviceToHost, s));
+    g.ok(cudaStreamSynchronize(s));
+    if (g.e != cudaSuccess) return map_err(g.e);
+    if (status != 0) return (fc2_status)status;
+    if (best) memcpy(best, recs.data(), sizeof(fc2_best) * p->H);
+    if (peaks) memcpy(peaks, recs.data() + p->H, sizeof(fc2_best) * p->top_k);
+    if (chi2_0) *chi2_0 = p->scal[SC_CHI0];
+    if (p->timing) {
+        for (int i = 0; i < 5; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, p->ev[i], p->ev[i + 1]);
+            p->stage_ms[i] += ms;
+        }
+        p->stage_n += 1;
+    }
+    return FC2_OK;
+}
+
+void fc2_plan_destroy(fc2_plan p) {
+    if (!p) return;
+    cudaSetDevice(p->device);
+    cudaStreamSynchronize(p->stream);
+    for (int i = 0; i < 8; ++i)
+        if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+    free_plan_memory(p);
+    cudaStreamSynchronize(p->stream);
+    if (p->own_stream) cudaStreamDestroy(p->stream);
+    delete p;
+}
+
+fc2_status fc2_execute_batched(int64_t C, const int64_t* offsets, const double* t,
+                               const double* x, const double* sigma, const int* H,
+                               const double* f_min, const double* df, const int64_t* N,
+                               int oversample, const fc2_options* opt, float* dchi2,
+                               fc2_best* peaks) {
+    (void)C; (void)offsets; (void)t; (void)x; (void)sigma; (void)H; (void)f_min; (void)df;
+    (void)N; (void)oversample; (void)opt; (void)dchi2; (void)peaks;
+    return FC2_ERR_UNSUPPORTED;
+}
+
+fc2_status fc2_backward(fc2_plan p, int K, const int64_t* peak_j, const double* grad_out,
+                        double* f_refined, double* dchi2_refined, double* d_df, double* d_dx,
+                        double* d_dsigma) {
+    (void)p; (void)K; (void)peak_j; (void)grad_out; (void)f_refined; (void)dchi2_refined;
+    (void)d_df; (void)d_dx; (void)d_dsigma;
+    return FC2_ERR_UNSUPPORTED;
+}
+
+/* Diagnostics (not in the public header): number of bins the last execute
+ * sent to the exact fix-up, and the spectra of the last execute. */
+int64_t fc2_debug_flag_count(fc2_plan p) { return p ? p->last_flag_count : -1; }
+
+/* Counts of the last execute: [0] bins re-solved in double (mixed path),
+ * [1] bins recomputed from exact sums (tier 1), [2] of those, bins that
+ * needed all-double sums (tier 2). */
+void fc2_debug_counts(fc2_plan p, int64_t* out3) {
+    if (!p || !out3) return;
+    out3[0] = p->last_resolve_count;
+    out3[1] = p->last_flag_count;
+    out3[2] = p->last_exact2_count;
+}
+
+fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im) {
+    if (!p || !re || !im) return FC2_ERR_INVALID_ARG;
+    const size_t cnt = (size_t)p->G * p->N;
+    std::vector<char> buf(cnt * (p->fp64 ? 16 : 8));
+    std::vector<char> dec((size_t)p->N * (p->fp64 ? 8 : 4));
+    if (cudaMemcpy(buf.data(), p->d_spec, buf.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FC2_ERR_CUDA;
+    if (cudaMemcpy(dec.data(), p->d_dec, dec.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FC2_ERR_CUDA;
+    for (size_t i = 0; i < cnt; ++i) {
+        size_t j = i % (size_t)p->N;
+        if (p->fp64) {
+            const double* b = (const double*)buf.data();
+            double d = ((const double*)dec.data())[j];
+            re[i] = b[2 * i] * d; im[i] = b[2 * i + 1] * d;
+        } else {
+            const float* b = (const float*)buf.data();
+            double d = ((const float*)dec.data())[j];
+            re[i] = b[2 * i] * d; im[i] = b[2 * i + 1] * d;
+        }
+    }
+    return FC2_OK;
+}
+
+double fc2_debug_t0(fc2_plan p) { return p ? p->scal[SC_T0] : 0.0; }
+
+/* Stage timing: while enabled, each execute records CUDA events on the plan's
+ * stream around (0) phase reduction + spreading, (1) FFT passes, (2) assembly
+ * and solve, (3) exact fix-up, (4) peaks and coefficients; fc2_stage_times
+ * returns the mean milliseconds per execute of each stage since enabling.
+ * Also reports the kernels launched by the last execute and the algorithmic
+ * bytes of the FFT passes. */
+fc2_status fc2_stage_timing(fc2_plan p, int enable) {
+    if (!p) return FC2_ERR_INVALID_ARG;
+    if (enable && !p->ev[0])
+        for (int i = 0; i < 8; ++i)
+            if (cudaEventCreate(&p->ev[i]) != cudaSuccess) return FC2_ERR_CUDA;
+    p->timing = enable != 0;
+    for (int i = 0; i < 8; ++i) p->stage_ms[i] = 0.0;
+    p->stage_n = 0;
+    return FC2_OK;
+}
+
+fc2_status fc2_stage_times(fc2_plan p, double* ms5, int64_t* launches, double* fft_bytes) {
+    if (!p) return FC2_ERR_INVALID_ARG;
+    if (ms5)
+        for (int i = 0; i < 5; ++i) ms5[i] = p->stage_n ? p->stage_ms[i] / (double)p->stage_n : 0.0;
+    if (launches) *launches = p->launches;
+    if (fft_bytes) *fft_bytes = p->fft_bytes;
+    return FC2_OK;
+}
+
+}  // extern "C"

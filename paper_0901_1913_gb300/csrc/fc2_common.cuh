@@ -1,0 +1,129 @@
+// fc2_common.cuh -- shared device helpers of libfc2 (complex arithmetic, small
+// DFTs, the spreading kernel, status reporting).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/fc2.h"
+
+#define FC2_HD __host__ __device__ __forceinline__
+#define FC2_D __device__ __forceinline__
+
+namespace fc2 {
+
+template <typename T>
+struct alignas(2 * sizeof(T)) cpx {
+    T x, y;
+};
+
+template <typename T> FC2_HD cpx<T> mk(T a, T b) { cpx<T> r; r.x = a; r.y = b; return r; }
+template <typename T> FC2_HD cpx<T> add(cpx<T> a, cpx<T> b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename T> FC2_HD cpx<T> sub(cpx<T> a, cpx<T> b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename T> FC2_HD cpx<T> mul(cpx<T> a, cpx<T> b) {
+    return mk(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+template <typename T> FC2_HD cpx<T> mul_i(cpx<T> a) { return mk(-a.y, a.x); }   // i * a
+template <typename T> FC2_HD cpx<T> mul_mi(cpx<T> a) { return mk(a.y, -a.x); }  // -i * a
+template <typename T> FC2_HD cpx<T> scale(cpx<T> a, T s) { return mk(a.x * s, a.y * s); }
+template <typename T> FC2_HD cpx<T> conj(cpx<T> a) { return mk(a.x, -a.y); }
+
+// Compile-time e^{+2 pi i k / Q} for Q | 16, from exact closed forms.
+template <typename T>
+FC2_HD cpx<T> root16(int k) {
+    // k in [0, 16); cos/sin of k*pi/8
+    const T c1 = (T)0.92387953251128675613;  // cos(pi/8)
+    const T s1 = (T)0.38268343236508977173;  // sin(pi/8)
+    const T r2 = (T)0.70710678118654752440;  // cos(pi/4)
+    const T cs[5] = {(T)1, c1, r2, s1, (T)0};
+    int q = k & 15;
+    int quad = q >> 2, rem = q & 3;
+    T c = cs[rem], s = cs[4 - rem];
+    // rotate by quad * pi/2
+    if (quad == 0) return mk(c, s);
+    if (quad == 1) return mk(-s, c);
+    if (quad == 2) return mk(-c, -s);
+    return mk(s, -c);
+}
+
+// In-register DFT of length Q (power of two <= 16), sign +: X_k = sum_n x_n e^{+2 pi i n k / Q}.
+template <typename T, int Q>
+struct SmallDFT {
+    static FC2_D void run(cpx<T>* v) {
+        cpx<T> e[Q / 2], o[Q / 2];
+#pragma unroll
+        for (int i = 0; i < Q / 2; ++i) { e[i] = v[2 * i]; o[i] = v[2 * i + 1]; }
+        SmallDFT<T, Q / 2>::run(e);
+        SmallDFT<T, Q / 2>::run(o);
+#pragma unroll
+        for (int k = 0; k < Q / 2; ++k) {
+            cpx<T> t;
+            if (k == 0) t = o[k];
+            else if (4 * k == Q) t = mul_i(o[k]);
+            else t = mul(o[k], root16<T>(k * (16 / Q)));
+            v[k] = add(e[k], t);
+            v[k + Q / 2] = sub(e[k], t);
+        }
+    }
+};
+template <typename T>
+struct SmallDFT<T, 1> { static FC2_D void run(cpx<T>*) {} };
+template <typename T>
+struct SmallDFT<T, 2> {
+    static FC2_D void run(cpx<T>* v) {
+        cpx<T> a = v[0], b = v[1];
+        v[0] = add(a, b);
+        v[1] = sub(a, b);
+    }
+};
+template <typename T>
+struct SmallDFT<T, 4> {
+    static FC2_D void run(cpx<T>* v) {
+        cpx<T> a = add(v[0], v[2]), b = sub(v[0], v[2]);
+        cpx<T> c = add(v[1], v[3]), d = sub(v[1], v[3]);
+        v[0] = add(a, c);
+        v[2] = sub(a, c);
+        v[1] = add(b, mul_i(d));
+        v[3] = sub(b, mul_i(d));
+    }
+};
+
+// Exponential-of-semicircle spreading kernel (Barnett, Magland & af Klinteberg,
+// SIAM J. Sci. Comput. 41 (2019) C479):  phi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1))
+// for |z| < w/2, zero outside.  beta = 0.97 pi (1 - 1/(2 sigma)) w.
+FC2_HD double es_beta(int w, int oversample) {
+    return 0.97 * 3.14159265358979323846 * (1.0 - 0.5 / (double)oversample) * (double)w;
+}
+
+template <typename T>
+FC2_D T es_kernel(T z, T inv_half_w, T beta) {
+    T s = z * inv_half_w;
+    T a = (T)1 - s * s;
+    return a > (T)0 ? exp(beta * (sqrt(a) - (T)1)) : (T)0;
+}
+template <>
+FC2_D float es_kernel<float>(float z, float inv_half_w, float beta) {
+    float s = z * inv_half_w;
+    float a = 1.0f - s * s;
+    return a > 0.0f ? expf(beta * (sqrtf(a) - 1.0f)) : 0.0f;
+}
+
+// Device status word: first error code wins.
+FC2_D void set_status(int* st, int code) {
+    if (st) atomicCAS(st, 0, code);
+}
+
+// Neumaier-compensated accumulator.
+template <typename T>
+struct CompSum {
+    T s, c;
+    FC2_D void init() { s = (T)0; c = (T)0; }
+    FC2_D void add(T v) {
+        T t = s + v;
+        c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
+        s = t;
+    }
+    FC2_D T val() const { return s + c; }
+};
+
+}  // namespace fc2

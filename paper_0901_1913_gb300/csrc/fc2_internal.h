@@ -1,0 +1,165 @@
+// fc2_internal.h -- plan object and kernel launchers shared by the libfc2
+// translation units.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/fc2.h"
+
+namespace fc2 {
+
+// Scalars per curve written by the moments kernel (doubles).
+enum ScalarSlot {
+    SC_W = 0,        // sum w
+    SC_XBAR = 1,     // weighted mean (Sec. 3b)
+    SC_CHI0 = 2,     // chi2_0 (Sec. 3c)
+    SC_S1 = 3,       // sum w (x - xbar), zero up to rounding
+    SC_T0 = 4,       // min t (time origin for phase conditioning, Sec. 3b "T_0 <= all t_i")
+    SC_TAUMAX = 5,   // max t - T0
+    SC_SORTED = 6,   // 1 if t is non-decreasing
+    SC_RW = 7,       // max(sqrt(sum w^2) / W, sqrt(sum w^2 d^2) / sqrt(W chi2_0)): scale of
+                     // independent per-sample rounding errors relative to the sums
+    SC_COUNT = 8
+};
+
+struct GridGeom {
+    int k;            // harmonic multiple of this transform
+    int kind;         // 0 = Q (weights), 1 = P (weighted data)
+    int64_t L;        // occupied extent in cells (rows beyond are zero)
+    int wraps;        // samples wrap the fold period -> keys need sorting
+};
+
+struct FftPass {
+    int logR;
+    int64_t Ns;       // product of the radices of earlier passes
+    int64_t rows_nz;  // rows r < rows_nz may be nonzero (first pass), else R
+};
+
+struct Workspace;
+
+}  // namespace fc2
+
+struct fc2_plan_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    fc2_options opt;
+
+    int64_t n = 0;
+    int H = 0;
+    double f_min = 0, df = 0;
+    int64_t N = 0;
+    int oversample = 2;
+    int64_t M = 0;
+    int logM = 0;
+    int G = 0;                 // number of transforms = 3H
+    int w = 0;                 // spreading kernel width
+    double beta = 0;
+    double tau = 0;            // rank-drop threshold
+    int top_k = 8;
+    bool fp64 = true;
+
+    // host copies of scalars
+    double scal[fc2::SC_COUNT] = {0};
+
+    // device memory
+    double* d_t = nullptr;     // caller order (owned unless borrowed)
+    double* d_x = nullptr;
+    double* d_sigma = nullptr;
+    bool borrowed = false;
+    double* d_scal = nullptr;  // [SC_COUNT]
+    int* d_status = nullptr;
+    int32_t* d_perm = nullptr; // sorted position -> caller index
+    double* d_tau = nullptr;   // sorted tau = t - T0
+    double* d_wq = nullptr;    // sorted w
+    double* d_wp = nullptr;    // sorted w (x - xbar)
+
+    // per-transform sample arrays [G][n]
+    int32_t* d_key = nullptr;
+    void* d_dlt = nullptr;     // T
+    void* d_cs = nullptr;      // cpx<T>
+    // grids, ping-pong [G][M]
+    void* d_grid[2] = {nullptr, nullptr};
+    void* d_spec = nullptr;    // cpx<T> [G][N]
+    void* d_dec = nullptr;     // cpx<T> [N] deconvolution factors
+    void* d_twlo = nullptr;    // cpx<T>
+    void* d_twhi = nullptr;
+    int tw_shift = 0;
+    void* d_twst = nullptr;    // cpx<T> in-CTA stage twiddles per radix
+    int64_t twst_off[16] = {0};
+    double* d_dchi2 = nullptr; // [H][N]
+    float* d_minpiv = nullptr; // unused slot kept for diagnostics
+    int32_t* d_flag_list = nullptr;  // bins needing the exact fix-up
+    int32_t* d_flag_count = nullptr;
+    int64_t flag_cap = 0;
+    int64_t* d_L = nullptr;    // [G] occupied extent of each grid
+    double* d_part = nullptr;  // exact-sum partials [exact_cap][nch][6H]
+    uint64_t* d_phA = nullptr; // fixed-point phases frac(f_min tau) 2^64 [n]
+    uint64_t* d_phB = nullptr; // fixed-point phases frac(df tau) 2^64 [n]
+    float* d_wq32 = nullptr;   // w as float [n]
+    float* d_wp32 = nullptr;   // w (x - xbar) as float [n]
+    int64_t exact_cap = 0;
+    void* d_red = nullptr;     // reduction scratch
+    size_t red_bytes = 0;
+    fc2_best* d_best = nullptr;  // [H + top_k]
+
+    std::vector<fc2::GridGeom> geom;
+    std::vector<fc2::FftPass> passes;
+    int64_t last_flag_count = 0;
+    int64_t last_exact2_count = 0;
+    int64_t last_resolve_count = 0;
+    bool has_perm = false;
+    // stage timing (events recorded around each stage while enabled)
+    bool timing = false;
+    cudaEvent_t ev[8] = {nullptr};
+    double stage_ms[8] = {0};
+    int64_t stage_n = 0;
+    int64_t launches = 0;      // kernels launched by the last execute
+    double fft_bytes = 0;      // algorithmic bytes moved by the FFT passes per execute
+};
+
+namespace fc2 {
+
+// k_prep.cu
+cudaError_t launch_moments(const double* t, const double* x, const double* sigma,
+                           const int64_t* offs, int64_t C, int64_t n_single,
+                           double* scal, int* status, cudaStream_t s);
+cudaError_t launch_moments_long(const double* t, const double* x, const double* sigma, int64_t n,
+                                double* scal, int* status, void* scratch, cudaStream_t s);
+size_t moments_scratch_bytes(int64_t n);
+cudaError_t sort_by_time(const double* t, int64_t n, int32_t* perm, void* scratch,
+                         size_t scratch_bytes, cudaStream_t s);
+size_t sort_scratch_bytes(int64_t n);
+cudaError_t launch_gather_sorted(const double* t, const double* x, const double* sigma,
+                                 const int32_t* perm, int64_t n, const double* scal,
+                                 double* tau, double* wq, double* wp, cudaStream_t s);
+cudaError_t launch_phase(fc2_plan_s* p, cudaStream_t s);
+cudaError_t launch_spread(fc2_plan_s* p, cudaStream_t s);
+
+// k_fft.cu
+cudaError_t init_twiddles(fc2_plan_s* p, cudaStream_t s);
+cudaError_t init_deconv(fc2_plan_s* p, cudaStream_t s);
+void plan_fft_passes(fc2_plan_s* p);
+cudaError_t launch_fft(fc2_plan_s* p, cudaStream_t s);
+
+// k_solve.cu
+cudaError_t launch_assemble(fc2_plan_s* p, cudaStream_t s);
+cudaError_t launch_fixup(fc2_plan_s* p, int64_t count, cudaStream_t s);
+cudaError_t launch_peaks(fc2_plan_s* p, cudaStream_t s);
+size_t peaks_scratch_bytes(int64_t N, int H, int K);
+size_t exact_scratch_bytes(int64_t n, int H, int64_t cap);
+cudaError_t launch_phase_fx(fc2_plan_s* p, cudaStream_t s);
+
+// k_adjoint.cu
+cudaError_t launch_backward(fc2_plan_s* p, int K, const int64_t* d_j, const double* d_g,
+                            double* d_fref, double* d_dref, double* d_df, double* d_dx,
+                            double* d_ds, cudaStream_t s);
+
+// host helpers (fc2_host.cpp)
+void gauss_legendre(int nq, double* x, double* w);
+double kernel_ft_host(int w, double beta, double xi, int nq, const double* gx, const double* gw);
+int default_width(bool fp64, int oversample);
+
+}  // namespace fc2

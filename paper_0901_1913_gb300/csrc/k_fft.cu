@@ -1,0 +1,519 @@
+// k_fft.cu -- FFTs of the spread grids and the kernel-transform deconvolution table.
+//
+// Paper: Sec. 2 ("P and Q can be efficiently computed by the application of the
+// FFT to p and q"), Sec. 3b (FFT of the gridded arrays).  The sign is
+// e^{+i 2 pi f t} as in Eq. "eqPQ".
+//
+// Layout: grid g occupies M = 2^logM complex cells.  The transform is a
+// sequence of Stockham passes through HBM; each pass gives every CTA J
+// adjacent columns of R = 2^logR rows (a tile of R x J complex values staged
+// in shared memory), applies the inter-pass twiddles, runs an in-CTA
+// Stockham DFT of length R built from radix-16/8/4/2 register butterflies and
+// writes the tile back in autosorted order.  The first pass reads only the
+// rows that hold samples (the rest of the grid is zero padding); the last
+// pass keeps only the N centred modes and writes them, in trial-frequency
+// order, to the spectrum array.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fc2_common.cuh"
+#include "fc2_internal.h"
+
+namespace fc2 {
+
+// ------------------------------------------------------------------ twiddles
+// w_M^q = hi[q >> sh] * lo[q & (2^sh - 1)], each table entry rounded once from
+// a double sincospi with an exact rational argument.
+template <typename T>
+__global__ void k_init_tw(cpx<T>* lo, int64_t nlo, cpx<T>* hi, int64_t nhi, int logM, int sh) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double inv = ldexp(2.0, -logM);  // 2 / M
+    double s, c;
+    if (i < nlo) {
+        sincospi((double)i * inv, &s, &c);
+        lo[i] = mk<T>((T)c, (T)s);
+    }
+    if (i < nhi) {
+        sincospi((double)(i << sh) * inv, &s, &c);
+        hi[i] = mk<T>((T)c, (T)s);
+    }
+}
+
+template <typename T>
+FC2_D cpx<T> twiddle(const cpx<T>* __restrict__ lo, const cpx<T>* __restrict__ hi, int sh,
+                     int64_t q) {
+    return mul(hi[q >> sh], lo[q & ((1ll << sh) - 1)]);
+}
+
+// ---------------------------------------------------------- deconvolution
+// dec[j] = 1 / phihat((j - hN) / M), phihat the kernel's Fourier transform,
+// evaluated from a Chebyshev expansion in xi^2 fitted on the host.
+__host__ __device__ inline double cheb_clenshaw(const double* c, int nc, double x) {
+    double b1 = 0.0, b2 = 0.0;
+    for (int k = nc - 1; k >= 1; --k) {
+        double b0 = 2.0 * x * b1 - b2 + c[k];
+        b2 = b1;
+        b1 = b0;
+    }
+    return x * b1 - b2 + c[0];
+}
+
+constexpr int CHEB_N = 64;
+
+// phihat is even: thread m (0 <= m <= max(hN, N - hN)) fills both j = hN + m and
+// j = hN - m.
+template <typename T>
+__global__ void k_init_dec(T* dec, int64_t N, int64_t hN, int64_t M, const double* cheb,
+                           int nc, double ymax) {
+    __shared__ double c[CHEB_N];
+    if (threadIdx.x < CHEB_N) c[threadIdx.x] = cheb[threadIdx.x];
+    __syncthreads();
+    int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m > hN && m >= N - hN) return;
+    double xi = (double)m / (double)M;
+    double y = xi * xi;
+    double xx = 2.0 * y / ymax - 1.0;
+    T v = (T)(1.0 / cheb_clenshaw(c, nc, xx));
+    if (hN + m < N) dec[hN + m] = v;
+    if (m > 0 && hN - m >= 0) dec[hN - m] = v;
+}
+
+int cheb_fit_kernel_ft(int w, double beta, double xi_max, double* coef) {
+    int nq = 2 * w + 16;
+    std::vector<double> gx(nq), gw(nq);
+    gauss_legendre(nq, gx.data(), gw.data());
+    const double ymax = xi_max * xi_max;
+    std::vector<double> f(CHEB_N);
+    for (int i = 0; i < CHEB_N; ++i) {
+        double xc = cos(M_PI * (i + 0.5) / CHEB_N);
+        double y = 0.5 * ymax * (xc + 1.0);
+        f[i] = kernel_ft_host(w, beta, sqrt(y), nq, gx.data(), gw.data());
+    }
+    for (int k = 0; k < CHEB_N; ++k) {
+        double acc = 0.0;
+        for (int i = 0; i < CHEB_N; ++i) acc += f[i] * cos(M_PI * k * (i + 0.5) / CHEB_N);
+        coef[k] = acc * 2.0 / CHEB_N;
+    }
+    coef[0] *= 0.5;
+    // drop the negligible tail of the expansion
+    double mx = 0.0;
+    for (int k = 0; k < CHEB_N; ++k) mx = std::max(mx, fabs(coef[k]));
+    int nc = CHEB_N;
+    while (nc > 2 && fabs(coef[nc - 1]) < 1e-18 * mx) --nc;
+    return nc;
+}
+
+double cheb_eval_host(const double* coef, double xi, double xi_max) {
+    double ymax = xi_max * xi_max;
+    return cheb_clenshaw(coef, CHEB_N, 2.0 * xi * xi / ymax - 1.0);
+}
+
+cudaError_t init_deconv(fc2_plan_s* p, cudaStream_t s) {
+    double coef[CHEB_N];
+    const int64_t hN = p->N / 2;
+    const double xi_max = (double)std::max(hN, p->N - hN) / (double)p->M;
+    const int nc = cheb_fit_kernel_ft(p->w, p->beta, xi_max, coef);
+    double* d_coef = (double*)p->d_red;  // scratch, consumed before any other use
+    cudaError_t e = cudaMemcpyAsync(d_coef, coef, sizeof(coef), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    const int64_t mmax = std::max(hN, p->N - hN);
+    unsigned blocks = (unsigned)((mmax + 256) / 256);
+    if (p->fp64)
+        k_init_dec<double><<<blocks, 256, 0, s>>>((double*)p->d_dec, p->N, hN, p->M, d_coef, nc,
+                                                  xi_max * xi_max);
+    else
+        k_init_dec<float><<<blocks, 256, 0, s>>>((float*)p->d_dec, p->N, hN, p->M, d_coef, nc,
+                                                 xi_max * xi_max);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the coefficients live in reduction scratch: finish before it is reused
+    return cudaStreamSynchronize(s);
+}
+
+// ------------------------------------------------------------ in-CTA DFT
+// Shared tile of R rows x J columns; element (r, jj) has logical index
+// e = r * J + jj and lives at phys(e) = e + e / 32 (one pad slot per 32
+// elements keeps the strided butterfly writes free of bank conflicts).
+FC2_HD int phys(int e) { return e + (e >> 5); }
+
+// Stage decomposition of a length-2^LOGR DFT: the first stage takes LOGR % 4
+// bits (if nonzero), every other stage 4 bits (radix 16).
+FC2_HD constexpr int stage_bits(int LOGR, int DONE) {
+    return (DONE == 0 && (LOGR % 4) != 0) ? (LOGR % 4) : ((LOGR - DONE) >= 4 ? 4 : (LOGR - DONE));
+}
+// Twiddles of stage (Ns = 2^DONE, radix Q): table entry [(k-1) Ns + pm] =
+// w_{Ns Q}^{k pm}; stages are stored one after the other.
+FC2_HD constexpr int stage_tw_size(int LOGR) {
+    int tot = 0, done = 0;
+    while (done < LOGR) {
+        int qb = stage_bits(LOGR, done);
+        if (done > 0) tot += ((1 << qb) - 1) * (1 << done);
+        done += qb;
+    }
+    return tot;
+}
+
+template <typename T>
+__global__ void k_init_stage_tw(cpx<T>* tw, int LOGR) {
+    // thread i computes entry i of the concatenated stage tables
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int off = 0, done = 0;
+    while (done < LOGR) {
+        int qb = stage_bits(LOGR, done);
+        if (done > 0) {
+            int ns = 1 << done, q = 1 << qb;
+            int sz = (q - 1) * ns;
+            if (i >= off && i < off + sz) {
+                int k = (i - off) / ns + 1, pm = (i - off) % ns;
+                double sn, cn;
+                // w_{ns q}^{k pm}: exact rational argument 2 k pm / (ns q)
+                sincospi(2.0 * (double)(k * pm) / (double)(ns * q), &sn, &cn);
+                tw[i] = mk<T>((T)cn, (T)sn);
+                return;
+            }
+            off += sz;
+        }
+        done += qb;
+    }
+}
+
+struct TwgArgs {
+    int j0;       // first column of the tile
+    int nsg_mask; // NsG - 1 (NsG = product of earlier passes' radices)
+    int lts;      // log2(M / (NsG R))
+    int tws;      // two-level table split
+};
+
+// One in-CTA Stockham stage of radix Q (Ns = 2^DONE): butterfly (pp, jj) reads
+// rows pp + k R/Q, multiplies by w_{Ns Q}^{k (pp % Ns)} and writes rows
+// (pp / Ns) Ns Q + pp % Ns + k Ns.  With TWG (first stage of a later pass) the
+// inter-pass twiddle w_M^{r (j % NsG) M/(NsG R)} of each element is applied as
+// it is read; it is built as base * step^k from four table lookups per
+// butterfly.
+template <typename T, int R, int J, int NT, int QB, int DONE, int TOFF, bool TWG>
+FC2_D void cta_stage(cpx<T>* s, const cpx<T>* st, const TwgArgs& tg,
+                     const cpx<T>* __restrict__ twlo, const cpx<T>* __restrict__ twhi) {
+    constexpr int Q = 1 << QB;
+    constexpr int NS = 1 << DONE;
+    constexpr int NB = (R / Q) * J;
+    constexpr int PER = NB / NT;
+    static_assert(PER * NT == NB, "butterflies must divide evenly");
+    cpx<T> v[PER][Q];
+    int idx[PER], jj_[PER];
+#pragma unroll
+    for (int b = 0; b < PER; ++b) {
+        const int bi = threadIdx.x + b * NT;
+        const int jj = bi % J, pp = bi / J;
+#pragma unroll
+        for (int k = 0; k < Q; ++k) v[b][k] = s[phys((pp + k * (R / Q)) * J + jj)];
+        if constexpr (TWG) {
+            const int jm = (tg.j0 + jj) & tg.nsg_mask;
+            if (jm != 0) {
+                const cpx<T> base = twiddle(twlo, twhi, tg.tws, (int64_t)((pp * jm) << tg.lts));
+                const cpx<T> st1 = twiddle(twlo, twhi, tg.tws, (int64_t)(((R / Q) * jm) << tg.lts));
+                cpx<T> lo[4], hi[4];
+                lo[0] = mk<T>((T)1, (T)0);
+                lo[1] = st1;
+                if constexpr (Q > 2) { lo[2] = mul(st1, st1); lo[3] = mul(lo[2], st1); }
+                if constexpr (Q > 4) {
+                    hi[1] = mul(lo[2], lo[2]);
+                    if constexpr (Q > 8) { hi[2] = mul(hi[1], hi[1]); hi[3] = mul(hi[2], hi[1]); }
+                }
+                v[b][0] = mul(v[b][0], base);
+#pragma unroll
+                for (int k = 1; k < Q; ++k) {
+                    cpx<T> w = base;
+                    if ((k & 3) != 0) w = mul(w, lo[k & 3]);
+                    if ((k >> 2) != 0) w = mul(w, hi[k >> 2]);
+                    v[b][k] = mul(v[b][k], w);
+                }
+            }
+        }
+        const int pm = pp % NS;
+        if constexpr (NS > 1) {
+#pragma unroll
+            for (int k = 1; k < Q; ++k) v[b][k] = mul(v[b][k], st[TOFF + (k - 1) * NS + pm]);
+        }
+        SmallDFT<T, Q>::run(v[b]);
+        idx[b] = (pp / NS) * NS * Q + pm;
+        jj_[b] = jj;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < PER; ++b)
+#pragma unroll
+        for (int k = 0; k < Q; ++k) s[phys((idx[b] + k * NS) * J + jj_[b])] = v[b][k];
+    __syncthreads();
+}
+
+template <typename T, int LOGR, int J, int NT, int DONE, int TOFF>
+struct CtaDft {
+    static FC2_D void run(cpx<T>* s, const cpx<T>* st, const TwgArgs& tg, bool twg,
+                          const cpx<T>* twlo, const cpx<T>* twhi) {
+        constexpr int R = 1 << LOGR;
+        if constexpr (DONE < LOGR) {
+            constexpr int QB = stage_bits(LOGR, DONE);
+            constexpr int NTOFF = TOFF + (DONE > 0 ? ((1 << QB) - 1) * (1 << DONE) : 0);
+            if (DONE == 0 && twg)
+                cta_stage<T, R, J, NT, QB, DONE, TOFF, true>(s, st, tg, twlo, twhi);
+            else
+                cta_stage<T, R, J, NT, QB, DONE, TOFF, false>(s, st, tg, twlo, twhi);
+            CtaDft<T, LOGR, J, NT, DONE + QB, NTOFF>::run(s, st, tg, twg, twlo, twhi);
+        }
+    }
+};
+
+FC2_D void cp_async8(void* smem, const void* gmem) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+FC2_D void cp_async16(void* smem, const void* gmem) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+FC2_D void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+
+template <typename T>
+FC2_D void cp_elem(cpx<T>* smem, const cpx<T>* gmem) {
+    if constexpr (sizeof(cpx<T>) == 16) cp_async16(smem, gmem);
+    else cp_async8(smem, gmem);
+}
+
+struct PassArgs {
+    int logM;
+    int logNs;         // log2 of the product of the radices of earlier passes
+    int first, last;
+    int logRn, logJn;  // radix and tile width of the next pass (blocked output layout)
+    int N, hN;
+    int tws;
+};
+
+// One pass of the transform.  Logical Stockham indexing: column j (0 <= j < S,
+// S = M / R) takes rows r of X[j + r S]; output k of its length-R DFT is
+// X'[(j / Ns) Ns R + (j % Ns) + k Ns].
+// Physical layouts: the first pass reads the spread grid directly (row r of a
+// tile is J contiguous cells at j0 + r S; rows r >= ceil(L_g / S) are zero
+// padding and are not read).  Every later pass reads its input in the
+// "blocked" layout its predecessor wrote: the R x J tile of columns
+// [b J, (b + 1) J) is one contiguous run, element (r, jj) at b R J + r J + jj.
+// The last pass writes only the N centred modes m = o or o - M (o the output
+// index), in trial-frequency order, to spec[g][m + hN].
+template <typename T, int LOGR, int LOGJ, int NT>
+__global__ void __launch_bounds__(NT, 2) k_fft_pass(const cpx<T>* __restrict__ in,
+                                                    cpx<T>* __restrict__ out, PassArgs a,
+                                                    const int64_t* __restrict__ Lg,
+                                                    const cpx<T>* __restrict__ twlo,
+                                                    const cpx<T>* __restrict__ twhi,
+                                                    const cpx<T>* __restrict__ twst) {
+    constexpr int R = 1 << LOGR;
+    constexpr int J = 1 << LOGJ;
+    constexpr int E = R * J;
+    constexpr int NST = stage_tw_size(LOGR);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* s = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* st = s + phys(E - 1) + 1;
+    const int M = 1 << a.logM;
+    const int S = M >> LOGR;
+    const int g = blockIdx.y;
+    const int j0 = blockIdx.x * J;
+    const cpx<T>* gin = in + (int64_t)g * M;
+    if (a.first) {
+        const int L = (int)Lg[g];
+        int rows = (L + S - 1) / S;
+        if (rows > R) rows = R;
+        for (int e = threadIdx.x; e < E; e += NT) {
+            const int r = e >> LOGJ, jj = e & (J - 1);
+            if (r < rows) cp_elem(&s[phys(e)], &gin[j0 + jj + r * S]);
+            else s[phys(e)] = mk<T>((T)0, (T)0);
+        }
+    } else {
+        const cpx<T>* src = gin + (int64_t)blockIdx.x * E;
+        for (int e = threadIdx.x; e < E; e += NT) cp_elem(&s[phys(e)], &src[e]);
+    }
+    for (int i = threadIdx.x; i < NST; i += NT) cp_elem(&st[i], &twst[i]);
+    cp_async_wait_all();
+    __syncthreads();
+    TwgArgs tg;
+    tg.j0 = j0;
+    tg.nsg_mask = (1 << a.logNs) - 1;
+    tg.lts = a.logM - a.logNs - LOGR;
+    tg.tws = a.tws;
+    CtaDft<T, LOGR, J, NT, 0, 0>::run(s, st, tg, a.logNs > 0, twlo, twhi);
+    const int logNs = a.logNs;
+    if (!a.last) {
+        cpx<T>* gout = out + (int64_t)g * M;
+        const int LOGJn = a.logJn, Jn = 1 << a.logJn;
+        const int logBlk = a.logRn + a.logJn;  // Rn * Jn
+        if (logNs == 0 && a.logM - a.logRn == LOGR) {
+            // two-pass plan: logical output j R + k is column k, row j of the
+            // next (last) pass
+            for (int e = threadIdx.x; e < E; e += NT) {
+                const int kl = e & (Jn - 1);
+                const int jj = (e >> LOGJn) & (J - 1);
+                const int kb = e >> (LOGJn + LOGJ);
+                const int k = (kb << LOGJn) + kl;
+                gout[(kb << logBlk) + ((j0 + jj) << LOGJn) + kl] = s[phys(k * J + jj)];
+            }
+        } else {
+            const int logSn = a.logM - a.logRn;
+            for (int e = threadIdx.x; e < E; e += NT) {
+                const int kl = e & (Jn - 1);
+                const int jj = (e >> LOGJn) & (J - 1);
+                const int kb = e >> (LOGJn + LOGJ);
+                const int k = (kb << LOGJn) + kl;
+                const int j = j0 + jj;
+                const int i = ((j >> logNs) << (logNs + LOGR)) + (j & ((1 << logNs) - 1)) + (k << logNs);
+                const int jn = i & ((1 << logSn) - 1), rn = i >> logSn;
+                gout[((jn >> LOGJn) << logBlk) + (rn << LOGJn) + (jn & (Jn - 1))] = s[phys(k * J + jj)];
+            }
+        }
+    } else {
+        cpx<T>* spec = out + (int64_t)g * a.N;
+        for (int e = threadIdx.x; e < E; e += NT) {
+            const int k = e >> LOGJ, jj = e & (J - 1);
+            const int o = j0 + jj + (k << logNs);
+            const int m = (o < M / 2) ? o : o - M;
+            const int jf = m + a.hN;
+            if (jf >= 0 && jf < a.N) spec[jf] = s[phys(e)];
+        }
+    }
+}
+
+cudaError_t init_twiddles(fc2_plan_s* p, cudaStream_t s) {
+    int sh = (p->logM + 1) / 2;
+    int64_t nlo = 1ll << sh, nhi = p->M >> sh;
+    p->tw_shift = sh;
+    int64_t nmax = std::max(nlo, nhi);
+    unsigned blocks = (unsigned)((nmax + 255) / 256);
+    bool assigned[16] = {false};
+    int64_t off = 0;
+    for (auto& ps : p->passes) {
+        if (assigned[ps.logR]) continue;
+        assigned[ps.logR] = true;
+        p->twst_off[ps.logR] = off;
+        int n = stage_tw_size(ps.logR);
+        unsigned b2 = (unsigned)((n + 255) / 256);
+        if (n > 0) {
+            if (p->fp64) k_init_stage_tw<double><<<b2, 256, 0, s>>>((cpx<double>*)p->d_twst + off, ps.logR);
+            else k_init_stage_tw<float><<<b2, 256, 0, s>>>((cpx<float>*)p->d_twst + off, ps.logR);
+        }
+        off += n + 16;
+    }
+    if (p->fp64)
+        k_init_tw<double><<<blocks, 256, 0, s>>>((cpx<double>*)p->d_twlo, nlo,
+                                                 (cpx<double>*)p->d_twhi, nhi, p->logM, sh);
+    else
+        k_init_tw<float><<<blocks, 256, 0, s>>>((cpx<float>*)p->d_twlo, nlo,
+                                                (cpx<float>*)p->d_twhi, nhi, p->logM, sh);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- pass plan
+// fp32: tiles of 2^13 complex (64 KB), radix <= 2^12; fp64: 2^12 (64 KB), <= 2^11.
+template <typename T> struct FftCfg;
+template <> struct FftCfg<float> { static constexpr int LOGE = 13; static constexpr int NT = 512; static constexpr int MAXR = 12; };
+template <> struct FftCfg<double> { static constexpr int LOGE = 12; static constexpr int NT = 256; static constexpr int MAXR = 11; };
+
+void plan_fft_passes(fc2_plan_s* p) {
+    const int maxr = p->fp64 ? FftCfg<double>::MAXR : FftCfg<float>::MAXR;
+    p->passes.clear();
+    const int logM = p->logM;
+    if (logM <= maxr) {
+        p->passes.push_back({logM, 1, 0});
+        return;
+    }
+    const int P = (logM + maxr - 1) / maxr;
+    std::vector<int> rs(P, logM / P);
+    for (int i = 0; i < logM % P; ++i) rs[i] += 1;
+    int64_t Ns = 1;
+    for (int i = 0; i < P; ++i) {
+        p->passes.push_back({rs[i], Ns, 0});
+        Ns <<= rs[i];
+    }
+}
+
+template <typename T>
+static int logj_of(int logR, int logM) {
+    if (logR == logM) return 0;  // single pass: one column
+    return FftCfg<T>::LOGE - logR;
+}
+
+template <typename T, int LOGR, int LOGJ, int NT>
+static cudaError_t run_pass(fc2_plan_s* p, const void* in, void* out, const PassArgs& a,
+                            cudaStream_t s) {
+    constexpr int R = 1 << LOGR, J = 1 << LOGJ, E = R * J;
+    const int64_t S = p->M >> LOGR;
+    const size_t smem = (size_t)(phys(E - 1) + 1 + stage_tw_size(LOGR) + 1) * sizeof(cpx<T>);
+    auto kern = k_fft_pass<T, LOGR, LOGJ, NT>;
+    static bool attr_done = false;  // per instantiation, once per process
+    if (!attr_done) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_done = true;
+    }
+    dim3 grid((unsigned)(S / J), (unsigned)p->G);
+    kern<<<grid, NT, smem, s>>>((const cpx<T>*)in, (cpx<T>*)out, a, p->d_L,
+                                (const cpx<T>*)p->d_twlo, (const cpx<T>*)p->d_twhi,
+                                (const cpx<T>*)p->d_twst + p->twst_off[LOGR]);
+    return cudaGetLastError();
+}
+
+template <typename T, int LOGR>
+static cudaError_t run_radix(fc2_plan_s* p, const void* in, void* out, const PassArgs& a,
+                             cudaStream_t s) {
+    if (LOGR == p->logM) {
+        constexpr int NT = (1 << LOGR) / 16 < 32 ? 32 : (1 << LOGR) / 16;
+        if constexpr ((1 << LOGR) % (16 * NT) == 0 || (1 << LOGR) >= 16 * NT)
+            return run_pass<T, LOGR, 0, NT>(p, in, out, a, s);
+        return cudaErrorInvalidValue;
+    }
+    constexpr int LOGJ = FftCfg<T>::LOGE - LOGR;
+    if constexpr (LOGJ >= 0) return run_pass<T, LOGR, LOGJ, FftCfg<T>::NT>(p, in, out, a, s);
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t fft_impl(fc2_plan_s* p, cudaStream_t s) {
+    int src = 0;
+    const int P = (int)p->passes.size();
+    for (int i = 0; i < P; ++i) {
+        const FftPass& ps = p->passes[i];
+        PassArgs a;
+        a.logM = p->logM;
+        a.logNs = 0;
+        while ((1ll << a.logNs) < ps.Ns) ++a.logNs;
+        a.first = (i == 0);
+        a.last = (i == P - 1);
+        a.logRn = a.last ? 0 : p->passes[i + 1].logR;
+        a.logJn = a.last ? 0 : logj_of<T>(p->passes[i + 1].logR, p->logM);
+        a.N = (int)p->N;
+        a.hN = (int)(p->N / 2);
+        a.tws = p->tw_shift;
+        const void* in = p->d_grid[src];
+        void* out = a.last ? p->d_spec : p->d_grid[1 - src];
+        cudaError_t e;
+        switch (ps.logR) {
+            case 8: e = run_radix<T, 8>(p, in, out, a, s); break;
+            case 9: e = run_radix<T, 9>(p, in, out, a, s); break;
+            case 10: e = run_radix<T, 10>(p, in, out, a, s); break;
+            case 11: e = run_radix<T, 11>(p, in, out, a, s); break;
+            case 12:
+                if constexpr (sizeof(T) == 4) { e = run_radix<T, 12>(p, in, out, a, s); break; }
+                return cudaErrorInvalidValue;
+            case 7: e = run_radix<T, 7>(p, in, out, a, s); break;
+            case 6: e = run_radix<T, 6>(p, in, out, a, s); break;
+            case 5: e = run_radix<T, 5>(p, in, out, a, s); break;
+            default: return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+        src = 1 - src;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_fft(fc2_plan_s* p, cudaStream_t s) {
+    return p->fp64 ? fft_impl<double>(p, s) : fft_impl<float>(p, s);
+}
+
+}  // namespace fc2

@@ -1,0 +1,807 @@
+// k_solve.cu -- per-frequency normal equations, bordered Cholesky, exact
+// fix-up of ill-conditioned bins, peak selection and coefficients.
+//
+// Paper: Sec. 2 Eqs. "eqalphafirst".."eqalpha" (alpha from C', S' at (h -+ h') f),
+// the beta equations (C, S at h f), Eq. "eqchix" (chi2_min = X - beta^T alpha^-1 beta),
+// Eq. "eqcoeffs" (A = alpha^-1 beta), Sec. 3c (Delta chi^2 = beta^T alpha^-1 beta with
+// mean-subtracted data), Sec. 3e (best frequency = largest Delta chi^2; several
+// candidate frequencies).
+//
+// Bordered Cholesky: with alpha = L L^T and z = L^-1 beta, the leading
+// (2H'+1)-square block of alpha factors as the leading block of L, so
+//   Delta chi^2_{H'} = sum_{l=1..2H'} z_l^2
+// for every H' from one factorisation (z_0^2 = beta_0^2 / alpha_00 is the
+// constant-only projection, zero up to rounding, and is excluded).
+// Rank rule (the paper is silent on singular alpha): column l is dropped when
+// its relative pivot d_l / alpha_ll <= tau; dropped columns contribute nothing.
+#include <cuda_runtime.h>
+
+#include "fc2_common.cuh"
+#include "fc2_internal.h"
+
+#include <algorithm>
+
+namespace fc2 {
+
+// Normalised system: alpha' = alpha / W, beta' = beta / sqrt(W chi2_0), so
+// Delta chi^2' = Delta chi^2 / chi2_0 lies in [0, 1].
+template <typename TC, int H>
+struct Sys {
+    TC qr[2 * H + 1], qi[2 * H + 1], pr[H + 1], pi[H + 1];
+
+    FC2_HD TC alpha(int l, int k) const {
+        if (l < k) { int t = l; l = k; k = t; }
+        if (l == 0) return qr[0];
+        const int hl = (l + 1) >> 1;
+        const bool sl = (l & 1);
+        if (k == 0) return sl ? qi[hl] : qr[hl];
+        const int hk = (k + 1) >> 1;
+        const bool sk = (k & 1);
+        const int d = hl > hk ? hl - hk : hk - hl;
+        const TC sg = hl > hk ? (TC)1 : (hl < hk ? (TC)-1 : (TC)0);
+        const int s = hl + hk;
+        const TC h = (TC)0.5;
+        if (sl && sk) return h * (qr[d] - qr[s]);
+        if (!sl && !sk) return h * (qr[d] + qr[s]);
+        if (sl && !sk) return h * (qi[s] + sg * qi[d]);   // sin(hl) cos(hk)
+        return h * (qi[s] - sg * qi[d]);                  // cos(hl) sin(hk)
+    }
+    FC2_HD TC beta(int l) const {
+        if (l == 0) return pr[0];
+        const int h = (l + 1) >> 1;
+        return (l & 1) ? pi[h] : pr[h];
+    }
+};
+
+// Factor and solve; out[H'-1] = Delta chi^2'_{H'}.  Returns the minimum
+// relative pivot over all columns (clamped at 0).  With COEF, *anorm2 receives
+// max over H' of |A^{(H')}|^2 (A^{(H')} = the H'-harmonic coefficients, by
+// back-substitution L^T A = z on the leading block), the sensitivity of the
+// result to errors in alpha and beta.  Optionally keeps L and z.
+template <typename TC, int H, bool COEF>
+FC2_D TC chol_solve(const Sys<TC, H>& S, TC tau, TC* out, TC* anorm2,
+                    TC (*Lkeep)[2 * H + 1] = nullptr, TC* zkeep = nullptr) {
+    constexpr int m = 2 * H + 1;
+    TC L[m][m];
+    TC z[m], dinv[m];
+    TC acc = (TC)0, dmin = (TC)1;
+#pragma unroll
+    for (int l = 0; l < m; ++l) {
+#pragma unroll
+        for (int k = 0; k < l; ++k) {
+            TC a = S.alpha(l, k);
+#pragma unroll
+            for (int p = 0; p < k; ++p) a = fma(-L[l][p], L[k][p], a);
+            L[l][k] = a * dinv[k];
+        }
+        const TC all = S.alpha(l, l);
+        TC d = all;
+#pragma unroll
+        for (int p = 0; p < l; ++p) d = fma(-L[l][p], L[l][p], d);
+        TC b = S.beta(l);
+#pragma unroll
+        for (int p = 0; p < l; ++p) b = fma(-L[l][p], z[p], b);
+        const TC ratio = (all > (TC)0) ? d / all : (TC)0;
+        if (ratio > tau) {
+            const TC sq = sqrt(d);
+            L[l][l] = sq;
+            dinv[l] = (TC)1 / sq;
+            z[l] = b * dinv[l];
+        } else {
+            L[l][l] = (TC)0;
+            dinv[l] = (TC)0;
+            z[l] = (TC)0;
+        }
+        const TC rc = ratio > (TC)0 ? ratio : (TC)0;
+        dmin = rc < dmin ? rc : dmin;
+        if (l > 0) acc = fma(z[l], z[l], acc);
+        if (l > 0 && (l & 1) == 0) out[(l >> 1) - 1] = acc;
+    }
+    if constexpr (COEF) {
+        TC amax = (TC)0;
+#pragma unroll
+        for (int hp = 1; hp <= H; ++hp) {
+            constexpr int dummy = 0;
+            (void)dummy;
+            const int mp = 2 * hp + 1;
+            TC A[m];
+            TC nrm = (TC)0;
+#pragma unroll
+            for (int l = m - 1; l >= 0; --l) {
+                if (l < mp) {
+                    TC a = z[l];
+#pragma unroll
+                    for (int k = l + 1; k < m; ++k)
+                        if (k < mp) a = fma(-L[k][l], A[k], a);
+                    A[l] = a * dinv[l];
+                    nrm = fma(A[l], A[l], nrm);
+                }
+            }
+            amax = nrm > amax ? nrm : amax;
+        }
+        *anorm2 = amax;
+    }
+    if (Lkeep) {
+#pragma unroll
+        for (int l = 0; l < m; ++l)
+#pragma unroll
+            for (int k = 0; k <= l; ++k) Lkeep[l][k] = L[l][k];
+#pragma unroll
+        for (int l = 0; l < m; ++l) zkeep[l] = z[l];
+    }
+    return dmin;
+}
+
+// Error model of a result computed from an alpha and beta whose entries carry
+// absolute errors ~eps (normalised units): with A the coefficient vector,
+// dDelta = 2 A^T dbeta - A^T dalpha A, so |dDelta| <~ eps (m |A|^2 + 2 sqrt(m) |A|).
+template <typename TC>
+FC2_HD TC est_err(TC anorm2, int m, TC eps) {
+    return eps * ((TC)m * anorm2 + (TC)2 * sqrt((TC)m * anorm2));
+}
+
+struct SolveParams {
+    int64_t N;
+    double tau;        // rank-drop threshold
+    double eps_spec;   // absolute error of the normalised gridded alpha/beta entries
+    double eps_f32;    // extra error of a float factorisation
+    double err_fix;    // bins whose estimated normalised error exceeds this are recomputed
+    double sq, sp, chi0, s1n;  // 1/W, 1/sqrt(W chi2_0), chi2_0, sum w(x - xbar) / sqrt(W chi2_0)
+};
+
+template <typename TS, int H>
+FC2_D void load_gridded(const cpx<TS>* __restrict__ spec, const TS* __restrict__ dec, int64_t N,
+                        int64_t j, TS sq, TS sp, TS s1n, Sys<TS, H>& S) {
+    const TS d = dec[j];
+    const TS dq = d * sq, dp = d * sp;
+    S.qr[0] = (TS)1;
+    S.qi[0] = (TS)0;
+    S.pr[0] = s1n;
+    S.pi[0] = (TS)0;
+#pragma unroll
+    for (int k = 1; k <= 2 * H; ++k) {
+        cpx<TS> v = spec[(int64_t)(k - 1) * N + j];
+        S.qr[k] = v.x * dq;
+        S.qi[k] = v.y * dq;
+    }
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        cpx<TS> v = spec[(int64_t)(2 * H + k - 1) * N + j];
+        S.pr[k] = v.x * dp;
+        S.pi[k] = v.y * dp;
+    }
+}
+
+// Per trial frequency: deconvolve and normalise the 3H spectra, factor, and
+// write Delta chi^2 for every H'.  A bin whose estimated error is too large
+// for this precision goes to a list: the float path sends it to a double
+// re-solve of the same spectra, the double path to the exact fix-up.
+template <typename TS, int H>
+__global__ void __launch_bounds__(128) k_assemble(const cpx<TS>* __restrict__ spec,
+                                                  const TS* __restrict__ dec,
+                                                  double* __restrict__ dchi2, SolveParams sp,
+                                                  int32_t* __restrict__ list,
+                                                  int32_t* __restrict__ list_count,
+                                                  int64_t cap) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= sp.N) return;
+    constexpr int m = 2 * H + 1;
+    Sys<TS, H> S;
+    load_gridded<TS, H>(spec, dec, sp.N, j, (TS)sp.sq, (TS)sp.sp, (TS)sp.s1n, S);
+    TS out[H];
+    TS an2 = (TS)0;
+    chol_solve<TS, H, true>(S, (TS)sp.tau, out, &an2);
+    const TS eps = (TS)(sizeof(TS) == 4 ? sp.eps_spec + sp.eps_f32 : sp.eps_spec);
+    if (!(est_err<TS>(an2, m, eps) <= (TS)sp.err_fix)) {
+        int32_t pos = atomicAdd(list_count, 1);
+        if (pos < cap) list[pos] = (int32_t)j;
+    }
+    const TS c0 = (TS)sp.chi0;
+#pragma unroll
+    for (int h = 0; h < H; ++h) dchi2[(int64_t)h * sp.N + j] = (double)(out[h] * c0);
+}
+
+// Double re-solve of float-path bins; bins still too sensitive go on to the
+// exact fix-up list.
+template <int H>
+__global__ void __launch_bounds__(128) k_resolve(const cpx<float>* __restrict__ spec,
+                                                 const float* __restrict__ dec,
+                                                 double* __restrict__ dchi2, SolveParams sp,
+                                                 const int32_t* __restrict__ rlist,
+                                                 const int32_t* __restrict__ rcount, int64_t rcap,
+                                                 int32_t* __restrict__ flist,
+                                                 int32_t* __restrict__ fcount, int64_t fcap) {
+    int64_t cnt = *rcount;
+    if (cnt > rcap) cnt = rcap;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < cnt;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = rlist[b];
+        Sys<float, H> Sf;
+        load_gridded<float, H>(spec, dec, sp.N, j, (float)sp.sq, (float)sp.sp, (float)sp.s1n, Sf);
+        Sys<double, H> S;
+#pragma unroll
+        for (int k = 0; k <= 2 * H; ++k) { S.qr[k] = Sf.qr[k]; S.qi[k] = Sf.qi[k]; }
+#pragma unroll
+        for (int k = 0; k <= H; ++k) { S.pr[k] = Sf.pr[k]; S.pi[k] = Sf.pi[k]; }
+        double out[H], an2 = 0.0;
+        chol_solve<double, H, true>(S, sp.tau, out, &an2);
+        if (!(est_err<double>(an2, 2 * H + 1, sp.eps_spec) <= sp.err_fix)) {
+            int32_t pos = atomicAdd(fcount, 1);
+            if (pos < fcap) flist[pos] = (int32_t)j;
+        }
+#pragma unroll
+        for (int h = 0; h < H; ++h) dchi2[(int64_t)h * sp.N + j] = out[h] * sp.chi0;
+    }
+}
+
+// ------------------------------------------------- exact sums per bin
+// Q_k = sum_i w_i e^{2 pi i k f tau_i} (k = 1..2H) and P_k = sum_i w_i (x_i - xbar)
+// e^{2 pi i k f tau_i} (k = 1..H) straight from the samples (Eq. "eqPQ").
+// Work items are (bin, chunk of samples); each CTA reduces its chunk in a fixed
+// order and the final kernels add the chunks in order (reproducible).
+// Two precisions:
+//  - tier 1: the phase f tau_i is reduced in double and held as a 32-bit
+//    fixed-point fraction, so harmonic k's phase is an exact integer product;
+//    sine/cosine in float, accumulation in compensated float per thread and
+//    double across threads.  Each term carries an independent ~2e-7 relative
+//    error, so the sums are good to ~2e-7 * sqrt(sum w^2), far below the
+//    gridded spectra's error for large n.
+//  - tier 2: everything in double (powers of e^{2 pi i f tau_i}).
+constexpr int EX_NT = 256;
+
+// Fixed-point phases: A_i = frac(f_min tau_i) 2^64 and B_i = frac(df tau_i) 2^64
+// (u64, from the exact double-double products), so that the phase of trial
+// bin j is A_i + j B_i modulo 2^64 -- an exact integer, as is k times it.
+FC2_D uint64_t frac_fx(double a, double b) {
+    const double p = __dmul_rn(a, b);
+    const double e = fma(a, b, -p);  // a b = p + e exactly
+    const double fl = floor(p);
+    const double r = __dsub_rn(p, fl);  // exact
+    const uint64_t hi = (uint64_t)ldexp(r, 64 - 1) * 2ull + (uint64_t)0;  // r 2^64 (r < 1)
+    const int64_t lo = (int64_t)ldexp(e, 63) * 2;                          // e 2^64
+    return hi + (uint64_t)lo;
+}
+
+__global__ void k_phase_fx(const double* __restrict__ tau, const double* __restrict__ wq,
+                           const double* __restrict__ wp, int64_t n, double f_min, double df,
+                           uint64_t* __restrict__ A, uint64_t* __restrict__ B,
+                           float* __restrict__ wq32, float* __restrict__ wp32) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    A[i] = frac_fx(f_min, tau[i]);
+    B[i] = frac_fx(df, tau[i]);
+    wq32[i] = (float)wq[i];
+    wp32[i] = (float)wp[i];
+}
+
+template <int HM, int TIER>
+__global__ void __launch_bounds__(EX_NT) k_exact_partial(
+    const uint64_t* __restrict__ Aph, const uint64_t* __restrict__ Bph,
+    const float* __restrict__ wq32, const float* __restrict__ wp32,
+    const double* __restrict__ wq, const double* __restrict__ wp, int64_t n,
+    const int32_t* __restrict__ bins32, const int64_t* __restrict__ bins64,
+    const int32_t* __restrict__ count_dev, int64_t count, int64_t base, int64_t cap,
+    int64_t chunk, int nch, int H, double* __restrict__ part) {
+    constexpr int NV = 6 * HM;
+    __shared__ double red[EX_NT / 32][NV];
+    int64_t cnt = count_dev ? (int64_t)(*count_dev) - base : count;
+    if (cnt > cap) cnt = cap;
+    const int64_t items = cnt > 0 ? cnt * nch : 0;
+    const int lane = threadIdx.x & 31, wpi = threadIdx.x >> 5;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int64_t b = it / nch;
+        const int c = (int)(it % nch);
+        const int64_t j = bins32 ? (int64_t)bins32[base + b] : bins64[base + b];
+        double acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+        if (j >= 0) {
+            const uint64_t ju = (uint64_t)j;
+            const int64_t i0 = (int64_t)c * chunk;
+            const int64_t i1 = min(n, i0 + chunk);
+            if constexpr (TIER == 1) {
+                CompSum<float> fa[NV];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) fa[v].init();
+                for (int64_t i = i0 + threadIdx.x; i < i1; i += EX_NT) {
+                    const uint32_t u = (uint32_t)((Aph[i] + ju * Bph[i]) >> 32);
+                    const float a = wq32[i], bb = wp32[i];
+#pragma unroll
+                    for (int k = 1; k <= 2 * HM; ++k) {
+                        if (k <= 2 * H) {
+                            const int32_t ph = (int32_t)(u * (uint32_t)k);  // [-1/2, 1/2) cycles
+                            float sn, cn;
+                            sincospif((float)ph * 4.656612873077393e-10f, &sn, &cn);  // 2^-31
+                            fa[2 * (k - 1)].add(a * cn);
+                            fa[2 * (k - 1) + 1].add(a * sn);
+                            if (k <= H) {
+                                fa[4 * HM + 2 * (k - 1)].add(bb * cn);
+                                fa[4 * HM + 2 * (k - 1) + 1].add(bb * sn);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < NV; ++v) acc[v] = (double)fa[v].s + (double)fa[v].c;
+            } else {
+                for (int64_t i = i0 + threadIdx.x; i < i1; i += EX_NT) {
+                    const int64_t ph = (int64_t)(Aph[i] + ju * Bph[i]);
+                    double s1, c1;
+                    sincospi(ldexp((double)ph, -63), &s1, &c1);
+                    double cr = c1, ci = s1;
+                    const double a = wq[i], bb = wp[i];
+#pragma unroll
+                    for (int k = 0; k < 2 * HM; ++k) {
+                        if (k < 2 * H) {
+                            acc[2 * k] = fma(a, cr, acc[2 * k]);
+                            acc[2 * k + 1] = fma(a, ci, acc[2 * k + 1]);
+                            if (k < H) {
+                                acc[4 * HM + 2 * k] = fma(bb, cr, acc[4 * HM + 2 * k]);
+                                acc[4 * HM + 2 * k + 1] = fma(bb, ci, acc[4 * HM + 2 * k + 1]);
+                            }
+                            const double nr = cr * c1 - ci * s1;
+                            const double ni = cr * s1 + ci * c1;
+                            cr = nr;
+                            ci = ni;
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double x = acc[v];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+            if (lane == 0) red[wpi][v] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x < NV) {
+            double x = 0.0;
+#pragma unroll
+            for (int q = 0; q < EX_NT / 32; ++q) x += red[q][threadIdx.x];
+            part[((b * nch) + c) * NV + threadIdx.x] = x;
+        }
+        __syncthreads();
+    }
+}
+
+template <int HM>
+FC2_D void exact_sys_from_sums(const double* acc, int H, const double* __restrict__ scal,
+                               Sys<double, HM>& S) {
+    const double W = scal[SC_W], chi0 = scal[SC_CHI0];
+    const double sq = (chi0 > 0.0) ? 1.0 / sqrt(W * chi0) : 0.0;
+#pragma unroll
+    for (int k = 0; k <= 2 * HM; ++k) { S.qr[k] = 0.0; S.qi[k] = 0.0; }
+#pragma unroll
+    for (int k = 0; k <= HM; ++k) { S.pr[k] = 0.0; S.pi[k] = 0.0; }
+    S.qr[0] = 1.0;
+    S.pr[0] = scal[SC_S1] * sq;
+#pragma unroll
+    for (int k = 1; k <= 2 * HM; ++k)
+        if (k <= 2 * H) { S.qr[k] = acc[2 * (k - 1)] / W; S.qi[k] = acc[2 * (k - 1) + 1] / W; }
+#pragma unroll
+    for (int k = 1; k <= HM; ++k)
+        if (k <= H) { S.pr[k] = acc[4 * HM + 2 * (k - 1)] * sq; S.pi[k] = acc[4 * HM + 2 * (k - 1) + 1] * sq; }
+}
+
+// Warp w of the CTA owns record b: lanes add the chunk partials of values
+// v = lane, lane + 32, ... in chunk order, then lane 0 holds the full sums.
+template <int HM>
+FC2_D bool warp_sum_chunks(const double* __restrict__ part, int64_t b, int nch, double* sh) {
+    constexpr int NV = 6 * HM;
+    const int lane = threadIdx.x & 31;
+    for (int v = lane; v < NV; v += 32) {
+        double a = 0.0;
+        for (int c = 0; c < nch; ++c) a += part[((b * nch) + c) * NV + v];
+        sh[v] = a;
+    }
+    __syncwarp();
+    return lane == 0;
+}
+
+// Final step of a fix-up round: solve from the exact sums; with a tier-1 round,
+// bins whose estimated error with eps_t1 still exceeds err_fix are queued for
+// tier 2.
+template <int H>
+__global__ void __launch_bounds__(128) k_exact_dchi2(const double* __restrict__ part, int nch,
+                              const int32_t* __restrict__ list,
+                              const int32_t* __restrict__ count_dev, int64_t base, int64_t cap,
+                              const double* __restrict__ scal, double tau_drop, double eps_t1,
+                              double err_fix, int32_t* __restrict__ next,
+                              int32_t* __restrict__ next_count, int64_t next_cap,
+                              double* __restrict__ dchi2, int64_t N) {
+    __shared__ double sh[4][6 * H];
+    int64_t cnt = (int64_t)(*count_dev) - base;
+    if (cnt > cap) cnt = cap;
+    const int w = threadIdx.x >> 5;
+    const int64_t b = (int64_t)blockIdx.x * 4 + w;
+    if (b >= cnt) return;
+    if (!warp_sum_chunks<H>(part, b, nch, sh[w])) return;
+    const int64_t j = list[base + b];
+    Sys<double, H> S;
+    exact_sys_from_sums<H>(sh[w], H, scal, S);
+    double out[H], an2 = 0.0;
+    chol_solve<double, H, true>(S, tau_drop, out, &an2);
+    if (next && !(est_err<double>(an2, 2 * H + 1, eps_t1) <= err_fix)) {
+        int32_t pos = atomicAdd(next_count, 1);
+        if (pos < next_cap) next[pos] = (int32_t)j;
+    }
+    const double chi0 = scal[SC_CHI0];
+#pragma unroll
+    for (int h = 0; h < H; ++h) dchi2[(int64_t)h * N + j] = out[h] * chi0;
+}
+
+// Coefficients of each record (Eq. "eqcoeffs"): back-substitution (dropped
+// columns = 0), rotation of each (sin, cos) pair from the tau = t - T0 frame to
+// absolute time, and xbar added to A_0 (Sec. 3b).
+template <int HM>
+__global__ void __launch_bounds__(128) k_exact_coeffs(const double* __restrict__ part, int nch,
+                               const int64_t* __restrict__ rec_j, int nrec, int H,
+                               const double* __restrict__ scal, double f_min, double df,
+                               double tau_drop, fc2_best* __restrict__ out) {
+    __shared__ double sh[4][6 * HM];
+    const int w = threadIdx.x >> 5;
+    const int r = blockIdx.x * 4 + w;
+    if (r >= nrec) return;
+    if (!warp_sum_chunks<HM>(part, r, nch, sh[w])) return;
+    const int64_t j = rec_j[r];
+    const int Hp = (r < H) ? r + 1 : H;  // best[h] has h + 1 harmonics; peaks have H
+    fc2_best b;
+    b.j = j; b.f = 0; b.dchi2 = 0; b.H = Hp; b.flags = 0;
+    for (int l = 0; l < 2 * FC2_MAX_H + 1; ++l) b.A[l] = 0.0;
+    if (j < 0) { out[r] = b; return; }
+    Sys<double, HM> S;
+    exact_sys_from_sums<HM>(sh[w], H, scal, S);
+    double outv[HM], an2;
+    double Lk[2 * HM + 1][2 * HM + 1];
+    double zk[2 * HM + 1];
+    chol_solve<double, HM, false>(S, tau_drop, outv, &an2, Lk, zk);
+    const int m = 2 * Hp + 1;
+    double A[2 * HM + 1];
+    for (int l = m - 1; l >= 0; --l) {
+        double a = zk[l];
+        for (int k = l + 1; k < m; ++k) a -= Lk[k][l] * A[k];
+        A[l] = (Lk[l][l] > 0.0) ? a / Lk[l][l] : 0.0;
+    }
+    const double W = scal[SC_W], chi0 = scal[SC_CHI0];
+    const double unit = (W > 0.0) ? sqrt(chi0 / W) : 0.0;
+    const double f = f_min + (double)j * df;
+    b.f = f;
+    b.dchi2 = outv[Hp - 1] * chi0;
+    b.A[0] = A[0] * unit + scal[SC_XBAR];
+    const double fT0 = f * scal[SC_T0];
+    for (int h = 1; h <= Hp; ++h) {
+        const double ph = (double)h * (fT0 - floor(fT0));
+        double sn, cn;
+        sincospi(2.0 * (ph - floor(ph)), &sn, &cn);
+        const double as = A[2 * h - 1] * unit, ac = A[2 * h] * unit;
+        b.A[2 * h - 1] = as * cn + ac * sn;
+        b.A[2 * h] = ac * cn - as * sn;
+    }
+    out[r] = b;
+}
+
+// ----------------------------------------------------------------- peaks
+struct Cand { double v; int64_t j; };
+FC2_D bool better(double v1, int64_t j1, double v2, int64_t j2) {
+    return v1 > v2 || (v1 == v2 && j1 < j2);
+}
+FC2_D void warp_best(double& v, int64_t& j) {  // all lanes get the winner
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        int64_t j2 = __shfl_xor_sync(0xffffffffu, j, o);
+        if (better(v2, j2, v, j)) { v = v2; j = j2; }
+    }
+}
+
+constexpr int PK_NT = 256;
+constexpr int PK_PER = 16;
+constexpr int PK_B = PK_NT * PK_PER;
+constexpr int PK_NW = PK_NT / 32;
+constexpr int PK_KMAX = 64;
+
+// Stage 1: per block of PK_B bins, the argmax of every row (ties -> lowest j)
+// and the top-K local maxima of row H (value > left, >= right; edges one-sided).
+__global__ void __launch_bounds__(PK_NT) k_peaks1(const double* __restrict__ d, int64_t N, int H,
+                                                  int K, Cand* __restrict__ amax,
+                                                  Cand* __restrict__ tops, int nblk) {
+    __shared__ Cand wres[PK_NW][FC2_MAX_H];
+    __shared__ Cand wtop[PK_NW][PK_KMAX];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * PK_B;
+    for (int h = 0; h < H; ++h) {
+        const double* row = d + (int64_t)h * N;
+        double v = -INFINITY;
+        int64_t j = INT64_MAX;
+#pragma unroll 4
+        for (int q = 0; q < PK_PER; ++q) {
+            int64_t jj = base + threadIdx.x + (int64_t)q * PK_NT;
+            if (jj < N) {
+                double x = row[jj];
+                if (better(x, jj, v, j)) { v = x; j = jj; }
+            }
+        }
+        warp_best(v, j);
+        if (lane == 0) wres[w][h] = Cand{v, j};
+    }
+    const double* row = d + (int64_t)(H - 1) * N;
+    double cv[PK_PER];
+    int64_t cj[PK_PER];
+#pragma unroll
+    for (int q = 0; q < PK_PER; ++q) {
+        int64_t jj = base + lane + (int64_t)(w * PK_PER + q) * 32;  // warp-contiguous
+        cv[q] = -INFINITY;
+        cj[q] = INT64_MAX;
+        if (jj < N) {
+            double x = row[jj];
+            bool left = (jj == 0) || (x > row[jj - 1]);
+            bool right = (jj == N - 1) || (x >= row[jj + 1]);
+            if (left && right) { cv[q] = x; cj[q] = jj; }
+        }
+    }
+    for (int r = 0; r < K; ++r) {
+        double v = -INFINITY;
+        int64_t j = INT64_MAX;
+#pragma unroll
+        for (int q = 0; q < PK_PER; ++q)
+            if (better(cv[q], cj[q], v, j)) { v = cv[q]; j = cj[q]; }
+        warp_best(v, j);
+#pragma unroll
+        for (int q = 0; q < PK_PER; ++q)
+            if (cj[q] == j) { cv[q] = -INFINITY; cj[q] = INT64_MAX; }
+        if (lane == 0) wtop[w][r] = Cand{v, j};
+    }
+    __syncthreads();
+    if (w == 0) {
+        for (int h = 0; h < H; ++h) {
+            double v = lane < PK_NW ? wres[lane][h].v : -INFINITY;
+            int64_t j = lane < PK_NW ? wres[lane][h].j : INT64_MAX;
+            warp_best(v, j);
+            if (lane == 0) amax[(int64_t)h * nblk + blockIdx.x] = Cand{v, j};
+        }
+        // merge the warps' lists: K rounds over PK_NW * K candidates
+        const int tot = PK_NW * K;
+        for (int r = 0; r < K; ++r) {
+            double v = -INFINITY;
+            int64_t j = INT64_MAX;
+            int pos = -1;
+            for (int e = lane; e < tot; e += 32) {
+                Cand c = wtop[e / K][e % K];
+                if (better(c.v, c.j, v, j)) { v = c.v; j = c.j; pos = e; }
+            }
+            double bv = v;
+            int64_t bj = j;
+            warp_best(bv, bj);
+            if (pos >= 0 && j == bj && bj != INT64_MAX) wtop[pos / K][pos % K] = Cand{-INFINITY, INT64_MAX};
+            __syncwarp();
+            if (lane == 0) tops[(int64_t)blockIdx.x * K + r] = Cand{bv, bj};
+        }
+    }
+}
+
+// Stage 2: one block merges the per-block results.
+__global__ void __launch_bounds__(1024) k_peaks2(const Cand* __restrict__ amax,
+                                                 const Cand* __restrict__ tops, int nblk, int H,
+                                                 int K, int64_t* __restrict__ best_j,
+                                                 int64_t* __restrict__ peak_j) {
+    __shared__ Cand ws[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int h = 0; h < H; ++h) {
+        double v = -INFINITY;
+        int64_t j = INT64_MAX;
+        for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+            Cand c = amax[(int64_t)h * nblk + b];
+            if (better(c.v, c.j, v, j)) { v = c.v; j = c.j; }
+        }
+        warp_best(v, j);
+        if (lane == 0) ws[w] = Cand{v, j};
+        __syncthreads();
+        if (w == 0) {
+            v = lane < nw ? ws[lane].v : -INFINITY;
+            j = lane < nw ? ws[lane].j : INT64_MAX;
+            warp_best(v, j);
+            if (lane == 0) best_j[h] = (j == INT64_MAX) ? -1 : j;
+        }
+        __syncthreads();
+    }
+    const int64_t total = (int64_t)nblk * K;
+    double pv = INFINITY;
+    int64_t pj = -1;
+    for (int r = 0; r < K; ++r) {
+        double v = -INFINITY;
+        int64_t j = INT64_MAX;
+        for (int64_t b = threadIdx.x; b < total; b += blockDim.x) {
+            Cand c = tops[b];
+            if (c.j != INT64_MAX && better(pv, pj, c.v, c.j) && better(c.v, c.j, v, j)) {
+                v = c.v;
+                j = c.j;
+            }
+        }
+        warp_best(v, j);
+        if (lane == 0) ws[w] = Cand{v, j};
+        __syncthreads();
+        if (w == 0) {
+            v = lane < nw ? ws[lane].v : -INFINITY;
+            j = lane < nw ? ws[lane].j : INT64_MAX;
+            warp_best(v, j);
+            if (lane == 0) { ws[0] = Cand{v, j}; peak_j[r] = (j == INT64_MAX) ? -1 : j; }
+        }
+        __syncthreads();
+        pv = ws[0].v;
+        pj = ws[0].j;
+        __syncthreads();
+        if (pj == INT64_MAX) pv = -INFINITY;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+static SolveParams solve_params(const fc2_plan_s* p) {
+    SolveParams sp;
+    sp.N = p->N;
+    sp.tau = p->tau;
+    sp.eps_spec = p->fp64 ? 1e-13 : 1e-7;
+    sp.eps_f32 = 3e-7;
+    sp.err_fix = 2e-5;
+    const double W = p->scal[SC_W], chi0 = p->scal[SC_CHI0];
+    sp.sq = 1.0 / W;
+    sp.sp = (chi0 > 0.0) ? 1.0 / sqrt(W * chi0) : 0.0;
+    sp.chi0 = chi0;
+    sp.s1n = p->scal[SC_S1] * sp.sp;
+    return sp;
+}
+
+template <typename TS>
+static cudaError_t assemble_impl(fc2_plan_s* p, cudaStream_t s) {
+    const SolveParams sp = solve_params(p);
+    dim3 grid((unsigned)((p->N + 127) / 128));
+    const cpx<TS>* spec = (const cpx<TS>*)p->d_spec;
+    const TS* dec = (const TS*)p->d_dec;
+    cudaMemsetAsync(p->d_flag_count, 0, 4 * sizeof(int32_t), s);
+    // float path: list = re-solve list (counter 1); double path: exact list (counter 0)
+    int32_t* list = p->fp64 ? p->d_flag_list : p->d_flag_list + p->flag_cap;
+    int32_t* cnt = p->fp64 ? p->d_flag_count : p->d_flag_count + 1;
+#define FC2_ASM(HH)                                                                           \
+    case HH:                                                                                  \
+        k_assemble<TS, HH><<<grid, 128, 0, s>>>(spec, dec, p->d_dchi2, sp, list, cnt,         \
+                                                p->flag_cap);                                 \
+        if (!p->fp64)                                                                         \
+            k_resolve<HH><<<4 * 152, 128, 0, s>>>((const cpx<float>*)spec, (const float*)dec, \
+                                                  p->d_dchi2, sp, list, cnt, p->flag_cap,     \
+                                                  p->d_flag_list, p->d_flag_count,            \
+                                                  p->flag_cap);                               \
+        break;
+    switch (p->H) {
+        FC2_ASM(1) FC2_ASM(2) FC2_ASM(3) FC2_ASM(4) FC2_ASM(5) FC2_ASM(6) FC2_ASM(7) FC2_ASM(8)
+        default: return cudaErrorInvalidValue;
+    }
+#undef FC2_ASM
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(fc2_plan_s* p, cudaStream_t s) {
+    return p->fp64 ? assemble_impl<double>(p, s) : assemble_impl<float>(p, s);
+}
+
+void exact_geometry(int64_t n, int64_t* chunk, int* nch) {
+    int64_t c = (n + 63) / 64;
+    if (c < 2048) c = 2048;
+    c = ((c + EX_NT - 1) / EX_NT) * EX_NT;
+    *chunk = c;
+    *nch = (int)((n + c - 1) / c);
+}
+
+template <int HH, int TIER>
+static void launch_partial(fc2_plan_s* p, const int32_t* b32, const int64_t* b64,
+                           const int32_t* cnt_dev, int64_t cnt, int64_t base, int64_t cap,
+                           cudaStream_t s) {
+    int64_t chunk;
+    int nch;
+    exact_geometry(p->n, &chunk, &nch);
+    k_exact_partial<HH, TIER><<<4 * 152, EX_NT, 0, s>>>(p->d_phA, p->d_phB, p->d_wq32, p->d_wp32,
+                                                        p->d_wq, p->d_wp, p->n, b32, b64, cnt_dev,
+                                                        cnt, base, cap, chunk, nch, p->H,
+                                                        p->d_part);
+}
+
+// Exact fix-up of the flagged bins (list 0, `count` entries): a tier-1 round,
+// then tier 2 (all double) for the bins tier 1 could not settle.  Rounds of at
+// most exact_cap bins.  Returns the number of tier-2 bins through *n2.
+template <int HH>
+static cudaError_t fixup_h(fc2_plan_s* p, int64_t count, int64_t* n2, cudaStream_t s) {
+    int64_t chunk;
+    int nch;
+    exact_geometry(p->n, &chunk, &nch);
+    const int64_t cap = p->exact_cap;
+    const double eps_t1 = 2e-7 * p->scal[SC_RW];
+    int32_t* list2 = p->d_flag_list + p->flag_cap;  // re-solve list is consumed by now
+    int32_t* cnt2 = p->d_flag_count + 2;
+    cudaMemsetAsync(cnt2, 0, 4, s);
+    for (int64_t base = 0; base < count; base += cap) {
+        const int64_t nb = std::min(cap, count - base);
+        launch_partial<HH, 1>(p, p->d_flag_list, nullptr, p->d_flag_count, 0, base, cap, s);
+        k_exact_dchi2<HH><<<(unsigned)((nb + 3) / 4), 128, 0, s>>>(
+            p->d_part, nch, p->d_flag_list, p->d_flag_count, base, cap, p->d_scal, 1e-13, eps_t1,
+            2e-5, list2, cnt2, p->flag_cap, p->d_dchi2, p->N);
+    }
+    int32_t c2 = 0;
+    cudaMemcpyAsync(&c2, cnt2, 4, cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    *n2 = c2;
+    for (int64_t base = 0; base < c2; base += cap) {
+        const int64_t nb = std::min(cap, (int64_t)c2 - base);
+        launch_partial<HH, 2>(p, list2, nullptr, cnt2, 0, base, cap, s);
+        k_exact_dchi2<HH><<<(unsigned)((nb + 3) / 4), 128, 0, s>>>(
+            p->d_part, nch, list2, cnt2, base, cap, p->d_scal, 1e-13, 0.0, 2e-5, nullptr,
+            nullptr, 0, p->d_dchi2, p->N);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fixup(fc2_plan_s* p, int64_t count, cudaStream_t s) {
+    int64_t n2 = 0;
+    cudaError_t e;
+    switch (p->H) {
+        case 1: e = fixup_h<1>(p, count, &n2, s); break;
+        case 2: e = fixup_h<2>(p, count, &n2, s); break;
+        case 3: e = fixup_h<3>(p, count, &n2, s); break;
+        case 4: e = fixup_h<4>(p, count, &n2, s); break;
+        case 5: e = fixup_h<5>(p, count, &n2, s); break;
+        case 6: e = fixup_h<6>(p, count, &n2, s); break;
+        case 7: e = fixup_h<7>(p, count, &n2, s); break;
+        case 8: e = fixup_h<8>(p, count, &n2, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    p->last_exact2_count = n2;
+    return e;
+}
+
+size_t peaks_scratch_bytes(int64_t N, int H, int K) {
+    int64_t nblk = (N + PK_B - 1) / PK_B;
+    return (size_t)nblk * (H + K) * sizeof(Cand) + (size_t)(H + K) * 16 + 4096;
+}
+
+cudaError_t launch_peaks(fc2_plan_s* p, cudaStream_t s) {
+    const int64_t nblk = (p->N + PK_B - 1) / PK_B;
+    const int H = p->H, K = p->top_k;
+    char* base = (char*)p->d_red;
+    Cand* amax = (Cand*)base;
+    Cand* tops = amax + nblk * H;
+    int64_t* rec_j = (int64_t*)(tops + nblk * K);
+    k_peaks1<<<(unsigned)nblk, PK_NT, 0, s>>>(p->d_dchi2, p->N, H, K, amax, tops, (int)nblk);
+    k_peaks2<<<1, 1024, 0, s>>>(amax, tops, (int)nblk, H, K, rec_j, rec_j + H);
+    int64_t chunk;
+    int nch;
+    exact_geometry(p->n, &chunk, &nch);
+    const int nrec = H + K;
+#define FC2_CO(HH)                                                                            \
+    case HH:                                                                                  \
+        launch_partial<HH, 1>(p, nullptr, rec_j, nullptr, nrec, 0, nrec, s);                  \
+        k_exact_coeffs<HH><<<(nrec + 3) / 4, 128, 0, s>>>(p->d_part, nch, rec_j, nrec, H, p->d_scal,        \
+                                            p->f_min, p->df, 1e-13, p->d_best);               \
+        break;
+    switch (H) {
+        FC2_CO(1) FC2_CO(2) FC2_CO(3) FC2_CO(4) FC2_CO(5) FC2_CO(6) FC2_CO(7) FC2_CO(8)
+        default: return cudaErrorInvalidValue;
+    }
+#undef FC2_CO
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phase_fx(fc2_plan_s* p, cudaStream_t s) {
+    k_phase_fx<<<(unsigned)((p->n + 255) / 256), 256, 0, s>>>(p->d_tau, p->d_wq, p->d_wp, p->n,
+                                                             p->f_min, p->df, p->d_phA, p->d_phB,
+                                                             p->d_wq32, p->d_wp32);
+    return cudaGetLastError();
+}
+
+size_t exact_scratch_bytes(int64_t n, int H, int64_t cap) {
+    int64_t chunk;
+    int nch;
+    exact_geometry(n, &chunk, &nch);
+    return (size_t)cap * nch * 6 * H * sizeof(double);
+}
+
+}  // namespace fc2
