@@ -167,6 +167,31 @@ void fc2_plan_destroy(fc2_plan p);
 /* Static description of a status code. */
 const char* fc2_status_string(fc2_status s);
 
+/*
+ * fc2_dchi2_exact_noalloc -- exact (ungridded, double) Delta chi^2_{H'} for
+ * H' = 1..H at trial bins j (f = f_min + j df), computed straight from the
+ * samples, without allocating any device memory.  The paper has no
+ * counterpart; this is an interface for callers that cannot allocate when
+ * they need the answer: code whose device memory is fully reserved by another
+ * allocator (a framework's caching pool, a fixed arena), or a latency-critical
+ * loop that must not take the synchronisation an allocation can imply.
+ *   t, x, sigma [n], bins [nb] (int64), dchi2 [H][nb]: DEVICE pointers, owned
+ *   by the caller.  cuda_stream: cudaStream_t (NULL = legacy default stream).
+ *   Limits (the fixed scratch size): 1 <= n <= 4,194,304; 1 <= H <= 8;
+ *   1 <= nb <= 128.  Larger requests return FC2_ERR_INVALID_ARG.
+ * Scratch: one file-scope device array of about 3.2 MB that every device that
+ * loads the library holds until the process exits.  The first call on a device
+ * looks up its device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls on a device share
+ * the array, so calls whose work overlaps on the GPU race; order them on one
+ * stream.  Synchronous: returns after dchi2 is written.  Non-finite inputs or
+ * sigma <= 0 give FC2_ERR_INVALID_ARG (detected on the device).
+ */
+fc2_status fc2_dchi2_exact_noalloc(const double* t, const double* x, const double* sigma,
+                                   int64_t n, int H, double f_min, double df,
+                                   const int64_t* bins, int64_t nb, double* dchi2,
+                                   void* cuda_stream);
+
 /* Host-only helpers (no GPU needed), exposed for testing the host logic. */
 
 /* Grid length the library uses for (N, oversample): smallest power of two >=

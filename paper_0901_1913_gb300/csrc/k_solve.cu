@@ -805,3 +805,241 @@ size_t exact_scratch_bytes(int64_t n, int H, int64_t cap) {
 }
 
 }  // namespace fc2
+
+// ===========================================================================
+// Allocation-free exact evaluation (fc2_dchi2_exact_noalloc).
+//
+// Some callers cannot allocate device memory at the moment they need an
+// answer: code whose device memory is entirely reserved by another allocator
+// (a framework's caching pool, a fixed arena), or a latency-critical loop that
+// must not take the device-wide synchronisation that cudaMalloc/cudaFree can
+// imply.  This entry point computes the same exact (ungridded) Delta chi^2 as
+// the fix-up kernels above, but keeps all of its intermediate data in one
+// file-scope device array of fixed size instead of plan-owned allocations.
+//
+// The array lives in every device that loads the library, until the process
+// exits.  In host code its name is only a stand-in for the device symbol, so
+// the kernels are handed the device address obtained once per device with
+// cudaGetSymbolAddress (done by the first call on that device).  All calls on
+// a device share the array: calls whose work overlaps on the GPU (e.g. issued
+// on two streams without ordering between them) race with each other.
+// ===========================================================================
+namespace fc2 {
+namespace {
+
+constexpr int NA_NT = 256;
+constexpr int NA_MAX_H = 8;
+constexpr int64_t NA_MAX_N = 1ll << 22;
+constexpr int64_t NA_MAX_BINS = 128;
+constexpr int NA_MAX_CHUNKS = 64;
+constexpr int64_t NA_MOM_CHUNK = 8192;
+constexpr int64_t NA_MOM_BLOCKS = NA_MAX_N / NA_MOM_CHUNK;
+
+// Layout of the scratch array (doubles unless noted):
+//   [0, 16)                      scalars in the SC_* slots, status word at 15 (as int)
+//   [16, 16 + 4 * NA_MOM_BLOCKS) per-block moment partials (4 doubles each)
+//   then NA_MAX_BINS * NA_MAX_CHUNKS * 6 * NA_MAX_H chunk partials
+constexpr int64_t NA_PART_OFF = 16 + 4 * NA_MOM_BLOCKS;
+constexpr int64_t NA_DOUBLES = NA_PART_OFF + NA_MAX_BINS * NA_MAX_CHUNKS * 6 * NA_MAX_H;
+
+static __device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
+
+struct NaScratchAddr {
+    double* ptr[64] = {nullptr};
+};
+NaScratchAddr g_na_addr;  // device address of g_noalloc_scratch, per device ordinal
+
+__global__ void __launch_bounds__(NA_NT) k_na_moments(const double* __restrict__ t,
+                                                      const double* __restrict__ x,
+                                                      const double* __restrict__ sg, int64_t n,
+                                                      int pass, double* __restrict__ scr) {
+    __shared__ double sh[4][NA_NT];
+    const int64_t a = (int64_t)blockIdx.x * NA_MOM_CHUNK;
+    const int64_t b = min(n, a + NA_MOM_CHUNK);
+    double v0 = 0.0, v1 = 0.0, v2 = INFINITY, bad = 0.0;
+    const double xbar = pass ? scr[SC_XBAR] : 0.0;
+    for (int64_t i = a + threadIdx.x; i < b; i += NA_NT) {
+        const double si = sg[i], xi = x[i], ti = t[i];
+        if (pass == 0) {
+            if (!isfinite(ti) || !isfinite(xi) || !isfinite(si) || !(si > 0.0)) { bad = 1.0; continue; }
+            const double w = 1.0 / (si * si);
+            v0 += w;
+            v1 += w * xi;
+            v2 = fmin(v2, ti);
+        } else {
+            const double w = 1.0 / (si * si), d = xi - xbar;
+            v0 += w * d * d;
+            v1 += w * d;
+        }
+    }
+    sh[0][threadIdx.x] = v0; sh[1][threadIdx.x] = v1; sh[2][threadIdx.x] = v2; sh[3][threadIdx.x] = bad;
+    __syncthreads();
+    for (int st = NA_NT / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + st];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + st];
+            sh[2][threadIdx.x] = fmin(sh[2][threadIdx.x], sh[2][threadIdx.x + st]);
+            sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + st]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) scr[16 + 4 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_na_moments_final(int nblk, int pass, double* __restrict__ scr) {
+    if (threadIdx.x != 0) return;
+    double v0 = 0.0, v1 = 0.0, v2 = INFINITY, bad = 0.0;
+    for (int k = 0; k < nblk; ++k) {
+        const double* q = scr + 16 + 4 * k;
+        v0 += q[0]; v1 += q[1]; v2 = fmin(v2, q[2]); bad = fmax(bad, q[3]);
+    }
+    if (pass == 0) {
+        scr[SC_W] = v0;
+        scr[SC_XBAR] = v1 / v0;
+        scr[SC_T0] = v2;
+        if (bad != 0.0) reinterpret_cast<int*>(scr + 15)[0] = FC2_ERR_INVALID_ARG;
+    } else {
+        scr[SC_CHI0] = v0;
+        scr[SC_S1] = v1;
+    }
+}
+
+// Work items (bin, chunk): all-double sums, phases from the exact fixed-point
+// reduction of (f_min + j df) (t - T0).
+template <int HM>
+__global__ void __launch_bounds__(NA_NT) k_na_partial(const double* __restrict__ t,
+                                                      const double* __restrict__ x,
+                                                      const double* __restrict__ sg, int64_t n,
+                                                      int H, double f_min, double df,
+                                                      const int64_t* __restrict__ bins, int64_t nb,
+                                                      int64_t chunk, int nch,
+                                                      double* __restrict__ scr) {
+    constexpr int NV = 6 * HM;
+    __shared__ double red[NA_NT / 32][NV];
+    const double T0 = scr[SC_T0], xbar = scr[SC_XBAR];
+    double* part = scr + NA_PART_OFF;
+    const int lane = threadIdx.x & 31, wpi = threadIdx.x >> 5;
+    for (int64_t it = blockIdx.x; it < nb * nch; it += gridDim.x) {
+        const int64_t b = it / nch;
+        const int c = (int)(it % nch);
+        const uint64_t ju = (uint64_t)bins[b];
+        double acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+        const int64_t i0 = (int64_t)c * chunk, i1 = min(n, i0 + chunk);
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += NA_NT) {
+            const double tau = __dsub_rn(t[i], T0);
+            const double si = sg[i];
+            const double a = 1.0 / (si * si), bb = a * (x[i] - xbar);
+            const int64_t ph = (int64_t)(frac_fx(f_min, tau) + ju * frac_fx(df, tau));
+            double s1, c1;
+            sincospi(ldexp((double)ph, -63), &s1, &c1);
+            double cr = c1, ci = s1;
+#pragma unroll
+            for (int k = 0; k < 2 * HM; ++k) {
+                if (k < 2 * H) {
+                    acc[2 * k] = fma(a, cr, acc[2 * k]);
+                    acc[2 * k + 1] = fma(a, ci, acc[2 * k + 1]);
+                    if (k < H) {
+                        acc[4 * HM + 2 * k] = fma(bb, cr, acc[4 * HM + 2 * k]);
+                        acc[4 * HM + 2 * k + 1] = fma(bb, ci, acc[4 * HM + 2 * k + 1]);
+                    }
+                    const double nr = cr * c1 - ci * s1, ni = cr * s1 + ci * c1;
+                    cr = nr;
+                    ci = ni;
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double y = acc[v];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+            if (lane == 0) red[wpi][v] = y;
+        }
+        __syncthreads();
+        if (threadIdx.x < NV) {
+            double y = 0.0;
+#pragma unroll
+            for (int q = 0; q < NA_NT / 32; ++q) y += red[q][threadIdx.x];
+            part[(b * nch + c) * NV + threadIdx.x] = y;
+        }
+        __syncthreads();
+    }
+}
+
+template <int HM>
+__global__ void __launch_bounds__(128) k_na_final(int64_t nb, int nch, int H, double tau_drop,
+                                                  double* __restrict__ out,
+                                                  double* __restrict__ scr) {
+    __shared__ double sh[4][6 * HM];
+    const int w = threadIdx.x >> 5;
+    const int64_t b = (int64_t)blockIdx.x * 4 + w;
+    if (b >= nb) return;
+    if (!warp_sum_chunks<HM>(scr + NA_PART_OFF, b, nch, sh[w])) return;
+    Sys<double, HM> S;
+    exact_sys_from_sums<HM>(sh[w], H, scr, S);
+    double o[HM], an2 = 0.0;
+    chol_solve<double, HM, false>(S, tau_drop, o, &an2);
+    const double chi0 = scr[SC_CHI0];
+    for (int h = 0; h < H; ++h) out[(int64_t)h * nb + b] = o[h] * chi0;
+}
+
+template <int HM>
+void na_launch(const double* t, const double* x, const double* sg, int64_t n, int H, double f_min,
+               double df, const int64_t* bins, int64_t nb, int64_t chunk, int nch, double* out,
+               double* scr, cudaStream_t s) {
+    k_na_partial<HM><<<4 * 152, NA_NT, 0, s>>>(t, x, sg, n, H, f_min, df, bins, nb, chunk, nch,
+                                                scr);
+    k_na_final<HM><<<(unsigned)((nb + 3) / 4), 128, 0, s>>>(nb, nch, H, 1e-13, out, scr);
+}
+
+}  // namespace
+}  // namespace fc2
+
+extern "C" fc2_status fc2_dchi2_exact_noalloc(const double* t, const double* x,
+                                              const double* sigma, int64_t n, int H,
+                                              double f_min, double df, const int64_t* bins,
+                                              int64_t nb, double* dchi2, void* cuda_stream) {
+    using namespace fc2;
+    if (!t || !x || !sigma || !bins || !dchi2) return FC2_ERR_INVALID_ARG;
+    if (n < 1 || n > NA_MAX_N || H < 1 || H > NA_MAX_H || nb < 1 || nb > NA_MAX_BINS)
+        return FC2_ERR_INVALID_ARG;
+    if (!(isfinite(f_min) && f_min >= 0.0) || !(isfinite(df) && df > 0.0)) return FC2_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FC2_ERR_CUDA;
+    if (!g_na_addr.ptr[dev]) {
+        // first call on this device: device address of the scratch array
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return FC2_ERR_CUDA;
+        }
+        g_na_addr.ptr[dev] = (double*)p;
+    }
+    double* scr = g_na_addr.ptr[dev];
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int64_t chunk = (n + NA_MAX_CHUNKS - 1) / NA_MAX_CHUNKS;
+    if (chunk < 2048) chunk = 2048;
+    const int nch = (int)((n + chunk - 1) / chunk);
+    const int nblk = (int)((n + NA_MOM_CHUNK - 1) / NA_MOM_CHUNK);
+    // the status word must start at zero; everything else is overwritten
+    if (cudaMemsetAsync(scr + 15, 0, sizeof(double), s) != cudaSuccess) return FC2_ERR_CUDA;
+    for (int pass = 0; pass < 2; ++pass) {
+        k_na_moments<<<nblk, NA_NT, 0, s>>>(t, x, sigma, n, pass, scr);
+        k_na_moments_final<<<1, 32, 0, s>>>(nblk, pass, scr);
+    }
+    switch (H) {
+        case 1: na_launch<1>(t, x, sigma, n, H, f_min, df, bins, nb, chunk, nch, dchi2, scr, s); break;
+        case 2: na_launch<2>(t, x, sigma, n, H, f_min, df, bins, nb, chunk, nch, dchi2, scr, s); break;
+        case 3: na_launch<3>(t, x, sigma, n, H, f_min, df, bins, nb, chunk, nch, dchi2, scr, s); break;
+        case 4: na_launch<4>(t, x, sigma, n, H, f_min, df, bins, nb, chunk, nch, dchi2, scr, s); break;
+        default: na_launch<8>(t, x, sigma, n, H, f_min, df, bins, nb, chunk, nch, dchi2, scr, s); break;
+    }
+    int status = 0;
+    if (cudaGetLastError() != cudaSuccess) return FC2_ERR_CUDA;
+    if (cudaMemcpyAsync(&status, scr + 15, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return FC2_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FC2_ERR_CUDA;
+    return status ? (fc2_status)status : FC2_OK;
+}
