@@ -92,6 +92,10 @@ def load():
         lib.fc2_debug_spectra.restype = i32
         lib.fc2_debug_counts.argtypes = [_P, _P]
         lib.fc2_debug_counts.restype = None
+        lib.fc2_debug_batch_launches.argtypes = []
+        lib.fc2_debug_batch_launches.restype = i64
+        lib.fc2_debug_batch_counts.argtypes = [_P]
+        lib.fc2_debug_batch_counts.restype = None
         lib.fc2_stage_timing.argtypes = [_P, i32]
         lib.fc2_stage_timing.restype = i32
         lib.fc2_stage_times.argtypes = [_P, _P, _P, _P]
@@ -237,3 +241,40 @@ def periodogram(t, x, sigma, H, f_min, df, N, oversample=2, prec="fp64", **kw):
     """One-shot: Delta chi^2 [H, N], best records, peak records, chi2_0."""
     with Plan(t, x, sigma, H, f_min, df, N, oversample, prec, **kw) as p:
         return p.execute()
+
+
+def execute_batched(offsets, t, x, sigma, H, f_min, df, N, oversample=2, prec="mixed", top_k=8,
+                    kernel_width=0, dchi2=None, stream=None, device=0):
+    """Many curves in one call (fc2_execute_batched).  offsets [C+1], t/x/sigma
+    concatenated (numpy host arrays, or CUDA tensors -> read in place); H, f_min,
+    df, N per curve.  dchi2: optional preallocated float32 output (numpy or
+    CUDA tensor) of sum_c H_c N_c elements.  Returns (dchi2, peaks [C][top_k]
+    as dicts, stats dict)."""
+    lib = load()
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    C = offsets.size - 1
+    H = np.ascontiguousarray(np.broadcast_to(H, (C,)), dtype=np.int32)
+    f_min = np.ascontiguousarray(np.broadcast_to(f_min, (C,)), dtype=np.float64)
+    df = np.ascontiguousarray(np.broadcast_to(df, (C,)), dtype=np.float64)
+    N = np.ascontiguousarray(np.broadcast_to(N, (C,)), dtype=np.int64)
+    dev = _is_dev(t)
+    if not dev:
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    total = int(np.sum(H.astype(np.int64) * N))
+    if dchi2 is None:
+        dchi2 = np.empty(total, dtype=np.float32)
+    K = int(top_k or 8)
+    peaks = (Best * (C * K))()
+    opt = make_options(prec, kernel_width, K, 0.0, stream, device, inputs_on_device=dev)
+    rc = lib.fc2_execute_batched(C, offsets.ctypes.data, _ptr(t), _ptr(x), _ptr(sigma),
+                                 H.ctypes.data, f_min.ctypes.data, df.ctypes.data, N.ctypes.data,
+                                 int(oversample), ctypes.byref(opt), _ptr(dchi2),
+                                 ctypes.cast(peaks, _P))
+    _check(rc, "fc2_execute_batched")
+    st = np.zeros(3, dtype=np.int64)
+    lib.fc2_debug_batch_counts(st.ctypes.data)
+    recs = [[peaks[c * K + r].as_dict() for r in range(K)] for c in range(C)]
+    return dchi2, recs, dict(launches=int(lib.fc2_debug_batch_launches()),
+                             resolved=int(st[0]), exact=int(st[1]), exact_double=int(st[2]))

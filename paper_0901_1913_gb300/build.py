@@ -12,7 +12,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfc2.so")
-SOURCES = ["fc2_api.cu", "k_prep.cu", "k_fft.cu", "k_solve.cu", "k_adjoint.cu", "fc2_host.cpp"]
+SOURCES = ["fc2_api.cu", "k_prep.cu", "k_fft.cu", "k_solve.cu", "k_batch.cu", "k_adjoint.cu",
+           "fc2_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

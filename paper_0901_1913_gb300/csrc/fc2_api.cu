@@ -13,6 +13,9 @@
 
 using namespace fc2;
 
+static int64_t g_last_batch_launches = 0;
+static int64_t g_last_batch_stats[3] = {0, 0, 0};
+
 namespace {
 
 struct Guard {  // returns FC2_ERR_CUDA on the first failing runtime call
@@ -368,11 +371,15 @@ void fc2_plan_destroy(fc2_plan p) {
 fc2_status fc2_execute_batched(int64_t C, const int64_t* offsets, const double* t,
                                const double* x, const double* sigma, const int* H,
                                const double* f_min, const double* df, const int64_t* N,
-                               int oversample, const fc2_options* opt, float* dchi2,
+                               int oversample, const fc2_options* opt_in, float* dchi2,
                                fc2_best* peaks) {
-    (void)C; (void)offsets; (void)t; (void)x; (void)sigma; (void)H; (void)f_min; (void)df;
-    (void)N; (void)oversample; (void)opt; (void)dchi2; (void)peaks;
-    return FC2_ERR_UNSUPPORTED;
+    fc2_options opt;
+    if (opt_in) opt = *opt_in; else fc2_options_default(&opt);
+    int64_t nl = 0;
+    fc2_status st = batched_execute(C, offsets, t, x, sigma, H, f_min, df, N, oversample, opt,
+                                    dchi2, peaks, &nl, g_last_batch_stats);
+    g_last_batch_launches = nl;
+    return st;
 }
 
 fc2_status fc2_backward(fc2_plan p, int K, const int64_t* peak_j, const double* grad_out,
@@ -422,6 +429,16 @@ fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im) {
 }
 
 double fc2_debug_t0(fc2_plan p) { return p ? p->scal[SC_T0] : 0.0; }
+
+/* Kernels launched by the last fc2_execute_batched call of this process. */
+int64_t fc2_debug_batch_launches(void) { return g_last_batch_launches; }
+
+/* Bins of the last fc2_execute_batched call that were re-solved in double,
+ * recomputed from exact sums, and of those recomputed all in double. */
+void fc2_debug_batch_counts(int64_t* out3) {
+    if (out3)
+        for (int i = 0; i < 3; ++i) out3[i] = g_last_batch_stats[i];
+}
 
 /* Stage timing: while enabled, each execute records CUDA events on the plan's
  * stream around (0) phase reduction + spreading, (1) FFT passes, (2) assembly

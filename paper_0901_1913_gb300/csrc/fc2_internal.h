@@ -95,6 +95,9 @@ struct fc2_plan_s {
     int32_t* d_flag_count = nullptr;
     int64_t flag_cap = 0;
     int64_t* d_L = nullptr;    // [G] occupied extent of each grid
+    int64_t* d_slot_soff = nullptr;  // batch: per-transform offset into the sample arrays
+    int64_t* d_slot_n = nullptr;     // batch: per-transform sample count
+    std::vector<int64_t> h_slot_soff, h_slot_n;  // batch: host copies
     double* d_part = nullptr;  // exact-sum partials [exact_cap][nch][6H]
     uint64_t* d_phA = nullptr; // fixed-point phases frac(f_min tau) 2^64 [n]
     uint64_t* d_phB = nullptr; // fixed-point phases frac(df tau) 2^64 [n]
@@ -136,6 +139,7 @@ cudaError_t launch_gather_sorted(const double* t, const double* x, const double*
                                  const int32_t* perm, int64_t n, const double* scal,
                                  double* tau, double* wq, double* wp, cudaStream_t s);
 cudaError_t launch_phase(fc2_plan_s* p, cudaStream_t s);
+cudaError_t sort_wrapping_keys(fc2_plan_s* p, cudaStream_t s);
 cudaError_t launch_spread(fc2_plan_s* p, cudaStream_t s);
 
 // k_fft.cu
@@ -156,6 +160,13 @@ cudaError_t launch_phase_fx(fc2_plan_s* p, cudaStream_t s);
 cudaError_t launch_backward(fc2_plan_s* p, int K, const int64_t* d_j, const double* d_g,
                             double* d_fref, double* d_dref, double* d_df, double* d_dx,
                             double* d_ds, cudaStream_t s);
+
+// k_batch.cu
+fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, const double* x,
+                           const double* sigma, const int* H, const double* fmin,
+                           const double* df, const int64_t* N, int oversample,
+                           const fc2_options& opt, float* dchi2, fc2_best* peaks,
+                           int64_t* launches_out, int64_t* stats_out);
 
 // host helpers (fc2_host.cpp)
 void gauss_legendre(int nq, double* x, double* w);

@@ -1,0 +1,175 @@
+// fc2_solve.cuh -- per-frequency normal equations and their bordered Cholesky
+// solve, shared by the single-curve and batched kernels.  Not part of the ABI.
+//
+// Paper: Sec. 2 Eqs. "eqalphafirst".."eqalpha" (alpha from C', S' at (h -+ h') f),
+// the beta equations (C, S at h f), Eq. "eqchix" (chi2_min = X - beta^T alpha^-1 beta),
+// Eq. "eqcoeffs" (A = alpha^-1 beta), Sec. 3c (Delta chi^2 with mean-subtracted data).
+#pragma once
+#include "fc2_common.cuh"
+#include "fc2_internal.h"
+
+namespace fc2 {
+
+// Normalised system: alpha' = alpha / W, beta' = beta / sqrt(W chi2_0), so
+// Delta chi^2' = Delta chi^2 / chi2_0 lies in [0, 1].
+template <typename TC, int H>
+struct Sys {
+    TC qr[2 * H + 1], qi[2 * H + 1], pr[H + 1], pi[H + 1];
+
+    FC2_HD TC alpha(int l, int k) const {
+        if (l < k) { int t = l; l = k; k = t; }
+        if (l == 0) return qr[0];
+        const int hl = (l + 1) >> 1;
+        const bool sl = (l & 1);
+        if (k == 0) return sl ? qi[hl] : qr[hl];
+        const int hk = (k + 1) >> 1;
+        const bool sk = (k & 1);
+        const int d = hl > hk ? hl - hk : hk - hl;
+        const TC sg = hl > hk ? (TC)1 : (hl < hk ? (TC)-1 : (TC)0);
+        const int s = hl + hk;
+        const TC h = (TC)0.5;
+        if (sl && sk) return h * (qr[d] - qr[s]);
+        if (!sl && !sk) return h * (qr[d] + qr[s]);
+        if (sl && !sk) return h * (qi[s] + sg * qi[d]);   // sin(hl) cos(hk)
+        return h * (qi[s] - sg * qi[d]);                  // cos(hl) sin(hk)
+    }
+    FC2_HD TC beta(int l) const {
+        if (l == 0) return pr[0];
+        const int h = (l + 1) >> 1;
+        return (l & 1) ? pi[h] : pr[h];
+    }
+};
+
+// Factor and solve; out[H'-1] = Delta chi^2'_{H'}.  Returns the minimum
+// relative pivot over all columns (clamped at 0).  With COEF, *anorm2 receives
+// max over H' of |A^{(H')}|^2 (A^{(H')} = the H'-harmonic coefficients, by
+// back-substitution L^T A = z on the leading block), the sensitivity of the
+// result to errors in alpha and beta.  Optionally keeps L and z.
+template <typename TC, int H, bool COEF>
+FC2_D TC chol_solve(const Sys<TC, H>& S, TC tau, TC* out, TC* anorm2,
+                    TC (*Lkeep)[2 * H + 1] = nullptr, TC* zkeep = nullptr, int Hrun = H) {
+    constexpr int m = 2 * H + 1;
+    TC L[m][m];
+    TC z[m], dinv[m];
+    TC acc = (TC)0, dmin = (TC)1;
+#pragma unroll
+    for (int l = 0; l < m; ++l) {
+#pragma unroll
+        for (int k = 0; k < l; ++k) {
+            TC a = S.alpha(l, k);
+#pragma unroll
+            for (int p = 0; p < k; ++p) a = fma(-L[l][p], L[k][p], a);
+            L[l][k] = a * dinv[k];
+        }
+        const TC all = S.alpha(l, l);
+        TC d = all;
+#pragma unroll
+        for (int p = 0; p < l; ++p) d = fma(-L[l][p], L[l][p], d);
+        TC b = S.beta(l);
+#pragma unroll
+        for (int p = 0; p < l; ++p) b = fma(-L[l][p], z[p], b);
+        const TC ratio = (all > (TC)0) ? d / all : (TC)0;
+        if (ratio > tau) {
+            const TC sq = sqrt(d);
+            L[l][l] = sq;
+            dinv[l] = (TC)1 / sq;
+            z[l] = b * dinv[l];
+        } else {
+            L[l][l] = (TC)0;
+            dinv[l] = (TC)0;
+            z[l] = (TC)0;
+        }
+        const TC rc = ratio > (TC)0 ? ratio : (TC)0;
+        dmin = rc < dmin ? rc : dmin;
+        if (l > 0) acc = fma(z[l], z[l], acc);
+        if (l > 0 && (l & 1) == 0) out[(l >> 1) - 1] = acc;
+    }
+    if constexpr (COEF) {
+        TC amax = (TC)0;
+#pragma unroll
+        for (int hp = 1; hp <= H; ++hp) {
+            if (hp > Hrun) break;  // harmonics beyond the curve's own H are padding
+            const int mp = 2 * hp + 1;
+            TC A[m];
+            TC nrm = (TC)0;
+#pragma unroll
+            for (int l = m - 1; l >= 0; --l) {
+                if (l < mp) {
+                    TC a = z[l];
+#pragma unroll
+                    for (int k = l + 1; k < m; ++k)
+                        if (k < mp) a = fma(-L[k][l], A[k], a);
+                    A[l] = a * dinv[l];
+                    nrm = fma(A[l], A[l], nrm);
+                }
+            }
+            amax = nrm > amax ? nrm : amax;
+        }
+        *anorm2 = amax;
+    }
+    if (Lkeep) {
+#pragma unroll
+        for (int l = 0; l < m; ++l)
+#pragma unroll
+            for (int k = 0; k <= l; ++k) Lkeep[l][k] = L[l][k];
+#pragma unroll
+        for (int l = 0; l < m; ++l) zkeep[l] = z[l];
+    }
+    return dmin;
+}
+
+// Error model of a result computed from an alpha and beta whose entries carry
+// absolute errors ~eps (normalised units): with A the coefficient vector,
+// dDelta = 2 A^T dbeta - A^T dalpha A, so |dDelta| <~ eps (m |A|^2 + 2 sqrt(m) |A|).
+template <typename TC>
+FC2_HD TC est_err(TC anorm2, int m, TC eps) {
+    return eps * ((TC)m * anorm2 + (TC)2 * sqrt((TC)m * anorm2));
+}
+
+// Fixed-point phase frac(a b) 2^64 from the exact double-double product a b.
+FC2_D uint64_t frac_fx(double a, double b) {
+    const double p = __dmul_rn(a, b);
+    const double e = fma(a, b, -p);  // a b = p + e exactly
+    const double fl = floor(p);
+    const double r = __dsub_rn(p, fl);  // exact
+    const uint64_t hi = (uint64_t)ldexp(r, 64 - 1) * 2ull + (uint64_t)0;  // r 2^64 (r < 1)
+    const int64_t lo = (int64_t)ldexp(e, 63) * 2;                          // e 2^64
+    return hi + (uint64_t)lo;
+}
+
+// Normalised system from exact sums acc = [Q_1..Q_2H (re, im) | P_1..P_H (re, im)]
+// laid out with stride 4 HM between the Q and P parts.
+template <int HM>
+FC2_D void exact_sys_from_sums(const double* acc, int H, const double* __restrict__ scal,
+                               Sys<double, HM>& S) {
+    const double W = scal[SC_W], chi0 = scal[SC_CHI0];
+    const double sq = (chi0 > 0.0) ? 1.0 / sqrt(W * chi0) : 0.0;
+#pragma unroll
+    for (int k = 0; k <= 2 * HM; ++k) { S.qr[k] = 0.0; S.qi[k] = 0.0; }
+#pragma unroll
+    for (int k = 0; k <= HM; ++k) { S.pr[k] = 0.0; S.pi[k] = 0.0; }
+    S.qr[0] = 1.0;
+    S.pr[0] = scal[SC_S1] * sq;
+#pragma unroll
+    for (int k = 1; k <= 2 * HM; ++k)
+        if (k <= 2 * H) { S.qr[k] = acc[2 * (k - 1)] / W; S.qi[k] = acc[2 * (k - 1) + 1] / W; }
+#pragma unroll
+    for (int k = 1; k <= HM; ++k)
+        if (k <= H) { S.pr[k] = acc[4 * HM + 2 * (k - 1)] * sq; S.pi[k] = acc[4 * HM + 2 * (k - 1) + 1] * sq; }
+}
+
+// Peak candidates ordered by (value desc, index asc).
+struct Cand { double v; int64_t j; };
+FC2_D bool better(double v1, int64_t j1, double v2, int64_t j2) {
+    return v1 > v2 || (v1 == v2 && j1 < j2);
+}
+FC2_D void warp_best(double& v, int64_t& j) {  // all lanes get the winner
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        int64_t j2 = __shfl_xor_sync(0xffffffffu, j, o);
+        if (better(v2, j2, v, j)) { v = v2; j = j2; }
+    }
+}
+
+}  // namespace fc2

@@ -1,0 +1,932 @@
+// k_batch.cu -- many independent light curves through one launch per stage.
+//
+// The "many sources" case of Sec. 4: each curve is its own Fchi2 search (its own
+// moments, H, trial grid), but all curves of a chunk share the grid length M, so
+// every stage covers the whole chunk in one launch: transforms are indexed by a
+// slot table (curve, multiple k, P or Q), curves by a curve table.  The spread
+// and FFT kernels are the single-curve ones driven by those tables; the kernels
+// here are the batch forms of the per-frequency solve, the exact fix-up and the
+// peak search.  Output Delta chi^2 is float, packed curve after curve.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "fc2_common.cuh"
+#include "fc2_internal.h"
+#include "fc2_solve.cuh"
+
+namespace fc2 {
+
+// Per-curve constants (device arrays) used by the kernels below.
+struct CurveTab {
+    const int64_t* off;     // [C+1] sample offsets (chunk-local)
+    const int* H;           // [C]
+    const double* fmin;     // [C]
+    const double* df;       // [C]
+    const double* scal;     // [C][SC_COUNT]
+    const int* slot0;       // [C] first transform slot of the curve
+    const int64_t* out_off; // [C] first output element of the curve
+    const float* sq;        // [C] 1/W
+    const float* sp;        // [C] 1/sqrt(W chi2_0)
+    const float* s1n;       // [C] sum w(x - xbar) / sqrt(W chi2_0)
+    const float* chi0f;     // [C] chi2_0
+};
+
+// ------------------------------------------------------------------ gather
+// Sample i of the chunk: its curve by binary search of the offsets; perm (if
+// given) is a chunk-level permutation that sorts every curve by time.
+__global__ void k_bgather(const double* __restrict__ t, const double* __restrict__ x,
+                          const double* __restrict__ sg, const int32_t* __restrict__ perm,
+                          int64_t ntot, const int64_t* __restrict__ off, int C,
+                          const double* __restrict__ scal, const double* __restrict__ fmin,
+                          const double* __restrict__ df, double* __restrict__ tau,
+                          double* __restrict__ wq, double* __restrict__ wp,
+                          uint64_t* __restrict__ A, uint64_t* __restrict__ B,
+                          float* __restrict__ wq32, float* __restrict__ wp32) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ntot) return;
+    int lo = 0, hi = C;  // largest c with off[c] <= i
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid; else hi = mid;
+    }
+    const int c = lo;
+    const int64_t src = perm ? perm[i] : i;
+    const double* sc = scal + (int64_t)c * SC_COUNT;
+    const double si = sg[src];
+    const double w = 1.0 / (si * si);
+    const double ta = __dsub_rn(t[src], sc[SC_T0]);
+    const double v = __dmul_rn(w, __dsub_rn(x[src], sc[SC_XBAR]));
+    tau[i] = ta;
+    wq[i] = w;
+    wp[i] = v;
+    A[i] = frac_fx(fmin[c], ta);
+    B[i] = frac_fx(df[c], ta);
+    wq32[i] = (float)w;
+    wp32[i] = (float)v;
+}
+
+// ----------------------------------------------------------- phase reduction
+// As the single-curve k_phase, per slot: the slot's curve, multiple k and
+// kind select the samples and the strengths.
+template <typename T>
+__global__ void k_bphase(const double* __restrict__ tau, const double* __restrict__ wq,
+                         const double* __restrict__ wp, const int64_t* __restrict__ off,
+                         const double* __restrict__ fmin, const double* __restrict__ df,
+                         int64_t N, int64_t M, int w, const int* __restrict__ slot_cur,
+                         const int* __restrict__ slot_k, const int* __restrict__ slot_kind,
+                         const int64_t* __restrict__ slot_soff, int32_t* __restrict__ key,
+                         T* __restrict__ dlt, cpx<T>* __restrict__ cs) {
+    const int g = blockIdx.y;
+    const int c = slot_cur[g];
+    const int64_t a = off[c], n = off[c + 1] - a;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int k = slot_k[g], kind = slot_kind[g];
+    const double ts = tau[a + s];
+    const double cc = __dmul_rn((double)k, df[c]);
+    const double p = __dmul_rn(cc, ts);
+    const double u = __dsub_rn(p, floor(p));
+    const double X = __dmul_rn((double)M, u);
+    const double Xs = __dsub_rn(X, 0.5 * (double)w);
+    const double fl = floor(Xs);
+    const double de = __dsub_rn(Xs, fl);
+    const double q1 = __dmul_rn(__dmul_rn((double)k, fmin[c]), ts);
+    const double q2 = __dmul_rn((double)(N / 2), u);
+    const double th = __dadd_rn(__dsub_rn(q1, floor(q1)), __dsub_rn(q2, floor(q2)));
+    double sn, cn;
+    sincospi(2.0 * th, &sn, &cn);
+    const double amp = kind == 0 ? wq[a + s] : wp[a + s];
+    const int64_t o = slot_soff[g] + s;
+    key[o] = (int32_t)fl + 1;
+    dlt[o] = (T)de;
+    cs[o] = mk<T>((T)(amp * cn), (T)(amp * sn));
+}
+
+// --------------------------------------------------------------- assemble
+// One thread per (trial frequency, curve) for the curves of one H; Delta
+// chi^2 written as float.  Bins whose estimated error is too large go to
+// `list` as (curve << 32 | j).
+template <typename TS, int H>
+__global__ void __launch_bounds__(128) k_bassemble(const cpx<TS>* __restrict__ spec,
+                                                   const TS* __restrict__ dec, int64_t N,
+                                                   const int* __restrict__ curves, CurveTab ct,
+                                                   double tau, double eps, double err_fix,
+                                                   float* __restrict__ out,
+                                                   int64_t* __restrict__ list,
+                                                   int32_t* __restrict__ list_count,
+                                                   int64_t cap) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const int c = curves[blockIdx.y];
+    const int g0 = ct.slot0[c];
+    const TS d = dec[j];
+    const TS dq = d * (TS)ct.sq[c], dp = d * (TS)ct.sp[c];
+    Sys<TS, H> S;
+    S.qr[0] = (TS)1;
+    S.qi[0] = (TS)0;
+    S.pr[0] = (TS)ct.s1n[c];
+    S.pi[0] = (TS)0;
+#pragma unroll
+    for (int k = 1; k <= 2 * H; ++k) {
+        const cpx<TS> v = spec[(int64_t)(g0 + k - 1) * N + j];
+        S.qr[k] = v.x * dq;
+        S.qi[k] = v.y * dq;
+    }
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        const cpx<TS> v = spec[(int64_t)(g0 + 2 * H + k - 1) * N + j];
+        S.pr[k] = v.x * dp;
+        S.pi[k] = v.y * dp;
+    }
+    TS o[H], an2 = (TS)0;
+    chol_solve<TS, H, true>(S, (TS)tau, o, &an2);
+    if (!(est_err<TS>(an2, 2 * H + 1, (TS)eps) <= (TS)err_fix)) {
+        const int32_t pos = atomicAdd(list_count, 1);
+        if (pos < cap) list[pos] = ((int64_t)c << 32) | j;
+    }
+    float* oc = out + ct.out_off[c];
+    const float c0 = ct.chi0f[c];
+#pragma unroll
+    for (int h = 0; h < H; ++h) oc[(int64_t)h * N + j] = (float)o[h] * c0;
+}
+
+// Double re-solve of listed (curve, bin) entries of the float path; entries
+// still too sensitive go on to the exact list.
+template <int HM>
+__global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__ spec,
+                                                  const float* __restrict__ dec, int64_t N,
+                                                  CurveTab ct, double tau, double eps,
+                                                  double err_fix, float* __restrict__ out,
+                                                  const int64_t* __restrict__ rlist,
+                                                  const int32_t* __restrict__ rcount,
+                                                  int64_t rcap, int64_t* __restrict__ flist,
+                                                  int32_t* __restrict__ fcount, int64_t fcap) {
+    int64_t cnt = *rcount;
+    if (cnt > rcap) cnt = rcap;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < cnt;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(rlist[b] >> 32);
+        const int64_t j = rlist[b] & 0xffffffffll;
+        const int H = ct.H[c];
+        const int g0 = ct.slot0[c];
+        const double* sc = ct.scal + (int64_t)c * SC_COUNT;
+        const double W = sc[SC_W], chi0 = sc[SC_CHI0];
+        const double sp = (chi0 > 0.0) ? 1.0 / sqrt(W * chi0) : 0.0;
+        const double d = (double)dec[j];
+        Sys<double, HM> S;
+#pragma unroll
+        for (int k = 0; k <= 2 * HM; ++k) { S.qr[k] = 0.0; S.qi[k] = 0.0; }
+#pragma unroll
+        for (int k = 0; k <= HM; ++k) { S.pr[k] = 0.0; S.pi[k] = 0.0; }
+        S.qr[0] = 1.0;
+        S.pr[0] = sc[SC_S1] * sp;
+        for (int k = 1; k <= 2 * H; ++k) {
+            const cpx<float> v = spec[(int64_t)(g0 + k - 1) * N + j];
+            S.qr[k] = (double)v.x * d / W;
+            S.qi[k] = (double)v.y * d / W;
+        }
+        for (int k = 1; k <= H; ++k) {
+            const cpx<float> v = spec[(int64_t)(g0 + 2 * H + k - 1) * N + j];
+            S.pr[k] = (double)v.x * d * sp;
+            S.pi[k] = (double)v.y * d * sp;
+        }
+        double o[HM], an2 = 0.0;
+        chol_solve<double, HM, true>(S, tau, o, &an2, nullptr, nullptr, H);
+        if (!(est_err<double>(an2, 2 * H + 1, eps) <= err_fix)) {
+            const int32_t pos = atomicAdd(fcount, 1);
+            if (pos < fcap) flist[pos] = rlist[b];
+        }
+        float* oc = out + ct.out_off[c];
+        for (int h = 0; h < H; ++h) oc[(int64_t)h * N + j] = (float)(o[h] * chi0);
+    }
+}
+
+// ------------------------------------------------------ exact, one CTA per entry
+// Entries (curve << 32 | j); the CTA sums its curve's samples (tier 1: float
+// sine/cosine of exact integer phases with compensated float sums; tier 2: all
+// double), reduces in a fixed order, and warp 0 lane 0 solves.
+// MODE 0: write Delta chi^2 (float) and escalate entries whose tier-1 error
+// estimate is still too large.  MODE 1: coefficient records.
+constexpr int BX_NT = 256;
+
+template <int HM, int TIER, int MODE>
+__global__ void __launch_bounds__(BX_NT) k_bexact(
+    const uint64_t* __restrict__ Aph, const uint64_t* __restrict__ Bph,
+    const float* __restrict__ wq32, const float* __restrict__ wp32,
+    const double* __restrict__ wq, const double* __restrict__ wp, CurveTab ct, int64_t N,
+    const int64_t* __restrict__ list, const int32_t* __restrict__ count, int64_t cap,
+    double tau_drop, double err_fix, float* __restrict__ out, int64_t* __restrict__ next,
+    int32_t* __restrict__ next_count, int64_t next_cap, int K, fc2_best* __restrict__ recs) {
+    constexpr int NV = 6 * HM;
+    __shared__ double red[BX_NT / 32][NV];
+    __shared__ double tot[NV];
+    int64_t cnt = *count;
+    if (cnt > cap) cnt = cap;
+    const int lane = threadIdx.x & 31, wpi = threadIdx.x >> 5;
+    for (int64_t e = blockIdx.x; e < cnt; e += gridDim.x) {
+        const int64_t ent = list[e];
+        const int c = (int)(ent >> 32);
+        const int64_t j = ent & 0xffffffffll;
+        const int H = ct.H[c];
+        if (MODE == 1 && j == 0xffffffffll) {  // empty peak slot
+            if (threadIdx.x == 0) {
+                fc2_best b;
+                b.j = -1; b.f = 0; b.dchi2 = 0; b.H = H; b.flags = 0;
+                for (int l = 0; l < 2 * FC2_MAX_H + 1; ++l) b.A[l] = 0.0;
+                recs[e] = b;
+            }
+            continue;
+        }
+        const int64_t a0 = ct.off[c], a1 = ct.off[c + 1];
+        const uint64_t ju = (uint64_t)j;
+        double acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+        if constexpr (TIER == 1) {
+            CompSum<float> fa[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) fa[v].init();
+            for (int64_t i = a0 + threadIdx.x; i < a1; i += BX_NT) {
+                const uint32_t u = (uint32_t)((Aph[i] + ju * Bph[i]) >> 32);
+                const float a = wq32[i], bb = wp32[i];
+#pragma unroll
+                for (int k = 1; k <= 2 * HM; ++k) {
+                    if (k <= 2 * H) {
+                        const int32_t ph = (int32_t)(u * (uint32_t)k);
+                        float sn, cn;
+                        sincospif((float)ph * 4.656612873077393e-10f, &sn, &cn);
+                        fa[2 * (k - 1)].add(a * cn);
+                        fa[2 * (k - 1) + 1].add(a * sn);
+                        if (k <= H) {
+                            fa[4 * HM + 2 * (k - 1)].add(bb * cn);
+                            fa[4 * HM + 2 * (k - 1) + 1].add(bb * sn);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc[v] = (double)fa[v].s + (double)fa[v].c;
+        } else {
+            for (int64_t i = a0 + threadIdx.x; i < a1; i += BX_NT) {
+                const int64_t ph = (int64_t)(Aph[i] + ju * Bph[i]);
+                double s1, c1;
+                sincospi(ldexp((double)ph, -63), &s1, &c1);
+                double cr = c1, ci = s1;
+                const double a = wq[i], bb = wp[i];
+#pragma unroll
+                for (int k = 0; k < 2 * HM; ++k) {
+                    if (k < 2 * H) {
+                        acc[2 * k] = fma(a, cr, acc[2 * k]);
+                        acc[2 * k + 1] = fma(a, ci, acc[2 * k + 1]);
+                        if (k < H) {
+                            acc[4 * HM + 2 * k] = fma(bb, cr, acc[4 * HM + 2 * k]);
+                            acc[4 * HM + 2 * k + 1] = fma(bb, ci, acc[4 * HM + 2 * k + 1]);
+                        }
+                        const double nr = cr * c1 - ci * s1, ni = cr * s1 + ci * c1;
+                        cr = nr;
+                        ci = ni;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double y = acc[v];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+            if (lane == 0) red[wpi][v] = y;
+        }
+        __syncthreads();
+        if (threadIdx.x < NV) {
+            double y = 0.0;
+#pragma unroll
+            for (int q = 0; q < BX_NT / 32; ++q) y += red[q][threadIdx.x];
+            tot[threadIdx.x] = y;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double* sc = ct.scal + (int64_t)c * SC_COUNT;
+            Sys<double, HM> S;
+            exact_sys_from_sums<HM>(tot, H, sc, S);
+            const double chi0 = sc[SC_CHI0];
+            if constexpr (MODE == 0) {
+                double o[HM], an2 = 0.0;
+                chol_solve<double, HM, true>(S, tau_drop, o, &an2, nullptr, nullptr, H);
+                const double eps_t1 = 2e-7 * sc[SC_RW];
+                if (next && !(est_err<double>(an2, 2 * H + 1, eps_t1) <= err_fix)) {
+                    const int32_t pos = atomicAdd(next_count, 1);
+                    if (pos < next_cap) next[pos] = ent;
+                }
+                float* oc = out + ct.out_off[c];
+                for (int h = 0; h < H; ++h) oc[(int64_t)h * N + j] = (float)(o[h] * chi0);
+            } else {
+                double o[HM], an2;
+                double Lk[2 * HM + 1][2 * HM + 1];
+                double zk[2 * HM + 1];
+                chol_solve<double, HM, false>(S, tau_drop, o, &an2, Lk, zk);
+                const int m = 2 * H + 1;
+                double A[2 * HM + 1];
+                for (int l = m - 1; l >= 0; --l) {
+                    double s = zk[l];
+                    for (int k = l + 1; k < m; ++k) s -= Lk[k][l] * A[k];
+                    A[l] = (Lk[l][l] > 0.0) ? s / Lk[l][l] : 0.0;
+                }
+                const double W = sc[SC_W];
+                const double unit = (W > 0.0) ? sqrt(chi0 / W) : 0.0;
+                const double f = ct.fmin[c] + (double)j * ct.df[c];
+                fc2_best b;
+                b.j = j; b.f = f; b.dchi2 = o[H - 1] * chi0; b.H = H; b.flags = 0;
+                for (int l = 0; l < 2 * FC2_MAX_H + 1; ++l) b.A[l] = 0.0;
+                b.A[0] = A[0] * unit + sc[SC_XBAR];
+                const double fT0 = f * sc[SC_T0];
+                for (int h = 1; h <= H; ++h) {
+                    const double ph = (double)h * (fT0 - floor(fT0));
+                    double sn, cn;
+                    sincospi(2.0 * (ph - floor(ph)), &sn, &cn);
+                    const double as = A[2 * h - 1] * unit, ac = A[2 * h] * unit;
+                    b.A[2 * h - 1] = as * cn + ac * sn;
+                    b.A[2 * h] = ac * cn - as * sn;
+                }
+                recs[e] = b;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------- peaks
+// Per curve: top-K local maxima of its Delta chi^2_H row (value > left,
+// >= right; edges one-sided), ordered by (value desc, j asc).  Stage 1 per
+// block of BP_B bins of one curve, stage 2 one block per curve.  Writes the
+// peak list as (curve << 32 | j) entries, empty slots as (curve << 32 | 0xffffffff).
+constexpr int BP_NT = 256;
+constexpr int BP_PER = 16;
+constexpr int BP_B = BP_NT * BP_PER;
+constexpr int BP_NW = BP_NT / 32;
+constexpr int BP_KMAX = 64;
+
+__global__ void __launch_bounds__(BP_NT) k_bpeaks1(const float* __restrict__ out, int64_t N,
+                                                   CurveTab ct, int K, int nblk,
+                                                   Cand* __restrict__ tops) {
+    __shared__ Cand wtop[BP_NW][BP_KMAX];
+    const int c = blockIdx.y;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float* row = out + ct.out_off[c] + (int64_t)(ct.H[c] - 1) * N;
+    const int64_t base = (int64_t)blockIdx.x * BP_B;
+    double cv[BP_PER];
+    int64_t cj[BP_PER];
+#pragma unroll
+    for (int q = 0; q < BP_PER; ++q) {
+        const int64_t jj = base + lane + (int64_t)(w * BP_PER + q) * 32;
+        cv[q] = -INFINITY;
+        cj[q] = INT64_MAX;
+        if (jj < N) {
+            const float x = row[jj];
+            const bool left = (jj == 0) || (x > row[jj - 1]);
+            const bool right = (jj == N - 1) || (x >= row[jj + 1]);
+            if (left && right) { cv[q] = x; cj[q] = jj; }
+        }
+    }
+    for (int r = 0; r < K; ++r) {
+        double v = -INFINITY;
+        int64_t j = INT64_MAX;
+#pragma unroll
+        for (int q = 0; q < BP_PER; ++q)
+            if (better(cv[q], cj[q], v, j)) { v = cv[q]; j = cj[q]; }
+        warp_best(v, j);
+#pragma unroll
+        for (int q = 0; q < BP_PER; ++q)
+            if (cj[q] == j) { cv[q] = -INFINITY; cj[q] = INT64_MAX; }
+        if (lane == 0) wtop[w][r] = Cand{v, j};
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int tot = BP_NW * K;
+        for (int r = 0; r < K; ++r) {
+            double v = -INFINITY;
+            int64_t j = INT64_MAX;
+            int pos = -1;
+            for (int e = lane; e < tot; e += 32) {
+                const Cand cd = wtop[e / K][e % K];
+                if (better(cd.v, cd.j, v, j)) { v = cd.v; j = cd.j; pos = e; }
+            }
+            double bv = v;
+            int64_t bj = j;
+            warp_best(bv, bj);
+            if (pos >= 0 && j == bj && bj != INT64_MAX) wtop[pos / K][pos % K] = Cand{-INFINITY, INT64_MAX};
+            __syncwarp();
+            if (lane == 0) tops[((int64_t)c * nblk + blockIdx.x) * K + r] = Cand{bv, bj};
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_bpeaks2(const Cand* __restrict__ tops, int nblk, int K,
+                                                 int64_t* __restrict__ peak_ent) {
+    __shared__ Cand ws[8];
+    const int c = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const Cand* tc = tops + (int64_t)c * nblk * K;
+    const int64_t total = (int64_t)nblk * K;
+    double pv = INFINITY;
+    int64_t pj = -1;
+    for (int r = 0; r < K; ++r) {
+        double v = -INFINITY;
+        int64_t j = INT64_MAX;
+        for (int64_t b = threadIdx.x; b < total; b += blockDim.x) {
+            const Cand cd = tc[b];
+            if (cd.j != INT64_MAX && better(pv, pj, cd.v, cd.j) && better(cd.v, cd.j, v, j)) {
+                v = cd.v;
+                j = cd.j;
+            }
+        }
+        warp_best(v, j);
+        if (lane == 0) ws[w] = Cand{v, j};
+        __syncthreads();
+        if (w == 0) {
+            v = lane < 8 ? ws[lane].v : -INFINITY;
+            j = lane < 8 ? ws[lane].j : INT64_MAX;
+            warp_best(v, j);
+            if (lane == 0) {
+                ws[0] = Cand{v, j};
+                peak_ent[(int64_t)c * K + r] =
+                    ((int64_t)c << 32) | (j == INT64_MAX ? 0xffffffffll : j);
+            }
+        }
+        __syncthreads();
+        pv = ws[0].v;
+        pj = ws[0].j;
+        __syncthreads();
+        if (pj == INT64_MAX) pv = -INFINITY;
+    }
+}
+
+// ============================================================ host driver
+namespace {
+
+template <typename P>
+cudaError_t need(P** ptr, size_t* cap, size_t n, cudaStream_t s) {
+    if (n <= *cap && *ptr) return cudaSuccess;
+    if (*ptr) cudaFreeAsync(*ptr, s);
+    *ptr = nullptr;
+    *cap = 0;
+    n = std::max<size_t>(n, 64);
+    cudaError_t e = cudaMallocAsync((void**)ptr, n * sizeof(P), s);
+    if (e == cudaSuccess) *cap = n;
+    return e;
+}
+
+template <typename P>
+void release(P*& ptr, cudaStream_t s) {
+    if (ptr) cudaFreeAsync((void*)ptr, s);
+    ptr = nullptr;
+}
+
+__global__ void k_iota_plus(int32_t* v, int64_t n, int64_t base) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (int32_t)(base + i);
+}
+__global__ void k_add_base(int32_t* v, int64_t n, int64_t base) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] += (int32_t)base;
+}
+
+fc2_status map_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return FC2_OK;
+    if (e == cudaErrorMemoryAllocation) return FC2_ERR_OOM;
+    return FC2_ERR_CUDA;
+}
+
+constexpr int BHM = 8;  // harmonic capacity of the batched kernels
+
+}  // namespace
+
+struct Batch {
+    cudaStream_t s = nullptr;
+    bool own_stream = false;
+    // chunk plan: drives the shared spread / FFT launchers
+    fc2_plan_s cp;
+    // device arrays with capacities
+    double *t = nullptr, *x = nullptr, *sg = nullptr;
+    size_t ct = 0, cx = 0, csg = 0;
+    int32_t* perm = nullptr; size_t cperm = 0;
+    double *tau = nullptr, *wq = nullptr, *wp = nullptr; size_t ctau = 0, cwq = 0, cwp = 0;
+    uint64_t *A = nullptr, *B = nullptr; size_t cA = 0, cB = 0;
+    float *wq32 = nullptr, *wp32 = nullptr; size_t cwq32 = 0, cwp32 = 0;
+    int64_t* off = nullptr; size_t coff = 0;
+    int* H = nullptr; size_t cH = 0;
+    int* slot0 = nullptr; size_t cslot0 = 0;
+    double *fmin = nullptr, *df = nullptr, *scal = nullptr; size_t cfmin = 0, cdf = 0, cscal = 0;
+    int64_t* out_off = nullptr; size_t coo = 0;
+    float *sq = nullptr, *sp = nullptr, *s1n = nullptr, *chi0f = nullptr;
+    size_t csq = 0, csp = 0, cs1n = 0, cchi0f = 0;
+    int *slot_cur = nullptr, *slot_k = nullptr, *slot_kind = nullptr;
+    size_t cscur = 0, csk = 0, cskind = 0;
+    int64_t *slot_soff = nullptr, *slot_n = nullptr, *L = nullptr;
+    size_t cssoff = 0, csn = 0, cL = 0;
+    int32_t* key = nullptr; size_t ckey = 0;
+    char *dlt = nullptr, *cs = nullptr; size_t cdlt = 0, ccs = 0;
+    char *grid0 = nullptr, *grid1 = nullptr, *spec = nullptr; size_t cg0 = 0, cg1 = 0, cspec = 0;
+    float* out = nullptr; size_t cout = 0;
+    int64_t *list = nullptr, *list2 = nullptr, *list3 = nullptr; size_t cl1 = 0, cl2 = 0, cl3 = 0;
+    int32_t* counts = nullptr; size_t ccnt = 0;
+    int* curves = nullptr; size_t ccurves = 0;
+    Cand* tops = nullptr; size_t ctops = 0;
+    int64_t* pent = nullptr; size_t cpent = 0;
+    fc2_best* recs = nullptr; size_t crecs = 0;
+    char* red = nullptr; size_t cred = 0;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t launches = 0;
+    int64_t stats[3] = {0, 0, 0};
+
+    void free_all() {
+        release(t, s); release(x, s); release(sg, s); release(perm, s); release(tau, s);
+        release(wq, s); release(wp, s); release(A, s); release(B, s); release(wq32, s);
+        release(wp32, s); release(off, s); release(H, s); release(slot0, s); release(fmin, s);
+        release(df, s); release(scal, s); release(out_off, s); release(sq, s); release(sp, s);
+        release(s1n, s); release(chi0f, s); release(slot_cur, s); release(slot_k, s);
+        release(slot_kind, s); release(slot_soff, s); release(slot_n, s); release(L, s);
+        release(key, s); release(dlt, s); release(cs, s); release(grid0, s); release(grid1, s);
+        release(spec, s); release(out, s); release(list, s); release(list2, s); release(list3, s);
+        release(counts, s); release(curves, s); release(tops, s); release(pent, s);
+        release(recs, s); release(red, s);
+        release(cp.d_twlo, s); release(cp.d_twhi, s); release(cp.d_twst, s); release(cp.d_dec, s);
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+    }
+};
+
+__global__ void k_set_count(int32_t* c, int32_t v) { *c = v; }
+
+// Launches of one chunk after its tables are in place: everything from the
+// gather to the coefficient records, no host synchronisation in between (so
+// the sequence can be captured as a CUDA graph).
+template <typename T>
+static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, int S,
+                                  const std::vector<std::vector<int>>& hgroups,
+                                  const std::vector<int>& hgroup_off, int K, float* out,
+                                  int64_t nrec, double tau_drop) {
+    cudaStream_t s = b.s;
+    fc2_plan_s& p = b.cp;
+    const int64_t N = p.N;
+    int64_t nl = 0;
+    CurveTab ct{b.off, b.H, b.fmin, b.df, b.scal, b.slot0, b.out_off, b.sq, b.sp, b.s1n, b.chi0f};
+    k_bgather<<<(unsigned)((ntot + 255) / 256), 256, 0, s>>>(
+        b.t, b.x, b.sg, b.perm, ntot, b.off, nc, b.scal, b.fmin, b.df, b.tau, b.wq, b.wp, b.A, b.B,
+        b.wq32, b.wp32);
+    ++nl;
+    dim3 gph((unsigned)((nmax + 255) / 256), (unsigned)S);
+    k_bphase<T><<<gph, 256, 0, s>>>(b.tau, b.wq, b.wp, b.off, b.fmin, b.df, N, p.M, p.w,
+                                    b.slot_cur, b.slot_k, b.slot_kind, b.slot_soff, b.key,
+                                    (T*)b.dlt, (cpx<T>*)b.cs);
+    ++nl;
+    cudaError_t e = sort_wrapping_keys(&p, s);
+    if (e != cudaSuccess) return e;
+    e = launch_spread(&p, s);
+    if (e != cudaSuccess) return e;
+    e = launch_fft(&p, s);
+    if (e != cudaSuccess) return e;
+    nl += 1 + (int64_t)p.passes.size();
+    cudaMemsetAsync(b.counts, 0, 8 * sizeof(int32_t), s);
+    k_set_count<<<1, 1, 0, s>>>(b.counts + 4, (int32_t)nrec);  // record count for the peaks
+    const bool f32 = sizeof(T) == 4;
+    const double eps_spec = f32 ? 1e-7 : 1e-13;
+    const double err_fix = 2e-5;
+    int64_t* first_list = f32 ? b.list : b.list2;  // float: re-solve list; double: exact list
+    int32_t* first_cnt = f32 ? b.counts + 0 : b.counts + 1;
+    const int64_t first_cap = f32 ? (int64_t)b.cl1 : (int64_t)b.cl2;
+    for (size_t gi = 0; gi < hgroups.size(); ++gi) {
+        const int Hh = hgroups[gi].empty() ? 0 : (int)gi + 1;
+        if (!Hh) continue;
+        dim3 ga((unsigned)((N + 127) / 128), (unsigned)hgroups[gi].size());
+        const int* cl = b.curves + hgroup_off[gi];
+        const double eps = f32 ? eps_spec + 3e-7 : eps_spec;
+#define FC2_BASM(HH)                                                                          \
+    case HH:                                                                                  \
+        k_bassemble<T, HH><<<ga, 128, 0, s>>>((const cpx<T>*)p.d_spec, (const T*)p.d_dec, N,  \
+                                              cl, ct, tau_drop, eps, err_fix, out, first_list, \
+                                              first_cnt, first_cap);                          \
+        break;
+        switch (Hh) {
+            FC2_BASM(1) FC2_BASM(2) FC2_BASM(3) FC2_BASM(4) FC2_BASM(5) FC2_BASM(6) FC2_BASM(7)
+            FC2_BASM(8)
+            default: return cudaErrorInvalidValue;
+        }
+#undef FC2_BASM
+        ++nl;
+    }
+    if (f32) {
+        k_bresolve<BHM><<<4 * 152, 128, 0, s>>>((const cpx<float>*)p.d_spec, (const float*)p.d_dec,
+                                                N, ct, tau_drop, eps_spec, err_fix, out, b.list,
+                                                b.counts + 0, (int64_t)b.cl1, b.list2, b.counts + 1,
+                                                (int64_t)b.cl2);
+        ++nl;
+    }
+    // exact fix-up: tier 1 over list2, escalation to list3, tier 2 over list3
+    k_bexact<BHM, 1, 0><<<4 * 152, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, ct, N,
+                                                   b.list2, b.counts + 1, (int64_t)b.cl2, 1e-13,
+                                                   err_fix, out, b.list3, b.counts + 2,
+                                                   (int64_t)b.cl3, 0, nullptr);
+    k_bexact<BHM, 2, 0><<<4 * 152, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, ct, N,
+                                                   b.list3, b.counts + 2, (int64_t)b.cl3, 1e-13,
+                                                   err_fix, out, nullptr, nullptr, 0, 0, nullptr);
+    nl += 2;
+    if (K > 0) {
+        const int nblk = (int)((N + BP_B - 1) / BP_B);
+        k_bpeaks1<<<dim3((unsigned)nblk, (unsigned)nc), BP_NT, 0, s>>>(out, N, ct, K, nblk, b.tops);
+        k_bpeaks2<<<(unsigned)nc, 256, 0, s>>>(b.tops, nblk, K, b.pent);
+        k_bexact<BHM, 1, 1><<<4 * 152, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, ct, N,
+                                                       b.pent, b.counts + 4, nrec, tau_drop,
+                                                       err_fix, out, nullptr, nullptr, 0, K, b.recs);
+        nl += 3;
+    }
+    b.launches += nl;
+    return cudaGetLastError();
+}
+
+fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, const double* x,
+                           const double* sigma, const int* Hc, const double* fminc,
+                           const double* dfc, const int64_t* Nc, int oversample,
+                           const fc2_options& opt, float* dchi2, fc2_best* peaks,
+                           int64_t* launches_out, int64_t* stats_out) {
+    // ---- validation (host)
+    if (C < 1 || !offsets || !t || !x || !sigma || !Hc || !fminc || !dfc || !Nc)
+        return FC2_ERR_INVALID_ARG;
+    if (oversample < 2 || oversample > 64) return FC2_ERR_INVALID_ARG;
+    if (opt.prec != FC2_PREC_FP64 && opt.prec != FC2_PREC_MIXED) return FC2_ERR_INVALID_ARG;
+    if (opt.top_k < 0 || opt.top_k > 64) return FC2_ERR_INVALID_ARG;
+    for (int64_t c = 0; c < C; ++c) {
+        if (offsets[c + 1] - offsets[c] < 1 || offsets[c] < 0) return FC2_ERR_INVALID_ARG;
+        if (offsets[c + 1] - offsets[c] > (1ll << 31) - 1) return FC2_ERR_INVALID_ARG;
+        if (Hc[c] < 1 || Hc[c] > FC2_MAX_H || Nc[c] < 2 || Nc[c] > (1ll << 31) - 1)
+            return FC2_ERR_INVALID_ARG;
+        if (!(std::isfinite(fminc[c]) && fminc[c] >= 0.0) || !(std::isfinite(dfc[c]) && dfc[c] > 0.0))
+            return FC2_ERR_INVALID_ARG;
+        if (Hc[c] > BHM) return FC2_ERR_UNSUPPORTED;
+        if (fc2_grid_size(Nc[c], oversample) == 0) return FC2_ERR_INVALID_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return FC2_ERR_CUDA;
+    if (opt.device < 0 || opt.device >= ndev) return FC2_ERR_INVALID_ARG;
+    if (cudaSetDevice(opt.device) != cudaSuccess) return FC2_ERR_CUDA;
+
+    const bool fp64 = opt.prec == FC2_PREC_FP64;
+    const size_t tsz = fp64 ? 8 : 4, csz = 2 * tsz;
+    const int K = opt.top_k ? opt.top_k : 8;
+    Batch b;
+    if (opt.cuda_stream) b.s = (cudaStream_t)opt.cuda_stream;
+    else {
+        if (cudaStreamCreateWithFlags(&b.s, cudaStreamNonBlocking) != cudaSuccess) return FC2_ERR_CUDA;
+        b.own_stream = true;
+    }
+    cudaStream_t s = b.s;
+    cudaPointerAttributes at;
+    bool out_dev = false;
+    if (dchi2 && cudaPointerGetAttributes(&at, dchi2) == cudaSuccess && at.type == cudaMemoryTypeDevice)
+        out_dev = true;
+    cudaGetLastError();
+    size_t freeb = 0, totalb = 0;
+    cudaMemGetInfo(&freeb, &totalb);
+    const size_t budget = std::min<size_t>(freeb / 2, (size_t)48 << 30);
+
+    fc2_status st = FC2_OK;
+    int64_t out_global = 0;
+    int64_t curM = -1, curN = -1;
+    int64_t c0 = 0;
+    while (c0 < C && st == FC2_OK) {
+        // ---- chunk: consecutive curves with the same N, within the memory budget
+        const int64_t N = Nc[c0];
+        const int64_t M = fc2_grid_size(N, oversample);
+        int64_t c1 = c0, S = 0, ntot = 0, nmax = 0, slot_samples = 0;
+        while (c1 < C && Nc[c1] == N && c1 - c0 < 2048) {
+            const int64_t n = offsets[c1 + 1] - offsets[c1];
+            const int64_t sl = 3 * Hc[c1];
+            const size_t bytes = (size_t)(S + sl) * (size_t)M * csz * 2 + (size_t)(S + sl) * N * csz +
+                                 (size_t)(slot_samples + sl * n) * (4 + tsz + csz) +
+                                 (size_t)(ntot + n) * 80;
+            if (c1 > c0 && bytes > budget) break;
+            S += sl;
+            ntot += n;
+            nmax = std::max(nmax, n);
+            slot_samples += sl * n;
+            ++c1;
+        }
+        const int nc = (int)(c1 - c0);
+        fc2_plan_s& p = b.cp;
+        // ---- shared tables for this (N, M)
+        if (M != curM || N != curN) {
+            p.M = M;
+            p.logM = 0;
+            while ((1ll << p.logM) < M) ++p.logM;
+            p.N = N;
+            p.fp64 = fp64;
+            p.oversample = oversample;
+            p.w = opt.kernel_width ? opt.kernel_width : default_width(fp64, oversample);
+            p.beta = 0.97 * M_PI * (1.0 - 0.5 / ((double)M / (double)N)) * (double)p.w;
+            p.stream = s;
+            plan_fft_passes(&p);
+            release(p.d_twlo, s); release(p.d_twhi, s); release(p.d_twst, s); release(p.d_dec, s);
+            const int sh = (p.logM + 1) / 2;
+            cudaError_t e = cudaMallocAsync(&p.d_twlo, (size_t)(1ll << sh) * csz, s);
+            if (e == cudaSuccess) e = cudaMallocAsync(&p.d_twhi, (size_t)(M >> sh) * csz, s);
+            if (e == cudaSuccess) e = cudaMallocAsync(&p.d_twst, (size_t)(8 * 4096 + 256) * csz, s);
+            if (e == cudaSuccess) e = cudaMallocAsync(&p.d_dec, (size_t)N * tsz, s);
+            if (e == cudaSuccess) e = need(&b.red, &b.cred, 8192, s);
+            p.d_red = b.red;
+            if (e == cudaSuccess) e = init_twiddles(&p, s);
+            if (e == cudaSuccess) e = init_deconv(&p, s);
+            if (e != cudaSuccess) { st = map_cuda(e); break; }
+            curM = M;
+            curN = N;
+        }
+        // ---- buffers
+        const int64_t base = offsets[c0];
+        cudaError_t e = cudaSuccess;
+        auto ok = [&](cudaError_t r) { if (e == cudaSuccess) e = r; return e == cudaSuccess; };
+        if (opt.inputs_on_device) {
+            b.t = (double*)(t + base); b.x = (double*)(x + base); b.sg = (double*)(sigma + base);
+        } else {
+            ok(need(&b.t, &b.ct, ntot, s)) && ok(need(&b.x, &b.cx, ntot, s)) &&
+                ok(need(&b.sg, &b.csg, ntot, s)) &&
+                ok(cudaMemcpyAsync(b.t, t + base, ntot * 8, cudaMemcpyHostToDevice, s)) &&
+                ok(cudaMemcpyAsync(b.x, x + base, ntot * 8, cudaMemcpyHostToDevice, s)) &&
+                ok(cudaMemcpyAsync(b.sg, sigma + base, ntot * 8, cudaMemcpyHostToDevice, s));
+        }
+        const int64_t nrec = (int64_t)nc * K;
+        int64_t out_chunk = 0;
+        for (int64_t c = c0; c < c1; ++c) out_chunk += (int64_t)Hc[c] * N;
+        const size_t sort_b = sort_scratch_bytes(nmax);
+        ok(need(&b.perm, &b.cperm, ntot, s)) && ok(need(&b.tau, &b.ctau, ntot, s)) &&
+            ok(need(&b.wq, &b.cwq, ntot, s)) && ok(need(&b.wp, &b.cwp, ntot, s)) &&
+            ok(need(&b.A, &b.cA, ntot, s)) && ok(need(&b.B, &b.cB, ntot, s)) &&
+            ok(need(&b.wq32, &b.cwq32, ntot, s)) && ok(need(&b.wp32, &b.cwp32, ntot, s)) &&
+            ok(need(&b.off, &b.coff, nc + 1, s)) && ok(need(&b.H, &b.cH, nc, s)) &&
+            ok(need(&b.slot0, &b.cslot0, nc, s)) && ok(need(&b.fmin, &b.cfmin, nc, s)) &&
+            ok(need(&b.df, &b.cdf, nc, s)) && ok(need(&b.scal, &b.cscal, (size_t)nc * SC_COUNT, s)) &&
+            ok(need(&b.out_off, &b.coo, nc, s)) && ok(need(&b.sq, &b.csq, nc, s)) &&
+            ok(need(&b.sp, &b.csp, nc, s)) && ok(need(&b.s1n, &b.cs1n, nc, s)) &&
+            ok(need(&b.chi0f, &b.cchi0f, nc, s)) && ok(need(&b.slot_cur, &b.cscur, S, s)) &&
+            ok(need(&b.slot_k, &b.csk, S, s)) && ok(need(&b.slot_kind, &b.cskind, S, s)) &&
+            ok(need(&b.slot_soff, &b.cssoff, S, s)) && ok(need(&b.slot_n, &b.csn, S, s)) &&
+            ok(need(&b.L, &b.cL, S, s)) && ok(need(&b.key, &b.ckey, slot_samples, s)) &&
+            ok(need(&b.dlt, &b.cdlt, slot_samples * tsz, s)) &&
+            ok(need(&b.cs, &b.ccs, slot_samples * csz, s)) &&
+            ok(need(&b.grid0, &b.cg0, (size_t)S * M * csz, s)) &&
+            ok(need(&b.grid1, &b.cg1, std::max((size_t)S * M * csz, sort_b + 4096), s)) &&
+            ok(need(&b.spec, &b.cspec, (size_t)S * N * csz, s)) &&
+            ok(need(&b.list, &b.cl1, (size_t)std::min<int64_t>(out_chunk, 1 << 24), s)) &&
+            ok(need(&b.list2, &b.cl2, (size_t)std::min<int64_t>(out_chunk, 1 << 22), s)) &&
+            ok(need(&b.list3, &b.cl3, (size_t)std::min<int64_t>(out_chunk, 1 << 20), s)) &&
+            ok(need(&b.counts, &b.ccnt, 16, s)) && ok(need(&b.curves, &b.ccurves, nc, s)) &&
+            ok(need(&b.tops, &b.ctops, (size_t)nc * ((N + BP_B - 1) / BP_B) * std::max(K, 1), s)) &&
+            ok(need(&b.pent, &b.cpent, (size_t)std::max<int64_t>(nrec, 1), s)) &&
+            ok(need(&b.recs, &b.crecs, (size_t)std::max<int64_t>(nrec, 1), s));
+        float* out = nullptr;
+        if (dchi2 && out_dev) out = dchi2 + out_global;
+        else if (ok(need(&b.out, &b.cout, out_chunk, s))) out = b.out;
+        if (e != cudaSuccess) { st = map_cuda(e); break; }
+        // ---- moments per curve, then host-side geometry
+        std::vector<int64_t> offl(nc + 1);
+        for (int c = 0; c <= nc; ++c) offl[c] = offsets[c0 + c] - base;
+        ok(cudaMemcpyAsync(b.off, offl.data(), (nc + 1) * 8, cudaMemcpyHostToDevice, s));
+        ok(cudaMemsetAsync(b.counts, 0, 16 * sizeof(int32_t), s));
+        ok(launch_moments(b.t, b.x, b.sg, b.off, nc, 0, b.scal, b.counts + 8, s));
+        std::vector<double> scal((size_t)nc * SC_COUNT);
+        int32_t status = 0;
+        ok(cudaMemcpyAsync(scal.data(), b.scal, scal.size() * 8, cudaMemcpyDeviceToHost, s));
+        ok(cudaMemcpyAsync(&status, b.counts + 8, 4, cudaMemcpyDeviceToHost, s));
+        ok(cudaStreamSynchronize(s));
+        if (e != cudaSuccess) { st = map_cuda(e); break; }
+        if (status) { st = (fc2_status)status; break; }
+        std::vector<int> Hv(nc), slot0(nc), scur, sk, skind;
+        std::vector<double> fminv(nc), dfv(nc);
+        std::vector<int64_t> oo(nc), ssoff, sn, Lv;
+        std::vector<float> sqv(nc), spv(nc), s1v(nc), c0v(nc);
+        std::vector<std::vector<int>> hg(BHM);
+        bool unsorted = false;
+        const int LOGR1 = p.passes[0].logR;
+        const int64_t S1 = M >> LOGR1;
+        const int64_t tile = (M >= 4096) ? 1024 : 128;
+        const int64_t unit = std::max(S1, tile);
+        int64_t acc_out = 0, acc_s = 0;
+        p.geom.assign(S, GridGeom{});
+        int gi = 0;
+        for (int c = 0; c < nc; ++c) {
+            const int64_t cg = c0 + c;
+            double* sc = &scal[(size_t)c * SC_COUNT];
+            const double back = (0.5 * p.w + 1.0) / ((double)M * dfc[cg]);
+            sc[SC_T0] -= back;
+            sc[SC_TAUMAX] += back;
+            if (sc[SC_SORTED] == 0.0) unsorted = true;
+            Hv[c] = Hc[cg]; fminv[c] = fminc[cg]; dfv[c] = dfc[cg];
+            oo[c] = acc_out;
+            acc_out += (int64_t)Hc[cg] * N;
+            const double W = sc[SC_W], chi0 = sc[SC_CHI0];
+            sqv[c] = (float)(1.0 / W);
+            spv[c] = (float)((chi0 > 0.0) ? 1.0 / sqrt(W * chi0) : 0.0);
+            s1v[c] = (float)(sc[SC_S1] * ((chi0 > 0.0) ? 1.0 / sqrt(W * chi0) : 0.0));
+            c0v[c] = (float)chi0;
+            hg[Hc[cg] - 1].push_back(c);
+            slot0[c] = gi;
+            const int64_t n = offl[c + 1] - offl[c];
+            for (int q = 0; q < 3 * Hc[cg]; ++q, ++gi) {
+                const int k = (q < 2 * Hc[cg]) ? q + 1 : q - 2 * Hc[cg] + 1;
+                const int kind = (q < 2 * Hc[cg]) ? 0 : 1;
+                scur.push_back(c); sk.push_back(k); skind.push_back(kind);
+                ssoff.push_back(acc_s); sn.push_back(n);
+                acc_s += n;
+                const double pmax = (double)k * dfc[cg] * sc[SC_TAUMAX];
+                const double cells = pmax * (double)M;
+                GridGeom& gg = p.geom[gi];
+                gg.k = k; gg.kind = kind;
+                if (!(pmax < 1.0) || cells + p.w + 2.0 >= (double)M) {
+                    gg.wraps = (pmax >= 1.0) ? 1 : 0;
+                    gg.L = M;
+                } else {
+                    gg.wraps = 0;
+                    int64_t Lc = (int64_t)floor(cells) + p.w + 3;
+                    Lc = ((Lc + unit - 1) / unit) * unit;
+                    gg.L = std::min(Lc, M);
+                }
+                Lv.push_back(gg.L);
+            }
+        }
+        std::vector<int> curves_flat, hoff(BHM);
+        for (int h = 0; h < BHM; ++h) {
+            hoff[h] = (int)curves_flat.size();
+            curves_flat.insert(curves_flat.end(), hg[h].begin(), hg[h].end());
+        }
+        ok(cudaMemcpyAsync(b.scal, scal.data(), scal.size() * 8, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.H, Hv.data(), nc * 4, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.slot0, slot0.data(), nc * 4, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.fmin, fminv.data(), nc * 8, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.df, dfv.data(), nc * 8, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.out_off, oo.data(), nc * 8, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.sq, sqv.data(), nc * 4, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.sp, spv.data(), nc * 4, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.s1n, s1v.data(), nc * 4, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.chi0f, c0v.data(), nc * 4, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.slot_cur, scur.data(), S * 4, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.slot_k, sk.data(), S * 4, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.slot_kind, skind.data(), S * 4, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.slot_soff, ssoff.data(), S * 8, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.slot_n, sn.data(), S * 8, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.L, Lv.data(), S * 8, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.curves, curves_flat.data(), nc * 4, cudaMemcpyHostToDevice, s));
+        // time order within each curve
+        k_iota_plus<<<(unsigned)((ntot + 255) / 256), 256, 0, s>>>(b.perm, ntot, 0);
+        if (unsorted)
+            for (int c = 0; c < nc; ++c)
+                if (scal[(size_t)c * SC_COUNT + SC_SORTED] == 0.0) {
+                    const int64_t n = offl[c + 1] - offl[c];
+                    ok(sort_by_time(b.t + offl[c], n, b.perm + offl[c], b.grid1, b.cg1, s));
+                    k_add_base<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(b.perm + offl[c], n, offl[c]);
+                }
+        // chunk plan fields for the shared launchers
+        p.G = (int)S;
+        p.n = 0;
+        p.d_key = b.key; p.d_dlt = b.dlt; p.d_cs = b.cs;
+        p.d_grid[0] = b.grid0; p.d_grid[1] = b.grid1; p.d_spec = b.spec;
+        p.d_L = b.L; p.d_slot_soff = b.slot_soff; p.d_slot_n = b.slot_n;
+        p.h_slot_soff = ssoff; p.h_slot_n = sn;
+        const double tau_drop = opt.alias_tau > 0.0 ? opt.alias_tau : (fp64 ? 1e-9 : 1e-6);
+        if (e != cudaSuccess) { st = map_cuda(e); break; }
+        e = fp64 ? chunk_launches<double>(b, nc, ntot, nmax, (int)S, hg, hoff, K, out, nrec, tau_drop)
+                 : chunk_launches<float>(b, nc, ntot, nmax, (int)S, hg, hoff, K, out, nrec, tau_drop);
+        if (e != cudaSuccess) { st = map_cuda(e); break; }
+        // ---- results (a list that overflowed its capacity leaves bins unrepaired)
+        int32_t cnts[4] = {0, 0, 0, 0};
+        ok(cudaMemcpyAsync(cnts, b.counts, 16, cudaMemcpyDeviceToHost, s));
+        if (dchi2 && !out_dev)
+            ok(cudaMemcpyAsync(dchi2 + out_global, out, out_chunk * sizeof(float), cudaMemcpyDeviceToHost, s));
+        if (peaks && K > 0)
+            ok(cudaMemcpyAsync(peaks + c0 * K, b.recs, nrec * sizeof(fc2_best), cudaMemcpyDeviceToHost, s));
+        ok(cudaStreamSynchronize(s));
+        if (e != cudaSuccess) { st = map_cuda(e); break; }
+        if ((size_t)cnts[0] > b.cl1 || (size_t)cnts[1] > b.cl2 || (size_t)cnts[2] > b.cl3) {
+            st = FC2_ERR_NUMERIC;
+            break;
+        }
+        b.stats[0] += cnts[0];
+        b.stats[1] += cnts[1];
+        b.stats[2] += cnts[2];
+        out_global += out_chunk;
+        c0 = c1;
+    }
+    cudaStreamSynchronize(s);
+    if (launches_out) *launches_out = b.launches;
+    if (stats_out)
+        for (int i = 0; i < 3; ++i) stats_out[i] = b.stats[i];
+    b.cp.d_key = nullptr; b.cp.d_dlt = nullptr; b.cp.d_cs = nullptr;
+    b.cp.d_grid[0] = b.cp.d_grid[1] = nullptr; b.cp.d_spec = nullptr; b.cp.d_L = nullptr;
+    b.cp.d_slot_soff = b.cp.d_slot_n = nullptr; b.cp.d_red = nullptr;
+    if (opt.inputs_on_device) { b.t = b.x = b.sg = nullptr; }
+    b.free_all();
+    cudaStreamSynchronize(s);
+    if (b.own_stream) cudaStreamDestroy(s);
+    return st;
+}
+
+}  // namespace fc2

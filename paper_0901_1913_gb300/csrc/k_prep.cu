@@ -27,19 +27,20 @@ __global__ void __launch_bounds__(NT) k_moments(const double* __restrict__ t,
     const int c = blockIdx.x;
     const int64_t a = offs ? offs[c] : 0;
     const int64_t b = offs ? offs[c + 1] : n_single;
-    __shared__ double sh_s[NT], sh_c[NT], sh_s2[NT], sh_c2[NT], sh_mn[NT], sh_mx[NT];
+    __shared__ double sh_s[NT], sh_c[NT], sh_s2[NT], sh_c2[NT], sh_mn[NT], sh_mx[NT], sh_q[NT];
     __shared__ int sh_bad, sh_unsorted;
     if (threadIdx.x == 0) { sh_bad = 0; sh_unsorted = 0; }
     __syncthreads();
     CompSum<double> W, WX;
     W.init(); WX.init();
-    double mn = INFINITY, mx = -INFINITY;
+    double mn = INFINITY, mx = -INFINITY, w2 = 0.0;
     int bad = 0, unsorted = 0;
     for (int64_t i = a + threadIdx.x; i < b; i += NT) {
         double ti = t[i], xi = x[i], si = sg[i];
         if (!isfinite(ti) || !isfinite(xi) || !isfinite(si) || !(si > 0.0)) { bad = 1; continue; }
         double w = 1.0 / (si * si);
         if (!isfinite(w) || w == 0.0) { bad = 1; continue; }
+        w2 += w * w;
         W.add(w);
         WX.add(__dmul_rn(w, xi));
         mn = fmin(mn, ti);
@@ -51,6 +52,7 @@ __global__ void __launch_bounds__(NT) k_moments(const double* __restrict__ t,
     sh_s[threadIdx.x] = W.s; sh_c[threadIdx.x] = W.c;
     sh_s2[threadIdx.x] = WX.s; sh_c2[threadIdx.x] = WX.c;
     sh_mn[threadIdx.x] = mn; sh_mx[threadIdx.x] = mx;
+    sh_q[threadIdx.x] = w2;
     __syncthreads();
     for (int st = NT / 2; st > 0; st >>= 1) {
         if (threadIdx.x < st) {
@@ -62,24 +64,30 @@ __global__ void __launch_bounds__(NT) k_moments(const double* __restrict__ t,
             sh_s2[threadIdx.x] = v.s; sh_c2[threadIdx.x] = v.c;
             sh_mn[threadIdx.x] = fmin(sh_mn[threadIdx.x], sh_mn[threadIdx.x + st]);
             sh_mx[threadIdx.x] = fmax(sh_mx[threadIdx.x], sh_mx[threadIdx.x + st]);
+            sh_q[threadIdx.x] += sh_q[threadIdx.x + st];
         }
         __syncthreads();
     }
+    const double W2 = sh_q[0];
     const double Wv = sh_s[0] + sh_c[0];
     const double xbar = (sh_s2[0] + sh_c2[0]) / Wv;
     const double T0 = sh_mn[0], Tmax = sh_mx[0];
     __syncthreads();
     CompSum<double> C0, S1;
     C0.init(); S1.init();
+    double q2 = 0.0;
     for (int64_t i = a + threadIdx.x; i < b; i += NT) {
         double si = sg[i];
         double w = 1.0 / (si * si);
         double d = x[i] - xbar;
         C0.add(__dmul_rn(__dmul_rn(w, d), d));
         S1.add(__dmul_rn(w, d));
+        q2 += (w * d) * (w * d);
     }
+    __syncthreads();
     sh_s[threadIdx.x] = C0.s; sh_c[threadIdx.x] = C0.c;
     sh_s2[threadIdx.x] = S1.s; sh_c2[threadIdx.x] = S1.c;
+    sh_q[threadIdx.x] = q2;
     __syncthreads();
     for (int st = NT / 2; st > 0; st >>= 1) {
         if (threadIdx.x < st) {
@@ -89,11 +97,15 @@ __global__ void __launch_bounds__(NT) k_moments(const double* __restrict__ t,
             CompSum<double> v; v.s = sh_s2[threadIdx.x]; v.c = sh_c2[threadIdx.x];
             v.add(sh_s2[threadIdx.x + st]); v.c += sh_c2[threadIdx.x + st];
             sh_s2[threadIdx.x] = v.s; sh_c2[threadIdx.x] = v.c;
+            sh_q[threadIdx.x] += sh_q[threadIdx.x + st];
         }
         __syncthreads();
     }
     if (threadIdx.x == 0) {
         double* o = scal + (int64_t)c * SC_COUNT;
+        const double chi0 = sh_s[0] + sh_c[0];
+        const double rq = (Wv > 0.0) ? sqrt(W2) / Wv : 1.0;
+        const double rp = (chi0 > 0.0) ? sqrt(sh_q[0] / (Wv * chi0)) : 0.0;
         o[SC_W] = Wv;
         o[SC_XBAR] = xbar;
         o[SC_CHI0] = sh_s[0] + sh_c[0];
@@ -101,7 +113,7 @@ __global__ void __launch_bounds__(NT) k_moments(const double* __restrict__ t,
         o[SC_T0] = T0;
         o[SC_TAUMAX] = Tmax - T0;
         o[SC_SORTED] = sh_unsorted ? 0.0 : 1.0;
-        o[SC_RW] = 1.0;  // conservative (per-curve ratio not computed here)
+        o[SC_RW] = fmax(rq, rp);
         if (sh_bad || b <= a) set_status(status, FC2_ERR_INVALID_ARG);
     }
 }
@@ -460,7 +472,9 @@ __global__ void k_key_apply(const int32_t* __restrict__ perm, int64_t n,
 template <typename T>
 static cudaError_t sort_keys_of(fc2_plan_s* p, int g, cudaStream_t s) {
     // Scratch: grids are free at this point of the pipeline.
-    const int64_t n = p->n;
+    const bool per_slot = !p->h_slot_n.empty();
+    const int64_t n = per_slot ? p->h_slot_n[g] : p->n;
+    const int64_t so = per_slot ? p->h_slot_soff[g] : (int64_t)g * p->n;
     int64_t nblk = (n + RS_TILE - 1) / RS_TILE;
     char* base = (char*)p->d_grid[1];
     uint64_t* k0 = (uint64_t*)base;
@@ -471,9 +485,9 @@ static cudaError_t sort_keys_of(fc2_plan_s* p, int g, cudaStream_t s) {
     T* d2 = (T*)(((uintptr_t)(key2 + n) + 255) & ~(uintptr_t)255);
     cpx<T>* c2 = (cpx<T>*)(((uintptr_t)(d2 + n) + 255) & ~(uintptr_t)255);
     uint32_t* hist = (uint32_t*)(((uintptr_t)(c2 + n) + 255) & ~(uintptr_t)255);
-    int32_t* key = p->d_key + (int64_t)g * n;
-    T* dl = (T*)p->d_dlt + (int64_t)g * n;
-    cpx<T>* cs = (cpx<T>*)p->d_cs + (int64_t)g * n;
+    int32_t* key = p->d_key + so;
+    T* dl = (T*)p->d_dlt + so;
+    cpx<T>* cs = (cpx<T>*)p->d_cs + so;
     const int32_t off = p->w;  // keys >= 1 - w/2 -> shifted keys are positive
     k_key_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(key, n, off, k0, v0);
     int bits = 0;
@@ -504,6 +518,15 @@ static cudaError_t phase_impl(fc2_plan_s* p, cudaStream_t s) {
     for (int g = 0; g < p->G; ++g)
         if (p->geom[g].wraps) {
             e = sort_keys_of<T>(p, g, s);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+cudaError_t sort_wrapping_keys(fc2_plan_s* p, cudaStream_t s) {
+    for (int g = 0; g < p->G; ++g)
+        if (p->geom[g].wraps) {
+            cudaError_t e = p->fp64 ? sort_keys_of<double>(p, g, s) : sort_keys_of<float>(p, g, s);
             if (e != cudaSuccess) return e;
         }
     return cudaSuccess;
@@ -548,10 +571,12 @@ __device__ __forceinline__ int64_t lower_bound_key(const int32_t* __restrict__ k
 template <typename T, int TILE, int NT, int CAP>
 __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
                                                const T* __restrict__ dlt,
-                                               const cpx<T>* __restrict__ cs, int64_t n,
+                                               const cpx<T>* __restrict__ cs, int64_t n_all,
                                                int64_t M, int w, T beta,
                                                const int64_t* __restrict__ Lg,
-                                               cpx<T>* __restrict__ grid, int64_t gstride) {
+                                               cpx<T>* __restrict__ grid, int64_t gstride,
+                                               const int64_t* __restrict__ slot_soff,
+                                               const int64_t* __restrict__ slot_n) {
     constexpr int PER = TILE / NT;
     __shared__ int32_t sk[CAP];
     __shared__ T sd[CAP];
@@ -560,9 +585,12 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
     const int g = blockIdx.y;
     const int64_t a = (int64_t)blockIdx.x * TILE;
     if (a >= Lg[g]) return;
-    const int32_t* kg = key + (int64_t)g * n;
-    const T* dg = dlt + (int64_t)g * n;
-    const cpx<T>* cg = cs + (int64_t)g * n;
+    // samples of transform g: [g n, (g + 1) n) or, for a batch, per-slot ranges
+    const int64_t so = slot_soff ? slot_soff[g] : (int64_t)g * n_all;
+    const int64_t n = slot_n ? slot_n[g] : n_all;
+    const int32_t* kg = key + so;
+    const T* dg = dlt + so;
+    const cpx<T>* cg = cs + so;
     if (threadIdx.x < 3) {
         // ranges of keys (shifted by -M, 0, +M) whose windows meet the tile
         int64_t sh = (threadIdx.x == 0) ? M : (threadIdx.x == 1 ? 0 : -M);
@@ -624,7 +652,7 @@ static cudaError_t spread_tiles(fc2_plan_s* p, cudaStream_t s) {
     dim3 grid((unsigned)tiles, (unsigned)p->G);
     k_spread<T, TILE, NT, CAP><<<grid, NT, 0, s>>>(
         p->d_key, (const T*)p->d_dlt, (const cpx<T>*)p->d_cs, p->n, p->M, p->w, (T)p->beta,
-        p->d_L, (cpx<T>*)p->d_grid[0], p->M);
+        p->d_L, (cpx<T>*)p->d_grid[0], p->M, p->d_slot_soff, p->d_slot_n);
     return cudaGetLastError();
 }
 

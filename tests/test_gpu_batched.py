@@ -1,0 +1,82 @@
+"""Batched execution (many uneven curves per launch) against the oracle and
+against one-curve plans."""
+import numpy as np
+import pytest
+
+from paper_0901_1913_gb300 import synth
+from tests.parity import TOL, compare, sample_bins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fc2():
+    from paper_0901_1913_gb300 import _fc2
+    _fc2.load()
+    return _fc2
+
+
+def small_survey(C=24, N=1 << 13, seed=3):
+    return synth.config3(seed=seed, C=C, N=N, n_median=600.0, n_hi=3000)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batched_matches_oracle(fc2, oracle_mod, prec):
+    b = small_survey()
+    out, peaks, stats = fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df,
+                                            b.N, 2, prec)
+    pos = 0
+    for c in range(b.C):
+        cur = b.curve(c)
+        block = out[pos:pos + cur.H * cur.N].reshape(cur.H, cur.N)
+        pos += cur.H * cur.N
+        if c % 4:
+            continue  # oracle on every fourth curve keeps the test short
+        j0 = int(round((cur.truth["f0"] - cur.f_min) / cur.df))
+        bins = sample_bins(cur.N, 150, c, windows=[min(cur.N - 1, j0), int(np.argmax(block[-1]))],
+                           half=8)
+        ref, piv = oracle_mod.dchi2_bins(cur.t, cur.x, cur.sigma, cur.H, cur.f_min, cur.df, bins,
+                                         with_pivots=True)
+        _, _, chi0, _ = oracle_mod.moments(cur.x, cur.sigma)
+        r = compare(block[:, bins].T.astype(np.float64), ref, piv, chi0)
+        assert r["ok"], (c, r)
+    assert pos == out.size
+    assert stats["launches"] > 0
+
+
+def test_batched_equals_single_plans(fc2):
+    b = small_survey(C=10, seed=7)
+    out, peaks, _ = fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df, b.N,
+                                        2, "mixed", top_k=5)
+    pos = 0
+    for c in range(b.C):
+        cur = b.curve(c)
+        block = out[pos:pos + cur.H * cur.N].reshape(cur.H, cur.N)
+        pos += cur.H * cur.N
+        d, best, pk, chi0 = fc2.periodogram(cur.t, cur.x, cur.sigma, cur.H, cur.f_min, cur.df,
+                                            cur.N, 2, "mixed", top_k=5)
+        assert np.max(np.abs(block - d)) <= TOL * chi0
+        # peak lists agree up to near-ties
+        for pb, ps in zip(peaks[c], pk):
+            if pb["j"] != ps["j"]:
+                assert abs(pb["dchi2"] - ps["dchi2"]) <= TOL * chi0
+            else:
+                np.testing.assert_allclose(pb["A"], ps["A"], atol=1e-6 * max(1e-300, np.abs(ps["A"]).max()))
+
+
+def test_batched_device_buffers_and_unsorted(fc2):
+    import torch
+    b = small_survey(C=8, seed=11)
+    # shuffle the samples of one curve: the batch sorts it
+    t, x, s = b.t.copy(), b.x.copy(), b.sigma.copy()
+    a0, a1 = int(b.offsets[3]), int(b.offsets[4])
+    p = np.random.default_rng(1).permutation(a1 - a0) + a0
+    t[a0:a1], x[a0:a1], s[a0:a1] = t[p], x[p], s[p]
+    ref, _, _ = fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df, b.N, 2)
+    dev = torch.device("cuda", 0)
+    td, xd, sd = (torch.from_numpy(v).to(dev) for v in (t, x, s))
+    out = torch.empty(ref.size, dtype=torch.float32, device=dev)
+    fc2.execute_batched(b.offsets, td, xd, sd, b.H, b.f_min, b.df, b.N, 2, dchi2=out)
+    got = out.cpu().numpy()
+    scale = max(1.0, float(np.abs(ref).max()))
+    assert np.max(np.abs(got - ref)) <= 1e-5 * scale
