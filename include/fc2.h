@@ -146,20 +146,38 @@ fc2_status fc2_execute_batched(int64_t C, const int64_t* offsets,
 /*
  * fc2_backward -- exact (ungridded) gradients and Newton refinement at peaks,
  * the local refinement "using the ungridded data" of Sec. 3e.
- *   K peaks at bins peak_j [K] (host).  For each k, with f = f_min + peak_j[k] df
- *   and the H-harmonic model:
- *     d_df[k]        = g_k * dDelta/df,
- *     d_dx[k][i]     = g_k * dDelta/dx_i,
- *     d_dsigma[k][i] = g_k * dDelta/dsigma_i      (i in the caller's sample order),
- *   with g_k = grad_out[k] (NULL = all ones), Delta = Delta chi^2_H computed by
- *   direct double sums over the samples.  f_refined[k] is the Newton maximiser
- *   of the exact Delta chi^2_H within one df of the bin (stopping when the step
- *   is below 1e-9 /d... or 1e-3 df, whichever is smaller) and dchi2_refined[k]
- *   its value.  Any output may be NULL; d_dx/d_dsigma follow outputs_on_device.
+ *   K >= 1 peaks at bins peak_j [K] (host, 0 <= j < N).  For each k, with
+ *   f = f_min + peak_j[k] df and the H-harmonic model (H <= 8):
+ *     d_df[k]          = g_k * dDelta/df,
+ *     d_dx[k * n + i]  = g_k * dDelta/dx_i,
+ *     d_dsigma[k*n + i] = g_k * dDelta/dsigma_i   (i in the caller's sample order),
+ *   with g_k = grad_out[k] (NULL = all ones) and Delta = Delta chi^2_H computed
+ *   by direct double sums over the samples (envelope theorem: xbar and the
+ *   coefficients are minimisers and need no derivative).
+ *   f_refined[k]: maximiser of the exact Delta chi^2_H(f) within one df of the
+ *   bin by safeguarded Newton steps (exact second derivative), stopping when
+ *   the step is below 1e-10 /d; dchi2_refined[k] its value.
+ *   Any output may be NULL; each output pointer may be host or device memory
+ *   (detected from the pointer).  Synchronous.
  */
 fc2_status fc2_backward(fc2_plan p, int K, const int64_t* peak_j, const double* grad_out,
                         double* f_refined, double* dchi2_refined, double* d_df,
                         double* d_dx, double* d_dsigma);
+
+/*
+ * fc2_backward_batched -- fc2_backward for K peaks of each of C curves laid out
+ * as in fc2_execute_batched.  peak_j [C][K], grad_out [C][K] (NULL = ones),
+ * f_refined / dchi2_refined / d_df [C][K]; d_dx and d_dsigma hold, for curve c
+ * and peak r, n_c values starting at K * (offsets[c] - offsets[0]) + r * n_c.
+ * t, x, sigma follow opt->inputs_on_device; outputs may be host or device.
+ */
+fc2_status fc2_backward_batched(int64_t C, const int64_t* offsets,
+                                const double* t, const double* x, const double* sigma,
+                                const int* H, const double* f_min, const double* df,
+                                const int64_t* N, int K, const int64_t* peak_j,
+                                const double* grad_out, const fc2_options* opt,
+                                double* f_refined, double* dchi2_refined, double* d_df,
+                                double* d_dx, double* d_dsigma);
 
 /* Release a plan and its device memory.  NULL is ignored. */
 void fc2_plan_destroy(fc2_plan p);

@@ -278,3 +278,108 @@ def execute_batched(offsets, t, x, sigma, H, f_min, df, N, oversample=2, prec="m
     recs = [[peaks[c * K + r].as_dict() for r in range(K)] for c in range(C)]
     return dchi2, recs, dict(launches=int(lib.fc2_debug_batch_launches()),
                              resolved=int(st[0]), exact=int(st[1]), exact_double=int(st[2]))
+
+
+def _backward_argtypes(lib):
+    if getattr(lib, "_bw_ready", False):
+        return
+    lib.fc2_backward.argtypes = [_P, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P]
+    lib.fc2_backward.restype = ctypes.c_int
+    lib.fc2_backward_batched.argtypes = [ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P,
+                                         ctypes.c_int, _P, _P, ctypes.POINTER(Options), _P, _P,
+                                         _P, _P, _P]
+    lib.fc2_backward_batched.restype = ctypes.c_int
+    lib._bw_ready = True
+
+
+def plan_backward(plan, peak_j, grad_out=None, want_samples=True):
+    """fc2_backward on a Plan: exact gradients at the bins peak_j and Newton
+    refinement.  Returns dict(f_refined, dchi2_refined, d_df [K], d_dx [K, n],
+    d_dsigma [K, n]) as numpy arrays."""
+    lib = load()
+    _backward_argtypes(lib)
+    pj = np.ascontiguousarray(peak_j, dtype=np.int64)
+    K = pj.size
+    g = None if grad_out is None else np.ascontiguousarray(grad_out, dtype=np.float64)
+    fr, dr, dd = np.zeros(K), np.zeros(K), np.zeros(K)
+    dx = np.zeros((K, plan.n)) if want_samples else None
+    ds = np.zeros((K, plan.n)) if want_samples else None
+    rc = lib.fc2_backward(plan.h, K, pj.ctypes.data, None if g is None else g.ctypes.data,
+                          fr.ctypes.data, dr.ctypes.data, dd.ctypes.data,
+                          None if dx is None else dx.ctypes.data,
+                          None if ds is None else ds.ctypes.data)
+    _check(rc, "fc2_backward")
+    return dict(f_refined=fr, dchi2_refined=dr, d_df=dd, d_dx=dx, d_dsigma=ds)
+
+
+Plan.backward = plan_backward
+
+
+def backward_batched(offsets, t, x, sigma, H, f_min, df, N, peak_j, grad_out=None, stream=None,
+                     device=0, d_dx=None, d_dsigma=None):
+    """fc2_backward_batched: peak_j [C, K].  Returns dict of f_refined, dchi2_refined,
+    d_df ([C, K]) and d_dx, d_dsigma (flat, curve c peak r at K*off[c] + r*n_c)."""
+    lib = load()
+    _backward_argtypes(lib)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    C = offsets.size - 1
+    pj = np.ascontiguousarray(peak_j, dtype=np.int64).reshape(C, -1)
+    K = pj.shape[1]
+    H = np.ascontiguousarray(np.broadcast_to(H, (C,)), dtype=np.int32)
+    f_min = np.ascontiguousarray(np.broadcast_to(f_min, (C,)), dtype=np.float64)
+    df = np.ascontiguousarray(np.broadcast_to(df, (C,)), dtype=np.float64)
+    N = np.ascontiguousarray(np.broadcast_to(N, (C,)), dtype=np.int64)
+    dev = _is_dev(t)
+    if not dev:
+        t = np.ascontiguousarray(t, dtype=np.float64)
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    g = None if grad_out is None else np.ascontiguousarray(grad_out, dtype=np.float64)
+    ntot = int(offsets[-1] - offsets[0])
+    fr, dr, dd = np.zeros((C, K)), np.zeros((C, K)), np.zeros((C, K))
+    if d_dx is None:
+        d_dx = np.zeros(K * ntot)
+    if d_dsigma is None:
+        d_dsigma = np.zeros(K * ntot)
+    opt = make_options("fp64", 0, K, 0.0, stream, device, inputs_on_device=dev)
+    rc = lib.fc2_backward_batched(C, offsets.ctypes.data, _ptr(t), _ptr(x), _ptr(sigma),
+                                  H.ctypes.data, f_min.ctypes.data, df.ctypes.data, N.ctypes.data,
+                                  K, pj.ctypes.data, None if g is None else g.ctypes.data,
+                                  ctypes.byref(opt), fr.ctypes.data, dr.ctypes.data,
+                                  dd.ctypes.data, _ptr(d_dx), _ptr(d_dsigma))
+    _check(rc, "fc2_backward_batched")
+    return dict(f_refined=fr, dchi2_refined=dr, d_df=dd, d_dx=d_dx, d_dsigma=d_dsigma)
+
+
+def peaks_function():
+    """torch.autograd.Function: (x, sigma) -> Delta chi^2_H at the top-K peak
+    bins of a fixed time grid; backward through fc2_backward (exact adjoint)."""
+    import torch
+
+    class Fchi2Peaks(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x, sigma, t, H, f_min, df, N, oversample=2, prec="mixed", top_k=8):
+            xn = x.detach().cpu().numpy().astype(np.float64)
+            sn = sigma.detach().cpu().numpy().astype(np.float64)
+            tn = np.asarray(t, dtype=np.float64)
+            plan = Plan(tn, xn, sn, H, f_min, df, N, oversample, prec, top_k=top_k)
+            _, _, peaks, _ = plan.execute()
+            js = np.array([p["j"] for p in peaks if p["j"] >= 0], dtype=np.int64)
+            vals = torch.tensor([p["dchi2"] for p in peaks if p["j"] >= 0], dtype=torch.float64)
+            ctx.plan = plan
+            ctx.js = js
+            ctx.dev = x.device
+            jt = torch.from_numpy(js).to(x.device)
+            ctx.mark_non_differentiable(jt)
+            return vals.to(x.device), jt
+
+        @staticmethod
+        def backward(ctx, g_vals, g_js):
+            g = g_vals.detach().cpu().numpy().astype(np.float64)
+            r = ctx.plan.backward(ctx.js, grad_out=g)
+            gx = torch.from_numpy(r["d_dx"].sum(axis=0)).to(ctx.dev)
+            gs = torch.from_numpy(r["d_dsigma"].sum(axis=0)).to(ctx.dev)
+            ctx.plan.close()
+            return gx, gs, None, None, None, None, None, None, None, None
+
+    return Fchi2Peaks

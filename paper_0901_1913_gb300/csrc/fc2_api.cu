@@ -356,6 +356,19 @@ fc2_status fc2_execute(fc2_plan p, double* dchi2, fc2_best* best, fc2_best* peak
     return FC2_OK;
 }
 
+fc2_status fc2_backward_batched(int64_t C, const int64_t* offsets, const double* t,
+                                const double* x, const double* sigma, const int* H,
+                                const double* f_min, const double* df, const int64_t* N, int K,
+                                const int64_t* peak_j, const double* grad_out,
+                                const fc2_options* opt_in, double* f_refined,
+                                double* dchi2_refined, double* d_df, double* d_dx,
+                                double* d_dsigma) {
+    fc2_options opt;
+    if (opt_in) opt = *opt_in; else fc2_options_default(&opt);
+    return batched_backward(C, offsets, t, x, sigma, H, f_min, df, N, K, peak_j, grad_out, opt,
+                            f_refined, dchi2_refined, d_df, d_dx, d_dsigma);
+}
+
 void fc2_plan_destroy(fc2_plan p) {
     if (!p) return;
     cudaSetDevice(p->device);
@@ -385,9 +398,7 @@ fc2_status fc2_execute_batched(int64_t C, const int64_t* offsets, const double* 
 fc2_status fc2_backward(fc2_plan p, int K, const int64_t* peak_j, const double* grad_out,
                         double* f_refined, double* dchi2_refined, double* d_df, double* d_dx,
                         double* d_dsigma) {
-    (void)p; (void)K; (void)peak_j; (void)grad_out; (void)f_refined; (void)dchi2_refined;
-    (void)d_df; (void)d_dx; (void)d_dsigma;
-    return FC2_ERR_UNSUPPORTED;
+    return plan_backward(p, K, peak_j, grad_out, f_refined, dchi2_refined, d_df, d_dx, d_dsigma);
 }
 
 /* Diagnostics (not in the public header): number of bins the last execute

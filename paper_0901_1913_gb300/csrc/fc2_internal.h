@@ -156,10 +156,37 @@ size_t peaks_scratch_bytes(int64_t N, int H, int K);
 size_t exact_scratch_bytes(int64_t n, int H, int64_t cap);
 cudaError_t launch_phase_fx(fc2_plan_s* p, cudaStream_t s);
 
-// k_adjoint.cu
-cudaError_t launch_backward(fc2_plan_s* p, int K, const int64_t* d_j, const double* d_g,
-                            double* d_fref, double* d_dref, double* d_df, double* d_dx,
-                            double* d_ds, cudaStream_t s);
+// k_adjoint.cu: one entry = (curve << 32 | bin) of a curve table
+struct AdjTab {
+    const int64_t* off;      // [C+1]
+    const int* H;            // [C]
+    const double* fmin;      // [C]
+    const double* df;        // [C]
+    const double* scal;      // [C][SC_COUNT]
+    const double* tau;       // sorted samples: t - T0
+    const double* wq;        // w
+    const double* wp;        // w (x - xbar)
+    const int32_t* perm;     // sorted position -> caller position (global), or null
+    const int64_t* ent;      // [E] (curve << 32 | j)
+    const double* gout;      // [E] upstream gradients or null (= 1)
+    int K;                   // entries per curve (output layout of d_dx / d_dsigma)
+    double tol;              // Newton stopping step
+    int max_iter;
+};
+
+struct AdjOut {
+    double* f_ref;
+    double* d_ref;
+    double* d_df;
+    double* d_dx;     // entry (c, r): K off[c] + r n_c + i, caller order within the curve
+    double* d_dsig;
+};
+
+
+cudaError_t launch_backward_tab(const AdjTab& tb, int64_t E, const AdjOut& out, cudaStream_t s);
+fc2_status plan_backward(fc2_plan_s* p, int K, const int64_t* peak_j, const double* grad_out,
+                         double* f_ref, double* d_ref, double* d_df, double* d_dx,
+                         double* d_dsig);
 
 // k_batch.cu
 fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, const double* x,
@@ -167,6 +194,12 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
                            const double* df, const int64_t* N, int oversample,
                            const fc2_options& opt, float* dchi2, fc2_best* peaks,
                            int64_t* launches_out, int64_t* stats_out);
+
+fc2_status batched_backward(int64_t C, const int64_t* offsets, const double* t, const double* x,
+                            const double* sigma, const int* H, const double* fmin,
+                            const double* df, const int64_t* N, int K, const int64_t* peak_j,
+                            const double* grad_out, const fc2_options& opt, double* f_ref,
+                            double* d_ref, double* d_df, double* d_dx, double* d_dsig);
 
 // host helpers (fc2_host.cpp)
 void gauss_legendre(int nq, double* x, double* w);

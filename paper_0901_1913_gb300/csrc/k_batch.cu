@@ -929,4 +929,132 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     return st;
 }
 
+
+// Gradients and Newton refinement for K peaks of each of C curves
+// (fc2_backward_batched): per-curve moments, time order and the sample
+// arrays, then the adjoint kernel over all C K entries.
+fc2_status batched_backward(int64_t C, const int64_t* offsets, const double* t, const double* x,
+                            const double* sigma, const int* Hc, const double* fminc,
+                            const double* dfc, const int64_t* Nc, int K, const int64_t* peak_j,
+                            const double* grad_out, const fc2_options& opt, double* f_ref,
+                            double* d_ref, double* d_df, double* d_dx, double* d_dsig) {
+    if (C < 1 || K < 1 || !offsets || !t || !x || !sigma || !Hc || !fminc || !dfc || !Nc || !peak_j)
+        return FC2_ERR_INVALID_ARG;
+    for (int64_t c = 0; c < C; ++c) {
+        if (offsets[c + 1] - offsets[c] < 1 || offsets[c] < 0) return FC2_ERR_INVALID_ARG;
+        if (Hc[c] < 1 || Hc[c] > FC2_MAX_H || Nc[c] < 2) return FC2_ERR_INVALID_ARG;
+        if (Hc[c] > 8) return FC2_ERR_UNSUPPORTED;
+        if (!(std::isfinite(fminc[c]) && fminc[c] >= 0.0) || !(std::isfinite(dfc[c]) && dfc[c] > 0.0))
+            return FC2_ERR_INVALID_ARG;
+        for (int k = 0; k < K; ++k)
+            if (peak_j[c * K + k] < 0 || peak_j[c * K + k] >= Nc[c]) return FC2_ERR_INVALID_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return FC2_ERR_CUDA;
+    if (opt.device < 0 || opt.device >= ndev) return FC2_ERR_INVALID_ARG;
+    if (cudaSetDevice(opt.device) != cudaSuccess) return FC2_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)opt.cuda_stream;
+    bool own = false;
+    if (!s) {
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return FC2_ERR_CUDA;
+        own = true;
+    }
+    const int64_t base = offsets[0], ntot = offsets[C] - base;
+    const int64_t E = C * K;
+    auto is_dev = [&](const void* q) {
+        cudaPointerAttributes at;
+        bool d = q && cudaPointerGetAttributes(&at, q) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+        cudaGetLastError();
+        return d;
+    };
+    std::vector<void*> owned;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (e != cudaSuccess) return;
+        e = cudaMallocAsync(p, std::max<size_t>(bytes, 64), s);
+        if (e == cudaSuccess) owned.push_back(*p);
+    };
+    double *dt = nullptr, *dx = nullptr, *ds = nullptr;
+    if (opt.inputs_on_device) { dt = (double*)(t + base); dx = (double*)(x + base); ds = (double*)(sigma + base); }
+    else {
+        alloc((void**)&dt, ntot * 8); alloc((void**)&dx, ntot * 8); alloc((void**)&ds, ntot * 8);
+        if (e == cudaSuccess) {
+            cudaMemcpyAsync(dt, t + base, ntot * 8, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(dx, x + base, ntot * 8, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(ds, sigma + base, ntot * 8, cudaMemcpyHostToDevice, s);
+        }
+    }
+    int64_t* off = nullptr; int* Hd = nullptr; double *fm = nullptr, *dfd = nullptr, *scal = nullptr;
+    int32_t *perm = nullptr, *status = nullptr; double *tau = nullptr, *wq = nullptr, *wp = nullptr;
+    uint64_t *A = nullptr, *B = nullptr; float *w32 = nullptr, *p32 = nullptr;
+    int64_t* ent = nullptr; double* g = nullptr;
+    double *of = nullptr, *od = nullptr, *og = nullptr, *oxx = nullptr, *oss = nullptr;
+    alloc((void**)&off, (C + 1) * 8); alloc((void**)&Hd, C * 4); alloc((void**)&fm, C * 8);
+    alloc((void**)&dfd, C * 8); alloc((void**)&scal, C * SC_COUNT * 8); alloc((void**)&status, 16);
+    alloc((void**)&perm, ntot * 4); alloc((void**)&tau, ntot * 8); alloc((void**)&wq, ntot * 8);
+    alloc((void**)&wp, ntot * 8); alloc((void**)&A, ntot * 8); alloc((void**)&B, ntot * 8);
+    alloc((void**)&w32, ntot * 4); alloc((void**)&p32, ntot * 4); alloc((void**)&ent, E * 8);
+    alloc((void**)&of, E * 8); alloc((void**)&od, E * 8); alloc((void**)&og, E * 8);
+    if (grad_out) alloc((void**)&g, E * 8);
+    const bool dx_dev = is_dev(d_dx), ds_dev = is_dev(d_dsig);
+    if (d_dx && !dx_dev) alloc((void**)&oxx, (size_t)K * ntot * 8);
+    if (d_dsig && !ds_dev) alloc((void**)&oss, (size_t)K * ntot * 8);
+    int64_t nmax = 0;
+    std::vector<int64_t> offl(C + 1), entv(E);
+    for (int64_t c = 0; c <= C; ++c) offl[c] = offsets[c] - base;
+    for (int64_t c = 0; c < C; ++c) {
+        nmax = std::max(nmax, offl[c + 1] - offl[c]);
+        for (int k = 0; k < K; ++k) entv[c * K + k] = (c << 32) | peak_j[c * K + k];
+    }
+    fc2_status st = FC2_OK;
+    if (e == cudaSuccess) {
+        cudaMemcpyAsync(off, offl.data(), (C + 1) * 8, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(Hd, Hc, C * 4, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(fm, fminc, C * 8, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(dfd, dfc, C * 8, cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(ent, entv.data(), E * 8, cudaMemcpyHostToDevice, s);
+        if (grad_out) cudaMemcpyAsync(g, grad_out, E * 8, cudaMemcpyDefault, s);
+        cudaMemsetAsync(status, 0, 16, s);
+        launch_moments(dt, dx, ds, off, C, 0, scal, status, s);
+        std::vector<double> hs((size_t)C * SC_COUNT);
+        int32_t hst = 0;
+        cudaMemcpyAsync(hs.data(), scal, hs.size() * 8, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&hst, status, 4, cudaMemcpyDeviceToHost, s);
+        e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && hst) st = (fc2_status)hst;
+        if (e == cudaSuccess && st == FC2_OK) {
+            k_iota_plus<<<(unsigned)((ntot + 255) / 256), 256, 0, s>>>(perm, ntot, 0);
+            char* scratch = nullptr;
+            const size_t sb = sort_scratch_bytes(nmax) + 4096;
+            for (int64_t c = 0; c < C && e == cudaSuccess; ++c)
+                if (hs[c * SC_COUNT + SC_SORTED] == 0.0) {
+                    if (!scratch) { alloc((void**)&scratch, sb); if (e != cudaSuccess) break; }
+                    const int64_t n = offl[c + 1] - offl[c];
+                    e = sort_by_time(dt + offl[c], n, perm + offl[c], scratch, sb, s);
+                    k_add_base<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(perm + offl[c], n, offl[c]);
+                }
+            k_bgather<<<(unsigned)((ntot + 255) / 256), 256, 0, s>>>(dt, dx, ds, perm, ntot, off, (int)C,
+                                                                    scal, fm, dfd, tau, wq, wp, A, B,
+                                                                    w32, p32);
+            AdjTab tb{off, Hd, fm, dfd, scal, tau, wq, wp, perm, ent, g, K, 1e-10, 40};
+            AdjOut out{of, od, og, d_dx ? (dx_dev ? d_dx : oxx) : nullptr,
+                       d_dsig ? (ds_dev ? d_dsig : oss) : nullptr};
+            if (e == cudaSuccess) e = launch_backward_tab(tb, E, out, s);
+            if (e == cudaSuccess) {
+                if (f_ref) cudaMemcpyAsync(f_ref, of, E * 8, cudaMemcpyDefault, s);
+                if (d_ref) cudaMemcpyAsync(d_ref, od, E * 8, cudaMemcpyDefault, s);
+                if (d_df) cudaMemcpyAsync(d_df, og, E * 8, cudaMemcpyDefault, s);
+                if (d_dx && !dx_dev) cudaMemcpyAsync(d_dx, oxx, (size_t)K * ntot * 8, cudaMemcpyDeviceToHost, s);
+                if (d_dsig && !ds_dev) cudaMemcpyAsync(d_dsig, oss, (size_t)K * ntot * 8, cudaMemcpyDeviceToHost, s);
+                e = cudaStreamSynchronize(s);
+            }
+        }
+    }
+    for (void* q : owned) cudaFreeAsync(q, s);
+    cudaStreamSynchronize(s);
+    if (own) cudaStreamDestroy(s);
+    if (st != FC2_OK) return st;
+    return map_cuda(e);
+}
+
 }  // namespace fc2
