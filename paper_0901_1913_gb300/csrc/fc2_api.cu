@@ -2,6 +2,7 @@
 // management and the order of kernel launches.  No kernel arithmetic here.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -115,6 +116,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     p->tau = opt.alias_tau > 0.0 ? opt.alias_tau : (p->fp64 ? 1e-9 : 1e-6);
     p->top_k = opt.top_k ? opt.top_k : 8;
     plan_fft_passes(p);
+    p->use_r64 = (getenv("FC2_FFT_RADIX16") == nullptr);  // A/B switch for the transform kernels
 
     const size_t tsz = p->fp64 ? 8 : 4;
     const size_t csz = 2 * tsz;

@@ -46,7 +46,24 @@ FC2_HD cpx<T> root16(int k) {
     return mk(s, -c);
 }
 
-// In-register DFT of length Q (power of two <= 16), sign +: X_k = sum_n x_n e^{+2 pi i n k / Q}.
+// e^{+2 pi i k / 64} from cos(k pi / 32), k = 0..16 (double literals).
+template <typename T>
+FC2_HD cpx<T> root64(int k) {
+    const double c[17] = {1.0, 0.99518472667219689, 0.98078528040323043, 0.95694033573220882,
+                          0.92387953251128674, 0.88192126434835505, 0.83146961230254524,
+                          0.77301045336273699, 0.70710678118654757, 0.63439328416364549,
+                          0.55557023301960229, 0.47139673682599781, 0.38268343236508984,
+                          0.29028467725446233, 0.19509032201612833, 0.098017140329560604, 0.0};
+    const int q = k & 63;
+    const int quad = q >> 4, rem = q & 15;
+    const T cs = (T)c[rem], sn = (T)c[16 - rem];
+    if (quad == 0) return mk(cs, sn);
+    if (quad == 1) return mk(-sn, cs);
+    if (quad == 2) return mk(-cs, -sn);
+    return mk(sn, -cs);
+}
+
+// In-register DFT of length Q (power of two <= 64), sign +: X_k = sum_n x_n e^{+2 pi i n k / Q}.
 template <typename T, int Q>
 struct SmallDFT {
     static FC2_D void run(cpx<T>* v) {
@@ -60,7 +77,8 @@ struct SmallDFT {
             cpx<T> t;
             if (k == 0) t = o[k];
             else if (4 * k == Q) t = mul_i(o[k]);
-            else t = mul(o[k], root16<T>(k * (16 / Q)));
+            else if constexpr (Q <= 16) t = mul(o[k], root16<T>(k * (16 / Q)));
+            else t = mul(o[k], root64<T>(k * (64 / Q)));
             v[k] = add(e[k], t);
             v[k + Q / 2] = sub(e[k], t);
         }

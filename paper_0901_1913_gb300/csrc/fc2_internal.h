@@ -89,6 +89,8 @@ struct fc2_plan_s {
     int tw_shift = 0;
     void* d_twst = nullptr;    // cpx<T> in-CTA stage twiddles per radix
     int64_t twst_off[16] = {0};
+    int64_t tw64_off[16] = {0};
+    bool use_r64 = true;       // float passes of radix 2^10..2^12 use the two-stage kernel
     double* d_dchi2 = nullptr; // [H][N]
     float* d_minpiv = nullptr; // unused slot kept for diagnostics
     int32_t* d_flag_list = nullptr;  // bins needing the exact fix-up

@@ -9,6 +9,8 @@
 // peak search.  Output Delta chi^2 is float, packed curve after curve.
 #include <cuda_runtime.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
 #include <map>
 #include <vector>
@@ -727,6 +729,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             p.beta = 0.97 * M_PI * (1.0 - 0.5 / ((double)M / (double)N)) * (double)p.w;
             p.stream = s;
             plan_fft_passes(&p);
+            p.use_r64 = (getenv("FC2_FFT_RADIX16") == nullptr);
             release(p.d_twlo, s); release(p.d_twhi, s); release(p.d_twst, s); release(p.d_dec, s);
             const int sh = (p.logM + 1) / 2;
             cudaError_t e = cudaMallocAsync(&p.d_twlo, (size_t)(1ll << sh) * csz, s);

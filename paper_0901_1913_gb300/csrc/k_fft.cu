@@ -381,6 +381,156 @@ __global__ void __launch_bounds__(NT, 2) k_fft_pass(const cpx<T>* __restrict__ i
     }
 }
 
+// ------------------------------------------------- two-stage radix-64 pass
+// Float passes of radix R = 2^10..2^12 in two register stages, QA = R/64 then
+// 64, with 128 threads per 8192-element tile.  Stage A reads its butterfly
+// straight from global memory (coalesced along the tile's columns), applies
+// the inter-pass twiddle and writes to shared memory; stage B reads, applies
+// the stage twiddle w_R^{k pp}, and writes its outputs back to the same slots;
+// then the tile is stored as by k_fft_pass.  Shared memory holds one tile,
+// swizzled (e ^ ((e >> 7) & 31)) so both stages' access patterns are free of
+// bank conflicts, plus the stage-B twiddles.
+FC2_HD int swz(int e) { return e ^ ((e >> 7) & 31); }
+
+template <typename T>
+__global__ void k_init_tw64(cpx<T>* tw, int LOGR) {
+    const int QA = 1 << (LOGR - 6);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 63 * QA) return;
+    const int k = i / QA + 1, pm = i % QA;
+    double sn, cn;
+    sincospi(2.0 * (double)(k * pm) / (double)(1 << LOGR), &sn, &cn);
+    tw[i] = mk<T>((T)cn, (T)sn);
+}
+
+template <int LOGR, int LOGJ>
+__global__ void __launch_bounds__(128, 2) k_fft_pass64(const cpx<float>* __restrict__ in,
+                                                       cpx<float>* __restrict__ out, PassArgs a,
+                                                       const int64_t* __restrict__ Lg,
+                                                       const cpx<float>* __restrict__ twlo,
+                                                       const cpx<float>* __restrict__ twhi,
+                                                       const cpx<float>* __restrict__ tw64) {
+    using T = float;
+    constexpr int R = 1 << LOGR, J = 1 << LOGJ, E = R * J, NT = 128;
+    constexpr int QAB = LOGR - 6, QA = 1 << QAB;
+    constexpr int PERA = 64 / QA;  // stage-A butterflies per thread
+    static_assert(E == 64 * NT, "tile must be 64 elements per thread");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* s = reinterpret_cast<cpx<T>*>(smem_raw);
+    cpx<T>* st = s + E;
+    const int M = 1 << a.logM;
+    const int S = M >> LOGR;
+    const int g = blockIdx.y;
+    const int j0 = blockIdx.x * J;
+    const cpx<T>* gin = in + (int64_t)g * M;
+    for (int i = threadIdx.x; i < 63 * QA; i += NT) cp_elem(&st[i], &tw64[i]);
+    int rows = R;
+    if (a.first) {
+        const int L = (int)Lg[g];
+        rows = (L + S - 1) / S;
+        if (rows > R) rows = R;
+    }
+    const int nsg_mask = (1 << a.logNs) - 1;
+    const int lts = a.logM - a.logNs - LOGR;
+    // ---- stage A: radix QA, rows pp + k 64 -> rows pp QA + k
+#pragma unroll
+    for (int b = 0; b < PERA; ++b) {
+        const int bi = threadIdx.x + b * NT;
+        const int jj = bi % J, pp = bi / J;  // pp < 64
+        cpx<T> v[QA];
+        if (a.first) {
+#pragma unroll
+            for (int k = 0; k < QA; ++k) {
+                const int r = pp + k * 64;
+                v[k] = (r < rows) ? gin[j0 + jj + r * S] : mk<T>(0.f, 0.f);
+            }
+        } else {
+            const cpx<T>* src = gin + (int64_t)blockIdx.x * E;
+#pragma unroll
+            for (int k = 0; k < QA; ++k) v[k] = src[(pp + k * 64) * J + jj];
+        }
+        const int jm = (j0 + jj) & nsg_mask;
+        if (a.logNs > 0 && jm != 0) {
+            // w_M^{(pp + 64 k) jm 2^lts} = base * step^k, step^k = lo[k & 7] hi[k >> 3]
+            const cpx<T> base = twiddle(twlo, twhi, a.tws, (int64_t)((pp * jm) << lts));
+            const cpx<T> st1 = twiddle(twlo, twhi, a.tws, (int64_t)((64 * jm) << lts));
+            cpx<T> lo[8], hi[8];
+            lo[0] = mk<T>(1.f, 0.f);
+            lo[1] = st1;
+#pragma unroll
+            for (int q = 2; q < 8; ++q) lo[q] = mul(lo[q - 1], st1);
+            const cpx<T> s8 = mul(lo[7], st1);
+            hi[0] = mk<T>(1.f, 0.f);
+            hi[1] = s8;
+#pragma unroll
+            for (int q = 2; q < 8; ++q) hi[q] = mul(hi[q - 1], s8);
+#pragma unroll
+            for (int k = 0; k < QA; ++k) {
+                cpx<T> w = base;
+                if ((k & 7) != 0) w = mul(w, lo[k & 7]);
+                if ((k >> 3) != 0) w = mul(w, hi[k >> 3]);
+                v[k] = mul(v[k], w);
+            }
+        }
+        SmallDFT<T, QA>::run(v);
+#pragma unroll
+        for (int k = 0; k < QA; ++k) s[swz((pp * QA + k) * J + jj)] = v[k];
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // ---- stage B: radix 64, rows pp + k QA (in place)
+    {
+        const int jj = threadIdx.x % J, pp = threadIdx.x / J;  // pp < QA
+        cpx<T> v[64];
+#pragma unroll
+        for (int k = 0; k < 64; ++k) v[k] = s[swz((pp + k * QA) * J + jj)];
+        if constexpr (QA > 1) {
+#pragma unroll
+            for (int k = 1; k < 64; ++k) v[k] = mul(v[k], st[(k - 1) * QA + pp]);
+        }
+        SmallDFT<T, 64>::run(v);
+#pragma unroll
+        for (int k = 0; k < 64; ++k) s[swz((pp + k * QA) * J + jj)] = v[k];
+    }
+    __syncthreads();
+    const int logNs = a.logNs;
+    if (!a.last) {
+        cpx<T>* gout = out + (int64_t)g * M;
+        const int LOGJn = a.logJn, Jn = 1 << a.logJn;
+        const int logBlk = a.logRn + a.logJn;
+        if (logNs == 0 && a.logM - a.logRn == LOGR) {
+            for (int e = threadIdx.x; e < E; e += NT) {
+                const int kl = e & (Jn - 1);
+                const int jj = (e >> LOGJn) & (J - 1);
+                const int kb = e >> (LOGJn + LOGJ);
+                const int k = (kb << LOGJn) + kl;
+                gout[(kb << logBlk) + ((j0 + jj) << LOGJn) + kl] = s[swz(k * J + jj)];
+            }
+        } else {
+            const int logSn = a.logM - a.logRn;
+            for (int e = threadIdx.x; e < E; e += NT) {
+                const int kl = e & (Jn - 1);
+                const int jj = (e >> LOGJn) & (J - 1);
+                const int kb = e >> (LOGJn + LOGJ);
+                const int k = (kb << LOGJn) + kl;
+                const int j = j0 + jj;
+                const int i = ((j >> logNs) << (logNs + LOGR)) + (j & ((1 << logNs) - 1)) + (k << logNs);
+                const int jn = i & ((1 << logSn) - 1), rn = i >> logSn;
+                gout[((jn >> LOGJn) << logBlk) + (rn << LOGJn) + (jn & (Jn - 1))] = s[swz(k * J + jj)];
+            }
+        }
+    } else {
+        cpx<T>* spec = out + (int64_t)g * a.N;
+        for (int e = threadIdx.x; e < E; e += NT) {
+            const int k = e >> LOGJ, jj = e & (J - 1);
+            const int o = j0 + jj + (k << logNs);
+            const int m = (o < M / 2) ? o : o - M;
+            const int jf = m + a.hN;
+            if (jf >= 0 && jf < a.N) spec[jf] = s[swz(e)];
+        }
+    }
+}
+
 cudaError_t init_twiddles(fc2_plan_s* p, cudaStream_t s) {
     int sh = (p->logM + 1) / 2;
     int64_t nlo = 1ll << sh, nhi = p->M >> sh;
@@ -399,6 +549,15 @@ cudaError_t init_twiddles(fc2_plan_s* p, cudaStream_t s) {
             if (p->fp64) k_init_stage_tw<double><<<b2, 256, 0, s>>>((cpx<double>*)p->d_twst + off, ps.logR);
             else k_init_stage_tw<float><<<b2, 256, 0, s>>>((cpx<float>*)p->d_twst + off, ps.logR);
         }
+        off += n + 16;
+    }
+    // tables of the two-stage radix-64 float kernel (stage-B twiddles)
+    for (auto& ps : p->passes) {
+        if (p->fp64 || ps.logR < 10 || ps.logR > 12 || p->tw64_off[ps.logR] != 0) continue;
+        p->tw64_off[ps.logR] = off;
+        const int n = 63 * (1 << (ps.logR - 6));
+        k_init_tw64<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((cpx<float>*)p->d_twst + off,
+                                                                      ps.logR);
         off += n + 16;
     }
     if (p->fp64)
@@ -459,9 +618,31 @@ static cudaError_t run_pass(fc2_plan_s* p, const void* in, void* out, const Pass
     return cudaGetLastError();
 }
 
+template <int LOGR>
+static cudaError_t run_pass64(fc2_plan_s* p, const void* in, void* out, const PassArgs& a,
+                              cudaStream_t s) {
+    constexpr int LOGJ = 13 - LOGR, E = 1 << 13;
+    const int64_t S = p->M >> LOGR;
+    const size_t smem = (size_t)(E + 63 * (1 << (LOGR - 6))) * sizeof(cpx<float>);
+    auto kern = k_fft_pass64<LOGR, LOGJ>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_done = true;
+    }
+    dim3 grid((unsigned)(S >> LOGJ), (unsigned)p->G);
+    kern<<<grid, 128, smem, s>>>((const cpx<float>*)in, (cpx<float>*)out, a, p->d_L,
+                                 (const cpx<float>*)p->d_twlo, (const cpx<float>*)p->d_twhi,
+                                 (const cpx<float>*)p->d_twst + p->tw64_off[LOGR]);
+    return cudaGetLastError();
+}
+
 template <typename T, int LOGR>
 static cudaError_t run_radix(fc2_plan_s* p, const void* in, void* out, const PassArgs& a,
                              cudaStream_t s) {
+    if constexpr (sizeof(T) == 4 && LOGR >= 10 && LOGR <= 12) {
+        if (LOGR != p->logM && p->use_r64) return run_pass64<LOGR>(p, in, out, a, s);
+    }
     if (LOGR == p->logM) {
         constexpr int NT = (1 << LOGR) / 16 < 32 ? 32 : (1 << LOGR) / 16;
         if constexpr ((1 << LOGR) % (16 * NT) == 0 || (1 << LOGR) >= 16 * NT)
