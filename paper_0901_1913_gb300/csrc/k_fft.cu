@@ -388,9 +388,18 @@ __global__ void __launch_bounds__(NT, 2) k_fft_pass(const cpx<T>* __restrict__ i
 // the inter-pass twiddle and writes to shared memory; stage B reads, applies
 // the stage twiddle w_R^{k pp}, and writes its outputs back to the same slots;
 // then the tile is stored as by k_fft_pass.  Shared memory holds one tile,
-// swizzled (e ^ ((e >> 7) & 31)) so both stages' access patterns are free of
-// bank conflicts, plus the stage-B twiddles.
-FC2_HD int swz(int e) { return e ^ ((e >> 7) & 31); }
+// swizzled (bits [LOGJ, LOGJ + 3) of the element index XORed with bits
+// [7, 10)) so both stages' access patterns reach the minimum number of
+// shared-memory wavefronts, plus the stage-B twiddles.  The kernel is
+// persistent: each CTA walks tiles with a stride of the grid size and asks L2
+// to prefetch its next tile while it computes the current one.
+template <int LOGJ>
+FC2_HD int swz(int e) { return e ^ (((e >> 7) & 7) << LOGJ); }
+
+FC2_D void prefetch_l2_bulk(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+FC2_D void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
 
 template <typename T>
 __global__ void k_init_tw64(cpx<T>* tw, int LOGR) {
@@ -409,7 +418,8 @@ __global__ void __launch_bounds__(128, 2) k_fft_pass64(const cpx<float>* __restr
                                                        const int64_t* __restrict__ Lg,
                                                        const cpx<float>* __restrict__ twlo,
                                                        const cpx<float>* __restrict__ twhi,
-                                                       const cpx<float>* __restrict__ tw64) {
+                                                       const cpx<float>* __restrict__ tw64,
+                                                       int G) {
     using T = float;
     constexpr int R = 1 << LOGR, J = 1 << LOGJ, E = R * J, NT = 128;
     constexpr int QAB = LOGR - 6, QA = 1 << QAB;
@@ -420,114 +430,142 @@ __global__ void __launch_bounds__(128, 2) k_fft_pass64(const cpx<float>* __restr
     cpx<T>* st = s + E;
     const int M = 1 << a.logM;
     const int S = M >> LOGR;
-    const int g = blockIdx.y;
-    const int j0 = blockIdx.x * J;
-    const cpx<T>* gin = in + (int64_t)g * M;
-    for (int i = threadIdx.x; i < 63 * QA; i += NT) cp_elem(&st[i], &tw64[i]);
-    int rows = R;
-    if (a.first) {
-        const int L = (int)Lg[g];
-        rows = (L + S - 1) / S;
-        if (rows > R) rows = R;
-    }
+    const int tiles_x = S >> LOGJ;
+    const int ntiles = tiles_x * G;
     const int nsg_mask = (1 << a.logNs) - 1;
     const int lts = a.logM - a.logNs - LOGR;
-    // ---- stage A: radix QA, rows pp + k 64 -> rows pp QA + k
-#pragma unroll
-    for (int b = 0; b < PERA; ++b) {
-        const int bi = threadIdx.x + b * NT;
-        const int jj = bi % J, pp = bi / J;  // pp < 64
-        cpx<T> v[QA];
-        if (a.first) {
-#pragma unroll
-            for (int k = 0; k < QA; ++k) {
-                const int r = pp + k * 64;
-                v[k] = (r < rows) ? gin[j0 + jj + r * S] : mk<T>(0.f, 0.f);
-            }
-        } else {
-            const cpx<T>* src = gin + (int64_t)blockIdx.x * E;
-#pragma unroll
-            for (int k = 0; k < QA; ++k) v[k] = src[(pp + k * 64) * J + jj];
-        }
-        const int jm = (j0 + jj) & nsg_mask;
-        if (a.logNs > 0 && jm != 0) {
-            // w_M^{(pp + 64 k) jm 2^lts} = base * step^k, step^k = lo[k & 7] hi[k >> 3]
-            const cpx<T> base = twiddle(twlo, twhi, a.tws, (int64_t)((pp * jm) << lts));
-            const cpx<T> st1 = twiddle(twlo, twhi, a.tws, (int64_t)((64 * jm) << lts));
-            cpx<T> lo[8], hi[8];
-            lo[0] = mk<T>(1.f, 0.f);
-            lo[1] = st1;
-#pragma unroll
-            for (int q = 2; q < 8; ++q) lo[q] = mul(lo[q - 1], st1);
-            const cpx<T> s8 = mul(lo[7], st1);
-            hi[0] = mk<T>(1.f, 0.f);
-            hi[1] = s8;
-#pragma unroll
-            for (int q = 2; q < 8; ++q) hi[q] = mul(hi[q - 1], s8);
-#pragma unroll
-            for (int k = 0; k < QA; ++k) {
-                cpx<T> w = base;
-                if ((k & 7) != 0) w = mul(w, lo[k & 7]);
-                if ((k >> 3) != 0) w = mul(w, hi[k >> 3]);
-                v[k] = mul(v[k], w);
-            }
-        }
-        SmallDFT<T, QA>::run(v);
-#pragma unroll
-        for (int k = 0; k < QA; ++k) s[swz((pp * QA + k) * J + jj)] = v[k];
-    }
+    for (int i = threadIdx.x; i < 63 * QA; i += NT) cp_elem(&st[i], &tw64[i]);
     cp_async_wait_all();
-    __syncthreads();
-    // ---- stage B: radix 64, rows pp + k QA (in place)
-    {
-        const int jj = threadIdx.x % J, pp = threadIdx.x / J;  // pp < QA
-        cpx<T> v[64];
-#pragma unroll
-        for (int k = 0; k < 64; ++k) v[k] = s[swz((pp + k * QA) * J + jj)];
-        if constexpr (QA > 1) {
-#pragma unroll
-            for (int k = 1; k < 64; ++k) v[k] = mul(v[k], st[(k - 1) * QA + pp]);
+    auto rows_of = [&](int g) {
+        int rows = R;
+        if (a.first) {
+            const int L = (int)Lg[g];
+            rows = (L + S - 1) / S;
+            if (rows > R) rows = R;
         }
-        SmallDFT<T, 64>::run(v);
+        return rows;
+    };
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int g = tile / tiles_x;
+        const int bx = tile - g * tiles_x;
+        const int j0 = bx * J;
+        const cpx<T>* gin = in + (int64_t)g * M;
+        // ask L2 for the tile this CTA handles next
+        {
+            const int tn = tile + gridDim.x;
+            if (tn < ntiles) {
+                const int gn = tn / tiles_x, bn = tn - gn * tiles_x;
+                const cpx<T>* ginn = in + (int64_t)gn * M;
+                if (!a.first) {
+                    constexpr int CH = 4096;  // bytes per prefetch request
+                    constexpr int NCH = E * (int)sizeof(cpx<T>) / CH;
+                    const char* base = reinterpret_cast<const char*>(ginn + (int64_t)bn * E);
+                    if (threadIdx.x < NCH) prefetch_l2_bulk(base + threadIdx.x * CH, CH);
+                } else {
+                    const int rn = rows_of(gn);
+                    for (int r = threadIdx.x; r < rn; r += NT) prefetch_l2(ginn + bn * J + r * S);
+                }
+            }
+        }
+        const int rows = rows_of(g);
+        // ---- stage A: radix QA, rows pp + k 64 -> rows pp QA + k
 #pragma unroll
-        for (int k = 0; k < 64; ++k) s[swz((pp + k * QA) * J + jj)] = v[k];
-    }
-    __syncthreads();
-    const int logNs = a.logNs;
-    if (!a.last) {
-        cpx<T>* gout = out + (int64_t)g * M;
-        const int LOGJn = a.logJn, Jn = 1 << a.logJn;
-        const int logBlk = a.logRn + a.logJn;
-        if (logNs == 0 && a.logM - a.logRn == LOGR) {
-            for (int e = threadIdx.x; e < E; e += NT) {
-                const int kl = e & (Jn - 1);
-                const int jj = (e >> LOGJn) & (J - 1);
-                const int kb = e >> (LOGJn + LOGJ);
-                const int k = (kb << LOGJn) + kl;
-                gout[(kb << logBlk) + ((j0 + jj) << LOGJn) + kl] = s[swz(k * J + jj)];
+        for (int b = 0; b < PERA; ++b) {
+            const int bi = threadIdx.x + b * NT;
+            const int jj = bi % J, pp = bi / J;  // pp < 64
+            cpx<T> v[QA];
+            if (a.first) {
+#pragma unroll
+                for (int k = 0; k < QA; ++k) {
+                    const int r = pp + k * 64;
+                    v[k] = (r < rows) ? gin[j0 + jj + r * S] : mk<T>(0.f, 0.f);
+                }
+            } else {
+                const cpx<T>* src = gin + (int64_t)bx * E;
+#pragma unroll
+                for (int k = 0; k < QA; ++k) v[k] = src[(pp + k * 64) * J + jj];
+            }
+            const int jm = (j0 + jj) & nsg_mask;
+            if (a.logNs > 0 && jm != 0) {
+                // w_M^{(pp + 64 k) jm 2^lts} = base * step^k, step^k = lo[k & 7] hi[k >> 3]
+                const cpx<T> base = twiddle(twlo, twhi, a.tws, (int64_t)((pp * jm) << lts));
+                const cpx<T> st1 = twiddle(twlo, twhi, a.tws, (int64_t)((64 * jm) << lts));
+                cpx<T> lo[8], hi[8];
+                lo[0] = mk<T>(1.f, 0.f);
+                lo[1] = st1;
+#pragma unroll
+                for (int q = 2; q < 8; ++q) lo[q] = mul(lo[q - 1], st1);
+                const cpx<T> s8 = mul(lo[7], st1);
+                hi[0] = mk<T>(1.f, 0.f);
+                hi[1] = s8;
+#pragma unroll
+                for (int q = 2; q < 8; ++q) hi[q] = mul(hi[q - 1], s8);
+#pragma unroll
+                for (int k = 0; k < QA; ++k) {
+                    cpx<T> w = base;
+                    if ((k & 7) != 0) w = mul(w, lo[k & 7]);
+                    if ((k >> 3) != 0) w = mul(w, hi[k >> 3]);
+                    v[k] = mul(v[k], w);
+                }
+            }
+            SmallDFT<T, QA>::run(v);
+#pragma unroll
+            for (int k = 0; k < QA; ++k) s[swz<LOGJ>((pp * QA + k) * J + jj)] = v[k];
+        }
+        __syncthreads();
+        // ---- stage B: radix 64, rows pp + k QA (in place)
+        {
+            const int jj = threadIdx.x % J, pp = threadIdx.x / J;  // pp < QA
+            cpx<T> v[64];
+#pragma unroll
+            for (int k = 0; k < 64; ++k) v[k] = s[swz<LOGJ>((pp + k * QA) * J + jj)];
+            if constexpr (QA > 1) {
+#pragma unroll
+                for (int k = 1; k < 64; ++k) v[k] = mul(v[k], st[(k - 1) * QA + pp]);
+            }
+            SmallDFT<T, 64>::run(v);
+#pragma unroll
+            for (int k = 0; k < 64; ++k) s[swz<LOGJ>((pp + k * QA) * J + jj)] = v[k];
+        }
+        __syncthreads();
+        const int logNs = a.logNs;
+        if (!a.last) {
+            cpx<T>* gout = out + (int64_t)g * M;
+            const int LOGJn = a.logJn, Jn = 1 << a.logJn;
+            const int logBlk = a.logRn + a.logJn;
+            if (logNs == 0 && a.logM - a.logRn == LOGR) {
+                for (int e = threadIdx.x; e < E; e += NT) {
+                    const int kl = e & (Jn - 1);
+                    const int jj = (e >> LOGJn) & (J - 1);
+                    const int kb = e >> (LOGJn + LOGJ);
+                    const int k = (kb << LOGJn) + kl;
+                    gout[(kb << logBlk) + ((j0 + jj) << LOGJn) + kl] = s[swz<LOGJ>(k * J + jj)];
+                }
+            } else {
+                const int logSn = a.logM - a.logRn;
+                for (int e = threadIdx.x; e < E; e += NT) {
+                    const int kl = e & (Jn - 1);
+                    const int jj = (e >> LOGJn) & (J - 1);
+                    const int kb = e >> (LOGJn + LOGJ);
+                    const int k = (kb << LOGJn) + kl;
+                    const int j = j0 + jj;
+                    const int i = ((j >> logNs) << (logNs + LOGR)) + (j & ((1 << logNs) - 1)) + (k << logNs);
+                    const int jn = i & ((1 << logSn) - 1), rn = i >> logSn;
+                    gout[((jn >> LOGJn) << logBlk) + (rn << LOGJn) + (jn & (Jn - 1))] =
+                        s[swz<LOGJ>(k * J + jj)];
+                }
             }
         } else {
-            const int logSn = a.logM - a.logRn;
+            cpx<T>* spec = out + (int64_t)g * a.N;
             for (int e = threadIdx.x; e < E; e += NT) {
-                const int kl = e & (Jn - 1);
-                const int jj = (e >> LOGJn) & (J - 1);
-                const int kb = e >> (LOGJn + LOGJ);
-                const int k = (kb << LOGJn) + kl;
-                const int j = j0 + jj;
-                const int i = ((j >> logNs) << (logNs + LOGR)) + (j & ((1 << logNs) - 1)) + (k << logNs);
-                const int jn = i & ((1 << logSn) - 1), rn = i >> logSn;
-                gout[((jn >> LOGJn) << logBlk) + (rn << LOGJn) + (jn & (Jn - 1))] = s[swz(k * J + jj)];
+                const int k = e >> LOGJ, jj = e & (J - 1);
+                const int o = j0 + jj + (k << logNs);
+                const int m = (o < M / 2) ? o : o - M;
+                const int jf = m + a.hN;
+                if (jf >= 0 && jf < a.N) spec[jf] = s[swz<LOGJ>(e)];
             }
         }
-    } else {
-        cpx<T>* spec = out + (int64_t)g * a.N;
-        for (int e = threadIdx.x; e < E; e += NT) {
-            const int k = e >> LOGJ, jj = e & (J - 1);
-            const int o = j0 + jj + (k << logNs);
-            const int m = (o < M / 2) ? o : o - M;
-            const int jf = m + a.hN;
-            if (jf >= 0 && jf < a.N) spec[jf] = s[swz(e)];
-        }
+        __syncthreads();  // the tile buffer is reused by the next iteration
     }
 }
 
@@ -630,10 +668,18 @@ static cudaError_t run_pass64(fc2_plan_s* p, const void* in, void* out, const Pa
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_done = true;
     }
-    dim3 grid((unsigned)(S >> LOGJ), (unsigned)p->G);
-    kern<<<grid, 128, smem, s>>>((const cpx<float>*)in, (cpx<float>*)out, a, p->d_L,
-                                 (const cpx<float>*)p->d_twlo, (const cpx<float>*)p->d_twhi,
-                                 (const cpx<float>*)p->d_twst + p->tw64_off[LOGR]);
+    const int64_t ntiles = (S >> LOGJ) * (int64_t)p->G;
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 152;
+    }
+    const unsigned blocks = (unsigned)std::min<int64_t>(ntiles, 2 * (int64_t)nsm);
+    kern<<<blocks, 128, smem, s>>>((const cpx<float>*)in, (cpx<float>*)out, a, p->d_L,
+                                   (const cpx<float>*)p->d_twlo, (const cpx<float>*)p->d_twhi,
+                                   (const cpx<float>*)p->d_twst + p->tw64_off[LOGR], p->G);
     return cudaGetLastError();
 }
 
