@@ -322,10 +322,27 @@ def run_gpu(args):
         "stage_ms": {k: round(v, 4) for k, v in zip(["spread", "fft", "assemble", "fixup", "peaks"],
                                                     stage_ms)},
         "bins_resolved_double": counts[0], "bins_exact_sums": counts[1],
-        "bins_exact_double": counts[2],
+        "bins_exact_double_float": counts[2], "bins_exact_double": counts[3],
         "parity": parity,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_profile(args):
+    """Only `warmup + steps` mixed executes of the workload, optionally with
+    fewer harmonics (--H): the command profiled by ncu.  Prints one short line
+    that is not a benchmark result."""
+    import torch
+    from paper_0901_1913_gb300 import _fc2, synth
+    c = synth.config2(seed=2, H=args.H or 6)
+    dev = torch.device("cuda", 0)
+    out = torch.empty((c.H, c.N), dtype=torch.float64, device=dev)
+    with _fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed") as p:
+        for _ in range(args.warmup + args.steps):
+            _, best, _, _ = p.execute(out, want_records=True)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": True, "H": c.H, "N": c.N, "n": c.n,
+                          "best_j": int(best[-1]["j"]), "counts": list(p.counts)}), flush=True)
 
 
 def main():
@@ -339,8 +356,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-bins", type=int, default=48)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only run the mixed executes (for ncu); no benchmark line")
+    ap.add_argument("--H", type=int, default=0, help="harmonics of the --profile run (default 6)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

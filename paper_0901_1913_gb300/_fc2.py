@@ -100,6 +100,8 @@ def load():
         lib.fc2_stage_timing.restype = i32
         lib.fc2_stage_times.argtypes = [_P, _P, _P, _P]
         lib.fc2_stage_times.restype = i32
+        lib.fc2_debug_exact_bins.argtypes = [_P, _P, i64, i32, _P]
+        lib.fc2_debug_exact_bins.restype = i32
         lib.fc2_debug_t0.argtypes = [_P]
         lib.fc2_debug_t0.restype = dbl
         _lib = lib
@@ -207,10 +209,19 @@ class Plan:
     @property
     def counts(self):
         """(bins re-solved in double, bins recomputed from exact sums, of which
-        all-double) in the last execute."""
-        c = np.zeros(3, dtype=np.int64)
+        double-float, of which all-double) in the last execute."""
+        c = np.zeros(4, dtype=np.int64)
         load().fc2_debug_counts(self.h, c.ctypes.data)
         return tuple(int(v) for v in c)
+
+    def exact_bins(self, bins, tier):
+        """Delta chi^2 [H, len(bins)] at the given bins from the exact sums of one
+        tier (1 float, 2 double-float, 3 double)."""
+        b = np.ascontiguousarray(bins, dtype=np.int64)
+        out = np.empty((self.H, b.size))
+        _check(load().fc2_debug_exact_bins(self.h, b.ctypes.data, b.size, int(tier),
+                                           out.ctypes.data), "exact_bins")
+        return out
 
     def spectra(self):
         G = 3 * self.H

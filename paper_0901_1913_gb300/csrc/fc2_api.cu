@@ -59,6 +59,7 @@ void free_plan_memory(fc2_plan_s* p) {
     dfree(p->d_dchi2, s); dfree(p->d_flag_list, s); dfree(p->d_flag_count, s);
     dfree(p->d_L, s); dfree(p->d_red, s); dfree(p->d_best, s); dfree(p->d_part, s);
     dfree(p->d_phA, s); dfree(p->d_phB, s); dfree(p->d_wq32, s); dfree(p->d_wp32, s);
+    dfree(p->d_dftab, s);
 }
 
 }  // namespace
@@ -168,7 +169,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         g.ok(dalloc(&p->d_twhi, (size_t)(M >> ((p->logM + 1) / 2)) * csz, s)) &&
         g.ok(dalloc(&p->d_twst, (size_t)(8 * 4096 + 256) * csz, s)) &&
         g.ok(dalloc(&p->d_dchi2, (size_t)H * N * 8, s)) &&
-        g.ok(dalloc(&p->d_flag_list, (size_t)N * 4 * 2, s)) &&
+        g.ok(dalloc(&p->d_flag_list, (size_t)N * 4 * 3, s)) &&
         g.ok(dalloc(&p->d_flag_count, 16, s)) && g.ok(dalloc(&p->d_L, (size_t)G * 8, s)) &&
         g.ok(dalloc(&p->d_red, red_b, s)) &&
         g.ok(dalloc(&p->d_best, (size_t)(H + p->top_k) * sizeof(fc2_best), s));
@@ -176,7 +177,8 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     p->exact_cap = std::max<int64_t>(2048, H + p->top_k);
     g.ok(dalloc(&p->d_part, exact_scratch_bytes(n, H, p->exact_cap), s)) &&
         g.ok(dalloc(&p->d_phA, (size_t)n * 8, s)) && g.ok(dalloc(&p->d_phB, (size_t)n * 8, s)) &&
-        g.ok(dalloc(&p->d_wq32, (size_t)n * 4, s)) && g.ok(dalloc(&p->d_wp32, (size_t)n * 4, s));
+        g.ok(dalloc(&p->d_wq32, (size_t)n * 8, s)) && g.ok(dalloc(&p->d_wp32, (size_t)n * 8, s)) &&
+        g.ok(dalloc(&p->d_dftab, 512 * 16, s));
     if (g.e != cudaSuccess) {
         fc2_status st = map_err(g.e);
         free_plan_memory(p);
@@ -306,8 +308,8 @@ static fc2_status run_pipeline(fc2_plan_s* p) {
     g.ok(launch_peaks(p, s));
     rec(p, 5);
     const int64_t cap = p->exact_cap;
-    const int64_t r1 = (nfix + cap - 1) / cap, r2 = (p->last_exact2_count + cap - 1) / cap;
-    p->launches = launches_front(p) + 2 * (r1 + r2) + 4;
+    const int64_t r1 = (nfix + cap - 1) / cap;
+    p->launches = launches_front(p) + 6 * r1 + 4;
     return map_err(g.e);
 }
 
@@ -341,8 +343,12 @@ fc2_status fc2_execute(fc2_plan p, double* dchi2, fc2_best* best, fc2_best* peak
         g.ok(cudaMemcpyAsync(recs.data(), p->d_best, recs.size() * sizeof(fc2_best),
                              cudaMemcpyDeviceToHost, s));
     g.ok(cudaMemcpyAsync(&status, p->d_status, 4, cudaMemcpyDeviceToHost, s));
+    int32_t tiers[2] = {0, 0};
+    g.ok(cudaMemcpyAsync(tiers, p->d_flag_count + 2, 8, cudaMemcpyDeviceToHost, s));
     g.ok(cudaStreamSynchronize(s));
     if (g.e != cudaSuccess) return map_err(g.e);
+    p->last_exact2_count = p->last_flag_count > 0 ? tiers[0] : 0;
+    p->last_exact3_count = p->last_flag_count > 0 ? tiers[1] : 0;
     if (status != 0) return (fc2_status)status;
     if (best) memcpy(best, recs.data(), sizeof(fc2_best) * p->H);
     if (peaks) memcpy(peaks, recs.data() + p->H, sizeof(fc2_best) * p->top_k);
@@ -409,12 +415,14 @@ int64_t fc2_debug_flag_count(fc2_plan p) { return p ? p->last_flag_count : -1; }
 
 /* Counts of the last execute: [0] bins re-solved in double (mixed path),
  * [1] bins recomputed from exact sums (tier 1), [2] of those, bins that
- * needed all-double sums (tier 2). */
-void fc2_debug_counts(fc2_plan p, int64_t* out3) {
-    if (!p || !out3) return;
-    out3[0] = p->last_resolve_count;
-    out3[1] = p->last_flag_count;
-    out3[2] = p->last_exact2_count;
+ * needed double-float sums (tier 2), [3] of those, bins that needed all-double
+ * sums (tier 3). */
+void fc2_debug_counts(fc2_plan p, int64_t* out4) {
+    if (!p || !out4) return;
+    out4[0] = p->last_resolve_count;
+    out4[1] = p->last_flag_count;
+    out4[2] = p->last_exact2_count;
+    out4[3] = p->last_exact3_count;
 }
 
 fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im) {
@@ -442,6 +450,30 @@ fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im) {
 }
 
 double fc2_debug_t0(fc2_plan p) { return p ? p->scal[SC_T0] : 0.0; }
+
+/* Delta chi^2 [H][nb] at the given bins from the exact sums of one tier
+ * (1 float, 2 double-float, 3 double), for tests of each tier.  Overwrites
+ * those bins of the plan's internal output.  nb <= min(N, exact-round size). */
+fc2_status fc2_debug_exact_bins(fc2_plan p, const int64_t* bins, int64_t nb, int tier,
+                                double* out) {
+    if (!p || !bins || !out || nb < 1 || nb > p->N || nb > p->exact_cap || tier < 1 || tier > 3)
+        return FC2_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < nb; ++i)
+        if (bins[i] < 0 || bins[i] >= p->N) return FC2_ERR_INVALID_ARG;
+    if (cudaSetDevice(p->device) != cudaSuccess) return FC2_ERR_CUDA;
+    cudaStream_t s = p->stream;
+    std::vector<int32_t> b32(bins, bins + nb);
+    if (cudaMemcpyAsync(p->d_flag_list, b32.data(), (size_t)nb * 4, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return FC2_ERR_CUDA;
+    if (launch_exact_bins(p, nb, tier, s) != cudaSuccess) return FC2_ERR_CUDA;
+    for (int h = 0; h < p->H; ++h)
+        for (int64_t i = 0; i < nb; ++i)
+            if (cudaMemcpy(out + (size_t)h * nb + i, p->d_dchi2 + (size_t)h * p->N + bins[i], 8,
+                           cudaMemcpyDeviceToHost) != cudaSuccess)
+                return FC2_ERR_CUDA;
+    return FC2_OK;
+}
 
 /* Kernels launched by the last fc2_execute_batched call of this process. */
 int64_t fc2_debug_batch_launches(void) { return g_last_batch_launches; }

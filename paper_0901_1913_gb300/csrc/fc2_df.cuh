@@ -1,0 +1,110 @@
+// fc2_df.cuh -- double-float ("float-float") arithmetic for the exact sums.
+//
+// A value is an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2,
+// which carries about 48 significant bits.  The error-free transformations are
+// Knuth's two-sum and the fused multiply-add product error (Dekker, Numer.
+// Math. 18 (1971) 224; Joldes, Muller & Popescu, ACM TOMS 44 (2017) 48).  The
+// float pipes of this part are some sixty times wider than its double pipe,
+// so sums that need more than float but less than double precision are
+// cheaper this way.  Not part of the public ABI.
+#pragma once
+#include "fc2_common.cuh"
+
+namespace fc2 {
+
+struct dfl {
+    float h, l;
+};
+struct dfc {
+    dfl re, im;
+};
+
+// s + e = a + b exactly (any magnitudes)
+FC2_D dfl df_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return dfl{s, (a - (s - bb)) + (b - bb)};
+}
+// s + e = a + b exactly, for |a| >= |b| (or a == 0)
+FC2_D dfl df_fast_sum(float a, float b) {
+    const float s = a + b;
+    return dfl{s, b - (s - a)};
+}
+// a * b, relative error ~2^-47
+FC2_D dfl df_mul(dfl a, dfl b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return df_fast_sum(p, e);
+}
+
+// a * b for double-float complex numbers of modulus about one; each component
+// is formed as one two-sum of the leading products plus the small terms, so
+// its absolute error is ~2^-47 |a| |b|.
+FC2_D dfc dfc_mul(const dfc& a, const dfc& b) {
+    dfc r;
+    {
+        const float p1 = a.re.h * b.re.h, p2 = a.im.h * b.im.h;
+        const float e1 = fmaf(a.re.h, b.re.h, -p1), e2 = fmaf(a.im.h, b.im.h, -p2);
+        const dfl s = df_two_sum(p1, -p2);
+        float lo = s.l + (e1 - e2);
+        lo = fmaf(a.re.h, b.re.l, lo);
+        lo = fmaf(a.re.l, b.re.h, lo);
+        lo = fmaf(-a.im.h, b.im.l, lo);
+        lo = fmaf(-a.im.l, b.im.h, lo);
+        r.re = df_two_sum(s.h, lo);
+    }
+    {
+        const float p1 = a.re.h * b.im.h, p2 = a.im.h * b.re.h;
+        const float e1 = fmaf(a.re.h, b.im.h, -p1), e2 = fmaf(a.im.h, b.re.h, -p2);
+        const dfl s = df_two_sum(p1, p2);
+        float lo = s.l + (e1 + e2);
+        lo = fmaf(a.re.h, b.im.l, lo);
+        lo = fmaf(a.re.l, b.im.h, lo);
+        lo = fmaf(a.im.h, b.re.l, lo);
+        lo = fmaf(a.im.l, b.re.h, lo);
+        r.im = df_two_sum(s.h, lo);
+    }
+    return r;
+}
+
+// Accumulator acc += w * z (w, z double-float reals); the running sum keeps
+// its rounding errors in acc.l.
+FC2_D void df_acc_mul(dfl& acc, dfl w, dfl z) {
+    const float p = w.h * z.h;
+    float e = fmaf(w.h, z.h, -p);
+    e = fmaf(w.h, z.l, e);
+    e = fmaf(w.l, z.h, e);
+    const dfl s = df_two_sum(acc.h, p);
+    acc.h = s.h;
+    acc.l += s.l + e;
+}
+
+FC2_D dfl df_from_double(double v) {
+    const float h = (float)v;
+    return dfl{h, (float)(v - (double)h)};
+}
+
+// e^{2 pi i u 2^-64} for a 64-bit phase u, to ~2^-46: the top 16 bits select
+// two table factors e^{2 pi i a / 256} and e^{2 pi i b / 65536} (double-float,
+// t1[a] and t2[b]); the remaining 48 bits give theta = 2 pi delta < 1e-4 and
+// e^{i theta} = 1 - theta^2/2 + i (theta - theta^3/6) (the next terms are
+// below 1e-17).
+FC2_D dfc df_phasor(uint64_t u, const dfc* t1, const dfc* t2) {
+    const int a = (int)(u >> 56), b = (int)((u >> 48) & 255u);
+    const uint64_t r = u & ((1ull << 48) - 1);
+    const float rh = (float)(uint32_t)(r >> 24), rl = (float)(uint32_t)(r & 0xffffffu);
+    const dfl d = df_two_sum(rh * 9.094947017729282e-13f, rl * 5.421010862427522e-20f);  // 2^-40, 2^-64
+    const dfl th = df_mul(d, dfl{6.28318548202514648f, -1.74845553146951525e-07f});  // 2 pi
+    const dfl t2s = df_mul(th, th);
+    dfc e;
+    e.re = df_two_sum(1.0f, -0.5f * t2s.h);
+    e.re.l -= 0.5f * t2s.l;
+    e.re = df_fast_sum(e.re.h, e.re.l);
+    const float t3 = th.h * th.h * th.h * (1.0f / 6.0f);
+    e.im = df_fast_sum(th.h, th.l - t3);
+    return dfc_mul(dfc_mul(t1[a], t2[b]), e);
+}
+
+}  // namespace fc2

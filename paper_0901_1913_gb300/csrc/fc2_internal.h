@@ -103,8 +103,9 @@ struct fc2_plan_s {
     double* d_part = nullptr;  // exact-sum partials [exact_cap][nch][6H]
     uint64_t* d_phA = nullptr; // fixed-point phases frac(f_min tau) 2^64 [n]
     uint64_t* d_phB = nullptr; // fixed-point phases frac(df tau) 2^64 [n]
-    float* d_wq32 = nullptr;   // w as float [n]
-    float* d_wp32 = nullptr;   // w (x - xbar) as float [n]
+    float* d_wq32 = nullptr;   // w as float [n], then the low parts w - (float)w [n]
+    float* d_wp32 = nullptr;   // w (x - xbar) likewise [2n]
+    void* d_dftab = nullptr;   // double-float phasor tables of the tier-2 sums [512]
     int64_t exact_cap = 0;
     void* d_red = nullptr;     // reduction scratch
     size_t red_bytes = 0;
@@ -114,6 +115,7 @@ struct fc2_plan_s {
     std::vector<fc2::FftPass> passes;
     int64_t last_flag_count = 0;
     int64_t last_exact2_count = 0;
+    int64_t last_exact3_count = 0;
     int64_t last_resolve_count = 0;
     bool has_perm = false;
     // stage timing (events recorded around each stage while enabled)
@@ -153,6 +155,7 @@ cudaError_t launch_fft(fc2_plan_s* p, cudaStream_t s);
 // k_solve.cu
 cudaError_t launch_assemble(fc2_plan_s* p, cudaStream_t s);
 cudaError_t launch_fixup(fc2_plan_s* p, int64_t count, cudaStream_t s);
+cudaError_t launch_exact_bins(fc2_plan_s* p, int64_t nb, int tier, cudaStream_t s);
 cudaError_t launch_peaks(fc2_plan_s* p, cudaStream_t s);
 size_t peaks_scratch_bytes(int64_t N, int H, int K);
 size_t exact_scratch_bytes(int64_t n, int H, int64_t cap);

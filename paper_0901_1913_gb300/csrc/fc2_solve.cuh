@@ -159,16 +159,31 @@ FC2_D void exact_sys_from_sums(const double* acc, int H, const double* __restric
 }
 
 // Peak candidates ordered by (value desc, index asc).
-struct Cand { double v; int64_t j; };
-FC2_D bool better(double v1, int64_t j1, double v2, int64_t j2) {
-    return v1 > v2 || (v1 == v2 && j1 < j2);
+// Candidates for arg-max / top-K searches carry an integer sort key instead of
+// the value: comparisons then run on the integer pipes (double compares are
+// slow on this part).  okey() maps a double to an int64 with the same order
+// (-0 just below +0, NaN below everything); KEY_NONE marks an empty slot.
+constexpr int64_t KEY_NONE = INT64_MIN;
+FC2_D int64_t okey(double v) {
+    const int64_t b = __double_as_longlong(v);
+    if ((b & 0x7fffffffffffffffll) > 0x7ff0000000000000ll) return KEY_NONE;  // NaN
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
 }
-FC2_D void warp_best(double& v, int64_t& j) {  // all lanes get the winner
+FC2_D int64_t okey(float v) {
+    const int32_t b = __float_as_int(v);
+    if ((b & 0x7fffffff) > 0x7f800000) return KEY_NONE;
+    return (int64_t)(b ^ ((b >> 31) & 0x7fffffff));
+}
+struct Cand { int64_t k; int64_t j; };
+FC2_D bool better(int64_t k1, int64_t j1, int64_t k2, int64_t j2) {
+    return k1 > k2 || (k1 == k2 && j1 < j2);
+}
+FC2_D void warp_best(int64_t& k, int64_t& j) {  // all lanes get the winner
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-        int64_t j2 = __shfl_xor_sync(0xffffffffu, j, o);
-        if (better(v2, j2, v, j)) { v = v2; j = j2; }
+        const int64_t k2 = __shfl_xor_sync(0xffffffffu, k, o);
+        const int64_t j2 = __shfl_xor_sync(0xffffffffu, j, o);
+        if (better(k2, j2, k, j)) { k = k2; j = j2; }
     }
 }
 

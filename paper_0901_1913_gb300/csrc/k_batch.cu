@@ -378,49 +378,41 @@ __global__ void __launch_bounds__(BP_NT) k_bpeaks1(const float* __restrict__ out
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float* row = out + ct.out_off[c] + (int64_t)(ct.H[c] - 1) * N;
     const int64_t base = (int64_t)blockIdx.x * BP_B;
-    double cv[BP_PER];
-    int64_t cj[BP_PER];
+    int64_t cv[BP_PER], cj[BP_PER];
 #pragma unroll
     for (int q = 0; q < BP_PER; ++q) {
         const int64_t jj = base + lane + (int64_t)(w * BP_PER + q) * 32;
-        cv[q] = -INFINITY;
+        cv[q] = KEY_NONE;
         cj[q] = INT64_MAX;
         if (jj < N) {
-            const float x = row[jj];
-            const bool left = (jj == 0) || (x > row[jj - 1]);
-            const bool right = (jj == N - 1) || (x >= row[jj + 1]);
+            const int64_t x = okey(row[jj]);
+            const bool left = (jj == 0) || (x > okey(row[jj - 1]));
+            const bool right = (jj == N - 1) || (x >= okey(row[jj + 1]));
             if (left && right) { cv[q] = x; cj[q] = jj; }
         }
     }
     for (int r = 0; r < K; ++r) {
-        double v = -INFINITY;
-        int64_t j = INT64_MAX;
+        int64_t v = KEY_NONE, j = INT64_MAX;
 #pragma unroll
         for (int q = 0; q < BP_PER; ++q)
             if (better(cv[q], cj[q], v, j)) { v = cv[q]; j = cj[q]; }
         warp_best(v, j);
 #pragma unroll
         for (int q = 0; q < BP_PER; ++q)
-            if (cj[q] == j) { cv[q] = -INFINITY; cj[q] = INT64_MAX; }
+            if (cj[q] == j) { cv[q] = KEY_NONE; cj[q] = INT64_MAX; }
         if (lane == 0) wtop[w][r] = Cand{v, j};
     }
     __syncthreads();
     if (w == 0) {
-        const int tot = BP_NW * K;
+        // merge the warps' sorted lists by their heads
+        int head = 0;
         for (int r = 0; r < K; ++r) {
-            double v = -INFINITY;
-            int64_t j = INT64_MAX;
-            int pos = -1;
-            for (int e = lane; e < tot; e += 32) {
-                const Cand cd = wtop[e / K][e % K];
-                if (better(cd.v, cd.j, v, j)) { v = cd.v; j = cd.j; pos = e; }
-            }
-            double bv = v;
-            int64_t bj = j;
-            warp_best(bv, bj);
-            if (pos >= 0 && j == bj && bj != INT64_MAX) wtop[pos / K][pos % K] = Cand{-INFINITY, INT64_MAX};
-            __syncwarp();
-            if (lane == 0) tops[((int64_t)c * nblk + blockIdx.x) * K + r] = Cand{bv, bj};
+            int64_t v = KEY_NONE, j = INT64_MAX;
+            if (lane < BP_NW && head < K) { v = wtop[lane][head].k; j = wtop[lane][head].j; }
+            const int64_t mj = j;
+            warp_best(v, j);
+            if (lane < BP_NW && mj == j && j != INT64_MAX) ++head;
+            if (lane == 0) tops[((int64_t)c * nblk + blockIdx.x) * K + r] = Cand{v, j};
         }
     }
 }
@@ -432,15 +424,13 @@ __global__ void __launch_bounds__(256) k_bpeaks2(const Cand* __restrict__ tops, 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const Cand* tc = tops + (int64_t)c * nblk * K;
     const int64_t total = (int64_t)nblk * K;
-    double pv = INFINITY;
-    int64_t pj = -1;
+    int64_t pv = INT64_MAX, pj = -1;
     for (int r = 0; r < K; ++r) {
-        double v = -INFINITY;
-        int64_t j = INT64_MAX;
+        int64_t v = KEY_NONE, j = INT64_MAX;
         for (int64_t b = threadIdx.x; b < total; b += blockDim.x) {
             const Cand cd = tc[b];
-            if (cd.j != INT64_MAX && better(pv, pj, cd.v, cd.j) && better(cd.v, cd.j, v, j)) {
-                v = cd.v;
+            if (cd.j != INT64_MAX && better(pv, pj, cd.k, cd.j) && better(cd.k, cd.j, v, j)) {
+                v = cd.k;
                 j = cd.j;
             }
         }
@@ -448,7 +438,7 @@ __global__ void __launch_bounds__(256) k_bpeaks2(const Cand* __restrict__ tops, 
         if (lane == 0) ws[w] = Cand{v, j};
         __syncthreads();
         if (w == 0) {
-            v = lane < 8 ? ws[lane].v : -INFINITY;
+            v = lane < 8 ? ws[lane].k : KEY_NONE;
             j = lane < 8 ? ws[lane].j : INT64_MAX;
             warp_best(v, j);
             if (lane == 0) {
@@ -458,10 +448,10 @@ __global__ void __launch_bounds__(256) k_bpeaks2(const Cand* __restrict__ tops, 
             }
         }
         __syncthreads();
-        pv = ws[0].v;
+        pv = ws[0].k;
         pj = ws[0].j;
         __syncthreads();
-        if (pj == INT64_MAX) pv = -INFINITY;
+        if (pj == INT64_MAX) pv = KEY_NONE;
     }
 }
 

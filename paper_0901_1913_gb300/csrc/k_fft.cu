@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "fc2_common.cuh"
@@ -381,6 +382,30 @@ __global__ void __launch_bounds__(NT, 2) k_fft_pass(const cpx<T>* __restrict__ i
     }
 }
 
+// ------------------------------------------------- pruned small transform
+// Q-point DFT (sign +) of v when only v[0..MZ) can be nonzero: with
+// k = (Q/MZ) k1 + k2, X_k = sum_{n<MZ} (v_n w_Q^{n k2}) w_MZ^{n k1}, i.e. Q/MZ
+// twiddled MZ-point transforms (MZ = 1: every output is v_0).
+template <typename T, int Q, int MZ>
+struct PrunedDFT {
+    static FC2_D void run(cpx<T>* v) {
+        constexpr int D = Q / MZ;
+        cpx<T> x[MZ];
+#pragma unroll
+        for (int n = 0; n < MZ; ++n) x[n] = v[n];
+#pragma unroll
+        for (int k2 = 0; k2 < D; ++k2) {
+            cpx<T> y[MZ];
+#pragma unroll
+            for (int n = 0; n < MZ; ++n)
+                y[n] = (n * k2 == 0) ? x[n] : mul(x[n], root64<T>(((64 / Q) * n * k2) & 63));
+            SmallDFT<T, MZ>::run(y);
+#pragma unroll
+            for (int k1 = 0; k1 < MZ; ++k1) v[D * k1 + k2] = y[k1];
+        }
+    }
+};
+
 // ------------------------------------------------- two-stage radix-64 pass
 // Float passes of radix R = 2^10..2^12 in two register stages, QA = R/64 then
 // 64, with 128 threads per 8192-element tile.  Stage A reads its butterfly
@@ -468,52 +493,85 @@ __global__ void __launch_bounds__(128, 2) k_fft_pass64(const cpx<float>* __restr
             }
         }
         const int rows = rows_of(g);
-        // ---- stage A: radix QA, rows pp + k 64 -> rows pp QA + k
+        // ---- stage A: radix QA, rows pp + k 64 -> rows pp QA + k.  In the first
+        // pass only rows < `rows` hold samples, so only the leading
+        // ceil(rows / 64) inputs of each stage-A transform can be nonzero: a
+        // pruned transform (PrunedDFT) skips the zeros.
+        auto stage_a = [&](auto mz_tag) {
+            constexpr int MZ = decltype(mz_tag)::value;
 #pragma unroll
-        for (int b = 0; b < PERA; ++b) {
-            const int bi = threadIdx.x + b * NT;
-            const int jj = bi % J, pp = bi / J;  // pp < 64
-            cpx<T> v[QA];
-            if (a.first) {
+            for (int b = 0; b < PERA; ++b) {
+                const int bi = threadIdx.x + b * NT;
+                const int jj = bi % J, pp = bi / J;  // pp < 64
+                cpx<T> v[QA];
+                if constexpr (MZ < QA) {
 #pragma unroll
-                for (int k = 0; k < QA; ++k) {
-                    const int r = pp + k * 64;
-                    v[k] = (r < rows) ? gin[j0 + jj + r * S] : mk<T>(0.f, 0.f);
+                    for (int k = 0; k < MZ; ++k) {
+                        const int r = pp + k * 64;
+                        v[k] = (r < rows) ? gin[j0 + jj + r * S] : mk<T>(0.f, 0.f);
+                    }
+                    PrunedDFT<T, QA, MZ>::run(v);
+                } else {
+                    if (a.first) {
+#pragma unroll
+                        for (int k = 0; k < QA; ++k) {
+                            const int r = pp + k * 64;
+                            v[k] = (r < rows) ? gin[j0 + jj + r * S] : mk<T>(0.f, 0.f);
+                        }
+                    } else {
+                        const cpx<T>* src = gin + (int64_t)bx * E;
+#pragma unroll
+                        for (int k = 0; k < QA; ++k) v[k] = src[(pp + k * 64) * J + jj];
+                    }
+                    const int jm = (j0 + jj) & nsg_mask;
+                    if (a.logNs > 0 && jm != 0) {
+                        // w_M^{(pp + 64 k) jm 2^lts} = base * step^k, step^k = lo[k & 7] hi[k >> 3]
+                        const cpx<T> base = twiddle(twlo, twhi, a.tws, (int64_t)((pp * jm) << lts));
+                        const cpx<T> st1 = twiddle(twlo, twhi, a.tws, (int64_t)((64 * jm) << lts));
+                        cpx<T> lo[8], hi[8];
+                        lo[0] = mk<T>(1.f, 0.f);
+                        lo[1] = st1;
+#pragma unroll
+                        for (int q = 2; q < 8; ++q) lo[q] = mul(lo[q - 1], st1);
+                        const cpx<T> s8 = mul(lo[7], st1);
+                        hi[0] = mk<T>(1.f, 0.f);
+                        hi[1] = s8;
+#pragma unroll
+                        for (int q = 2; q < 8; ++q) hi[q] = mul(hi[q - 1], s8);
+#pragma unroll
+                        for (int k = 0; k < QA; ++k) {
+                            cpx<T> w = base;
+                            if ((k & 7) != 0) w = mul(w, lo[k & 7]);
+                            if ((k >> 3) != 0) w = mul(w, hi[k >> 3]);
+                            v[k] = mul(v[k], w);
+                        }
+                    }
+                    SmallDFT<T, QA>::run(v);
                 }
-            } else {
-                const cpx<T>* src = gin + (int64_t)bx * E;
 #pragma unroll
-                for (int k = 0; k < QA; ++k) v[k] = src[(pp + k * 64) * J + jj];
+                for (int k = 0; k < QA; ++k) s[swz<LOGJ>((pp * QA + k) * J + jj)] = v[k];
             }
-            const int jm = (j0 + jj) & nsg_mask;
-            if (a.logNs > 0 && jm != 0) {
-                // w_M^{(pp + 64 k) jm 2^lts} = base * step^k, step^k = lo[k & 7] hi[k >> 3]
-                const cpx<T> base = twiddle(twlo, twhi, a.tws, (int64_t)((pp * jm) << lts));
-                const cpx<T> st1 = twiddle(twlo, twhi, a.tws, (int64_t)((64 * jm) << lts));
-                cpx<T> lo[8], hi[8];
-                lo[0] = mk<T>(1.f, 0.f);
-                lo[1] = st1;
-#pragma unroll
-                for (int q = 2; q < 8; ++q) lo[q] = mul(lo[q - 1], st1);
-                const cpx<T> s8 = mul(lo[7], st1);
-                hi[0] = mk<T>(1.f, 0.f);
-                hi[1] = s8;
-#pragma unroll
-                for (int q = 2; q < 8; ++q) hi[q] = mul(hi[q - 1], s8);
-#pragma unroll
-                for (int k = 0; k < QA; ++k) {
-                    cpx<T> w = base;
-                    if ((k & 7) != 0) w = mul(w, lo[k & 7]);
-                    if ((k >> 3) != 0) w = mul(w, hi[k >> 3]);
-                    v[k] = mul(v[k], w);
-                }
-            }
-            SmallDFT<T, QA>::run(v);
-#pragma unroll
-            for (int k = 0; k < QA; ++k) s[swz<LOGJ>((pp * QA + k) * J + jj)] = v[k];
+        };
+        int mz = QA;
+        if (a.first) {
+            const int kz = (rows + 63) >> 6;
+            mz = 1;
+            while (mz < kz && mz < QA) mz <<= 1;
         }
+        if (mz >= QA) stage_a(std::integral_constant<int, QA>{});
+        else if (mz == 1) stage_a(std::integral_constant<int, 1>{});
+        else if (mz == 2) stage_a(std::integral_constant<int, 2>{});
+        else if (mz == 4) stage_a(std::integral_constant<int, 4>{});
+        else if (mz == 8) stage_a(std::integral_constant<int, (QA > 8 ? 8 : QA)>{});
+        else if (mz == 16) stage_a(std::integral_constant<int, (QA > 16 ? 16 : QA)>{});
+        else stage_a(std::integral_constant<int, (QA > 32 ? 32 : QA)>{});
         __syncthreads();
-        // ---- stage B: radix 64, rows pp + k QA (in place)
+        // ---- stage B: radix 64, rows pp + k QA.  Where a warp's stores from
+        // registers hit the same 32-byte sectors as a smem-staged store would
+        // (the last pass, and a next pass of the same radix), the results go
+        // straight to global memory; otherwise they are staged in place.
+        const int logNs = a.logNs;
+        const bool same_radix = (logNs == 0 && a.logM - a.logRn == LOGR);
         {
             const int jj = threadIdx.x % J, pp = threadIdx.x / J;  // pp < QA
             cpx<T> v[64];
@@ -524,45 +582,46 @@ __global__ void __launch_bounds__(128, 2) k_fft_pass64(const cpx<float>* __restr
                 for (int k = 1; k < 64; ++k) v[k] = mul(v[k], st[(k - 1) * QA + pp]);
             }
             SmallDFT<T, 64>::run(v);
+            if (a.last) {
+                cpx<T>* spec = out + (int64_t)g * a.N;
 #pragma unroll
-            for (int k = 0; k < 64; ++k) s[swz<LOGJ>((pp + k * QA) * J + jj)] = v[k];
+                for (int k = 0; k < 64; ++k) {
+                    const int o = j0 + jj + ((pp + k * QA) << logNs);
+                    const int m = (o < M / 2) ? o : o - M;
+                    const int jf = m + a.hN;
+                    if (jf >= 0 && jf < a.N) spec[jf] = v[k];
+                }
+            } else if (same_radix) {
+                cpx<T>* gout = out + (int64_t)g * M;
+                const int LOGJn = a.logJn, Jn = 1 << a.logJn;
+                const int logBlk = a.logRn + a.logJn;
+                const int col = (j0 + jj) << LOGJn;
+#pragma unroll
+                for (int k = 0; k < 64; ++k) {
+                    const int kr = pp + k * QA;
+                    gout[((kr >> LOGJn) << logBlk) + col + (kr & (Jn - 1))] = v[k];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 64; ++k) s[swz<LOGJ>((pp + k * QA) * J + jj)] = v[k];
+            }
         }
-        __syncthreads();
-        const int logNs = a.logNs;
-        if (!a.last) {
+        if (!a.last && !same_radix) {
+            __syncthreads();
             cpx<T>* gout = out + (int64_t)g * M;
             const int LOGJn = a.logJn, Jn = 1 << a.logJn;
             const int logBlk = a.logRn + a.logJn;
-            if (logNs == 0 && a.logM - a.logRn == LOGR) {
-                for (int e = threadIdx.x; e < E; e += NT) {
-                    const int kl = e & (Jn - 1);
-                    const int jj = (e >> LOGJn) & (J - 1);
-                    const int kb = e >> (LOGJn + LOGJ);
-                    const int k = (kb << LOGJn) + kl;
-                    gout[(kb << logBlk) + ((j0 + jj) << LOGJn) + kl] = s[swz<LOGJ>(k * J + jj)];
-                }
-            } else {
-                const int logSn = a.logM - a.logRn;
-                for (int e = threadIdx.x; e < E; e += NT) {
-                    const int kl = e & (Jn - 1);
-                    const int jj = (e >> LOGJn) & (J - 1);
-                    const int kb = e >> (LOGJn + LOGJ);
-                    const int k = (kb << LOGJn) + kl;
-                    const int j = j0 + jj;
-                    const int i = ((j >> logNs) << (logNs + LOGR)) + (j & ((1 << logNs) - 1)) + (k << logNs);
-                    const int jn = i & ((1 << logSn) - 1), rn = i >> logSn;
-                    gout[((jn >> LOGJn) << logBlk) + (rn << LOGJn) + (jn & (Jn - 1))] =
-                        s[swz<LOGJ>(k * J + jj)];
-                }
-            }
-        } else {
-            cpx<T>* spec = out + (int64_t)g * a.N;
+            const int logSn = a.logM - a.logRn;
             for (int e = threadIdx.x; e < E; e += NT) {
-                const int k = e >> LOGJ, jj = e & (J - 1);
-                const int o = j0 + jj + (k << logNs);
-                const int m = (o < M / 2) ? o : o - M;
-                const int jf = m + a.hN;
-                if (jf >= 0 && jf < a.N) spec[jf] = s[swz<LOGJ>(e)];
+                const int kl = e & (Jn - 1);
+                const int jj = (e >> LOGJn) & (J - 1);
+                const int kb = e >> (LOGJn + LOGJ);
+                const int k = (kb << LOGJn) + kl;
+                const int j = j0 + jj;
+                const int i = ((j >> logNs) << (logNs + LOGR)) + (j & ((1 << logNs) - 1)) + (k << logNs);
+                const int jn = i & ((1 << logSn) - 1), rn = i >> logSn;
+                gout[((jn >> LOGJn) << logBlk) + (rn << LOGJn) + (jn & (Jn - 1))] =
+                    s[swz<LOGJ>(k * J + jj)];
             }
         }
         __syncthreads();  // the tile buffer is reused by the next iteration

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include "fc2_common.cuh"
+#include "fc2_df.cuh"
 #include "fc2_internal.h"
 #include "fc2_solve.cuh"
 
@@ -123,15 +124,35 @@ __global__ void __launch_bounds__(128) k_resolve(const cpx<float>* __restrict__ 
 // e^{2 pi i k f tau_i} (k = 1..H) straight from the samples (Eq. "eqPQ").
 // Work items are (bin, chunk of samples); each CTA reduces its chunk in a fixed
 // order and the final kernels add the chunks in order (reproducible).
-// Two precisions:
+// Three precisions, tried in turn for a bin until its error estimate (the
+// coefficient-norm model of chol_solve) is within budget:
 //  - tier 1: the phase f tau_i is reduced in double and held as a 32-bit
 //    fixed-point fraction, so harmonic k's phase is an exact integer product;
-//    sine/cosine in float, accumulation in compensated float per thread and
-//    double across threads.  Each term carries an independent ~2e-7 relative
-//    error, so the sums are good to ~2e-7 * sqrt(sum w^2), far below the
-//    gridded spectra's error for large n.
-//  - tier 2: everything in double (powers of e^{2 pi i f tau_i}).
+//    sine/cosine in float, accumulation in compensated float.  Each term
+//    carries an independent ~2e-7 relative error, so the sums are good to
+//    ~2e-7 * sqrt(sum w^2), far below the gridded spectra's error for large n.
+//  - tier 2: double-float phasors (table + Taylor from the exact 64-bit phase,
+//    powers by multiplication) and double-float accumulation; worst-case
+//    error ~1e-12 * sum w, on the float pipes.
+//  - tier 3: everything in double (powers of e^{2 pi i f tau_i}).
 constexpr int EX_NT = 256;
+constexpr int EX_GRID = 4 * 152;
+constexpr int EX_MAX_CHUNKS = 64;
+
+// Chunks of the sample range for `count` bins: about two work items per CTA
+// of the EX_GRID-CTA grid, at least 16 samples per thread, at most
+// EX_MAX_CHUNKS chunks.  Evaluated identically on host and device, so kernels
+// that read the bin count from device memory derive the same geometry.
+FC2_HD void exact_geometry(int64_t n, int64_t count, int64_t* chunk, int* nch) {
+    if (count < 1) count = 1;
+    int64_t want = (2 * EX_GRID + count - 1) / count;
+    if (want > EX_MAX_CHUNKS) want = EX_MAX_CHUNKS;
+    int64_t c = (n + want - 1) / want;
+    if (c < 16 * EX_NT) c = 16 * EX_NT;
+    c = ((c + EX_NT - 1) / EX_NT) * EX_NT;
+    *chunk = c;
+    *nch = (int)((n + c - 1) / c);
+}
 
 // Fixed-point phases: A_i = frac(f_min tau_i) 2^64 and B_i = frac(df tau_i) 2^64
 // (u64, from the exact double-double products), so that the phase of trial
@@ -144,90 +165,155 @@ __global__ void k_phase_fx(const double* __restrict__ tau, const double* __restr
     if (i >= n) return;
     A[i] = frac_fx(f_min, tau[i]);
     B[i] = frac_fx(df, tau[i]);
-    wq32[i] = (float)wq[i];
-    wp32[i] = (float)wp[i];
+    const float qh = (float)wq[i], ph = (float)wp[i];
+    wq32[i] = qh;
+    wp32[i] = ph;
+    wq32[n + i] = (float)(wq[i] - (double)qh);  // low parts for double-float sums
+    wp32[n + i] = (float)(wp[i] - (double)ph);
+}
+
+// Double-float tables e^{2 pi i a / 256} (entries 0..255) and
+// e^{2 pi i b / 65536} (entries 256..511) for df_phasor.
+__global__ void k_init_dftab(dfc* __restrict__ tab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 512) return;
+    const double x = (i < 256) ? (double)i / 128.0 : (double)(i - 256) / 32768.0;
+    double sn, cn;
+    sincospi(x, &sn, &cn);
+    tab[i] = dfc{df_from_double(cn), df_from_double(sn)};
+}
+
+// Lane 0 receives the warp's sum of (hi, lo) float pairs, added with
+// error-free two-sums.
+FC2_D double warp_sum_pair(float hi, float lo) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        const dfl t = df_two_sum(hi, h2);
+        hi = t.h;
+        lo = lo + l2 + t.l;
+    }
+    return (double)hi + (double)lo;
 }
 
 template <int HM, int TIER>
 __global__ void __launch_bounds__(EX_NT) k_exact_partial(
     const uint64_t* __restrict__ Aph, const uint64_t* __restrict__ Bph,
     const float* __restrict__ wq32, const float* __restrict__ wp32,
-    const double* __restrict__ wq, const double* __restrict__ wp, int64_t n,
-    const int32_t* __restrict__ bins32, const int64_t* __restrict__ bins64,
-    const int32_t* __restrict__ count_dev, int64_t count, int64_t base, int64_t cap,
-    int64_t chunk, int nch, int H, double* __restrict__ part) {
+    const double* __restrict__ wq, const double* __restrict__ wp, const dfc* __restrict__ dftab,
+    int64_t n, const int32_t* __restrict__ bins32, const int64_t* __restrict__ bins64,
+    const int32_t* __restrict__ count_dev, int64_t count, int64_t base, int64_t cap, int H,
+    double* __restrict__ part) {
     constexpr int NV = 6 * HM;
     __shared__ double red[EX_NT / 32][NV];
+    __shared__ dfc stab[TIER == 2 ? 512 : 1];
     int64_t cnt = count_dev ? (int64_t)(*count_dev) - base : count;
     if (cnt > cap) cnt = cap;
-    const int64_t items = cnt > 0 ? cnt * nch : 0;
+    if (cnt <= 0) return;
+    int64_t chunk;
+    int nch;
+    exact_geometry(n, cnt, &chunk, &nch);
+    const int64_t items = cnt * nch;
     const int lane = threadIdx.x & 31, wpi = threadIdx.x >> 5;
+    if constexpr (TIER == 2) {
+        for (int i = threadIdx.x; i < 512; i += EX_NT) stab[i] = dftab[i];
+        __syncthreads();
+    }
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int64_t b = it / nch;
         const int c = (int)(it % nch);
         const int64_t j = bins32 ? (int64_t)bins32[base + b] : bins64[base + b];
-        double acc[NV];
+        const uint64_t ju = (uint64_t)(j >= 0 ? j : 0);
+        const int64_t i0 = (int64_t)c * chunk;
+        const int64_t i1 = (j >= 0) ? min(n, i0 + chunk) : i0;
+        if constexpr (TIER == 1) {
+            CompSum<float> fa[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = 0.0;
-        if (j >= 0) {
-            const uint64_t ju = (uint64_t)j;
-            const int64_t i0 = (int64_t)c * chunk;
-            const int64_t i1 = min(n, i0 + chunk);
-            if constexpr (TIER == 1) {
-                CompSum<float> fa[NV];
+            for (int v = 0; v < NV; ++v) fa[v].init();
+            for (int64_t i = i0 + threadIdx.x; i < i1; i += EX_NT) {
+                const uint32_t u = (uint32_t)((Aph[i] + ju * Bph[i]) >> 32);
+                const float a = wq32[i], bb = wp32[i];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) fa[v].init();
-                for (int64_t i = i0 + threadIdx.x; i < i1; i += EX_NT) {
-                    const uint32_t u = (uint32_t)((Aph[i] + ju * Bph[i]) >> 32);
-                    const float a = wq32[i], bb = wp32[i];
-#pragma unroll
-                    for (int k = 1; k <= 2 * HM; ++k) {
-                        if (k <= 2 * H) {
-                            const int32_t ph = (int32_t)(u * (uint32_t)k);  // [-1/2, 1/2) cycles
-                            float sn, cn;
-                            sincospif((float)ph * 4.656612873077393e-10f, &sn, &cn);  // 2^-31
-                            fa[2 * (k - 1)].add(a * cn);
-                            fa[2 * (k - 1) + 1].add(a * sn);
-                            if (k <= H) {
-                                fa[4 * HM + 2 * (k - 1)].add(bb * cn);
-                                fa[4 * HM + 2 * (k - 1) + 1].add(bb * sn);
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int v = 0; v < NV; ++v) acc[v] = (double)fa[v].s + (double)fa[v].c;
-            } else {
-                for (int64_t i = i0 + threadIdx.x; i < i1; i += EX_NT) {
-                    const int64_t ph = (int64_t)(Aph[i] + ju * Bph[i]);
-                    double s1, c1;
-                    sincospi(ldexp((double)ph, -63), &s1, &c1);
-                    double cr = c1, ci = s1;
-                    const double a = wq[i], bb = wp[i];
-#pragma unroll
-                    for (int k = 0; k < 2 * HM; ++k) {
-                        if (k < 2 * H) {
-                            acc[2 * k] = fma(a, cr, acc[2 * k]);
-                            acc[2 * k + 1] = fma(a, ci, acc[2 * k + 1]);
-                            if (k < H) {
-                                acc[4 * HM + 2 * k] = fma(bb, cr, acc[4 * HM + 2 * k]);
-                                acc[4 * HM + 2 * k + 1] = fma(bb, ci, acc[4 * HM + 2 * k + 1]);
-                            }
-                            const double nr = cr * c1 - ci * s1;
-                            const double ni = cr * s1 + ci * c1;
-                            cr = nr;
-                            ci = ni;
+                for (int k = 1; k <= 2 * HM; ++k) {
+                    if (k <= 2 * H) {
+                        const int32_t ph = (int32_t)(u * (uint32_t)k);  // [-1/2, 1/2) cycles
+                        float sn, cn;
+                        sincospif((float)ph * 4.656612873077393e-10f, &sn, &cn);  // 2^-31
+                        fa[2 * (k - 1)].add(a * cn);
+                        fa[2 * (k - 1) + 1].add(a * sn);
+                        if (k <= H) {
+                            fa[4 * HM + 2 * (k - 1)].add(bb * cn);
+                            fa[4 * HM + 2 * (k - 1) + 1].add(bb * sn);
                         }
                     }
                 }
             }
-        }
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            double x = acc[v];
+            for (int v = 0; v < NV; ++v) {
+                const double x = warp_sum_pair(fa[v].s, fa[v].c);
+                if (lane == 0) red[wpi][v] = x;
+            }
+        } else if constexpr (TIER == 2) {
+            dfl fa[NV];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-            if (lane == 0) red[wpi][v] = x;
+            for (int v = 0; v < NV; ++v) fa[v] = dfl{0.f, 0.f};
+            for (int64_t i = i0 + threadIdx.x; i < i1; i += EX_NT) {
+                const uint64_t u = Aph[i] + ju * Bph[i];
+                const dfl a{wq32[i], wq32[n + i]}, bb{wp32[i], wp32[n + i]};
+                const dfc z1 = df_phasor(u, stab, stab + 256);
+                dfc z = z1;
+#pragma unroll
+                for (int k = 0; k < 2 * HM; ++k) {
+                    if (k < 2 * H) {
+                        df_acc_mul(fa[2 * k], a, z.re);
+                        df_acc_mul(fa[2 * k + 1], a, z.im);
+                        if (k < H) {
+                            df_acc_mul(fa[4 * HM + 2 * k], bb, z.re);
+                            df_acc_mul(fa[4 * HM + 2 * k + 1], bb, z.im);
+                        }
+                        if (k + 1 < 2 * H) z = dfc_mul(z, z1);
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const double x = warp_sum_pair(fa[v].h, fa[v].l);
+                if (lane == 0) red[wpi][v] = x;
+            }
+        } else {
+            double acc[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+            for (int64_t i = i0 + threadIdx.x; i < i1; i += EX_NT) {
+                const int64_t ph = (int64_t)(Aph[i] + ju * Bph[i]);
+                double s1, c1;
+                sincospi(ldexp((double)ph, -63), &s1, &c1);
+                double cr = c1, ci = s1;
+                const double a = wq[i], bb = wp[i];
+#pragma unroll
+                for (int k = 0; k < 2 * HM; ++k) {
+                    if (k < 2 * H) {
+                        acc[2 * k] = fma(a, cr, acc[2 * k]);
+                        acc[2 * k + 1] = fma(a, ci, acc[2 * k + 1]);
+                        if (k < H) {
+                            acc[4 * HM + 2 * k] = fma(bb, cr, acc[4 * HM + 2 * k]);
+                            acc[4 * HM + 2 * k + 1] = fma(bb, ci, acc[4 * HM + 2 * k + 1]);
+                        }
+                        const double nr = cr * c1 - ci * s1;
+                        const double ni = cr * s1 + ci * c1;
+                        cr = nr;
+                        ci = ni;
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                double x = acc[v];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+                if (lane == 0) red[wpi][v] = x;
+            }
         }
         __syncthreads();
         if (threadIdx.x < NV) {
@@ -255,14 +341,14 @@ FC2_D bool warp_sum_chunks(const double* __restrict__ part, int64_t b, int nch, 
     return lane == 0;
 }
 
-// Final step of a fix-up round: solve from the exact sums; with a tier-1 round,
-// bins whose estimated error with eps_t1 still exceeds err_fix are queued for
-// tier 2.
+// Final step of a fix-up round: solve from the exact sums; bins whose
+// estimated error with the round's sum precision eps_sums still exceeds
+// err_fix are queued for the next tier (when `next` is given).
 template <int H>
-__global__ void __launch_bounds__(128) k_exact_dchi2(const double* __restrict__ part, int nch,
+__global__ void __launch_bounds__(128) k_exact_dchi2(const double* __restrict__ part, int64_t n,
                               const int32_t* __restrict__ list,
                               const int32_t* __restrict__ count_dev, int64_t base, int64_t cap,
-                              const double* __restrict__ scal, double tau_drop, double eps_t1,
+                              const double* __restrict__ scal, double tau_drop, double eps_sums,
                               double err_fix, int32_t* __restrict__ next,
                               int32_t* __restrict__ next_count, int64_t next_cap,
                               double* __restrict__ dchi2, int64_t N) {
@@ -272,13 +358,16 @@ __global__ void __launch_bounds__(128) k_exact_dchi2(const double* __restrict__ 
     const int w = threadIdx.x >> 5;
     const int64_t b = (int64_t)blockIdx.x * 4 + w;
     if (b >= cnt) return;
+    int64_t chunk;
+    int nch;
+    exact_geometry(n, cnt, &chunk, &nch);
     if (!warp_sum_chunks<H>(part, b, nch, sh[w])) return;
     const int64_t j = list[base + b];
     Sys<double, H> S;
     exact_sys_from_sums<H>(sh[w], H, scal, S);
     double out[H], an2 = 0.0;
     chol_solve<double, H, true>(S, tau_drop, out, &an2);
-    if (next && !(est_err<double>(an2, 2 * H + 1, eps_t1) <= err_fix)) {
+    if (next && !(est_err<double>(an2, 2 * H + 1, eps_sums) <= err_fix)) {
         int32_t pos = atomicAdd(next_count, 1);
         if (pos < next_cap) next[pos] = (int32_t)j;
     }
@@ -355,13 +444,12 @@ __global__ void __launch_bounds__(PK_NT) k_peaks1(const double* __restrict__ d, 
     const int64_t base = (int64_t)blockIdx.x * PK_B;
     for (int h = 0; h < H; ++h) {
         const double* row = d + (int64_t)h * N;
-        double v = -INFINITY;
-        int64_t j = INT64_MAX;
-#pragma unroll 4
+        int64_t v = KEY_NONE, j = INT64_MAX;
+#pragma unroll 8
         for (int q = 0; q < PK_PER; ++q) {
-            int64_t jj = base + threadIdx.x + (int64_t)q * PK_NT;
+            const int64_t jj = base + threadIdx.x + (int64_t)q * PK_NT;
             if (jj < N) {
-                double x = row[jj];
+                const int64_t x = okey(row[jj]);
                 if (better(x, jj, v, j)) { v = x; j = jj; }
             }
         }
@@ -369,56 +457,48 @@ __global__ void __launch_bounds__(PK_NT) k_peaks1(const double* __restrict__ d, 
         if (lane == 0) wres[w][h] = Cand{v, j};
     }
     const double* row = d + (int64_t)(H - 1) * N;
-    double cv[PK_PER];
-    int64_t cj[PK_PER];
+    int64_t cv[PK_PER], cj[PK_PER];
 #pragma unroll
     for (int q = 0; q < PK_PER; ++q) {
-        int64_t jj = base + lane + (int64_t)(w * PK_PER + q) * 32;  // warp-contiguous
-        cv[q] = -INFINITY;
+        const int64_t jj = base + lane + (int64_t)(w * PK_PER + q) * 32;  // warp-contiguous
+        cv[q] = KEY_NONE;
         cj[q] = INT64_MAX;
         if (jj < N) {
-            double x = row[jj];
-            bool left = (jj == 0) || (x > row[jj - 1]);
-            bool right = (jj == N - 1) || (x >= row[jj + 1]);
+            const int64_t x = okey(row[jj]);
+            const bool left = (jj == 0) || (x > okey(row[jj - 1]));
+            const bool right = (jj == N - 1) || (x >= okey(row[jj + 1]));
             if (left && right) { cv[q] = x; cj[q] = jj; }
         }
     }
     for (int r = 0; r < K; ++r) {
-        double v = -INFINITY;
-        int64_t j = INT64_MAX;
+        int64_t v = KEY_NONE, j = INT64_MAX;
 #pragma unroll
         for (int q = 0; q < PK_PER; ++q)
             if (better(cv[q], cj[q], v, j)) { v = cv[q]; j = cj[q]; }
         warp_best(v, j);
 #pragma unroll
         for (int q = 0; q < PK_PER; ++q)
-            if (cj[q] == j) { cv[q] = -INFINITY; cj[q] = INT64_MAX; }
+            if (cj[q] == j) { cv[q] = KEY_NONE; cj[q] = INT64_MAX; }
         if (lane == 0) wtop[w][r] = Cand{v, j};
     }
     __syncthreads();
     if (w == 0) {
         for (int h = 0; h < H; ++h) {
-            double v = lane < PK_NW ? wres[lane][h].v : -INFINITY;
+            int64_t v = lane < PK_NW ? wres[lane][h].k : KEY_NONE;
             int64_t j = lane < PK_NW ? wres[lane][h].j : INT64_MAX;
             warp_best(v, j);
             if (lane == 0) amax[(int64_t)h * nblk + blockIdx.x] = Cand{v, j};
         }
-        // merge the warps' lists: K rounds over PK_NW * K candidates
-        const int tot = PK_NW * K;
+        // merge the warps' sorted lists: K rounds, lane q < PK_NW looks at the
+        // head of warp q's list
+        int head = 0;
         for (int r = 0; r < K; ++r) {
-            double v = -INFINITY;
-            int64_t j = INT64_MAX;
-            int pos = -1;
-            for (int e = lane; e < tot; e += 32) {
-                Cand c = wtop[e / K][e % K];
-                if (better(c.v, c.j, v, j)) { v = c.v; j = c.j; pos = e; }
-            }
-            double bv = v;
-            int64_t bj = j;
-            warp_best(bv, bj);
-            if (pos >= 0 && j == bj && bj != INT64_MAX) wtop[pos / K][pos % K] = Cand{-INFINITY, INT64_MAX};
-            __syncwarp();
-            if (lane == 0) tops[(int64_t)blockIdx.x * K + r] = Cand{bv, bj};
+            int64_t v = KEY_NONE, j = INT64_MAX;
+            if (lane < PK_NW && head < K) { v = wtop[lane][head].k; j = wtop[lane][head].j; }
+            const int64_t mj = j;
+            warp_best(v, j);
+            if (lane < PK_NW && mj == j && j != INT64_MAX) ++head;
+            if (lane == 0) tops[(int64_t)blockIdx.x * K + r] = Cand{v, j};
         }
     }
 }
@@ -431,33 +511,31 @@ __global__ void __launch_bounds__(1024) k_peaks2(const Cand* __restrict__ amax,
     __shared__ Cand ws[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int h = 0; h < H; ++h) {
-        double v = -INFINITY;
-        int64_t j = INT64_MAX;
+        int64_t v = KEY_NONE, j = INT64_MAX;
         for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
-            Cand c = amax[(int64_t)h * nblk + b];
-            if (better(c.v, c.j, v, j)) { v = c.v; j = c.j; }
+            const Cand c = amax[(int64_t)h * nblk + b];
+            if (better(c.k, c.j, v, j)) { v = c.k; j = c.j; }
         }
         warp_best(v, j);
         if (lane == 0) ws[w] = Cand{v, j};
         __syncthreads();
         if (w == 0) {
-            v = lane < nw ? ws[lane].v : -INFINITY;
+            v = lane < nw ? ws[lane].k : KEY_NONE;
             j = lane < nw ? ws[lane].j : INT64_MAX;
             warp_best(v, j);
             if (lane == 0) best_j[h] = (j == INT64_MAX) ? -1 : j;
         }
         __syncthreads();
     }
+    // each block's list is sorted, so K rounds of "best head" merge them
     const int64_t total = (int64_t)nblk * K;
-    double pv = INFINITY;
-    int64_t pj = -1;
+    int64_t pv = INT64_MAX, pj = -1;
     for (int r = 0; r < K; ++r) {
-        double v = -INFINITY;
-        int64_t j = INT64_MAX;
+        int64_t v = KEY_NONE, j = INT64_MAX;
         for (int64_t b = threadIdx.x; b < total; b += blockDim.x) {
-            Cand c = tops[b];
-            if (c.j != INT64_MAX && better(pv, pj, c.v, c.j) && better(c.v, c.j, v, j)) {
-                v = c.v;
+            const Cand c = tops[b];
+            if (c.j != INT64_MAX && better(pv, pj, c.k, c.j) && better(c.k, c.j, v, j)) {
+                v = c.k;
                 j = c.j;
             }
         }
@@ -465,16 +543,16 @@ __global__ void __launch_bounds__(1024) k_peaks2(const Cand* __restrict__ amax,
         if (lane == 0) ws[w] = Cand{v, j};
         __syncthreads();
         if (w == 0) {
-            v = lane < nw ? ws[lane].v : -INFINITY;
+            v = lane < nw ? ws[lane].k : KEY_NONE;
             j = lane < nw ? ws[lane].j : INT64_MAX;
             warp_best(v, j);
             if (lane == 0) { ws[0] = Cand{v, j}; peak_j[r] = (j == INT64_MAX) ? -1 : j; }
         }
         __syncthreads();
-        pv = ws[0].v;
+        pv = ws[0].k;
         pj = ws[0].j;
         __syncthreads();
-        if (pj == INT64_MAX) pv = -INFINITY;
+        if (pj == INT64_MAX) pv = KEY_NONE;
     }
 }
 
@@ -526,78 +604,103 @@ cudaError_t launch_assemble(fc2_plan_s* p, cudaStream_t s) {
     return p->fp64 ? assemble_impl<double>(p, s) : assemble_impl<float>(p, s);
 }
 
-void exact_geometry(int64_t n, int64_t* chunk, int* nch) {
-    int64_t c = (n + 63) / 64;
-    if (c < 2048) c = 2048;
-    c = ((c + EX_NT - 1) / EX_NT) * EX_NT;
-    *chunk = c;
-    *nch = (int)((n + c - 1) / c);
-}
-
 template <int HH, int TIER>
 static void launch_partial(fc2_plan_s* p, const int32_t* b32, const int64_t* b64,
                            const int32_t* cnt_dev, int64_t cnt, int64_t base, int64_t cap,
                            cudaStream_t s) {
-    int64_t chunk;
-    int nch;
-    exact_geometry(p->n, &chunk, &nch);
-    k_exact_partial<HH, TIER><<<4 * 152, EX_NT, 0, s>>>(p->d_phA, p->d_phB, p->d_wq32, p->d_wp32,
-                                                        p->d_wq, p->d_wp, p->n, b32, b64, cnt_dev,
-                                                        cnt, base, cap, chunk, nch, p->H,
-                                                        p->d_part);
+    k_exact_partial<HH, TIER><<<EX_GRID, EX_NT, 0, s>>>(
+        p->d_phA, p->d_phB, p->d_wq32, p->d_wp32, p->d_wq, p->d_wp, (const dfc*)p->d_dftab, p->n,
+        b32, b64, cnt_dev, cnt, base, cap, p->H, p->d_part);
 }
 
-// Exact fix-up of the flagged bins (list 0, `count` entries): a tier-1 round,
-// then tier 2 (all double) for the bins tier 1 could not settle.  Rounds of at
-// most exact_cap bins.  Returns the number of tier-2 bins through *n2.
+// Worst-case relative error of the double-float sums: phasor powers up to
+// k = 16 by repeated multiplication, each step ~3 * 2^-47.
+constexpr double EPS_DF = 1.5e-12;
+constexpr double ERR_FIX = 2e-5;
+
+// Exact fix-up of the flagged bins (list 0, `count` entries) in up to three
+// tiers: every bin gets tier-1 sums; bins tier 1 cannot settle go to tier 2
+// and from there to tier 3.  Rounds of at most exact_cap bins.  The later
+// tiers read their bin counts on the device, so nothing waits for the host.
 template <int HH>
-static cudaError_t fixup_h(fc2_plan_s* p, int64_t count, int64_t* n2, cudaStream_t s) {
-    int64_t chunk;
-    int nch;
-    exact_geometry(p->n, &chunk, &nch);
+static cudaError_t fixup_h(fc2_plan_s* p, int64_t count, cudaStream_t s) {
     const int64_t cap = p->exact_cap;
     const double eps_t1 = 2e-7 * p->scal[SC_RW];
+    int32_t* list1 = p->d_flag_list;
     int32_t* list2 = p->d_flag_list + p->flag_cap;  // re-solve list is consumed by now
+    int32_t* list3 = p->d_flag_list + 2 * p->flag_cap;
+    int32_t* cnt1 = p->d_flag_count;
     int32_t* cnt2 = p->d_flag_count + 2;
-    cudaMemsetAsync(cnt2, 0, 4, s);
+    int32_t* cnt3 = p->d_flag_count + 3;
+    cudaMemsetAsync(cnt2, 0, 8, s);
+    if (count <= 0) return cudaGetLastError();
     for (int64_t base = 0; base < count; base += cap) {
-        const int64_t nb = std::min(cap, count - base);
-        launch_partial<HH, 1>(p, p->d_flag_list, nullptr, p->d_flag_count, 0, base, cap, s);
-        k_exact_dchi2<HH><<<(unsigned)((nb + 3) / 4), 128, 0, s>>>(
-            p->d_part, nch, p->d_flag_list, p->d_flag_count, base, cap, p->d_scal, 1e-13, eps_t1,
-            2e-5, list2, cnt2, p->flag_cap, p->d_dchi2, p->N);
+        const unsigned blocks = (unsigned)((std::min(cap, count - base) + 3) / 4);
+        launch_partial<HH, 1>(p, list1, nullptr, cnt1, 0, base, cap, s);
+        k_exact_dchi2<HH><<<blocks, 128, 0, s>>>(p->d_part, p->n, list1, cnt1, base, cap, p->d_scal,
+                                                 1e-13, eps_t1, ERR_FIX, list2, cnt2, p->flag_cap,
+                                                 p->d_dchi2, p->N);
     }
-    int32_t c2 = 0;
-    cudaMemcpyAsync(&c2, cnt2, 4, cudaMemcpyDeviceToHost, s);
-    cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return e;
-    *n2 = c2;
-    for (int64_t base = 0; base < c2; base += cap) {
-        const int64_t nb = std::min(cap, (int64_t)c2 - base);
+    for (int64_t base = 0; base < count; base += cap) {
+        const unsigned blocks = (unsigned)((std::min(cap, count - base) + 3) / 4);
         launch_partial<HH, 2>(p, list2, nullptr, cnt2, 0, base, cap, s);
-        k_exact_dchi2<HH><<<(unsigned)((nb + 3) / 4), 128, 0, s>>>(
-            p->d_part, nch, list2, cnt2, base, cap, p->d_scal, 1e-13, 0.0, 2e-5, nullptr,
-            nullptr, 0, p->d_dchi2, p->N);
+        k_exact_dchi2<HH><<<blocks, 128, 0, s>>>(p->d_part, p->n, list2, cnt2, base, cap, p->d_scal,
+                                                 1e-13, EPS_DF, ERR_FIX, list3, cnt3, p->flag_cap,
+                                                 p->d_dchi2, p->N);
+    }
+    for (int64_t base = 0; base < count; base += cap) {
+        const unsigned blocks = (unsigned)((std::min(cap, count - base) + 3) / 4);
+        launch_partial<HH, 3>(p, list3, nullptr, cnt3, 0, base, cap, s);
+        k_exact_dchi2<HH><<<blocks, 128, 0, s>>>(p->d_part, p->n, list3, cnt3, base, cap, p->d_scal,
+                                                 1e-13, 0.0, ERR_FIX, nullptr, nullptr, 0,
+                                                 p->d_dchi2, p->N);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_fixup(fc2_plan_s* p, int64_t count, cudaStream_t s) {
-    int64_t n2 = 0;
-    cudaError_t e;
+// Delta chi^2 of nb given bins from tier-`tier` exact sums alone, written
+// into the plan's output array (diagnostics and tests of each tier).
+template <int HH>
+static cudaError_t exact_bins_h(fc2_plan_s* p, int64_t nb, int tier, cudaStream_t s) {
+    int32_t* list = p->d_flag_list;
+    const unsigned blocks = (unsigned)((nb + 3) / 4);
+    if (tier == 1) launch_partial<HH, 1>(p, list, nullptr, nullptr, nb, 0, nb, s);
+    else if (tier == 2) launch_partial<HH, 2>(p, list, nullptr, nullptr, nb, 0, nb, s);
+    else launch_partial<HH, 3>(p, list, nullptr, nullptr, nb, 0, nb, s);
+    int32_t* cnt = p->d_flag_count + 3;
+    const int32_t nb32 = (int32_t)nb;
+    cudaMemcpyAsync(cnt, &nb32, 4, cudaMemcpyHostToDevice, s);
+    k_exact_dchi2<HH><<<blocks, 128, 0, s>>>(p->d_part, p->n, list, cnt, 0, nb, p->d_scal, 1e-13,
+                                             0.0, ERR_FIX, nullptr, nullptr, 0, p->d_dchi2, p->N);
+    return cudaStreamSynchronize(s);
+}
+
+cudaError_t launch_exact_bins(fc2_plan_s* p, int64_t nb, int tier, cudaStream_t s) {
     switch (p->H) {
-        case 1: e = fixup_h<1>(p, count, &n2, s); break;
-        case 2: e = fixup_h<2>(p, count, &n2, s); break;
-        case 3: e = fixup_h<3>(p, count, &n2, s); break;
-        case 4: e = fixup_h<4>(p, count, &n2, s); break;
-        case 5: e = fixup_h<5>(p, count, &n2, s); break;
-        case 6: e = fixup_h<6>(p, count, &n2, s); break;
-        case 7: e = fixup_h<7>(p, count, &n2, s); break;
-        case 8: e = fixup_h<8>(p, count, &n2, s); break;
+        case 1: return exact_bins_h<1>(p, nb, tier, s);
+        case 2: return exact_bins_h<2>(p, nb, tier, s);
+        case 3: return exact_bins_h<3>(p, nb, tier, s);
+        case 4: return exact_bins_h<4>(p, nb, tier, s);
+        case 5: return exact_bins_h<5>(p, nb, tier, s);
+        case 6: return exact_bins_h<6>(p, nb, tier, s);
+        case 7: return exact_bins_h<7>(p, nb, tier, s);
+        case 8: return exact_bins_h<8>(p, nb, tier, s);
         default: return cudaErrorInvalidValue;
     }
-    p->last_exact2_count = n2;
-    return e;
+}
+
+cudaError_t launch_fixup(fc2_plan_s* p, int64_t count, cudaStream_t s) {
+    switch (p->H) {
+        case 1: return fixup_h<1>(p, count, s);
+        case 2: return fixup_h<2>(p, count, s);
+        case 3: return fixup_h<3>(p, count, s);
+        case 4: return fixup_h<4>(p, count, s);
+        case 5: return fixup_h<5>(p, count, s);
+        case 6: return fixup_h<6>(p, count, s);
+        case 7: return fixup_h<7>(p, count, s);
+        case 8: return fixup_h<8>(p, count, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 size_t peaks_scratch_bytes(int64_t N, int H, int K) {
@@ -614,13 +717,13 @@ cudaError_t launch_peaks(fc2_plan_s* p, cudaStream_t s) {
     int64_t* rec_j = (int64_t*)(tops + nblk * K);
     k_peaks1<<<(unsigned)nblk, PK_NT, 0, s>>>(p->d_dchi2, p->N, H, K, amax, tops, (int)nblk);
     k_peaks2<<<1, 1024, 0, s>>>(amax, tops, (int)nblk, H, K, rec_j, rec_j + H);
+    const int nrec = H + K;
     int64_t chunk;
     int nch;
-    exact_geometry(p->n, &chunk, &nch);
-    const int nrec = H + K;
+    exact_geometry(p->n, nrec, &chunk, &nch);
 #define FC2_CO(HH)                                                                            \
     case HH:                                                                                  \
-        launch_partial<HH, 1>(p, nullptr, rec_j, nullptr, nrec, 0, nrec, s);                  \
+        launch_partial<HH, 1>(p, nullptr, rec_j, nullptr, nrec, 0, nrec, s);               \
         k_exact_coeffs<HH><<<(nrec + 3) / 4, 128, 0, s>>>(p->d_part, nch, rec_j, nrec, H, p->d_scal,        \
                                             p->f_min, p->df, 1e-13, p->d_best);               \
         break;
@@ -636,14 +739,13 @@ cudaError_t launch_phase_fx(fc2_plan_s* p, cudaStream_t s) {
     k_phase_fx<<<(unsigned)((p->n + 255) / 256), 256, 0, s>>>(p->d_tau, p->d_wq, p->d_wp, p->n,
                                                              p->f_min, p->df, p->d_phA, p->d_phB,
                                                              p->d_wq32, p->d_wp32);
+    k_init_dftab<<<2, 256, 0, s>>>((dfc*)p->d_dftab);
     return cudaGetLastError();
 }
 
 size_t exact_scratch_bytes(int64_t n, int H, int64_t cap) {
-    int64_t chunk;
-    int nch;
-    exact_geometry(n, &chunk, &nch);
-    return (size_t)cap * nch * 6 * H * sizeof(double);
+    (void)n;
+    return (size_t)cap * EX_MAX_CHUNKS * 6 * H * sizeof(double);
 }
 
 }  // namespace fc2

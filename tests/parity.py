@@ -17,10 +17,10 @@ TOL = 1e-4
 NEAR_ALIAS = 1e-8
 
 
-def compare(d_gpu, d_or, piv_or, chi0, tol=TOL):
+def compare(d_gpu, d_or, piv_or, chi0, tol=TOL, near_alias=NEAR_ALIAS):
     """d_gpu, d_or, piv_or: [nbins, H] arrays on the same bins."""
     d_gpu = np.asarray(d_gpu, dtype=np.float64)
-    near = piv_or < NEAR_ALIAS
+    near = piv_or < near_alias
     err = np.abs(d_gpu - d_or)
     strict = err[~near]
     out = dict(

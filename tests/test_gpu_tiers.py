@@ -1,0 +1,57 @@
+"""Each precision tier of the exact (ungridded) evaluation against the oracle,
+on bins that include the sampling aliases of a seasonal, nightly window."""
+import numpy as np
+import pytest
+
+from paper_0901_1913_gb300 import synth
+from tests.parity import TOL, compare, sample_bins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fc2():
+    from paper_0901_1913_gb300 import _fc2
+    _fc2.load()
+    return _fc2
+
+
+@pytest.fixture(scope="module")
+def case(oracle_mod):
+    c = synth.config2(n=20000, N=1 << 18)
+    # half-integer cycles per day: the daily and yearly window peaks make the
+    # normal equations of those bins nearly singular
+    centres = [int(round((0.5 * m - c.f_min) / c.df)) for m in range(1, 12)]
+    centres.append(int(round((c.truth["f0"] - c.f_min) / c.df)))
+    bins = sample_bins(c.N, 120, 5, windows=centres, half=3)
+    ref, piv = oracle_mod.dchi2_bins(c.t, c.x, c.sigma, c.H, c.f_min, c.df, bins,
+                                     with_pivots=True)
+    _, _, chi0, _ = oracle_mod.moments(c.x, c.sigma)
+    return c, bins, ref, piv, chi0
+
+
+# (tier, tolerance relative to chi2_0, oracle pivot below which a bin only has
+# to respect the bounds).  Tier 1 (float sums) is only meant for well-posed bins.
+@pytest.mark.parametrize("tier,tol,near", [(1, TOL, 1e-3), (2, 1e-6, 1e-8), (3, 1e-8, 1e-8)])
+def test_tier_matches_oracle(fc2, case, tier, tol, near):
+    c, bins, ref, piv, chi0 = case
+    with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed") as p:
+        p.execute()
+        got = p.exact_bins(bins, tier).T
+    r = compare(got, ref, piv, chi0, tol=tol, near_alias=near)
+    print(tier, r)
+    assert r["ok"], (tier, r)
+
+
+def test_double_float_tracks_double(fc2, case):
+    """Tier 2 agrees with tier 3 far beyond the parity tolerance on every bin
+    whose oracle pivot is not at a rank decision."""
+    c, bins, ref, piv, chi0 = case
+    with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed") as p:
+        p.execute()
+        d2 = p.exact_bins(bins, 2).T
+        d3 = p.exact_bins(bins, 3).T
+    ok = piv >= 1e-8
+    err = np.abs(d2 - d3)[ok].max() / chi0
+    print("tier2 vs tier3", err)
+    assert err <= 1e-8
