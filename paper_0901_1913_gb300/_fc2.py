@@ -102,6 +102,8 @@ def load():
         lib.fc2_stage_times.restype = i32
         lib.fc2_debug_exact_bins.argtypes = [_P, _P, i64, i32, _P]
         lib.fc2_debug_exact_bins.restype = i32
+        lib.fc2_debug_tier_bins.argtypes = [_P, i32, _P, i64]
+        lib.fc2_debug_tier_bins.restype = i64
         lib.fc2_debug_t0.argtypes = [_P]
         lib.fc2_debug_t0.restype = dbl
         _lib = lib
@@ -213,6 +215,14 @@ class Plan:
         c = np.zeros(4, dtype=np.int64)
         load().fc2_debug_counts(self.h, c.ctypes.data)
         return tuple(int(v) for v in c)
+
+    def tier_bins(self, tier, cap=1 << 16):
+        """Bins of the last execute handled by fix-up tier 2 or 3."""
+        out = np.empty(cap, dtype=np.int64)
+        nb = load().fc2_debug_tier_bins(self.h, int(tier), out.ctypes.data, cap)
+        if nb < 0:
+            raise RuntimeError("tier_bins failed")
+        return out[:nb].copy()
 
     def exact_bins(self, bins, tier):
         """Delta chi^2 [H, len(bins)] at the given bins from the exact sums of one

@@ -178,7 +178,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     g.ok(dalloc(&p->d_part, exact_scratch_bytes(n, H, p->exact_cap), s)) &&
         g.ok(dalloc(&p->d_phA, (size_t)n * 8, s)) && g.ok(dalloc(&p->d_phB, (size_t)n * 8, s)) &&
         g.ok(dalloc(&p->d_wq32, (size_t)n * 8, s)) && g.ok(dalloc(&p->d_wp32, (size_t)n * 8, s)) &&
-        g.ok(dalloc(&p->d_dftab, 512 * 16, s));
+        g.ok(dalloc(&p->d_dftab, 2 * 512 * 16, s));
     if (g.e != cudaSuccess) {
         fc2_status st = map_err(g.e);
         free_plan_memory(p);
@@ -450,6 +450,20 @@ fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im) {
 }
 
 double fc2_debug_t0(fc2_plan p) { return p ? p->scal[SC_T0] : 0.0; }
+
+/* Bins of the last execute that tier `tier` (2 or 3) of the exact fix-up
+ * handled; returns how many were copied (at most cap), or -1. */
+int64_t fc2_debug_tier_bins(fc2_plan p, int tier, int64_t* out, int64_t cap) {
+    if (!p || !out || cap < 0 || (tier != 2 && tier != 3)) return -1;
+    const int64_t cnt = tier == 2 ? p->last_exact2_count : p->last_exact3_count;
+    const int64_t nb = std::min(cap, std::min(cnt, (int64_t)p->flag_cap));
+    std::vector<int32_t> b((size_t)std::max<int64_t>(nb, 1));
+    if (nb > 0 && cudaMemcpy(b.data(), p->d_flag_list + (size_t)(tier - 1) * p->flag_cap,
+                             (size_t)nb * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -1;
+    for (int64_t i = 0; i < nb; ++i) out[i] = b[(size_t)i];
+    return nb;
+}
 
 /* Delta chi^2 [H][nb] at the given bins from the exact sums of one tier
  * (1 float, 2 double-float, 3 double), for tests of each tier.  Overwrites

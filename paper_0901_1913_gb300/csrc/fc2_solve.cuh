@@ -118,6 +118,98 @@ FC2_D TC chol_solve(const Sys<TC, H>& S, TC tau, TC* out, TC* anorm2,
     return dmin;
 }
 
+// Warp-cooperative chol_solve<double> for one system per warp (all 32 lanes
+// call it with the same S): lane l holds row l of [alpha | beta] and the
+// factorisation is right-looking, so each double instruction of the warp does
+// up to m lanes of work (double instructions are expensive on this part
+// whatever the number of active lanes).  Every lane returns the same out[]
+// and minimum relative pivot.  With COEF, *anorm2 gets max over H' <= Hrun of
+// |A^{(H')}|^2 computed in float (it only feeds the error estimate).  With
+// coef != nullptr, coef[0..2Hc] gets the Hc-harmonic coefficients in double.
+template <int H, bool COEF>
+FC2_D double warp_chol_solve(const Sys<double, H>& S, double tau, double* out, double* anorm2,
+                             int Hrun = H, double* coef = nullptr, int Hc = 0) {
+    constexpr int m = 2 * H + 1;
+    static_assert(m <= 32, "one row per lane");
+    constexpr unsigned FULL = 0xffffffffu;
+    const int l = threadIdx.x & 31;
+    const bool act = l < m;
+    double a[m];
+#pragma unroll
+    for (int k = 0; k < m; ++k) a[k] = (act && k <= l) ? S.alpha(l, k) : 0.0;
+    const double all = act ? S.alpha(l, l) : 0.0;
+    double b = act ? S.beta(l) : 0.0;
+    double Lr[m], z[m], dinv[m];
+    double acc = 0.0;
+    float dmin = 1.0f;
+#pragma unroll
+    for (int k = 0; k < m; ++k) {
+        const double dk = __shfl_sync(FULL, a[k], k);
+        const double allk = __shfl_sync(FULL, all, k);
+        const double bk = __shfl_sync(FULL, b, k);
+        const bool keep = allk > 0.0 && dk > tau * allk;
+        const double di = keep ? rsqrt(dk) : 0.0;
+        dinv[k] = di;
+        const double zk = bk * di;
+        z[k] = zk;
+        const double Llk = (act && l > k) ? a[k] * di : 0.0;
+        Lr[k] = Llk;
+#pragma unroll
+        for (int j = k + 1; j < m; ++j) {
+            const double Ljk = __shfl_sync(FULL, Llk, j);
+            if (j <= l) a[j] = fma(-Llk, Ljk, a[j]);
+        }
+        b = fma(-Llk, zk, b);
+        const float rc = allk > 0.0 ? fmaxf((float)dk / (float)allk, 0.0f) : 0.0f;
+        dmin = fminf(dmin, rc);
+        if (k > 0) acc = fma(zk, zk, acc);
+        if (k > 0 && (k & 1) == 0) out[(k >> 1) - 1] = acc;
+    }
+    if constexpr (COEF) {
+        float Lf[m], zf[m], df[m];
+#pragma unroll
+        for (int k = 0; k < m; ++k) { Lf[k] = (float)Lr[k]; zf[k] = (float)z[k]; df[k] = (float)dinv[k]; }
+        float amax = 0.0f;
+#pragma unroll
+        for (int hp = 1; hp <= H; ++hp) {
+            if (hp > Hrun) break;
+            const int mp = 2 * hp + 1;
+            float mine = 0.0f, nrm = 0.0f;
+#pragma unroll
+            for (int k = m - 1; k >= 0; --k) {
+                if (k < mp) {
+                    float t = (l > k && l < mp) ? Lf[k] * mine : 0.0f;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+                    const float A = (zf[k] - t) * df[k];
+                    if (l == k) mine = A;
+                    nrm = fmaf(A, A, nrm);
+                }
+            }
+            amax = fmaxf(amax, nrm);
+        }
+        *anorm2 = (double)amax;
+    }
+    if (coef) {
+        const int mp = 2 * Hc + 1;
+        double mine = 0.0;
+#pragma unroll
+        for (int k = m - 1; k >= 0; --k) {
+            if (k < mp) {
+                double t = (l > k && l < mp) ? Lr[k] * mine : 0.0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+                const double A = (z[k] - t) * dinv[k];
+                if (l == k) mine = A;
+                coef[k] = A;
+            } else {
+                coef[k] = 0.0;
+            }
+        }
+    }
+    return (double)dmin;
+}
+
 // Error model of a result computed from an alpha and beta whose entries carry
 // absolute errors ~eps (normalised units): with A the coefficient vector,
 // dDelta = 2 A^T dbeta - A^T dalpha A, so |dDelta| <~ eps (m |A|^2 + 2 sqrt(m) |A|).
@@ -143,7 +235,8 @@ template <int HM>
 FC2_D void exact_sys_from_sums(const double* acc, int H, const double* __restrict__ scal,
                                Sys<double, HM>& S) {
     const double W = scal[SC_W], chi0 = scal[SC_CHI0];
-    const double sq = (chi0 > 0.0) ? 1.0 / sqrt(W * chi0) : 0.0;
+    const double sq = (chi0 > 0.0) ? rsqrt(W * chi0) : 0.0;
+    const double iw = 1.0 / W;
 #pragma unroll
     for (int k = 0; k <= 2 * HM; ++k) { S.qr[k] = 0.0; S.qi[k] = 0.0; }
 #pragma unroll
@@ -152,7 +245,7 @@ FC2_D void exact_sys_from_sums(const double* acc, int H, const double* __restric
     S.pr[0] = scal[SC_S1] * sq;
 #pragma unroll
     for (int k = 1; k <= 2 * HM; ++k)
-        if (k <= 2 * H) { S.qr[k] = acc[2 * (k - 1)] / W; S.qi[k] = acc[2 * (k - 1) + 1] / W; }
+        if (k <= 2 * H) { S.qr[k] = acc[2 * (k - 1)] * iw; S.qi[k] = acc[2 * (k - 1) + 1] * iw; }
 #pragma unroll
     for (int k = 1; k <= HM; ++k)
         if (k <= H) { S.pr[k] = acc[4 * HM + 2 * (k - 1)] * sq; S.pi[k] = acc[4 * HM + 2 * (k - 1) + 1] * sq; }

@@ -448,6 +448,46 @@ __global__ void k_phase(const double* __restrict__ tau, const double* __restrict
     cs[o] = mk<T>((T)(amp * cn), (T)(amp * sn));
 }
 
+// Mixed-precision phase reduction from the plan's exact fixed-point phases
+// A_i = frac(f_min tau_i) 2^64 and B_i = frac(df tau_i) 2^64: for harmonic k,
+// u_i 2^64 = k B_i and theta_i 2^64 = k A_i + hN k B_i, both exact modulo
+// 2^64 in integer arithmetic, so no double instruction is needed.  The cell
+// offset keeps 24 fraction bits (the spreading runs in float).
+__global__ void k_phase_fx32(const uint64_t* __restrict__ A, const uint64_t* __restrict__ B,
+                             const float* __restrict__ wq32, const float* __restrict__ wp32,
+                             int64_t n, int H, int64_t N, int logM, int w,
+                             int32_t* __restrict__ key, float* __restrict__ dlt,
+                             cpx<float>* __restrict__ cs) {
+    const int g = blockIdx.y;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    int k, kind;
+    if (g < 2 * H) { k = g + 1; kind = 0; } else { k = g - 2 * H + 1; kind = 1; }
+    const uint64_t uk = (uint64_t)k * B[s];
+    const int32_t cell = (int32_t)(uk >> (64 - logM));                 // floor(M u)
+    const float fx = (float)(uint32_t)((uk << logM) >> 40) * 5.9604644775390625e-08f;  // 2^-24
+    int32_t kk;
+    float de;
+    if ((w & 1) == 0) {
+        kk = cell - w / 2 + 1;
+        de = fx;
+    } else if (fx >= 0.5f) {
+        kk = cell - (w - 1) / 2 + 1;
+        de = fx - 0.5f;
+    } else {
+        kk = cell - (w - 1) / 2;
+        de = fx + 0.5f;
+    }
+    const uint64_t th = (uint64_t)k * A[s] + (uint64_t)(N / 2) * uk;
+    float sn, cn;
+    sincospif((float)(int32_t)(th >> 32) * 4.656612873077393e-10f, &sn, &cn);  // 2^-31
+    const float amp = kind == 0 ? wq32[s] : wp32[s];
+    const int64_t o = (int64_t)g * n + s;
+    key[o] = kk;
+    dlt[o] = de;
+    cs[o] = mk<float>(amp * cn, amp * sn);
+}
+
 // Keys of a wrapping transform are sorted with their payload by a stable
 // radix sort on the key (ties keep time order).
 __global__ void k_key_init(const int32_t* __restrict__ key, int64_t n, int32_t off,
@@ -511,8 +551,14 @@ static cudaError_t sort_keys_of(fc2_plan_s* p, int g, cudaStream_t s) {
 template <typename T>
 static cudaError_t phase_impl(fc2_plan_s* p, cudaStream_t s) {
     dim3 grid((unsigned)((p->n + 255) / 256), (unsigned)p->G);
-    k_phase<T><<<grid, 256, 0, s>>>(p->d_tau, p->d_wq, p->d_wp, p->n, p->H, p->f_min, p->df,
-                                    p->N, p->M, p->w, p->d_key, (T*)p->d_dlt, (cpx<T>*)p->d_cs);
+    if constexpr (sizeof(T) == 4)
+        k_phase_fx32<<<grid, 256, 0, s>>>(p->d_phA, p->d_phB, p->d_wq32, p->d_wp32, p->n, p->H,
+                                          p->N, p->logM, p->w, p->d_key, (float*)p->d_dlt,
+                                          (cpx<float>*)p->d_cs);
+    else
+        k_phase<T><<<grid, 256, 0, s>>>(p->d_tau, p->d_wq, p->d_wp, p->n, p->H, p->f_min, p->df,
+                                        p->N, p->M, p->w, p->d_key, (T*)p->d_dlt,
+                                        (cpx<T>*)p->d_cs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     for (int g = 0; g < p->G; ++g)

@@ -98,8 +98,9 @@ __global__ void __launch_bounds__(128) k_resolve(const cpx<float>* __restrict__ 
                                                  int32_t* __restrict__ fcount, int64_t fcap) {
     int64_t cnt = *rcount;
     if (cnt > rcap) cnt = rcap;
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < cnt;
-         b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t wpb = blockDim.x >> 5;
+    for (int64_t b = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); b < cnt;
+         b += (int64_t)gridDim.x * wpb) {
         const int64_t j = rlist[b];
         Sys<float, H> Sf;
         load_gridded<float, H>(spec, dec, sp.N, j, (float)sp.sq, (float)sp.sp, (float)sp.s1n, Sf);
@@ -109,13 +110,15 @@ __global__ void __launch_bounds__(128) k_resolve(const cpx<float>* __restrict__ 
 #pragma unroll
         for (int k = 0; k <= H; ++k) { S.pr[k] = Sf.pr[k]; S.pi[k] = Sf.pi[k]; }
         double out[H], an2 = 0.0;
-        chol_solve<double, H, true>(S, sp.tau, out, &an2);
-        if (!(est_err<double>(an2, 2 * H + 1, sp.eps_spec) <= sp.err_fix)) {
-            int32_t pos = atomicAdd(fcount, 1);
-            if (pos < fcap) flist[pos] = (int32_t)j;
-        }
+        warp_chol_solve<H, true>(S, sp.tau, out, &an2);
+        if ((threadIdx.x & 31) == 0) {
+            if (!(est_err<double>(an2, 2 * H + 1, sp.eps_spec) <= sp.err_fix)) {
+                int32_t pos = atomicAdd(fcount, 1);
+                if (pos < fcap) flist[pos] = (int32_t)j;
+            }
 #pragma unroll
-        for (int h = 0; h < H; ++h) dchi2[(int64_t)h * sp.N + j] = out[h] * sp.chi0;
+            for (int h = 0; h < H; ++h) dchi2[(int64_t)h * sp.N + j] = out[h] * sp.chi0;
+        }
     }
 }
 
@@ -172,20 +175,35 @@ __global__ void k_phase_fx(const double* __restrict__ tau, const double* __restr
     wp32[n + i] = (float)(wp[i] - (double)ph);
 }
 
-// Double-float tables e^{2 pi i a / 256} (entries 0..255) and
-// e^{2 pi i b / 65536} (entries 256..511) for df_phasor.
-__global__ void k_init_dftab(dfc* __restrict__ tab) {
+// Tables e^{2 pi i a / 256} (entries 0..255) and e^{2 pi i b / 65536}
+// (entries 256..511): double-float for df_phasor (tier 2), then the same in
+// double (tier 3).
+__global__ void k_init_dftab(dfc* __restrict__ tab, double2* __restrict__ tab64) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 512) return;
     const double x = (i < 256) ? (double)i / 128.0 : (double)(i - 256) / 32768.0;
     double sn, cn;
     sincospi(x, &sn, &cn);
     tab[i] = dfc{df_from_double(cn), df_from_double(sn)};
+    tab64[i] = make_double2(cn, sn);
+}
+
+// e^{2 pi i u 2^-64} in double from the same split as df_phasor: two table
+// factors times 1 - theta^2/2 + i (theta - theta^3/6), theta < 1e-4 (the
+// dropped terms are below 4e-18).
+FC2_D double2 d_phasor(uint64_t u, const double2* t1, const double2* t2) {
+    const double2 A = t1[(int)(u >> 56)], B = t2[(int)((u >> 48) & 255u)];
+    const double th = (double)(int64_t)(u & ((1ull << 48) - 1)) * 3.4061215800865545e-19;  // 2 pi 2^-64
+    const double th2 = th * th;
+    const double c = fma(-0.5, th2, 1.0);
+    const double s = fma(th * th2, -1.0 / 6.0, th);
+    const double pr = fma(A.x, B.x, -A.y * B.y), pi = fma(A.x, B.y, A.y * B.x);
+    return make_double2(fma(pr, c, -pi * s), fma(pr, s, pi * c));
 }
 
 // Lane 0 receives the warp's sum of (hi, lo) float pairs, added with
-// error-free two-sums.
-FC2_D double warp_sum_pair(float hi, float lo) {
+// error-free two-sums (all on the float pipes).
+FC2_D float2 warp_sum_pair(float hi, float lo) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const float h2 = __shfl_down_sync(0xffffffffu, hi, o);
@@ -194,7 +212,7 @@ FC2_D double warp_sum_pair(float hi, float lo) {
         hi = t.h;
         lo = lo + l2 + t.l;
     }
-    return (double)hi + (double)lo;
+    return make_float2(hi, lo);
 }
 
 template <int HM, int TIER>
@@ -206,8 +224,10 @@ __global__ void __launch_bounds__(EX_NT) k_exact_partial(
     const int32_t* __restrict__ count_dev, int64_t count, int64_t base, int64_t cap, int H,
     double* __restrict__ part) {
     constexpr int NV = 6 * HM;
-    __shared__ double red[EX_NT / 32][NV];
+    __shared__ double red[TIER == 3 ? EX_NT / 32 : 1][NV];
+    __shared__ float2 redf[TIER == 3 ? 1 : EX_NT / 32][NV];
     __shared__ dfc stab[TIER == 2 ? 512 : 1];
+    __shared__ double2 stab64[TIER == 3 ? 512 : 1];
     int64_t cnt = count_dev ? (int64_t)(*count_dev) - base : count;
     if (cnt > cap) cnt = cap;
     if (cnt <= 0) return;
@@ -218,6 +238,11 @@ __global__ void __launch_bounds__(EX_NT) k_exact_partial(
     const int lane = threadIdx.x & 31, wpi = threadIdx.x >> 5;
     if constexpr (TIER == 2) {
         for (int i = threadIdx.x; i < 512; i += EX_NT) stab[i] = dftab[i];
+        __syncthreads();
+    }
+    if constexpr (TIER == 3) {
+        const double2* t64 = reinterpret_cast<const double2*>(dftab + 512);
+        for (int i = threadIdx.x; i < 512; i += EX_NT) stab64[i] = t64[i];
         __syncthreads();
     }
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
@@ -251,8 +276,8 @@ __global__ void __launch_bounds__(EX_NT) k_exact_partial(
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const double x = warp_sum_pair(fa[v].s, fa[v].c);
-                if (lane == 0) red[wpi][v] = x;
+                const float2 x = warp_sum_pair(fa[v].s, fa[v].c);
+                if (lane == 0) redf[wpi][v] = x;
             }
         } else if constexpr (TIER == 2) {
             dfl fa[NV];
@@ -278,17 +303,16 @@ __global__ void __launch_bounds__(EX_NT) k_exact_partial(
             }
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const double x = warp_sum_pair(fa[v].h, fa[v].l);
-                if (lane == 0) red[wpi][v] = x;
+                const float2 x = warp_sum_pair(fa[v].h, fa[v].l);
+                if (lane == 0) redf[wpi][v] = x;
             }
         } else {
             double acc[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) acc[v] = 0.0;
             for (int64_t i = i0 + threadIdx.x; i < i1; i += EX_NT) {
-                const int64_t ph = (int64_t)(Aph[i] + ju * Bph[i]);
-                double s1, c1;
-                sincospi(ldexp((double)ph, -63), &s1, &c1);
+                const double2 z1 = d_phasor(Aph[i] + ju * Bph[i], stab64, stab64 + 256);
+                const double c1 = z1.x, s1 = z1.y;
                 double cr = c1, ci = s1;
                 const double a = wq[i], bb = wp[i];
 #pragma unroll
@@ -318,8 +342,20 @@ __global__ void __launch_bounds__(EX_NT) k_exact_partial(
         __syncthreads();
         if (threadIdx.x < NV) {
             double x = 0.0;
+            if constexpr (TIER == 3) {
 #pragma unroll
-            for (int q = 0; q < EX_NT / 32; ++q) x += red[q][threadIdx.x];
+                for (int q = 0; q < EX_NT / 32; ++q) x += red[q][threadIdx.x];
+            } else {
+                float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+                for (int q = 0; q < EX_NT / 32; ++q) {
+                    const float2 y = redf[q][threadIdx.x];
+                    const dfl t = df_two_sum(hi, y.x);
+                    hi = t.h;
+                    lo += y.y + t.l;
+                }
+                x = (double)hi + (double)lo;
+            }
             part[((b * nch) + c) * NV + threadIdx.x] = x;
         }
         __syncthreads();
@@ -327,9 +363,10 @@ __global__ void __launch_bounds__(EX_NT) k_exact_partial(
 }
 
 // Warp w of the CTA owns record b: lanes add the chunk partials of values
-// v = lane, lane + 32, ... in chunk order, then lane 0 holds the full sums.
+// v = lane, lane + 32, ... in chunk order into sh[], then every lane of the
+// warp can read the full sums.
 template <int HM>
-FC2_D bool warp_sum_chunks(const double* __restrict__ part, int64_t b, int nch, double* sh) {
+FC2_D void warp_sum_chunks(const double* __restrict__ part, int64_t b, int nch, double* sh) {
     constexpr int NV = 6 * HM;
     const int lane = threadIdx.x & 31;
     for (int v = lane; v < NV; v += 32) {
@@ -338,7 +375,6 @@ FC2_D bool warp_sum_chunks(const double* __restrict__ part, int64_t b, int nch, 
         sh[v] = a;
     }
     __syncwarp();
-    return lane == 0;
 }
 
 // Final step of a fix-up round: solve from the exact sums; bins whose
@@ -356,17 +392,18 @@ __global__ void __launch_bounds__(128) k_exact_dchi2(const double* __restrict__ 
     int64_t cnt = (int64_t)(*count_dev) - base;
     if (cnt > cap) cnt = cap;
     const int w = threadIdx.x >> 5;
-    const int64_t b = (int64_t)blockIdx.x * 4 + w;
+    const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + w;  // one system per warp
     if (b >= cnt) return;
     int64_t chunk;
     int nch;
     exact_geometry(n, cnt, &chunk, &nch);
-    if (!warp_sum_chunks<H>(part, b, nch, sh[w])) return;
+    warp_sum_chunks<H>(part, b, nch, sh[w]);
     const int64_t j = list[base + b];
     Sys<double, H> S;
     exact_sys_from_sums<H>(sh[w], H, scal, S);
     double out[H], an2 = 0.0;
-    chol_solve<double, H, true>(S, tau_drop, out, &an2);
+    warp_chol_solve<H, true>(S, tau_drop, out, &an2);
+    if ((threadIdx.x & 31) != 0) return;
     if (next && !(est_err<double>(an2, 2 * H + 1, eps_sums) <= err_fix)) {
         int32_t pos = atomicAdd(next_count, 1);
         if (pos < next_cap) next[pos] = (int32_t)j;
@@ -386,28 +423,24 @@ __global__ void __launch_bounds__(128) k_exact_coeffs(const double* __restrict__
                                double tau_drop, fc2_best* __restrict__ out) {
     __shared__ double sh[4][6 * HM];
     const int w = threadIdx.x >> 5;
-    const int r = blockIdx.x * 4 + w;
+    const int r = blockIdx.x * (blockDim.x >> 5) + w;
     if (r >= nrec) return;
-    if (!warp_sum_chunks<HM>(part, r, nch, sh[w])) return;
+    warp_sum_chunks<HM>(part, r, nch, sh[w]);
     const int64_t j = rec_j[r];
     const int Hp = (r < H) ? r + 1 : H;  // best[h] has h + 1 harmonics; peaks have H
     fc2_best b;
     b.j = j; b.f = 0; b.dchi2 = 0; b.H = Hp; b.flags = 0;
     for (int l = 0; l < 2 * FC2_MAX_H + 1; ++l) b.A[l] = 0.0;
-    if (j < 0) { out[r] = b; return; }
+    if (j < 0) {
+        if ((threadIdx.x & 31) == 0) out[r] = b;
+        return;
+    }
     Sys<double, HM> S;
     exact_sys_from_sums<HM>(sh[w], H, scal, S);
     double outv[HM], an2;
-    double Lk[2 * HM + 1][2 * HM + 1];
-    double zk[2 * HM + 1];
-    chol_solve<double, HM, false>(S, tau_drop, outv, &an2, Lk, zk);
-    const int m = 2 * Hp + 1;
     double A[2 * HM + 1];
-    for (int l = m - 1; l >= 0; --l) {
-        double a = zk[l];
-        for (int k = l + 1; k < m; ++k) a -= Lk[k][l] * A[k];
-        A[l] = (Lk[l][l] > 0.0) ? a / Lk[l][l] : 0.0;
-    }
+    warp_chol_solve<HM, false>(S, tau_drop, outv, &an2, H, A, Hp);
+    if ((threadIdx.x & 31) != 0) return;
     const double W = scal[SC_W], chi0 = scal[SC_CHI0];
     const double unit = (W > 0.0) ? sqrt(chi0 / W) : 0.0;
     const double f = f_min + (double)j * df;
@@ -431,21 +464,26 @@ constexpr int PK_NT = 256;
 constexpr int PK_PER = 16;
 constexpr int PK_B = PK_NT * PK_PER;
 constexpr int PK_NW = PK_NT / 32;
-constexpr int PK_KMAX = 64;
 
+// Top-K local maxima by a threshold: the K-th best of the per-block best
+// local maxima, theta, is a lower bound of the K-th best local maximum overall
+// (those K block maxima are K distinct local maxima >= theta), so the global
+// top K are among the local maxima >= theta, which lie in at most K blocks.
+// Order everywhere: key desc, then j asc (key = okey(value)).
+//
 // Stage 1: per block of PK_B bins, the argmax of every row (ties -> lowest j)
-// and the top-K local maxima of row H (value > left, >= right; edges one-sided).
+// and the best local maximum of row H (value > left, >= right; edges
+// one-sided).
 __global__ void __launch_bounds__(PK_NT) k_peaks1(const double* __restrict__ d, int64_t N, int H,
-                                                  int K, Cand* __restrict__ amax,
-                                                  Cand* __restrict__ tops, int nblk) {
-    __shared__ Cand wres[PK_NW][FC2_MAX_H];
-    __shared__ Cand wtop[PK_NW][PK_KMAX];
+                                                  Cand* __restrict__ amax,
+                                                  Cand* __restrict__ bmax, int nblk) {
+    __shared__ Cand wres[PK_NW][FC2_MAX_H + 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t base = (int64_t)blockIdx.x * PK_B;
     for (int h = 0; h < H; ++h) {
         const double* row = d + (int64_t)h * N;
         int64_t v = KEY_NONE, j = INT64_MAX;
-#pragma unroll 8
+#pragma unroll
         for (int q = 0; q < PK_PER; ++q) {
             const int64_t jj = base + threadIdx.x + (int64_t)q * PK_NT;
             if (jj < N) {
@@ -456,30 +494,21 @@ __global__ void __launch_bounds__(PK_NT) k_peaks1(const double* __restrict__ d, 
         warp_best(v, j);
         if (lane == 0) wres[w][h] = Cand{v, j};
     }
-    const double* row = d + (int64_t)(H - 1) * N;
-    int64_t cv[PK_PER], cj[PK_PER];
-#pragma unroll
-    for (int q = 0; q < PK_PER; ++q) {
-        const int64_t jj = base + lane + (int64_t)(w * PK_PER + q) * 32;  // warp-contiguous
-        cv[q] = KEY_NONE;
-        cj[q] = INT64_MAX;
-        if (jj < N) {
-            const int64_t x = okey(row[jj]);
-            const bool left = (jj == 0) || (x > okey(row[jj - 1]));
-            const bool right = (jj == N - 1) || (x >= okey(row[jj + 1]));
-            if (left && right) { cv[q] = x; cj[q] = jj; }
-        }
-    }
-    for (int r = 0; r < K; ++r) {
+    {
+        const double* row = d + (int64_t)(H - 1) * N;
         int64_t v = KEY_NONE, j = INT64_MAX;
 #pragma unroll
-        for (int q = 0; q < PK_PER; ++q)
-            if (better(cv[q], cj[q], v, j)) { v = cv[q]; j = cj[q]; }
+        for (int q = 0; q < PK_PER; ++q) {
+            const int64_t jj = base + threadIdx.x + (int64_t)q * PK_NT;
+            if (jj < N) {
+                const int64_t x = okey(row[jj]);
+                const bool left = (jj == 0) || (x > okey(row[jj - 1]));
+                const bool right = (jj == N - 1) || (x >= okey(row[jj + 1]));
+                if (left && right && better(x, jj, v, j)) { v = x; j = jj; }
+            }
+        }
         warp_best(v, j);
-#pragma unroll
-        for (int q = 0; q < PK_PER; ++q)
-            if (cj[q] == j) { cv[q] = KEY_NONE; cj[q] = INT64_MAX; }
-        if (lane == 0) wtop[w][r] = Cand{v, j};
+        if (lane == 0) wres[w][FC2_MAX_H] = Cand{v, j};
     }
     __syncthreads();
     if (w == 0) {
@@ -489,70 +518,118 @@ __global__ void __launch_bounds__(PK_NT) k_peaks1(const double* __restrict__ d, 
             warp_best(v, j);
             if (lane == 0) amax[(int64_t)h * nblk + blockIdx.x] = Cand{v, j};
         }
-        // merge the warps' sorted lists: K rounds, lane q < PK_NW looks at the
-        // head of warp q's list
-        int head = 0;
-        for (int r = 0; r < K; ++r) {
-            int64_t v = KEY_NONE, j = INT64_MAX;
-            if (lane < PK_NW && head < K) { v = wtop[lane][head].k; j = wtop[lane][head].j; }
-            const int64_t mj = j;
-            warp_best(v, j);
-            if (lane < PK_NW && mj == j && j != INT64_MAX) ++head;
-            if (lane == 0) tops[(int64_t)blockIdx.x * K + r] = Cand{v, j};
-        }
+        int64_t v = lane < PK_NW ? wres[lane][FC2_MAX_H].k : KEY_NONE;
+        int64_t j = lane < PK_NW ? wres[lane][FC2_MAX_H].j : INT64_MAX;
+        warp_best(v, j);
+        if (lane == 0) bmax[blockIdx.x] = Cand{v, j};
     }
 }
 
-// Stage 2: one block merges the per-block results.
-__global__ void __launch_bounds__(1024) k_peaks2(const Cand* __restrict__ amax,
-                                                 const Cand* __restrict__ tops, int nblk, int H,
-                                                 int K, int64_t* __restrict__ best_j,
-                                                 int64_t* __restrict__ peak_j) {
-    __shared__ Cand ws[32];
+// Block-wide best of (v, j) over the CTA (blockDim.x <= 1024); every thread
+// gets the winner.
+FC2_D Cand block_best(int64_t v, int64_t j, Cand* ws) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    warp_best(v, j);
+    if (lane == 0) ws[w] = Cand{v, j};
+    __syncthreads();
+    if (w == 0) {
+        v = lane < nw ? ws[lane].k : KEY_NONE;
+        j = lane < nw ? ws[lane].j : INT64_MAX;
+        warp_best(v, j);
+        if (lane == 0) ws[32] = Cand{v, j};
+    }
+    __syncthreads();
+    const Cand r = ws[32];
+    __syncthreads();
+    return r;
+}
+
+// Stage 2 (one CTA): best bin of every row, and theta = the K-th best block
+// maximum (K rounds, each excluding what the previous rounds took).
+__global__ void __launch_bounds__(1024) k_peaks2(const Cand* __restrict__ amax,
+                                                 const Cand* __restrict__ bmax, int nblk, int H,
+                                                 int K, int64_t* __restrict__ best_j,
+                                                 Cand* __restrict__ theta,
+                                                 int32_t* __restrict__ ncand) {
+    __shared__ Cand ws[33];
     for (int h = 0; h < H; ++h) {
         int64_t v = KEY_NONE, j = INT64_MAX;
         for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
             const Cand c = amax[(int64_t)h * nblk + b];
             if (better(c.k, c.j, v, j)) { v = c.k; j = c.j; }
         }
-        warp_best(v, j);
-        if (lane == 0) ws[w] = Cand{v, j};
-        __syncthreads();
-        if (w == 0) {
-            v = lane < nw ? ws[lane].k : KEY_NONE;
-            j = lane < nw ? ws[lane].j : INT64_MAX;
-            warp_best(v, j);
-            if (lane == 0) best_j[h] = (j == INT64_MAX) ? -1 : j;
-        }
-        __syncthreads();
+        const Cand r = block_best(v, j, ws);
+        if (threadIdx.x == 0) best_j[h] = (r.j == INT64_MAX) ? -1 : r.j;
     }
-    // each block's list is sorted, so K rounds of "best head" merge them
-    const int64_t total = (int64_t)nblk * K;
     int64_t pv = INT64_MAX, pj = -1;
+    Cand th{KEY_NONE, INT64_MAX};
     for (int r = 0; r < K; ++r) {
         int64_t v = KEY_NONE, j = INT64_MAX;
-        for (int64_t b = threadIdx.x; b < total; b += blockDim.x) {
-            const Cand c = tops[b];
+        for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+            const Cand c = bmax[b];
             if (c.j != INT64_MAX && better(pv, pj, c.k, c.j) && better(c.k, c.j, v, j)) {
                 v = c.k;
                 j = c.j;
             }
         }
-        warp_best(v, j);
-        if (lane == 0) ws[w] = Cand{v, j};
-        __syncthreads();
-        if (w == 0) {
-            v = lane < nw ? ws[lane].k : KEY_NONE;
-            j = lane < nw ? ws[lane].j : INT64_MAX;
-            warp_best(v, j);
-            if (lane == 0) { ws[0] = Cand{v, j}; peak_j[r] = (j == INT64_MAX) ? -1 : j; }
+        const Cand c = block_best(v, j, ws);
+        if (c.j == INT64_MAX) {  // fewer than K blocks hold a local maximum: keep them all
+            th = Cand{KEY_NONE, INT64_MAX};
+            break;
         }
-        __syncthreads();
-        pv = ws[0].k;
-        pj = ws[0].j;
-        __syncthreads();
-        if (pj == INT64_MAX) pv = KEY_NONE;
+        th = c;
+        pv = c.k;
+        pj = c.j;
+    }
+    if (threadIdx.x == 0) {
+        *theta = th;
+        *ncand = 0;
+    }
+}
+
+// Stage 3: blocks whose best local maximum reaches theta list their local
+// maxima that do (at most K blocks, PK_B / 2 maxima each, so `cap` =
+// K PK_B / 2 entries never overflow).
+__global__ void __launch_bounds__(PK_NT) k_peaks3(const double* __restrict__ d, int64_t N, int H,
+                                                  const Cand* __restrict__ bmax,
+                                                  const Cand* __restrict__ theta,
+                                                  Cand* __restrict__ cand,
+                                                  int32_t* __restrict__ ncand, int cap) {
+    const Cand th = *theta;
+    const Cand bm = bmax[blockIdx.x];
+    if (bm.j == INT64_MAX || better(th.k, th.j, bm.k, bm.j)) return;
+    const double* row = d + (int64_t)(H - 1) * N;
+    const int64_t base = (int64_t)blockIdx.x * PK_B;
+    for (int q = 0; q < PK_PER; ++q) {
+        const int64_t jj = base + threadIdx.x + (int64_t)q * PK_NT;
+        if (jj >= N) break;
+        const int64_t x = okey(row[jj]);
+        const bool left = (jj == 0) || (x > okey(row[jj - 1]));
+        const bool right = (jj == N - 1) || (x >= okey(row[jj + 1]));
+        if (left && right && !better(th.k, th.j, x, jj)) {
+            const int32_t pos = atomicAdd(ncand, 1);
+            if (pos < cap) cand[pos] = Cand{x, jj};
+        }
+    }
+}
+
+// Stage 4 (one CTA): the K best candidates in order.
+__global__ void __launch_bounds__(1024) k_peaks4(const Cand* __restrict__ cand,
+                                                 const int32_t* __restrict__ ncand, int cap,
+                                                 int K, int64_t* __restrict__ peak_j) {
+    __shared__ Cand ws[33];
+    const int64_t total = min((int64_t)*ncand, (int64_t)cap);
+    int64_t pv = INT64_MAX, pj = -1;
+    for (int r = 0; r < K; ++r) {
+        int64_t v = KEY_NONE, j = INT64_MAX;
+        for (int64_t b = threadIdx.x; b < total; b += blockDim.x) {
+            const Cand c = cand[b];
+            if (better(pv, pj, c.k, c.j) && better(c.k, c.j, v, j)) { v = c.k; j = c.j; }
+        }
+        const Cand c = block_best(v, j, ws);
+        if (threadIdx.x == 0) peak_j[r] = (c.j == INT64_MAX) ? -1 : c.j;
+        pv = c.j == INT64_MAX ? KEY_NONE : c.k;
+        pj = c.j;
     }
 }
 
@@ -587,7 +664,7 @@ static cudaError_t assemble_impl(fc2_plan_s* p, cudaStream_t s) {
         k_assemble<TS, HH><<<grid, 128, 0, s>>>(spec, dec, p->d_dchi2, sp, list, cnt,         \
                                                 p->flag_cap);                                 \
         if (!p->fp64)                                                                         \
-            k_resolve<HH><<<4 * 152, 128, 0, s>>>((const cpx<float>*)spec, (const float*)dec, \
+            k_resolve<HH><<<8 * 152, 32, 0, s>>>((const cpx<float>*)spec, (const float*)dec, \
                                                   p->d_dchi2, sp, list, cnt, p->flag_cap,     \
                                                   p->d_flag_list, p->d_flag_count,            \
                                                   p->flag_cap);                               \
@@ -635,23 +712,23 @@ static cudaError_t fixup_h(fc2_plan_s* p, int64_t count, cudaStream_t s) {
     cudaMemsetAsync(cnt2, 0, 8, s);
     if (count <= 0) return cudaGetLastError();
     for (int64_t base = 0; base < count; base += cap) {
-        const unsigned blocks = (unsigned)((std::min(cap, count - base) + 3) / 4);
+        const unsigned blocks = (unsigned)std::min(cap, count - base);
         launch_partial<HH, 1>(p, list1, nullptr, cnt1, 0, base, cap, s);
-        k_exact_dchi2<HH><<<blocks, 128, 0, s>>>(p->d_part, p->n, list1, cnt1, base, cap, p->d_scal,
+        k_exact_dchi2<HH><<<blocks, 32, 0, s>>>(p->d_part, p->n, list1, cnt1, base, cap, p->d_scal,
                                                  1e-13, eps_t1, ERR_FIX, list2, cnt2, p->flag_cap,
                                                  p->d_dchi2, p->N);
     }
     for (int64_t base = 0; base < count; base += cap) {
-        const unsigned blocks = (unsigned)((std::min(cap, count - base) + 3) / 4);
+        const unsigned blocks = (unsigned)std::min(cap, count - base);
         launch_partial<HH, 2>(p, list2, nullptr, cnt2, 0, base, cap, s);
-        k_exact_dchi2<HH><<<blocks, 128, 0, s>>>(p->d_part, p->n, list2, cnt2, base, cap, p->d_scal,
+        k_exact_dchi2<HH><<<blocks, 32, 0, s>>>(p->d_part, p->n, list2, cnt2, base, cap, p->d_scal,
                                                  1e-13, EPS_DF, ERR_FIX, list3, cnt3, p->flag_cap,
                                                  p->d_dchi2, p->N);
     }
     for (int64_t base = 0; base < count; base += cap) {
-        const unsigned blocks = (unsigned)((std::min(cap, count - base) + 3) / 4);
+        const unsigned blocks = (unsigned)std::min(cap, count - base);
         launch_partial<HH, 3>(p, list3, nullptr, cnt3, 0, base, cap, s);
-        k_exact_dchi2<HH><<<blocks, 128, 0, s>>>(p->d_part, p->n, list3, cnt3, base, cap, p->d_scal,
+        k_exact_dchi2<HH><<<blocks, 32, 0, s>>>(p->d_part, p->n, list3, cnt3, base, cap, p->d_scal,
                                                  1e-13, 0.0, ERR_FIX, nullptr, nullptr, 0,
                                                  p->d_dchi2, p->N);
     }
@@ -663,14 +740,14 @@ static cudaError_t fixup_h(fc2_plan_s* p, int64_t count, cudaStream_t s) {
 template <int HH>
 static cudaError_t exact_bins_h(fc2_plan_s* p, int64_t nb, int tier, cudaStream_t s) {
     int32_t* list = p->d_flag_list;
-    const unsigned blocks = (unsigned)((nb + 3) / 4);
+    const unsigned blocks = (unsigned)nb;
     if (tier == 1) launch_partial<HH, 1>(p, list, nullptr, nullptr, nb, 0, nb, s);
     else if (tier == 2) launch_partial<HH, 2>(p, list, nullptr, nullptr, nb, 0, nb, s);
     else launch_partial<HH, 3>(p, list, nullptr, nullptr, nb, 0, nb, s);
     int32_t* cnt = p->d_flag_count + 3;
     const int32_t nb32 = (int32_t)nb;
     cudaMemcpyAsync(cnt, &nb32, 4, cudaMemcpyHostToDevice, s);
-    k_exact_dchi2<HH><<<blocks, 128, 0, s>>>(p->d_part, p->n, list, cnt, 0, nb, p->d_scal, 1e-13,
+    k_exact_dchi2<HH><<<blocks, 32, 0, s>>>(p->d_part, p->n, list, cnt, 0, nb, p->d_scal, 1e-13,
                                              0.0, ERR_FIX, nullptr, nullptr, 0, p->d_dchi2, p->N);
     return cudaStreamSynchronize(s);
 }
@@ -703,20 +780,28 @@ cudaError_t launch_fixup(fc2_plan_s* p, int64_t count, cudaStream_t s) {
     }
 }
 
+// Scratch of the peak search: amax [H][nblk], bmax [nblk], theta, the
+// candidate count and list [K PK_B / 2], then the record bins [H + K].
+static int64_t peaks_cap(int K) { return (int64_t)K * (PK_B / 2); }
 size_t peaks_scratch_bytes(int64_t N, int H, int K) {
-    int64_t nblk = (N + PK_B - 1) / PK_B;
-    return (size_t)nblk * (H + K) * sizeof(Cand) + (size_t)(H + K) * 16 + 4096;
+    const int64_t nblk = (N + PK_B - 1) / PK_B;
+    return (size_t)(nblk * (H + 1) + 2 + peaks_cap(K)) * sizeof(Cand) + (size_t)(H + K) * 8 + 4096;
 }
 
 cudaError_t launch_peaks(fc2_plan_s* p, cudaStream_t s) {
     const int64_t nblk = (p->N + PK_B - 1) / PK_B;
     const int H = p->H, K = p->top_k;
-    char* base = (char*)p->d_red;
-    Cand* amax = (Cand*)base;
-    Cand* tops = amax + nblk * H;
-    int64_t* rec_j = (int64_t*)(tops + nblk * K);
-    k_peaks1<<<(unsigned)nblk, PK_NT, 0, s>>>(p->d_dchi2, p->N, H, K, amax, tops, (int)nblk);
-    k_peaks2<<<1, 1024, 0, s>>>(amax, tops, (int)nblk, H, K, rec_j, rec_j + H);
+    const int cap = (int)peaks_cap(K);
+    Cand* amax = (Cand*)p->d_red;
+    Cand* bmax = amax + nblk * H;
+    Cand* theta = bmax + nblk;
+    int32_t* ncand = (int32_t*)(theta + 1);
+    Cand* cand = theta + 2;
+    int64_t* rec_j = (int64_t*)(cand + cap);
+    k_peaks1<<<(unsigned)nblk, PK_NT, 0, s>>>(p->d_dchi2, p->N, H, amax, bmax, (int)nblk);
+    k_peaks2<<<1, 1024, 0, s>>>(amax, bmax, (int)nblk, H, K, rec_j, theta, ncand);
+    k_peaks3<<<(unsigned)nblk, PK_NT, 0, s>>>(p->d_dchi2, p->N, H, bmax, theta, cand, ncand, cap);
+    k_peaks4<<<1, 1024, 0, s>>>(cand, ncand, cap, K, rec_j + H);
     const int nrec = H + K;
     int64_t chunk;
     int nch;
@@ -724,7 +809,7 @@ cudaError_t launch_peaks(fc2_plan_s* p, cudaStream_t s) {
 #define FC2_CO(HH)                                                                            \
     case HH:                                                                                  \
         launch_partial<HH, 1>(p, nullptr, rec_j, nullptr, nrec, 0, nrec, s);               \
-        k_exact_coeffs<HH><<<(nrec + 3) / 4, 128, 0, s>>>(p->d_part, nch, rec_j, nrec, H, p->d_scal,        \
+        k_exact_coeffs<HH><<<nrec, 32, 0, s>>>(p->d_part, nch, rec_j, nrec, H, p->d_scal,        \
                                             p->f_min, p->df, 1e-13, p->d_best);               \
         break;
     switch (H) {
@@ -739,7 +824,7 @@ cudaError_t launch_phase_fx(fc2_plan_s* p, cudaStream_t s) {
     k_phase_fx<<<(unsigned)((p->n + 255) / 256), 256, 0, s>>>(p->d_tau, p->d_wq, p->d_wp, p->n,
                                                              p->f_min, p->df, p->d_phA, p->d_phB,
                                                              p->d_wq32, p->d_wp32);
-    k_init_dftab<<<2, 256, 0, s>>>((dfc*)p->d_dftab);
+    k_init_dftab<<<2, 256, 0, s>>>((dfc*)p->d_dftab, (double2*)((dfc*)p->d_dftab + 512));
     return cudaGetLastError();
 }
 
@@ -918,13 +1003,14 @@ __global__ void __launch_bounds__(128) k_na_final(int64_t nb, int nch, int H, do
                                                   double* __restrict__ scr) {
     __shared__ double sh[4][6 * HM];
     const int w = threadIdx.x >> 5;
-    const int64_t b = (int64_t)blockIdx.x * 4 + w;
+    const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + w;  // one system per warp
     if (b >= nb) return;
-    if (!warp_sum_chunks<HM>(scr + NA_PART_OFF, b, nch, sh[w])) return;
+    warp_sum_chunks<HM>(scr + NA_PART_OFF, b, nch, sh[w]);
     Sys<double, HM> S;
     exact_sys_from_sums<HM>(sh[w], H, scr, S);
     double o[HM], an2 = 0.0;
-    chol_solve<double, HM, false>(S, tau_drop, o, &an2);
+    warp_chol_solve<HM, false>(S, tau_drop, o, &an2);
+    if ((threadIdx.x & 31) != 0) return;
     const double chi0 = scr[SC_CHI0];
     for (int h = 0; h < H; ++h) out[(int64_t)h * nb + b] = o[h] * chi0;
 }
@@ -935,7 +1021,7 @@ void na_launch(const double* t, const double* x, const double* sg, int64_t n, in
                double* scr, cudaStream_t s) {
     k_na_partial<HM><<<4 * 152, NA_NT, 0, s>>>(t, x, sg, n, H, f_min, df, bins, nb, chunk, nch,
                                                 scr);
-    k_na_final<HM><<<(unsigned)((nb + 3) / 4), 128, 0, s>>>(nb, nch, H, 1e-13, out, scr);
+    k_na_final<HM><<<(unsigned)nb, 32, 0, s>>>(nb, nch, H, 1e-13, out, scr);
 }
 
 }  // namespace

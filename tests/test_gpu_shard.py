@@ -1,0 +1,43 @@
+"""Band sharding of one curve, with the bands run one after another on one
+GPU: the concatenated bands and the merged records match the unsharded run."""
+import numpy as np
+import pytest
+
+from paper_0901_1913_gb300 import shard, synth
+from tests.parity import TOL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fc2():
+    from paper_0901_1913_gb300 import _fc2
+    _fc2.load()
+    return _fc2
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_bands_match_unsharded(fc2, world):
+    c = synth.config2(n=20000, N=1 << 16)
+    K = 8
+    with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed",
+                  top_k=K) as p:
+        d_full, best_full, peaks_full, chi0 = p.execute()
+    recs, parts = [], []
+    for band in shard.band_partition(c.N, world):
+        fm, nb = shard.band_curve_args(c.f_min, c.df, band)
+        with fc2.Plan(c.t, c.x, c.sigma, c.H, fm, c.df, nb, c.oversample, "mixed",
+                      top_k=K + 2) as p:
+            d, best, peaks, _ = p.execute()
+        recs.append(shard.band_record(band, best, peaks, (d[-1, 0], d[-1, -1])))
+        parts.append(d)
+    d_cat = np.concatenate(parts, axis=1)
+    # both runs are within TOL chi2_0 of the exact values
+    assert np.max(np.abs(d_cat - d_full)) <= 2 * TOL * chi0
+    best, peaks = shard.merge_records(recs, K)
+    for h in range(c.H):
+        j1, j2 = best[h]["j"], best_full[h]["j"]
+        assert j1 == j2 or abs(d_full[h, j1] - d_full[h, j2]) <= 2 * TOL * chi0
+    full_j = [q["j"] for q in peaks_full]
+    for q, r in zip(peaks, peaks_full):
+        assert q["j"] in full_j or abs(q["dchi2"] - r["dchi2"]) <= 2 * TOL * chi0
