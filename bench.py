@@ -276,7 +276,7 @@ def run_gpu(args):
     except Exception:
         traffic = None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "kernel": "k_fft_pass (2 passes/step)",
+            "frac": achieved / peak, "traffic": traffic, "kernel": "k_fft_pass64 (2 passes/step)",
             "algorithmic_bytes_per_launch": fft_bytes / P, "launch_ms": fft_ms / P,
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
 

@@ -115,7 +115,7 @@ template <typename TS, int H>
 __global__ void __launch_bounds__(128) k_bassemble(const cpx<TS>* __restrict__ spec,
                                                    const TS* __restrict__ dec, int64_t N,
                                                    const int* __restrict__ curves, CurveTab ct,
-                                                   double tau, double eps, double err_fix,
+                                                   TS tau, TS eps, TS err_fix,
                                                    float* __restrict__ out,
                                                    int64_t* __restrict__ list,
                                                    int32_t* __restrict__ list_count,
@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(128) k_bassemble(const cpx<TS>* __restrict__ s
         S.pi[k] = v.y * dp;
     }
     TS o[H], an2 = (TS)0;
-    chol_solve<TS, H, true>(S, (TS)tau, o, &an2);
-    if (!(est_err<TS>(an2, 2 * H + 1, (TS)eps) <= (TS)err_fix)) {
+    chol_solve<TS, H, true>(S, tau, o, &an2);
+    if (!(est_err<TS>(an2, 2 * H + 1, eps) <= err_fix)) {
         const int32_t pos = atomicAdd(list_count, 1);
         if (pos < cap) list[pos] = ((int64_t)c << 32) | j;
     }
@@ -598,7 +598,8 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
 #define FC2_BASM(HH)                                                                          \
     case HH:                                                                                  \
         k_bassemble<T, HH><<<ga, 128, 0, s>>>((const cpx<T>*)p.d_spec, (const T*)p.d_dec, N,  \
-                                              cl, ct, tau_drop, eps, err_fix, out, first_list, \
+                                              cl, ct, (T)tau_drop, (T)eps, (T)err_fix, out,   \
+                                              first_list,                                     \
                                               first_cnt, first_cap);                          \
         break;
         switch (Hh) {

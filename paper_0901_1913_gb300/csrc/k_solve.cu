@@ -32,7 +32,48 @@ struct SolveParams {
     double eps_f32;    // extra error of a float factorisation
     double err_fix;    // bins whose estimated normalised error exceeds this are recomputed
     double sq, sp, chi0, s1n;  // 1/W, 1/sqrt(W chi2_0), chi2_0, sum w(x - xbar) / sqrt(W chi2_0)
+    // float copies for the float path (a conversion per thread would run on the
+    // double pipe): sq, sp, chi0, s1n, tau, eps_spec + eps_f32, err_fix
+    float fsq, fsp, fchi0, fs1n, ftau, feps, ferr;
 };
+
+// Exact float -> double conversion on the integer pipes (the double pipe of
+// this part is narrow).  Handles zeros, subnormals, infinities and NaN.
+FC2_D double f2d_exact(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint64_t sign = (uint64_t)(b >> 31) << 63;
+    uint32_t e = (b >> 23) & 0xffu, man = b & 0x7fffffu;
+    uint64_t r;
+    if (e == 0xffu) {
+        r = sign | (0x7ffull << 52) | ((uint64_t)man << 29);
+    } else if (e != 0) {
+        r = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)man << 29);
+    } else if (man == 0) {
+        r = sign;
+    } else {  // subnormal float: normalise
+        const int sh = __clz(man) - 8;  // shift that moves the leading 1 to bit 23
+        man = (man << sh) & 0x7fffffu;
+        r = sign | ((uint64_t)(897u - (uint32_t)sh) << 52) | ((uint64_t)man << 29);
+    }
+    return __longlong_as_double((long long)r);
+}
+
+template <typename TS>
+struct SP;  // solve parameters in the path's precision
+template <>
+struct SP<float> {
+    float sq, sp, chi0, s1n, tau, eps, err;
+    FC2_HD explicit SP(const SolveParams& p)
+        : sq(p.fsq), sp(p.fsp), chi0(p.fchi0), s1n(p.fs1n), tau(p.ftau), eps(p.feps), err(p.ferr) {}
+};
+template <>
+struct SP<double> {
+    double sq, sp, chi0, s1n, tau, eps, err;
+    FC2_HD explicit SP(const SolveParams& p)
+        : sq(p.sq), sp(p.sp), chi0(p.chi0), s1n(p.s1n), tau(p.tau), eps(p.eps_spec), err(p.err_fix) {}
+};
+FC2_D double to_double(float v) { return f2d_exact(v); }
+FC2_D double to_double(double v) { return v; }
 
 template <typename TS, int H>
 FC2_D void load_gridded(const cpx<TS>* __restrict__ spec, const TS* __restrict__ dec, int64_t N,
@@ -71,19 +112,18 @@ __global__ void __launch_bounds__(128) k_assemble(const cpx<TS>* __restrict__ sp
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= sp.N) return;
     constexpr int m = 2 * H + 1;
+    const SP<TS> q(sp);
     Sys<TS, H> S;
-    load_gridded<TS, H>(spec, dec, sp.N, j, (TS)sp.sq, (TS)sp.sp, (TS)sp.s1n, S);
+    load_gridded<TS, H>(spec, dec, sp.N, j, q.sq, q.sp, q.s1n, S);
     TS out[H];
     TS an2 = (TS)0;
-    chol_solve<TS, H, true>(S, (TS)sp.tau, out, &an2);
-    const TS eps = (TS)(sizeof(TS) == 4 ? sp.eps_spec + sp.eps_f32 : sp.eps_spec);
-    if (!(est_err<TS>(an2, m, eps) <= (TS)sp.err_fix)) {
+    chol_solve<TS, H, true>(S, q.tau, out, &an2);
+    if (!(est_err<TS>(an2, m, q.eps) <= q.err)) {
         int32_t pos = atomicAdd(list_count, 1);
         if (pos < cap) list[pos] = (int32_t)j;
     }
-    const TS c0 = (TS)sp.chi0;
 #pragma unroll
-    for (int h = 0; h < H; ++h) dchi2[(int64_t)h * sp.N + j] = (double)(out[h] * c0);
+    for (int h = 0; h < H; ++h) dchi2[(int64_t)h * sp.N + j] = to_double(out[h] * q.chi0);
 }
 
 // Double re-solve of float-path bins; bins still too sensitive go on to the
@@ -103,7 +143,7 @@ __global__ void __launch_bounds__(128) k_resolve(const cpx<float>* __restrict__ 
          b += (int64_t)gridDim.x * wpb) {
         const int64_t j = rlist[b];
         Sys<float, H> Sf;
-        load_gridded<float, H>(spec, dec, sp.N, j, (float)sp.sq, (float)sp.sp, (float)sp.s1n, Sf);
+        load_gridded<float, H>(spec, dec, sp.N, j, sp.fsq, sp.fsp, sp.fs1n, Sf);
         Sys<double, H> S;
 #pragma unroll
         for (int k = 0; k <= 2 * H; ++k) { S.qr[k] = Sf.qr[k]; S.qi[k] = Sf.qi[k]; }
@@ -646,6 +686,9 @@ static SolveParams solve_params(const fc2_plan_s* p) {
     sp.sp = (chi0 > 0.0) ? 1.0 / sqrt(W * chi0) : 0.0;
     sp.chi0 = chi0;
     sp.s1n = p->scal[SC_S1] * sp.sp;
+    sp.fsq = (float)sp.sq; sp.fsp = (float)sp.sp; sp.fchi0 = (float)sp.chi0;
+    sp.fs1n = (float)sp.s1n; sp.ftau = (float)sp.tau;
+    sp.feps = (float)(sp.eps_spec + sp.eps_f32); sp.ferr = (float)sp.err_fix;
     return sp;
 }
 
