@@ -55,7 +55,7 @@ void free_plan_memory(fc2_plan_s* p) {
     dfree(p->d_tau, s); dfree(p->d_wq, s); dfree(p->d_wp, s);
     dfree(p->d_key, s); dfree(p->d_dlt, s); dfree(p->d_cs, s);
     dfree(p->d_grid[0], s); dfree(p->d_grid[1], s); dfree(p->d_spec, s);
-    dfree(p->d_dec, s); dfree(p->d_twlo, s); dfree(p->d_twhi, s); dfree(p->d_twst, s);
+    dfree(p->d_dec, s); dfree(p->d_dec_p, s); dfree(p->d_twlo, s); dfree(p->d_twhi, s); dfree(p->d_twst, s);
     dfree(p->d_dchi2, s); dfree(p->d_flag_list, s); dfree(p->d_flag_count, s);
     dfree(p->d_L, s); dfree(p->d_red, s); dfree(p->d_best, s); dfree(p->d_part, s);
     dfree(p->d_phA, s); dfree(p->d_phB, s); dfree(p->d_wq32, s); dfree(p->d_wp32, s);
@@ -114,6 +114,26 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     p->w = opt.kernel_width ? opt.kernel_width : default_width(p->fp64, oversample);
     const double sig_eff = (double)M / (double)N;
     p->beta = 0.97 * M_PI * (1.0 - 0.5 / sig_eff) * (double)p->w;
+    // Packed transforms: when f_min is a whole number sh of df steps, Q_k and
+    // P_k share positions frac(k df tau) and need no modulation, so their
+    // strengths w and w (x - xbar) are real and one complex grid carries both
+    // (Q_k = (F(m) + conj F(-m)) / 2, P_k = (F(m) - conj F(-m)) / 2i at modes
+    // m = sh + j).  The modes then reach |m| = sh + N - 1, so this needs a grid
+    // with at least 2x oversampling of that range.
+    {
+        const double r = f_min / df;
+        const double shd = floor(r + 0.5);
+        const int64_t mmax = (int64_t)shd + N - 1;
+        if (!p->fp64 && !opt.kernel_width && shd >= 0.0 && shd < 1e15 &&
+            fabs(r - shd) <= 1e-9 * std::max(1.0, r) && 4 * std::max<int64_t>(mmax, 1) <= M) {
+            p->npk = H;
+            p->sh = (int64_t)shd;
+            p->G = 2 * H;
+            const double sig_p = (double)M / (2.0 * (double)std::max<int64_t>(mmax, 1));
+            p->w_p = default_width(false, 2);
+            p->beta_p = 0.97 * M_PI * (1.0 - 0.5 / std::min(sig_p, 2.0)) * (double)p->w_p;
+        }
+    }
     p->tau = opt.alias_tau > 0.0 ? opt.alias_tau : (p->fp64 ? 1e-9 : 1e-6);
     p->top_k = opt.top_k ? opt.top_k : 8;
     plan_fft_passes(p);
@@ -163,8 +183,9 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         g.ok(dalloc(&p->d_cs, (size_t)G * n * csz, s)) &&
         g.ok(dalloc(&p->d_grid[0], grid_bytes, s)) &&
         g.ok(dalloc(&p->d_grid[1], std::max(grid_bytes, keysort_b), s)) &&
-        g.ok(dalloc(&p->d_spec, (size_t)G * N * csz, s)) &&
+        g.ok(dalloc(&p->d_spec, (size_t)3 * H * N * csz, s)) &&
         g.ok(dalloc(&p->d_dec, (size_t)N * tsz, s)) &&
+        g.ok(dalloc(&p->d_dec_p, (size_t)N * tsz, s)) &&
         g.ok(dalloc(&p->d_twlo, (size_t)(1ll << ((p->logM + 1) / 2)) * csz, s)) &&
         g.ok(dalloc(&p->d_twhi, (size_t)(M >> ((p->logM + 1) / 2)) * csz, s)) &&
         g.ok(dalloc(&p->d_twst, (size_t)(8 * 4096 + 256) * csz, s)) &&
@@ -199,7 +220,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     if (st == FC2_OK) {
         // Time origin: the earliest sample, moved back by (w/2 + 1) cells of
         // the k = 1 grid so no sample's spreading window reaches below cell 0.
-        const double back = (0.5 * p->w + 1.0) / ((double)M * df);
+        const double back = (0.5 * std::max(p->w, p->w_p) + 1.0) / ((double)M * df);
         p->scal[SC_T0] -= back;
         p->scal[SC_TAUMAX] += back;
         g.ok(cudaMemcpyAsync(p->d_scal, p->scal, sizeof(p->scal), cudaMemcpyHostToDevice, s));
@@ -222,15 +243,17 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         for (int gi = 0; gi < G; ++gi) {
             GridGeom& gg = p->geom[gi];
             if (gi < 2 * H) { gg.k = gi + 1; gg.kind = 0; } else { gg.k = gi - 2 * H + 1; gg.kind = 1; }
+            if (gi < p->npk) gg.kind = 2;  // packed Q_k + i P_k
+            const int wg = (gi < p->npk) ? p->w_p : p->w;
             const double c = (double)gg.k * df;
             const double pmax = c * p->scal[SC_TAUMAX];
             const double cells = pmax * (double)M;
-            if (!(pmax < 1.0) || cells + p->w + 2.0 >= (double)M) {
+            if (!(pmax < 1.0) || cells + wg + 2.0 >= (double)M) {
                 gg.wraps = (pmax >= 1.0) ? 1 : 0;
                 gg.L = M;
             } else {
                 gg.wraps = 0;
-                int64_t L = (int64_t)floor(cells) + p->w + 3;
+                int64_t L = (int64_t)floor(cells) + wg + 3;
                 L = ((L + unit - 1) / unit) * unit;
                 gg.L = std::min(L, M);
             }
@@ -248,7 +271,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
                 for (int gi = 0; gi < G; ++gi) {
                     int64_t rd = M;
                     if (pi == 0) rd = std::min(R, (Lh[gi] + Sp - 1) / Sp) * Sp;
-                    const int64_t wr = (pi == P - 1) ? N : M;
+                    const int64_t wr = (pi == P - 1) ? (gi < p->npk ? 2 * N : N) : M;
                     fb += (double)(rd + wr) * (double)csz;
                 }
             }
@@ -274,7 +297,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
 static int64_t launches_front(const fc2_plan_s* p) {
     int64_t n = 1 + 1 + (int64_t)p->passes.size() + 1 + (p->fp64 ? 0 : 1);  // phase, spread, fft, assemble(+resolve)
     int bits = 0;
-    while ((1ll << bits) < p->M + 2 * p->w + 2) ++bits;
+    while ((1ll << bits) < p->M + 2 * std::max(p->w, p->w_p) + 2) ++bits;
     for (auto& g : p->geom)
         if (g.wraps) n += 2 + 3 * ((bits + 7) / 8);
     return n;
@@ -427,25 +450,60 @@ void fc2_debug_counts(fc2_plan p, int64_t* out4) {
 
 fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im) {
     if (!p || !re || !im) return FC2_ERR_INVALID_ARG;
-    const size_t cnt = (size_t)p->G * p->N;
+    const size_t N = (size_t)p->N;
+    const size_t rows = (size_t)3 * p->H;  // spectra rows as stored (packed or not)
+    const size_t cnt = rows * N;
     std::vector<char> buf(cnt * (p->fp64 ? 16 : 8));
-    std::vector<char> dec((size_t)p->N * (p->fp64 ? 8 : 4));
+    std::vector<char> dec(N * (p->fp64 ? 8 : 4)), decp(N * 4);
     if (cudaMemcpy(buf.data(), p->d_spec, buf.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
         return FC2_ERR_CUDA;
     if (cudaMemcpy(dec.data(), p->d_dec, dec.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
         return FC2_ERR_CUDA;
-    for (size_t i = 0; i < cnt; ++i) {
-        size_t j = i % (size_t)p->N;
+    if (p->npk > 0 &&
+        cudaMemcpy(decp.data(), p->d_dec_p, decp.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FC2_ERR_CUDA;
+    auto val = [&](size_t row, size_t j, double* r, double* i) {
         if (p->fp64) {
             const double* b = (const double*)buf.data();
-            double d = ((const double*)dec.data())[j];
-            re[i] = b[2 * i] * d; im[i] = b[2 * i + 1] * d;
+            *r = b[2 * (row * N + j)]; *i = b[2 * (row * N + j) + 1];
         } else {
             const float* b = (const float*)buf.data();
-            double d = ((const float*)dec.data())[j];
-            re[i] = b[2 * i] * d; im[i] = b[2 * i + 1] * d;
+            *r = b[2 * (row * N + j)]; *i = b[2 * (row * N + j) + 1];
         }
-    }
+    };
+    auto dd = [&](size_t j) {
+        return p->fp64 ? ((const double*)dec.data())[j] : (double)((const float*)dec.data())[j];
+    };
+    // output rows: Q_1..Q_2H, then P_1..P_H
+    const int H = p->H;
+    for (int k = 1; k <= 2 * H; ++k)
+        for (size_t j = 0; j < N; ++j) {
+            double ar, ai, br, bi;
+            const size_t o = (size_t)(k - 1) * N + j;
+            if (k <= p->npk) {
+                const double d = 0.5 * ((const float*)decp.data())[j];
+                val(2 * (k - 1), j, &ar, &ai);
+                val(2 * (k - 1) + 1, j, &br, &bi);
+                re[o] = (ar + br) * d; im[o] = (ai - bi) * d;
+            } else {
+                val(p->npk + k - 1, j, &ar, &ai);
+                re[o] = ar * dd(j); im[o] = ai * dd(j);
+            }
+        }
+    for (int k = 1; k <= H; ++k)
+        for (size_t j = 0; j < N; ++j) {
+            double ar, ai, br, bi;
+            const size_t o = (size_t)(2 * H + k - 1) * N + j;
+            if (k <= p->npk) {
+                const double d = 0.5 * ((const float*)decp.data())[j];
+                val(2 * (k - 1), j, &ar, &ai);
+                val(2 * (k - 1) + 1, j, &br, &bi);
+                re[o] = (ai + bi) * d; im[o] = (br - ar) * d;
+            } else {
+                val(p->npk + 2 * H + k - 1, j, &ar, &ai);
+                re[o] = ar * dd(j); im[o] = ai * dd(j);
+            }
+        }
     return FC2_OK;
 }
 

@@ -54,9 +54,18 @@ struct fc2_plan_s {
     int oversample = 2;
     int64_t M = 0;
     int logM = 0;
-    int G = 0;                 // number of transforms = 3H
+    int G = 0;                 // number of transforms: 3H, or 2H when packed
     int w = 0;                 // spreading kernel width
     double beta = 0;
+    // Packed transforms (mixed path, f_min = sh df, grids oversampled >= 4x):
+    // grids g < npk carry Q_k + i P_k (k = g + 1) with real strengths and no
+    // modulation; their spectra are kept at modes +-(sh + j).  Kernel width
+    // and shape of those grids: w_p, beta_p; deconvolution table d_dec_p.
+    int npk = 0;
+    int64_t sh = 0;
+    int w_p = 0;
+    double beta_p = 0;
+    void* d_dec_p = nullptr;
     double tau = 0;            // rank-drop threshold
     int top_k = 8;
     bool fp64 = true;

@@ -81,6 +81,18 @@ __global__ void k_init_dec(T* dec, int64_t N, int64_t hN, int64_t M, const doubl
     if (m > 0 && hN - m >= 0) dec[hN - m] = v;
 }
 
+// dec[j] = 1 / phihat((sh + j) / M), j < N.
+__global__ void k_init_dec_shift(float* dec, int64_t N, int64_t sh, int64_t M,
+                                 const double* cheb, int nc, double ymax) {
+    __shared__ double c[CHEB_N];
+    if (threadIdx.x < CHEB_N) c[threadIdx.x] = cheb[threadIdx.x];
+    __syncthreads();
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    const double xi = (double)(sh + j) / (double)M;
+    dec[j] = (float)(1.0 / cheb_clenshaw(c, nc, 2.0 * xi * xi / ymax - 1.0));
+}
+
 int cheb_fit_kernel_ft(int w, double beta, double xi_max, double* coef) {
     int nq = 2 * w + 16;
     std::vector<double> gx(nq), gw(nq);
@@ -129,6 +141,20 @@ cudaError_t init_deconv(fc2_plan_s* p, cudaStream_t s) {
                                                  xi_max * xi_max);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (p->npk > 0) {
+        // packed grids: dec_p[j] = 1 / phihat_p((sh + j) / M) (the modes -(sh + j)
+        // share it: phihat is even)
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return e;
+        const double xi_p = (double)(p->sh + p->N) / (double)p->M;
+        const int ncp = cheb_fit_kernel_ft(p->w_p, p->beta_p, xi_p, coef);
+        e = cudaMemcpyAsync(d_coef, coef, sizeof(coef), cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return e;
+        k_init_dec_shift<<<(unsigned)((p->N + 255) / 256), 256, 0, s>>>(
+            (float*)p->d_dec_p, p->N, p->sh, p->M, d_coef, ncp, xi_p * xi_p);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     // the coefficients live in reduction scratch: finish before it is reused
     return cudaStreamSynchronize(s);
 }
@@ -289,7 +315,24 @@ struct PassArgs {
     int logRn, logJn;  // radix and tile width of the next pass (blocked output layout)
     int N, hN;
     int tws;
+    int npk, sh;       // packed grids (g < npk) keep modes +-(sh + j), others j - hN
 };
+
+// Last pass: mode m of grid g goes to its place in the spectra.  Grid
+// g < npk (packed) stores F(sh + j) at [2g][j] and F(-(sh + j)) at [2g + 1][j];
+// any other grid stores F(j - hN) at [npk + g][j].
+template <typename T>
+FC2_D void store_mode(cpx<T>* __restrict__ spec, const PassArgs& a, int g, int m, cpx<T> v) {
+    if (g < a.npk) {
+        const int jp = m - a.sh;
+        if (jp >= 0 && jp < a.N) spec[(int64_t)(2 * g) * a.N + jp] = v;
+        const int jm = -m - a.sh;
+        if (jm >= 0 && jm < a.N) spec[(int64_t)(2 * g + 1) * a.N + jm] = v;
+    } else {
+        const int jf = m + a.hN;
+        if (jf >= 0 && jf < a.N) spec[(int64_t)(a.npk + g) * a.N + jf] = v;
+    }
+}
 
 // One pass of the transform.  Logical Stockham indexing: column j (0 <= j < S,
 // S = M / R) takes rows r of X[j + r S]; output k of its length-R DFT is
@@ -371,13 +414,11 @@ __global__ void __launch_bounds__(NT, 2) k_fft_pass(const cpx<T>* __restrict__ i
             }
         }
     } else {
-        cpx<T>* spec = out + (int64_t)g * a.N;
         for (int e = threadIdx.x; e < E; e += NT) {
             const int k = e >> LOGJ, jj = e & (J - 1);
             const int o = j0 + jj + (k << logNs);
             const int m = (o < M / 2) ? o : o - M;
-            const int jf = m + a.hN;
-            if (jf >= 0 && jf < a.N) spec[jf] = s[phys(e)];
+            store_mode<T>(out, a, g, m, s[phys(e)]);
         }
     }
 }
@@ -583,13 +624,11 @@ __global__ void __launch_bounds__(128, 2) k_fft_pass64(const cpx<float>* __restr
             }
             SmallDFT<T, 64>::run(v);
             if (a.last) {
-                cpx<T>* spec = out + (int64_t)g * a.N;
 #pragma unroll
                 for (int k = 0; k < 64; ++k) {
                     const int o = j0 + jj + ((pp + k * QA) << logNs);
                     const int m = (o < M / 2) ? o : o - M;
-                    const int jf = m + a.hN;
-                    if (jf >= 0 && jf < a.N) spec[jf] = v[k];
+                    store_mode<T>(out, a, g, m, v[k]);
                 }
             } else if (same_radix) {
                 cpx<T>* gout = out + (int64_t)g * M;
@@ -776,6 +815,8 @@ static cudaError_t fft_impl(fc2_plan_s* p, cudaStream_t s) {
         a.N = (int)p->N;
         a.hN = (int)(p->N / 2);
         a.tws = p->tw_shift;
+        a.npk = p->npk;
+        a.sh = (int)p->sh;
         const void* in = p->d_grid[src];
         void* out = a.last ? p->d_spec : p->d_grid[1 - src];
         cudaError_t e;

@@ -455,7 +455,7 @@ __global__ void k_phase(const double* __restrict__ tau, const double* __restrict
 // offset keeps 24 fraction bits (the spreading runs in float).
 __global__ void k_phase_fx32(const uint64_t* __restrict__ A, const uint64_t* __restrict__ B,
                              const float* __restrict__ wq32, const float* __restrict__ wp32,
-                             int64_t n, int H, int64_t N, int logM, int w,
+                             int64_t n, int H, int64_t N, int logM, int w, int npk, int w_p,
                              int32_t* __restrict__ key, float* __restrict__ dlt,
                              cpx<float>* __restrict__ cs) {
     const int g = blockIdx.y;
@@ -463,6 +463,7 @@ __global__ void k_phase_fx32(const uint64_t* __restrict__ A, const uint64_t* __r
     if (s >= n) return;
     int k, kind;
     if (g < 2 * H) { k = g + 1; kind = 0; } else { k = g - 2 * H + 1; kind = 1; }
+    if (g < npk) { kind = 2; w = w_p; }  // packed: real strengths w + i w (x - xbar)
     const uint64_t uk = (uint64_t)k * B[s];
     const int32_t cell = (int32_t)(uk >> (64 - logM));                 // floor(M u)
     const float fx = (float)(uint32_t)((uk << logM) >> 40) * 5.9604644775390625e-08f;  // 2^-24
@@ -478,13 +479,17 @@ __global__ void k_phase_fx32(const uint64_t* __restrict__ A, const uint64_t* __r
         kk = cell - (w - 1) / 2;
         de = fx + 0.5f;
     }
+    const int64_t o = (int64_t)g * n + s;
+    key[o] = kk;
+    dlt[o] = de;
+    if (kind == 2) {
+        cs[o] = mk<float>(wq32[s], wp32[s]);
+        return;
+    }
     const uint64_t th = (uint64_t)k * A[s] + (uint64_t)(N / 2) * uk;
     float sn, cn;
     sincospif((float)(int32_t)(th >> 32) * 4.656612873077393e-10f, &sn, &cn);  // 2^-31
     const float amp = kind == 0 ? wq32[s] : wp32[s];
-    const int64_t o = (int64_t)g * n + s;
-    key[o] = kk;
-    dlt[o] = de;
     cs[o] = mk<float>(amp * cn, amp * sn);
 }
 
@@ -528,10 +533,11 @@ static cudaError_t sort_keys_of(fc2_plan_s* p, int g, cudaStream_t s) {
     int32_t* key = p->d_key + so;
     T* dl = (T*)p->d_dlt + so;
     cpx<T>* cs = (cpx<T>*)p->d_cs + so;
-    const int32_t off = p->w;  // keys >= 1 - w/2 -> shifted keys are positive
+    const int wmax = std::max(p->w, p->w_p);
+    const int32_t off = wmax;  // keys >= 1 - w/2 -> shifted keys are positive
     k_key_init<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(key, n, off, k0, v0);
     int bits = 0;
-    while ((1ll << bits) < p->M + 2 * p->w + 2) ++bits;
+    while ((1ll << bits) < p->M + 2 * wmax + 2) ++bits;
     int npass = (bits + 7) / 8;
     for (int pass = 0; pass < npass; ++pass) {
         k_rs_hist<<<(unsigned)nblk, RS_NT, 0, s>>>(k0, n, pass * 8, hist, (int)nblk);
@@ -553,8 +559,8 @@ static cudaError_t phase_impl(fc2_plan_s* p, cudaStream_t s) {
     dim3 grid((unsigned)((p->n + 255) / 256), (unsigned)p->G);
     if constexpr (sizeof(T) == 4)
         k_phase_fx32<<<grid, 256, 0, s>>>(p->d_phA, p->d_phB, p->d_wq32, p->d_wp32, p->n, p->H,
-                                          p->N, p->logM, p->w, p->d_key, (float*)p->d_dlt,
-                                          (cpx<float>*)p->d_cs);
+                                          p->N, p->logM, p->w, p->npk, p->w_p, p->d_key,
+                                          (float*)p->d_dlt, (cpx<float>*)p->d_cs);
     else
         k_phase<T><<<grid, 256, 0, s>>>(p->d_tau, p->d_wq, p->d_wp, p->n, p->H, p->f_min, p->df,
                                         p->N, p->M, p->w, p->d_key, (T*)p->d_dlt,
@@ -618,8 +624,8 @@ template <typename T, int TILE, int NT, int CAP>
 __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
                                                const T* __restrict__ dlt,
                                                const cpx<T>* __restrict__ cs, int64_t n_all,
-                                               int64_t M, int w, T beta,
-                                               const int64_t* __restrict__ Lg,
+                                               int64_t M, int w, T beta, int npk, int w_p,
+                                               T beta_p, const int64_t* __restrict__ Lg,
                                                cpx<T>* __restrict__ grid, int64_t gstride,
                                                const int64_t* __restrict__ slot_soff,
                                                const int64_t* __restrict__ slot_n) {
@@ -631,6 +637,7 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
     const int g = blockIdx.y;
     const int64_t a = (int64_t)blockIdx.x * TILE;
     if (a >= Lg[g]) return;
+    if (g < npk) { w = w_p; beta = beta_p; }
     // samples of transform g: [g n, (g + 1) n) or, for a batch, per-slot ranges
     const int64_t so = slot_soff ? slot_soff[g] : (int64_t)g * n_all;
     const int64_t n = slot_n ? slot_n[g] : n_all;
@@ -698,7 +705,7 @@ static cudaError_t spread_tiles(fc2_plan_s* p, cudaStream_t s) {
     dim3 grid((unsigned)tiles, (unsigned)p->G);
     k_spread<T, TILE, NT, CAP><<<grid, NT, 0, s>>>(
         p->d_key, (const T*)p->d_dlt, (const cpx<T>*)p->d_cs, p->n, p->M, p->w, (T)p->beta,
-        p->d_L, (cpx<T>*)p->d_grid[0], p->M, p->d_slot_soff, p->d_slot_n);
+        p->npk, p->w_p, (T)p->beta_p, p->d_L, (cpx<T>*)p->d_grid[0], p->M, p->d_slot_soff, p->d_slot_n);
     return cudaGetLastError();
 }
 

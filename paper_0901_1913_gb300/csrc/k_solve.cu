@@ -75,15 +75,41 @@ struct SP<double> {
 FC2_D double to_double(float v) { return f2d_exact(v); }
 FC2_D double to_double(double v) { return v; }
 
+// Normalised system of bin j from the gridded spectra.  Grids g < npk are
+// packed: F = Q_k + i P_k (k = g + 1) kept at modes +(sh + j) (row 2g) and
+// -(sh + j) (row 2g + 1), so Q_k = (F+ + conj F-) / 2 and
+// P_k = (F+ - conj F-) / 2i, deconvolved by dec_p; the other grids are in
+// rows npk + g, deconvolved by dec.
 template <typename TS, int H>
-FC2_D void load_gridded(const cpx<TS>* __restrict__ spec, const TS* __restrict__ dec, int64_t N,
-                        int64_t j, TS sq, TS sp, TS s1n, Sys<TS, H>& S) {
+FC2_D void load_gridded(const cpx<TS>* __restrict__ spec, const TS* __restrict__ dec,
+                        const TS* __restrict__ dec_p, int npk, int64_t N, int64_t j, TS sq,
+                        TS sp, TS s1n, Sys<TS, H>& S) {
     const TS d = dec[j];
     const TS dq = d * sq, dp = d * sp;
     S.qr[0] = (TS)1;
     S.qi[0] = (TS)0;
     S.pr[0] = s1n;
     S.pi[0] = (TS)0;
+    if (npk > 0) {
+        const TS e = dec_p[j] * (TS)0.5;
+        const TS eq = e * sq, ep = e * sp;
+#pragma unroll
+        for (int k = 1; k <= H; ++k) {
+            const cpx<TS> a = spec[(int64_t)(2 * k - 2) * N + j];
+            const cpx<TS> b = spec[(int64_t)(2 * k - 1) * N + j];
+            S.qr[k] = (a.x + b.x) * eq;
+            S.qi[k] = (a.y - b.y) * eq;
+            S.pr[k] = (a.y + b.y) * ep;
+            S.pi[k] = (b.x - a.x) * ep;
+        }
+#pragma unroll
+        for (int k = H + 1; k <= 2 * H; ++k) {
+            const cpx<TS> v = spec[(int64_t)(npk + k - 1) * N + j];
+            S.qr[k] = v.x * dq;
+            S.qi[k] = v.y * dq;
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 1; k <= 2 * H; ++k) {
         cpx<TS> v = spec[(int64_t)(k - 1) * N + j];
@@ -105,6 +131,7 @@ FC2_D void load_gridded(const cpx<TS>* __restrict__ spec, const TS* __restrict__
 template <typename TS, int H>
 __global__ void __launch_bounds__(128) k_assemble(const cpx<TS>* __restrict__ spec,
                                                   const TS* __restrict__ dec,
+                                                  const TS* __restrict__ dec_p, int npk,
                                                   double* __restrict__ dchi2, SolveParams sp,
                                                   int32_t* __restrict__ list,
                                                   int32_t* __restrict__ list_count,
@@ -114,7 +141,7 @@ __global__ void __launch_bounds__(128) k_assemble(const cpx<TS>* __restrict__ sp
     constexpr int m = 2 * H + 1;
     const SP<TS> q(sp);
     Sys<TS, H> S;
-    load_gridded<TS, H>(spec, dec, sp.N, j, q.sq, q.sp, q.s1n, S);
+    load_gridded<TS, H>(spec, dec, dec_p, npk, sp.N, j, q.sq, q.sp, q.s1n, S);
     TS out[H];
     TS an2 = (TS)0;
     chol_solve<TS, H, true>(S, q.tau, out, &an2);
@@ -131,6 +158,7 @@ __global__ void __launch_bounds__(128) k_assemble(const cpx<TS>* __restrict__ sp
 template <int H>
 __global__ void __launch_bounds__(128) k_resolve(const cpx<float>* __restrict__ spec,
                                                  const float* __restrict__ dec,
+                                                 const float* __restrict__ dec_p, int npk,
                                                  double* __restrict__ dchi2, SolveParams sp,
                                                  const int32_t* __restrict__ rlist,
                                                  const int32_t* __restrict__ rcount, int64_t rcap,
@@ -143,7 +171,7 @@ __global__ void __launch_bounds__(128) k_resolve(const cpx<float>* __restrict__ 
          b += (int64_t)gridDim.x * wpb) {
         const int64_t j = rlist[b];
         Sys<float, H> Sf;
-        load_gridded<float, H>(spec, dec, sp.N, j, sp.fsq, sp.fsp, sp.fs1n, Sf);
+        load_gridded<float, H>(spec, dec, dec_p, npk, sp.N, j, sp.fsq, sp.fsp, sp.fs1n, Sf);
         Sys<double, H> S;
 #pragma unroll
         for (int k = 0; k <= 2 * H; ++k) { S.qr[k] = Sf.qr[k]; S.qi[k] = Sf.qi[k]; }
@@ -704,10 +732,11 @@ static cudaError_t assemble_impl(fc2_plan_s* p, cudaStream_t s) {
     int32_t* cnt = p->fp64 ? p->d_flag_count : p->d_flag_count + 1;
 #define FC2_ASM(HH)                                                                           \
     case HH:                                                                                  \
-        k_assemble<TS, HH><<<grid, 128, 0, s>>>(spec, dec, p->d_dchi2, sp, list, cnt,         \
-                                                p->flag_cap);                                 \
+        k_assemble<TS, HH><<<grid, 128, 0, s>>>(spec, dec, (const TS*)p->d_dec_p, p->npk,     \
+                                                p->d_dchi2, sp, list, cnt, p->flag_cap);      \
         if (!p->fp64)                                                                         \
             k_resolve<HH><<<8 * 152, 32, 0, s>>>((const cpx<float>*)spec, (const float*)dec, \
+                                                  (const float*)p->d_dec_p, p->npk,           \
                                                   p->d_dchi2, sp, list, cnt, p->flag_cap,     \
                                                   p->d_flag_list, p->d_flag_count,            \
                                                   p->flag_cap);                               \

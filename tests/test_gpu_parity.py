@@ -37,6 +37,28 @@ def test_spectra_match_direct_sums(fc2, oracle_mod, prec, tol):
         assert err < tol, (prec, g, err)
 
 
+def test_packed_spectra_match_direct_sums(fc2, oracle_mod):
+    """With f_min a whole number of df steps and 4x grids, the mixed path packs
+    Q_k + i P_k into one transform; the unpacked spectra still equal the direct
+    sums of Eq. eqPQ."""
+    c = synth.config2(n=3000, N=1 << 14)
+    assert abs(c.f_min / c.df - round(c.f_min / c.df)) < 1e-12 and c.oversample == 4
+    with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed") as p:
+        p.execute()
+        spec = p.spectra()
+        t0 = p.t0
+    w = 1.0 / c.sigma ** 2
+    W, xbar, _, _ = oracle_mod.moments(c.x, c.sigma)
+    cp = w * (c.x - xbar)
+    bins = sample_bins(c.N, 200, 2, windows=[0, c.N - 1])
+    f = c.f_min + bins * c.df
+    for g in range(3 * c.H):
+        k, amp = (g + 1, w) if g < 2 * c.H else (g - 2 * c.H + 1, cp)
+        ref = oracle_mod.trig_sums(c.t - t0, amp, k * f)
+        err = np.max(np.abs(spec[g, bins] - ref)) / np.sum(np.abs(amp))
+        assert err < 2e-6, (g, err)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_config1_full_periodogram(fc2, oracle_mod, prec):
     c = synth.config1()
