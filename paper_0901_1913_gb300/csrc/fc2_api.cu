@@ -126,9 +126,11 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         const int64_t mmax = (int64_t)shd + N - 1;
         if (!p->fp64 && !opt.kernel_width && shd >= 0.0 && shd < 1e15 &&
             fabs(r - shd) <= 1e-9 * std::max(1.0, r) && 4 * std::max<int64_t>(mmax, 1) <= M) {
-            p->npk = H;
+            p->packed = true;
             p->sh = (int64_t)shd;
-            p->G = 2 * H;
+            p->G = H + (H + 1) / 2;
+            p->npk = p->G;
+            p->nsrc = 2 * H;
             const double sig_p = (double)M / (2.0 * (double)std::max<int64_t>(mmax, 1));
             p->w_p = default_width(false, 2);
             p->beta_p = 0.97 * M_PI * (1.0 - 0.5 / std::min(sig_p, 2.0)) * (double)p->w_p;
@@ -142,12 +144,14 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     const size_t tsz = p->fp64 ? 8 : 4;
     const size_t csz = 2 * tsz;
     const int G = p->G;
+    const int NSRC = p->nsrc ? p->nsrc : G;  // sample sets
+    const size_t spec_rows = p->packed ? (size_t)2 * G : (size_t)3 * H;
     // memory estimate
     size_t need = 0;
     need += (size_t)n * 8 * 6 + (size_t)n * 4;
-    need += (size_t)G * n * (4 + tsz + csz);
+    need += (size_t)NSRC * n * (4 + tsz + csz);
     need += 2 * (size_t)G * M * csz;
-    need += (size_t)G * N * csz + (size_t)N * tsz + (size_t)H * N * 8 + (size_t)N * 4;
+    need += spec_rows * N * csz + (size_t)N * tsz + (size_t)H * N * 8 + (size_t)N * 4;
     size_t freeb = 0, totalb = 0;
     if (cudaMemGetInfo(&freeb, &totalb) == cudaSuccess && need > freeb) {
         if (p->own_stream) cudaStreamDestroy(p->stream);
@@ -178,12 +182,12 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     g.ok(dalloc(&p->d_scal, SC_COUNT * 8, s)) && g.ok(dalloc(&p->d_status, 16, s)) &&
         g.ok(dalloc(&p->d_perm, n * 4, s)) && g.ok(dalloc(&p->d_tau, n * 8, s)) &&
         g.ok(dalloc(&p->d_wq, n * 8, s)) && g.ok(dalloc(&p->d_wp, n * 8, s)) &&
-        g.ok(dalloc(&p->d_key, (size_t)G * n * 4, s)) &&
-        g.ok(dalloc(&p->d_dlt, (size_t)G * n * tsz, s)) &&
-        g.ok(dalloc(&p->d_cs, (size_t)G * n * csz, s)) &&
+        g.ok(dalloc(&p->d_key, (size_t)NSRC * n * 4, s)) &&
+        g.ok(dalloc(&p->d_dlt, (size_t)NSRC * n * tsz, s)) &&
+        g.ok(dalloc(&p->d_cs, (size_t)NSRC * n * csz, s)) &&
         g.ok(dalloc(&p->d_grid[0], grid_bytes, s)) &&
         g.ok(dalloc(&p->d_grid[1], std::max(grid_bytes, keysort_b), s)) &&
-        g.ok(dalloc(&p->d_spec, (size_t)3 * H * N * csz, s)) &&
+        g.ok(dalloc(&p->d_spec, spec_rows * N * csz, s)) &&
         g.ok(dalloc(&p->d_dec, (size_t)N * tsz, s)) &&
         g.ok(dalloc(&p->d_dec_p, (size_t)N * tsz, s)) &&
         g.ok(dalloc(&p->d_twlo, (size_t)(1ll << ((p->logM + 1) / 2)) * csz, s)) &&
@@ -238,13 +242,13 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         const int64_t S1 = M >> LOGR1;
         const int64_t tile = (M >= 4096) ? 1024 : 128;
         const int64_t unit = std::max(S1, tile);
-        p->geom.resize(G);
-        std::vector<int64_t> Lh(G);
-        for (int gi = 0; gi < G; ++gi) {
+        p->geom.resize(NSRC);
+        std::vector<int64_t> Ls(NSRC), Lh(G);
+        for (int gi = 0; gi < NSRC; ++gi) {  // per sample set
             GridGeom& gg = p->geom[gi];
             if (gi < 2 * H) { gg.k = gi + 1; gg.kind = 0; } else { gg.k = gi - 2 * H + 1; gg.kind = 1; }
-            if (gi < p->npk) gg.kind = 2;  // packed Q_k + i P_k
-            const int wg = (gi < p->npk) ? p->w_p : p->w;
+            if (p->packed) gg.kind = 2;
+            const int wg = p->packed ? p->w_p : p->w;
             const double c = (double)gg.k * df;
             const double pmax = c * p->scal[SC_TAUMAX];
             const double cells = pmax * (double)M;
@@ -257,7 +261,15 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
                 L = ((L + unit - 1) / unit) * unit;
                 gg.L = std::min(L, M);
             }
-            Lh[gi] = gg.L;
+            Ls[gi] = gg.L;
+        }
+        for (int gi = 0; gi < G; ++gi) {  // a grid's occupied extent: that of its sets
+            if (!p->packed || gi < H) {
+                Lh[gi] = Ls[gi];
+            } else {
+                const int t0 = H + 2 * (gi - H);
+                Lh[gi] = std::max(Ls[t0], t0 + 1 < NSRC ? Ls[t0 + 1] : 0);
+            }
         }
         g.ok(cudaMemcpyAsync(p->d_L, Lh.data(), G * 8, cudaMemcpyHostToDevice, s));
         // Algorithmic bytes of the transform: each pass reads its input once
@@ -451,7 +463,7 @@ void fc2_debug_counts(fc2_plan p, int64_t* out4) {
 fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im) {
     if (!p || !re || !im) return FC2_ERR_INVALID_ARG;
     const size_t N = (size_t)p->N;
-    const size_t rows = (size_t)3 * p->H;  // spectra rows as stored (packed or not)
+    const size_t rows = p->packed ? (size_t)2 * p->G : (size_t)3 * p->H;  // rows as stored
     const size_t cnt = rows * N;
     std::vector<char> buf(cnt * (p->fp64 ? 16 : 8));
     std::vector<char> dec(N * (p->fp64 ? 8 : 4)), decp(N * 4);
@@ -459,7 +471,7 @@ fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im) {
         return FC2_ERR_CUDA;
     if (cudaMemcpy(dec.data(), p->d_dec, dec.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
         return FC2_ERR_CUDA;
-    if (p->npk > 0 &&
+    if (p->packed &&
         cudaMemcpy(decp.data(), p->d_dec_p, decp.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
         return FC2_ERR_CUDA;
     auto val = [&](size_t row, size_t j, double* r, double* i) {
@@ -476,34 +488,28 @@ fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im) {
     };
     // output rows: Q_1..Q_2H, then P_1..P_H
     const int H = p->H;
-    for (int k = 1; k <= 2 * H; ++k)
+    for (int r = 0; r < 3 * H; ++r) {
+        const bool isq = r < 2 * H;
+        const int k = isq ? r + 1 : r - 2 * H + 1;
         for (size_t j = 0; j < N; ++j) {
+            const size_t o = (size_t)r * N + j;
             double ar, ai, br, bi;
-            const size_t o = (size_t)(k - 1) * N + j;
-            if (k <= p->npk) {
+            if (p->packed) {
+                // grid and part (0 = real, 1 = imaginary) of this transform
+                int g, part;
+                if (k <= H) { g = k - 1; part = isq ? 0 : 1; }
+                else { g = H + (k - H - 1) / 2; part = (k - H - 1) & 1; }
                 const double d = 0.5 * ((const float*)decp.data())[j];
-                val(2 * (k - 1), j, &ar, &ai);
-                val(2 * (k - 1) + 1, j, &br, &bi);
-                re[o] = (ar + br) * d; im[o] = (ai - bi) * d;
+                val(2 * (size_t)g, j, &ar, &ai);
+                val(2 * (size_t)g + 1, j, &br, &bi);
+                if (part == 0) { re[o] = (ar + br) * d; im[o] = (ai - bi) * d; }
+                else { re[o] = (ai + bi) * d; im[o] = (br - ar) * d; }
             } else {
-                val(p->npk + k - 1, j, &ar, &ai);
+                val((size_t)r, j, &ar, &ai);
                 re[o] = ar * dd(j); im[o] = ai * dd(j);
             }
         }
-    for (int k = 1; k <= H; ++k)
-        for (size_t j = 0; j < N; ++j) {
-            double ar, ai, br, bi;
-            const size_t o = (size_t)(2 * H + k - 1) * N + j;
-            if (k <= p->npk) {
-                const double d = 0.5 * ((const float*)decp.data())[j];
-                val(2 * (k - 1), j, &ar, &ai);
-                val(2 * (k - 1) + 1, j, &br, &bi);
-                re[o] = (ai + bi) * d; im[o] = (br - ar) * d;
-            } else {
-                val(p->npk + 2 * H + k - 1, j, &ar, &ai);
-                re[o] = ar * dd(j); im[o] = ai * dd(j);
-            }
-        }
+    }
     return FC2_OK;
 }
 

@@ -54,13 +54,19 @@ struct fc2_plan_s {
     int oversample = 2;
     int64_t M = 0;
     int logM = 0;
-    int G = 0;                 // number of transforms: 3H, or 2H when packed
+    int G = 0;                 // number of grids: 3H, or H + ceil(H/2) when packed
     int w = 0;                 // spreading kernel width
     double beta = 0;
     // Packed transforms (mixed path, f_min = sh df, grids oversampled >= 4x):
-    // grids g < npk carry Q_k + i P_k (k = g + 1) with real strengths and no
-    // modulation; their spectra are kept at modes +-(sh + j).  Kernel width
-    // and shape of those grids: w_p, beta_p; deconvolution table d_dec_p.
+    // every transform has real strengths and no modulation, and each complex
+    // grid carries two of them: grid g < H holds Q_k + i P_k (k = g + 1, one
+    // set of sample positions), grid H + q holds Q_{H+2q+1} + i Q_{H+2q+2}
+    // (two sets).  Their spectra are kept at modes +-(sh + j).  Samples are
+    // organised per source (nsrc = 2H: source t is transform Q_{t+1}, with
+    // P_{t+1} as its imaginary part when t < H).  npk = number of packed grids
+    // (all of them); kernel width and shape w_p, beta_p; deconvolution d_dec_p.
+    bool packed = false;
+    int nsrc = 0;              // sample sets (sources); 0 = one per grid
     int npk = 0;
     int64_t sh = 0;
     int w_p = 0;
@@ -120,7 +126,7 @@ struct fc2_plan_s {
     size_t red_bytes = 0;
     fc2_best* d_best = nullptr;  // [H + top_k]
 
-    std::vector<fc2::GridGeom> geom;
+    std::vector<fc2::GridGeom> geom;  // per source (sample set)
     std::vector<fc2::FftPass> passes;
     int64_t last_flag_count = 0;
     int64_t last_exact2_count = 0;

@@ -461,9 +461,12 @@ __global__ void k_phase_fx32(const uint64_t* __restrict__ A, const uint64_t* __r
     const int g = blockIdx.y;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
+    // g indexes sample sets: Q_{g+1}, P_{g-2H+1} unpacked; packed (npk > 0):
+    // set g is Q_{g+1}, carrying P_{g+1} as imaginary part when g < H and
+    // otherwise placed in the real (even g - H) or imaginary part of its grid
     int k, kind;
     if (g < 2 * H) { k = g + 1; kind = 0; } else { k = g - 2 * H + 1; kind = 1; }
-    if (g < npk) { kind = 2; w = w_p; }  // packed: real strengths w + i w (x - xbar)
+    if (npk > 0) { kind = 2; w = w_p; }
     const uint64_t uk = (uint64_t)k * B[s];
     const int32_t cell = (int32_t)(uk >> (64 - logM));                 // floor(M u)
     const float fx = (float)(uint32_t)((uk << logM) >> 40) * 5.9604644775390625e-08f;  // 2^-24
@@ -483,7 +486,9 @@ __global__ void k_phase_fx32(const uint64_t* __restrict__ A, const uint64_t* __r
     key[o] = kk;
     dlt[o] = de;
     if (kind == 2) {
-        cs[o] = mk<float>(wq32[s], wp32[s]);
+        const float q = wq32[s];
+        cs[o] = (g < H) ? mk<float>(q, wp32[s]) : (((g - H) & 1) ? mk<float>(0.f, q)
+                                                                  : mk<float>(q, 0.f));
         return;
     }
     const uint64_t th = (uint64_t)k * A[s] + (uint64_t)(N / 2) * uk;
@@ -556,7 +561,8 @@ static cudaError_t sort_keys_of(fc2_plan_s* p, int g, cudaStream_t s) {
 
 template <typename T>
 static cudaError_t phase_impl(fc2_plan_s* p, cudaStream_t s) {
-    dim3 grid((unsigned)((p->n + 255) / 256), (unsigned)p->G);
+    const int nsrc = p->nsrc ? p->nsrc : p->G;
+    dim3 grid((unsigned)((p->n + 255) / 256), (unsigned)nsrc);
     if constexpr (sizeof(T) == 4)
         k_phase_fx32<<<grid, 256, 0, s>>>(p->d_phA, p->d_phB, p->d_wq32, p->d_wp32, p->n, p->H,
                                           p->N, p->logM, p->w, p->npk, p->w_p, p->d_key,
@@ -567,7 +573,7 @@ static cudaError_t phase_impl(fc2_plan_s* p, cudaStream_t s) {
                                         (cpx<T>*)p->d_cs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    for (int g = 0; g < p->G; ++g)
+    for (int g = 0; g < nsrc; ++g)
         if (p->geom[g].wraps) {
             e = sort_keys_of<T>(p, g, s);
             if (e != cudaSuccess) return e;
@@ -576,7 +582,7 @@ static cudaError_t phase_impl(fc2_plan_s* p, cudaStream_t s) {
 }
 
 cudaError_t sort_wrapping_keys(fc2_plan_s* p, cudaStream_t s) {
-    for (int g = 0; g < p->G; ++g)
+    for (int g = 0; g < (int)p->geom.size(); ++g)
         if (p->geom[g].wraps) {
             cudaError_t e = p->fp64 ? sort_keys_of<double>(p, g, s) : sort_keys_of<float>(p, g, s);
             if (e != cudaSuccess) return e;
@@ -624,8 +630,9 @@ template <typename T, int TILE, int NT, int CAP>
 __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
                                                const T* __restrict__ dlt,
                                                const cpx<T>* __restrict__ cs, int64_t n_all,
-                                               int64_t M, int w, T beta, int npk, int w_p,
-                                               T beta_p, const int64_t* __restrict__ Lg,
+                                               int64_t M, int w, T beta, int npk, int pH,
+                                               int w_p, T beta_p,
+                                               const int64_t* __restrict__ Lg,
                                                cpx<T>* __restrict__ grid, int64_t gstride,
                                                const int64_t* __restrict__ slot_soff,
                                                const int64_t* __restrict__ slot_n) {
@@ -637,57 +644,70 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
     const int g = blockIdx.y;
     const int64_t a = (int64_t)blockIdx.x * TILE;
     if (a >= Lg[g]) return;
-    if (g < npk) { w = w_p; beta = beta_p; }
-    // samples of transform g: [g n, (g + 1) n) or, for a batch, per-slot ranges
-    const int64_t so = slot_soff ? slot_soff[g] : (int64_t)g * n_all;
-    const int64_t n = slot_n ? slot_n[g] : n_all;
-    const int32_t* kg = key + so;
-    const T* dg = dlt + so;
-    const cpx<T>* cg = cs + so;
-    if (threadIdx.x < 3) {
-        // ranges of keys (shifted by -M, 0, +M) whose windows meet the tile
-        int64_t sh = (threadIdx.x == 0) ? M : (threadIdx.x == 1 ? 0 : -M);
-        int64_t lo = lower_bound_key(kg, n, a - w + 1 + sh);
-        int64_t hi = lower_bound_key(kg, n, a + TILE + sh);
-        rng[2 * threadIdx.x] = lo;
-        rng[2 * threadIdx.x + 1] = hi;
+    // sample sets of grid g: one, or (packed grids g >= H) two
+    int t0 = g, nset = 1;
+    if (npk > 0) {
+        w = w_p;
+        beta = beta_p;
+        if (g >= pH) {
+            t0 = pH + 2 * (g - pH);
+            nset = (t0 + 1 < 2 * pH) ? 2 : 1;
+        }
     }
-    __syncthreads();
-    const int64_t c0 = rng[1] - rng[0], c1 = rng[3] - rng[2], c2 = rng[5] - rng[4];
-    const int64_t total = c0 + c1 + c2;
     const T ihw = (T)2 / (T)w;
     const T hw = (T)0.5 * (T)w;
     Acc<T> acc[PER];
 #pragma unroll
     for (int q = 0; q < PER; ++q) acc[q].init();
-    for (int64_t cb = 0; cb < total; cb += CAP) {
-        const int cnt = (int)min((int64_t)CAP, total - cb);
-        for (int e = threadIdx.x; e < cnt; e += NT) {
-            int64_t v = cb + e;
-            int64_t src;
-            int64_t sh;
-            if (v < c0) { src = rng[0] + v; sh = -M; }
-            else if (v < c0 + c1) { src = rng[2] + (v - c0); sh = 0; }
-            else { src = rng[4] + (v - c0 - c1); sh = M; }
-            sk[e] = (int32_t)((int64_t)kg[src] + sh - a);  // tile-relative key
-            sd[e] = dg[src];
-            sc[e] = cg[src];
+    for (int si = 0; si < nset; ++si) {
+        const int t = t0 + si;
+        // samples of set t: [t n, (t + 1) n) or, for a batch, per-slot ranges
+        const int64_t so = slot_soff ? slot_soff[t] : (int64_t)t * n_all;
+        const int64_t n = slot_n ? slot_n[t] : n_all;
+        const int32_t* kg = key + so;
+        const T* dg = dlt + so;
+        const cpx<T>* cg = cs + so;
+        if (threadIdx.x < 3) {
+            // ranges of keys (shifted by -M, 0, +M) whose windows meet the tile
+            int64_t sh = (threadIdx.x == 0) ? M : (threadIdx.x == 1 ? 0 : -M);
+            int64_t lo = lower_bound_key(kg, n, a - w + 1 + sh);
+            int64_t hi = lower_bound_key(kg, n, a + TILE + sh);
+            rng[2 * threadIdx.x] = lo;
+            rng[2 * threadIdx.x + 1] = hi;
         }
         __syncthreads();
-#pragma unroll
-        for (int q = 0; q < PER; ++q) {
-            const int l = threadIdx.x + q * NT;  // tile-relative cell
-            // samples with l - w + 1 <= key <= l, contiguous in sorted order
-            int lo = 0, hi = cnt;
-            while (lo < hi) { int mid = (lo + hi) >> 1; if (sk[mid] < l - w + 1) lo = mid + 1; else hi = mid; }
-            int e = lo;
-            for (; e < cnt && sk[e] <= l; ++e) {
-                T z = (T)(l - sk[e]) + (T)1 - sd[e] - hw;
-                T ph = es_kernel<T>(z, ihw, beta);
-                acc[q].add(sc[e].x * ph, sc[e].y * ph);
+        const int64_t c0 = rng[1] - rng[0], c1 = rng[3] - rng[2], c2 = rng[5] - rng[4];
+        const int64_t total = c0 + c1 + c2;
+        for (int64_t cb = 0; cb < total; cb += CAP) {
+            const int cnt = (int)min((int64_t)CAP, total - cb);
+            for (int e = threadIdx.x; e < cnt; e += NT) {
+                int64_t v = cb + e;
+                int64_t src;
+                int64_t shv;
+                if (v < c0) { src = rng[0] + v; shv = -M; }
+                else if (v < c0 + c1) { src = rng[2] + (v - c0); shv = 0; }
+                else { src = rng[4] + (v - c0 - c1); shv = M; }
+                sk[e] = (int32_t)((int64_t)kg[src] + shv - a);  // tile-relative key
+                sd[e] = dg[src];
+                sc[e] = cg[src];
             }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int l = threadIdx.x + q * NT;  // tile-relative cell
+                // samples with l - w + 1 <= key <= l, contiguous in sorted order
+                int lo = 0, hi = cnt;
+                while (lo < hi) { int mid = (lo + hi) >> 1; if (sk[mid] < l - w + 1) lo = mid + 1; else hi = mid; }
+                int e = lo;
+                for (; e < cnt && sk[e] <= l; ++e) {
+                    T z = (T)(l - sk[e]) + (T)1 - sd[e] - hw;
+                    T ph = es_kernel<T>(z, ihw, beta);
+                    acc[q].add(sc[e].x * ph, sc[e].y * ph);
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        __syncthreads();  // rng is rewritten for the next set
     }
     cpx<T>* gg = grid + (int64_t)g * gstride + a;
 #pragma unroll
@@ -705,7 +725,7 @@ static cudaError_t spread_tiles(fc2_plan_s* p, cudaStream_t s) {
     dim3 grid((unsigned)tiles, (unsigned)p->G);
     k_spread<T, TILE, NT, CAP><<<grid, NT, 0, s>>>(
         p->d_key, (const T*)p->d_dlt, (const cpx<T>*)p->d_cs, p->n, p->M, p->w, (T)p->beta,
-        p->npk, p->w_p, (T)p->beta_p, p->d_L, (cpx<T>*)p->d_grid[0], p->M, p->d_slot_soff, p->d_slot_n);
+        p->npk, p->H, p->w_p, (T)p->beta_p, p->d_L, (cpx<T>*)p->d_grid[0], p->M, p->d_slot_soff, p->d_slot_n);
     return cudaGetLastError();
 }
 

@@ -75,11 +75,12 @@ struct SP<double> {
 FC2_D double to_double(float v) { return f2d_exact(v); }
 FC2_D double to_double(double v) { return v; }
 
-// Normalised system of bin j from the gridded spectra.  Grids g < npk are
-// packed: F = Q_k + i P_k (k = g + 1) kept at modes +(sh + j) (row 2g) and
-// -(sh + j) (row 2g + 1), so Q_k = (F+ + conj F-) / 2 and
-// P_k = (F+ - conj F-) / 2i, deconvolved by dec_p; the other grids are in
-// rows npk + g, deconvolved by dec.
+// Normalised system of bin j from the gridded spectra.  Packed layout
+// (npk > 0): grid g keeps F = X_a + i X_b at modes +(sh + j) (row 2g) and
+// -(sh + j) (row 2g + 1), so X_a = (F+ + conj F-) / 2 and
+// X_b = (F+ - conj F-) / 2i, deconvolved by dec_p; grid k - 1 holds (Q_k, P_k)
+// for k <= H, grid H + q holds (Q_{H+2q+1}, Q_{H+2q+2}).  Otherwise row g is
+// transform g (Q_1..Q_2H, P_1..P_H), deconvolved by dec.
 template <typename TS, int H>
 FC2_D void load_gridded(const cpx<TS>* __restrict__ spec, const TS* __restrict__ dec,
                         const TS* __restrict__ dec_p, int npk, int64_t N, int64_t j, TS sq,
@@ -104,9 +105,16 @@ FC2_D void load_gridded(const cpx<TS>* __restrict__ spec, const TS* __restrict__
         }
 #pragma unroll
         for (int k = H + 1; k <= 2 * H; ++k) {
-            const cpx<TS> v = spec[(int64_t)(npk + k - 1) * N + j];
-            S.qr[k] = v.x * dq;
-            S.qi[k] = v.y * dq;
+            const int g = H + (k - H - 1) / 2;
+            const cpx<TS> a = spec[(int64_t)(2 * g) * N + j];
+            const cpx<TS> b = spec[(int64_t)(2 * g + 1) * N + j];
+            if (((k - H - 1) & 1) == 0) {
+                S.qr[k] = (a.x + b.x) * eq;
+                S.qi[k] = (a.y - b.y) * eq;
+            } else {
+                S.qr[k] = (a.y + b.y) * eq;
+                S.qi[k] = (b.x - a.x) * eq;
+            }
         }
         return;
     }
