@@ -624,11 +624,29 @@ __global__ void __launch_bounds__(128, 2) k_fft_pass64(const cpx<float>* __restr
             }
             SmallDFT<T, 64>::run(v);
             if (a.last) {
+                // output index o of element k grows by QA Ns per k; mode m = o or o - M
+                const int o0 = j0 + jj + (pp << logNs);
+                const int step = QA << logNs;
+                if (g < a.npk) {
+                    cpx<T>* plus = out + (int64_t)(2 * g) * a.N;
+                    cpx<T>* minus = plus + a.N;
 #pragma unroll
-                for (int k = 0; k < 64; ++k) {
-                    const int o = j0 + jj + ((pp + k * QA) << logNs);
-                    const int m = (o < M / 2) ? o : o - M;
-                    store_mode<T>(out, a, g, m, v[k]);
+                    for (int k = 0; k < 64; ++k) {
+                        const int o = o0 + k * step;
+                        const int jp = o - a.sh;                    // mode +(sh + jp)
+                        const int jm = ((M - o) & (M - 1)) - a.sh;  // mode -(sh + jm)
+                        if ((unsigned)jp < (unsigned)a.N) plus[jp] = v[k];
+                        if ((unsigned)jm < (unsigned)a.N) minus[jm] = v[k];
+                    }
+                } else {
+                    cpx<T>* spec = out + (int64_t)(a.npk + g) * a.N;
+                    const int lo_end = a.N - a.hN, hi_start = M - a.hN;
+#pragma unroll
+                    for (int k = 0; k < 64; ++k) {
+                        const int o = o0 + k * step;
+                        if (o < lo_end) spec[o + a.hN] = v[k];
+                        else if (o >= hi_start) spec[o - hi_start] = v[k];
+                    }
                 }
             } else if (same_radix) {
                 cpx<T>* gout = out + (int64_t)g * M;
