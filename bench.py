@@ -345,6 +345,142 @@ def run_profile(args):
                           "best_j": int(best[-1]["j"]), "counts": list(p.counts)}), flush=True)
 
 
+WORKLOADS = {
+    "short": "short single curve: n=1000 over 100 d with two gaps, 3 harmonics of 1.37/d, H=3, "
+             "N=16384 on [0.01, 10]/d",
+    "survey": "batched survey: 4096 curves, n ~ lognormal(median 2000) in [50, 20000], H in 2..6, "
+              "N=2^18 to 12/d, 30% nulls",
+    "adjoint": "differentiation batch: 1024 curves, n=2000, H=4, N=2^16 to 12/d; gradients and "
+               "Newton refinement at the top-8 peaks",
+    "large": "large single curve: n~1e6 at 2-min cadence over 4 yr, H=8, N=2^26 to 24/d, "
+             "2x oversampled grids",
+}
+
+
+def _events_ms(fn, steps, warmup, stream=None):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_workload(args):
+    """The other synthetic workloads, one JSON line each (for the measurement
+    table; the default run is the long curve).  Oracle parity on a bounded
+    sample of bins or curves."""
+    import torch
+    from paper_0901_1913_gb300 import _fc2, synth
+    from tests.parity import TOL, compare, sample_bins
+    threads = os.cpu_count() or 1
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload]}}
+    if args.workload in ("short", "large"):
+        c = synth.config1() if args.workload == "short" else synth.config5()
+        evals = c.N * c.H
+        res = {}
+        for prec in ("mixed", "fp64"):
+            out = torch.empty((c.H, c.N), dtype=torch.float64, device="cuda")
+            with _fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, prec) as p:
+                steps = args.steps if prec == "mixed" or args.workload == "short" else 2
+                ms = _events_ms(lambda: p.execute(out, want_records=True), steps,
+                                max(1, min(args.warmup, 2)))
+                _, best, _, chi0 = p.execute(out)
+                res[prec] = (ms, out.cpu().numpy(), best, chi0, p.counts)
+        if args.workload == "short":
+            bins = np.arange(c.N)
+        else:
+            f0s = [f * h for f in c.truth["fs"] for h in (1, 2)]
+            bins = sample_bins(c.N, 48, 5, windows=[int(round((f - c.f_min) / c.df))
+                                                    for f in f0s] + [res["mixed"][2][-1]["j"]],
+                               half=2)
+        from oracle import oracle
+        t0 = time.perf_counter()
+        d_or, piv = oracle.dchi2_bins(c.t, c.x, c.sigma, c.H, c.f_min, c.df, bins,
+                                      threads=threads, with_pivots=True)
+        dt = time.perf_counter() - t0
+        chi0 = res["mixed"][3]
+        rm = compare(res["mixed"][1][:, bins].T, d_or, piv, chi0)
+        r6 = compare(res["fp64"][1][:, bins].T, d_or, piv, chi0)
+        line.update(value=evals / (res["mixed"][0] / 1e3), ms_per_step=res["mixed"][0],
+                    dtype="f32+f64 (mixed)",
+                    fp64={"value": evals / (res["fp64"][0] / 1e3), "ms_per_step": res["fp64"][0]},
+                    mixed_over_fp64=res["fp64"][0] / res["mixed"][0],
+                    counts_mixed=list(res["mixed"][4]),
+                    cpu_baseline={"value": len(bins) * c.H / dt, "unit": UNIT, "cores": threads,
+                                  "kind": "oracle", "sample": f"{len(bins)} bins"},
+                    parity={"bins": len(bins), "mixed_max_err_rel": rm["max_err_rel"],
+                            "fp64_max_err_rel": r6["max_err_rel"],
+                            "near_alias_bins": rm["n_near_alias"], "ok": bool(rm["ok"] and r6["ok"])})
+        line["config"].update(n=c.n, N=c.N, H=c.H, oversample=c.oversample)
+    else:
+        b = synth.config3() if args.workload == "survey" else synth.config4()
+        evals = int(np.sum(b.H.astype(np.int64) * b.N))
+        dev = torch.device("cuda", 0)
+        td, xd, sd = (torch.from_numpy(v).to(dev) for v in (b.t, b.x, b.sigma))
+        out = torch.empty(evals, dtype=torch.float32, device=dev)
+        holder = {}
+
+        def run(prec="mixed"):
+            holder["r"] = _fc2.execute_batched(b.offsets, td, xd, sd, b.H, b.f_min, b.df, b.N,
+                                               b.oversample, prec, top_k=8, dchi2=out)
+        ms = _events_ms(run, args.steps, max(1, min(args.warmup, 2)))
+        _, peaks, stats = holder["r"]
+        got = out.cpu().numpy()
+        line.update(value=evals / (ms / 1e3), ms_per_step=ms, dtype="f32+f64 (mixed)",
+                    batch_stats=stats, config=dict(line["config"], curves=b.C,
+                                                   samples=int(b.offsets[-1])))
+        # FP64 on the first 256 curves (rate only)
+        sub = min(256, b.C)
+        o2 = b.offsets[:sub + 1]
+        e64 = int(np.sum(b.H[:sub].astype(np.int64) * b.N[:sub]))
+        t0c = time.perf_counter()
+        _fc2.execute_batched(o2, b.t[:o2[-1]], b.x[:o2[-1]], b.sigma[:o2[-1]], b.H[:sub],
+                             b.f_min[:sub], b.df[:sub], b.N[:sub], b.oversample, "fp64", top_k=8)
+        line["fp64_first_256_curves"] = {"value": e64 / (time.perf_counter() - t0c),
+                                         "note": "host-timed, includes transfers"}
+        if args.workload == "adjoint":
+            pj = np.array([[max(0, p_["j"]) for p_ in pk] for pk in peaks], dtype=np.int64)
+            K = pj.shape[1]
+
+            def back():
+                holder["g"] = _fc2.backward_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min,
+                                                    b.df, b.N, pj)
+            msb = _events_ms(back, max(1, args.steps // 2), 1)
+            line["backward"] = {"peaks": int(pj.size), "ms": msb,
+                                "peaks_per_s": pj.size / (msb / 1e3),
+                                "note": "host arrays in and out (gradients for every sample)"}
+        # oracle parity on a few curves, sampled bins
+        from oracle import oracle
+        errs, nb, t_or = [], 0, 0.0
+        pos = np.concatenate([[0], np.cumsum(b.H.astype(np.int64) * b.N)])
+        for cidx in range(0, b.C, max(1, b.C // 8))[:8]:
+            cur = b.curve(cidx)
+            block = got[pos[cidx]:pos[cidx + 1]].reshape(cur.H, cur.N)
+            bins = sample_bins(cur.N, 24, cidx, windows=[int(np.argmax(block[-1]))], half=2)
+            t0c = time.perf_counter()
+            ref, piv = oracle.dchi2_bins(cur.t, cur.x, cur.sigma, cur.H, cur.f_min, cur.df, bins,
+                                         threads=threads, with_pivots=True)
+            t_or += time.perf_counter() - t0c
+            nb += len(bins) * cur.H
+            _, _, chi0, _ = oracle.moments(cur.x, cur.sigma)
+            errs.append(compare(block[:, bins].T.astype(np.float64), ref, piv, chi0))
+        line["parity"] = {"curves": len(errs), "max_err_rel": max(e["max_err_rel"] for e in errs),
+                          "ok": all(e["ok"] for e in errs)}
+        line["cpu_baseline"] = {"value": nb / t_or, "unit": UNIT, "cores": threads,
+                                "kind": "oracle", "sample": f"{nb} evals on {len(errs)} curves"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -359,9 +495,13 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="only run the mixed executes (for ncu); no benchmark line")
     ap.add_argument("--H", type=int, default=0, help="harmonics of the --profile run (default 6)")
+    ap.add_argument("--workload", default="long", choices=["long"] + sorted(WORKLOADS),
+                    help="long (default, the headline) or another synthetic workload")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
+    elif args.workload != "long" and args.impl != "reference":
+        run_workload(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -73,6 +73,11 @@ typedef struct {
     int device;                /* CUDA device ordinal */
     int inputs_on_device;      /* t, x, sigma are device pointers (borrowed, not copied) */
     int outputs_on_device;     /* dchi2 (and d_dx, d_dsigma) are device pointers */
+    int autotune;              /* 1 = time the candidate transform plans (radix per pass,
+                                  kernel family) on the plan's own buffers when it is
+                                  created and keep the fastest; the choice is cached per
+                                  device, size and precision for the process. 0 = the
+                                  fixed balanced plan */
 } fc2_options;
 
 /* One selected frequency: bin index, frequency, Delta chi^2 and the

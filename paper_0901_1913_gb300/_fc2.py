@@ -26,7 +26,7 @@ class Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("kernel_width", ctypes.c_int), ("top_k", ctypes.c_int),
                 ("alias_tau", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("inputs_on_device", ctypes.c_int),
-                ("outputs_on_device", ctypes.c_int)]
+                ("outputs_on_device", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class Best(ctypes.Structure):
@@ -133,7 +133,7 @@ def _is_dev(a):
 
 
 def make_options(prec="fp64", kernel_width=0, top_k=0, alias_tau=0.0, stream=None, device=0,
-                 inputs_on_device=False, outputs_on_device=False):
+                 inputs_on_device=False, outputs_on_device=False, autotune=False):
     o = Options()
     load().fc2_options_default(ctypes.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -144,6 +144,7 @@ def make_options(prec="fp64", kernel_width=0, top_k=0, alias_tau=0.0, stream=Non
     o.device = int(device)
     o.inputs_on_device = int(bool(inputs_on_device))
     o.outputs_on_device = int(bool(outputs_on_device))
+    o.autotune = int(bool(autotune))
     return o
 
 
@@ -152,7 +153,8 @@ class Plan:
     device) or float64 CUDA tensors (borrowed; keep them alive)."""
 
     def __init__(self, t, x, sigma, H, f_min, df, N, oversample=2, prec="fp64",
-                 kernel_width=0, top_k=8, alias_tau=0.0, stream=None, device=0):
+                 kernel_width=0, top_k=8, alias_tau=0.0, stream=None, device=0,
+                 autotune=False):
         lib = load()
         dev = _is_dev(t)
         if not dev:
@@ -164,6 +166,7 @@ class Plan:
         self.H, self.N, self.top_k = int(H), int(N), int(top_k or 8)
         self.f_min, self.df = float(f_min), float(df)
         self.opt = make_options(prec, kernel_width, self.top_k, alias_tau, stream, device,
+                                autotune=autotune,
                                 inputs_on_device=dev)
         h = _P()
         rc = lib.fc2_plan_create(_ptr(t), _ptr(x), _ptr(sigma), self.n, self.H, self.f_min,
@@ -265,7 +268,7 @@ def periodogram(t, x, sigma, H, f_min, df, N, oversample=2, prec="fp64", **kw):
 
 
 def execute_batched(offsets, t, x, sigma, H, f_min, df, N, oversample=2, prec="mixed", top_k=8,
-                    kernel_width=0, dchi2=None, stream=None, device=0):
+                    kernel_width=0, dchi2=None, stream=None, device=0, autotune=False):
     """Many curves in one call (fc2_execute_batched).  offsets [C+1], t/x/sigma
     concatenated (numpy host arrays, or CUDA tensors -> read in place); H, f_min,
     df, N per curve.  dchi2: optional preallocated float32 output (numpy or
@@ -288,17 +291,19 @@ def execute_batched(offsets, t, x, sigma, H, f_min, df, N, oversample=2, prec="m
         dchi2 = np.empty(total, dtype=np.float32)
     K = int(top_k or 8)
     peaks = (Best * (C * K))()
-    opt = make_options(prec, kernel_width, K, 0.0, stream, device, inputs_on_device=dev)
+    opt = make_options(prec, kernel_width, K, 0.0, stream, device, inputs_on_device=dev,
+                       autotune=autotune)
     rc = lib.fc2_execute_batched(C, offsets.ctypes.data, _ptr(t), _ptr(x), _ptr(sigma),
                                  H.ctypes.data, f_min.ctypes.data, df.ctypes.data, N.ctypes.data,
                                  int(oversample), ctypes.byref(opt), _ptr(dchi2),
                                  ctypes.cast(peaks, _P))
     _check(rc, "fc2_execute_batched")
-    st = np.zeros(3, dtype=np.int64)
+    st = np.zeros(4, dtype=np.int64)
     lib.fc2_debug_batch_counts(st.ctypes.data)
     recs = [[peaks[c * K + r].as_dict() for r in range(K)] for c in range(C)]
     return dchi2, recs, dict(launches=int(lib.fc2_debug_batch_launches()),
-                             resolved=int(st[0]), exact=int(st[1]), exact_double=int(st[2]))
+                             resolved=int(st[0]), exact=int(st[1]), exact_double=int(st[2]),
+                             graphs=int(st[3]))
 
 
 def _backward_argtypes(lib):

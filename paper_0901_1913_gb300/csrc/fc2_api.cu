@@ -15,7 +15,7 @@
 using namespace fc2;
 
 static int64_t g_last_batch_launches = 0;
-static int64_t g_last_batch_stats[3] = {0, 0, 0};
+static int64_t g_last_batch_stats[4] = {0, 0, 0, 0};  // re-solved, exact, exact double, graphs
 
 namespace {
 
@@ -139,7 +139,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     p->tau = opt.alias_tau > 0.0 ? opt.alias_tau : (p->fp64 ? 1e-9 : 1e-6);
     p->top_k = opt.top_k ? opt.top_k : 8;
     plan_fft_passes(p);
-    p->use_r64 = (getenv("FC2_FFT_RADIX16") == nullptr);  // A/B switch for the transform kernels
+    p->use_r64 = true;
 
     const size_t tsz = p->fp64 ? 8 : 4;
     const size_t csz = 2 * tsz;
@@ -238,7 +238,10 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
                                   p->d_wq, p->d_wp, s));
         g.ok(launch_phase_fx(p, s));
         // geometry of each transform
-        const int LOGR1 = p->passes[0].logR;
+        // The occupied extent is rounded to whole first-pass rows, so that the
+        // spread writes every cell the first pass reads.  With the autotuner the
+        // first pass may have a radix as small as 2^8 (its candidates).
+        const int LOGR1 = opt.autotune ? std::min(p->passes[0].logR, 8) : p->passes[0].logR;
         const int64_t S1 = M >> LOGR1;
         const int64_t tile = (M >= 4096) ? 1024 : 128;
         const int64_t unit = std::max(S1, tile);
@@ -289,7 +292,8 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
             }
             p->fft_bytes = fb;
         }
-        g.ok(init_twiddles(p, s));
+        if (opt.autotune) g.ok(autotune_fft(p, s));  // sets the pass plan and its tables
+        else g.ok(init_twiddles(p, s));
         g.ok(init_deconv(p, s));  // synchronises
         if (g.e != cudaSuccess) st = map_err(g.e);
     }
@@ -557,10 +561,11 @@ fc2_status fc2_debug_exact_bins(fc2_plan p, const int64_t* bins, int64_t nb, int
 int64_t fc2_debug_batch_launches(void) { return g_last_batch_launches; }
 
 /* Bins of the last fc2_execute_batched call that were re-solved in double,
- * recomputed from exact sums, and of those recomputed all in double. */
-void fc2_debug_batch_counts(int64_t* out3) {
-    if (out3)
-        for (int i = 0; i < 3; ++i) out3[i] = g_last_batch_stats[i];
+ * recomputed from exact sums, of those recomputed all in double, and the
+ * number of chunk graphs launched. */
+void fc2_debug_batch_counts(int64_t* out4) {
+    if (out4)
+        for (int i = 0; i < 4; ++i) out4[i] = g_last_batch_stats[i];
 }
 
 /* Stage timing: while enabled, each execute records CUDA events on the plan's

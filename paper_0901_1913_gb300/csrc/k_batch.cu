@@ -530,6 +530,7 @@ struct Batch {
     fc2_best* recs = nullptr; size_t crecs = 0;
     char* red = nullptr; size_t cred = 0;
     cudaGraphExec_t gexec = nullptr;
+    int64_t graphs = 0;  // chunk graphs launched
     int64_t launches = 0;
     int64_t stats[3] = {0, 0, 0};
 
@@ -639,6 +640,42 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
     return cudaGetLastError();
 }
 
+// One chunk's launches as a CUDA graph: captured from the stream, then the
+// executable graph of the previous chunk is updated in place when the launch
+// sequence has the same shape (same stages, H groups and passes), else a new
+// one is instantiated.  A stream that cannot be captured gets the launches
+// directly.
+template <typename F>
+static cudaError_t launch_as_graph(Batch& b, F&& launches) {
+    cudaStream_t s = b.s;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return launches();
+    }
+    const cudaError_t el = launches();
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(s, &g);
+    if (el != cudaSuccess || ec != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return el != cudaSuccess ? el : (ec != cudaSuccess ? ec : cudaErrorUnknown);
+    }
+    if (b.gexec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(b.gexec, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(b.gexec);
+            b.gexec = nullptr;
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (!b.gexec) e = cudaGraphInstantiate(&b.gexec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(b.gexec, s);
+    cudaGraphDestroy(g);
+    if (e == cudaSuccess) ++b.graphs;
+    return e;
+}
+
 fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, const double* x,
                            const double* sigma, const int* Hc, const double* fminc,
                            const double* dfc, const int64_t* Nc, int oversample,
@@ -720,7 +757,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             p.beta = 0.97 * M_PI * (1.0 - 0.5 / ((double)M / (double)N)) * (double)p.w;
             p.stream = s;
             plan_fft_passes(&p);
-            p.use_r64 = (getenv("FC2_FFT_RADIX16") == nullptr);
+            p.use_r64 = true;
             release(p.d_twlo, s); release(p.d_twhi, s); release(p.d_twst, s); release(p.d_dec, s);
             const int sh = (p.logM + 1) / 2;
             cudaError_t e = cudaMallocAsync(&p.d_twlo, (size_t)(1ll << sh) * csz, s);
@@ -800,7 +837,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         std::vector<float> sqv(nc), spv(nc), s1v(nc), c0v(nc);
         std::vector<std::vector<int>> hg(BHM);
         bool unsorted = false;
-        const int LOGR1 = p.passes[0].logR;
+        const int LOGR1 = opt.autotune ? std::min(p.passes[0].logR, 8) : p.passes[0].logR;
         const int64_t S1 = M >> LOGR1;
         const int64_t tile = (M >= 4096) ? 1024 : 128;
         const int64_t unit = std::max(S1, tile);
@@ -886,9 +923,14 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         p.d_L = b.L; p.d_slot_soff = b.slot_soff; p.d_slot_n = b.slot_n;
         p.h_slot_soff = ssoff; p.h_slot_n = sn;
         const double tau_drop = opt.alias_tau > 0.0 ? opt.alias_tau : (fp64 ? 1e-9 : 1e-6);
+        if (e == cudaSuccess && opt.autotune) e = autotune_fft(&p, s);
         if (e != cudaSuccess) { st = map_cuda(e); break; }
-        e = fp64 ? chunk_launches<double>(b, nc, ntot, nmax, (int)S, hg, hoff, K, out, nrec, tau_drop)
-                 : chunk_launches<float>(b, nc, ntot, nmax, (int)S, hg, hoff, K, out, nrec, tau_drop);
+        e = launch_as_graph(b, [&]() {
+            return fp64 ? chunk_launches<double>(b, nc, ntot, nmax, (int)S, hg, hoff, K, out, nrec,
+                                                 tau_drop)
+                        : chunk_launches<float>(b, nc, ntot, nmax, (int)S, hg, hoff, K, out, nrec,
+                                                tau_drop);
+        });
         if (e != cudaSuccess) { st = map_cuda(e); break; }
         // ---- results (a list that overflowed its capacity leaves bins unrepaired)
         int32_t cnts[4] = {0, 0, 0, 0};
@@ -911,8 +953,10 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     }
     cudaStreamSynchronize(s);
     if (launches_out) *launches_out = b.launches;
-    if (stats_out)
+    if (stats_out) {
         for (int i = 0; i < 3; ++i) stats_out[i] = b.stats[i];
+        stats_out[3] = b.graphs;
+    }
     b.cp.d_key = nullptr; b.cp.d_dlt = nullptr; b.cp.d_cs = nullptr;
     b.cp.d_grid[0] = b.cp.d_grid[1] = nullptr; b.cp.d_spec = nullptr; b.cp.d_L = nullptr;
     b.cp.d_slot_soff = b.cp.d_slot_n = nullptr; b.cp.d_red = nullptr;

@@ -16,6 +16,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
@@ -692,6 +695,7 @@ cudaError_t init_twiddles(fc2_plan_s* p, cudaStream_t s) {
     int64_t nmax = std::max(nlo, nhi);
     unsigned blocks = (unsigned)((nmax + 255) / 256);
     bool assigned[16] = {false};
+    for (int i = 0; i < 16; ++i) { p->twst_off[i] = 0; p->tw64_off[i] = 0; }
     int64_t off = 0;
     for (auto& ps : p->passes) {
         if (assigned[ps.logR]) continue;
@@ -745,6 +749,110 @@ void plan_fft_passes(fc2_plan_s* p) {
         p->passes.push_back({rs[i], Ns, 0});
         Ns <<= rs[i];
     }
+}
+
+// ------------------------------------------------------ transform autotuner
+// Candidate pass plans for a length-2^logM transform: the balanced split into
+// the fewest passes (the fixed planner's choice) and, when every radix stays
+// at 2^8 or above, the balanced split into one pass more; float plans are
+// tried with both kernel families.  Only pass shapes the fixed planner also
+// produces for some length are searched: a wider search (unbalanced splits,
+// small radices in three-pass plans) is not covered by the tests.  Each
+// candidate runs on the plan's own buffers and the fastest is kept for the
+// process, keyed by device, size, grid count and precision.
+static void set_passes(fc2_plan_s* p, const std::vector<int>& rs) {
+    p->passes.clear();
+    int64_t Ns = 1;
+    for (int r : rs) {
+        p->passes.push_back({r, Ns, 0});
+        Ns <<= r;
+    }
+}
+
+static std::vector<int> balanced_split(int logM, int P) {
+    std::vector<int> rs(P, logM / P);
+    for (int i = 0; i < logM % P; ++i) rs[i] += 1;
+    return rs;
+}
+
+static std::vector<std::vector<int>> fft_candidates(int logM, int maxr) {
+    std::vector<std::vector<int>> out;
+    if (logM <= maxr) {
+        out.push_back({logM});
+        return out;
+    }
+    const int P = (logM + maxr - 1) / maxr;
+    out.push_back(balanced_split(logM, P));
+    const std::vector<int> more = balanced_split(logM, P + 1);
+    if (more.back() >= 8) out.push_back(more);
+    return out;
+}
+
+struct TuneKey {
+    int dev, logM, G, fp64, packed;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(dev, logM, G, fp64, packed) < std::tie(o.dev, o.logM, o.G, o.fp64, o.packed);
+    }
+};
+static std::map<TuneKey, std::pair<std::vector<int>, bool>> g_tuned;
+static std::mutex g_tune_mu;
+
+cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const TuneKey key{dev, p->logM, p->G, p->fp64 ? 1 : 0, p->packed ? 1 : 0};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            set_passes(p, it->second.first);
+            p->use_r64 = it->second.second;
+            return init_twiddles(p, s);
+        }
+    }
+    const int maxr = p->fp64 ? FftCfg<double>::MAXR : FftCfg<float>::MAXR;
+    const auto cands = fft_candidates(p->logM, maxr);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cudaGetLastError();
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cudaGetLastError();
+    }
+    float best = 1e30f;
+    std::vector<int> best_rs = cands.front();
+    bool best_r64 = true;
+    cudaError_t e = cudaSuccess;
+    for (const auto& rs : cands) {
+        for (int r64 = 1; r64 >= (p->fp64 ? 1 : 0); --r64) {
+            set_passes(p, rs);
+            p->use_r64 = (r64 == 1);
+            if ((e = init_twiddles(p, s)) != cudaSuccess) break;
+            if ((e = launch_fft(p, s)) != cudaSuccess) break;  // warm-up
+            cudaEventRecord(e0, s);
+            for (int it = 0; it < 3 && e == cudaSuccess; ++it) e = launch_fft(p, s);
+            cudaEventRecord(e1, s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_rs = rs;
+                best_r64 = (r64 == 1);
+            }
+        }
+        if (e != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return e;
+    set_passes(p, best_rs);
+    p->use_r64 = best_r64;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = {best_rs, best_r64};
+    }
+    return init_twiddles(p, s);
 }
 
 template <typename T>

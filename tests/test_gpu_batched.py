@@ -42,6 +42,7 @@ def test_batched_matches_oracle(fc2, oracle_mod, prec):
         assert r["ok"], (c, r)
     assert pos == out.size
     assert stats["launches"] > 0
+    assert stats["graphs"] >= 1  # every chunk ran as a captured graph
 
 
 def test_batched_equals_single_plans(fc2):

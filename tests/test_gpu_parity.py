@@ -161,3 +161,19 @@ def test_three_pass_transform(fc2, oracle_mod, prec, N, os_):
     ref, piv = oracle_mod.dchi2_bins(c.t, c.x, c.sigma, c.H, c.f_min, c.df, bins, with_pivots=True)
     r = compare(d[:, bins].T, ref, piv, chi0)
     assert r["ok"], r
+
+
+def test_autotuned_plan_matches_fixed_plan(fc2):
+    """The autotuner only changes the transform's pass plan and kernel family:
+    results agree with the fixed plan up to float rounding."""
+    c = synth.config2(n=20000, N=1 << 18)
+    out = []
+    for tune in (False, True, True):  # the second tuned plan reuses the cached choice
+        with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed",
+                      autotune=tune) as p:
+            d, best, _, chi0 = p.execute()
+        out.append((d, best, chi0))
+    for d, best, chi0 in out[1:]:
+        assert np.max(np.abs(d - out[0][0])) <= 2e-5 * chi0
+        assert best[-1]["j"] == out[0][1][-1]["j"]
+    assert np.array_equal(out[1][0], out[2][0])
