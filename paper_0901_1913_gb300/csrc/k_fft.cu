@@ -481,8 +481,11 @@ __global__ void k_init_tw64(cpx<T>* tw, int LOGR) {
     tw[i] = mk<T>((T)cn, (T)sn);
 }
 
+constexpr int P64_NT = 256;                 // threads of a radix-64 pass CTA (one CTA per SM)
+constexpr int P64_LOGE = 14;                // log2 of its tile: 64 elements per thread
+
 template <int LOGR, int LOGJ>
-__global__ void __launch_bounds__(128, 2) k_fft_pass64(const cpx<float>* __restrict__ in,
+__global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __restrict__ in,
                                                        cpx<float>* __restrict__ out, PassArgs a,
                                                        const int64_t* __restrict__ Lg,
                                                        const cpx<float>* __restrict__ twlo,
@@ -490,7 +493,7 @@ __global__ void __launch_bounds__(128, 2) k_fft_pass64(const cpx<float>* __restr
                                                        const cpx<float>* __restrict__ tw64,
                                                        int G) {
     using T = float;
-    constexpr int R = 1 << LOGR, J = 1 << LOGJ, E = R * J, NT = 128;
+    constexpr int R = 1 << LOGR, J = 1 << LOGJ, E = R * J, NT = P64_NT;
     constexpr int QAB = LOGR - 6, QA = 1 << QAB;
     constexpr int PERA = 64 / QA;  // stage-A butterflies per thread
     static_assert(E == 64 * NT, "tile must be 64 elements per thread");
@@ -855,9 +858,12 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
     return init_twiddles(p, s);
 }
 
+// Tile width (columns) of the pass with radix 2^logR: the radix-64 kernel's
+// tiles hold 2^P64_LOGE elements, the radix-16 kernel's 2^LOGE.
 template <typename T>
-static int logj_of(int logR, int logM) {
-    if (logR == logM) return 0;  // single pass: one column
+static int logj_of(const fc2_plan_s* p, int logR) {
+    if (logR == p->logM) return 0;  // single pass: one column
+    if (sizeof(T) == 4 && p->use_r64 && logR >= 10 && logR <= 12) return P64_LOGE - logR;
     return FftCfg<T>::LOGE - logR;
 }
 
@@ -883,7 +889,7 @@ static cudaError_t run_pass(fc2_plan_s* p, const void* in, void* out, const Pass
 template <int LOGR>
 static cudaError_t run_pass64(fc2_plan_s* p, const void* in, void* out, const PassArgs& a,
                               cudaStream_t s) {
-    constexpr int LOGJ = 13 - LOGR, E = 1 << 13;
+    constexpr int LOGJ = P64_LOGE - LOGR, E = 1 << P64_LOGE;
     const int64_t S = p->M >> LOGR;
     const size_t smem = (size_t)(E + 63 * (1 << (LOGR - 6))) * sizeof(cpx<float>);
     auto kern = k_fft_pass64<LOGR, LOGJ>;
@@ -900,8 +906,8 @@ static cudaError_t run_pass64(fc2_plan_s* p, const void* in, void* out, const Pa
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (nsm <= 0) nsm = 152;
     }
-    const unsigned blocks = (unsigned)std::min<int64_t>(ntiles, 2 * (int64_t)nsm);
-    kern<<<blocks, 128, smem, s>>>((const cpx<float>*)in, (cpx<float>*)out, a, p->d_L,
+    const unsigned blocks = (unsigned)std::min<int64_t>(ntiles, (int64_t)nsm);
+    kern<<<blocks, P64_NT, smem, s>>>((const cpx<float>*)in, (cpx<float>*)out, a, p->d_L,
                                    (const cpx<float>*)p->d_twlo, (const cpx<float>*)p->d_twhi,
                                    (const cpx<float>*)p->d_twst + p->tw64_off[LOGR], p->G);
     return cudaGetLastError();
@@ -937,7 +943,7 @@ static cudaError_t fft_impl(fc2_plan_s* p, cudaStream_t s) {
         a.first = (i == 0);
         a.last = (i == P - 1);
         a.logRn = a.last ? 0 : p->passes[i + 1].logR;
-        a.logJn = a.last ? 0 : logj_of<T>(p->passes[i + 1].logR, p->logM);
+        a.logJn = a.last ? 0 : logj_of<T>(p, p->passes[i + 1].logR);
         a.N = (int)p->N;
         a.hN = (int)(p->N / 2);
         a.tws = p->tw_shift;
