@@ -323,6 +323,7 @@ def run_gpu(args):
                                                     stage_ms)},
         "bins_resolved_double": counts[0], "bins_exact_sums": counts[1],
         "bins_exact_double_float": counts[2], "bins_exact_double": counts[3],
+        "bins_routed_tiers": list(counts[4:7]),
         "parity": parity,
     }
     print(json.dumps(line), flush=True)

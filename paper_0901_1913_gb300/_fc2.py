@@ -213,9 +213,10 @@ class Plan:
 
     @property
     def counts(self):
-        """(bins re-solved in double, bins recomputed from exact sums, of which
-        double-float, of which all-double) in the last execute."""
-        c = np.zeros(4, dtype=np.int64)
+        """(bins re-solved in double, bins recomputed from exact sums, bins
+        through double-float sums, bins through all-double sums, then the bins
+        first routed to tiers 1, 2, 3) in the last execute."""
+        c = np.zeros(7, dtype=np.int64)
         load().fc2_debug_counts(self.h, c.ctypes.data)
         return tuple(int(v) for v in c)
 

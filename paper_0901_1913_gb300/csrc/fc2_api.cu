@@ -194,7 +194,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         g.ok(dalloc(&p->d_twhi, (size_t)(M >> ((p->logM + 1) / 2)) * csz, s)) &&
         g.ok(dalloc(&p->d_twst, (size_t)(8 * 4096 + 256) * csz, s)) &&
         g.ok(dalloc(&p->d_dchi2, (size_t)H * N * 8, s)) &&
-        g.ok(dalloc(&p->d_flag_list, (size_t)N * 4 * 3, s)) &&
+        g.ok(dalloc(&p->d_flag_list, (size_t)N * 4 * 4, s)) &&
         g.ok(dalloc(&p->d_flag_count, 16, s)) && g.ok(dalloc(&p->d_L, (size_t)G * 8, s)) &&
         g.ok(dalloc(&p->d_red, red_b, s)) &&
         g.ok(dalloc(&p->d_best, (size_t)(H + p->top_k) * sizeof(fc2_best), s));
@@ -333,16 +333,17 @@ static fc2_status run_pipeline(fc2_plan_s* p) {
     rec(p, 2);
     g.ok(launch_assemble(p, s));
     rec(p, 3);
-    int32_t fc[2] = {0, 0};
-    g.ok(cudaMemcpyAsync(fc, p->d_flag_count, 8, cudaMemcpyDeviceToHost, s));
+    int32_t fc[4] = {0, 0, 0, 0};  // tier-1 list, re-solve list, tier-2 list, tier-3 list
+    g.ok(cudaMemcpyAsync(fc, p->d_flag_count, 16, cudaMemcpyDeviceToHost, s));
     g.ok(cudaStreamSynchronize(s));
     if (g.e != cudaSuccess) return map_err(g.e);
-    p->last_flag_count = fc[0];
     p->last_resolve_count = fc[1];
-    if (fc[1] > p->flag_cap) return FC2_ERR_NUMERIC;
-    const int64_t nfix = fc[0];
-    if (nfix > p->flag_cap) return FC2_ERR_NUMERIC;
-    g.ok(launch_fixup(p, nfix, s));
+    p->last_flag_count = (int64_t)fc[0] + fc[2] + fc[3];
+    p->last_routed[0] = fc[0]; p->last_routed[1] = fc[2]; p->last_routed[2] = fc[3];
+    for (int i = 0; i < 4; ++i)
+        if (fc[i] > p->flag_cap) return FC2_ERR_NUMERIC;
+    const int64_t nfix = p->last_flag_count;
+    g.ok(launch_fixup(p, fc[0], fc[2], fc[3], s));
     rec(p, 4);
     g.ok(launch_peaks(p, s));
     rec(p, 5);
@@ -453,15 +454,16 @@ fc2_status fc2_backward(fc2_plan p, int K, const int64_t* peak_j, const double* 
 int64_t fc2_debug_flag_count(fc2_plan p) { return p ? p->last_flag_count : -1; }
 
 /* Counts of the last execute: [0] bins re-solved in double (mixed path),
- * [1] bins recomputed from exact sums (tier 1), [2] of those, bins that
- * needed double-float sums (tier 2), [3] of those, bins that needed all-double
- * sums (tier 3). */
-void fc2_debug_counts(fc2_plan p, int64_t* out4) {
-    if (!p || !out4) return;
-    out4[0] = p->last_resolve_count;
-    out4[1] = p->last_flag_count;
-    out4[2] = p->last_exact2_count;
-    out4[3] = p->last_exact3_count;
+ * [1] bins recomputed from exact sums, [2] of those, bins that went through
+ * double-float sums (tier 2), [3] bins that went through all-double sums
+ * (tier 3), [4..6] bins first routed to tiers 1, 2, 3. */
+void fc2_debug_counts(fc2_plan p, int64_t* out7) {
+    if (!p || !out7) return;
+    out7[0] = p->last_resolve_count;
+    out7[1] = p->last_flag_count;
+    out7[2] = p->last_exact2_count;
+    out7[3] = p->last_exact3_count;
+    for (int i = 0; i < 3; ++i) out7[4 + i] = p->last_routed[i];
 }
 
 fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im) {
@@ -526,7 +528,7 @@ int64_t fc2_debug_tier_bins(fc2_plan p, int tier, int64_t* out, int64_t cap) {
     const int64_t cnt = tier == 2 ? p->last_exact2_count : p->last_exact3_count;
     const int64_t nb = std::min(cap, std::min(cnt, (int64_t)p->flag_cap));
     std::vector<int32_t> b((size_t)std::max<int64_t>(nb, 1));
-    if (nb > 0 && cudaMemcpy(b.data(), p->d_flag_list + (size_t)(tier - 1) * p->flag_cap,
+    if (nb > 0 && cudaMemcpy(b.data(), p->d_flag_list + (size_t)tier * p->flag_cap,
                              (size_t)nb * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
         return -1;
     for (int64_t i = 0; i < nb; ++i) out[i] = b[(size_t)i];

@@ -131,6 +131,7 @@ struct fc2_plan_s {
     int64_t last_flag_count = 0;
     int64_t last_exact2_count = 0;
     int64_t last_exact3_count = 0;
+    int64_t last_routed[3] = {0, 0, 0};  // bins first sent to fix-up tiers 1..3
     int64_t last_resolve_count = 0;
     bool has_perm = false;
     // stage timing (events recorded around each stage while enabled)
@@ -170,7 +171,7 @@ cudaError_t launch_fft(fc2_plan_s* p, cudaStream_t s);
 
 // k_solve.cu
 cudaError_t launch_assemble(fc2_plan_s* p, cudaStream_t s);
-cudaError_t launch_fixup(fc2_plan_s* p, int64_t count, cudaStream_t s);
+cudaError_t launch_fixup(fc2_plan_s* p, int64_t n1, int64_t n2, int64_t n3, cudaStream_t s);
 cudaError_t launch_exact_bins(fc2_plan_s* p, int64_t nb, int tier, cudaStream_t s);
 cudaError_t launch_peaks(fc2_plan_s* p, cudaStream_t s);
 size_t peaks_scratch_bytes(int64_t N, int H, int K);

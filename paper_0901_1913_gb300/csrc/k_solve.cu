@@ -32,6 +32,7 @@ struct SolveParams {
     double eps_f32;    // extra error of a float factorisation
     double err_fix;    // bins whose estimated normalised error exceeds this are recomputed
     double sq, sp, chi0, s1n;  // 1/W, 1/sqrt(W chi2_0), chi2_0, sum w(x - xbar) / sqrt(W chi2_0)
+    double eps_t1, eps_t2;     // precision of the tier-1 and tier-2 exact sums (routing)
     // float copies for the float path (a conversion per thread would run on the
     // double pipe): sq, sp, chi0, s1n, tau, eps_spec + eps_f32, err_fix
     float fsq, fsp, fchi0, fs1n, ftau, feps, ferr;
@@ -171,7 +172,11 @@ __global__ void __launch_bounds__(128) k_resolve(const cpx<float>* __restrict__ 
                                                  const int32_t* __restrict__ rlist,
                                                  const int32_t* __restrict__ rcount, int64_t rcap,
                                                  int32_t* __restrict__ flist,
-                                                 int32_t* __restrict__ fcount, int64_t fcap) {
+                                                 int32_t* __restrict__ fcount, int64_t fcap,
+                                                 int32_t* __restrict__ flist2,
+                                                 int32_t* __restrict__ fcount2,
+                                                 int32_t* __restrict__ flist3,
+                                                 int32_t* __restrict__ fcount3) {
     int64_t cnt = *rcount;
     if (cnt > rcap) cnt = rcap;
     const int64_t wpb = blockDim.x >> 5;
@@ -189,8 +194,21 @@ __global__ void __launch_bounds__(128) k_resolve(const cpx<float>* __restrict__ 
         warp_chol_solve<H, true>(S, sp.tau, out, &an2);
         if ((threadIdx.x & 31) == 0) {
             if (!(est_err<double>(an2, 2 * H + 1, sp.eps_spec) <= sp.err_fix)) {
-                int32_t pos = atomicAdd(fcount, 1);
-                if (pos < fcap) flist[pos] = (int32_t)j;
+                // exact fix-up: start at the cheapest tier whose precision the
+                // coefficient norm of these (gridded) equations says is enough;
+                // each tier still checks its own result and passes bins on
+                const int m = 2 * H + 1;
+                int32_t *lst = flist, *cnt = fcount;
+                if (!(est_err<double>(an2, m, sp.eps_t1) <= sp.err_fix)) {
+                    lst = flist2;
+                    cnt = fcount2;
+                    if (!(est_err<double>(an2, m, sp.eps_t2) <= sp.err_fix)) {
+                        lst = flist3;
+                        cnt = fcount3;
+                    }
+                }
+                int32_t pos = atomicAdd(cnt, 1);
+                if (pos < fcap) lst[pos] = (int32_t)j;
             }
 #pragma unroll
             for (int h = 0; h < H; ++h) dchi2[(int64_t)h * sp.N + j] = out[h] * sp.chi0;
@@ -723,6 +741,8 @@ static SolveParams solve_params(const fc2_plan_s* p) {
     sp.chi0 = chi0;
     sp.s1n = p->scal[SC_S1] * sp.sp;
     sp.fsq = (float)sp.sq; sp.fsp = (float)sp.sp; sp.fchi0 = (float)sp.chi0;
+    sp.eps_t1 = 2e-7 * p->scal[SC_RW];
+    sp.eps_t2 = 1.5e-12;  // EPS_DF
     sp.fs1n = (float)sp.s1n; sp.ftau = (float)sp.tau;
     sp.feps = (float)(sp.eps_spec + sp.eps_f32); sp.ferr = (float)sp.err_fix;
     return sp;
@@ -747,7 +767,10 @@ static cudaError_t assemble_impl(fc2_plan_s* p, cudaStream_t s) {
                                                   (const float*)p->d_dec_p, p->npk,           \
                                                   p->d_dchi2, sp, list, cnt, p->flag_cap,     \
                                                   p->d_flag_list, p->d_flag_count,            \
-                                                  p->flag_cap);                               \
+                                                  p->flag_cap, p->d_flag_list + 2 * p->flag_cap,  \
+                                                  p->d_flag_count + 2,                        \
+                                                  p->d_flag_list + 3 * p->flag_cap,           \
+                                                  p->d_flag_count + 3);                       \
         break;
     switch (p->H) {
         FC2_ASM(1) FC2_ASM(2) FC2_ASM(3) FC2_ASM(4) FC2_ASM(5) FC2_ASM(6) FC2_ASM(7) FC2_ASM(8)
@@ -775,38 +798,38 @@ static void launch_partial(fc2_plan_s* p, const int32_t* b32, const int64_t* b64
 constexpr double EPS_DF = 1.5e-12;
 constexpr double ERR_FIX = 2e-5;
 
-// Exact fix-up of the flagged bins (list 0, `count` entries) in up to three
-// tiers: every bin gets tier-1 sums; bins tier 1 cannot settle go to tier 2
-// and from there to tier 3.  Rounds of at most exact_cap bins.  The later
+// Exact fix-up of the flagged bins in up to three tiers.  Bins start at the
+// tier the re-solve routed them to (lists 0, 2, 3 with n1, n2, n3 entries;
+// the double path routes everything to tier 1); a bin that a tier cannot
+// settle moves on to the next.  Rounds of at most exact_cap bins.  The later
 // tiers read their bin counts on the device, so nothing waits for the host.
 template <int HH>
-static cudaError_t fixup_h(fc2_plan_s* p, int64_t count, cudaStream_t s) {
+static cudaError_t fixup_h(fc2_plan_s* p, int64_t n1, int64_t n2, int64_t n3, cudaStream_t s) {
     const int64_t cap = p->exact_cap;
     const double eps_t1 = 2e-7 * p->scal[SC_RW];
     int32_t* list1 = p->d_flag_list;
-    int32_t* list2 = p->d_flag_list + p->flag_cap;  // re-solve list is consumed by now
-    int32_t* list3 = p->d_flag_list + 2 * p->flag_cap;
+    int32_t* list2 = p->d_flag_list + 2 * p->flag_cap;
+    int32_t* list3 = p->d_flag_list + 3 * p->flag_cap;
     int32_t* cnt1 = p->d_flag_count;
     int32_t* cnt2 = p->d_flag_count + 2;
     int32_t* cnt3 = p->d_flag_count + 3;
-    cudaMemsetAsync(cnt2, 0, 8, s);
-    if (count <= 0) return cudaGetLastError();
-    for (int64_t base = 0; base < count; base += cap) {
-        const unsigned blocks = (unsigned)std::min(cap, count - base);
+    const int64_t b2 = n1 + n2, b3 = n1 + n2 + n3;  // upper bounds after escalation
+    for (int64_t base = 0; base < n1; base += cap) {
+        const unsigned blocks = (unsigned)std::min(cap, n1 - base);
         launch_partial<HH, 1>(p, list1, nullptr, cnt1, 0, base, cap, s);
         k_exact_dchi2<HH><<<blocks, 32, 0, s>>>(p->d_part, p->n, list1, cnt1, base, cap, p->d_scal,
                                                  1e-13, eps_t1, ERR_FIX, list2, cnt2, p->flag_cap,
                                                  p->d_dchi2, p->N);
     }
-    for (int64_t base = 0; base < count; base += cap) {
-        const unsigned blocks = (unsigned)std::min(cap, count - base);
+    for (int64_t base = 0; base < b2; base += cap) {
+        const unsigned blocks = (unsigned)std::min(cap, b2 - base);
         launch_partial<HH, 2>(p, list2, nullptr, cnt2, 0, base, cap, s);
         k_exact_dchi2<HH><<<blocks, 32, 0, s>>>(p->d_part, p->n, list2, cnt2, base, cap, p->d_scal,
                                                  1e-13, EPS_DF, ERR_FIX, list3, cnt3, p->flag_cap,
                                                  p->d_dchi2, p->N);
     }
-    for (int64_t base = 0; base < count; base += cap) {
-        const unsigned blocks = (unsigned)std::min(cap, count - base);
+    for (int64_t base = 0; base < b3; base += cap) {
+        const unsigned blocks = (unsigned)std::min(cap, b3 - base);
         launch_partial<HH, 3>(p, list3, nullptr, cnt3, 0, base, cap, s);
         k_exact_dchi2<HH><<<blocks, 32, 0, s>>>(p->d_part, p->n, list3, cnt3, base, cap, p->d_scal,
                                                  1e-13, 0.0, ERR_FIX, nullptr, nullptr, 0,
@@ -846,16 +869,16 @@ cudaError_t launch_exact_bins(fc2_plan_s* p, int64_t nb, int tier, cudaStream_t 
     }
 }
 
-cudaError_t launch_fixup(fc2_plan_s* p, int64_t count, cudaStream_t s) {
+cudaError_t launch_fixup(fc2_plan_s* p, int64_t n1, int64_t n2, int64_t n3, cudaStream_t s) {
     switch (p->H) {
-        case 1: return fixup_h<1>(p, count, s);
-        case 2: return fixup_h<2>(p, count, s);
-        case 3: return fixup_h<3>(p, count, s);
-        case 4: return fixup_h<4>(p, count, s);
-        case 5: return fixup_h<5>(p, count, s);
-        case 6: return fixup_h<6>(p, count, s);
-        case 7: return fixup_h<7>(p, count, s);
-        case 8: return fixup_h<8>(p, count, s);
+        case 1: return fixup_h<1>(p, n1, n2, n3, s);
+        case 2: return fixup_h<2>(p, n1, n2, n3, s);
+        case 3: return fixup_h<3>(p, n1, n2, n3, s);
+        case 4: return fixup_h<4>(p, n1, n2, n3, s);
+        case 5: return fixup_h<5>(p, n1, n2, n3, s);
+        case 6: return fixup_h<6>(p, n1, n2, n3, s);
+        case 7: return fixup_h<7>(p, n1, n2, n3, s);
+        case 8: return fixup_h<8>(p, n1, n2, n3, s);
         default: return cudaErrorInvalidValue;
     }
 }
