@@ -191,6 +191,20 @@ void fc2_plan_destroy(fc2_plan p);
 const char* fc2_status_string(fc2_status s);
 
 /*
+ * fc2_trim_device_memory -- return to the system the device memory the
+ * library keeps for reuse on `device`.
+ *
+ * Plans and batched calls take device memory from a stream-ordered pool the
+ * library owns (one per device); memory they release stays in that pool so the
+ * next plan does not have to map it again.  No counterpart in the paper.
+ * Waits for all work on the device, then trims the pool to zero bytes.
+ * Returns FC2_OK (also when the library never allocated on `device`) or
+ * FC2_ERR_CUDA.  Must not be called while plans on that device are in use
+ * from other threads.
+ */
+fc2_status fc2_trim_device_memory(int device);
+
+/*
  * fc2_dchi2_exact_noalloc -- exact (ungridded, double) Delta chi^2_{H'} for
  * H' = 1..H at trial bins j (f = f_min + j df), computed straight from the
  * samples, without allocating any device memory.  The paper has no

@@ -104,6 +104,8 @@ def load():
         lib.fc2_debug_exact_bins.restype = i32
         lib.fc2_debug_tier_bins.argtypes = [_P, i32, _P, i64]
         lib.fc2_debug_tier_bins.restype = i64
+        lib.fc2_trim_device_memory.argtypes = [i32]
+        lib.fc2_trim_device_memory.restype = i32
         lib.fc2_debug_t0.argtypes = [_P]
         lib.fc2_debug_t0.restype = dbl
         _lib = lib
@@ -260,6 +262,11 @@ class Plan:
     @property
     def t0(self):
         return float(load().fc2_debug_t0(self.h))
+
+
+def trim_device_memory(device=0):
+    """Return the library's cached device memory on `device` to the system."""
+    _check(load().fc2_trim_device_memory(int(device)), "fc2_trim_device_memory")
 
 
 def periodogram(t, x, sigma, H, f_min, df, N, oversample=2, prec="fp64", **kw):

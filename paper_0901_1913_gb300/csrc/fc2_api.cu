@@ -7,6 +7,8 @@
 
 #include <algorithm>
 #include <new>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "fc2_common.cuh"
@@ -16,6 +18,50 @@ using namespace fc2;
 
 static int64_t g_last_batch_launches = 0;
 static int64_t g_last_batch_stats[4] = {0, 0, 0, 0};  // re-solved, exact, exact double, graphs
+
+// Device memory comes from one stream-ordered pool per device owned by the
+// library.  Memory that a destroyed plan returns stays mapped in the pool
+// (unlimited release threshold), so plans created one after another reuse it
+// instead of mapping gigabytes afresh; fc2_trim_device_memory hands it back.
+namespace fc2 {
+static std::mutex g_pool_mu;
+static std::map<int, cudaMemPool_t> g_pools;
+
+static cudaMemPool_t device_pool(int dev) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) return it->second;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    g_pools[dev] = pool;
+    return pool;
+}
+
+cudaError_t pool_alloc(void** ptr, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    cudaMemPool_t pool = device_pool(dev);
+    if (!pool) return cudaMallocAsync(ptr, bytes, s);
+    return cudaMallocFromPoolAsync(ptr, bytes, pool, s);
+}
+
+static cudaMemPool_t existing_pool(int dev) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    return it == g_pools.end() ? nullptr : it->second;
+}
+}  // namespace fc2
 
 namespace {
 
@@ -27,6 +73,7 @@ struct Guard {  // returns FC2_ERR_CUDA on the first failing runtime call
     }
 };
 
+
 fc2_status map_err(cudaError_t e) {
     if (e == cudaSuccess) return FC2_OK;
     if (e == cudaErrorMemoryAllocation) return FC2_ERR_OOM;
@@ -37,7 +84,7 @@ template <typename P>
 cudaError_t dalloc(P** ptr, size_t bytes, cudaStream_t s) {
     *ptr = nullptr;
     if (bytes == 0) bytes = 16;
-    return cudaMallocAsync((void**)ptr, bytes, s);
+    return pool_alloc((void**)ptr, bytes, s);
 }
 
 template <typename P>
@@ -585,6 +632,14 @@ fc2_status fc2_stage_timing(fc2_plan p, int enable) {
     for (int i = 0; i < 8; ++i) p->stage_ms[i] = 0.0;
     p->stage_n = 0;
     return FC2_OK;
+}
+
+fc2_status fc2_trim_device_memory(int device) {
+    cudaMemPool_t pool = existing_pool(device);
+    if (!pool) return FC2_OK;
+    if (cudaSetDevice(device) != cudaSuccess) return FC2_ERR_CUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return FC2_ERR_CUDA;
+    return cudaMemPoolTrimTo(pool, 0) == cudaSuccess ? FC2_OK : FC2_ERR_CUDA;
 }
 
 fc2_status fc2_stage_times(fc2_plan p, double* ms5, int64_t* launches, double* fft_bytes) {

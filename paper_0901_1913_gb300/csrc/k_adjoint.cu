@@ -273,13 +273,13 @@ fc2_status plan_backward(fc2_plan_s* p, int K, const int64_t* peak_j, const doub
     double *o_f = nullptr, *o_d = nullptr, *o_df = nullptr, *o_dx = nullptr, *o_ds = nullptr;
     cudaError_t e = cudaSuccess;
     auto ok = [&](cudaError_t r) { if (e == cudaSuccess) e = r; return e == cudaSuccess; };
-    ok(cudaMallocAsync(&d_off, 16, s)) && ok(cudaMallocAsync(&d_H, 4, s)) &&
-        ok(cudaMallocAsync(&d_fmin, 8, s)) && ok(cudaMallocAsync(&d_df_c, 8, s)) &&
-        ok(cudaMallocAsync(&d_ent, K * 8, s)) && ok(cudaMallocAsync(&o_f, K * 8, s)) &&
-        ok(cudaMallocAsync(&o_d, K * 8, s)) && ok(cudaMallocAsync(&o_df, K * 8, s));
-    if (grad_out) ok(cudaMallocAsync(&d_g, K * 8, s));
-    if (d_dx && !dx_dev) ok(cudaMallocAsync(&o_dx, (size_t)K * n * 8, s));
-    if (d_dsig && !ds_dev) ok(cudaMallocAsync(&o_ds, (size_t)K * n * 8, s));
+    ok(pool_alloc((void**)&d_off, 16, s)) && ok(pool_alloc((void**)&d_H, 4, s)) &&
+        ok(pool_alloc((void**)&d_fmin, 8, s)) && ok(pool_alloc((void**)&d_df_c, 8, s)) &&
+        ok(pool_alloc((void**)&d_ent, K * 8, s)) && ok(pool_alloc((void**)&o_f, K * 8, s)) &&
+        ok(pool_alloc((void**)&o_d, K * 8, s)) && ok(pool_alloc((void**)&o_df, K * 8, s));
+    if (grad_out) ok(pool_alloc((void**)&d_g, K * 8, s));
+    if (d_dx && !dx_dev) ok(pool_alloc((void**)&o_dx, (size_t)K * n * 8, s));
+    if (d_dsig && !ds_dev) ok(pool_alloc((void**)&o_ds, (size_t)K * n * 8, s));
     std::vector<int64_t> ent(K);
     for (int k = 0; k < K; ++k) ent[k] = peak_j[k];
     const int64_t offh[2] = {0, n};

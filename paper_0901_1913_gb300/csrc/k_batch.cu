@@ -465,7 +465,7 @@ cudaError_t need(P** ptr, size_t* cap, size_t n, cudaStream_t s) {
     *ptr = nullptr;
     *cap = 0;
     n = std::max<size_t>(n, 64);
-    cudaError_t e = cudaMallocAsync((void**)ptr, n * sizeof(P), s);
+    cudaError_t e = pool_alloc((void**)ptr, n * sizeof(P), s);
     if (e == cudaSuccess) *cap = n;
     return e;
 }
@@ -760,10 +760,10 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             p.use_r64 = true;
             release(p.d_twlo, s); release(p.d_twhi, s); release(p.d_twst, s); release(p.d_dec, s);
             const int sh = (p.logM + 1) / 2;
-            cudaError_t e = cudaMallocAsync(&p.d_twlo, (size_t)(1ll << sh) * csz, s);
-            if (e == cudaSuccess) e = cudaMallocAsync(&p.d_twhi, (size_t)(M >> sh) * csz, s);
-            if (e == cudaSuccess) e = cudaMallocAsync(&p.d_twst, (size_t)(8 * 4096 + 256) * csz, s);
-            if (e == cudaSuccess) e = cudaMallocAsync(&p.d_dec, (size_t)N * tsz, s);
+            cudaError_t e = pool_alloc((void**)&p.d_twlo, (size_t)(1ll << sh) * csz, s);
+            if (e == cudaSuccess) e = pool_alloc((void**)&p.d_twhi, (size_t)(M >> sh) * csz, s);
+            if (e == cudaSuccess) e = pool_alloc((void**)&p.d_twst, (size_t)(8 * 4096 + 256) * csz, s);
+            if (e == cudaSuccess) e = pool_alloc((void**)&p.d_dec, (size_t)N * tsz, s);
             if (e == cudaSuccess) e = need(&b.red, &b.cred, 8192, s);
             p.d_red = b.red;
             if (e == cudaSuccess) e = init_twiddles(&p, s);
@@ -1009,7 +1009,7 @@ fc2_status batched_backward(int64_t C, const int64_t* offsets, const double* t, 
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** p, size_t bytes) {
         if (e != cudaSuccess) return;
-        e = cudaMallocAsync(p, std::max<size_t>(bytes, 64), s);
+        e = pool_alloc((void**)p, std::max<size_t>(bytes, 64), s);
         if (e == cudaSuccess) owned.push_back(*p);
     };
     double *dt = nullptr, *dx = nullptr, *ds = nullptr;

@@ -96,7 +96,7 @@ __global__ void k_init_dec_shift(float* dec, int64_t N, int64_t sh, int64_t M,
     dec[j] = (float)(1.0 / cheb_clenshaw(c, nc, 2.0 * xi * xi / ymax - 1.0));
 }
 
-int cheb_fit_kernel_ft(int w, double beta, double xi_max, double* coef) {
+int cheb_fit_kernel_ft(int w, double beta, double xi_max, double* coef, double trim) {
     int nq = 2 * w + 16;
     std::vector<double> gx(nq), gw(nq);
     gauss_legendre(nq, gx.data(), gw.data());
@@ -117,7 +117,7 @@ int cheb_fit_kernel_ft(int w, double beta, double xi_max, double* coef) {
     double mx = 0.0;
     for (int k = 0; k < CHEB_N; ++k) mx = std::max(mx, fabs(coef[k]));
     int nc = CHEB_N;
-    while (nc > 2 && fabs(coef[nc - 1]) < 1e-18 * mx) --nc;
+    while (nc > 2 && fabs(coef[nc - 1]) < trim * mx) --nc;
     return nc;
 }
 
@@ -128,11 +128,15 @@ double cheb_eval_host(const double* coef, double xi, double xi_max) {
 
 cudaError_t init_deconv(fc2_plan_s* p, cudaStream_t s) {
     double coef[CHEB_N];
+    double* d_coef = (double*)p->d_red;  // scratch, consumed before any other use
+    cudaError_t e;
+    if (p->packed) goto packed;  // every grid is packed: only the shifted table is used
+    {
     const int64_t hN = p->N / 2;
     const double xi_max = (double)std::max(hN, p->N - hN) / (double)p->M;
-    const int nc = cheb_fit_kernel_ft(p->w, p->beta, xi_max, coef);
-    double* d_coef = (double*)p->d_red;  // scratch, consumed before any other use
-    cudaError_t e = cudaMemcpyAsync(d_coef, coef, sizeof(coef), cudaMemcpyHostToDevice, s);
+    // drop the expansion's tail below the table's precision
+    const int nc = cheb_fit_kernel_ft(p->w, p->beta, xi_max, coef, p->fp64 ? 1e-18 : 1e-11);
+    e = cudaMemcpyAsync(d_coef, coef, sizeof(coef), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     const int64_t mmax = std::max(hN, p->N - hN);
     unsigned blocks = (unsigned)((mmax + 256) / 256);
@@ -144,13 +148,15 @@ cudaError_t init_deconv(fc2_plan_s* p, cudaStream_t s) {
                                                  xi_max * xi_max);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    }
+packed:
     if (p->npk > 0) {
         // packed grids: dec_p[j] = 1 / phihat_p((sh + j) / M) (the modes -(sh + j)
         // share it: phihat is even)
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
         const double xi_p = (double)(p->sh + p->N) / (double)p->M;
-        const int ncp = cheb_fit_kernel_ft(p->w_p, p->beta_p, xi_p, coef);
+        const int ncp = cheb_fit_kernel_ft(p->w_p, p->beta_p, xi_p, coef, 1e-11);
         e = cudaMemcpyAsync(d_coef, coef, sizeof(coef), cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return e;
         k_init_dec_shift<<<(unsigned)((p->N + 255) / 256), 256, 0, s>>>(

@@ -86,8 +86,6 @@ template <typename TS, int H>
 FC2_D void load_gridded(const cpx<TS>* __restrict__ spec, const TS* __restrict__ dec,
                         const TS* __restrict__ dec_p, int npk, int64_t N, int64_t j, TS sq,
                         TS sp, TS s1n, Sys<TS, H>& S) {
-    const TS d = dec[j];
-    const TS dq = d * sq, dp = d * sp;
     S.qr[0] = (TS)1;
     S.qi[0] = (TS)0;
     S.pr[0] = s1n;
@@ -119,6 +117,8 @@ FC2_D void load_gridded(const cpx<TS>* __restrict__ spec, const TS* __restrict__
         }
         return;
     }
+    const TS d = dec[j];
+    const TS dq = d * sq, dp = d * sp;
 #pragma unroll
     for (int k = 1; k <= 2 * H; ++k) {
         cpx<TS> v = spec[(int64_t)(k - 1) * N + j];
@@ -191,21 +191,21 @@ __global__ void __launch_bounds__(128) k_resolve(const cpx<float>* __restrict__ 
 #pragma unroll
         for (int k = 0; k <= H; ++k) { S.pr[k] = Sf.pr[k]; S.pi[k] = Sf.pi[k]; }
         double out[H], an2 = 0.0;
-        warp_chol_solve<H, true>(S, sp.tau, out, &an2);
+        const double dmin = warp_chol_solve<H, true>(S, sp.tau, out, &an2);
         if ((threadIdx.x & 31) == 0) {
             if (!(est_err<double>(an2, 2 * H + 1, sp.eps_spec) <= sp.err_fix)) {
-                // exact fix-up: start at the cheapest tier whose precision the
-                // coefficient norm of these (gridded) equations says is enough;
-                // each tier still checks its own result and passes bins on
+                // exact fix-up: bins that these (gridded) equations already show
+                // to be beyond float sums -- by the coefficient norm, or by a
+                // small relative pivot (columns this solve drops come back with
+                // large coefficients in the exact solve) -- start at the
+                // double-float tier.  The double tier is only reached by
+                // escalation: the gridded equations are too coarse to tell which
+                // bins need it.  Each tier checks its own result and passes bins on.
                 const int m = 2 * H + 1;
                 int32_t *lst = flist, *cnt = fcount;
-                if (!(est_err<double>(an2, m, sp.eps_t1) <= sp.err_fix)) {
+                if (!(est_err<double>(an2, m, sp.eps_t1) <= sp.err_fix) || dmin < 3e-3) {
                     lst = flist2;
                     cnt = fcount2;
-                    if (!(est_err<double>(an2, m, sp.eps_t2) <= sp.err_fix)) {
-                        lst = flist3;
-                        cnt = fcount3;
-                    }
                 }
                 int32_t pos = atomicAdd(cnt, 1);
                 if (pos < fcap) lst[pos] = (int32_t)j;

@@ -177,3 +177,16 @@ def test_autotuned_plan_matches_fixed_plan(fc2):
         assert np.max(np.abs(d - out[0][0])) <= 2e-5 * chi0
         assert best[-1]["j"] == out[0][1][-1]["j"]
     assert np.array_equal(out[1][0], out[2][0])
+
+
+def test_pool_reuse_and_trim(fc2):
+    """Plans created one after another reuse the library's device pool and give
+    identical results; trimming the pool between plans changes nothing."""
+    c = synth.config1(n=500, N=4096)
+    outs = []
+    for it in range(3):
+        with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, 2, "mixed") as p:
+            outs.append(p.execute()[0])
+        if it == 1:
+            fc2.trim_device_memory(0)
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[1], outs[2])
