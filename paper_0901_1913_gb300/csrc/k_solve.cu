@@ -496,9 +496,14 @@ __global__ void __launch_bounds__(128) k_exact_dchi2(const double* __restrict__ 
     Sys<double, H> S;
     exact_sys_from_sums<H>(sh[w], H, scal, S);
     double out[H], an2 = 0.0;
-    warp_chol_solve<H, true>(S, tau_drop, out, &an2);
+    const double dmin = warp_chol_solve<H, true>(S, tau_drop, out, &an2);
     if ((threadIdx.x & 31) != 0) return;
-    if (next && !(est_err<double>(an2, 2 * H + 1, eps_sums) <= err_fix)) {
+    // The coefficient norm only measures the error if these sums resolve the
+    // system's smallest pivot: a relative pivot within 1e3 of the sums'
+    // precision may be an artefact of their errors (which can also make the
+    // coefficients look small), so such bins go on to the next tier too.
+    if (next && (!(est_err<double>(an2, 2 * H + 1, eps_sums) <= err_fix) ||
+                 dmin < 1e3 * eps_sums)) {
         int32_t pos = atomicAdd(next_count, 1);
         if (pos < next_cap) next[pos] = (int32_t)j;
     }

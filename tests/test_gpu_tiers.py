@@ -55,3 +55,22 @@ def test_double_float_tracks_double(fc2, case):
     err = np.abs(d2 - d3)[ok].max() / chi0
     print("tier2 vs tier3", err)
     assert err <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_pipeline_on_degenerate_bins(fc2, oracle_mod, prec):
+    """The whole pipeline (gridded solve, routing, every fix-up tier) on the
+    bins that need the most precision: periods longer than the span (f near 0)
+    and the daily aliases, against the oracle."""
+    c = synth.config2(n=20000, N=1 << 18)
+    one = int(round((1.0 - c.f_min) / c.df))
+    bins = np.unique(np.concatenate([np.arange(0, 96), np.arange(one - 40, one + 41),
+                                     np.arange(2 * one - 20, 2 * one + 21)]))
+    with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, prec) as p:
+        d, _, _, chi0 = p.execute()
+        counts = p.counts
+    ref, piv = oracle_mod.dchi2_bins(c.t, c.x, c.sigma, c.H, c.f_min, c.df, bins,
+                                     with_pivots=True)
+    r = compare(d[:, bins].T, ref, piv, chi0)
+    print(prec, counts, r)
+    assert r["ok"], r
