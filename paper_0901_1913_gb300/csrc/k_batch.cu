@@ -316,9 +316,14 @@ __global__ void __launch_bounds__(BX_NT) k_bexact(
             const double chi0 = sc[SC_CHI0];
             if constexpr (MODE == 0) {
                 double o[HM], an2 = 0.0;
-                chol_solve<double, HM, true>(S, tau_drop, o, &an2, nullptr, nullptr, H);
+                const double dmin = chol_solve<double, HM, true>(S, tau_drop, o, &an2, nullptr,
+                                                                 nullptr, H);
                 const double eps_t1 = 2e-7 * sc[SC_RW];
-                if (next && !(est_err<double>(an2, 2 * H + 1, eps_t1) <= err_fix)) {
+                // float sums cannot vouch for a pivot near their precision (their
+                // errors can also make the coefficients look small): such bins
+                // go on to the double tier as well
+                if (next && (!(est_err<double>(an2, 2 * H + 1, eps_t1) <= err_fix) ||
+                             dmin < 1e3 * eps_t1)) {
                     const int32_t pos = atomicAdd(next_count, 1);
                     if (pos < next_cap) next[pos] = ent;
                 }
