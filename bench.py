@@ -335,6 +335,15 @@ def run_profile(args):
     that is not a benchmark result."""
     import torch
     from paper_0901_1913_gb300 import _fc2, synth
+    if args.workload in ("survey", "adjoint"):
+        b = synth.config3(C=args.curves) if args.workload == "survey" else synth.config4(C=args.curves)
+        for _ in range(args.warmup + args.steps):
+            _, _, stats = _fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df,
+                                               b.N, b.oversample, "mixed", top_k=8)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": True, "workload": args.workload, "curves": b.C,
+                          "stats": stats}), flush=True)
+        return
     c = synth.config2(seed=2, H=args.H or 6)
     dev = torch.device("cuda", 0)
     out = torch.empty((c.H, c.N), dtype=torch.float64, device=dev)
@@ -498,6 +507,8 @@ def main():
     ap.add_argument("--H", type=int, default=0, help="harmonics of the --profile run (default 6)")
     ap.add_argument("--workload", default="long", choices=["long"] + sorted(WORKLOADS),
                     help="long (default, the headline) or another synthetic workload")
+    ap.add_argument("--curves", type=int, default=512,
+                    help="curves of a --profile run of the survey or adjoint workload")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

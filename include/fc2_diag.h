@@ -1,0 +1,91 @@
+/*
+ * fc2_diag.h -- diagnostic and measurement entry points of libfc2.
+ *
+ * These calls expose the internal state of the last execute of a plan (or of
+ * the last batched execute of the process) for tests and benchmarks: how many
+ * bins each precision tier of the exact fix-up handled, the intermediate
+ * trigonometric sums, per-stage timings.  They are not needed to compute a
+ * periodogram and their layout may change with the implementation.
+ *
+ * The exact fix-up (Sec. 3e: bins whose gridded normal equations are too
+ * ill-conditioned for the interpolated sums are recomputed from sums over the
+ * samples, Eq. "eqPQ" evaluated directly) runs in three precision tiers:
+ *   tier 1  float sine / cosine of the exact integer phases, compensated
+ *           float sums;
+ *   tier 2  double-float phasors and sums (about 48 significant bits);
+ *   tier 3  double phasors and sums.
+ * Each tier checks its own result (error estimate from the coefficient norm
+ * and the smallest relative pivot of the bordered Cholesky factorisation) and
+ * passes the bins it cannot vouch for to the next.
+ *
+ * Conventions are those of fc2.h: plain C arrays, host pointers unless
+ * stated, fc2_status returns, nothing throws across the ABI.  Calls that read
+ * device state synchronise the plan's stream.
+ */
+#ifndef FC2_DIAG_H
+#define FC2_DIAG_H
+
+#include <stdint.h>
+
+#include "fc2.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Bins the last fc2_execute of p sent to the exact fix-up; -1 if p is NULL. */
+int64_t fc2_debug_flag_count(fc2_plan p);
+
+/* Counts of the last fc2_execute of p into out7[0..6]: [0] bins re-solved in
+ * double from the float spectra (mixed precision), [1] bins recomputed from
+ * exact sums, [2] of those, bins that went through tier 2, [3] bins that went
+ * through tier 3, [4..6] bins first routed to tiers 1, 2, 3.  No-op on NULL. */
+void fc2_debug_counts(fc2_plan p, int64_t* out7);
+
+/* The deconvolved trigonometric sums of the last execute (Eq. "eqPQ"):
+ * re/im [3H][N] each, rows Q(f_j), Q(2 f_j) .. Q(2H f_j), then P(f_j) ..
+ * P(H f_j), as double (float spectra are widened).  Caller-owned buffers of
+ * 3 H N doubles.  Returns FC2_ERR_INVALID_ARG on NULL, FC2_ERR_CUDA if a copy
+ * fails. */
+fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im);
+
+/* The time origin T0 the plan measures phases from (Sec. 3b); 0 on NULL. */
+double fc2_debug_t0(fc2_plan p);
+
+/* Bins of the last execute that tier `tier` (2 or 3) handled, into out[0..cap).
+ * Returns how many were copied, or -1 on a bad argument or a failed copy. */
+int64_t fc2_debug_tier_bins(fc2_plan p, int tier, int64_t* out, int64_t cap);
+
+/* Delta chi^2 [H][nb] at bins[0..nb) from the exact sums of one tier
+ * (1, 2 or 3), written to out (H * nb doubles).  Overwrites those bins of the
+ * plan's device output.  FC2_ERR_INVALID_ARG for a bin outside [0, N), a bad
+ * tier, or nb above N or above the plan's exact-round size. */
+fc2_status fc2_debug_exact_bins(fc2_plan p, const int64_t* bins, int64_t nb, int tier,
+                                double* out);
+
+/* Kernels launched by the last fc2_execute_batched call of this process. */
+int64_t fc2_debug_batch_launches(void);
+
+/* Counts of the last fc2_execute_batched call into out5[0..4]: entries
+ * re-solved in double, entries recomputed by tier 1, tier 2 and tier 3, and
+ * the number of chunk graphs launched.  No-op on NULL. */
+void fc2_debug_batch_counts(int64_t* out5);
+
+/* Stage timing of p on (enable != 0) or off; resets the accumulated times.
+ * While on, each execute records CUDA events on the plan's stream around
+ * (0) phase reduction and spreading, (1) FFT passes, (2) assembly and solve,
+ * (3) exact fix-up, (4) peaks and coefficients.  FC2_ERR_CUDA if an event
+ * cannot be created. */
+fc2_status fc2_stage_timing(fc2_plan p, int enable);
+
+/* Mean milliseconds per execute of each of the five stages since timing was
+ * enabled (ms5[0..4], may be NULL), the kernels launched by the last execute
+ * (may be NULL), and the algorithmic bytes of one execute's FFT passes (may
+ * be NULL). */
+fc2_status fc2_stage_times(fc2_plan p, double* ms5, int64_t* launches, double* fft_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FC2_DIAG_H */

@@ -306,12 +306,13 @@ def execute_batched(offsets, t, x, sigma, H, f_min, df, N, oversample=2, prec="m
                                  int(oversample), ctypes.byref(opt), _ptr(dchi2),
                                  ctypes.cast(peaks, _P))
     _check(rc, "fc2_execute_batched")
-    st = np.zeros(4, dtype=np.int64)
+    st = np.zeros(5, dtype=np.int64)
     lib.fc2_debug_batch_counts(st.ctypes.data)
     recs = [[peaks[c * K + r].as_dict() for r in range(K)] for c in range(C)]
     return dchi2, recs, dict(launches=int(lib.fc2_debug_batch_launches()),
-                             resolved=int(st[0]), exact=int(st[1]), exact_double=int(st[2]),
-                             graphs=int(st[3]))
+                             resolved=int(st[0]), exact=int(st[1]),
+                             exact_double_float=int(st[2]), exact_double=int(st[3]),
+                             graphs=int(st[4]))
 
 
 def _backward_argtypes(lib):

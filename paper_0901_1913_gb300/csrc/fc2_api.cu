@@ -12,12 +12,13 @@
 #include <vector>
 
 #include "fc2_common.cuh"
+#include "../../include/fc2_diag.h"
 #include "fc2_internal.h"
 
 using namespace fc2;
 
 static int64_t g_last_batch_launches = 0;
-static int64_t g_last_batch_stats[4] = {0, 0, 0, 0};  // re-solved, exact, exact double, graphs
+static int64_t g_last_batch_stats[5] = {0, 0, 0, 0, 0};  // re-solved, exact float / double-float / double, graphs
 
 // Device memory comes from one stream-ordered pool per device owned by the
 // library.  Memory that a destroyed plan returns stays mapped in the pool
@@ -496,7 +497,7 @@ fc2_status fc2_backward(fc2_plan p, int K, const int64_t* peak_j, const double* 
     return plan_backward(p, K, peak_j, grad_out, f_refined, dchi2_refined, d_df, d_dx, d_dsigma);
 }
 
-/* Diagnostics (not in the public header): number of bins the last execute
+/* Diagnostics (declared in fc2_diag.h): number of bins the last execute
  * sent to the exact fix-up, and the spectra of the last execute. */
 int64_t fc2_debug_flag_count(fc2_plan p) { return p ? p->last_flag_count : -1; }
 
@@ -610,11 +611,11 @@ fc2_status fc2_debug_exact_bins(fc2_plan p, const int64_t* bins, int64_t nb, int
 int64_t fc2_debug_batch_launches(void) { return g_last_batch_launches; }
 
 /* Bins of the last fc2_execute_batched call that were re-solved in double,
- * recomputed from exact sums, of those recomputed all in double, and the
- * number of chunk graphs launched. */
-void fc2_debug_batch_counts(int64_t* out4) {
-    if (out4)
-        for (int i = 0; i < 4; ++i) out4[i] = g_last_batch_stats[i];
+ * recomputed from float, double-float and double exact sums, and the number
+ * of chunk graphs launched (out5[0..4]). */
+void fc2_debug_batch_counts(int64_t* out5) {
+    if (out5)
+        for (int i = 0; i < 5; ++i) out5[i] = g_last_batch_stats[i];
 }
 
 /* Stage timing: while enabled, each execute records CUDA events on the plan's

@@ -107,4 +107,32 @@ FC2_D dfc df_phasor(uint64_t u, const dfc* t1, const dfc* t2) {
     return dfc_mul(dfc_mul(t1[a], t2[b]), e);
 }
 
+// e^{2 pi i u 2^-64} in double from the same split as df_phasor: two table
+// factors times 1 - theta^2/2 + i (theta - theta^3/6), theta < 1e-4 (the
+// dropped terms are below 4e-18).
+FC2_D double2 d_phasor(uint64_t u, const double2* t1, const double2* t2) {
+    const double2 A = t1[(int)(u >> 56)], B = t2[(int)((u >> 48) & 255u)];
+    const double th = (double)(int64_t)(u & ((1ull << 48) - 1)) * 3.4061215800865545e-19;  // 2 pi 2^-64
+    const double th2 = th * th;
+    const double c = fma(-0.5, th2, 1.0);
+    const double s = fma(th * th2, -1.0 / 6.0, th);
+    const double pr = fma(A.x, B.x, -A.y * B.y), pi = fma(A.x, B.y, A.y * B.x);
+    return make_double2(fma(pr, c, -pi * s), fma(pr, s, pi * c));
+}
+
+// Every lane receives the warp's sum of (hi, lo) float pairs (butterfly of
+// error-free two-sums; two-sum is symmetric in its operands, so all lanes end
+// with the same bits).
+FC2_D float2 warp_allsum_pair(float hi, float lo) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        const dfl t = df_two_sum(hi, h2);
+        hi = t.h;
+        lo = (lo + l2) + t.l;
+    }
+    return make_float2(hi, lo);
+}
+
 }  // namespace fc2

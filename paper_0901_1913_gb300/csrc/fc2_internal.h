@@ -178,6 +178,9 @@ cudaError_t launch_peaks(fc2_plan_s* p, cudaStream_t s);
 size_t peaks_scratch_bytes(int64_t N, int H, int K);
 size_t exact_scratch_bytes(int64_t n, int H, int64_t cap);
 cudaError_t launch_phase_fx(fc2_plan_s* p, cudaStream_t s);
+// Phasor tables of the exact sums (512 double-float pairs, then 512 double2)
+// into tab (2 * 512 * 16 bytes).
+cudaError_t launch_init_dftab(void* tab, cudaStream_t s);
 
 // k_adjoint.cu: one entry = (curve << 32 | bin) of a curve table
 struct AdjTab {
@@ -216,7 +219,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
                            const double* sigma, const int* H, const double* fmin,
                            const double* df, const int64_t* N, int oversample,
                            const fc2_options& opt, float* dchi2, fc2_best* peaks,
-                           int64_t* launches_out, int64_t* stats_out);
+                           int64_t* launches_out, int64_t* stats_out);  // stats_out[5]
 
 fc2_status batched_backward(int64_t C, const int64_t* offsets, const double* t, const double* x,
                             const double* sigma, const int* H, const double* fmin,

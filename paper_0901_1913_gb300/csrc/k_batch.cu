@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "fc2_common.cuh"
+#include "fc2_df.cuh"
 #include "fc2_internal.h"
 #include "fc2_solve.cuh"
 
@@ -66,8 +67,11 @@ __global__ void k_bgather(const double* __restrict__ t, const double* __restrict
     wp[i] = v;
     A[i] = frac_fx(fmin[c], ta);
     B[i] = frac_fx(df[c], ta);
-    wq32[i] = (float)w;
-    wp32[i] = (float)v;
+    const float qh = (float)w, ph = (float)v;
+    wq32[i] = qh;
+    wp32[i] = ph;
+    wq32[ntot + i] = (float)(w - (double)qh);  // low parts for double-float sums
+    wp32[ntot + i] = (float)(v - (double)ph);
 }
 
 // ----------------------------------------------------------- phase reduction
@@ -155,8 +159,11 @@ __global__ void __launch_bounds__(128) k_bassemble(const cpx<TS>* __restrict__ s
     for (int h = 0; h < H; ++h) oc[(int64_t)h * N + j] = (float)o[h] * c0;
 }
 
-// Double re-solve of listed (curve, bin) entries of the float path; entries
-// still too sensitive go on to the exact list.
+// Double re-solve of listed (curve, bin) entries of the float path.  Entries
+// still too sensitive go on to the exact sums: to the float tier, or straight
+// to the double-float tier when the float sums could not settle them either
+// (error estimate at the float sums' precision above the bar, or a small
+// relative pivot).
 template <int HM>
 __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__ spec,
                                                   const float* __restrict__ dec, int64_t N,
@@ -165,19 +172,23 @@ __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__
                                                   const int64_t* __restrict__ rlist,
                                                   const int32_t* __restrict__ rcount,
                                                   int64_t rcap, int64_t* __restrict__ flist,
-                                                  int32_t* __restrict__ fcount, int64_t fcap) {
+                                                  int32_t* __restrict__ fcount, int64_t fcap,
+                                                  int64_t* __restrict__ flist2,
+                                                  int32_t* __restrict__ fcount2, int64_t fcap2) {
     int64_t cnt = *rcount;
     if (cnt > rcap) cnt = rcap;
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < cnt;
-         b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t wpb = blockDim.x >> 5;  // one entry per warp (warp-cooperative solve)
+    for (int64_t b = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); b < cnt;
+         b += (int64_t)gridDim.x * wpb) {
         const int c = (int)(rlist[b] >> 32);
         const int64_t j = rlist[b] & 0xffffffffll;
         const int H = ct.H[c];
         const int g0 = ct.slot0[c];
         const double* sc = ct.scal + (int64_t)c * SC_COUNT;
         const double W = sc[SC_W], chi0 = sc[SC_CHI0];
-        const double sp = (chi0 > 0.0) ? 1.0 / sqrt(W * chi0) : 0.0;
+        const double sp = (chi0 > 0.0) ? rsqrt(W * chi0) : 0.0;
         const double d = (double)dec[j];
+        const double dw = d / W;
         Sys<double, HM> S;
 #pragma unroll
         for (int k = 0; k <= 2 * HM; ++k) { S.qr[k] = 0.0; S.qi[k] = 0.0; }
@@ -187,8 +198,8 @@ __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__
         S.pr[0] = sc[SC_S1] * sp;
         for (int k = 1; k <= 2 * H; ++k) {
             const cpx<float> v = spec[(int64_t)(g0 + k - 1) * N + j];
-            S.qr[k] = (double)v.x * d / W;
-            S.qi[k] = (double)v.y * d / W;
+            S.qr[k] = (double)v.x * dw;
+            S.qi[k] = (double)v.y * dw;
         }
         for (int k = 1; k <= H; ++k) {
             const cpx<float> v = spec[(int64_t)(g0 + 2 * H + k - 1) * N + j];
@@ -196,45 +207,73 @@ __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__
             S.pi[k] = (double)v.y * d * sp;
         }
         double o[HM], an2 = 0.0;
-        chol_solve<double, HM, true>(S, tau, o, &an2, nullptr, nullptr, H);
-        if (!(est_err<double>(an2, 2 * H + 1, eps) <= err_fix)) {
-            const int32_t pos = atomicAdd(fcount, 1);
-            if (pos < fcap) flist[pos] = rlist[b];
+        const double dmin = warp_chol_solve<HM, true>(S, tau, o, &an2, H);
+        if ((threadIdx.x & 31) == 0) {
+            const int m = 2 * H + 1;
+            if (!(est_err<double>(an2, m, eps) <= err_fix)) {
+                if (!(est_err<double>(an2, m, 2e-7 * sc[SC_RW]) <= err_fix) || dmin < 3e-3) {
+                    const int32_t pos = atomicAdd(fcount2, 1);
+                    if (pos < fcap2) flist2[pos] = rlist[b];
+                } else {
+                    const int32_t pos = atomicAdd(fcount, 1);
+                    if (pos < fcap) flist[pos] = rlist[b];
+                }
+            }
+            float* oc = out + ct.out_off[c];
+            for (int h = 0; h < H; ++h) oc[(int64_t)h * N + j] = (float)(o[h] * chi0);
         }
-        float* oc = out + ct.out_off[c];
-        for (int h = 0; h < H; ++h) oc[(int64_t)h * N + j] = (float)(o[h] * chi0);
     }
 }
 
-// ------------------------------------------------------ exact, one CTA per entry
-// Entries (curve << 32 | j); the CTA sums its curve's samples (tier 1: float
-// sine/cosine of exact integer phases with compensated float sums; tier 2: all
-// double), reduces in a fixed order, and warp 0 lane 0 solves.
-// MODE 0: write Delta chi^2 (float) and escalate entries whose tier-1 error
-// estimate is still too large.  MODE 1: coefficient records.
+// ----------------------------------------------------- exact, one warp per entry
+// Entries (curve << 32 | j).  The lanes of a warp sum the entry's curve
+// samples at stride 32, a butterfly gives every lane the totals (the same
+// bits on every lane), and the warp solves cooperatively.  Precision tiers of
+// the sums over the exact integer phases (Sec. 3's moments, Eqs. for Q and P):
+//   1: float sine / cosine, compensated float sums;
+//   2: double-float phasors, products and sums (about 48 bits);
+//   3: double phasors and sums.
+// MODE 0 writes Delta chi^2 (float) and passes on to `next` the entries whose
+// error estimate from the coefficient norm, or whose smallest relative pivot,
+// is beyond what the tier's sums can vouch for.  MODE 1 writes coefficient
+// records.  Weights: wq32 / wp32 hold the float high parts at [i] and the low
+// parts at [ntot + i].
 constexpr int BX_NT = 256;
+constexpr int BX_W = BX_NT / 32;
+constexpr double BX_EPS_DF = 1.5e-12;  // relative precision of the tier-2 sums
 
 template <int HM, int TIER, int MODE>
 __global__ void __launch_bounds__(BX_NT) k_bexact(
     const uint64_t* __restrict__ Aph, const uint64_t* __restrict__ Bph,
     const float* __restrict__ wq32, const float* __restrict__ wp32,
-    const double* __restrict__ wq, const double* __restrict__ wp, CurveTab ct, int64_t N,
-    const int64_t* __restrict__ list, const int32_t* __restrict__ count, int64_t cap,
-    double tau_drop, double err_fix, float* __restrict__ out, int64_t* __restrict__ next,
-    int32_t* __restrict__ next_count, int64_t next_cap, int K, fc2_best* __restrict__ recs) {
+    const double* __restrict__ wq, const double* __restrict__ wp, const dfc* __restrict__ dftab,
+    int64_t ntot, CurveTab ct, int64_t N, const int64_t* __restrict__ list,
+    const int32_t* __restrict__ count, int64_t cap, double tau_drop, double err_fix,
+    float* __restrict__ out, int64_t* __restrict__ next, int32_t* __restrict__ next_count,
+    int64_t next_cap, fc2_best* __restrict__ recs) {
     constexpr int NV = 6 * HM;
-    __shared__ double red[BX_NT / 32][NV];
-    __shared__ double tot[NV];
+    __shared__ dfc stab[TIER == 2 ? 512 : 1];
+    __shared__ double2 stab64[TIER == 3 ? 512 : 1];
+    if constexpr (TIER == 2) {
+        for (int i = threadIdx.x; i < 512; i += BX_NT) stab[i] = dftab[i];
+        __syncthreads();
+    }
+    if constexpr (TIER == 3) {
+        const double2* t64 = reinterpret_cast<const double2*>(dftab + 512);
+        for (int i = threadIdx.x; i < 512; i += BX_NT) stab64[i] = t64[i];
+        __syncthreads();
+    }
     int64_t cnt = *count;
     if (cnt > cap) cnt = cap;
-    const int lane = threadIdx.x & 31, wpi = threadIdx.x >> 5;
-    for (int64_t e = blockIdx.x; e < cnt; e += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t e = (int64_t)blockIdx.x * BX_W + (threadIdx.x >> 5); e < cnt;
+         e += (int64_t)gridDim.x * BX_W) {
         const int64_t ent = list[e];
         const int c = (int)(ent >> 32);
         const int64_t j = ent & 0xffffffffll;
         const int H = ct.H[c];
         if (MODE == 1 && j == 0xffffffffll) {  // empty peak slot
-            if (threadIdx.x == 0) {
+            if (lane == 0) {
                 fc2_best b;
                 b.j = -1; b.f = 0; b.dchi2 = 0; b.H = H; b.flags = 0;
                 for (int l = 0; l < 2 * FC2_MAX_H + 1; ++l) b.A[l] = 0.0;
@@ -244,22 +283,20 @@ __global__ void __launch_bounds__(BX_NT) k_bexact(
         }
         const int64_t a0 = ct.off[c], a1 = ct.off[c + 1];
         const uint64_t ju = (uint64_t)j;
-        double acc[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+        double tot[NV];
         if constexpr (TIER == 1) {
             CompSum<float> fa[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) fa[v].init();
-            for (int64_t i = a0 + threadIdx.x; i < a1; i += BX_NT) {
+            for (int64_t i = a0 + lane; i < a1; i += 32) {
                 const uint32_t u = (uint32_t)((Aph[i] + ju * Bph[i]) >> 32);
                 const float a = wq32[i], bb = wp32[i];
 #pragma unroll
                 for (int k = 1; k <= 2 * HM; ++k) {
                     if (k <= 2 * H) {
-                        const int32_t ph = (int32_t)(u * (uint32_t)k);
+                        const int32_t ph = (int32_t)(u * (uint32_t)k);  // [-1/2, 1/2) cycles
                         float sn, cn;
-                        sincospif((float)ph * 4.656612873077393e-10f, &sn, &cn);
+                        sincospif((float)ph * 4.656612873077393e-10f, &sn, &cn);  // 2^-31
                         fa[2 * (k - 1)].add(a * cn);
                         fa[2 * (k - 1) + 1].add(a * sn);
                         if (k <= H) {
@@ -270,22 +307,53 @@ __global__ void __launch_bounds__(BX_NT) k_bexact(
                 }
             }
 #pragma unroll
-            for (int v = 0; v < NV; ++v) acc[v] = (double)fa[v].s + (double)fa[v].c;
+            for (int v = 0; v < NV; ++v) {
+                const float2 x = warp_allsum_pair(fa[v].s, fa[v].c);
+                tot[v] = (double)x.x + (double)x.y;
+            }
+        } else if constexpr (TIER == 2) {
+            dfl fa[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) fa[v] = dfl{0.f, 0.f};
+            for (int64_t i = a0 + lane; i < a1; i += 32) {
+                const uint64_t u = Aph[i] + ju * Bph[i];
+                const dfl a{wq32[i], wq32[ntot + i]}, bb{wp32[i], wp32[ntot + i]};
+                const dfc z1 = df_phasor(u, stab, stab + 256);
+                dfc z = z1;
+#pragma unroll
+                for (int k = 0; k < 2 * HM; ++k) {
+                    if (k < 2 * H) {
+                        df_acc_mul(fa[2 * k], a, z.re);
+                        df_acc_mul(fa[2 * k + 1], a, z.im);
+                        if (k < H) {
+                            df_acc_mul(fa[4 * HM + 2 * k], bb, z.re);
+                            df_acc_mul(fa[4 * HM + 2 * k + 1], bb, z.im);
+                        }
+                        if (k + 1 < 2 * H) z = dfc_mul(z, z1);
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const float2 x = warp_allsum_pair(fa[v].h, fa[v].l);
+                tot[v] = (double)x.x + (double)x.y;
+            }
         } else {
-            for (int64_t i = a0 + threadIdx.x; i < a1; i += BX_NT) {
-                const int64_t ph = (int64_t)(Aph[i] + ju * Bph[i]);
-                double s1, c1;
-                sincospi(ldexp((double)ph, -63), &s1, &c1);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) tot[v] = 0.0;
+            for (int64_t i = a0 + lane; i < a1; i += 32) {
+                const double2 z1 = d_phasor(Aph[i] + ju * Bph[i], stab64, stab64 + 256);
+                const double c1 = z1.x, s1 = z1.y;
                 double cr = c1, ci = s1;
                 const double a = wq[i], bb = wp[i];
 #pragma unroll
                 for (int k = 0; k < 2 * HM; ++k) {
                     if (k < 2 * H) {
-                        acc[2 * k] = fma(a, cr, acc[2 * k]);
-                        acc[2 * k + 1] = fma(a, ci, acc[2 * k + 1]);
+                        tot[2 * k] = fma(a, cr, tot[2 * k]);
+                        tot[2 * k + 1] = fma(a, ci, tot[2 * k + 1]);
                         if (k < H) {
-                            acc[4 * HM + 2 * k] = fma(bb, cr, acc[4 * HM + 2 * k]);
-                            acc[4 * HM + 2 * k + 1] = fma(bb, ci, acc[4 * HM + 2 * k + 1]);
+                            tot[4 * HM + 2 * k] = fma(bb, cr, tot[4 * HM + 2 * k]);
+                            tot[4 * HM + 2 * k + 1] = fma(bb, ci, tot[4 * HM + 2 * k + 1]);
                         }
                         const double nr = cr * c1 - ci * s1, ni = cr * s1 + ci * c1;
                         cr = nr;
@@ -293,54 +361,36 @@ __global__ void __launch_bounds__(BX_NT) k_bexact(
                     }
                 }
             }
-        }
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            double y = acc[v];
+            for (int v = 0; v < NV; ++v) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
-            if (lane == 0) red[wpi][v] = y;
+                for (int o = 16; o > 0; o >>= 1) tot[v] += __shfl_xor_sync(0xffffffffu, tot[v], o);
+            }
         }
-        __syncthreads();
-        if (threadIdx.x < NV) {
-            double y = 0.0;
-#pragma unroll
-            for (int q = 0; q < BX_NT / 32; ++q) y += red[q][threadIdx.x];
-            tot[threadIdx.x] = y;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double* sc = ct.scal + (int64_t)c * SC_COUNT;
-            Sys<double, HM> S;
-            exact_sys_from_sums<HM>(tot, H, sc, S);
-            const double chi0 = sc[SC_CHI0];
-            if constexpr (MODE == 0) {
-                double o[HM], an2 = 0.0;
-                const double dmin = chol_solve<double, HM, true>(S, tau_drop, o, &an2, nullptr,
-                                                                 nullptr, H);
-                const double eps_t1 = 2e-7 * sc[SC_RW];
-                // float sums cannot vouch for a pivot near their precision (their
-                // errors can also make the coefficients look small): such bins
-                // go on to the double tier as well
-                if (next && (!(est_err<double>(an2, 2 * H + 1, eps_t1) <= err_fix) ||
-                             dmin < 1e3 * eps_t1)) {
+        const double* sc = ct.scal + (int64_t)c * SC_COUNT;
+        Sys<double, HM> S;
+        exact_sys_from_sums<HM>(tot, H, sc, S);
+        const double chi0 = sc[SC_CHI0];
+        if constexpr (MODE == 0) {
+            double o[HM], an2 = 0.0;
+            const double dmin = warp_chol_solve<HM, true>(S, tau_drop, o, &an2, H);
+            const double eps = TIER == 1 ? 2e-7 * sc[SC_RW] : BX_EPS_DF;
+            // sums cannot vouch for a pivot near their precision (their errors
+            // can also make the coefficients look small): such entries go on
+            if (lane == 0) {
+                if (next && (!(est_err<double>(an2, 2 * H + 1, eps) <= err_fix) ||
+                             dmin < 1e3 * eps)) {
                     const int32_t pos = atomicAdd(next_count, 1);
                     if (pos < next_cap) next[pos] = ent;
                 }
                 float* oc = out + ct.out_off[c];
                 for (int h = 0; h < H; ++h) oc[(int64_t)h * N + j] = (float)(o[h] * chi0);
-            } else {
-                double o[HM], an2;
-                double Lk[2 * HM + 1][2 * HM + 1];
-                double zk[2 * HM + 1];
-                chol_solve<double, HM, false>(S, tau_drop, o, &an2, Lk, zk);
-                const int m = 2 * H + 1;
-                double A[2 * HM + 1];
-                for (int l = m - 1; l >= 0; --l) {
-                    double s = zk[l];
-                    for (int k = l + 1; k < m; ++k) s -= Lk[k][l] * A[k];
-                    A[l] = (Lk[l][l] > 0.0) ? s / Lk[l][l] : 0.0;
-                }
+            }
+        } else {
+            double o[HM], an2;
+            double A[2 * HM + 1];
+            warp_chol_solve<HM, false>(S, tau_drop, o, &an2, H, A, H);
+            if (lane == 0) {
                 const double W = sc[SC_W];
                 const double unit = (W > 0.0) ? sqrt(chi0 / W) : 0.0;
                 const double f = ct.fmin[c] + (double)j * ct.df[c];
@@ -360,7 +410,6 @@ __global__ void __launch_bounds__(BX_NT) k_bexact(
                 recs[e] = b;
             }
         }
-        __syncthreads();
     }
 }
 
@@ -527,7 +576,9 @@ struct Batch {
     char *dlt = nullptr, *cs = nullptr; size_t cdlt = 0, ccs = 0;
     char *grid0 = nullptr, *grid1 = nullptr, *spec = nullptr; size_t cg0 = 0, cg1 = 0, cspec = 0;
     float* out = nullptr; size_t cout = 0;
-    int64_t *list = nullptr, *list2 = nullptr, *list3 = nullptr; size_t cl1 = 0, cl2 = 0, cl3 = 0;
+    int64_t *list = nullptr, *list2 = nullptr, *list3 = nullptr, *list4 = nullptr;
+    size_t cl1 = 0, cl2 = 0, cl3 = 0, cl4 = 0;
+    char* dftab = nullptr; size_t cdftab = 0;  // phasor tables of the exact sums
     int32_t* counts = nullptr; size_t ccnt = 0;
     int* curves = nullptr; size_t ccurves = 0;
     Cand* tops = nullptr; size_t ctops = 0;
@@ -537,7 +588,7 @@ struct Batch {
     cudaGraphExec_t gexec = nullptr;
     int64_t graphs = 0;  // chunk graphs launched
     int64_t launches = 0;
-    int64_t stats[3] = {0, 0, 0};
+    int64_t stats[4] = {0, 0, 0, 0};
 
     void free_all() {
         release(t, s); release(x, s); release(sg, s); release(perm, s); release(tau, s);
@@ -548,6 +599,7 @@ struct Batch {
         release(slot_kind, s); release(slot_soff, s); release(slot_n, s); release(L, s);
         release(key, s); release(dlt, s); release(cs, s); release(grid0, s); release(grid1, s);
         release(spec, s); release(out, s); release(list, s); release(list2, s); release(list3, s);
+        release(list4, s); release(dftab, s);
         release(counts, s); release(curves, s); release(tops, s); release(pent, s);
         release(recs, s); release(red, s);
         release(cp.d_twlo, s); release(cp.d_twhi, s); release(cp.d_twst, s); release(cp.d_dec, s);
@@ -575,12 +627,15 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
         b.t, b.x, b.sg, b.perm, ntot, b.off, nc, b.scal, b.fmin, b.df, b.tau, b.wq, b.wp, b.A, b.B,
         b.wq32, b.wp32);
     ++nl;
+    cudaError_t e = launch_init_dftab(b.dftab, s);
+    if (e != cudaSuccess) return e;
+    ++nl;
     dim3 gph((unsigned)((nmax + 255) / 256), (unsigned)S);
     k_bphase<T><<<gph, 256, 0, s>>>(b.tau, b.wq, b.wp, b.off, b.fmin, b.df, N, p.M, p.w,
                                     b.slot_cur, b.slot_k, b.slot_kind, b.slot_soff, b.key,
                                     (T*)b.dlt, (cpx<T>*)b.cs);
     ++nl;
-    cudaError_t e = sort_wrapping_keys(&p, s);
+    e = sort_wrapping_keys(&p, s);
     if (e != cudaSuccess) return e;
     e = launch_spread(&p, s);
     if (e != cudaSuccess) return e;
@@ -620,25 +675,31 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
         k_bresolve<BHM><<<4 * 152, 128, 0, s>>>((const cpx<float>*)p.d_spec, (const float*)p.d_dec,
                                                 N, ct, tau_drop, eps_spec, err_fix, out, b.list,
                                                 b.counts + 0, (int64_t)b.cl1, b.list2, b.counts + 1,
-                                                (int64_t)b.cl2);
+                                                (int64_t)b.cl2, b.list3, b.counts + 2,
+                                                (int64_t)b.cl3);
         ++nl;
     }
-    // exact fix-up: tier 1 over list2, escalation to list3, tier 2 over list3
-    k_bexact<BHM, 1, 0><<<4 * 152, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, ct, N,
-                                                   b.list2, b.counts + 1, (int64_t)b.cl2, 1e-13,
-                                                   err_fix, out, b.list3, b.counts + 2,
-                                                   (int64_t)b.cl3, 0, nullptr);
-    k_bexact<BHM, 2, 0><<<4 * 152, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, ct, N,
-                                                   b.list3, b.counts + 2, (int64_t)b.cl3, 1e-13,
-                                                   err_fix, out, nullptr, nullptr, 0, 0, nullptr);
-    nl += 2;
+    // exact fix-up: float sums over list2 (escalating to list3), double-float
+    // sums over list3 (escalating to list4), double sums over list4
+    const dfc* tab = (const dfc*)b.dftab;
+    const unsigned gx = 2 * 152;
+    k_bexact<BHM, 1, 0><<<gx, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, tab, ntot, ct, N,
+                                             b.list2, b.counts + 1, (int64_t)b.cl2, 1e-13, err_fix,
+                                             out, b.list3, b.counts + 2, (int64_t)b.cl3, nullptr);
+    k_bexact<BHM, 2, 0><<<gx, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, tab, ntot, ct, N,
+                                             b.list3, b.counts + 2, (int64_t)b.cl3, 1e-13, err_fix,
+                                             out, b.list4, b.counts + 3, (int64_t)b.cl4, nullptr);
+    k_bexact<BHM, 3, 0><<<gx, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, tab, ntot, ct, N,
+                                             b.list4, b.counts + 3, (int64_t)b.cl4, 1e-13, err_fix,
+                                             out, nullptr, nullptr, 0, nullptr);
+    nl += 3;
     if (K > 0) {
         const int nblk = (int)((N + BP_B - 1) / BP_B);
         k_bpeaks1<<<dim3((unsigned)nblk, (unsigned)nc), BP_NT, 0, s>>>(out, N, ct, K, nblk, b.tops);
         k_bpeaks2<<<(unsigned)nc, 256, 0, s>>>(b.tops, nblk, K, b.pent);
-        k_bexact<BHM, 1, 1><<<4 * 152, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, ct, N,
-                                                       b.pent, b.counts + 4, nrec, tau_drop,
-                                                       err_fix, out, nullptr, nullptr, 0, K, b.recs);
+        k_bexact<BHM, 2, 1><<<gx, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, tab, ntot, ct,
+                                                 N, b.pent, b.counts + 4, nrec, tau_drop, err_fix,
+                                                 out, nullptr, nullptr, 0, b.recs);
         nl += 3;
     }
     b.launches += nl;
@@ -797,7 +858,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         ok(need(&b.perm, &b.cperm, ntot, s)) && ok(need(&b.tau, &b.ctau, ntot, s)) &&
             ok(need(&b.wq, &b.cwq, ntot, s)) && ok(need(&b.wp, &b.cwp, ntot, s)) &&
             ok(need(&b.A, &b.cA, ntot, s)) && ok(need(&b.B, &b.cB, ntot, s)) &&
-            ok(need(&b.wq32, &b.cwq32, ntot, s)) && ok(need(&b.wp32, &b.cwp32, ntot, s)) &&
+            ok(need(&b.wq32, &b.cwq32, 2 * ntot, s)) && ok(need(&b.wp32, &b.cwp32, 2 * ntot, s)) &&
             ok(need(&b.off, &b.coff, nc + 1, s)) && ok(need(&b.H, &b.cH, nc, s)) &&
             ok(need(&b.slot0, &b.cslot0, nc, s)) && ok(need(&b.fmin, &b.cfmin, nc, s)) &&
             ok(need(&b.df, &b.cdf, nc, s)) && ok(need(&b.scal, &b.cscal, (size_t)nc * SC_COUNT, s)) &&
@@ -815,6 +876,8 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             ok(need(&b.list, &b.cl1, (size_t)std::min<int64_t>(out_chunk, 1 << 24), s)) &&
             ok(need(&b.list2, &b.cl2, (size_t)std::min<int64_t>(out_chunk, 1 << 22), s)) &&
             ok(need(&b.list3, &b.cl3, (size_t)std::min<int64_t>(out_chunk, 1 << 20), s)) &&
+            ok(need(&b.list4, &b.cl4, (size_t)std::min<int64_t>(out_chunk, 1 << 20), s)) &&
+            ok(need(&b.dftab, &b.cdftab, 2 * 512 * 16, s)) &&
             ok(need(&b.counts, &b.ccnt, 16, s)) && ok(need(&b.curves, &b.ccurves, nc, s)) &&
             ok(need(&b.tops, &b.ctops, (size_t)nc * ((N + BP_B - 1) / BP_B) * std::max(K, 1), s)) &&
             ok(need(&b.pent, &b.cpent, (size_t)std::max<int64_t>(nrec, 1), s)) &&
@@ -938,7 +1001,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         });
         if (e != cudaSuccess) { st = map_cuda(e); break; }
         // ---- results (a list that overflowed its capacity leaves bins unrepaired)
-        int32_t cnts[4] = {0, 0, 0, 0};
+        int32_t cnts[4] = {0, 0, 0, 0};  // re-solve, float, double-float, double lists
         ok(cudaMemcpyAsync(cnts, b.counts, 16, cudaMemcpyDeviceToHost, s));
         if (dchi2 && !out_dev)
             ok(cudaMemcpyAsync(dchi2 + out_global, out, out_chunk * sizeof(float), cudaMemcpyDeviceToHost, s));
@@ -946,21 +1009,23 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             ok(cudaMemcpyAsync(peaks + c0 * K, b.recs, nrec * sizeof(fc2_best), cudaMemcpyDeviceToHost, s));
         ok(cudaStreamSynchronize(s));
         if (e != cudaSuccess) { st = map_cuda(e); break; }
-        if ((size_t)cnts[0] > b.cl1 || (size_t)cnts[1] > b.cl2 || (size_t)cnts[2] > b.cl3) {
+        if ((size_t)cnts[0] > b.cl1 || (size_t)cnts[1] > b.cl2 || (size_t)cnts[2] > b.cl3 ||
+            (size_t)cnts[3] > b.cl4) {
             st = FC2_ERR_NUMERIC;
             break;
         }
         b.stats[0] += cnts[0];
         b.stats[1] += cnts[1];
         b.stats[2] += cnts[2];
+        b.stats[3] += cnts[3];
         out_global += out_chunk;
         c0 = c1;
     }
     cudaStreamSynchronize(s);
     if (launches_out) *launches_out = b.launches;
     if (stats_out) {
-        for (int i = 0; i < 3; ++i) stats_out[i] = b.stats[i];
-        stats_out[3] = b.graphs;
+        for (int i = 0; i < 4; ++i) stats_out[i] = b.stats[i];
+        stats_out[4] = b.graphs;
     }
     b.cp.d_key = nullptr; b.cp.d_dlt = nullptr; b.cp.d_cs = nullptr;
     b.cp.d_grid[0] = b.cp.d_grid[1] = nullptr; b.cp.d_spec = nullptr; b.cp.d_L = nullptr;
@@ -1036,7 +1101,9 @@ fc2_status batched_backward(int64_t C, const int64_t* offsets, const double* t, 
     alloc((void**)&dfd, C * 8); alloc((void**)&scal, C * SC_COUNT * 8); alloc((void**)&status, 16);
     alloc((void**)&perm, ntot * 4); alloc((void**)&tau, ntot * 8); alloc((void**)&wq, ntot * 8);
     alloc((void**)&wp, ntot * 8); alloc((void**)&A, ntot * 8); alloc((void**)&B, ntot * 8);
-    alloc((void**)&w32, ntot * 4); alloc((void**)&p32, ntot * 4); alloc((void**)&ent, E * 8);
+    // float weights: high parts at [i], low parts at [ntot + i]
+    alloc((void**)&w32, 2 * ntot * 4); alloc((void**)&p32, 2 * ntot * 4);
+    alloc((void**)&ent, E * 8);
     alloc((void**)&of, E * 8); alloc((void**)&od, E * 8); alloc((void**)&og, E * 8);
     if (grad_out) alloc((void**)&g, E * 8);
     const bool dx_dev = is_dev(d_dx), ds_dev = is_dev(d_dsig);

@@ -282,19 +282,6 @@ __global__ void k_init_dftab(dfc* __restrict__ tab, double2* __restrict__ tab64)
     tab64[i] = make_double2(cn, sn);
 }
 
-// e^{2 pi i u 2^-64} in double from the same split as df_phasor: two table
-// factors times 1 - theta^2/2 + i (theta - theta^3/6), theta < 1e-4 (the
-// dropped terms are below 4e-18).
-FC2_D double2 d_phasor(uint64_t u, const double2* t1, const double2* t2) {
-    const double2 A = t1[(int)(u >> 56)], B = t2[(int)((u >> 48) & 255u)];
-    const double th = (double)(int64_t)(u & ((1ull << 48) - 1)) * 3.4061215800865545e-19;  // 2 pi 2^-64
-    const double th2 = th * th;
-    const double c = fma(-0.5, th2, 1.0);
-    const double s = fma(th * th2, -1.0 / 6.0, th);
-    const double pr = fma(A.x, B.x, -A.y * B.y), pi = fma(A.x, B.y, A.y * B.x);
-    return make_double2(fma(pr, c, -pi * s), fma(pr, s, pi * c));
-}
-
 // Lane 0 receives the warp's sum of (hi, lo) float pairs, added with
 // error-free two-sums (all on the float pipes).
 FC2_D float2 warp_sum_pair(float hi, float lo) {
@@ -933,6 +920,11 @@ cudaError_t launch_phase_fx(fc2_plan_s* p, cudaStream_t s) {
                                                              p->f_min, p->df, p->d_phA, p->d_phB,
                                                              p->d_wq32, p->d_wp32);
     k_init_dftab<<<2, 256, 0, s>>>((dfc*)p->d_dftab, (double2*)((dfc*)p->d_dftab + 512));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_dftab(void* tab, cudaStream_t s) {
+    k_init_dftab<<<2, 256, 0, s>>>((dfc*)tab, (double2*)((dfc*)tab + 512));
     return cudaGetLastError();
 }
 

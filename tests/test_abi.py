@@ -1,4 +1,4 @@
-"""The C ABI library loads, exports what include/fc2.h declares, and its host
+"""The C ABI library loads, exports what the headers in include/ declare, and its host
 logic (validation, grid sizing, kernel transform) is right -- no GPU needed."""
 import ctypes
 import math
@@ -20,9 +20,13 @@ def lib():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "fc2.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(fc2_[a-z0-9_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(fc2_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_exports_every_declared_symbol(lib):

@@ -81,3 +81,29 @@ def test_batched_device_buffers_and_unsorted(fc2):
     got = out.cpu().numpy()
     scale = max(1.0, float(np.abs(ref).max()))
     assert np.max(np.abs(got - ref)) <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batched_degenerate_bins(fc2, oracle_mod, prec):
+    """Bins that need the exact tiers (periods longer than the span, near the
+    daily aliases) through the batched fix-up, against the oracle."""
+    b = small_survey(C=8, N=1 << 14, seed=5)
+    out, _, stats = fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df, b.N,
+                                        2, prec)
+    pos = 0
+    for c in range(b.C):
+        cur = b.curve(c)
+        block = out[pos:pos + cur.H * cur.N].reshape(cur.H, cur.N)
+        pos += cur.H * cur.N
+        if c % 2:
+            continue
+        one = int(round((1.0 - cur.f_min) / cur.df))
+        bins = np.unique(np.concatenate([np.arange(0, 48), np.arange(one - 24, one + 25),
+                                         np.arange(2 * one - 12, 2 * one + 13)]))
+        bins = bins[(bins >= 0) & (bins < cur.N)]
+        ref, piv = oracle_mod.dchi2_bins(cur.t, cur.x, cur.sigma, cur.H, cur.f_min, cur.df, bins,
+                                         with_pivots=True)
+        _, _, chi0, _ = oracle_mod.moments(cur.x, cur.sigma)
+        r = compare(block[:, bins].T.astype(np.float64), ref, piv, chi0)
+        assert r["ok"], (c, prec, stats, r)
+    print(prec, stats)
