@@ -184,7 +184,7 @@ def run_gpu(args):
 
     def make_plan(prec, t=c.t, x=c.x, s=c.sigma):
         return _fc2.Plan(t, x, s, c.H, c.f_min, c.df, c.N, c.oversample, prec,
-                         stream=stream.cuda_stream, device=local)
+                         stream=stream.cuda_stream, device=local, fft_kernel=args.fft_kernel)
 
     out = torch.empty((c.H, c.N), dtype=torch.float64, device=dev)
 
@@ -245,7 +245,7 @@ def run_gpu(args):
             barrier(ws)
             t_e2e = time.perf_counter()
         p = _fc2.Plan(tp, xp, sp, c.H, c.f_min, c.df, c.N, c.oversample, "mixed",
-                      stream=stream.cuda_stream, device=local)
+                      stream=stream.cuda_stream, device=local, fft_kernel=args.fft_kernel)
         p.execute(hout, want_records=True)
         p.close()
     torch.cuda.synchronize()
@@ -310,7 +310,8 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
         "config": {"workload": WORKLOAD, "precision": "mixed", "n": c.n, "N": c.N, "H": c.H,
                    "oversample": c.oversample, "parallelism": f"{ws} independent curves",
-                   "l2": "inputs larger than L2 (18 grids x 128 MiB)"},
+                   "l2": "inputs larger than L2 (18 grids x 128 MiB)",
+                   "fft_kernel": args.fft_kernel},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -339,7 +340,8 @@ def run_profile(args):
         b = synth.config3(C=args.curves) if args.workload == "survey" else synth.config4(C=args.curves)
         for _ in range(args.warmup + args.steps):
             _, _, stats = _fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df,
-                                               b.N, b.oversample, "mixed", top_k=8)
+                                               b.N, b.oversample, "mixed", top_k=8,
+                                               fft_kernel=args.fft_kernel)
         torch.cuda.synchronize()
         print(json.dumps({"profile_run": True, "workload": args.workload, "curves": b.C,
                           "stats": stats}), flush=True)
@@ -347,7 +349,8 @@ def run_profile(args):
     c = synth.config2(seed=2, H=args.H or 6)
     dev = torch.device("cuda", 0)
     out = torch.empty((c.H, c.N), dtype=torch.float64, device=dev)
-    with _fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed") as p:
+    with _fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed",
+                   fft_kernel=args.fft_kernel) as p:
         for _ in range(args.warmup + args.steps):
             _, best, _, _ = p.execute(out, want_records=True)
         torch.cuda.synchronize()
@@ -400,7 +403,8 @@ def run_workload(args):
         res = {}
         for prec in ("mixed", "fp64"):
             out = torch.empty((c.H, c.N), dtype=torch.float64, device="cuda")
-            with _fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, prec) as p:
+            with _fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, prec,
+                           fft_kernel=args.fft_kernel) as p:
                 steps = args.steps if prec == "mixed" or args.workload == "short" else 2
                 ms = _events_ms(lambda: p.execute(out, want_records=True), steps,
                                 max(1, min(args.warmup, 2)))
@@ -442,7 +446,8 @@ def run_workload(args):
 
         def run(prec="mixed"):
             holder["r"] = _fc2.execute_batched(b.offsets, td, xd, sd, b.H, b.f_min, b.df, b.N,
-                                               b.oversample, prec, top_k=8, dchi2=out)
+                                               b.oversample, prec, top_k=8, dchi2=out,
+                                               fft_kernel=args.fft_kernel)
         ms = _events_ms(run, args.steps, max(1, min(args.warmup, 2)))
         _, peaks, stats = holder["r"]
         got = out.cpu().numpy()
@@ -507,6 +512,8 @@ def main():
     ap.add_argument("--H", type=int, default=0, help="harmonics of the --profile run (default 6)")
     ap.add_argument("--workload", default="long", choices=["long"] + sorted(WORKLOADS),
                     help="long (default, the headline) or another synthetic workload")
+    ap.add_argument("--fft-kernel", default="default", choices=["default", "r64", "r16", "bulk"],
+                    help="kernel family of the float transform passes")
     ap.add_argument("--curves", type=int, default=512,
                     help="curves of a --profile run of the survey or adjoint workload")
     args = ap.parse_args()

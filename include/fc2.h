@@ -78,6 +78,14 @@ typedef struct {
                                   created and keep the fastest; the choice is cached per
                                   device, size and precision for the process. 0 = the
                                   fixed balanced plan */
+    int fft_kernel;            /* kernel family of the float transform passes when autotune
+                                  is 0: 0 = library default (= 1), 1 = two register stages
+                                  of radix R/64 and 64 for radix 2^10..2^12 passes and
+                                  family 3's kernel for 2^8 and 2^9, 2 = radix-16 stages in
+                                  shared memory, 3 = radix-16 stages fed by bulk
+                                  asynchronous copies (radix 2^8..2^12 passes).  Passes a
+                                  family does not cover use family 2.  FP64 ignores it;
+                                  values outside 0..3 are FC2_ERR_INVALID_ARG */
 } fc2_options;
 
 /* One selected frequency: bin index, frequency, Delta chi^2 and the

@@ -26,7 +26,11 @@ class Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("kernel_width", ctypes.c_int), ("top_k", ctypes.c_int),
                 ("alias_tau", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("inputs_on_device", ctypes.c_int),
-                ("outputs_on_device", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("outputs_on_device", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("fft_kernel", ctypes.c_int)]
+
+# fc2_options.fft_kernel values
+FFT_KERNELS = {"default": 0, "r64": 1, "r16": 2, "bulk": 3}
 
 
 class Best(ctypes.Structure):
@@ -135,7 +139,8 @@ def _is_dev(a):
 
 
 def make_options(prec="fp64", kernel_width=0, top_k=0, alias_tau=0.0, stream=None, device=0,
-                 inputs_on_device=False, outputs_on_device=False, autotune=False):
+                 inputs_on_device=False, outputs_on_device=False, autotune=False,
+                 fft_kernel="default"):
     o = Options()
     load().fc2_options_default(ctypes.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -147,6 +152,7 @@ def make_options(prec="fp64", kernel_width=0, top_k=0, alias_tau=0.0, stream=Non
     o.inputs_on_device = int(bool(inputs_on_device))
     o.outputs_on_device = int(bool(outputs_on_device))
     o.autotune = int(bool(autotune))
+    o.fft_kernel = FFT_KERNELS[fft_kernel] if isinstance(fft_kernel, str) else int(fft_kernel)
     return o
 
 
@@ -156,7 +162,7 @@ class Plan:
 
     def __init__(self, t, x, sigma, H, f_min, df, N, oversample=2, prec="fp64",
                  kernel_width=0, top_k=8, alias_tau=0.0, stream=None, device=0,
-                 autotune=False):
+                 autotune=False, fft_kernel="default"):
         lib = load()
         dev = _is_dev(t)
         if not dev:
@@ -168,7 +174,7 @@ class Plan:
         self.H, self.N, self.top_k = int(H), int(N), int(top_k or 8)
         self.f_min, self.df = float(f_min), float(df)
         self.opt = make_options(prec, kernel_width, self.top_k, alias_tau, stream, device,
-                                autotune=autotune,
+                                autotune=autotune, fft_kernel=fft_kernel,
                                 inputs_on_device=dev)
         h = _P()
         rc = lib.fc2_plan_create(_ptr(t), _ptr(x), _ptr(sigma), self.n, self.H, self.f_min,
@@ -276,7 +282,8 @@ def periodogram(t, x, sigma, H, f_min, df, N, oversample=2, prec="fp64", **kw):
 
 
 def execute_batched(offsets, t, x, sigma, H, f_min, df, N, oversample=2, prec="mixed", top_k=8,
-                    kernel_width=0, dchi2=None, stream=None, device=0, autotune=False):
+                    kernel_width=0, dchi2=None, stream=None, device=0, autotune=False,
+                    fft_kernel="default"):
     """Many curves in one call (fc2_execute_batched).  offsets [C+1], t/x/sigma
     concatenated (numpy host arrays, or CUDA tensors -> read in place); H, f_min,
     df, N per curve.  dchi2: optional preallocated float32 output (numpy or
@@ -300,7 +307,7 @@ def execute_batched(offsets, t, x, sigma, H, f_min, df, N, oversample=2, prec="m
     K = int(top_k or 8)
     peaks = (Best * (C * K))()
     opt = make_options(prec, kernel_width, K, 0.0, stream, device, inputs_on_device=dev,
-                       autotune=autotune)
+                       autotune=autotune, fft_kernel=fft_kernel)
     rc = lib.fc2_execute_batched(C, offsets.ctypes.data, _ptr(t), _ptr(x), _ptr(sigma),
                                  H.ctypes.data, f_min.ctypes.data, df.ctypes.data, N.ctypes.data,
                                  int(oversample), ctypes.byref(opt), _ptr(dchi2),

@@ -130,6 +130,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     if (opt.kernel_width != 0 && (opt.kernel_width < 2 || opt.kernel_width > 16))
         return FC2_ERR_INVALID_ARG;
     if (opt.top_k < 0 || opt.top_k > 64 || opt.alias_tau < 0.0) return FC2_ERR_INVALID_ARG;
+    if (opt.fft_kernel < 0 || opt.fft_kernel > 3) return FC2_ERR_INVALID_ARG;
     if (H > 8) return FC2_ERR_UNSUPPORTED;
     const int64_t M = fc2_grid_size(N, oversample);
     if (M == 0) return FC2_ERR_INVALID_ARG;
@@ -187,7 +188,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     p->tau = opt.alias_tau > 0.0 ? opt.alias_tau : (p->fp64 ? 1e-9 : 1e-6);
     p->top_k = opt.top_k ? opt.top_k : 8;
     plan_fft_passes(p);
-    p->use_r64 = true;
+    p->fft_family = fft_family_of(opt.fft_kernel);
 
     const size_t tsz = p->fp64 ? 8 : 4;
     const size_t csz = 2 * tsz;

@@ -24,6 +24,19 @@ enum ScalarSlot {
     SC_COUNT = 8
 };
 
+// Float transform kernel families (double passes always use FFT_R16).
+enum FftFamily {
+    FFT_R16 = 0,   // radix-16 stages in shared memory (k_fft_pass)
+    FFT_R64 = 1,   // two register stages of radix R/64 and 64 (k_fft_pass64) for radix
+                   // 2^10..2^12, FFT_BULK's kernel for 2^8 and 2^9
+    FFT_BULK = 2   // radix-16 stages fed by bulk asynchronous copies (k_fft_pass_tma), 2^8..2^12
+};
+
+// Family for fc2_options.fft_kernel (0 = library default).
+inline int fft_family_of(int fft_kernel) {
+    return fft_kernel == 2 ? FFT_R16 : fft_kernel == 3 ? FFT_BULK : FFT_R64;
+}
+
 struct GridGeom {
     int k;            // harmonic multiple of this transform
     int kind;         // 0 = Q (weights), 1 = P (weighted data)
@@ -105,7 +118,7 @@ struct fc2_plan_s {
     void* d_twst = nullptr;    // cpx<T> in-CTA stage twiddles per radix
     int64_t twst_off[16] = {0};
     int64_t tw64_off[16] = {0};
-    bool use_r64 = true;       // float passes of radix 2^10..2^12 use the two-stage kernel
+    int fft_family = fc2::FFT_R64;  // kernel family of the float passes (fc2::FftFamily)
     double* d_dchi2 = nullptr; // [H][N]
     float* d_minpiv = nullptr; // unused slot kept for diagnostics
     int32_t* d_flag_list = nullptr;  // bins needing the exact fix-up

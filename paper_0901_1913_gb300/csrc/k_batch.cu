@@ -753,6 +753,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     if (oversample < 2 || oversample > 64) return FC2_ERR_INVALID_ARG;
     if (opt.prec != FC2_PREC_FP64 && opt.prec != FC2_PREC_MIXED) return FC2_ERR_INVALID_ARG;
     if (opt.top_k < 0 || opt.top_k > 64) return FC2_ERR_INVALID_ARG;
+    if (opt.fft_kernel < 0 || opt.fft_kernel > 3) return FC2_ERR_INVALID_ARG;
     for (int64_t c = 0; c < C; ++c) {
         if (offsets[c + 1] - offsets[c] < 1 || offsets[c] < 0) return FC2_ERR_INVALID_ARG;
         if (offsets[c + 1] - offsets[c] > (1ll << 31) - 1) return FC2_ERR_INVALID_ARG;
@@ -823,7 +824,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             p.beta = 0.97 * M_PI * (1.0 - 0.5 / ((double)M / (double)N)) * (double)p.w;
             p.stream = s;
             plan_fft_passes(&p);
-            p.use_r64 = true;
+            p.fft_family = fft_family_of(opt.fft_kernel);
             release(p.d_twlo, s); release(p.d_twhi, s); release(p.d_twst, s); release(p.d_dec, s);
             const int sh = (p.logM + 1) / 2;
             cudaError_t e = pool_alloc((void**)&p.d_twlo, (size_t)(1ll << sh) * csz, s);

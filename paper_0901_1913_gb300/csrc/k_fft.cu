@@ -172,7 +172,7 @@ packed:
 // Shared tile of R rows x J columns; element (r, jj) has logical index
 // e = r * J + jj and lives at phys(e) = e + e / 32 (one pad slot per 32
 // elements keeps the strided butterfly writes free of bank conflicts).
-FC2_HD int phys(int e) { return e + (e >> 5); }
+FC2_HD constexpr int phys(int e) { return e + (e >> 5); }
 
 // Stage decomposition of a length-2^LOGR DFT: the first stage takes LOGR % 4
 // bits (if nonzero), every other stage 4 bits (radix 16).
@@ -578,19 +578,17 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
                     }
                     const int jm = (j0 + jj) & nsg_mask;
                     if (a.logNs > 0 && jm != 0) {
-                        // w_M^{(pp + 64 k) jm 2^lts} = base * step^k, step^k = lo[k & 7] hi[k >> 3]
+                        // w_M^{(pp + 64 k) jm 2^lts} = base * step^k, step^k = lo[k & 7] hi[k >> 3];
+                        // every factor is a table lookup (no chains of products)
                         const cpx<T> base = twiddle(twlo, twhi, a.tws, (int64_t)((pp * jm) << lts));
-                        const cpx<T> st1 = twiddle(twlo, twhi, a.tws, (int64_t)((64 * jm) << lts));
                         cpx<T> lo[8], hi[8];
                         lo[0] = mk<T>(1.f, 0.f);
-                        lo[1] = st1;
-#pragma unroll
-                        for (int q = 2; q < 8; ++q) lo[q] = mul(lo[q - 1], st1);
-                        const cpx<T> s8 = mul(lo[7], st1);
                         hi[0] = mk<T>(1.f, 0.f);
-                        hi[1] = s8;
 #pragma unroll
-                        for (int q = 2; q < 8; ++q) hi[q] = mul(hi[q - 1], s8);
+                        for (int q = 1; q < 8; ++q) {
+                            lo[q] = twiddle(twlo, twhi, a.tws, (int64_t)((64 * q * jm) << lts));
+                            hi[q] = twiddle(twlo, twhi, a.tws, (int64_t)((512 * q * jm) << lts));
+                        }
 #pragma unroll
                         for (int k = 0; k < QA; ++k) {
                             cpx<T> w = base;
@@ -694,6 +692,287 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
             }
         }
         __syncthreads();  // the tile buffer is reused by the next iteration
+    }
+}
+
+// ------------------------------------------- radix-16 pass fed by bulk copies
+// Float passes of radix R = 2^8..2^12 as the in-CTA Stockham stages of
+// k_fft_pass (radix 16; the first stage takes LOGR mod 4 bits when that is
+// nonzero), on tiles of 8192 elements with one persistent 512-thread CTA per
+// SM.  A later pass reads each tile -- one contiguous 64 KB run of the blocked
+// layout -- with bulk asynchronous copies (cp.async.bulk, completion counted
+// on an mbarrier) into one of two input buffers, so the next tile streams in
+// while the current one is transformed; the first pass reads the occupied
+// rows of the spread grid with plain loads.  Stage 1 reads the input buffer
+// and writes the padded work buffer, the middle stages work in place there,
+// and the last stage's results go from registers straight to global memory
+// where that fills whole 32-byte sectors (the last pass; a next pass of the
+// same radix), otherwise through the work buffer.  Every mbarrier wait is
+// bounded: a CTA that gives up sets FC2_ERR_TIMEOUT in *status, waits (again
+// bounded) for its other copy in flight and returns.
+constexpr int PT_NT = 512;
+constexpr int PT_LOGE = 13;
+constexpr long long PT_WAIT_CYCLES = 4000000000ll;  // about two seconds
+
+FC2_D uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+FC2_D void mbar_init(uint64_t* m, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(m)), "r"(count)
+                 : "memory");
+}
+FC2_D void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+FC2_D void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+FC2_D void mbar_expect_tx(uint64_t* m, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(m)),
+                 "r"(bytes)
+                 : "memory");
+}
+FC2_D void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* m) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(m))
+        : "memory");
+}
+FC2_D bool mbar_try_wait(uint64_t* m, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the completion of phase `parity` of *m.
+FC2_D bool mbar_wait_bounded(uint64_t* m, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(m, parity))
+        if (clock64() - t0 > PT_WAIT_CYCLES) return false;
+    return true;
+}
+
+template <int LOGR>
+constexpr size_t pass_tma_smem() {
+    return (size_t)(2 * (1 << PT_LOGE) + phys((1 << PT_LOGE) - 1) + 1 + stage_tw_size(LOGR)) *
+               sizeof(cpx<float>) +
+           2 * sizeof(uint64_t);
+}
+
+template <int LOGR>
+__global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __restrict__ in,
+                                                        cpx<float>* __restrict__ out, PassArgs a,
+                                                        const int64_t* __restrict__ Lg,
+                                                        const cpx<float>* __restrict__ twlo,
+                                                        const cpx<float>* __restrict__ twhi,
+                                                        const cpx<float>* __restrict__ twst,
+                                                        int G, int* __restrict__ status) {
+    using T = float;
+    constexpr int R = 1 << LOGR, LOGJ = PT_LOGE - LOGR, J = 1 << LOGJ, E = 1 << PT_LOGE;
+    constexpr int NT = PT_NT;
+    constexpr int NST = stage_tw_size(LOGR);
+    constexpr int NWK = phys(E - 1) + 1;
+    static_assert(LOGR >= 8 && LOGR <= 12, "radix 2^8..2^12");
+    // stage 1 (radix Q1), middle stages of radix 16, last stage of radix 16
+    constexpr int QB1 = stage_bits(LOGR, 0), Q1 = 1 << QB1;
+    constexpr int PER1 = ((R / Q1) * J) / NT;
+    constexpr int DL = LOGR - 4, NSL = 1 << DL;            // last stage: Ns = R / 16
+    constexpr int TOFF_L = NST - 15 * NSL;                 // its twiddle table
+    static_assert(PER1 * NT == (R / Q1) * J, "stage-1 butterflies must divide evenly");
+    static_assert(NSL * J == NT, "one last-stage butterfly per thread");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cpx<T>* ib = reinterpret_cast<cpx<T>*>(smem_raw);  // [2][E] input buffers
+    cpx<T>* wk = ib + 2 * E;                             // padded work buffer
+    cpx<T>* st = wk + NWK;                               // stage twiddles
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(st + NST);
+    const int tid = threadIdx.x;
+    const int M = 1 << a.logM;
+    const int S = M >> LOGR;
+    const int tiles_x = S >> LOGJ;
+    const int ntiles = tiles_x * G;
+    const bool bulk = !a.first;
+    for (int i = tid; i < NST; i += NT) st[i] = twst[i];
+    if (bulk && tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    // thread 0: copy tile t into input buffer b (four 16 KB pieces, one mbarrier)
+    auto issue = [&](int t, int b) {
+        const int gt = t / tiles_x, bt = t - gt * tiles_x;
+        const cpx<T>* src = in + (int64_t)gt * M + (int64_t)bt * E;
+        mbar_expect_tx(&mbar[b], (unsigned)(E * sizeof(cpx<T>)));
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            bulk_g2s(ib + b * E + c * (E / 4), src + c * (E / 4),
+                     (unsigned)(E / 4 * sizeof(cpx<T>)), &mbar[b]);
+    };
+    if (bulk && tid == 0) {
+        if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+        if ((int)(blockIdx.x + gridDim.x) < ntiles) issue(blockIdx.x + gridDim.x, 1);
+    }
+    const int nsg_mask = (1 << a.logNs) - 1;
+    const int lts = a.logM - a.logNs - LOGR;
+    const int logNs = a.logNs;
+    const bool same_radix = (logNs == 0 && a.logM - a.logRn == LOGR);
+    int it = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const int g = tile / tiles_x;
+        const int bx = tile - g * tiles_x;
+        const int j0 = bx * J;
+        if (bulk) {
+            const bool ok = mbar_wait_bounded(&mbar[buf], (unsigned)((it >> 1) & 1));
+            if (!__syncthreads_and(ok)) {
+                // give up: report, wait for the other buffer's copy if one is in flight
+                if (tid == 0 && status) atomicExch(status, (int)FC2_ERR_TIMEOUT);
+                if (tile + (int)gridDim.x < ntiles)
+                    mbar_wait_bounded(&mbar[buf ^ 1], (unsigned)(((it + 1) >> 1) & 1));
+                return;
+            }
+        }
+        // ---- stage 1: radix Q1 from the input (buffer or grid) into the work buffer
+        {
+            const cpx<T>* gin = in + (int64_t)g * M;
+            const cpx<T>* src = ib + buf * E;
+            int rows = R;
+            if (!bulk) {
+                rows = (int)((Lg[g] + S - 1) / S);
+                if (rows > R) rows = R;
+            }
+#pragma unroll
+            for (int b = 0; b < PER1; ++b) {
+                const int bi = tid + b * NT;
+                const int jj = bi & (J - 1), pp = bi >> LOGJ;
+                cpx<T> v[Q1];
+                if (!bulk) {
+#pragma unroll
+                    for (int k = 0; k < Q1; ++k) {
+                        const int r = pp + k * (R / Q1);
+                        v[k] = (r < rows) ? gin[j0 + jj + (int64_t)r * S] : mk<T>(0.f, 0.f);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < Q1; ++k) v[k] = src[(pp + k * (R / Q1)) * J + jj];
+                    const int jm = (j0 + jj) & nsg_mask;
+                    if (logNs > 0 && jm != 0) {
+                        // w_M^{(pp + k R/Q1) jm 2^lts} = base * step^k, step^k = lo[k & 3] hi[k >> 2]
+                        const cpx<T> base = twiddle(twlo, twhi, a.tws, (int64_t)((pp * jm) << lts));
+                        const cpx<T> st1 =
+                            twiddle(twlo, twhi, a.tws, (int64_t)(((R / Q1) * jm) << lts));
+                        cpx<T> lo[4], hi[4];
+                        lo[0] = mk<T>(1.f, 0.f);
+                        lo[1] = st1;
+                        lo[2] = mul(st1, st1);
+                        lo[3] = mul(lo[2], st1);
+                        hi[0] = mk<T>(1.f, 0.f);
+                        hi[1] = mul(lo[2], lo[2]);
+                        hi[2] = mul(hi[1], hi[1]);
+                        hi[3] = mul(hi[2], hi[1]);
+                        v[0] = mul(v[0], base);
+#pragma unroll
+                        for (int k = 1; k < Q1; ++k) {
+                            cpx<T> w = base;
+                            if ((k & 3) != 0) w = mul(w, lo[k & 3]);
+                            if ((k >> 2) != 0) w = mul(w, hi[k >> 2]);
+                            v[k] = mul(v[k], w);
+                        }
+                    }
+                }
+                SmallDFT<T, Q1>::run(v);
+#pragma unroll
+                for (int k = 0; k < Q1; ++k) wk[phys((pp * Q1 + k) * J + jj)] = v[k];
+            }
+        }
+        __syncthreads();
+        // the input buffer is free: ask for the tile after next
+        if (bulk && tid == 0 && tile + 2 * (int)gridDim.x < ntiles) {
+            fence_proxy_async_smem();
+            issue(tile + 2 * gridDim.x, buf);
+        }
+        // ---- middle stages, in place
+        TwgArgs tg;
+        tg.j0 = j0;
+        tg.nsg_mask = nsg_mask;
+        tg.lts = lts;
+        tg.tws = a.tws;
+        if constexpr (LOGR - QB1 > 4) {
+            cta_stage<T, R, J, NT, 4, QB1, 0, false>(wk, st, tg, twlo, twhi);
+            if constexpr (LOGR - QB1 > 8) {
+                constexpr int TOFF3 = 15 * (1 << QB1);
+                cta_stage<T, R, J, NT, 4, QB1 + 4, TOFF3, false>(wk, st, tg, twlo, twhi);
+            }
+        }
+        // ---- last stage (radix 16, Ns = R / 16): registers
+        const int jj = tid & (J - 1), pp = tid >> LOGJ;  // pp < NSL
+        cpx<T> v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = wk[phys((pp + k * NSL) * J + jj)];
+#pragma unroll
+        for (int k = 1; k < 16; ++k) v[k] = mul(v[k], st[TOFF_L + (k - 1) * NSL + pp]);
+        SmallDFT<T, 16>::run(v);
+        __syncthreads();  // every thread has read the work buffer
+        // output row of element k: pp + k NSL
+        if (a.last) {
+            const int o0 = j0 + jj + (pp << logNs);
+            const int step = NSL << logNs;
+            if (g < a.npk) {
+                cpx<T>* plus = out + (int64_t)(2 * g) * a.N;
+                cpx<T>* minus = plus + a.N;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int o = o0 + k * step;
+                    const int jp = o - a.sh;
+                    const int jmi = ((M - o) & (M - 1)) - a.sh;
+                    if ((unsigned)jp < (unsigned)a.N) plus[jp] = v[k];
+                    if ((unsigned)jmi < (unsigned)a.N) minus[jmi] = v[k];
+                }
+            } else {
+                cpx<T>* spec = out + (int64_t)(a.npk + g) * a.N;
+                const int lo_end = a.N - a.hN, hi_start = M - a.hN;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int o = o0 + k * step;
+                    if (o < lo_end) spec[o + a.hN] = v[k];
+                    else if (o >= hi_start) spec[o - hi_start] = v[k];
+                }
+            }
+        } else if (same_radix) {
+            cpx<T>* gout = out + (int64_t)g * M;
+            const int LOGJn = a.logJn, Jn = 1 << a.logJn;
+            const int logBlk = a.logRn + a.logJn;
+            const int col = (j0 + jj) << LOGJn;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int kr = pp + k * NSL;
+                gout[((int64_t)(kr >> LOGJn) << logBlk) + col + (kr & (Jn - 1))] = v[k];
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) wk[phys((pp + k * NSL) * J + jj)] = v[k];
+            __syncthreads();
+            cpx<T>* gout = out + (int64_t)g * M;
+            const int LOGJn = a.logJn, Jn = 1 << a.logJn;
+            const int logBlk = a.logRn + a.logJn;
+            const int logSn = a.logM - a.logRn;
+            for (int e = tid; e < E; e += NT) {
+                const int kl = e & (Jn - 1);
+                const int jc = (e >> LOGJn) & (J - 1);
+                const int kb = e >> (LOGJn + LOGJ);
+                const int k = (kb << LOGJn) + kl;
+                const int j = j0 + jc;
+                const int i = ((j >> logNs) << (logNs + LOGR)) + (j & ((1 << logNs) - 1)) +
+                              (k << logNs);
+                const int jn = i & ((1 << logSn) - 1), rn = i >> logSn;
+                gout[((int64_t)(jn >> LOGJn) << logBlk) + (rn << LOGJn) + (jn & (Jn - 1))] =
+                    wk[phys(k * J + jc)];
+            }
+            __syncthreads();
+        }
     }
 }
 
@@ -803,7 +1082,7 @@ struct TuneKey {
         return std::tie(dev, logM, G, fp64, packed) < std::tie(o.dev, o.logM, o.G, o.fp64, o.packed);
     }
 };
-static std::map<TuneKey, std::pair<std::vector<int>, bool>> g_tuned;
+static std::map<TuneKey, std::pair<std::vector<int>, int>> g_tuned;
 static std::mutex g_tune_mu;
 
 cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
@@ -815,7 +1094,7 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
             set_passes(p, it->second.first);
-            p->use_r64 = it->second.second;
+            p->fft_family = it->second.second;
             return init_twiddles(p, s);
         }
     }
@@ -829,12 +1108,15 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
     }
     float best = 1e30f;
     std::vector<int> best_rs = cands.front();
-    bool best_r64 = true;
+    int best_fam = FFT_R64;
     cudaError_t e = cudaSuccess;
+    const int fams_f32[3] = {FFT_BULK, FFT_R64, FFT_R16};
+    const int nfam = p->fp64 ? 1 : 3;
     for (const auto& rs : cands) {
-        for (int r64 = 1; r64 >= (p->fp64 ? 1 : 0); --r64) {
+        for (int fi = 0; fi < nfam; ++fi) {
+            const int fam = p->fp64 ? FFT_R16 : fams_f32[fi];
             set_passes(p, rs);
-            p->use_r64 = (r64 == 1);
+            p->fft_family = fam;
             if ((e = init_twiddles(p, s)) != cudaSuccess) break;
             if ((e = launch_fft(p, s)) != cudaSuccess) break;  // warm-up
             cudaEventRecord(e0, s);
@@ -847,7 +1129,7 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
             if (ms < best) {
                 best = ms;
                 best_rs = rs;
-                best_r64 = (r64 == 1);
+                best_fam = fam;
             }
         }
         if (e != cudaSuccess) break;
@@ -856,10 +1138,10 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
     cudaEventDestroy(e1);
     if (e != cudaSuccess) return e;
     set_passes(p, best_rs);
-    p->use_r64 = best_r64;
+    p->fft_family = best_fam;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[key] = {best_rs, best_r64};
+        g_tuned[key] = {best_rs, best_fam};
     }
     return init_twiddles(p, s);
 }
@@ -869,7 +1151,10 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
 template <typename T>
 static int logj_of(const fc2_plan_s* p, int logR) {
     if (logR == p->logM) return 0;  // single pass: one column
-    if (sizeof(T) == 4 && p->use_r64 && logR >= 10 && logR <= 12) return P64_LOGE - logR;
+    if (sizeof(T) == 4 && p->fft_family == FFT_R64 && logR >= 10 && logR <= 12)
+        return P64_LOGE - logR;
+    if (sizeof(T) == 4 && p->fft_family != FFT_R16 && logR >= 8 && logR <= 12)
+        return PT_LOGE - logR;
     return FftCfg<T>::LOGE - logR;
 }
 
@@ -919,11 +1204,44 @@ static cudaError_t run_pass64(fc2_plan_s* p, const void* in, void* out, const Pa
     return cudaGetLastError();
 }
 
+template <int LOGR>
+static cudaError_t run_pass_tma(fc2_plan_s* p, const void* in, void* out, const PassArgs& a,
+                                cudaStream_t s) {
+    constexpr int LOGJ = PT_LOGE - LOGR;
+    const int64_t S = p->M >> LOGR;
+    constexpr size_t smem = pass_tma_smem<LOGR>();
+    auto kern = k_fft_pass_tma<LOGR>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    const int64_t ntiles = (S >> LOGJ) * (int64_t)p->G;
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (nsm <= 0) nsm = 152;
+    }
+    const unsigned blocks = (unsigned)std::min<int64_t>(ntiles, (int64_t)nsm);
+    kern<<<blocks, PT_NT, smem, s>>>((const cpx<float>*)in, (cpx<float>*)out, a, p->d_L,
+                                     (const cpx<float>*)p->d_twlo, (const cpx<float>*)p->d_twhi,
+                                     (const cpx<float>*)p->d_twst + p->twst_off[LOGR], p->G,
+                                     p->d_status);
+    return cudaGetLastError();
+}
+
 template <typename T, int LOGR>
 static cudaError_t run_radix(fc2_plan_s* p, const void* in, void* out, const PassArgs& a,
                              cudaStream_t s) {
     if constexpr (sizeof(T) == 4 && LOGR >= 10 && LOGR <= 12) {
-        if (LOGR != p->logM && p->use_r64) return run_pass64<LOGR>(p, in, out, a, s);
+        if (LOGR != p->logM && p->fft_family == FFT_R64) return run_pass64<LOGR>(p, in, out, a, s);
+    }
+    if constexpr (sizeof(T) == 4 && LOGR >= 8 && LOGR <= 12) {
+        if (LOGR != p->logM && p->fft_family != FFT_R16) return run_pass_tma<LOGR>(p, in, out, a, s);
     }
     if (LOGR == p->logM) {
         constexpr int NT = (1 << LOGR) / 16 < 32 ? 32 : (1 << LOGR) / 16;

@@ -107,3 +107,24 @@ def test_batched_degenerate_bins(fc2, oracle_mod, prec):
         r = compare(block[:, bins].T.astype(np.float64), ref, piv, chi0)
         assert r["ok"], (c, prec, stats, r)
     print(prec, stats)
+
+
+@pytest.mark.parametrize("fft_kernel", ["r64", "r16", "bulk"])
+def test_batched_kernel_families_agree(fc2, oracle_mod, fft_kernel):
+    """The batch's transforms (2^14-point grids, passes (7, 7), and 2^19-point
+    ones, passes (10, 9)) give the same Delta chi^2 with every float kernel
+    family, up to float rounding."""
+    for N in (1 << 13, 1 << 18):
+        b = small_survey(C=6, N=N, seed=13)
+        ref, _, _ = fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df, b.N, 2,
+                                        "mixed", fft_kernel="r16")
+        out, _, _ = fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df, b.N, 2,
+                                        "mixed", fft_kernel=fft_kernel)
+        pos = 0
+        for c in range(b.C):
+            cur = b.curve(c)
+            blk = slice(pos, pos + cur.H * cur.N)
+            pos += cur.H * cur.N
+            _, _, chi0, _ = oracle_mod.moments(cur.x, cur.sigma)
+            assert np.max(np.abs(out[blk] - ref[blk])) <= 2e-5 * chi0, (fft_kernel, N, c)
+

@@ -59,6 +59,34 @@ def test_packed_spectra_match_direct_sums(fc2, oracle_mod):
         assert err < 2e-6, (g, err)
 
 
+@pytest.mark.parametrize("fft_kernel", ["r64", "r16", "bulk"])
+@pytest.mark.parametrize("logN,oversample", [(14, 4), (19, 4), (22, 4), (19, 2)])
+def test_fft_kernel_families_match_direct_sums(fc2, oracle_mod, fft_kernel, logN, oversample):
+    """Every float transform kernel family, on pass plans (8, 8), (11, 10) and
+    (12, 12) with packed grids and (10, 10) with unpacked ones, gives spectra
+    equal to the direct sums of Eq. eqPQ."""
+    c = synth.config2(n=3000, N=1 << logN)
+    with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, oversample, "mixed",
+                  fft_kernel=fft_kernel) as p:
+        p.execute()
+        spec = p.spectra()
+        t0 = p.t0
+    w = 1.0 / c.sigma ** 2
+    W, xbar, _, _ = oracle_mod.moments(c.x, c.sigma)
+    cp = w * (c.x - xbar)
+    bins = sample_bins(c.N, 120, logN, windows=[0, c.N // 2, c.N - 1])
+    f = c.f_min + bins * c.df
+    # float transform roundoff grows with the length: ~log2(M) * 2^-24 relative
+    tol = 2e-6 if logN < 20 else 1e-5
+    errs = []
+    for g in range(3 * c.H):
+        k, amp = (g + 1, w) if g < 2 * c.H else (g - 2 * c.H + 1, cp)
+        ref = oracle_mod.trig_sums(c.t - t0, amp, k * f)
+        errs.append(np.max(np.abs(spec[g, bins] - ref)) / np.sum(np.abs(amp)))
+    print(fft_kernel, logN, oversample, max(errs))
+    assert max(errs) < tol, (fft_kernel, logN, oversample, int(np.argmax(errs)), max(errs))
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_config1_full_periodogram(fc2, oracle_mod, prec):
     c = synth.config1()
