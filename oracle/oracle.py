@@ -12,6 +12,7 @@ releases the GIL during the foreign call, and the C code is re-entrant).
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -195,3 +196,49 @@ def periodogram(t, x, sigma, H, f_min, df, N, threads=None, tau_r=TAU_R, with_pi
     """Full oracle periodogram over all N bins: [N, H] (small cases only)."""
     return dchi2_bins(t, x, sigma, H, f_min, df, np.arange(N), threads=threads, tau_r=tau_r,
                       with_pivots=with_pivots)
+
+
+def chi2_logsf_even(x, Hp):
+    """ln P(chi^2 with 2 Hp degrees of freedom >= x) -- the cumulative chi^2
+    distribution of Sec. 3d's p(f) for a model with 2 Hp extra parameters.
+
+    For an even number of degrees of freedom the survival function is the
+    finite Poisson sum  e^{-y} sum_{i=0}^{Hp-1} y^i / i!,  y = x / 2, written
+    out here term by term in log space (log-sum-exp over the terms).  x <= 0
+    gives 0 (probability 1)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.maximum(x, 0.0) / 2.0
+    out = np.zeros_like(y)
+    pos = y > 0
+    yp = y[pos]
+    logs = np.stack([i * np.log(yp) - math.lgamma(i + 1) for i in range(int(Hp))])
+    m = logs.max(axis=0)
+    out[pos] = -yp + m + np.log(np.exp(logs - m).sum(axis=0))
+    return out
+
+
+def fhat(f_min, df, bins):
+    """Trial count 'so far' at f_j (Sec. 3d): f_j / df, the index of f_j on a
+    grid of spacing df that starts at 0, taken as at least 1."""
+    f = freq_of(f_min, df, np.asarray(bins, dtype=np.int64))
+    return np.maximum(f / df, 1.0)
+
+
+def log_false_alarm(dchi2, f_min, df, bins):
+    """ln p(f_j) = ln fhat_j + ln P_{2H', >= Delta chi^2}(Delta chi^2_{H'}(f_j))
+    (Sec. 3d), for dchi2 [len(bins), H] (columns H' = 1..H)."""
+    d = np.asarray(dchi2, dtype=np.float64)
+    lf = np.log(fhat(f_min, df, bins))
+    out = np.empty_like(d)
+    for h in range(d.shape[1]):
+        out[:, h] = lf + chi2_logsf_even(d[:, h], h + 1)
+    return out
+
+
+def adjusted_scale(dchi2_best, chi2_0, n):
+    """Factor s_{H'} with Delta chi^2_adj = s_{H'} Delta chi^2 (Sec. 3d's adjusted
+    Delta chi^2): the denominator is the best fit's residual chi^2 per degree of
+    freedom, (chi2_0 - Delta chi^2_best) / (n - 2H' - 1)."""
+    b = np.asarray(dchi2_best, dtype=np.float64)
+    Hs = np.arange(1, b.size + 1)
+    return (n - 2 * Hs - 1) / (chi2_0 - b)

@@ -336,3 +336,61 @@ def test_brent_refine_finds_the_peak(oracle_mod):
     _, g_f, _, _ = oracle_mod.grad(c.t, c.x, c.sigma, H, fs)
     _, g_far, _, _ = oracle_mod.grad(c.t, c.x, c.sigma, H, fs + 1e-5)
     assert abs(g_f) < 1e-4 * abs(g_far)
+
+
+# ------------------------------------------------------------ significance
+
+@pytest.mark.parametrize("Hp", [1, 2, 3, 5, 8, 16])
+def test_chi2_survival_matches_library(oracle_mod, Hp):
+    """The even-dof chi^2 survival function of p(f) (Sec. 3d) equals scipy's
+    chi^2 log survival function, from the body of the distribution far into
+    its tail."""
+    from scipy import stats
+    x = np.concatenate([[0.0, 1e-3, 0.5, 1.0], np.geomspace(2.0, 1200.0, 40)])
+    got = oracle_mod.chi2_logsf_even(x, Hp)
+    ref = stats.chi2.logsf(x, 2 * Hp)
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+    # far tail (scipy's survival function underflows): mpmath's regularised
+    # upper incomplete gamma at 50 digits
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    xt = np.geomspace(2000.0, 5e6, 12)
+    ref_t = [float(mpmath.log(mpmath.gammainc(Hp, a=mpmath.mpf(v) / 2, regularized=True)))
+             for v in xt]
+    np.testing.assert_allclose(oracle_mod.chi2_logsf_even(xt, Hp), ref_t, rtol=1e-13)
+    # one harmonic: exponential distribution, ln P = -x/2
+    if Hp == 1:
+        np.testing.assert_allclose(got, -x / 2, rtol=1e-15, atol=0)
+
+
+def test_false_alarm_is_uniform_under_the_null(oracle_mod):
+    """Under a constant source, P_{2H', >= Delta chi^2}(Delta chi^2) at a fixed
+    frequency is uniform on (0, 1) -- the oracle's Delta chi^2 fed through
+    the oracle's survival function (Sec. 3d's reading of P)."""
+    from scipy import stats
+    rng = np.random.default_rng(321)
+    n, R = 40, 2000
+    t = np.sort(rng.uniform(0, 20, n))
+    sigma = rng.uniform(0.3, 2.0, n)
+    vals = np.empty((R, 2))
+    for r in range(R):
+        x = 1.0 + sigma * rng.standard_normal(n)
+        vals[r] = oracle_mod.dchi2_freqs(t, x, sigma, 2, [0.731], threads=1)[0]
+    for Hp in (1, 2):
+        u = np.exp(oracle_mod.chi2_logsf_even(vals[:, Hp - 1], Hp))
+        assert stats.kstest(u, "uniform").pvalue > 1e-3
+
+
+def test_false_alarm_and_adjusted_hand_values(oracle_mod):
+    """fhat = f / df (at least 1) and the adjusted-Delta chi^2 factor on hand
+    examples (Sec. 3d)."""
+    # f_min = df: fhat = j + 1; f_min = 0: the first bin counts as one trial
+    np.testing.assert_array_equal(oracle_mod.fhat(0.5, 0.5, [0, 1, 9]), [1.0, 2.0, 10.0])
+    np.testing.assert_array_equal(oracle_mod.fhat(0.0, 0.25, [0, 1, 4]), [1.0, 1.0, 4.0])
+    d = np.array([[0.0, 0.0], [10.0, 12.0]])
+    lp = oracle_mod.log_false_alarm(d, 0.5, 0.5, [0, 3])
+    np.testing.assert_allclose(lp[0], [0.0, 0.0], atol=1e-15)
+    np.testing.assert_allclose(lp[1, 0], math.log(4.0) - 5.0, rtol=1e-14)
+    np.testing.assert_allclose(lp[1, 1], math.log(4.0) - 6.0 + math.log(7.0), rtol=1e-14)
+    s = oracle_mod.adjusted_scale([100.0, 200.0], 500.0, 100)
+    np.testing.assert_allclose(s, [97.0 / 400.0, 95.0 / 300.0], rtol=1e-15)
