@@ -192,6 +192,28 @@ fc2_status fc2_backward_batched(int64_t C, const int64_t* offsets,
                                 double* f_refined, double* dchi2_refined, double* d_df,
                                 double* d_dx, double* d_dsigma);
 
+/*
+ * fc2_significance -- significance of the trial frequencies of the last
+ * fc2_execute of p (Sec. 3d).
+ *   The paper ranks frequencies by p(f) = fhat * P_{2H', >= Delta chi^2}, the
+ *   chi^2 survival function with 2H' degrees of freedom at Delta chi^2_{H'}(f)
+ *   times the trial count so far, fhat = f / df (taken as at least 1).
+ *   log_p [H][N]: ln p(f_j) for every H' and j (row-major as dchi2), host or
+ *     device memory (detected), or NULL.  ln p = ln fhat - Delta chi^2 / 2 +
+ *     ln sum_{i < H'} (Delta chi^2 / 2)^i / i!, with the last two terms in float
+ *     (absolute error ~1e-5, far below the error of Delta chi^2 itself).
+ *   j_min [H], log_p_min [H] (host): per H' the bin with the smallest ln p
+ *     (ties to the lowest j) and that value.  May be NULL.
+ *   adj_scale [H] (host): s_{H'} = (n - 2H' - 1) / (chi2_0 - Delta chi^2_best),
+ *     so that the adjusted Delta chi^2_adj = s_{H'} Delta chi^2 (Sec. 3d, the
+ *     best fit's residual chi^2 per degree of freedom as the denominator);
+ *     0 when n <= 2H' + 1 or the best fit leaves no residual.  May be NULL.
+ * Returns FC2_ERR_INVALID_ARG if p is NULL or has not completed an execute.
+ * Synchronous; runs on the plan's stream.
+ */
+fc2_status fc2_significance(fc2_plan p, double* log_p, int64_t* j_min, double* log_p_min,
+                            double* adj_scale);
+
 /* Release a plan and its device memory.  NULL is ignored. */
 void fc2_plan_destroy(fc2_plan p);
 

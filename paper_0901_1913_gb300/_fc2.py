@@ -112,6 +112,8 @@ def load():
         lib.fc2_trim_device_memory.restype = i32
         lib.fc2_debug_t0.argtypes = [_P]
         lib.fc2_debug_t0.restype = dbl
+        lib.fc2_significance.argtypes = [_P, _P, _P, _P, _P]
+        lib.fc2_significance.restype = i32
         _lib = lib
         return lib
 
@@ -268,6 +270,20 @@ class Plan:
     @property
     def t0(self):
         return float(load().fc2_debug_t0(self.h))
+
+    def significance(self, log_p=None):
+        """Significance of the last execute (fc2_significance): returns
+        (log_p [H, N] or None, j_min [H], log_p_min [H], adj_scale [H]).
+        log_p: True for a new host array, or a preallocated float64 numpy array
+        or CUDA tensor of H*N elements; None skips the full array."""
+        if log_p is True:
+            log_p = np.empty((self.H, self.N), dtype=np.float64)
+        jmin = np.zeros(self.H, dtype=np.int64)
+        lpmin = np.zeros(self.H)
+        adj = np.zeros(self.H)
+        _check(load().fc2_significance(self.h, _ptr(log_p), jmin.ctypes.data, lpmin.ctypes.data,
+                                       adj.ctypes.data), "fc2_significance")
+        return log_p, jmin, lpmin, adj
 
 
 def trim_device_memory(device=0):

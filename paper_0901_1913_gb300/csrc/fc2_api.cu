@@ -439,6 +439,7 @@ fc2_status fc2_execute(fc2_plan p, double* dchi2, fc2_best* best, fc2_best* peak
     p->last_exact2_count = p->last_flag_count > 0 ? tiers[0] : 0;
     p->last_exact3_count = p->last_flag_count > 0 ? tiers[1] : 0;
     if (status != 0) return (fc2_status)status;
+    p->executed = true;
     if (best) memcpy(best, recs.data(), sizeof(fc2_best) * p->H);
     if (peaks) memcpy(peaks, recs.data() + p->H, sizeof(fc2_best) * p->top_k);
     if (chi2_0) *chi2_0 = p->scal[SC_CHI0];
@@ -634,6 +635,45 @@ fc2_status fc2_stage_timing(fc2_plan p, int enable) {
     for (int i = 0; i < 8; ++i) p->stage_ms[i] = 0.0;
     p->stage_n = 0;
     return FC2_OK;
+}
+
+fc2_status fc2_significance(fc2_plan p, double* log_p, int64_t* j_min, double* log_p_min,
+                            double* adj_scale) {
+    if (!p || !p->executed) return FC2_ERR_INVALID_ARG;
+    if (cudaSetDevice(p->device) != cudaSuccess) return FC2_ERR_CUDA;
+    cudaStream_t s = p->stream;
+    const int H = p->H;
+    const size_t cells = (size_t)H * p->N;
+    bool direct = false;
+    if (log_p) {
+        cudaPointerAttributes at;
+        direct = cudaPointerGetAttributes(&at, log_p) == cudaSuccess &&
+                 at.type == cudaMemoryTypeDevice && at.device == p->device;
+        cudaGetLastError();
+    }
+    Guard g;
+    double* dlp = nullptr;
+    char* small = nullptr;  // jmin [H] int64, lpmin [H], adj [H]
+    if (log_p && !direct) g.ok(pool_alloc((void**)&dlp, cells * 8, s));
+    g.ok(pool_alloc((void**)&small, (size_t)H * 24, s));
+    if (g.e == cudaSuccess) {
+        int64_t* djmin = (int64_t*)small;
+        double* dlpmin = (double*)(small + (size_t)H * 8);
+        double* dadj = (double*)(small + (size_t)H * 16);
+        g.ok(launch_significance(p, direct ? log_p : dlp, djmin, dlpmin, dadj, s));
+        std::vector<char> hs((size_t)H * 24);
+        g.ok(cudaMemcpyAsync(hs.data(), small, hs.size(), cudaMemcpyDeviceToHost, s));
+        if (log_p && !direct) g.ok(cudaMemcpyAsync(log_p, dlp, cells * 8, cudaMemcpyDeviceToHost, s));
+        g.ok(cudaStreamSynchronize(s));
+        if (g.e == cudaSuccess) {
+            if (j_min) memcpy(j_min, hs.data(), (size_t)H * 8);
+            if (log_p_min) memcpy(log_p_min, hs.data() + (size_t)H * 8, (size_t)H * 8);
+            if (adj_scale) memcpy(adj_scale, hs.data() + (size_t)H * 16, (size_t)H * 8);
+        }
+    }
+    if (dlp) cudaFreeAsync(dlp, s);
+    if (small) cudaFreeAsync(small, s);
+    return map_err(g.e);
 }
 
 fc2_status fc2_trim_device_memory(int device) {

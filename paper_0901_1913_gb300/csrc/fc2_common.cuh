@@ -127,6 +127,38 @@ FC2_D float es_kernel<float>(float z, float inv_half_w, float beta) {
 }
 
 // Device status word: first error code wins.
+// Exact float -> double conversion on the integer pipes (the double pipe of
+// this part is narrow).  Handles zeros, subnormals, infinities and NaN.
+FC2_D double f2d_exact(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint64_t sign = (uint64_t)(b >> 31) << 63;
+    uint32_t e = (b >> 23) & 0xffu, man = b & 0x7fffffu;
+    uint64_t r;
+    if (e == 0xffu) {
+        r = sign | (0x7ffull << 52) | ((uint64_t)man << 29);
+    } else if (e != 0) {
+        r = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)man << 29);
+    } else if (man == 0) {
+        r = sign;
+    } else {  // subnormal float: normalise
+        const int sh = __clz(man) - 8;  // shift that moves the leading 1 to bit 23
+        man = (man << sh) & 0x7fffffu;
+        r = sign | ((uint64_t)(897u - (uint32_t)sh) << 52) | ((uint64_t)man << 29);
+    }
+    return __longlong_as_double((long long)r);
+}
+
+// double -> float on the integer pipes, truncating the mantissa (relative
+// error below 2^-23); for finite v >= 0 -- values below the float range give
+// 0, values above it +inf.
+FC2_D float d2f_trunc(double v) {
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+    if (e <= 0) return 0.0f;
+    if (e >= 255) return __int_as_float(0x7f800000);
+    return __uint_as_float(((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
+}
+
 FC2_D void set_status(int* st, int code) {
     if (st) atomicCAS(st, 0, code);
 }

@@ -142,6 +142,7 @@ struct fc2_plan_s {
     std::vector<fc2::GridGeom> geom;  // per source (sample set)
     std::vector<fc2::FftPass> passes;
     int64_t last_flag_count = 0;
+    bool executed = false;     // the device output holds a completed execute
     int64_t last_exact2_count = 0;
     int64_t last_exact3_count = 0;
     int64_t last_routed[3] = {0, 0, 0};  // bins first sent to fix-up tiers 1..3
@@ -187,6 +188,10 @@ cudaError_t launch_fft(fc2_plan_s* p, cudaStream_t s);
 cudaError_t launch_assemble(fc2_plan_s* p, cudaStream_t s);
 cudaError_t launch_fixup(fc2_plan_s* p, int64_t n1, int64_t n2, int64_t n3, cudaStream_t s);
 cudaError_t launch_exact_bins(fc2_plan_s* p, int64_t nb, int tier, cudaStream_t s);
+// k_signif.cu: ln p(f) of the last execute (logp may be nullptr) and per row
+// the minimising bin, its ln p and the adjusted-Delta chi^2 factor (device arrays).
+cudaError_t launch_significance(fc2_plan_s* p, double* logp, int64_t* jmin, double* lpmin,
+                                double* adj, cudaStream_t s);
 cudaError_t launch_peaks(fc2_plan_s* p, cudaStream_t s);
 size_t peaks_scratch_bytes(int64_t N, int H, int K);
 size_t exact_scratch_bytes(int64_t n, int H, int64_t cap);

@@ -38,27 +38,6 @@ struct SolveParams {
     float fsq, fsp, fchi0, fs1n, ftau, feps, ferr;
 };
 
-// Exact float -> double conversion on the integer pipes (the double pipe of
-// this part is narrow).  Handles zeros, subnormals, infinities and NaN.
-FC2_D double f2d_exact(float f) {
-    const uint32_t b = __float_as_uint(f);
-    const uint64_t sign = (uint64_t)(b >> 31) << 63;
-    uint32_t e = (b >> 23) & 0xffu, man = b & 0x7fffffu;
-    uint64_t r;
-    if (e == 0xffu) {
-        r = sign | (0x7ffull << 52) | ((uint64_t)man << 29);
-    } else if (e != 0) {
-        r = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)man << 29);
-    } else if (man == 0) {
-        r = sign;
-    } else {  // subnormal float: normalise
-        const int sh = __clz(man) - 8;  // shift that moves the leading 1 to bit 23
-        man = (man << sh) & 0x7fffffu;
-        r = sign | ((uint64_t)(897u - (uint32_t)sh) << 52) | ((uint64_t)man << 29);
-    }
-    return __longlong_as_double((long long)r);
-}
-
 template <typename TS>
 struct SP;  // solve parameters in the path's precision
 template <>
