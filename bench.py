@@ -271,12 +271,14 @@ def run_gpu(args):
         ver = importlib.import_module("paper_0901_1913_gb300.build").kernel_version()
         with open(tpath) as fh:
             kv = dict(ln.strip().split("=", 1) for ln in fh if "=" in ln)
-        if kv.get("kernel_version") == ver:
+        if kv.get("kernel_version") == ver and args.fft_kernel in ("default", "r64"):
             traffic = float(kv["traffic_bytes_per_launch"])
     except Exception:
         traffic = None
+    kname = {"default": "k_fft_pass64", "r64": "k_fft_pass64", "r16": "k_fft_pass",
+             "bulk": "k_fft_pass_tma"}[args.fft_kernel]
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "kernel": "k_fft_pass64 (2 passes/step)",
+            "frac": achieved / peak, "traffic": traffic, "kernel": f"{kname} (2 passes/step)",
             "algorithmic_bytes_per_launch": fft_bytes / P, "launch_ms": fft_ms / P,
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
 
