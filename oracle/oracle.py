@@ -242,3 +242,21 @@ def adjusted_scale(dchi2_best, chi2_0, n):
     b = np.asarray(dchi2_best, dtype=np.float64)
     Hs = np.arange(1, b.size + 1)
     return (n - 2 * Hs - 1) / (chi2_0 - b)
+
+
+def paper_grid_times(t, T0, df, M):
+    """Sec. 3b's gridding, t_hat = floor((t - T0) / dt) with dt = 1 / (M df):
+    the sample times moved to the lower edge of their cell of an array of M
+    cells, returned relative to T0 as t_hat * dt (the array wraps with period
+    M dt = 1 / df, which no trial frequency f_min + j df, f_min a multiple of
+    df, can tell apart).  t - T0 is rounded to double as the library does;
+    the cell index is then exact (rational arithmetic)."""
+    from fractions import Fraction
+    tau = np.asarray(t, dtype=np.float64) - np.float64(T0)
+    fdf = Fraction(float(df))
+    cells = np.empty(tau.size, dtype=np.int64)
+    for i, v in enumerate(tau.tolist()):
+        u = fdf * Fraction(v)
+        frac = u - (u.numerator // u.denominator)
+        cells[i] = (frac * int(M)).__floor__()
+    return cells / (float(M) * float(df)), cells

@@ -394,3 +394,44 @@ def test_false_alarm_and_adjusted_hand_values(oracle_mod):
     np.testing.assert_allclose(lp[1, 1], math.log(4.0) - 6.0 + math.log(7.0), rtol=1e-14)
     s = oracle_mod.adjusted_scale([100.0, 200.0], 500.0, 100)
     np.testing.assert_allclose(s, [97.0 / 400.0, 95.0 / 300.0], rtol=1e-15)
+
+
+# ------------------------------------------------------ the paper's gridding
+
+def test_paper_grid_times_on_and_off_cell_edges(oracle_mod):
+    """Times on cell edges keep their place; just below an edge they fall to
+    the cell beneath (floor, Sec. 3b)."""
+    df, M, T0 = 2.0 ** -10, 2 ** 12, 3.0  # dt = 1 / (M df) = 1/4
+    k = np.array([0, 1, 5, 4095, 4096, 4100])
+    t = T0 + k * 0.25
+    tp, cells = oracle_mod.paper_grid_times(t, T0, df, M)
+    np.testing.assert_array_equal(cells, k % M)
+    np.testing.assert_array_equal(tp, (k % M) * 0.25)
+    tb = T0 + k[1:4] * 0.25 - 1e-9
+    np.testing.assert_array_equal(oracle_mod.paper_grid_times(tb, T0, df, M)[1], k[1:4] - 1)
+
+
+def test_paper_gridding_is_the_fft_of_the_binned_arrays(oracle_mod):
+    """The paper's Phat, Qhat (FFT of the Kronecker-delta binned weighted data
+    and weights, Sec. 3b) equal the direct sums of Eq. eqPQ at the snapped
+    times: numpy's FFT of explicitly binned arrays against the oracle's
+    trigonometric sums."""
+    rng = np.random.default_rng(17)
+    n, df, M = 300, 1.0 / 512.0, 4096
+    t = np.sort(rng.uniform(0.0, 400.0, n))
+    T0 = t.min()
+    w = rng.uniform(0.5, 2.0, n)
+    c = w * rng.standard_normal(n)
+    tp, cells = oracle_mod.paper_grid_times(t, T0, df, M)
+    qh = np.zeros(M)
+    ph = np.zeros(M)
+    np.add.at(qh, cells, w)
+    np.add.at(ph, cells, c)
+    # sign +i (Eq. eqPQ): sum_t a[t] e^{+2 pi i m t / M} = M * ifft(a)[m]
+    Q = M * np.fft.ifft(qh)
+    P = M * np.fft.ifft(ph)
+    m = np.arange(1, 200)
+    np.testing.assert_allclose(Q[m], oracle_mod.trig_sums(tp, w, m * df), rtol=0,
+                               atol=1e-9 * w.sum())
+    np.testing.assert_allclose(P[m], oracle_mod.trig_sums(tp, c, m * df), rtol=0,
+                               atol=1e-9 * np.abs(c).sum())
