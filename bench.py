@@ -369,6 +369,9 @@ WORKLOADS = {
                "Newton refinement at the top-8 peaks",
     "large": "large single curve: n~1e6 at 2-min cadence over 4 yr, H=8, N=2^26 to 24/d, "
              "2x oversampled grids",
+    "paper": "long single curve (n=100000, H=6, N=2^22 to 20/d) under the paper's own gridding: "
+             "nearest-lower-cell binning into one array of 2^27 cells, one transform, harmonics "
+             "read at multiples of the bin index",
 }
 
 
@@ -387,6 +390,74 @@ def _events_ms(fn, steps, warmup, stream=None):
     return e0.elapsed_time(e1) / steps
 
 
+def run_paper_gridding(args, line, threads):
+    """The paper's own method (fc2_options.gridding = 1) on the long curve: GPU
+    rates with the stage split, the same method on the host (numpy FFT and
+    batched regression; the FFT in full, the regression on a sample of bins and
+    scaled), parity against the oracle at the snapped times and the gridding
+    error against the exact periodogram."""
+    import torch
+    from paper_0901_1913_gb300 import _fc2, synth
+    from tests.parity import compare, sample_bins
+    from oracle import oracle, paper_method
+    c = synth.config2()
+    evals = c.N * c.H
+    res = {}
+    for prec in ("mixed", "fp64"):
+        out = torch.empty((c.H, c.N), dtype=torch.float64, device="cuda")
+        with _fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, prec,
+                       gridding="paper", fft_kernel=args.fft_kernel) as p:
+            steps = args.steps if prec == "mixed" else max(2, min(args.steps, 3))
+            for _ in range(max(1, min(args.warmup, 3))):
+                p.execute(out, want_records=True)
+            torch.cuda.synchronize()
+            p.stage_timing(True)
+            ms = _events_ms(lambda: p.execute(out, want_records=True), steps, 0)
+            stage, _, _ = p.stage_times()
+            p.stage_timing(False)
+            _, best, _, chi0 = p.execute(out)
+            res[prec] = (ms, out.cpu().numpy(), best, chi0, [float(v) for v in stage], p.t0)
+    s0 = int(round(c.f_min / c.df))
+    M = 1024
+    while M < 4 * c.H * (s0 + c.N - 1) + 1:
+        M *= 2
+    T0 = res["fp64"][5]
+    f0 = c.truth["f0"]
+    bins = sample_bins(c.N, 40, 7, windows=[int(round((f0 - c.f_min) / c.df)),
+                                            int(res["fp64"][2][-1]["j"])], half=2)
+    tp, _ = oracle.paper_grid_times(c.t, T0, c.df, M)
+    ref, piv = oracle.dchi2_bins(tp, c.x, c.sigma, c.H, c.f_min, c.df, bins, threads=threads,
+                                 with_pivots=True)
+    exact = oracle.dchi2_bins(c.t, c.x, c.sigma, c.H, c.f_min, c.df, bins, threads=threads)
+    chi0 = res["fp64"][3]
+    par = {prec: compare(res[prec][1][:, bins].T, ref, piv, chi0) for prec in res}
+    # the same method on the host: full transform, regression on a sample of bins
+    sample = np.unique(np.concatenate([np.arange(0, c.N, max(1, c.N // 65536)), bins]))
+    d_cpu, tcpu = paper_method.fchi2_paper(c.t, c.x, c.sigma, c.H, c.f_min, c.df, sample, M, T0=T0)
+    solve_full = tcpu["solve_s"] * c.N / sample.size
+    cpu_total = tcpu["grid_s"] + tcpu["fft_s"] + solve_full
+    idx = np.searchsorted(sample, bins)
+    names = ["binning", "transform", "regression", "exact fix-up", "peaks"]
+    line.update(value=evals / (res["mixed"][0] / 1e3), ms_per_step=res["mixed"][0],
+                dtype="f32+f64 (mixed)",
+                fp64={"value": evals / (res["fp64"][0] / 1e3), "ms_per_step": res["fp64"][0]},
+                stage_ms={prec: dict(zip(names, res[prec][4])) for prec in res},
+                parity_snapped_times={prec: {"max_err_rel": par[prec]["max_err_rel"],
+                                              "near_alias_bins": par[prec]["n_near_alias"],
+                                              "ok": bool(par[prec]["ok"])} for prec in res},
+                gridding_error_vs_exact=float(np.max(np.abs(res["fp64"][1][:, bins].T - exact)) / chi0),
+                cpu_baseline={"value": evals / cpu_total, "unit": UNIT, "cores": 1,
+                              "kind": "paper-method (numpy FFT + batched regression, host)",
+                              "sample": f"transform in full (M = {M}); regression on "
+                                        f"{sample.size} of {c.N} bins, scaled",
+                              "split_s": {"binning": tcpu["grid_s"], "transform": tcpu["fft_s"],
+                                          "regression": solve_full},
+                              "max_diff_vs_gpu_fp64_rel": float(
+                                  np.max(np.abs(d_cpu[idx] - res["fp64"][1][:, bins].T)) / chi0)})
+    line["config"].update(n=c.n, N=c.N, H=c.H, M=M, gridding="paper")
+    print(json.dumps(line), flush=True)
+
+
 def run_workload(args):
     """The other synthetic workloads, one JSON line each (for the measurement
     table; the default run is the long curve).  Oracle parity on a bounded
@@ -399,6 +470,9 @@ def run_workload(args):
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload]}}
+    if args.workload == "paper":
+        run_paper_gridding(args, line, threads)
+        return
     if args.workload in ("short", "large"):
         c = synth.config1() if args.workload == "short" else synth.config5()
         evals = c.N * c.H

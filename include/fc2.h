@@ -86,6 +86,24 @@ typedef struct {
                                   asynchronous copies (radix 2^8..2^12 passes).  Passes a
                                   family does not cover use family 2.  FP64 ignores it;
                                   values outside 0..3 are FC2_ERR_INVALID_ARG */
+    int gridding;              /* 0 = spreading kernel of width kernel_width with its
+                                  Fourier transform divided out, one transform per
+                                  harmonic multiple (default; meets 1e-4 chi2_0).
+                                  1 = the paper's gridding (Sec. 3b): weights and
+                                  weighted data binned into the lower cell
+                                  floor((t - T0) / dt) of one zero-padded array
+                                  (Kronecker delta, no correction), T0 = min t,
+                                  dt = 1 / (M df), one transform of length M (the
+                                  smallest power of two above 4 H (f_min/df + N - 1),
+                                  oversample ignored), harmonics read at k fhat
+                                  (Sec. 3c).  Delta chi^2 then equals the exact value
+                                  for times moved to their cell's lower edge: the
+                                  paper's gridding error is kept, not bounded.  Needs
+                                  f_min a whole number of df steps; no exact fix-up
+                                  (flagged bins keep the double re-solve of the
+                                  gridded sums); peak records still come from direct
+                                  sums at their bins.  Not available in
+                                  fc2_execute_batched (FC2_ERR_UNSUPPORTED) */
 } fc2_options;
 
 /* One selected frequency: bin index, frequency, Delta chi^2 and the

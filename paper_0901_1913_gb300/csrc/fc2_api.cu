@@ -131,9 +131,24 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         return FC2_ERR_INVALID_ARG;
     if (opt.top_k < 0 || opt.top_k > 64 || opt.alias_tau < 0.0) return FC2_ERR_INVALID_ARG;
     if (opt.fft_kernel < 0 || opt.fft_kernel > 3) return FC2_ERR_INVALID_ARG;
+    if (opt.gridding < 0 || opt.gridding > 1) return FC2_ERR_INVALID_ARG;
     if (H > 8) return FC2_ERR_UNSUPPORTED;
-    const int64_t M = fc2_grid_size(N, oversample);
+    int64_t M = fc2_grid_size(N, oversample);
     if (M == 0) return FC2_ERR_INVALID_ARG;
+    // The paper's gridding (Sec. 3b-3c): trial frequencies are bins fhat = s0 + j
+    // of one transform of length M whose multiples k fhat, k <= 2H, stay below M/2.
+    int64_t s0 = 0;
+    if (opt.gridding == 1) {
+        const double r = f_min / df;
+        const double rs = floor(r + 0.5);
+        if (!(rs >= 0.0 && rs < 1e12 && fabs(r - rs) <= 1e-9 * std::max(1.0, r)))
+            return FC2_ERR_INVALID_ARG;
+        s0 = (int64_t)rs;
+        const double top = 4.0 * H * (double)(s0 + N - 1) + 1.0;
+        if (top > (double)(1ll << 30)) return FC2_ERR_UNSUPPORTED;
+        M = 1024;
+        while ((double)M < top) M <<= 1;
+    }
 
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return FC2_ERR_CUDA;
@@ -160,6 +175,9 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     while ((1ll << p->logM) < M) ++p->logM;
     p->G = 3 * H;
     p->fp64 = (opt.prec == FC2_PREC_FP64);
+    p->paper = (opt.gridding == 1);
+    p->s0 = s0;
+    if (p->paper) p->G = 1;
     p->w = opt.kernel_width ? opt.kernel_width : default_width(p->fp64, oversample);
     const double sig_eff = (double)M / (double)N;
     p->beta = 0.97 * M_PI * (1.0 - 0.5 / sig_eff) * (double)p->w;
@@ -173,7 +191,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         const double r = f_min / df;
         const double shd = floor(r + 0.5);
         const int64_t mmax = (int64_t)shd + N - 1;
-        if (!p->fp64 && !opt.kernel_width && shd >= 0.0 && shd < 1e15 &&
+        if (!p->paper && !p->fp64 && !opt.kernel_width && shd >= 0.0 && shd < 1e15 &&
             fabs(r - shd) <= 1e-9 * std::max(1.0, r) && 4 * std::max<int64_t>(mmax, 1) <= M) {
             p->packed = true;
             p->sh = (int64_t)shd;
@@ -195,12 +213,13 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     const int G = p->G;
     const int NSRC = p->nsrc ? p->nsrc : G;  // sample sets
     const size_t spec_rows = p->packed ? (size_t)2 * G : (size_t)3 * H;
+    const size_t spec_bytes = p->paper ? (size_t)M * csz : spec_rows * N * csz;
     // memory estimate
     size_t need = 0;
     need += (size_t)n * 8 * 6 + (size_t)n * 4;
     need += (size_t)NSRC * n * (4 + tsz + csz);
     need += 2 * (size_t)G * M * csz;
-    need += spec_rows * N * csz + (size_t)N * tsz + (size_t)H * N * 8 + (size_t)N * 4;
+    need += spec_bytes + (size_t)N * tsz + (size_t)H * N * 8 + (size_t)N * 4;
     size_t freeb = 0, totalb = 0;
     if (cudaMemGetInfo(&freeb, &totalb) == cudaSuccess && need > freeb) {
         if (p->own_stream) cudaStreamDestroy(p->stream);
@@ -236,7 +255,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         g.ok(dalloc(&p->d_cs, (size_t)NSRC * n * csz, s)) &&
         g.ok(dalloc(&p->d_grid[0], grid_bytes, s)) &&
         g.ok(dalloc(&p->d_grid[1], std::max(grid_bytes, keysort_b), s)) &&
-        g.ok(dalloc(&p->d_spec, spec_rows * N * csz, s)) &&
+        g.ok(dalloc(&p->d_spec, spec_bytes, s)) &&
         g.ok(dalloc(&p->d_dec, (size_t)N * tsz, s)) &&
         g.ok(dalloc(&p->d_dec_p, (size_t)N * tsz, s)) &&
         g.ok(dalloc(&p->d_twlo, (size_t)(1ll << ((p->logM + 1) / 2)) * csz, s)) &&
@@ -272,8 +291,10 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     else if (status != 0) st = (fc2_status)status;
     if (st == FC2_OK) {
         // Time origin: the earliest sample, moved back by (w/2 + 1) cells of
-        // the k = 1 grid so no sample's spreading window reaches below cell 0.
-        const double back = (0.5 * std::max(p->w, p->w_p) + 1.0) / ((double)M * df);
+        // the k = 1 grid so no sample's spreading window reaches below cell 0
+        // (the paper's gridding: T0 = min t, its "T0 <= all t_i").
+        const double back =
+            p->paper ? 0.0 : (0.5 * std::max(p->w, p->w_p) + 1.0) / ((double)M * df);
         p->scal[SC_T0] -= back;
         p->scal[SC_TAUMAX] += back;
         g.ok(cudaMemcpyAsync(p->d_scal, p->scal, sizeof(p->scal), cudaMemcpyHostToDevice, s));
@@ -323,6 +344,17 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
                 Lh[gi] = std::max(Ls[t0], t0 + 1 < NSRC ? Ls[t0 + 1] : 0);
             }
         }
+        if (p->paper) {  // one array: cells floor(frac(df tau) M), all of them if it wraps
+            const double cells = df * p->scal[SC_TAUMAX] * (double)M;
+            int64_t L = M;
+            if (df * p->scal[SC_TAUMAX] < 1.0 && cells + 2.0 < (double)M) {
+                L = ((int64_t)floor(cells) + 2 + unit - 1) / unit * unit;
+                L = std::min(L, M);
+            }
+            Lh[0] = L;
+            p->geom[0].L = L;
+            p->geom[0].wraps = (L == M) ? 1 : 0;
+        }
         g.ok(cudaMemcpyAsync(p->d_L, Lh.data(), G * 8, cudaMemcpyHostToDevice, s));
         // Algorithmic bytes of the transform: each pass reads its input once
         // (the first pass only the rows that hold samples) and writes its output
@@ -335,7 +367,8 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
                 for (int gi = 0; gi < G; ++gi) {
                     int64_t rd = M;
                     if (pi == 0) rd = std::min(R, (Lh[gi] + Sp - 1) / Sp) * Sp;
-                    const int64_t wr = (pi == P - 1) ? (gi < p->npk ? 2 * N : N) : M;
+                    const int64_t wr =
+                        (pi == P - 1 && !p->paper) ? (gi < p->npk ? 2 * N : N) : M;
                     fb += (double)(rd + wr) * (double)csz;
                 }
             }
@@ -343,7 +376,8 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         }
         if (opt.autotune) g.ok(autotune_fft(p, s));  // sets the pass plan and its tables
         else g.ok(init_twiddles(p, s));
-        g.ok(init_deconv(p, s));  // synchronises
+        if (p->paper) g.ok(cudaStreamSynchronize(s));  // no deconvolution
+        else g.ok(init_deconv(p, s));                   // synchronises
         if (g.e != cudaSuccess) st = map_err(g.e);
     }
     if (st != FC2_OK) {
@@ -360,6 +394,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
 
 // Kernel launches per stage (for the launch count the benchmark reports).
 static int64_t launches_front(const fc2_plan_s* p) {
+    if (p->paper) return 1 + (int64_t)p->passes.size() + 1 + (p->fp64 ? 0 : 1);  // bin, fft, assemble(+resolve)
     int64_t n = 1 + 1 + (int64_t)p->passes.size() + 1 + (p->fp64 ? 0 : 1);  // phase, spread, fft, assemble(+resolve)
     int bits = 0;
     while ((1ll << bits) < p->M + 2 * std::max(p->w, p->w_p) + 2) ++bits;
@@ -376,7 +411,8 @@ static fc2_status run_pipeline(fc2_plan_s* p) {
     cudaStream_t s = p->stream;
     Guard g;
     rec(p, 0);
-    g.ok(launch_phase(p, s)) && g.ok(launch_spread(p, s));
+    if (p->paper) g.ok(launch_bin(p, s));
+    else g.ok(launch_phase(p, s)) && g.ok(launch_spread(p, s));
     rec(p, 1);
     g.ok(launch_fft(p, s));
     rec(p, 2);
@@ -386,13 +422,14 @@ static fc2_status run_pipeline(fc2_plan_s* p) {
     g.ok(cudaMemcpyAsync(fc, p->d_flag_count, 16, cudaMemcpyDeviceToHost, s));
     g.ok(cudaStreamSynchronize(s));
     if (g.e != cudaSuccess) return map_err(g.e);
+    if (p->paper) fc[0] = fc[2] = fc[3] = 0;  // no exact fix-up under the paper's gridding
     p->last_resolve_count = fc[1];
     p->last_flag_count = (int64_t)fc[0] + fc[2] + fc[3];
     p->last_routed[0] = fc[0]; p->last_routed[1] = fc[2]; p->last_routed[2] = fc[3];
     for (int i = 0; i < 4; ++i)
         if (fc[i] > p->flag_cap) return FC2_ERR_NUMERIC;
     const int64_t nfix = p->last_flag_count;
-    g.ok(launch_fixup(p, fc[0], fc[2], fc[3], s));
+    if (nfix > 0) g.ok(launch_fixup(p, fc[0], fc[2], fc[3], s));
     rec(p, 4);
     g.ok(launch_peaks(p, s));
     rec(p, 5);
@@ -519,6 +556,32 @@ void fc2_debug_counts(fc2_plan p, int64_t* out7) {
 fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im) {
     if (!p || !re || !im) return FC2_ERR_INVALID_ARG;
     const size_t N = (size_t)p->N;
+    if (p->paper) {  // one spectrum Z = Qhat + i Phat, mode m at [M/2 + m]
+        const size_t M = (size_t)p->M;
+        std::vector<char> zb(M * (p->fp64 ? 16 : 8));
+        if (cudaMemcpy(zb.data(), p->d_spec, zb.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return FC2_ERR_CUDA;
+        auto z = [&](int64_t m, double* r, double* i) {
+            const size_t k = (size_t)((int64_t)(M / 2) + m);
+            if (p->fp64) { *r = ((const double*)zb.data())[2 * k]; *i = ((const double*)zb.data())[2 * k + 1]; }
+            else { *r = ((const float*)zb.data())[2 * k]; *i = ((const float*)zb.data())[2 * k + 1]; }
+        };
+        const int H = p->H;
+        for (int r = 0; r < 3 * H; ++r) {
+            const bool isq = r < 2 * H;
+            const int k = isq ? r + 1 : r - 2 * H + 1;
+            for (size_t j = 0; j < N; ++j) {
+                const int64_t m = (int64_t)k * (p->s0 + (int64_t)j);
+                double ar, ai, br, bi;
+                z(m, &ar, &ai);
+                z(-m, &br, &bi);
+                const size_t o = (size_t)r * N + j;
+                if (isq) { re[o] = 0.5 * (ar + br); im[o] = 0.5 * (ai - bi); }
+                else { re[o] = 0.5 * (ai + bi); im[o] = 0.5 * (br - ar); }
+            }
+        }
+        return FC2_OK;
+    }
     const size_t rows = p->packed ? (size_t)2 * p->G : (size_t)3 * p->H;  // rows as stored
     const size_t cnt = rows * N;
     std::vector<char> buf(cnt * (p->fp64 ? 16 : 8));

@@ -143,6 +143,8 @@ struct fc2_plan_s {
     std::vector<fc2::FftPass> passes;
     int64_t last_flag_count = 0;
     bool executed = false;     // the device output holds a completed execute
+    bool paper = false;        // the paper's nearest-lower-cell gridding (one packed grid)
+    int64_t s0 = 0;            // f_min / df (paper gridding)
     int64_t last_exact2_count = 0;
     int64_t last_exact3_count = 0;
     int64_t last_routed[3] = {0, 0, 0};  // bins first sent to fix-up tiers 1..3
@@ -175,6 +177,8 @@ cudaError_t launch_gather_sorted(const double* t, const double* x, const double*
 cudaError_t launch_phase(fc2_plan_s* p, cudaStream_t s);
 cudaError_t sort_wrapping_keys(fc2_plan_s* p, cudaStream_t s);
 cudaError_t launch_spread(fc2_plan_s* p, cudaStream_t s);
+// The paper's nearest-lower-cell binning into grid 0 (paper gridding).
+cudaError_t launch_bin(fc2_plan_s* p, cudaStream_t s);
 
 // k_fft.cu
 cudaError_t init_twiddles(fc2_plan_s* p, cudaStream_t s);

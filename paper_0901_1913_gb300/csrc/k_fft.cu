@@ -1268,10 +1268,11 @@ static cudaError_t fft_impl(fc2_plan_s* p, cudaStream_t s) {
         a.last = (i == P - 1);
         a.logRn = a.last ? 0 : p->passes[i + 1].logR;
         a.logJn = a.last ? 0 : logj_of<T>(p, p->passes[i + 1].logR);
-        a.N = (int)p->N;
-        a.hN = (int)(p->N / 2);
+        // the paper's gridding keeps every mode: mode m at spec[M/2 + m]
+        a.N = p->paper ? (int)p->M : (int)p->N;
+        a.hN = p->paper ? (int)(p->M / 2) : (int)(p->N / 2);
         a.tws = p->tw_shift;
-        a.npk = p->npk;
+        a.npk = p->paper ? 0 : p->npk;
         a.sh = (int)p->sh;
         const void* in = p->d_grid[src];
         void* out = a.last ? p->d_spec : p->d_grid[1 - src];

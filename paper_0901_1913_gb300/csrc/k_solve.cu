@@ -36,6 +36,10 @@ struct SolveParams {
     // float copies for the float path (a conversion per thread would run on the
     // double pipe): sq, sp, chi0, s1n, tau, eps_spec + eps_f32, err_fix
     float fsq, fsp, fchi0, fs1n, ftau, feps, ferr;
+    // the paper's gridding: one spectrum Z = Qhat + i Phat of length pM, bin j
+    // at index fhat = s0 + j
+    int paper;
+    int64_t pM, s0;
 };
 
 template <typename TS>
@@ -112,6 +116,36 @@ FC2_D void load_gridded(const cpx<TS>* __restrict__ spec, const TS* __restrict__
     }
 }
 
+// Normalised system of bin j under the paper's gridding (Sec. 3b-3c): one
+// spectrum Z = Qhat + i Phat of the binned weights and weighted data, read at
+// the multiples k fhat of the bin's index (Q at k = 1..2H, P at k = 1..H), the
+// two real transforms separated by Qhat(m) = (Z(m) + conj Z(-m)) / 2 and
+// Phat(m) = (Z(m) - conj Z(-m)) / 2i; no deconvolution (the paper's Kronecker
+// delta has none).  The transform stores mode m at spec[M/2 + m]; k fhat < M/2
+// by the choice of M.
+template <typename TS, int H>
+FC2_D void load_paper(const cpx<TS>* __restrict__ spec, int64_t M, int64_t fh, TS sq, TS sp,
+                      TS s1n, Sys<TS, H>& S) {
+    S.qr[0] = (TS)1;
+    S.qi[0] = (TS)0;
+    S.pr[0] = s1n;
+    S.pi[0] = (TS)0;
+    const TS hq = (TS)0.5 * sq, hp = (TS)0.5 * sp;
+    const cpx<TS>* z0 = spec + M / 2;
+#pragma unroll
+    for (int k = 1; k <= 2 * H; ++k) {
+        const int64_t m = (int64_t)k * fh;
+        const cpx<TS> a = z0[m];
+        const cpx<TS> b = z0[-m];
+        S.qr[k] = (a.x + b.x) * hq;
+        S.qi[k] = (a.y - b.y) * hq;
+        if (k <= H) {
+            S.pr[k] = (a.y + b.y) * hp;
+            S.pi[k] = (b.x - a.x) * hp;
+        }
+    }
+}
+
 // Per trial frequency: deconvolve and normalise the 3H spectra, factor, and
 // write Delta chi^2 for every H'.  A bin whose estimated error is too large
 // for this precision goes to a list: the float path sends it to a double
@@ -129,7 +163,8 @@ __global__ void __launch_bounds__(128) k_assemble(const cpx<TS>* __restrict__ sp
     constexpr int m = 2 * H + 1;
     const SP<TS> q(sp);
     Sys<TS, H> S;
-    load_gridded<TS, H>(spec, dec, dec_p, npk, sp.N, j, q.sq, q.sp, q.s1n, S);
+    if (sp.paper) load_paper<TS, H>(spec, sp.pM, sp.s0 + j, q.sq, q.sp, q.s1n, S);
+    else load_gridded<TS, H>(spec, dec, dec_p, npk, sp.N, j, q.sq, q.sp, q.s1n, S);
     TS out[H];
     TS an2 = (TS)0;
     chol_solve<TS, H, true>(S, q.tau, out, &an2);
@@ -163,7 +198,8 @@ __global__ void __launch_bounds__(128) k_resolve(const cpx<float>* __restrict__ 
          b += (int64_t)gridDim.x * wpb) {
         const int64_t j = rlist[b];
         Sys<float, H> Sf;
-        load_gridded<float, H>(spec, dec, dec_p, npk, sp.N, j, sp.fsq, sp.fsp, sp.fs1n, Sf);
+        if (sp.paper) load_paper<float, H>(spec, sp.pM, sp.s0 + j, sp.fsq, sp.fsp, sp.fs1n, Sf);
+        else load_gridded<float, H>(spec, dec, dec_p, npk, sp.N, j, sp.fsq, sp.fsp, sp.fs1n, Sf);
         Sys<double, H> S;
 #pragma unroll
         for (int k = 0; k <= 2 * H; ++k) { S.qr[k] = Sf.qr[k]; S.qi[k] = Sf.qi[k]; }
@@ -716,6 +752,9 @@ static SolveParams solve_params(const fc2_plan_s* p) {
     sp.eps_t2 = 1.5e-12;  // EPS_DF
     sp.fs1n = (float)sp.s1n; sp.ftau = (float)sp.tau;
     sp.feps = (float)(sp.eps_spec + sp.eps_f32); sp.ferr = (float)sp.err_fix;
+    sp.paper = p->paper ? 1 : 0;
+    sp.pM = p->M;
+    sp.s0 = p->s0;
     return sp;
 }
 
