@@ -260,3 +260,21 @@ def paper_grid_times(t, T0, df, M):
         frac = u - (u.numerator // u.denominator)
         cells[i] = (frac * int(M)).__floor__()
     return cells / (float(M) * float(df)), cells
+
+
+def detrend(t, x, sigma, degree):
+    """x minus its weighted least-squares polynomial of the given degree in t
+    (weights sigma^-2): the polynomial detrending of the reference
+    implementation described in Sec. 4 ("detrend the data with a polynomial
+    fit ... removing variation out to t^3").  The fit is a library least-squares
+    solve on the design 1, u, .., u^degree with u = (t - t_c) / s, t_c and s the
+    centre and half-width of the time span (a change of basis only)."""
+    t = np.asarray(t, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    sw = 1.0 / np.asarray(sigma, dtype=np.float64)
+    lo, hi = t.min(), t.max()
+    s = 0.5 * (hi - lo) if hi > lo else 1.0
+    u = (t - 0.5 * (hi + lo)) / s
+    D = np.vander(u, int(degree) + 1, increasing=True)
+    c, *_ = np.linalg.lstsq(D * sw[:, None], x * sw, rcond=None)
+    return x - D @ c

@@ -454,3 +454,28 @@ def test_paper_method_equals_least_squares_at_snapped_times(oracle_mod):
     assert strict.mean() > 0.9
     np.testing.assert_allclose(d[strict], ref[strict], rtol=0, atol=1e-9 * chi0)
     assert set(times) == {"grid_s", "fft_s", "solve_s"}
+
+
+# ------------------------------------------------------------ detrending
+
+@pytest.mark.parametrize("degree", [0, 1, 2, 3])
+def test_detrend_removes_polynomials_and_is_orthogonal(oracle_mod, degree):
+    """A polynomial of the fitted degree is removed exactly; in general the
+    residual is weighted-orthogonal to 1, t, .., t^degree; degree 0 is the
+    weighted mean of Sec. 3b."""
+    rng = np.random.default_rng(degree)
+    n = 400
+    t = np.sort(rng.uniform(1000.0, 1600.0, n))
+    sigma = rng.uniform(0.5, 2.0, n)
+    w = 1.0 / sigma ** 2
+    tc = (t - 1300.0) / 300.0
+    poly = sum((k + 1.5) * tc ** k for k in range(degree + 1))
+    r = oracle_mod.detrend(t, poly, sigma, degree)
+    assert np.max(np.abs(r)) < 1e-10 * np.max(np.abs(poly))
+    x = poly + np.sin(2 * np.pi * 0.37 * t) + sigma * rng.standard_normal(n)
+    r = oracle_mod.detrend(t, x, sigma, degree)
+    for k in range(degree + 1):
+        assert abs(np.sum(w * r * tc ** k)) < 1e-9 * np.sum(w * np.abs(x) * np.abs(tc) ** k)
+    if degree == 0:
+        _, xbar, _, _ = oracle_mod.moments(x, sigma)
+        np.testing.assert_allclose(r, x - xbar, rtol=0, atol=1e-12 * np.abs(x).max())
