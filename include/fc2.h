@@ -104,6 +104,17 @@ typedef struct {
                                   gridded sums); peak records still come from direct
                                   sums at their bins.  Not available in
                                   fc2_execute_batched (FC2_ERR_UNSUPPORTED) */
+    int detrend;               /* degree D (0..3) of the polynomial removed from x before
+                                  the search: "detrend the data with a polynomial fit"
+                                  (Sec. 4).  The weighted (sigma^-2) least-squares
+                                  polynomial of degree D in t is subtracted at plan
+                                  creation; chi2_0, Delta chi^2 and the records then
+                                  describe the residuals (A_0 is their mean, the trend
+                                  is not added back).  0 = none (the weighted mean is
+                                  always removed, Sec. 3b).  FC2_ERR_INVALID_ARG outside
+                                  0..3 or when the samples cannot fix the polynomial;
+                                  fc2_backward and fc2_execute_batched return
+                                  FC2_ERR_UNSUPPORTED for D > 0 */
 } fc2_options;
 
 /* One selected frequency: bin index, frequency, Delta chi^2 and the

@@ -99,6 +99,7 @@ bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 void free_plan_memory(fc2_plan_s* p) {
     cudaStream_t s = p->stream;
     if (!p->borrowed) { dfree(p->d_t, s); dfree(p->d_x, s); dfree(p->d_sigma, s); }
+    dfree(p->d_xdet, s);
     dfree(p->d_scal, s); dfree(p->d_status, s); dfree(p->d_perm, s);
     dfree(p->d_tau, s); dfree(p->d_wq, s); dfree(p->d_wp, s);
     dfree(p->d_key, s); dfree(p->d_dlt, s); dfree(p->d_cs, s);
@@ -132,6 +133,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     if (opt.top_k < 0 || opt.top_k > 64 || opt.alias_tau < 0.0) return FC2_ERR_INVALID_ARG;
     if (opt.fft_kernel < 0 || opt.fft_kernel > 3) return FC2_ERR_INVALID_ARG;
     if (opt.gridding < 0 || opt.gridding > 1) return FC2_ERR_INVALID_ARG;
+    if (opt.detrend < 0 || opt.detrend > 3) return FC2_ERR_INVALID_ARG;
     if (H > 8) return FC2_ERR_UNSUPPORTED;
     int64_t M = fc2_grid_size(N, oversample);
     if (M == 0) return FC2_ERR_INVALID_ARG;
@@ -177,6 +179,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     p->fp64 = (opt.prec == FC2_PREC_FP64);
     p->paper = (opt.gridding == 1);
     p->s0 = s0;
+    p->detrend = opt.detrend;
     if (p->paper) p->G = 1;
     p->w = opt.kernel_width ? opt.kernel_width : default_width(p->fp64, oversample);
     const double sig_eff = (double)M / (double)N;
@@ -289,6 +292,30 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     fc2_status st = FC2_OK;
     if (g.e != cudaSuccess) st = map_err(g.e);
     else if (status != 0) st = (fc2_status)status;
+    if (st == FC2_OK && p->detrend > 0) {
+        // Polynomial detrending (Sec. 4), then the moments of the residuals.
+        // A borrowed x is left untouched: the residuals go to a plan buffer.
+        double* xo = p->d_x;
+        if (p->borrowed) {
+            g.ok(dalloc(&p->d_xdet, (size_t)n * 8, s));
+            xo = p->d_xdet;
+        }
+        void* scratch = nullptr;
+        g.ok(pool_alloc(&scratch, trend_scratch_bytes(n), s));
+        if (g.e == cudaSuccess) {
+            g.ok(launch_detrend(p->d_t, p->d_x, p->d_sigma, n, p->detrend, p->d_scal, p->d_status,
+                                scratch, xo, s));
+            p->d_x = xo;
+            g.ok(launch_moments_long(p->d_t, p->d_x, p->d_sigma, n, p->d_scal, p->d_status,
+                                     p->d_red, s));
+            g.ok(cudaMemcpyAsync(p->scal, p->d_scal, sizeof(p->scal), cudaMemcpyDeviceToHost, s));
+            g.ok(cudaMemcpyAsync(&status, p->d_status, 4, cudaMemcpyDeviceToHost, s));
+            cudaFreeAsync(scratch, s);
+            g.ok(cudaStreamSynchronize(s));
+        }
+        if (g.e != cudaSuccess) st = map_err(g.e);
+        else if (status != 0) st = (fc2_status)status;
+    }
     if (st == FC2_OK) {
         // Time origin: the earliest sample, moved back by (w/2 + 1) cells of
         // the k = 1 grid so no sample's spreading window reaches below cell 0
@@ -533,6 +560,7 @@ fc2_status fc2_execute_batched(int64_t C, const int64_t* offsets, const double* 
 fc2_status fc2_backward(fc2_plan p, int K, const int64_t* peak_j, const double* grad_out,
                         double* f_refined, double* dchi2_refined, double* d_df, double* d_dx,
                         double* d_dsigma) {
+    if (p && p->detrend > 0) return FC2_ERR_UNSUPPORTED;  // gradients through the detrend fit
     return plan_backward(p, K, peak_j, grad_out, f_refined, dchi2_refined, d_df, d_dx, d_dsigma);
 }
 

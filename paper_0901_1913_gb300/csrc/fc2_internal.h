@@ -144,6 +144,8 @@ struct fc2_plan_s {
     int64_t last_flag_count = 0;
     bool executed = false;     // the device output holds a completed execute
     bool paper = false;        // the paper's nearest-lower-cell gridding (one packed grid)
+    int detrend = 0;           // degree of the polynomial removed from x (0 = none)
+    double* d_xdet = nullptr;  // detrended x when the caller's x is borrowed
     int64_t s0 = 0;            // f_min / df (paper gridding)
     int64_t last_exact2_count = 0;
     int64_t last_exact3_count = 0;
@@ -179,6 +181,11 @@ cudaError_t sort_wrapping_keys(fc2_plan_s* p, cudaStream_t s);
 cudaError_t launch_spread(fc2_plan_s* p, cudaStream_t s);
 // The paper's nearest-lower-cell binning into grid 0 (paper gridding).
 cudaError_t launch_bin(fc2_plan_s* p, cudaStream_t s);
+// Polynomial detrending of x (degree D <= 3) into xo; scal holds T0 and max tau.
+size_t trend_scratch_bytes(int64_t n);
+cudaError_t launch_detrend(const double* t, const double* x, const double* sigma, int64_t n,
+                           int D, const double* scal, int* status, void* scratch, double* xo,
+                           cudaStream_t s);
 
 // k_fft.cu
 cudaError_t init_twiddles(fc2_plan_s* p, cudaStream_t s);

@@ -756,6 +756,8 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     if (opt.fft_kernel < 0 || opt.fft_kernel > 3) return FC2_ERR_INVALID_ARG;
     if (opt.gridding < 0 || opt.gridding > 1) return FC2_ERR_INVALID_ARG;
     if (opt.gridding == 1) return FC2_ERR_UNSUPPORTED;
+    if (opt.detrend < 0 || opt.detrend > 3) return FC2_ERR_INVALID_ARG;
+    if (opt.detrend != 0) return FC2_ERR_UNSUPPORTED;
     for (int64_t c = 0; c < C; ++c) {
         if (offsets[c + 1] - offsets[c] < 1 || offsets[c] < 0) return FC2_ERR_INVALID_ARG;
         if (offsets[c + 1] - offsets[c] > (1ll << 31) - 1) return FC2_ERR_INVALID_ARG;

@@ -238,6 +238,120 @@ cudaError_t launch_moments_long(const double* t, const double* x, const double* 
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------- polynomial detrending
+// "Detrend the data with a polynomial fit" (Sec. 4): the weighted least-squares
+// polynomial of degree D <= 3 in u = (t - t_c) / s (t_c, s the centre and
+// half-width of the span, from the moments' T0 and max tau) is subtracted from
+// x.  Per block: sums of w u^k (k <= 2D) and w x u^p (p <= D); one thread adds
+// the block sums in block order, solves the (D+1)-square normal equations by
+// Cholesky, and a last kernel writes x - poly(u).
+constexpr int TR_NT = 256;
+constexpr int TR_NV = 11;  // 2D + 1 + D + 1 at D = 3
+
+__global__ void __launch_bounds__(TR_NT) k_trend_partial(const double* __restrict__ t,
+                                                         const double* __restrict__ x,
+                                                         const double* __restrict__ sigma,
+                                                         int64_t n, const double* __restrict__ scal,
+                                                         int D, double* __restrict__ part) {
+    __shared__ double red[TR_NT / 32][TR_NV];
+    const double tc = scal[SC_T0] + 0.5 * scal[SC_TAUMAX];
+    const double is = scal[SC_TAUMAX] > 0.0 ? 2.0 / scal[SC_TAUMAX] : 1.0;
+    double acc[TR_NV];
+#pragma unroll
+    for (int v = 0; v < TR_NV; ++v) acc[v] = 0.0;
+    const int64_t i = (int64_t)blockIdx.x * TR_NT + threadIdx.x;
+    if (i < n) {
+        const double w = 1.0 / (sigma[i] * sigma[i]);
+        const double u = (t[i] - tc) * is;
+        double uk = 1.0;
+        for (int k = 0; k <= 2 * D; ++k) {
+            acc[k] = w * uk;
+            if (k <= D) acc[2 * D + 1 + k] = w * x[i] * uk;
+            uk *= u;
+        }
+    }
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < TR_NV; ++v) {
+        double y = acc[v];
+        for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xffffffffu, y, o);
+        if (lane == 0) red[wi][v] = y;
+    }
+    __syncthreads();
+    if (threadIdx.x < TR_NV) {
+        double y = 0.0;
+        for (int q = 0; q < TR_NT / 32; ++q) y += red[q][threadIdx.x];
+        part[(int64_t)blockIdx.x * TR_NV + threadIdx.x] = y;
+    }
+}
+
+__global__ void k_trend_solve(const double* __restrict__ part, int nblk, int D,
+                              double* __restrict__ coef, int* __restrict__ status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double sum[TR_NV];
+    for (int v = 0; v < TR_NV; ++v) sum[v] = 0.0;
+    for (int b = 0; b < nblk; ++b)
+        for (int v = 0; v < TR_NV; ++v) sum[v] += part[(int64_t)b * TR_NV + v];
+    const int m = D + 1;
+    double L[4][4], z[4];
+    for (int r = 0; r < m; ++r) {
+        for (int c = 0; c <= r; ++c) {
+            double v = sum[r + c];
+            for (int k = 0; k < c; ++k) v -= L[r][k] * L[c][k];
+            if (r == c) {
+                if (!(v > 1e-14 * sum[2 * r])) {  // samples cannot fix this degree
+                    if (status) atomicExch(status, (int)FC2_ERR_INVALID_ARG);
+                    for (int q = 0; q < 4; ++q) coef[q] = 0.0;
+                    return;
+                }
+                L[r][r] = sqrt(v);
+            } else {
+                L[r][c] = v / L[c][c];
+            }
+        }
+    }
+    for (int r = 0; r < m; ++r) {
+        double v = sum[2 * D + 1 + r];
+        for (int k = 0; k < r; ++k) v -= L[r][k] * z[k];
+        z[r] = v / L[r][r];
+    }
+    for (int r = m - 1; r >= 0; --r) {
+        double v = z[r];
+        for (int k = r + 1; k < m; ++k) v -= L[k][r] * coef[k];
+        coef[r] = v / L[r][r];
+    }
+    for (int q = m; q < 4; ++q) coef[q] = 0.0;
+}
+
+__global__ void k_trend_apply(const double* __restrict__ t, const double* __restrict__ x,
+                              int64_t n, const double* __restrict__ scal,
+                              const double* __restrict__ coef, int D, double* __restrict__ xo) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double tc = scal[SC_T0] + 0.5 * scal[SC_TAUMAX];
+    const double is = scal[SC_TAUMAX] > 0.0 ? 2.0 / scal[SC_TAUMAX] : 1.0;
+    const double u = (t[i] - tc) * is;
+    double v = coef[D];
+    for (int k = D - 1; k >= 0; --k) v = fma(v, u, coef[k]);
+    xo[i] = x[i] - v;
+}
+
+size_t trend_scratch_bytes(int64_t n) {
+    return (size_t)((n + TR_NT - 1) / TR_NT) * TR_NV * sizeof(double) + 64;
+}
+
+cudaError_t launch_detrend(const double* t, const double* x, const double* sigma, int64_t n,
+                           int D, const double* scal, int* status, void* scratch, double* xo,
+                           cudaStream_t s) {
+    const int nblk = (int)((n + TR_NT - 1) / TR_NT);
+    double* part = (double*)scratch;
+    double* coef = part + (size_t)nblk * TR_NV;
+    k_trend_partial<<<nblk, TR_NT, 0, s>>>(t, x, sigma, n, scal, D, part);
+    k_trend_solve<<<1, 32, 0, s>>>(part, nblk, D, coef, status);
+    k_trend_apply<<<nblk, TR_NT, 0, s>>>(t, x, n, scal, coef, D, xo);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_moments(const double* t, const double* x, const double* sigma,
                            const int64_t* offs, int64_t C, int64_t n_single, double* scal,
                            int* status, cudaStream_t s) {
