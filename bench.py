@@ -369,6 +369,9 @@ WORKLOADS = {
                "Newton refinement at the top-8 peaks",
     "large": "large single curve: n~1e6 at 2-min cadence over 4 yr, H=8, N=2^26 to 24/d, "
              "2x oversampled grids",
+    "shared": "many sources in one field: 4096 curves sharing 2000 epochs over 1000 d, errors "
+              "proportional to one set, H=4, N=2^18 to 12/d; the weights' transforms computed "
+              "once per chunk",
     "paper": "long single curve (n=100000, H=6, N=2^22 to 20/d) under the paper's own gridding: "
              "nearest-lower-cell binning into one array of 2^27 cells, one transform, harmonics "
              "read at multiples of the bin index",
@@ -458,6 +461,78 @@ def run_paper_gridding(args, line, threads):
     print(json.dumps(line), flush=True)
 
 
+def _shared_vs_independent(b, a, r):
+    """Entries where the shared and independent runs differ by more than
+    1e-4 chi2_0 of their curve, and the highest bin among them (they are the
+    nearly singular bins at periods longer than the span)."""
+    offs = np.concatenate([[0], np.cumsum(b.H.astype(np.int64) * b.N)])
+    big, top_j, worst = 0, -1, 0.0
+    for c in range(b.C):
+        sl = slice(offs[c], offs[c + 1])
+        w = 1.0 / b.sigma[b.offsets[c]:b.offsets[c + 1]] ** 2
+        x = b.x[b.offsets[c]:b.offsets[c + 1]]
+        xb = np.sum(w * x) / np.sum(w)
+        chi0 = np.sum(w * (x - xb) ** 2)
+        d = (np.abs(a[sl] - r[sl]) / chi0).reshape(int(b.H[c]), int(b.N[c]))
+        worst = max(worst, float(d.max()))
+        hit = np.nonzero((d > 1e-4).any(axis=0))[0]
+        big += int((d > 1e-4).sum())
+        if hit.size:
+            top_j = max(top_j, int(hit.max()))
+    return {"max_rel_chi2_0": worst, "entries_above_1e-4": big,
+            "entries": int(offs[-1]), "highest_bin_above_1e-4": top_j}
+
+
+def run_shared_field(args, line, threads):
+    """Shared sampling (fc2_options.shared_sampling): the same batch run with
+    the weights' transforms shared and as independent curves; oracle parity on
+    a few curves."""
+    import torch
+    from paper_0901_1913_gb300 import _fc2, synth
+    from tests.parity import compare, sample_bins
+    from oracle import oracle
+    b = synth.shared_field(C=4096)
+    evals = int(np.sum(b.H.astype(np.int64) * b.N))
+    dev = torch.device("cuda", 0)
+    td, xd, sd = (torch.from_numpy(v).to(dev) for v in (b.t, b.x, b.sigma))
+    out = torch.empty(evals, dtype=torch.float32, device=dev)
+    holder = {}
+    res = {}
+    for shared in (True, False):
+        def run():
+            holder["r"] = _fc2.execute_batched(b.offsets, td, xd, sd, b.H, b.f_min, b.df, b.N,
+                                               b.oversample, "mixed", top_k=8, dchi2=out,
+                                               shared_sampling=shared, fft_kernel=args.fft_kernel)
+        ms = _events_ms(run, args.steps, max(1, min(args.warmup, 2)))
+        res[shared] = (ms, holder["r"][2], out.cpu().numpy())
+    got = res[True][2]
+    errs, nb = [], 0
+    t0 = time.perf_counter()
+    offs = np.concatenate([[0], np.cumsum(b.H.astype(np.int64) * b.N)])
+    for c in range(0, b.C, 512):
+        cur = b.curve(c)
+        blk = got[offs[c]:offs[c + 1]].reshape(cur.H, cur.N)
+        bins = sample_bins(cur.N, 24, c, windows=[0], half=2)
+        ref, piv = oracle.dchi2_bins(cur.t, cur.x, cur.sigma, cur.H, cur.f_min, cur.df, bins,
+                                     threads=threads, with_pivots=True)
+        _, _, chi0, _ = oracle.moments(cur.x, cur.sigma)
+        errs.append(compare(blk[:, bins].T.astype(np.float64), ref, piv, chi0))
+        nb += len(bins) * cur.H
+    dt = time.perf_counter() - t0
+    line.update(value=evals / (res[True][0] / 1e3), ms_per_step=res[True][0],
+                dtype="f32+f64 (mixed)", batch_stats=res[True][1],
+                independent_curves={"value": evals / (res[False][0] / 1e3),
+                                    "ms_per_step": res[False][0]},
+                shared_over_independent=res[False][0] / res[True][0],
+                vs_independent=_shared_vs_independent(b, res[True][2], res[False][2]),
+                parity={"curves": len(errs), "max_err_rel": max(r["max_err_rel"] for r in errs),
+                        "ok": all(r["ok"] for r in errs)},
+                cpu_baseline={"value": nb / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                              "sample": f"{nb} evals on {len(errs)} curves"},
+                config=dict(line["config"], curves=b.C, samples=int(b.offsets[-1])))
+    print(json.dumps(line), flush=True)
+
+
 def run_workload(args):
     """The other synthetic workloads, one JSON line each (for the measurement
     table; the default run is the long curve).  Oracle parity on a bounded
@@ -472,6 +547,9 @@ def run_workload(args):
             "config": {"workload": WORKLOADS[args.workload]}}
     if args.workload == "paper":
         run_paper_gridding(args, line, threads)
+        return
+    if args.workload == "shared":
+        run_shared_field(args, line, threads)
         return
     if args.workload in ("short", "large"):
         c = synth.config1() if args.workload == "short" else synth.config5()

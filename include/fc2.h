@@ -115,6 +115,17 @@ typedef struct {
                                   0..3 or when the samples cannot fix the polynomial;
                                   fc2_backward and fc2_execute_batched return
                                   FC2_ERR_UNSUPPORTED for D > 0 */
+    int shared_sampling;       /* fc2_execute_batched only: 1 = every curve was sampled at
+                                  the same times with errors proportional to one set
+                                  (sigma_c = r_c sigma), as for many sources measured
+                                  together in one field (Sec. 4).  Their normalised
+                                  weights agree, so the weights' transforms (Q, Eq.
+                                  eqPQ) are computed once per chunk of curves and every
+                                  curve only adds its H transforms of the weighted
+                                  data (P): 3H C transforms become 2H + H C.  All
+                                  curves need the same n, H, f_min, df and N and the
+                                  same times (checked on the device, FC2_ERR_INVALID_ARG
+                                  otherwise).  0 = independent curves */
 } fc2_options;
 
 /* One selected frequency: bin index, frequency, Delta chi^2 and the

@@ -28,7 +28,7 @@ class Options(ctypes.Structure):
                 ("device", ctypes.c_int), ("inputs_on_device", ctypes.c_int),
                 ("outputs_on_device", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("fft_kernel", ctypes.c_int), ("gridding", ctypes.c_int),
-                ("detrend", ctypes.c_int)]
+                ("detrend", ctypes.c_int), ("shared_sampling", ctypes.c_int)]
 
 # fc2_options.gridding values
 GRIDDING = {"kernel": 0, "paper": 1}
@@ -146,7 +146,7 @@ def _is_dev(a):
 
 def make_options(prec="fp64", kernel_width=0, top_k=0, alias_tau=0.0, stream=None, device=0,
                  inputs_on_device=False, outputs_on_device=False, autotune=False,
-                 fft_kernel="default", gridding="kernel", detrend=0):
+                 fft_kernel="default", gridding="kernel", detrend=0, shared_sampling=False):
     o = Options()
     load().fc2_options_default(ctypes.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -161,6 +161,7 @@ def make_options(prec="fp64", kernel_width=0, top_k=0, alias_tau=0.0, stream=Non
     o.fft_kernel = FFT_KERNELS[fft_kernel] if isinstance(fft_kernel, str) else int(fft_kernel)
     o.gridding = GRIDDING[gridding] if isinstance(gridding, str) else int(gridding)
     o.detrend = int(detrend)
+    o.shared_sampling = int(bool(shared_sampling))
     return o
 
 
@@ -305,7 +306,7 @@ def periodogram(t, x, sigma, H, f_min, df, N, oversample=2, prec="fp64", **kw):
 
 def execute_batched(offsets, t, x, sigma, H, f_min, df, N, oversample=2, prec="mixed", top_k=8,
                     kernel_width=0, dchi2=None, stream=None, device=0, autotune=False,
-                    fft_kernel="default"):
+                    fft_kernel="default", shared_sampling=False):
     """Many curves in one call (fc2_execute_batched).  offsets [C+1], t/x/sigma
     concatenated (numpy host arrays, or CUDA tensors -> read in place); H, f_min,
     df, N per curve.  dchi2: optional preallocated float32 output (numpy or
@@ -329,7 +330,7 @@ def execute_batched(offsets, t, x, sigma, H, f_min, df, N, oversample=2, prec="m
     K = int(top_k or 8)
     peaks = (Best * (C * K))()
     opt = make_options(prec, kernel_width, K, 0.0, stream, device, inputs_on_device=dev,
-                       autotune=autotune, fft_kernel=fft_kernel)
+                       autotune=autotune, fft_kernel=fft_kernel, shared_sampling=shared_sampling)
     rc = lib.fc2_execute_batched(C, offsets.ctypes.data, _ptr(t), _ptr(x), _ptr(sigma),
                                  H.ctypes.data, f_min.ctypes.data, df.ctypes.data, N.ctypes.data,
                                  int(oversample), ctypes.byref(opt), _ptr(dchi2),

@@ -35,6 +35,8 @@ struct CurveTab {
     const float* sp;        // [C] 1/sqrt(W chi2_0)
     const float* s1n;       // [C] sum w(x - xbar) / sqrt(W chi2_0)
     const float* chi0f;     // [C] chi2_0
+    const int* qown;        // [C] curve whose Q transforms (weights only) this curve reads
+    const int* pslot0;      // [C] first P transform slot of the curve
 };
 
 // ------------------------------------------------------------------ gather
@@ -127,9 +129,10 @@ __global__ void __launch_bounds__(128) k_bassemble(const cpx<TS>* __restrict__ s
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= N) return;
     const int c = curves[blockIdx.y];
-    const int g0 = ct.slot0[c];
+    const int qo = ct.qown[c];
+    const int gq = ct.slot0[qo], gp = ct.pslot0[c];
     const TS d = dec[j];
-    const TS dq = d * (TS)ct.sq[c], dp = d * (TS)ct.sp[c];
+    const TS dq = d * (TS)ct.sq[qo], dp = d * (TS)ct.sp[c];
     Sys<TS, H> S;
     S.qr[0] = (TS)1;
     S.qi[0] = (TS)0;
@@ -137,13 +140,13 @@ __global__ void __launch_bounds__(128) k_bassemble(const cpx<TS>* __restrict__ s
     S.pi[0] = (TS)0;
 #pragma unroll
     for (int k = 1; k <= 2 * H; ++k) {
-        const cpx<TS> v = spec[(int64_t)(g0 + k - 1) * N + j];
+        const cpx<TS> v = spec[(int64_t)(gq + k - 1) * N + j];
         S.qr[k] = v.x * dq;
         S.qi[k] = v.y * dq;
     }
 #pragma unroll
     for (int k = 1; k <= H; ++k) {
-        const cpx<TS> v = spec[(int64_t)(g0 + 2 * H + k - 1) * N + j];
+        const cpx<TS> v = spec[(int64_t)(gp + k - 1) * N + j];
         S.pr[k] = v.x * dp;
         S.pi[k] = v.y * dp;
     }
@@ -183,12 +186,13 @@ __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__
         const int c = (int)(rlist[b] >> 32);
         const int64_t j = rlist[b] & 0xffffffffll;
         const int H = ct.H[c];
-        const int g0 = ct.slot0[c];
+        const int qo = ct.qown[c];
+        const int gq = ct.slot0[qo], gp = ct.pslot0[c];
         const double* sc = ct.scal + (int64_t)c * SC_COUNT;
         const double W = sc[SC_W], chi0 = sc[SC_CHI0];
         const double sp = (chi0 > 0.0) ? rsqrt(W * chi0) : 0.0;
         const double d = (double)dec[j];
-        const double dw = d / W;
+        const double dw = d / ct.scal[(int64_t)qo * SC_COUNT + SC_W];
         Sys<double, HM> S;
 #pragma unroll
         for (int k = 0; k <= 2 * HM; ++k) { S.qr[k] = 0.0; S.qi[k] = 0.0; }
@@ -197,12 +201,12 @@ __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__
         S.qr[0] = 1.0;
         S.pr[0] = sc[SC_S1] * sp;
         for (int k = 1; k <= 2 * H; ++k) {
-            const cpx<float> v = spec[(int64_t)(g0 + k - 1) * N + j];
+            const cpx<float> v = spec[(int64_t)(gq + k - 1) * N + j];
             S.qr[k] = (double)v.x * dw;
             S.qi[k] = (double)v.y * dw;
         }
         for (int k = 1; k <= H; ++k) {
-            const cpx<float> v = spec[(int64_t)(g0 + 2 * H + k - 1) * N + j];
+            const cpx<float> v = spec[(int64_t)(gp + k - 1) * N + j];
             S.pr[k] = (double)v.x * d * sp;
             S.pi[k] = (double)v.y * d * sp;
         }
@@ -564,6 +568,7 @@ struct Batch {
     int64_t* off = nullptr; size_t coff = 0;
     int* H = nullptr; size_t cH = 0;
     int* slot0 = nullptr; size_t cslot0 = 0;
+    int *qown = nullptr, *pslot0 = nullptr; size_t cqown = 0, cpslot0 = 0;
     double *fmin = nullptr, *df = nullptr, *scal = nullptr; size_t cfmin = 0, cdf = 0, cscal = 0;
     int64_t* out_off = nullptr; size_t coo = 0;
     float *sq = nullptr, *sp = nullptr, *s1n = nullptr, *chi0f = nullptr;
@@ -594,6 +599,7 @@ struct Batch {
         release(t, s); release(x, s); release(sg, s); release(perm, s); release(tau, s);
         release(wq, s); release(wp, s); release(A, s); release(B, s); release(wq32, s);
         release(wp32, s); release(off, s); release(H, s); release(slot0, s); release(fmin, s);
+        release(qown, s); release(pslot0, s);
         release(df, s); release(scal, s); release(out_off, s); release(sq, s); release(sp, s);
         release(s1n, s); release(chi0f, s); release(slot_cur, s); release(slot_k, s);
         release(slot_kind, s); release(slot_soff, s); release(slot_n, s); release(L, s);
@@ -610,6 +616,28 @@ struct Batch {
 
 __global__ void k_set_count(int32_t* c, int32_t v) { *c = v; }
 
+// Shared sampling: every curve of the chunk must have the first curve's times
+// and errors proportional to its errors (sigma_c = r_c sigma_0, so that their
+// normalised weights and hence the Q transforms agree).  Violations set
+// FC2_ERR_INVALID_ARG in *status.
+__global__ void k_shared_check(const double* __restrict__ t, const double* __restrict__ sg,
+                               const int64_t* __restrict__ off, int nc,
+                               int* __restrict__ status) {
+    const int c = blockIdx.y + 1;
+    if (c >= nc) return;
+    const int64_t n0 = off[1] - off[0];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n0) return;
+    if (off[c + 1] - off[c] != n0) {
+        if (i == 0) atomicExch(status, (int)FC2_ERR_INVALID_ARG);
+        return;
+    }
+    const double r = sg[off[c]] / sg[off[0]];
+    const double a = sg[off[0] + i], b = sg[off[c] + i];
+    if (t[off[c] + i] != t[off[0] + i] || !(fabs(b - r * a) <= 1e-12 * b))
+        atomicExch(status, (int)FC2_ERR_INVALID_ARG);
+}
+
 // Launches of one chunk after its tables are in place: everything from the
 // gather to the coefficient records, no host synchronisation in between (so
 // the sequence can be captured as a CUDA graph).
@@ -622,7 +650,8 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
     fc2_plan_s& p = b.cp;
     const int64_t N = p.N;
     int64_t nl = 0;
-    CurveTab ct{b.off, b.H, b.fmin, b.df, b.scal, b.slot0, b.out_off, b.sq, b.sp, b.s1n, b.chi0f};
+    CurveTab ct{b.off, b.H, b.fmin, b.df, b.scal, b.slot0, b.out_off, b.sq, b.sp, b.s1n, b.chi0f,
+                b.qown, b.pslot0};
     k_bgather<<<(unsigned)((ntot + 255) / 256), 256, 0, s>>>(
         b.t, b.x, b.sg, b.perm, ntot, b.off, nc, b.scal, b.fmin, b.df, b.tau, b.wq, b.wp, b.A, b.B,
         b.wq32, b.wp32);
@@ -758,6 +787,12 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     if (opt.gridding == 1) return FC2_ERR_UNSUPPORTED;
     if (opt.detrend < 0 || opt.detrend > 3) return FC2_ERR_INVALID_ARG;
     if (opt.detrend != 0) return FC2_ERR_UNSUPPORTED;
+    if (opt.shared_sampling < 0 || opt.shared_sampling > 1) return FC2_ERR_INVALID_ARG;
+    const bool shared = opt.shared_sampling == 1;
+    for (int64_t c = 0; c < C && shared; ++c)  // one sampling: same n, H and trial grid
+        if (offsets[c + 1] - offsets[c] != offsets[1] - offsets[0] || Hc[c] != Hc[0] ||
+            fminc[c] != fminc[0] || dfc[c] != dfc[0] || Nc[c] != Nc[0])
+            return FC2_ERR_INVALID_ARG;
     for (int64_t c = 0; c < C; ++c) {
         if (offsets[c + 1] - offsets[c] < 1 || offsets[c] < 0) return FC2_ERR_INVALID_ARG;
         if (offsets[c + 1] - offsets[c] > (1ll << 31) - 1) return FC2_ERR_INVALID_ARG;
@@ -803,7 +838,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         int64_t c1 = c0, S = 0, ntot = 0, nmax = 0, slot_samples = 0;
         while (c1 < C && Nc[c1] == N && c1 - c0 < 2048) {
             const int64_t n = offsets[c1 + 1] - offsets[c1];
-            const int64_t sl = 3 * Hc[c1];
+            const int64_t sl = (shared && c1 > c0) ? Hc[c1] : 3 * Hc[c1];
             const size_t bytes = (size_t)(S + sl) * (size_t)M * csz * 2 + (size_t)(S + sl) * N * csz +
                                  (size_t)(slot_samples + sl * n) * (4 + tsz + csz) +
                                  (size_t)(ntot + n) * 80;
@@ -866,6 +901,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             ok(need(&b.wq32, &b.cwq32, 2 * ntot, s)) && ok(need(&b.wp32, &b.cwp32, 2 * ntot, s)) &&
             ok(need(&b.off, &b.coff, nc + 1, s)) && ok(need(&b.H, &b.cH, nc, s)) &&
             ok(need(&b.slot0, &b.cslot0, nc, s)) && ok(need(&b.fmin, &b.cfmin, nc, s)) &&
+            ok(need(&b.qown, &b.cqown, nc, s)) && ok(need(&b.pslot0, &b.cpslot0, nc, s)) &&
             ok(need(&b.df, &b.cdf, nc, s)) && ok(need(&b.scal, &b.cscal, (size_t)nc * SC_COUNT, s)) &&
             ok(need(&b.out_off, &b.coo, nc, s)) && ok(need(&b.sq, &b.csq, nc, s)) &&
             ok(need(&b.sp, &b.csp, nc, s)) && ok(need(&b.s1n, &b.cs1n, nc, s)) &&
@@ -896,6 +932,12 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         for (int c = 0; c <= nc; ++c) offl[c] = offsets[c0 + c] - base;
         ok(cudaMemcpyAsync(b.off, offl.data(), (nc + 1) * 8, cudaMemcpyHostToDevice, s));
         ok(cudaMemsetAsync(b.counts, 0, 16 * sizeof(int32_t), s));
+        if (shared && nc > 1) {
+            const int64_t n0 = offl[1] - offl[0];
+            k_shared_check<<<dim3((unsigned)((n0 + 255) / 256), (unsigned)(nc - 1)), 256, 0, s>>>(
+                b.t, b.sg, b.off, nc, b.counts + 8);
+            ok(cudaGetLastError());
+        }
         ok(launch_moments(b.t, b.x, b.sg, b.off, nc, 0, b.scal, b.counts + 8, s));
         std::vector<double> scal((size_t)nc * SC_COUNT);
         int32_t status = 0;
@@ -904,7 +946,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         ok(cudaStreamSynchronize(s));
         if (e != cudaSuccess) { st = map_cuda(e); break; }
         if (status) { st = (fc2_status)status; break; }
-        std::vector<int> Hv(nc), slot0(nc), scur, sk, skind;
+        std::vector<int> Hv(nc), slot0(nc), scur, sk, skind, qownv(nc), pslotv(nc);
         std::vector<double> fminv(nc), dfv(nc);
         std::vector<int64_t> oo(nc), ssoff, sn, Lv;
         std::vector<float> sqv(nc), spv(nc), s1v(nc), c0v(nc);
@@ -933,9 +975,13 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             s1v[c] = (float)(sc[SC_S1] * ((chi0 > 0.0) ? 1.0 / sqrt(W * chi0) : 0.0));
             c0v[c] = (float)chi0;
             hg[Hc[cg] - 1].push_back(c);
-            slot0[c] = gi;
+            // shared sampling: the chunk's first curve owns the Q transforms
+            const bool own_q = !shared || c == 0;
+            qownv[c] = own_q ? c : 0;
+            slot0[c] = own_q ? gi : slot0[0];
+            pslotv[c] = own_q ? gi + 2 * Hc[cg] : gi;
             const int64_t n = offl[c + 1] - offl[c];
-            for (int q = 0; q < 3 * Hc[cg]; ++q, ++gi) {
+            for (int q = own_q ? 0 : 2 * Hc[cg]; q < 3 * Hc[cg]; ++q, ++gi) {
                 const int k = (q < 2 * Hc[cg]) ? q + 1 : q - 2 * Hc[cg] + 1;
                 const int kind = (q < 2 * Hc[cg]) ? 0 : 1;
                 scur.push_back(c); sk.push_back(k); skind.push_back(kind);
@@ -965,6 +1011,8 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         ok(cudaMemcpyAsync(b.scal, scal.data(), scal.size() * 8, cudaMemcpyHostToDevice, s));
         ok(cudaMemcpyAsync(b.H, Hv.data(), nc * 4, cudaMemcpyHostToDevice, s));
         ok(cudaMemcpyAsync(b.slot0, slot0.data(), nc * 4, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.qown, qownv.data(), nc * 4, cudaMemcpyHostToDevice, s));
+        ok(cudaMemcpyAsync(b.pslot0, pslotv.data(), nc * 4, cudaMemcpyHostToDevice, s));
         ok(cudaMemcpyAsync(b.fmin, fminv.data(), nc * 8, cudaMemcpyHostToDevice, s));
         ok(cudaMemcpyAsync(b.df, dfv.data(), nc * 8, cudaMemcpyHostToDevice, s));
         ok(cudaMemcpyAsync(b.out_off, oo.data(), nc * 8, cudaMemcpyHostToDevice, s));

@@ -195,6 +195,48 @@ def config3(seed: int = 3, C: int = 4096, N: int = 1 << 18, T: float = 1000.0,
                  np.full(C, N, dtype=np.int64), 2, truth)
 
 
+def shared_field(seed: int = 6, C: int = 1024, n: int = 2000, N: int = 1 << 18,
+                 T: float = 1000.0, f_max: float = 12.0, H: int = 4) -> Batch:
+    """Many sources in one field (Sec. 4's shared sampling, reading): one
+    seasonal/nightly cadence of n epochs over T days shared by all C sources,
+    errors sigma_c = r_c sigma with one lognormal sigma per epoch and
+    r_c ~ U[0.5, 2]; signals as the survey's (f0 ~ U[0.05, 10] /d, sinusoid /
+    sawtooth / Gaussian pulse, per-point SNR ~ U[0.5, 5], 30% nulls); H = 4,
+    N = 2^18, f_min = df = f_max / N."""
+    top = _rng(seed)
+    t = seasonal_night_times(top, n, T)
+    sigma0 = lognormal_sigma(top, n)
+    r = top.uniform(0.5, 2.0, C)
+    f0s = top.uniform(0.05, 10.0, C)
+    shapes = top.integers(0, 3, C)
+    snrs = top.uniform(0.5, 5.0, C)
+    nulls = top.uniform(0, 1, C) < 0.3
+    xs, ss, truth = [], [], []
+    for c in range(C):
+        rng = _rng(seed, c)
+        sigma = r[c] * sigma0
+        if nulls[c]:
+            sig = np.zeros(n)
+        elif shapes[c] == 0:
+            sig = np.sin(2 * np.pi * f0s[c] * t + rng.uniform(0, 2 * np.pi))
+        elif shapes[c] == 1:
+            sig = sawtooth(t + rng.uniform(0, 1.0 / f0s[c]), f0s[c], 1.0)
+        else:
+            sig = gaussian_pulse(t, f0s[c], 1.0, 0.1, rng.uniform(0, 1))
+        if not nulls[c]:
+            rms = np.sqrt(np.mean((sig - sig.mean()) ** 2))
+            sig = sig * (snrs[c] * np.median(sigma) / max(rms, 1e-300))
+        xs.append(sig + sigma * rng.standard_normal(n))
+        ss.append(sigma)
+        truth.append(dict(f0=float(f0s[c]), shape=int(shapes[c]), null=bool(nulls[c]),
+                          r=float(r[c])))
+    offsets = np.arange(C + 1, dtype=np.int64) * n
+    df = f_max / N
+    return Batch(offsets, np.tile(t, C), np.concatenate(xs), np.concatenate(ss),
+                 np.full(C, H, dtype=np.int32), np.full(C, df), np.full(C, df),
+                 np.full(C, N, dtype=np.int64), 2, truth)
+
+
 def config4(seed: int = 4, C: int = 1024, n: int = 2000, N: int = 1 << 16,
             T: float = 500.0, f_max: float = 12.0, H: int = 4) -> Batch:
     """Differentiation batch: C curves of n = 2000 samples over a seasonal
