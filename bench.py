@@ -79,27 +79,39 @@ def load_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons every 20 ms, started before the
+    warm-up; only the samples stamped inside the timed region count."""
 
     def __init__(self, index):
         self.index = index
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.p = None
+        self.t0 = self.t1 = None
 
     def start(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
 
+    def begin(self):
+        import datetime
+        self.t0 = datetime.datetime.now()
+
+    def end(self):
+        import datetime
+        self.t1 = datetime.datetime.now()
+
     def stop(self):
+        import datetime
         if self.p is None:
             return None
+        time.sleep(0.1)  # let the sampler write past the end of the region
         self.p.terminate()
         try:
             self.p.wait(5)
@@ -110,19 +122,31 @@ class ClockSampler:
         with open(self.f.name) as fh:
             for ln in fh:
                 parts = [x.strip() for x in ln.split(",")]
-                if len(parts) >= 9:
-                    rows.append(parts)
+                if len(parts) < 10:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                except ValueError:
+                    ts = None  # unknown stamp format: the sample counts as inside
+                rows.append((ts, parts[1:]))
         os.unlink(self.f.name)
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        pad = datetime.timedelta(milliseconds=20)
+        inside = [r for ts, r in rows if ts is None or (self.t0 and self.t1 and
+                                                        self.t0 - pad <= ts <= self.t1 + pad)]
+        stamped = [(ts, r) for ts, r in rows if ts is not None]
+        if not inside and self.t0 and stamped:  # region shorter than a sample: the nearest one
+            mid = self.t0 + (self.t1 - self.t0) / 2
+            inside = [min(stamped, key=lambda tr: abs(tr[0] - mid))[1]]
+        sm = [float(r[1]) for r in inside if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[5 + i]
+        reasons = sorted({names[i] for r in inside for i in range(4) if "Active" in r[5 + i]
                           and "Not" not in r[5 + i]})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(rows)}
+                "samples": len(inside)}
 
 
 def oracle_sample(c, bins, threads):
@@ -189,13 +213,16 @@ def run_gpu(args):
     out = torch.empty((c.H, c.N), dtype=torch.float64, device=dev)
 
     def timed(plan, steps, warmup, sampler=None):
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)  # the sampler is running before the timed region starts
         for _ in range(warmup):
             plan.execute(out, want_records=True)
         barrier(ws)
         torch.cuda.synchronize()
         plan.stage_timing(True)
         if sampler:
-            sampler.start()
+            sampler.begin()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -203,6 +230,8 @@ def run_gpu(args):
             plan.execute(out, want_records=True)
         e1.record(stream)
         torch.cuda.synchronize()
+        if sampler:
+            sampler.end()
         clocks = sampler.stop() if sampler else None
         barrier(ws)
         ms = e0.elapsed_time(e1)

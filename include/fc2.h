@@ -266,8 +266,10 @@ const char* fc2_status_string(fc2_status s);
  *
  * Plans and batched calls take device memory from a stream-ordered pool the
  * library owns (one per device); memory they release stays in that pool so the
- * next plan does not have to map it again.  No counterpart in the paper.
- * Waits for all work on the device, then trims the pool to zero bytes.
+ * next plan does not have to map it again.  Plans of the same geometry also
+ * share deconvolution tables (kept by the library, at most 8 per process).
+ * No counterpart in the paper.  Waits for all work on the device, drops the
+ * device's cached tables, then trims the pool to zero bytes.
  * Returns FC2_OK (also when the library never allocated on `device`) or
  * FC2_ERR_CUDA.  Must not be called while plans on that device are in use
  * from other threads.

@@ -772,6 +772,8 @@ fc2_status fc2_trim_device_memory(int device) {
     if (!pool) return FC2_OK;
     if (cudaSetDevice(device) != cudaSuccess) return FC2_ERR_CUDA;
     if (cudaDeviceSynchronize() != cudaSuccess) return FC2_ERR_CUDA;
+    drop_deconv_cache(device);
+    if (cudaDeviceSynchronize() != cudaSuccess) return FC2_ERR_CUDA;
     return cudaMemPoolTrimTo(pool, 0) == cudaSuccess ? FC2_OK : FC2_ERR_CUDA;
 }
 

@@ -193,6 +193,7 @@ cudaError_t init_deconv(fc2_plan_s* p, cudaStream_t s);
 void plan_fft_passes(fc2_plan_s* p);
 cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s);  // choose and set up the pass plan
 cudaError_t pool_alloc(void** ptr, size_t bytes, cudaStream_t s);  // library device pool
+void drop_deconv_cache(int dev);  // k_fft.cu: cached deconvolution tables of a device
 cudaError_t launch_fft(fc2_plan_s* p, cudaStream_t s);
 
 // k_solve.cu

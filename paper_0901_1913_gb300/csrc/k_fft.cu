@@ -126,8 +126,83 @@ double cheb_eval_host(const double* coef, double xi, double xi_max) {
     return cheb_clenshaw(coef, CHEB_N, 2.0 * xi * xi / ymax - 1.0);
 }
 
+// Deconvolution tables depend only on the plan's geometry (device, N, M, the
+// kernel, the shift, the precision), so plans of the same geometry copy them
+// from a small process-wide cache instead of evaluating N Chebyshev sums in
+// double again.  Entries are kept in the library's device pool until
+// fc2_trim_device_memory drops them; at most DEC_CACHE_MAX at a time.
+struct DecKey {
+    int dev, kind, fp64, w;
+    int64_t N, M, sh;
+    double beta;
+    bool operator<(const DecKey& o) const {
+        return std::tie(dev, kind, fp64, w, N, M, sh, beta) <
+               std::tie(o.dev, o.kind, o.fp64, o.w, o.N, o.M, o.sh, o.beta);
+    }
+};
+constexpr size_t DEC_CACHE_MAX = 8;
+static std::mutex g_dec_mu;
+static std::map<DecKey, std::pair<void*, uint64_t>> g_dec_cache;  // table, last use
+static uint64_t g_dec_clock = 0;
+
+// Copy a cached table into dst (true), or return false.
+static bool dec_cache_get(const DecKey& k, void* dst, size_t bytes, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_dec_mu);
+    auto it = g_dec_cache.find(k);
+    if (it == g_dec_cache.end()) return false;
+    // finish the copy before the lock is released: an entry is only freed
+    // under the lock, so no copy from it is ever pending then
+    if (cudaMemcpyAsync(dst, it->second.first, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    it->second.second = ++g_dec_clock;
+    return true;
+}
+
+// Keep a copy of a freshly computed table (best effort: a failed allocation
+// only means no caching).
+static void dec_cache_put(const DecKey& k, const void* src, size_t bytes, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_dec_mu);
+    if (g_dec_cache.count(k)) return;
+    if (g_dec_cache.size() >= DEC_CACHE_MAX) {
+        auto old = g_dec_cache.begin();
+        for (auto it = g_dec_cache.begin(); it != g_dec_cache.end(); ++it)
+            if (it->second.second < old->second.second) old = it;
+        cudaFreeAsync(old->second.first, s);
+        g_dec_cache.erase(old);
+    }
+    void* buf = nullptr;
+    if (pool_alloc(&buf, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    if (cudaMemcpyAsync(buf, src, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(buf, s);
+        return;
+    }
+    g_dec_cache[k] = {buf, ++g_dec_clock};
+}
+
+void drop_deconv_cache(int dev) {
+    std::lock_guard<std::mutex> lk(g_dec_mu);
+    for (auto it = g_dec_cache.begin(); it != g_dec_cache.end();) {
+        if (it->first.dev == dev) {
+            cudaFreeAsync(it->second.first, (cudaStream_t)0);
+            it = g_dec_cache.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
 cudaError_t init_deconv(fc2_plan_s* p, cudaStream_t s) {
     double coef[CHEB_N];
+    int dev = 0;
+    cudaGetDevice(&dev);
     double* d_coef = (double*)p->d_red;  // scratch, consumed before any other use
     cudaError_t e;
     if (p->packed) goto packed;  // every grid is packed: only the shifted table is used
@@ -140,14 +215,19 @@ cudaError_t init_deconv(fc2_plan_s* p, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const int64_t mmax = std::max(hN, p->N - hN);
     unsigned blocks = (unsigned)((mmax + 256) / 256);
-    if (p->fp64)
-        k_init_dec<double><<<blocks, 256, 0, s>>>((double*)p->d_dec, p->N, hN, p->M, d_coef, nc,
-                                                  xi_max * xi_max);
-    else
-        k_init_dec<float><<<blocks, 256, 0, s>>>((float*)p->d_dec, p->N, hN, p->M, d_coef, nc,
-                                                 xi_max * xi_max);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    const DecKey key{dev, 0, p->fp64 ? 1 : 0, p->w, p->N, p->M, 0, p->beta};
+    const size_t bytes = (size_t)p->N * (p->fp64 ? 8 : 4);
+    if (!dec_cache_get(key, p->d_dec, bytes, s)) {
+        if (p->fp64)
+            k_init_dec<double><<<blocks, 256, 0, s>>>((double*)p->d_dec, p->N, hN, p->M, d_coef,
+                                                      nc, xi_max * xi_max);
+        else
+            k_init_dec<float><<<blocks, 256, 0, s>>>((float*)p->d_dec, p->N, hN, p->M, d_coef,
+                                                     nc, xi_max * xi_max);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        dec_cache_put(key, p->d_dec, bytes, s);
+    }
     }
 packed:
     if (p->npk > 0) {
@@ -155,14 +235,19 @@ packed:
         // share it: phihat is even)
         e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return e;
-        const double xi_p = (double)(p->sh + p->N) / (double)p->M;
-        const int ncp = cheb_fit_kernel_ft(p->w_p, p->beta_p, xi_p, coef, 1e-11);
-        e = cudaMemcpyAsync(d_coef, coef, sizeof(coef), cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) return e;
-        k_init_dec_shift<<<(unsigned)((p->N + 255) / 256), 256, 0, s>>>(
-            (float*)p->d_dec_p, p->N, p->sh, p->M, d_coef, ncp, xi_p * xi_p);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        const DecKey key{dev, 1, 0, p->w_p, p->N, p->M, p->sh, p->beta_p};
+        const size_t bytes = (size_t)p->N * 4;
+        if (!dec_cache_get(key, p->d_dec_p, bytes, s)) {
+            const double xi_p = (double)(p->sh + p->N) / (double)p->M;
+            const int ncp = cheb_fit_kernel_ft(p->w_p, p->beta_p, xi_p, coef, 1e-11);
+            e = cudaMemcpyAsync(d_coef, coef, sizeof(coef), cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) return e;
+            k_init_dec_shift<<<(unsigned)((p->N + 255) / 256), 256, 0, s>>>(
+                (float*)p->d_dec_p, p->N, p->sh, p->M, d_coef, ncp, xi_p * xi_p);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            dec_cache_put(key, p->d_dec_p, bytes, s);
+        }
     }
     // the coefficients live in reduction scratch: finish before it is reused
     return cudaStreamSynchronize(s);
