@@ -208,7 +208,8 @@ def run_gpu(args):
 
     def make_plan(prec, t=c.t, x=c.x, s=c.sigma):
         return _fc2.Plan(t, x, s, c.H, c.f_min, c.df, c.N, c.oversample, prec,
-                         stream=stream.cuda_stream, device=local, fft_kernel=args.fft_kernel)
+                         stream=stream.cuda_stream, device=local, fft_kernel=args.fft_kernel,
+                         fft_group=args.fft_group)
 
     out = torch.empty((c.H, c.N), dtype=torch.float64, device=dev)
 
@@ -274,7 +275,8 @@ def run_gpu(args):
             barrier(ws)
             t_e2e = time.perf_counter()
         p = _fc2.Plan(tp, xp, sp, c.H, c.f_min, c.df, c.N, c.oversample, "mixed",
-                      stream=stream.cuda_stream, device=local, fft_kernel=args.fft_kernel)
+                      stream=stream.cuda_stream, device=local, fft_kernel=args.fft_kernel,
+                      fft_group=args.fft_group)
         p.execute(hout, want_records=True)
         p.close()
     torch.cuda.synchronize()
@@ -342,7 +344,7 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "precision": "mixed", "n": c.n, "N": c.N, "H": c.H,
                    "oversample": c.oversample, "parallelism": f"{ws} independent curves",
                    "l2": "inputs larger than L2 (18 grids x 128 MiB)",
-                   "fft_kernel": args.fft_kernel},
+                   "fft_kernel": args.fft_kernel, "fft_group": args.fft_group},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -381,7 +383,7 @@ def run_profile(args):
     dev = torch.device("cuda", 0)
     out = torch.empty((c.H, c.N), dtype=torch.float64, device=dev)
     with _fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed",
-                   fft_kernel=args.fft_kernel) as p:
+                   fft_kernel=args.fft_kernel, fft_group=args.fft_group) as p:
         for _ in range(args.warmup + args.steps):
             _, best, _, _ = p.execute(out, want_records=True)
         torch.cuda.synchronize()
@@ -697,6 +699,8 @@ def main():
                     help="long (default, the headline) or another synthetic workload")
     ap.add_argument("--fft-kernel", default="default", choices=["default", "r64", "r16", "bulk"],
                     help="kernel family of the float transform passes")
+    ap.add_argument("--fft-group", type=int, default=0,
+                    help="grids taken through all transform passes together (0 = all)")
     ap.add_argument("--curves", type=int, default=512,
                     help="curves of a --profile run of the survey or adjoint workload")
     args = ap.parse_args()

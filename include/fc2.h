@@ -126,6 +126,11 @@ typedef struct {
                                   curves need the same n, H, f_min, df and N and the
                                   same times (checked on the device, FC2_ERR_INVALID_ARG
                                   otherwise).  0 = independent curves */
+    int fft_group;             /* when autotune is 0: the number of grids taken through all
+                                  transform passes before the next grids start (with one
+                                  or two, the data between passes largely stay in L2);
+                                  0 = library default (all grids pass by pass); values
+                                  below 0 are FC2_ERR_INVALID_ARG */
 } fc2_options;
 
 /* One selected frequency: bin index, frequency, Delta chi^2 and the

@@ -28,7 +28,8 @@ class Options(ctypes.Structure):
                 ("device", ctypes.c_int), ("inputs_on_device", ctypes.c_int),
                 ("outputs_on_device", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("fft_kernel", ctypes.c_int), ("gridding", ctypes.c_int),
-                ("detrend", ctypes.c_int), ("shared_sampling", ctypes.c_int)]
+                ("detrend", ctypes.c_int), ("shared_sampling", ctypes.c_int),
+                ("fft_group", ctypes.c_int)]
 
 # fc2_options.gridding values
 GRIDDING = {"kernel": 0, "paper": 1}
@@ -146,7 +147,8 @@ def _is_dev(a):
 
 def make_options(prec="fp64", kernel_width=0, top_k=0, alias_tau=0.0, stream=None, device=0,
                  inputs_on_device=False, outputs_on_device=False, autotune=False,
-                 fft_kernel="default", gridding="kernel", detrend=0, shared_sampling=False):
+                 fft_kernel="default", gridding="kernel", detrend=0, shared_sampling=False,
+                 fft_group=0):
     o = Options()
     load().fc2_options_default(ctypes.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -162,6 +164,7 @@ def make_options(prec="fp64", kernel_width=0, top_k=0, alias_tau=0.0, stream=Non
     o.gridding = GRIDDING[gridding] if isinstance(gridding, str) else int(gridding)
     o.detrend = int(detrend)
     o.shared_sampling = int(bool(shared_sampling))
+    o.fft_group = int(fft_group)
     return o
 
 
@@ -171,7 +174,8 @@ class Plan:
 
     def __init__(self, t, x, sigma, H, f_min, df, N, oversample=2, prec="fp64",
                  kernel_width=0, top_k=8, alias_tau=0.0, stream=None, device=0,
-                 autotune=False, fft_kernel="default", gridding="kernel", detrend=0):
+                 autotune=False, fft_kernel="default", gridding="kernel", detrend=0,
+                 fft_group=0):
         lib = load()
         dev = _is_dev(t)
         if not dev:
@@ -184,7 +188,7 @@ class Plan:
         self.f_min, self.df = float(f_min), float(df)
         self.opt = make_options(prec, kernel_width, self.top_k, alias_tau, stream, device,
                                 autotune=autotune, fft_kernel=fft_kernel, gridding=gridding,
-                                detrend=detrend, inputs_on_device=dev)
+                                detrend=detrend, fft_group=fft_group, inputs_on_device=dev)
         h = _P()
         rc = lib.fc2_plan_create(_ptr(t), _ptr(x), _ptr(sigma), self.n, self.H, self.f_min,
                                  self.df, self.N, int(oversample), ctypes.byref(self.opt),

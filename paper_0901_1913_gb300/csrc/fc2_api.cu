@@ -132,6 +132,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         return FC2_ERR_INVALID_ARG;
     if (opt.top_k < 0 || opt.top_k > 64 || opt.alias_tau < 0.0) return FC2_ERR_INVALID_ARG;
     if (opt.fft_kernel < 0 || opt.fft_kernel > 3) return FC2_ERR_INVALID_ARG;
+    if (opt.fft_group < 0) return FC2_ERR_INVALID_ARG;
     if (opt.gridding < 0 || opt.gridding > 1) return FC2_ERR_INVALID_ARG;
     if (opt.detrend < 0 || opt.detrend > 3) return FC2_ERR_INVALID_ARG;
     if (H > 8) return FC2_ERR_UNSUPPORTED;
@@ -210,6 +211,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     p->top_k = opt.top_k ? opt.top_k : 8;
     plan_fft_passes(p);
     p->fft_family = fft_family_of(opt.fft_kernel);
+    p->fft_group = opt.fft_group;
 
     const size_t tsz = p->fp64 ? 8 : 4;
     const size_t csz = 2 * tsz;

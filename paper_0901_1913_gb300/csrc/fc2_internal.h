@@ -119,6 +119,7 @@ struct fc2_plan_s {
     int64_t twst_off[16] = {0};
     int64_t tw64_off[16] = {0};
     int fft_family = fc2::FFT_R64;  // kernel family of the float passes (fc2::FftFamily)
+    int fft_group = 0;         // grids taken through all passes together (0 = all)
     double* d_dchi2 = nullptr; // [H][N]
     float* d_minpiv = nullptr; // unused slot kept for diagnostics
     int32_t* d_flag_list = nullptr;  // bins needing the exact fix-up

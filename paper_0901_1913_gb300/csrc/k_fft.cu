@@ -410,6 +410,7 @@ struct PassArgs {
     int N, hN;
     int tws;
     int npk, sh;       // packed grids (g < npk) keep modes +-(sh + j), others j - hN
+    int g0, ng;        // this launch covers grids g0 .. g0 + ng - 1
 };
 
 // Last pass: mode m of grid g goes to its place in the spectra.  Grid
@@ -454,7 +455,7 @@ __global__ void __launch_bounds__(NT, 2) k_fft_pass(const cpx<T>* __restrict__ i
     cpx<T>* st = s + phys(E - 1) + 1;
     const int M = 1 << a.logM;
     const int S = M >> LOGR;
-    const int g = blockIdx.y;
+    const int g = a.g0 + (int)blockIdx.y;
     const int j0 = blockIdx.x * J;
     const cpx<T>* gin = in + (int64_t)g * M;
     if (a.first) {
@@ -609,15 +610,16 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
         return rows;
     };
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int g = tile / tiles_x;
-        const int bx = tile - g * tiles_x;
+        const int gl = tile / tiles_x;
+        const int g = a.g0 + gl;
+        const int bx = tile - gl * tiles_x;
         const int j0 = bx * J;
         const cpx<T>* gin = in + (int64_t)g * M;
         // ask L2 for the tile this CTA handles next
         {
             const int tn = tile + gridDim.x;
             if (tn < ntiles) {
-                const int gn = tn / tiles_x, bn = tn - gn * tiles_x;
+                const int gnl = tn / tiles_x, bn = tn - gnl * tiles_x, gn = a.g0 + gnl;
                 const cpx<T>* ginn = in + (int64_t)gn * M;
                 if (!a.first) {
                     constexpr int CH = 4096;  // bytes per prefetch request
@@ -888,7 +890,7 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
     __syncthreads();
     // thread 0: copy tile t into input buffer b (four 16 KB pieces, one mbarrier)
     auto issue = [&](int t, int b) {
-        const int gt = t / tiles_x, bt = t - gt * tiles_x;
+        const int gtl = t / tiles_x, bt = t - gtl * tiles_x, gt = a.g0 + gtl;
         const cpx<T>* src = in + (int64_t)gt * M + (int64_t)bt * E;
         mbar_expect_tx(&mbar[b], (unsigned)(E * sizeof(cpx<T>)));
 #pragma unroll
@@ -907,8 +909,9 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
     int it = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         const int buf = it & 1;
-        const int g = tile / tiles_x;
-        const int bx = tile - g * tiles_x;
+        const int gl = tile / tiles_x;
+        const int g = a.g0 + gl;
+        const int bx = tile - gl * tiles_x;
         const int j0 = bx * J;
         if (bulk) {
             const bool ok = mbar_wait_bounded(&mbar[buf], (unsigned)((it >> 1) & 1));
@@ -1167,7 +1170,11 @@ struct TuneKey {
         return std::tie(dev, logM, G, fp64, packed) < std::tie(o.dev, o.logM, o.G, o.fp64, o.packed);
     }
 };
-static std::map<TuneKey, std::pair<std::vector<int>, int>> g_tuned;
+struct TuneChoice {
+    std::vector<int> rs;
+    int family, group;
+};
+static std::map<TuneKey, TuneChoice> g_tuned;
 static std::mutex g_tune_mu;
 
 cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
@@ -1178,8 +1185,9 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
-            set_passes(p, it->second.first);
-            p->fft_family = it->second.second;
+            set_passes(p, it->second.rs);
+            p->fft_family = it->second.family;
+            p->fft_group = it->second.group;
             return init_twiddles(p, s);
         }
     }
@@ -1193,28 +1201,35 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
     }
     float best = 1e30f;
     std::vector<int> best_rs = cands.front();
-    int best_fam = FFT_R64;
+    int best_fam = FFT_R64, best_grp = 0;
     cudaError_t e = cudaSuccess;
     const int fams_f32[3] = {FFT_BULK, FFT_R64, FFT_R16};
     const int nfam = p->fp64 ? 1 : 3;
+    std::vector<int> groups{0};
+    if (p->G > 1) groups.push_back(1);
+    if (p->G > 2) groups.push_back(2);
     for (const auto& rs : cands) {
-        for (int fi = 0; fi < nfam; ++fi) {
-            const int fam = p->fp64 ? FFT_R16 : fams_f32[fi];
-            set_passes(p, rs);
-            p->fft_family = fam;
-            if ((e = init_twiddles(p, s)) != cudaSuccess) break;
-            if ((e = launch_fft(p, s)) != cudaSuccess) break;  // warm-up
-            cudaEventRecord(e0, s);
-            for (int it = 0; it < 3 && e == cudaSuccess; ++it) e = launch_fft(p, s);
-            cudaEventRecord(e1, s);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            if (e != cudaSuccess) break;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) {
-                best = ms;
-                best_rs = rs;
-                best_fam = fam;
+        for (int fi = 0; fi < nfam && e == cudaSuccess; ++fi) {
+            for (int grp : groups) {
+                const int fam = p->fp64 ? FFT_R16 : fams_f32[fi];
+                set_passes(p, rs);
+                p->fft_family = fam;
+                p->fft_group = grp;
+                if ((e = init_twiddles(p, s)) != cudaSuccess) break;
+                if ((e = launch_fft(p, s)) != cudaSuccess) break;  // warm-up
+                cudaEventRecord(e0, s);
+                for (int it = 0; it < 3 && e == cudaSuccess; ++it) e = launch_fft(p, s);
+                cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) break;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    best_rs = rs;
+                    best_fam = fam;
+                    best_grp = grp;
+                }
             }
         }
         if (e != cudaSuccess) break;
@@ -1224,9 +1239,10 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     set_passes(p, best_rs);
     p->fft_family = best_fam;
+    p->fft_group = best_grp;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[key] = {best_rs, best_fam};
+        g_tuned[key] = TuneChoice{best_rs, best_fam, best_grp};
     }
     return init_twiddles(p, s);
 }
@@ -1255,7 +1271,7 @@ static cudaError_t run_pass(fc2_plan_s* p, const void* in, void* out, const Pass
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_done = true;
     }
-    dim3 grid((unsigned)(S / J), (unsigned)p->G);
+    dim3 grid((unsigned)(S / J), (unsigned)a.ng);
     kern<<<grid, NT, smem, s>>>((const cpx<T>*)in, (cpx<T>*)out, a, p->d_L,
                                 (const cpx<T>*)p->d_twlo, (const cpx<T>*)p->d_twhi,
                                 (const cpx<T>*)p->d_twst + p->twst_off[LOGR]);
@@ -1274,7 +1290,7 @@ static cudaError_t run_pass64(fc2_plan_s* p, const void* in, void* out, const Pa
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_done = true;
     }
-    const int64_t ntiles = (S >> LOGJ) * (int64_t)p->G;
+    const int64_t ntiles = (S >> LOGJ) * (int64_t)a.ng;
     static int nsm = 0;
     if (!nsm) {
         int dev = 0;
@@ -1285,7 +1301,7 @@ static cudaError_t run_pass64(fc2_plan_s* p, const void* in, void* out, const Pa
     const unsigned blocks = (unsigned)std::min<int64_t>(ntiles, (int64_t)nsm);
     kern<<<blocks, P64_NT, smem, s>>>((const cpx<float>*)in, (cpx<float>*)out, a, p->d_L,
                                    (const cpx<float>*)p->d_twlo, (const cpx<float>*)p->d_twhi,
-                                   (const cpx<float>*)p->d_twst + p->tw64_off[LOGR], p->G);
+                                   (const cpx<float>*)p->d_twst + p->tw64_off[LOGR], a.ng);
     return cudaGetLastError();
 }
 
@@ -1303,7 +1319,7 @@ static cudaError_t run_pass_tma(fc2_plan_s* p, const void* in, void* out, const 
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
-    const int64_t ntiles = (S >> LOGJ) * (int64_t)p->G;
+    const int64_t ntiles = (S >> LOGJ) * (int64_t)a.ng;
     static int nsm = 0;
     if (!nsm) {
         int dev = 0;
@@ -1314,7 +1330,7 @@ static cudaError_t run_pass_tma(fc2_plan_s* p, const void* in, void* out, const 
     const unsigned blocks = (unsigned)std::min<int64_t>(ntiles, (int64_t)nsm);
     kern<<<blocks, PT_NT, smem, s>>>((const cpx<float>*)in, (cpx<float>*)out, a, p->d_L,
                                      (const cpx<float>*)p->d_twlo, (const cpx<float>*)p->d_twhi,
-                                     (const cpx<float>*)p->d_twst + p->twst_off[LOGR], p->G,
+                                     (const cpx<float>*)p->d_twst + p->twst_off[LOGR], a.ng,
                                      p->d_status);
     return cudaGetLastError();
 }
@@ -1341,42 +1357,50 @@ static cudaError_t run_radix(fc2_plan_s* p, const void* in, void* out, const Pas
 
 template <typename T>
 static cudaError_t fft_impl(fc2_plan_s* p, cudaStream_t s) {
-    int src = 0;
+    // Grids go through all passes a group at a time (p->fft_group grids per
+    // group, 0 = all at once): with one or two grids per group the
+    // intermediate between passes largely stays in L2.
     const int P = (int)p->passes.size();
-    for (int i = 0; i < P; ++i) {
-        const FftPass& ps = p->passes[i];
-        PassArgs a;
-        a.logM = p->logM;
-        a.logNs = 0;
-        while ((1ll << a.logNs) < ps.Ns) ++a.logNs;
-        a.first = (i == 0);
-        a.last = (i == P - 1);
-        a.logRn = a.last ? 0 : p->passes[i + 1].logR;
-        a.logJn = a.last ? 0 : logj_of<T>(p, p->passes[i + 1].logR);
-        // the paper's gridding keeps every mode: mode m at spec[M/2 + m]
-        a.N = p->paper ? (int)p->M : (int)p->N;
-        a.hN = p->paper ? (int)(p->M / 2) : (int)(p->N / 2);
-        a.tws = p->tw_shift;
-        a.npk = p->paper ? 0 : p->npk;
-        a.sh = (int)p->sh;
-        const void* in = p->d_grid[src];
-        void* out = a.last ? p->d_spec : p->d_grid[1 - src];
-        cudaError_t e;
-        switch (ps.logR) {
-            case 8: e = run_radix<T, 8>(p, in, out, a, s); break;
-            case 9: e = run_radix<T, 9>(p, in, out, a, s); break;
-            case 10: e = run_radix<T, 10>(p, in, out, a, s); break;
-            case 11: e = run_radix<T, 11>(p, in, out, a, s); break;
-            case 12:
-                if constexpr (sizeof(T) == 4) { e = run_radix<T, 12>(p, in, out, a, s); break; }
-                return cudaErrorInvalidValue;
-            case 7: e = run_radix<T, 7>(p, in, out, a, s); break;
-            case 6: e = run_radix<T, 6>(p, in, out, a, s); break;
-            case 5: e = run_radix<T, 5>(p, in, out, a, s); break;
-            default: return cudaErrorInvalidValue;
+    const int grp = (p->fft_group > 0) ? std::min(p->fft_group, p->G) : p->G;
+    for (int g0 = 0; g0 < p->G; g0 += grp) {
+        int src = 0;
+        for (int i = 0; i < P; ++i) {
+            const FftPass& ps = p->passes[i];
+            PassArgs a;
+            a.logM = p->logM;
+            a.logNs = 0;
+            while ((1ll << a.logNs) < ps.Ns) ++a.logNs;
+            a.first = (i == 0);
+            a.last = (i == P - 1);
+            a.logRn = a.last ? 0 : p->passes[i + 1].logR;
+            a.logJn = a.last ? 0 : logj_of<T>(p, p->passes[i + 1].logR);
+            // the paper's gridding keeps every mode: mode m at spec[M/2 + m]
+            a.N = p->paper ? (int)p->M : (int)p->N;
+            a.hN = p->paper ? (int)(p->M / 2) : (int)(p->N / 2);
+            a.tws = p->tw_shift;
+            a.npk = p->paper ? 0 : p->npk;
+            a.sh = (int)p->sh;
+            a.g0 = g0;
+            a.ng = std::min(grp, p->G - g0);
+            const void* in = p->d_grid[src];
+            void* out = a.last ? p->d_spec : p->d_grid[1 - src];
+            cudaError_t e;
+            switch (ps.logR) {
+                case 8: e = run_radix<T, 8>(p, in, out, a, s); break;
+                case 9: e = run_radix<T, 9>(p, in, out, a, s); break;
+                case 10: e = run_radix<T, 10>(p, in, out, a, s); break;
+                case 11: e = run_radix<T, 11>(p, in, out, a, s); break;
+                case 12:
+                    if constexpr (sizeof(T) == 4) { e = run_radix<T, 12>(p, in, out, a, s); break; }
+                    return cudaErrorInvalidValue;
+                case 7: e = run_radix<T, 7>(p, in, out, a, s); break;
+                case 6: e = run_radix<T, 6>(p, in, out, a, s); break;
+                case 5: e = run_radix<T, 5>(p, in, out, a, s); break;
+                default: return cudaErrorInvalidValue;
+            }
+            if (e != cudaSuccess) return e;
+            src = 1 - src;
         }
-        if (e != cudaSuccess) return e;
-        src = 1 - src;
     }
     return cudaSuccess;
 }
