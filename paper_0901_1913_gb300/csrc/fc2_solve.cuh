@@ -40,6 +40,11 @@ struct Sys {
     }
 };
 
+// 1 / sqrt(d): one reciprocal square root in float (its rounding is far
+// inside the float solve's error budget), the exact quotient in double.
+FC2_D float inv_sqrt(float d) { return rsqrtf(d); }
+FC2_D double inv_sqrt(double d) { return 1.0 / sqrt(d); }
+
 // Factor and solve; out[H'-1] = Delta chi^2'_{H'}.  Returns the minimum
 // relative pivot over all columns (clamped at 0).  With COEF, *anorm2 receives
 // max over H' of |A^{(H')}|^2 (A^{(H')} = the H'-harmonic coefficients, by
@@ -68,17 +73,20 @@ FC2_D TC chol_solve(const Sys<TC, H>& S, TC tau, TC* out, TC* anorm2,
         TC b = S.beta(l);
 #pragma unroll
         for (int p = 0; p < l; ++p) b = fma(-L[l][p], z[p], b);
-        const TC ratio = (all > (TC)0) ? d / all : (TC)0;
-        if (ratio > tau) {
-            const TC sq = sqrt(d);
-            L[l][l] = sq;
-            dinv[l] = (TC)1 / sq;
-            z[l] = b * dinv[l];
+        // keep the column when its relative pivot d / alpha_ll exceeds tau; the
+        // quotient itself only feeds the returned minimum (and is dropped by
+        // the compiler when a caller ignores it)
+        if (all > (TC)0 && d > tau * all) {
+            const TC di = inv_sqrt(d);
+            L[l][l] = d * di;
+            dinv[l] = di;
+            z[l] = b * di;
         } else {
             L[l][l] = (TC)0;
             dinv[l] = (TC)0;
             z[l] = (TC)0;
         }
+        const TC ratio = (all > (TC)0) ? d / all : (TC)0;
         const TC rc = ratio > (TC)0 ? ratio : (TC)0;
         dmin = rc < dmin ? rc : dmin;
         if (l > 0) acc = fma(z[l], z[l], acc);
