@@ -426,7 +426,6 @@ __global__ void __launch_bounds__(RS_NT) k_rs_scatter(const uint64_t* __restrict
     constexpr int NW = RS_NT / 32;
     constexpr int PER_W = RS_TILE / NW;
     __shared__ uint32_t cnt[NW][256];
-    __shared__ uint32_t off[256];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     for (int d = threadIdx.x; d < NW * 256; d += RS_NT) (&cnt[0][0])[d] = 0;
     __syncthreads();
@@ -444,7 +443,6 @@ __global__ void __launch_bounds__(RS_NT) k_rs_scatter(const uint64_t* __restrict
     {
         int d = threadIdx.x;  // RS_NT == 256 digits
         uint32_t run = hist[(int64_t)d * nblk + blockIdx.x];
-        off[d] = run;
         for (int q = 0; q < NW; ++q) {
             uint32_t v = cnt[q][d];
             cnt[q][d] = run;
