@@ -464,7 +464,7 @@ static fc2_status run_pipeline(fc2_plan_s* p) {
     rec(p, 5);
     const int64_t cap = p->exact_cap;
     const int64_t r1 = (nfix + cap - 1) / cap;
-    p->launches = launches_front(p) + 6 * r1 + 4;
+    p->launches = launches_front(p) + 6 * r1 + 6;  // fix-up rounds: 3 tiers x 2; peaks: 4 + records 2
     return map_err(g.e);
 }
 
