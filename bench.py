@@ -171,7 +171,7 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_0901_1913_gb300 import synth
-    c = synth.config2(seed=2)
+    c = synth.long_curve(seed=2)
     threads = os.cpu_count() or 1
     per_step = max(threads, args.ref_bins)
     rng = np.random.default_rng(7)
@@ -202,7 +202,7 @@ def run_gpu(args):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    c = synth.config2(seed=2 + rank)
+    c = synth.long_curve(seed=2 + rank)
     stream = torch.cuda.Stream(device=dev)
     evals = c.N * c.H
 
@@ -370,7 +370,7 @@ def run_profile(args):
     import torch
     from paper_0901_1913_gb300 import _fc2, synth
     if args.workload in ("survey", "adjoint"):
-        b = synth.config3(C=args.curves) if args.workload == "survey" else synth.config4(C=args.curves)
+        b = synth.survey_batch(C=args.curves) if args.workload == "survey" else synth.adjoint_batch(C=args.curves)
         for _ in range(args.warmup + args.steps):
             _, _, stats = _fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df,
                                                b.N, b.oversample, "mixed", top_k=8,
@@ -379,7 +379,7 @@ def run_profile(args):
         print(json.dumps({"profile_run": True, "workload": args.workload, "curves": b.C,
                           "stats": stats}), flush=True)
         return
-    c = synth.config2(seed=2, H=args.H or 6)
+    c = synth.long_curve(seed=2, H=args.H or 6)
     dev = torch.device("cuda", 0)
     out = torch.empty((c.H, c.N), dtype=torch.float64, device=dev)
     with _fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed",
@@ -434,7 +434,7 @@ def run_paper_gridding(args, line, threads):
     from paper_0901_1913_gb300 import _fc2, synth
     from tests.parity import compare, sample_bins
     from oracle import oracle, paper_method
-    c = synth.config2()
+    c = synth.long_curve()
     evals = c.N * c.H
     res = {}
     for prec in ("mixed", "fp64"):
@@ -583,7 +583,7 @@ def run_workload(args):
         run_shared_field(args, line, threads)
         return
     if args.workload in ("short", "large"):
-        c = synth.config1() if args.workload == "short" else synth.config5()
+        c = synth.short_curve() if args.workload == "short" else synth.large_curve()
         evals = c.N * c.H
         res = {}
         for prec in ("mixed", "fp64"):
@@ -622,7 +622,7 @@ def run_workload(args):
                             "near_alias_bins": rm["n_near_alias"], "ok": bool(rm["ok"] and r6["ok"])})
         line["config"].update(n=c.n, N=c.N, H=c.H, oversample=c.oversample)
     else:
-        b = synth.config3() if args.workload == "survey" else synth.config4()
+        b = synth.survey_batch() if args.workload == "survey" else synth.adjoint_batch()
         evals = int(np.sum(b.H.astype(np.int64) * b.N))
         dev = torch.device("cuda", 0)
         td, xd, sd = (torch.from_numpy(v).to(dev) for v in (b.t, b.x, b.sigma))

@@ -106,7 +106,7 @@ def gaussian_pulse(t, f0, amp, duty=0.1, phase0=0.0):
 # "reading" and listed with the input recipe in the design notes.
 # ----------------------------------------------------------------------------
 
-def config1(seed: int = 0, n: int = 1000, N: int = 16384) -> Curve:
+def short_curve(seed: int = 0, n: int = 1000, N: int = 16384) -> Curve:
     """Single short curve: 1000 samples over 100 d minus two 10 d gaps, three
     harmonics of 1.37 /d, H = 3, N trial frequencies on [0.01, 10] /d."""
     rng = _rng(seed)
@@ -130,7 +130,7 @@ def config1(seed: int = 0, n: int = 1000, N: int = 16384) -> Curve:
                  dict(f0=f0, amps=amps, phases=tuple(phases)))
 
 
-def config2(seed: int = 2, n: int = 100_000, N: int = 1 << 22, T: float = 3000.0,
+def long_curve(seed: int = 2, n: int = 100_000, N: int = 1 << 22, T: float = 3000.0,
             f_max: float = 20.0, H: int = 6, oversample: int = 4) -> Curve:
     """Single long curve: seasonal (6 months on/off) nightly sampling over
     3000 d, 8-harmonic sawtooth at f0 = 0.7312 /d (reading) with
@@ -165,7 +165,7 @@ def _survey_curve(rng, n, T, H, f0, shape, snr, null):
     return t, x, sigma
 
 
-def config3(seed: int = 3, C: int = 4096, N: int = 1 << 18, T: float = 1000.0,
+def survey_batch(seed: int = 3, C: int = 4096, N: int = 1 << 18, T: float = 1000.0,
             f_max: float = 12.0, n_median: float = 2000.0, n_lo: int = 50,
             n_hi: int = 20000) -> Batch:
     """Batched survey: C curves, n_c ~ lognormal(median 2000, s = 1.0 reading)
@@ -237,7 +237,7 @@ def shared_field(seed: int = 6, C: int = 1024, n: int = 2000, N: int = 1 << 18,
                  np.full(C, N, dtype=np.int64), 2, truth)
 
 
-def config4(seed: int = 4, C: int = 1024, n: int = 2000, N: int = 1 << 16,
+def adjoint_batch(seed: int = 4, C: int = 1024, n: int = 2000, N: int = 1 << 16,
             T: float = 500.0, f_max: float = 12.0, H: int = 4) -> Batch:
     """Differentiation batch: C curves of n = 2000 samples over a seasonal
     500 d (reading), H = 4, N = 2^16, signals as the non-null survey curves."""
@@ -258,7 +258,7 @@ def config4(seed: int = 4, C: int = 1024, n: int = 2000, N: int = 1 << 16,
                  np.full(C, N, dtype=np.int64), 2, truth)
 
 
-def config5(seed: int = 5, cadence_min: float = 2.0, years: float = 4.0,
+def large_curve(seed: int = 5, cadence_min: float = 2.0, years: float = 4.0,
             N: int = 1 << 26, f_max: float = 24.0, H: int = 8,
             dropout: float = 0.05, oversample: int = 2) -> Curve:
     """Large single curve: regular cadence (2 min by default, reading; 30 min

@@ -17,7 +17,7 @@ def fc2():
 
 
 def test_backward_matches_oracle_and_fd(fc2, oracle_mod):
-    c = synth.config1(n=600, N=8192)
+    c = synth.short_curve(n=600, N=8192)
     with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, 2, "mixed", top_k=4) as p:
         _, best, peaks, chi0 = p.execute()
         js = np.array([q["j"] for q in peaks])
@@ -54,7 +54,7 @@ def test_backward_matches_oracle_and_fd(fc2, oracle_mod):
 
 
 def test_backward_unsorted_input_caller_order(fc2, oracle_mod):
-    c = synth.config1(n=300, N=4096)
+    c = synth.short_curve(n=300, N=4096)
     perm = np.random.default_rng(2).permutation(c.n)
     t, x, s = c.t[perm], c.x[perm], c.sigma[perm]
     with fc2.Plan(t, x, s, c.H, c.f_min, c.df, c.N, 2, "fp64", top_k=2) as p:
@@ -67,7 +67,7 @@ def test_backward_unsorted_input_caller_order(fc2, oracle_mod):
 
 
 def test_backward_batched(fc2, oracle_mod):
-    b = synth.config4(C=12, n=400, N=1 << 16)
+    b = synth.adjoint_batch(C=12, n=400, N=1 << 16)
     out, peaks, _ = fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df, b.N,
                                         2, "mixed", top_k=3)
     pj = np.array([[q["j"] for q in pk] for pk in peaks])
@@ -93,7 +93,7 @@ def test_backward_batched(fc2, oracle_mod):
 
 def test_autograd_function(fc2):
     import torch
-    c = synth.config1(n=200, N=2048)
+    c = synth.short_curve(n=200, N=2048)
     F = fc2.peaks_function()
     x = torch.tensor(c.x, dtype=torch.float64, requires_grad=True)
     s = torch.tensor(c.sigma, dtype=torch.float64, requires_grad=True)

@@ -17,7 +17,7 @@ def fc2():
 
 
 def small_survey(C=24, N=1 << 13, seed=3):
-    return synth.config3(seed=seed, C=C, N=N, n_median=600.0, n_hi=3000)
+    return synth.survey_batch(seed=seed, C=C, N=N, n_median=600.0, n_hi=3000)
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])

@@ -18,7 +18,7 @@ def fc2():
 
 
 def trended_curve():
-    c = synth.config2(n=6000, N=1 << 15)
+    c = synth.long_curve(n=6000, N=1 << 15)
     u = (c.t - c.t.mean()) / np.ptp(c.t)
     x = c.x + 3.0 * np.median(c.sigma) * (1.0 + 2.0 * u - 4.0 * u ** 2 + 5.0 * u ** 3)
     return c, x

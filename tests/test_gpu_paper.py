@@ -30,7 +30,7 @@ def paper_M(H, f_min, df, N):
 
 @pytest.mark.parametrize("prec,tol", [("mixed", 5e-6), ("fp64", 1e-10)])
 def test_paper_gridding_matches_oracle_on_snapped_times(fc2, oracle_mod, prec, tol):
-    c = synth.config2(n=3000, N=1 << 14)
+    c = synth.long_curve(n=3000, N=1 << 14)
     with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, prec,
                   gridding="paper") as p:
         d, best, _, chi0 = p.execute()
@@ -80,7 +80,7 @@ def test_paper_gridding_with_a_wrapping_fold(fc2, oracle_mod):
 
 
 def test_paper_gridding_needs_an_integer_offset(fc2):
-    c = synth.config1(n=200, N=1024)  # f_min = 0.01 is not a whole number of df steps
+    c = synth.short_curve(n=200, N=1024)  # f_min = 0.01 is not a whole number of df steps
     with pytest.raises(fc2.Fc2Error) as e:
         fc2.periodogram(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, 2, "mixed",
                         gridding="paper")

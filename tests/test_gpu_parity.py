@@ -19,7 +19,7 @@ def fc2():
 def test_spectra_match_direct_sums(fc2, oracle_mod, prec, tol):
     """P(k f_j), Q(k f_j) from spread + FFT + deconvolution equal the direct
     sums of Eq. eqPQ (relative to sum |c_i|)."""
-    c = synth.config1(n=700, N=4096)
+    c = synth.short_curve(n=700, N=4096)
     with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, 2, prec) as p:
         p.execute()
         spec = p.spectra()
@@ -41,7 +41,7 @@ def test_packed_spectra_match_direct_sums(fc2, oracle_mod):
     """With f_min a whole number of df steps and 4x grids, the mixed path packs
     Q_k + i P_k into one transform; the unpacked spectra still equal the direct
     sums of Eq. eqPQ."""
-    c = synth.config2(n=3000, N=1 << 14)
+    c = synth.long_curve(n=3000, N=1 << 14)
     assert abs(c.f_min / c.df - round(c.f_min / c.df)) < 1e-12 and c.oversample == 4
     with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed") as p:
         p.execute()
@@ -67,7 +67,7 @@ def test_fft_kernel_families_match_direct_sums(fc2, oracle_mod, fft_kernel, fft_
     """Every float transform kernel family, on pass plans (8, 8), (11, 10) and
     (12, 12) with packed grids and (10, 10) with unpacked ones, gives spectra
     equal to the direct sums of Eq. eqPQ."""
-    c = synth.config2(n=3000, N=1 << logN)
+    c = synth.long_curve(n=3000, N=1 << logN)
     with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, oversample, "mixed",
                   fft_kernel=fft_kernel, fft_group=fft_group) as p:
         p.execute()
@@ -90,8 +90,8 @@ def test_fft_kernel_families_match_direct_sums(fc2, oracle_mod, fft_kernel, fft_
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_config1_full_periodogram(fc2, oracle_mod, prec):
-    c = synth.config1()
+def test_short_curve_full_periodogram(fc2, oracle_mod, prec):
+    c = synth.short_curve()
     d, best, peaks, chi0 = fc2.periodogram(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, 2, prec)
     ref, piv = oracle_mod.periodogram(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, with_pivots=True)
     _, _, chi0_or, _ = oracle_mod.moments(c.x, c.sigma)
@@ -110,7 +110,7 @@ def test_config1_full_periodogram(fc2, oracle_mod, prec):
 
 
 def test_peaks_are_oracle_local_maxima(fc2, oracle_mod):
-    c = synth.config1()
+    c = synth.short_curve()
     d, best, peaks, chi0 = fc2.periodogram(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, 2, "fp64")
     row = d[c.H - 1]
     js = [p["j"] for p in peaks]
@@ -132,7 +132,7 @@ def test_peaks_are_oracle_local_maxima(fc2, oracle_mod):
 def test_long_curve_scaled(fc2, oracle_mod, prec):
     """Seasonal/nightly sampling of the long-curve workload, scaled to 8000
     samples and 2^16 bins, 4x oversampled grids."""
-    c = synth.config2(n=8000, N=1 << 16, T=3000.0)
+    c = synth.long_curve(n=8000, N=1 << 16, T=3000.0)
     d, best, peaks, chi0 = fc2.periodogram(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N,
                                            c.oversample, prec)
     f0 = c.truth["f0"]
@@ -158,7 +158,7 @@ def test_wrapping_fold(fc2, oracle_mod):
 
 
 def test_unsorted_input_and_determinism(fc2):
-    c = synth.config1(n=500, N=2048)
+    c = synth.short_curve(n=500, N=2048)
     p = np.random.default_rng(0).permutation(c.n)
     a = fc2.periodogram(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, 2, "mixed")[0]
     b = fc2.periodogram(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, 2, "mixed")[0]
@@ -168,7 +168,7 @@ def test_unsorted_input_and_determinism(fc2):
 
 
 def test_device_side_validation(fc2):
-    c = synth.config1(n=64, N=256)
+    c = synth.short_curve(n=64, N=256)
     s = c.sigma.copy()
     s[5] = 0.0
     with pytest.raises(fc2.Fc2Error) as e:
@@ -184,7 +184,7 @@ def test_device_side_validation(fc2):
 def test_three_pass_transform(fc2, oracle_mod, prec, N, os_):
     """Grids long enough for three FFT passes (the middle pass writes the
     blocked layout of a non-final pass); sampled bins against the oracle."""
-    c = synth.config2(n=3000, N=N, T=3000.0)
+    c = synth.long_curve(n=3000, N=N, T=3000.0)
     d, best, peaks, chi0 = fc2.periodogram(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, os_, prec)
     jf0 = int(round((c.truth["f0"] - c.f_min) / c.df))
     bins = sample_bins(c.N, 300, 9, windows=[jf0, best[-1]["j"], c.N - 1], half=16)
@@ -196,7 +196,7 @@ def test_three_pass_transform(fc2, oracle_mod, prec, N, os_):
 def test_autotuned_plan_matches_fixed_plan(fc2):
     """The autotuner only changes the transform's pass plan and kernel family:
     results agree with the fixed plan up to float rounding."""
-    c = synth.config2(n=20000, N=1 << 18)
+    c = synth.long_curve(n=20000, N=1 << 18)
     out = []
     for tune in (False, True, True):  # the second tuned plan reuses the cached choice
         with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed",
@@ -212,7 +212,7 @@ def test_autotuned_plan_matches_fixed_plan(fc2):
 def test_pool_reuse_and_trim(fc2):
     """Plans created one after another reuse the library's device pool and give
     identical results; trimming the pool between plans changes nothing."""
-    c = synth.config1(n=500, N=4096)
+    c = synth.short_curve(n=500, N=4096)
     outs = []
     for it in range(3):
         with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, 2, "mixed") as p:

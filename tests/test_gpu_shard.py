@@ -18,7 +18,7 @@ def fc2():
 
 @pytest.mark.parametrize("world", [2, 3])
 def test_bands_match_unsharded(fc2, world):
-    c = synth.config2(n=20000, N=1 << 16)
+    c = synth.long_curve(n=20000, N=1 << 16)
     K = 8
     with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed",
                   top_k=K) as p:

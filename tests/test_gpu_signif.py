@@ -19,7 +19,7 @@ def fc2():
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_significance_matches_oracle_formula(fc2, oracle_mod, prec):
     import torch
-    c = synth.config1()
+    c = synth.short_curve()
     with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, 2, prec) as p:
         with pytest.raises(fc2.Fc2Error) as e:
             p.significance()  # no execute yet
@@ -46,7 +46,7 @@ def test_significance_on_the_long_curve_sample(fc2, oracle_mod):
     """Scaled long-curve workload (seasonal, nightly): ln p on sampled bins from
     the oracle's own Delta chi^2 agrees to the Delta chi^2 tolerance."""
     from tests.parity import NEAR_ALIAS, TOL, sample_bins
-    c = synth.config2(n=8000, N=1 << 16)
+    c = synth.long_curve(n=8000, N=1 << 16)
     with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed") as p:
         d, best, _, chi0 = p.execute()
         lp, jmin, lpmin, adj = p.significance(log_p=True)

@@ -18,7 +18,7 @@ def fc2():
 
 @pytest.fixture(scope="module")
 def case(oracle_mod):
-    c = synth.config2(n=20000, N=1 << 18)
+    c = synth.long_curve(n=20000, N=1 << 18)
     # half-integer cycles per day: the daily and yearly window peaks make the
     # normal equations of those bins nearly singular
     centres = [int(round((0.5 * m - c.f_min) / c.df)) for m in range(1, 12)]
@@ -62,7 +62,7 @@ def test_pipeline_on_degenerate_bins(fc2, oracle_mod, prec):
     """The whole pipeline (gridded solve, routing, every fix-up tier) on the
     bins that need the most precision: periods longer than the span (f near 0)
     and the daily aliases, against the oracle."""
-    c = synth.config2(n=20000, N=1 << 18)
+    c = synth.long_curve(n=20000, N=1 << 18)
     one = int(round((1.0 - c.f_min) / c.df))
     bins = np.unique(np.concatenate([np.arange(0, 96), np.arange(one - 40, one + 41),
                                      np.arange(2 * one - 20, 2 * one + 21)]))

@@ -185,7 +185,7 @@ def gls_power(t, y, sigma, f):
 
 
 def test_h1_equals_generalised_lomb_scargle(oracle_mod):
-    c = synth.config1(n=300, N=512)
+    c = synth.short_curve(n=300, N=512)
     freqs = np.linspace(0.05, 5.0, 41)
     got = oracle_mod.dchi2_freqs(c.t, c.x, c.sigma, 1, freqs)[:, 0]
     _, _, chi0, _ = oracle_mod.moments(c.x, c.sigma)
@@ -324,7 +324,7 @@ def test_gradients_match_central_differences(oracle_mod):
 
 
 def test_brent_refine_finds_the_peak(oracle_mod):
-    c = synth.config1(n=400, N=4096)
+    c = synth.short_curve(n=400, N=4096)
     H = 3
     f0 = 1.37
     a, b = f0 - 0.004, f0 + 0.004

@@ -78,7 +78,7 @@ def _rank_main(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         from oracle import oracle
-        c = synth.config1(n=160, N=96)
+        c = synth.short_curve(n=160, N=96)
         K = 4
 
         class OraclePlan:
@@ -133,7 +133,7 @@ def test_two_rank_band_merge_equals_unsharded():
 
 
 def test_curve_shards_cover_the_batch_once():
-    b = synth.config3(seed=3, C=40, N=1 << 10, n_median=300.0, n_hi=1000)
+    b = synth.survey_batch(seed=3, C=40, N=1 << 10, n_median=300.0, n_hi=1000)
     seen = []
 
     def fake_execute(off, t, x, s, H, fm, df, N, **kw):

@@ -27,7 +27,7 @@ def test_noalloc_matches_execute_twice():
         ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
     lib.fc2_dchi2_exact_noalloc.restype = ctypes.c_int
 
-    c = synth.config1()
+    c = synth.short_curve()
     d_ref, best, _, chi0 = _fc2.periodogram(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, 2, "fp64")
     rng = np.random.default_rng(4)
     bins = np.unique(np.concatenate([[b["j"] for b in best],
