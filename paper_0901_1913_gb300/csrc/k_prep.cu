@@ -779,13 +779,31 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
         const int32_t* kg = key + so;
         const T* dg = dlt + so;
         const cpx<T>* cg = cs + so;
-        if (threadIdx.x < 3) {
-            // ranges of keys (shifted by -M, 0, +M) whose windows meet the tile
-            int64_t sh = (threadIdx.x == 0) ? M : (threadIdx.x == 1 ? 0 : -M);
-            int64_t lo = lower_bound_key(kg, n, a - w + 1 + sh);
-            int64_t hi = lower_bound_key(kg, n, a + TILE + sh);
-            rng[2 * threadIdx.x] = lo;
-            rng[2 * threadIdx.x + 1] = hi;
+        if (threadIdx.x < 32) {
+            // ranges of keys (shifted by -M, 0, +M) whose windows meet the tile:
+            // six lower bounds at once, five lanes each; every round five probes
+            // split a group's interval [lo, hi) into six and one ballot keeps
+            // the part that holds the bound (log_6 n rounds of one load each)
+            const int lane = threadIdx.x, grp = lane / 5, sub = lane % 5;
+            const int q = grp < 6 ? grp : 5;
+            const int64_t shv = (q >> 1) == 0 ? M : ((q >> 1) == 1 ? 0 : -M);
+            const int64_t v = (q & 1) ? a + TILE + shv : a - w + 1 + shv;
+            int64_t lo = 0, hi = n;
+            while (__any_sync(0xffffffffu, grp < 6 && lo < hi)) {
+                const bool act = grp < 6 && lo < hi;
+                const int64_t len = hi - lo;
+                const int64_t pr = lo + (len * (sub + 1)) / 6;
+                const bool less = act && (int64_t)kg[pr] < v;
+                const unsigned m = __ballot_sync(0xffffffffu, less);
+                const int c = __popc((m >> (5 * q)) & 31u);
+                if (act) {
+                    const int64_t nlo = (c == 0) ? lo : lo + (len * c) / 6 + 1;
+                    const int64_t nhi = (c == 5) ? hi : lo + (len * (c + 1)) / 6;
+                    lo = nlo;
+                    hi = nhi;
+                }
+            }
+            if (grp < 6 && sub == 0) rng[grp] = lo;
         }
         __syncthreads();
         const int64_t c0 = rng[1] - rng[0], c1 = rng[3] - rng[2], c2 = rng[5] - rng[4];
