@@ -59,11 +59,16 @@ def barrier(ws):
         dist.barrier()
 
 
-def allreduce_max(ws, v, device=None):
+def allreduce_max(ws, v):
+    """Max over ranks; NCCL needs the value on this rank's GPU, gloo on the host."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
+    if dist.get_backend() == "nccl":
+        device = torch.device("cuda", torch.cuda.current_device())
+    else:
+        device = None
     t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
@@ -245,8 +250,7 @@ def run_gpu(args):
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     ms, stage_ms, nlaunch, fft_bytes, clocks = timed(pm, args.steps, args.warmup, sampler)
     counts = pm.counts
-    ms_max = allreduce_max(ws, ms, dev if torch.distributed.is_initialized() and
-                           torch.distributed.get_backend() == "nccl" else None) if ws > 1 else ms
+    ms_max = allreduce_max(ws, ms)
     ms_step = ms_max / args.steps
     value = ws * evals / (ms_step / 1e3)
     dm = out.cpu().numpy()
@@ -257,8 +261,7 @@ def run_gpu(args):
     pf = make_plan("fp64")
     f_steps = max(2, min(args.steps, args.fp64_steps))
     ms64, stage64, _, fft_bytes64, _ = timed(pf, f_steps, max(1, min(args.warmup, 2)))
-    ms64_max = allreduce_max(ws, ms64, dev if ws > 1 and torch.distributed.get_backend() == "nccl"
-                             else None) if ws > 1 else ms64
+    ms64_max = allreduce_max(ws, ms64)
     d64 = out.cpu().numpy()
     pf.close()
     value64 = ws * evals / (ms64_max / f_steps / 1e3)
@@ -281,7 +284,7 @@ def run_gpu(args):
         p.close()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t_e2e) / e2e_steps
-    e2e_s = allreduce_max(ws, e2e_s) if ws > 1 else e2e_s
+    e2e_s = allreduce_max(ws, e2e_s)
     rec_bytes = (c.H + 8) * _fc2.ctypes.sizeof(_fc2.Best) + 8
     e2e = {"value": ws * evals / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(3 * c.n * 8), "d2h_bytes_per_step": int(c.H * c.N * 8 + rec_bytes),
