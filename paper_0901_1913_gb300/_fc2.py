@@ -49,6 +49,39 @@ class Best(ctypes.Structure):
                     flags=int(self.flags), A=np.array(self.A[:m]))
 
 
+# the same record as a numpy structured type (fields in fc2_best order)
+BEST_DTYPE = np.dtype([("j", "<i8"), ("f", "<f8"), ("dchi2", "<f8"), ("H", "<i4"),
+                       ("flags", "<i4"), ("A", "<f8", (2 * MAX_H + 1,))])
+assert BEST_DTYPE.itemsize == ctypes.sizeof(Best)
+
+
+def _rec_dict(r):
+    m = 2 * int(r["H"]) + 1
+    return dict(j=int(r["j"]), f=float(r["f"]), dchi2=float(r["dchi2"]), H=int(r["H"]),
+                flags=int(r["flags"]), A=np.array(r["A"][:m]))
+
+
+class BatchPeaks:
+    """Peak records of a batched call.  ``peaks[c]`` is curve c's list of K
+    records as dicts (made when accessed; keys as ``Best.as_dict``);
+    ``records`` is the structured array [C, K] of ``BEST_DTYPE``."""
+
+    def __init__(self, records):
+        self.records = records
+
+    def __len__(self):
+        return self.records.shape[0]
+
+    def __getitem__(self, c):
+        if isinstance(c, slice):
+            return [self[i] for i in range(*c.indices(len(self)))]
+        return [_rec_dict(r) for r in self.records[c]]
+
+    def __iter__(self):
+        for c in range(len(self)):
+            yield self[c]
+
+
 class Fc2Error(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -314,8 +347,8 @@ def execute_batched(offsets, t, x, sigma, H, f_min, df, N, oversample=2, prec="m
     """Many curves in one call (fc2_execute_batched).  offsets [C+1], t/x/sigma
     concatenated (numpy host arrays, or CUDA tensors -> read in place); H, f_min,
     df, N per curve.  dchi2: optional preallocated float32 output (numpy or
-    CUDA tensor) of sum_c H_c N_c elements.  Returns (dchi2, peaks [C][top_k]
-    as dicts, stats dict)."""
+    CUDA tensor) of sum_c H_c N_c elements.  Returns (dchi2, peaks, stats dict);
+    peaks[c][r] is record r of curve c as a dict (``BatchPeaks``)."""
     lib = load()
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
     C = offsets.size - 1
@@ -332,18 +365,17 @@ def execute_batched(offsets, t, x, sigma, H, f_min, df, N, oversample=2, prec="m
     if dchi2 is None:
         dchi2 = np.empty(total, dtype=np.float32)
     K = int(top_k or 8)
-    peaks = (Best * (C * K))()
+    peaks = np.zeros((C, K), dtype=BEST_DTYPE)
     opt = make_options(prec, kernel_width, K, 0.0, stream, device, inputs_on_device=dev,
                        autotune=autotune, fft_kernel=fft_kernel, shared_sampling=shared_sampling)
     rc = lib.fc2_execute_batched(C, offsets.ctypes.data, _ptr(t), _ptr(x), _ptr(sigma),
                                  H.ctypes.data, f_min.ctypes.data, df.ctypes.data, N.ctypes.data,
                                  int(oversample), ctypes.byref(opt), _ptr(dchi2),
-                                 ctypes.cast(peaks, _P))
+                                 peaks.ctypes.data)
     _check(rc, "fc2_execute_batched")
     st = np.zeros(5, dtype=np.int64)
     lib.fc2_debug_batch_counts(st.ctypes.data)
-    recs = [[peaks[c * K + r].as_dict() for r in range(K)] for c in range(C)]
-    return dchi2, recs, dict(launches=int(lib.fc2_debug_batch_launches()),
+    return dchi2, BatchPeaks(peaks), dict(launches=int(lib.fc2_debug_batch_launches()),
                              resolved=int(st[0]), exact=int(st[1]),
                              exact_double_float=int(st[2]), exact_double=int(st[3]),
                              graphs=int(st[4]))

@@ -162,11 +162,14 @@ __global__ void __launch_bounds__(128) k_bassemble(const cpx<TS>* __restrict__ s
     for (int h = 0; h < H; ++h) oc[(int64_t)h * N + j] = (float)o[h] * c0;
 }
 
+constexpr double BX_EPS_DF = 1.5e-12;  // relative precision of the tier-2 (double-float) sums
+
 // Double re-solve of listed (curve, bin) entries of the float path.  Entries
-// still too sensitive go on to the exact sums: to the float tier, or straight
-// to the double-float tier when the float sums could not settle them either
+// still too sensitive go on to the exact sums: to the float tier, straight to
+// the double-float tier when the float sums could not settle them either
 // (error estimate at the float sums' precision above the bar, or a small
-// relative pivot).
+// relative pivot), or straight to the double tier when the coefficient norm
+// is beyond the double-float sums as well.
 template <int HM>
 __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__ spec,
                                                   const float* __restrict__ dec, int64_t N,
@@ -177,7 +180,9 @@ __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__
                                                   int64_t rcap, int64_t* __restrict__ flist,
                                                   int32_t* __restrict__ fcount, int64_t fcap,
                                                   int64_t* __restrict__ flist2,
-                                                  int32_t* __restrict__ fcount2, int64_t fcap2) {
+                                                  int32_t* __restrict__ fcount2, int64_t fcap2,
+                                                  int64_t* __restrict__ flist3,
+                                                  int32_t* __restrict__ fcount3, int64_t fcap3) {
     int64_t cnt = *rcount;
     if (cnt > rcap) cnt = rcap;
     const int64_t wpb = blockDim.x >> 5;  // one entry per warp (warp-cooperative solve)
@@ -215,7 +220,10 @@ __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__
         if ((threadIdx.x & 31) == 0) {
             const int m = 2 * H + 1;
             if (!(est_err<double>(an2, m, eps) <= err_fix)) {
-                if (!(est_err<double>(an2, m, 2e-7 * sc[SC_RW]) <= err_fix) || dmin < 3e-3) {
+                if (!(est_err<double>(an2, m, BX_EPS_DF) <= err_fix)) {
+                    const int32_t pos = atomicAdd(fcount3, 1);
+                    if (pos < fcap3) flist3[pos] = rlist[b];
+                } else if (!(est_err<double>(an2, m, 2e-7 * sc[SC_RW]) <= err_fix) || dmin < 3e-3) {
                     const int32_t pos = atomicAdd(fcount2, 1);
                     if (pos < fcap2) flist2[pos] = rlist[b];
                 } else {
@@ -244,7 +252,6 @@ __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__
 // parts at [ntot + i].
 constexpr int BX_NT = 256;
 constexpr int BX_W = BX_NT / 32;
-constexpr double BX_EPS_DF = 1.5e-12;  // relative precision of the tier-2 sums
 
 template <int HM, int TIER, int MODE>
 __global__ void __launch_bounds__(BX_NT) k_bexact(
@@ -705,7 +712,8 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
                                                 N, ct, tau_drop, eps_spec, err_fix, out, b.list,
                                                 b.counts + 0, (int64_t)b.cl1, b.list2, b.counts + 1,
                                                 (int64_t)b.cl2, b.list3, b.counts + 2,
-                                                (int64_t)b.cl3);
+                                                (int64_t)b.cl3, b.list4, b.counts + 3,
+                                                (int64_t)b.cl4);
         ++nl;
     }
     // exact fix-up: float sums over list2 (escalating to list3), double-float

@@ -518,6 +518,46 @@ __global__ void __launch_bounds__(NT, 2) k_fft_pass(const cpx<T>* __restrict__ i
     }
 }
 
+// Store of a transformed tile, staged in shared memory (tile element k J + jj
+// at shared index sidx(k J + jj)), into the blocked layout the next pass
+// reads: logical output i of column j = j0 + jj goes to row i >> logSn,
+// column i mod Sn of that layout.  In a first pass into a pass of smaller
+// radix (logNs = 0, R | Sn) the row and column block of i = j R + k depend on
+// j alone, so element (kb, kl, jj), k = kb Jn + kl, lands at base(j) +
+// kb Rn Jn + kl; each thread keeps jj and kl and walks kb.
+template <int LOGR, int LOGJ, int NT, typename T, typename SIdx>
+FC2_D void store_tile_blocked(cpx<T>* __restrict__ gout, const cpx<T>* s, SIdx sidx, int j0,
+                              const PassArgs& a, int tid) {
+    constexpr int J = 1 << LOGJ, E = (1 << LOGR) * J;
+    const int logNs = a.logNs;
+    const int LOGJn = a.logJn, Jn = 1 << a.logJn;
+    const int logBlk = a.logRn + a.logJn;
+    const int logSn = a.logM - a.logRn;
+    if (logNs == 0 && LOGR <= logSn && LOGJn <= LOGR && (Jn << LOGJ) <= NT) {
+        const int kl = tid & (Jn - 1);
+        const int jj = (tid >> LOGJn) & (J - 1);
+        const int kb0 = tid >> (LOGJn + LOGJ);
+        const int i0 = (j0 + jj) << LOGR;
+        const int jb = i0 & ((1 << logSn) - 1), rn = i0 >> logSn;
+        cpx<T>* dst = gout + ((int64_t)((jb >> LOGJn) + kb0) << logBlk) + (rn << LOGJn) + kl;
+        const int e0 = (kb0 << (LOGJn + LOGJ)) + (kl << LOGJ) + jj;  // k J + jj
+        const int dkb = NT >> (LOGJn + LOGJ);
+#pragma unroll 8
+        for (int it = 0; it < E / NT; ++it) dst[(int64_t)(it * dkb) << logBlk] = s[sidx(e0 + it * NT)];
+        return;
+    }
+    for (int e = tid; e < E; e += NT) {
+        const int kl = e & (Jn - 1);
+        const int jj = (e >> LOGJn) & (J - 1);
+        const int kb = e >> (LOGJn + LOGJ);
+        const int k = (kb << LOGJn) + kl;
+        const int j = j0 + jj;
+        const int i = ((j >> logNs) << (logNs + LOGR)) + (j & ((1 << logNs) - 1)) + (k << logNs);
+        const int jn = i & ((1 << logSn) - 1), rn = i >> logSn;
+        gout[((int64_t)(jn >> LOGJn) << logBlk) + (rn << LOGJn) + (jn & (Jn - 1))] = s[sidx(k * J + jj)];
+    }
+}
+
 // ------------------------------------------------- pruned small transform
 // Q-point DFT (sign +) of v when only v[0..MZ) can be nonzero: with
 // k = (Q/MZ) k1 + k2, X_k = sum_{n<MZ} (v_n w_Q^{n k2}) w_MZ^{n k1}, i.e. Q/MZ
@@ -667,19 +707,18 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
                     if (a.logNs > 0 && jm != 0) {
                         // w_M^{(pp + 64 k) jm 2^lts} = base * step^k, step^k = lo[k & 7] hi[k >> 3];
                         // every factor is a table lookup (no chains of products)
-                        const cpx<T> base = twiddle(twlo, twhi, a.tws, (int64_t)((pp * jm) << lts));
-                        cpx<T> lo[8], hi[8];
-                        lo[0] = mk<T>(1.f, 0.f);
+                        // (base lo[q] formed once per q: the same products as per k)
+                        cpx<T> bl[8], hi[8];
+                        bl[0] = twiddle(twlo, twhi, a.tws, (int64_t)((pp * jm) << lts));
                         hi[0] = mk<T>(1.f, 0.f);
 #pragma unroll
                         for (int q = 1; q < 8; ++q) {
-                            lo[q] = twiddle(twlo, twhi, a.tws, (int64_t)((64 * q * jm) << lts));
+                            bl[q] = mul(bl[0], twiddle(twlo, twhi, a.tws, (int64_t)((64 * q * jm) << lts)));
                             hi[q] = twiddle(twlo, twhi, a.tws, (int64_t)((512 * q * jm) << lts));
                         }
 #pragma unroll
                         for (int k = 0; k < QA; ++k) {
-                            cpx<T> w = base;
-                            if ((k & 7) != 0) w = mul(w, lo[k & 7]);
+                            cpx<T> w = bl[k & 7];
                             if ((k >> 3) != 0) w = mul(w, hi[k >> 3]);
                             v[k] = mul(v[k], w);
                         }
@@ -762,21 +801,9 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
         }
         if (!a.last && !same_radix) {
             __syncthreads();
-            cpx<T>* gout = out + (int64_t)g * M;
-            const int LOGJn = a.logJn, Jn = 1 << a.logJn;
-            const int logBlk = a.logRn + a.logJn;
-            const int logSn = a.logM - a.logRn;
-            for (int e = threadIdx.x; e < E; e += NT) {
-                const int kl = e & (Jn - 1);
-                const int jj = (e >> LOGJn) & (J - 1);
-                const int kb = e >> (LOGJn + LOGJ);
-                const int k = (kb << LOGJn) + kl;
-                const int j = j0 + jj;
-                const int i = ((j >> logNs) << (logNs + LOGR)) + (j & ((1 << logNs) - 1)) + (k << logNs);
-                const int jn = i & ((1 << logSn) - 1), rn = i >> logSn;
-                gout[((jn >> LOGJn) << logBlk) + (rn << LOGJn) + (jn & (Jn - 1))] =
-                    s[swz<LOGJ>(k * J + jj)];
-            }
+            store_tile_blocked<LOGR, LOGJ, NT>(out + (int64_t)g * M, s,
+                                               [](int e) { return swz<LOGJ>(e); }, j0, a,
+                                               threadIdx.x);
         }
         __syncthreads();  // the tile buffer is reused by the next iteration
     }
@@ -1043,22 +1070,8 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
 #pragma unroll
             for (int k = 0; k < 16; ++k) wk[phys((pp + k * NSL) * J + jj)] = v[k];
             __syncthreads();
-            cpx<T>* gout = out + (int64_t)g * M;
-            const int LOGJn = a.logJn, Jn = 1 << a.logJn;
-            const int logBlk = a.logRn + a.logJn;
-            const int logSn = a.logM - a.logRn;
-            for (int e = tid; e < E; e += NT) {
-                const int kl = e & (Jn - 1);
-                const int jc = (e >> LOGJn) & (J - 1);
-                const int kb = e >> (LOGJn + LOGJ);
-                const int k = (kb << LOGJn) + kl;
-                const int j = j0 + jc;
-                const int i = ((j >> logNs) << (logNs + LOGR)) + (j & ((1 << logNs) - 1)) +
-                              (k << logNs);
-                const int jn = i & ((1 << logSn) - 1), rn = i >> logSn;
-                gout[((int64_t)(jn >> LOGJn) << logBlk) + (rn << LOGJn) + (jn & (Jn - 1))] =
-                    wk[phys(k * J + jc)];
-            }
+            store_tile_blocked<LOGR, LOGJ, NT>(out + (int64_t)g * M, wk,
+                                               [](int e) { return phys(e); }, j0, a, tid);
             __syncthreads();
         }
     }

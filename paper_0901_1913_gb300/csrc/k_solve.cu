@@ -213,12 +213,18 @@ __global__ void __launch_bounds__(128) k_resolve(const cpx<float>* __restrict__ 
                 // to be beyond float sums -- by the coefficient norm, or by a
                 // small relative pivot (columns this solve drops come back with
                 // large coefficients in the exact solve) -- start at the
-                // double-float tier.  The double tier is only reached by
-                // escalation: the gridded equations are too coarse to tell which
-                // bins need it.  Each tier checks its own result and passes bins on.
+                // double-float tier, and bins whose coefficient norm is beyond
+                // the double-float sums too start at the double tier.  A small
+                // pivot alone does not send a bin to the double tier: the
+                // gridded equations cannot resolve pivots near the double-float
+                // sums' precision.  Each tier checks its own result and passes
+                // bins on.
                 const int m = 2 * H + 1;
                 int32_t *lst = flist, *cnt = fcount;
-                if (!(est_err<double>(an2, m, sp.eps_t1) <= sp.err_fix) || dmin < 3e-3) {
+                if (!(est_err<double>(an2, m, sp.eps_t2) <= sp.err_fix)) {
+                    lst = flist3;
+                    cnt = fcount3;
+                } else if (!(est_err<double>(an2, m, sp.eps_t1) <= sp.err_fix) || dmin < 3e-3) {
                     lst = flist2;
                     cnt = fcount2;
                 }
