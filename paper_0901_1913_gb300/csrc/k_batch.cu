@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <map>
+#include <type_traits>
 #include <vector>
 
 #include "fc2_common.cuh"
@@ -237,14 +238,19 @@ __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__
     }
 }
 
-// ----------------------------------------------------- exact, one warp per entry
-// Entries (curve << 32 | j).  The lanes of a warp sum the entry's curve
-// samples at stride 32, a butterfly gives every lane the totals (the same
-// bits on every lane), and the warp solves cooperatively.  Precision tiers of
-// the sums over the exact integer phases (Sec. 3's moments, Eqs. for Q and P):
+// ------------------------------------------------------------ exact sums
+// Entries (curve << 32 | j).  Precision tiers of the sums over the exact
+// integer phases (Sec. 3's moments, Eqs. for Q and P):
 //   1: float sine / cosine, compensated float sums;
 //   2: double-float phasors, products and sums (about 48 bits);
 //   3: double phasors and sums.
+// An entry's samples are cut into work items of about BX_CH samples (at most
+// BX_QMAX per entry) so that the long curves of a batch spread over all SMs:
+// k_bx_split numbers the items in entry order, k_bx_part sums each item with
+// one warp (lanes at stride 32, then a butterfly) into a row of partial sums,
+// and k_bexact adds an entry's rows in item order, solves and routes.  Entries
+// beyond the item capacity are summed whole by k_bexact.  Every order is
+// fixed, so results do not depend on scheduling.
 // MODE 0 writes Delta chi^2 (float) and passes on to `next` the entries whose
 // error estimate from the coefficient norm, or whose smallest relative pivot,
 // is beyond what the tier's sums can vouch for.  MODE 1 writes coefficient
@@ -252,28 +258,243 @@ __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__
 // parts at [ntot + i].
 constexpr int BX_NT = 256;
 constexpr int BX_W = BX_NT / 32;
+constexpr int BX_CH = 2048;           // samples per work item
+constexpr int BX_QMAX = 64;           // work items per entry at most
+constexpr int BX_ITEMS = 1 << 18;     // work items per launch at most
+constexpr int BX_SPLIT_NT = 1024;     // threads of the (single-CTA) item numbering
 
+FC2_HD int bx_items_of(int64_t n) {
+    const int64_t q = (n + BX_CH - 1) / BX_CH;
+    return (int)(q < 1 ? 1 : (q > BX_QMAX ? BX_QMAX : q));
+}
+
+// The phasor tables of tiers 2 and 3, staged in shared memory by every CTA.
+template <int TIER>
+struct BxTables {
+    dfc t2[TIER == 2 ? 512 : 1];
+    double2 t3[TIER == 3 ? 512 : 1];
+    FC2_D void load(const dfc* __restrict__ dftab) {
+        if constexpr (TIER == 2)
+            for (int i = threadIdx.x; i < 512; i += blockDim.x) t2[i] = dftab[i];
+        if constexpr (TIER == 3) {
+            const double2* t64 = reinterpret_cast<const double2*>(dftab + 512);
+            for (int i = threadIdx.x; i < 512; i += blockDim.x) t3[i] = t64[i];
+        }
+        __syncthreads();
+    }
+};
+
+// Sums of samples [i0, i1) of one entry (bin ju, H harmonics) by one warp;
+// every lane returns the same totals tot[6 HM]: Q_k (k = 1..2H) re/im at
+// [2(k-1)], [2(k-1)+1], P_k (k = 1..H) at [4 HM + 2(k-1)], [4 HM + 2(k-1)+1].
+template <int HM, int TIER>
+FC2_D void bx_sums(const uint64_t* __restrict__ Aph, const uint64_t* __restrict__ Bph,
+                   const float* __restrict__ wq32, const float* __restrict__ wp32,
+                   const double* __restrict__ wq, const double* __restrict__ wp,
+                   const BxTables<TIER>& tb, int64_t ntot, uint64_t ju, int H, int64_t i0,
+                   int64_t i1, int lane, double* tot) {
+    constexpr int NV = 6 * HM;
+    if constexpr (TIER == 1) {
+        CompSum<float> fa[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) fa[v].init();
+        for (int64_t i = i0 + lane; i < i1; i += 32) {
+            const uint32_t u = (uint32_t)((Aph[i] + ju * Bph[i]) >> 32);
+            const float a = wq32[i], bb = wp32[i];
+#pragma unroll
+            for (int k = 1; k <= 2 * HM; ++k) {
+                if (k <= 2 * H) {
+                    const int32_t ph = (int32_t)(u * (uint32_t)k);  // [-1/2, 1/2) cycles
+                    float sn, cn;
+                    sincospif((float)ph * 4.656612873077393e-10f, &sn, &cn);  // 2^-31
+                    fa[2 * (k - 1)].add(a * cn);
+                    fa[2 * (k - 1) + 1].add(a * sn);
+                    if (k <= H) {
+                        fa[4 * HM + 2 * (k - 1)].add(bb * cn);
+                        fa[4 * HM + 2 * (k - 1) + 1].add(bb * sn);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float2 x = warp_allsum_pair(fa[v].s, fa[v].c);
+            tot[v] = (double)x.x + (double)x.y;
+        }
+    } else if constexpr (TIER == 2) {
+        dfl fa[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) fa[v] = dfl{0.f, 0.f};
+        for (int64_t i = i0 + lane; i < i1; i += 32) {
+            const uint64_t u = Aph[i] + ju * Bph[i];
+            const dfl a{wq32[i], wq32[ntot + i]}, bb{wp32[i], wp32[ntot + i]};
+            const dfc z1 = df_phasor(u, tb.t2, tb.t2 + 256);
+            dfc z = z1;
+#pragma unroll
+            for (int k = 0; k < 2 * HM; ++k) {
+                if (k < 2 * H) {
+                    df_acc_mul(fa[2 * k], a, z.re);
+                    df_acc_mul(fa[2 * k + 1], a, z.im);
+                    if (k < H) {
+                        df_acc_mul(fa[4 * HM + 2 * k], bb, z.re);
+                        df_acc_mul(fa[4 * HM + 2 * k + 1], bb, z.im);
+                    }
+                    if (k + 1 < 2 * H) z = dfc_mul(z, z1);
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float2 x = warp_allsum_pair(fa[v].h, fa[v].l);
+            tot[v] = (double)x.x + (double)x.y;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) tot[v] = 0.0;
+        for (int64_t i = i0 + lane; i < i1; i += 32) {
+            const double2 z1 = d_phasor(Aph[i] + ju * Bph[i], tb.t3, tb.t3 + 256);
+            const double c1 = z1.x, s1 = z1.y;
+            double cr = c1, ci = s1;
+            const double a = wq[i], bb = wp[i];
+#pragma unroll
+            for (int k = 0; k < 2 * HM; ++k) {
+                if (k < 2 * H) {
+                    tot[2 * k] = fma(a, cr, tot[2 * k]);
+                    tot[2 * k + 1] = fma(a, ci, tot[2 * k + 1]);
+                    if (k < H) {
+                        tot[4 * HM + 2 * k] = fma(bb, cr, tot[4 * HM + 2 * k]);
+                        tot[4 * HM + 2 * k + 1] = fma(bb, ci, tot[4 * HM + 2 * k + 1]);
+                    }
+                    const double nr = cr * c1 - ci * s1, ni = cr * s1 + ci * c1;
+                    cr = nr;
+                    ci = ni;
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tot[v] += __shfl_xor_sync(0xffffffffu, tot[v], o);
+        }
+    }
+}
+
+// Work items of the listed entries, numbered in entry order by one CTA (each
+// thread a run of entries, then a block scan): qbase[e] = first item of entry
+// e (items qbase[e] .. + bx_items_of(n) - 1), or -1 when the entry is summed
+// whole (an empty peak slot, or past the item capacity; the entries that fit
+// form a prefix); items[w] = e * BX_QMAX + q; *nitems = items placed.
+__global__ void __launch_bounds__(BX_SPLIT_NT) k_bx_split(CurveTab ct,
+                                                          const int64_t* __restrict__ list,
+                                                          const int32_t* __restrict__ count,
+                                                          int64_t cap, int32_t* __restrict__ qbase,
+                                                          int32_t* __restrict__ items,
+                                                          int32_t* __restrict__ nitems) {
+    __shared__ int32_t wsum[BX_SPLIT_NT / 32];
+    __shared__ int32_t placed;
+    int64_t cnt = *count;
+    if (cnt > cap) cnt = cap;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) placed = 0;
+    const int64_t per = (cnt + BX_SPLIT_NT - 1) / BX_SPLIT_NT;
+    const int64_t e0 = (int64_t)tid * per;
+    const int64_t e1 = (e0 + per < cnt) ? e0 + per : cnt;
+    auto items_of = [&](int64_t e) -> int {
+        const int64_t ent = list[e];
+        if ((ent & 0xffffffffll) == 0xffffffffll) return 0;  // empty peak slot
+        const int c = (int)(ent >> 32);
+        return bx_items_of(ct.off[c + 1] - ct.off[c]);
+    };
+    // item counts: at most (2^22 entries) x BX_QMAX in all, so int32 sums are exact
+    int32_t v = 0;
+    for (int64_t e = e0; e < e1; ++e) v += items_of(e);
+    int32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int32_t x = lane < BX_SPLIT_NT / 32 ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane < BX_SPLIT_NT / 32) wsum[lane] = x;
+    }
+    __syncthreads();
+    // entries in order: those whose items fit below the capacity form a prefix
+    int32_t base = (w > 0 ? wsum[w - 1] : 0) + (incl - v);
+    int32_t end = 0;
+    for (int64_t e = e0; e < e1; ++e) {
+        const int nq = items_of(e);
+        if (nq > 0 && base + nq <= BX_ITEMS) {
+            qbase[e] = base;
+            for (int q = 0; q < nq; ++q) items[base + q] = (int32_t)(e * BX_QMAX + q);
+            end = base + nq;
+        } else {
+            qbase[e] = -1;
+        }
+        base += nq;
+    }
+    atomicMax(&placed, end);
+    __syncthreads();
+    if (tid == 0) *nitems = placed;
+}
+
+// One warp per work item: the item's share of its entry's samples, summed
+// into row w of part (6 BHM doubles per row).
+template <int HM, int TIER>
+__global__ void __launch_bounds__(BX_NT) k_bx_part(
+    const uint64_t* __restrict__ Aph, const uint64_t* __restrict__ Bph,
+    const float* __restrict__ wq32, const float* __restrict__ wp32,
+    const double* __restrict__ wq, const double* __restrict__ wp, const dfc* __restrict__ dftab,
+    int64_t ntot, CurveTab ct, const int64_t* __restrict__ list,
+    const int32_t* __restrict__ items, const int32_t* __restrict__ nitems,
+    double* __restrict__ part) {
+    constexpr int NV = 6 * HM;
+    __shared__ BxTables<TIER> tb;
+    tb.load(dftab);
+    const int nw = *nitems;
+    const int lane = threadIdx.x & 31;
+    for (int w = blockIdx.x * BX_W + (threadIdx.x >> 5); w < nw; w += gridDim.x * BX_W) {
+        const int it = items[w];
+        const int64_t e = it / BX_QMAX;
+        const int q = it % BX_QMAX;
+        const int64_t ent = list[e];
+        const int c = (int)(ent >> 32);
+        const uint64_t ju = (uint64_t)(ent & 0xffffffffll);
+        const int64_t a0 = ct.off[c], n = ct.off[c + 1] - a0;
+        const int nq = bx_items_of(n);
+        const int64_t i0 = a0 + n * q / nq, i1 = a0 + n * (q + 1) / nq;
+        double tot[NV];
+        bx_sums<HM, TIER>(Aph, Bph, wq32, wp32, wq, wp, tb, ntot, ju, ct.H[c], i0, i1, lane, tot);
+        double* row = part + (int64_t)w * NV;
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            if ((v & 31) == lane) row[v] = tot[v];
+    }
+}
+
+// Entry totals in every lane: the entry's partial rows added in item order
+// (lanes own values v = lane, lane + 32), or the whole sum when it has none.
 template <int HM, int TIER, int MODE>
 __global__ void __launch_bounds__(BX_NT) k_bexact(
     const uint64_t* __restrict__ Aph, const uint64_t* __restrict__ Bph,
     const float* __restrict__ wq32, const float* __restrict__ wp32,
     const double* __restrict__ wq, const double* __restrict__ wp, const dfc* __restrict__ dftab,
     int64_t ntot, CurveTab ct, int64_t N, const int64_t* __restrict__ list,
-    const int32_t* __restrict__ count, int64_t cap, double tau_drop, double err_fix,
-    float* __restrict__ out, int64_t* __restrict__ next, int32_t* __restrict__ next_count,
-    int64_t next_cap, fc2_best* __restrict__ recs) {
+    const int32_t* __restrict__ count, int64_t cap, const int32_t* __restrict__ qbase,
+    const double* __restrict__ part, double tau_drop, double err_fix, float* __restrict__ out,
+    int64_t* __restrict__ next, int32_t* __restrict__ next_count, int64_t next_cap,
+    fc2_best* __restrict__ recs) {
     constexpr int NV = 6 * HM;
-    __shared__ dfc stab[TIER == 2 ? 512 : 1];
-    __shared__ double2 stab64[TIER == 3 ? 512 : 1];
-    if constexpr (TIER == 2) {
-        for (int i = threadIdx.x; i < 512; i += BX_NT) stab[i] = dftab[i];
-        __syncthreads();
-    }
-    if constexpr (TIER == 3) {
-        const double2* t64 = reinterpret_cast<const double2*>(dftab + 512);
-        for (int i = threadIdx.x; i < 512; i += BX_NT) stab64[i] = t64[i];
-        __syncthreads();
-    }
+    static_assert(NV <= 64, "two values per lane");
+    __shared__ BxTables<TIER> tb;
+    tb.load(dftab);
     int64_t cnt = *count;
     if (cnt > cap) cnt = cap;
     const int lane = threadIdx.x & 31;
@@ -293,90 +514,22 @@ __global__ void __launch_bounds__(BX_NT) k_bexact(
             continue;
         }
         const int64_t a0 = ct.off[c], a1 = ct.off[c + 1];
-        const uint64_t ju = (uint64_t)j;
         double tot[NV];
-        if constexpr (TIER == 1) {
-            CompSum<float> fa[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) fa[v].init();
-            for (int64_t i = a0 + lane; i < a1; i += 32) {
-                const uint32_t u = (uint32_t)((Aph[i] + ju * Bph[i]) >> 32);
-                const float a = wq32[i], bb = wp32[i];
-#pragma unroll
-                for (int k = 1; k <= 2 * HM; ++k) {
-                    if (k <= 2 * H) {
-                        const int32_t ph = (int32_t)(u * (uint32_t)k);  // [-1/2, 1/2) cycles
-                        float sn, cn;
-                        sincospif((float)ph * 4.656612873077393e-10f, &sn, &cn);  // 2^-31
-                        fa[2 * (k - 1)].add(a * cn);
-                        fa[2 * (k - 1) + 1].add(a * sn);
-                        if (k <= H) {
-                            fa[4 * HM + 2 * (k - 1)].add(bb * cn);
-                            fa[4 * HM + 2 * (k - 1) + 1].add(bb * sn);
-                        }
-                    }
-                }
+        const int qb = qbase[e];
+        if (qb >= 0) {
+            const int nq = bx_items_of(a1 - a0);
+            double lo = 0.0, hi = 0.0;
+            for (int q = 0; q < nq; ++q) {
+                const double* row = part + (int64_t)(qb + q) * NV;
+                lo += row[lane];
+                if (lane + 32 < NV) hi += row[lane + 32];
             }
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const float2 x = warp_allsum_pair(fa[v].s, fa[v].c);
-                tot[v] = (double)x.x + (double)x.y;
-            }
-        } else if constexpr (TIER == 2) {
-            dfl fa[NV];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) fa[v] = dfl{0.f, 0.f};
-            for (int64_t i = a0 + lane; i < a1; i += 32) {
-                const uint64_t u = Aph[i] + ju * Bph[i];
-                const dfl a{wq32[i], wq32[ntot + i]}, bb{wp32[i], wp32[ntot + i]};
-                const dfc z1 = df_phasor(u, stab, stab + 256);
-                dfc z = z1;
-#pragma unroll
-                for (int k = 0; k < 2 * HM; ++k) {
-                    if (k < 2 * H) {
-                        df_acc_mul(fa[2 * k], a, z.re);
-                        df_acc_mul(fa[2 * k + 1], a, z.im);
-                        if (k < H) {
-                            df_acc_mul(fa[4 * HM + 2 * k], bb, z.re);
-                            df_acc_mul(fa[4 * HM + 2 * k + 1], bb, z.im);
-                        }
-                        if (k + 1 < 2 * H) z = dfc_mul(z, z1);
-                    }
-                }
-            }
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const float2 x = warp_allsum_pair(fa[v].h, fa[v].l);
-                tot[v] = (double)x.x + (double)x.y;
-            }
+            for (int v = 0; v < NV; ++v)
+                tot[v] = __shfl_sync(0xffffffffu, v < 32 ? lo : hi, v & 31);
         } else {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) tot[v] = 0.0;
-            for (int64_t i = a0 + lane; i < a1; i += 32) {
-                const double2 z1 = d_phasor(Aph[i] + ju * Bph[i], stab64, stab64 + 256);
-                const double c1 = z1.x, s1 = z1.y;
-                double cr = c1, ci = s1;
-                const double a = wq[i], bb = wp[i];
-#pragma unroll
-                for (int k = 0; k < 2 * HM; ++k) {
-                    if (k < 2 * H) {
-                        tot[2 * k] = fma(a, cr, tot[2 * k]);
-                        tot[2 * k + 1] = fma(a, ci, tot[2 * k + 1]);
-                        if (k < H) {
-                            tot[4 * HM + 2 * k] = fma(bb, cr, tot[4 * HM + 2 * k]);
-                            tot[4 * HM + 2 * k + 1] = fma(bb, ci, tot[4 * HM + 2 * k + 1]);
-                        }
-                        const double nr = cr * c1 - ci * s1, ni = cr * s1 + ci * c1;
-                        cr = nr;
-                        ci = ni;
-                    }
-                }
-            }
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) tot[v] += __shfl_xor_sync(0xffffffffu, tot[v], o);
-            }
+            bx_sums<HM, TIER>(Aph, Bph, wq32, wp32, wq, wp, tb, ntot, (uint64_t)j, H, a0, a1,
+                              lane, tot);
         }
         const double* sc = ct.scal + (int64_t)c * SC_COUNT;
         Sys<double, HM> S;
@@ -591,6 +744,8 @@ struct Batch {
     int64_t *list = nullptr, *list2 = nullptr, *list3 = nullptr, *list4 = nullptr;
     size_t cl1 = 0, cl2 = 0, cl3 = 0, cl4 = 0;
     char* dftab = nullptr; size_t cdftab = 0;  // phasor tables of the exact sums
+    int32_t *qbase = nullptr, *items = nullptr; size_t cqbase = 0, citems = 0;  // exact-sum work items
+    double* part = nullptr; size_t cpart = 0;  // their partial sums
     int32_t* counts = nullptr; size_t ccnt = 0;
     int* curves = nullptr; size_t ccurves = 0;
     Cand* tops = nullptr; size_t ctops = 0;
@@ -612,7 +767,7 @@ struct Batch {
         release(slot_kind, s); release(slot_soff, s); release(slot_n, s); release(L, s);
         release(key, s); release(dlt, s); release(cs, s); release(grid0, s); release(grid1, s);
         release(spec, s); release(out, s); release(list, s); release(list2, s); release(list3, s);
-        release(list4, s); release(dftab, s);
+        release(list4, s); release(dftab, s); release(qbase, s); release(items, s); release(part, s);
         release(counts, s); release(curves, s); release(tops, s); release(pent, s);
         release(recs, s); release(red, s);
         release(cp.d_twlo, s); release(cp.d_twhi, s); release(cp.d_twst, s); release(cp.d_dec, s);
@@ -720,24 +875,37 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
     // sums over list3 (escalating to list4), double sums over list4
     const dfc* tab = (const dfc*)b.dftab;
     const unsigned gx = 2 * 152;
-    k_bexact<BHM, 1, 0><<<gx, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, tab, ntot, ct, N,
-                                             b.list2, b.counts + 1, (int64_t)b.cl2, 1e-13, err_fix,
-                                             out, b.list3, b.counts + 2, (int64_t)b.cl3, nullptr);
-    k_bexact<BHM, 2, 0><<<gx, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, tab, ntot, ct, N,
-                                             b.list3, b.counts + 2, (int64_t)b.cl3, 1e-13, err_fix,
-                                             out, b.list4, b.counts + 3, (int64_t)b.cl4, nullptr);
-    k_bexact<BHM, 3, 0><<<gx, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, tab, ntot, ct, N,
-                                             b.list4, b.counts + 3, (int64_t)b.cl4, 1e-13, err_fix,
-                                             out, nullptr, nullptr, 0, nullptr);
-    nl += 3;
+    int32_t* nitems = b.counts + 10;
+    // one tier (or the records) over `list`: number the work items, sum them,
+    // then add, solve and route each entry
+    auto exact = [&](auto tier_tag, auto mode_tag, const int64_t* list, const int32_t* cnt,
+                     int64_t cap, double tau, int64_t* next, int32_t* next_cnt, int64_t next_cap,
+                     fc2_best* recs) {
+        constexpr int TIER = decltype(tier_tag)::value, MODE = decltype(mode_tag)::value;
+        k_bx_split<<<1, BX_SPLIT_NT, 0, s>>>(ct, list, cnt, cap, b.qbase, b.items, nitems);
+        k_bx_part<BHM, TIER><<<gx, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, tab, ntot,
+                                                  ct, list, b.items, nitems, b.part);
+        k_bexact<BHM, TIER, MODE><<<gx, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, tab,
+                                                       ntot, ct, N, list, cnt, cap, b.qbase, b.part,
+                                                       tau, err_fix, out, next, next_cnt, next_cap,
+                                                       recs);
+        nl += 3;
+    };
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using I3 = std::integral_constant<int, 3>;
+    exact(I1{}, I0{}, b.list2, b.counts + 1, (int64_t)b.cl2, 1e-13, b.list3, b.counts + 2,
+          (int64_t)b.cl3, nullptr);
+    exact(I2{}, I0{}, b.list3, b.counts + 2, (int64_t)b.cl3, 1e-13, b.list4, b.counts + 3,
+          (int64_t)b.cl4, nullptr);
+    exact(I3{}, I0{}, b.list4, b.counts + 3, (int64_t)b.cl4, 1e-13, nullptr, nullptr, 0, nullptr);
     if (K > 0) {
         const int nblk = (int)((N + BP_B - 1) / BP_B);
         k_bpeaks1<<<dim3((unsigned)nblk, (unsigned)nc), BP_NT, 0, s>>>(out, N, ct, K, nblk, b.tops);
         k_bpeaks2<<<(unsigned)nc, 256, 0, s>>>(b.tops, nblk, K, b.pent);
-        k_bexact<BHM, 2, 1><<<gx, BX_NT, 0, s>>>(b.A, b.B, b.wq32, b.wp32, b.wq, b.wp, tab, ntot, ct,
-                                                 N, b.pent, b.counts + 4, nrec, tau_drop, err_fix,
-                                                 out, nullptr, nullptr, 0, b.recs);
-        nl += 3;
+        nl += 2;
+        exact(I2{}, I1{}, b.pent, b.counts + 4, nrec, tau_drop, nullptr, nullptr, 0, b.recs);
     }
     b.launches += nl;
     return cudaGetLastError();
@@ -927,6 +1095,10 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             ok(need(&b.list3, &b.cl3, (size_t)std::min<int64_t>(out_chunk, 1 << 20), s)) &&
             ok(need(&b.list4, &b.cl4, (size_t)std::min<int64_t>(out_chunk, 1 << 20), s)) &&
             ok(need(&b.dftab, &b.cdftab, 2 * 512 * 16, s)) &&
+            ok(need(&b.qbase, &b.cqbase,
+                    std::max<size_t>({b.cl2, b.cl3, b.cl4, (size_t)std::max<int64_t>(nrec, 1)}), s)) &&
+            ok(need(&b.items, &b.citems, (size_t)BX_ITEMS, s)) &&
+            ok(need(&b.part, &b.cpart, (size_t)BX_ITEMS * 6 * BHM, s)) &&
             ok(need(&b.counts, &b.ccnt, 16, s)) && ok(need(&b.curves, &b.ccurves, nc, s)) &&
             ok(need(&b.tops, &b.ctops, (size_t)nc * ((N + BP_B - 1) / BP_B) * std::max(K, 1), s)) &&
             ok(need(&b.pent, &b.cpent, (size_t)std::max<int64_t>(nrec, 1), s)) &&
