@@ -71,6 +71,13 @@ int64_t fc2_debug_batch_launches(void);
  * the number of chunk graphs launched.  No-op on NULL. */
 void fc2_debug_batch_counts(int64_t* out5);
 
+/* Host wall milliseconds of the last fc2_execute_batched call of this process
+ * in seven phases (out7[0..6]): setup before the chunk loop; per chunk,
+ * summed: buffer allocation and input uploads, per-curve moments and the wait for them, chunk
+ * layout and table uploads, graph capture / update and launch, the wait for
+ * the chunk's kernels and results; release at the end.  No-op on NULL. */
+void fc2_debug_batch_phase_ms(double* out7);
+
 /* Stage timing of p on (enable != 0) or off; resets the accumulated times.
  * While on, each execute records CUDA events on the plan's stream around
  * (0) phase reduction and spreading, (1) FFT passes, (2) assembly and solve,

@@ -138,6 +138,8 @@ def load():
         lib.fc2_debug_batch_launches.restype = i64
         lib.fc2_debug_batch_counts.argtypes = [_P]
         lib.fc2_debug_batch_counts.restype = None
+        lib.fc2_debug_batch_phase_ms.argtypes = [_P]
+        lib.fc2_debug_batch_phase_ms.restype = None
         lib.fc2_stage_timing.argtypes = [_P, i32]
         lib.fc2_stage_timing.restype = i32
         lib.fc2_stage_times.argtypes = [_P, _P, _P, _P]
@@ -375,10 +377,15 @@ def execute_batched(offsets, t, x, sigma, H, f_min, df, N, oversample=2, prec="m
     _check(rc, "fc2_execute_batched")
     st = np.zeros(5, dtype=np.int64)
     lib.fc2_debug_batch_counts(st.ctypes.data)
+    ph = np.zeros(7)
+    lib.fc2_debug_batch_phase_ms(ph.ctypes.data)
     return dchi2, BatchPeaks(peaks), dict(launches=int(lib.fc2_debug_batch_launches()),
                              resolved=int(st[0]), exact=int(st[1]),
                              exact_double_float=int(st[2]), exact_double=int(st[3]),
-                             graphs=int(st[4]))
+                             graphs=int(st[4]),
+                             host_phase_ms=dict(zip(("setup", "alloc", "moments", "layout",
+                                                     "graph", "wait", "release"),
+                                                    (float(v) for v in ph))))
 
 
 def _backward_argtypes(lib):

@@ -1,6 +1,7 @@
 // fc2_api.cu -- the C ABI of libfc2: validation, plan lifetime, buffer
 // management and the order of kernel launches.  No kernel arithmetic here.
 #include <cuda_runtime.h>
+#include <cstring>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -18,7 +19,9 @@
 using namespace fc2;
 
 static int64_t g_last_batch_launches = 0;
-static int64_t g_last_batch_stats[5] = {0, 0, 0, 0, 0};  // re-solved, exact float / double-float / double, graphs
+// re-solved, exact float / double-float / double, graphs; then the host
+// milliseconds of the call's seven phases (as doubles' bits)
+static int64_t g_last_batch_stats[12] = {0};
 
 // Device memory comes from one stream-ordered pool per device owned by the
 // library.  Memory that a destroyed plan returns stays mapped in the pool
@@ -711,6 +714,16 @@ int64_t fc2_debug_batch_launches(void) { return g_last_batch_launches; }
 void fc2_debug_batch_counts(int64_t* out5) {
     if (out5)
         for (int i = 0; i < 5; ++i) out5[i] = g_last_batch_stats[i];
+}
+
+/* Host wall milliseconds of the last fc2_execute_batched call in seven phases
+ * (out7[0..6]): setup before the chunk loop; per chunk (summed): buffer
+ * allocation and input uploads, moments and the wait for them, chunk layout and table uploads,
+ * graph capture / update and launch, the wait for the chunk's kernels and
+ * results; release of the buffers at the end. */
+void fc2_debug_batch_phase_ms(double* out7) {
+    if (out7)
+        for (int i = 0; i < 7; ++i) std::memcpy(&out7[i], &g_last_batch_stats[5 + i], 8);
 }
 
 /* Stage timing: while enabled, each execute records CUDA events on the plan's

@@ -250,7 +250,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
                            const double* sigma, const int* H, const double* fmin,
                            const double* df, const int64_t* N, int oversample,
                            const fc2_options& opt, float* dchi2, fc2_best* peaks,
-                           int64_t* launches_out, int64_t* stats_out);  // stats_out[5]
+                           int64_t* launches_out, int64_t* stats_out);  // stats_out[12]
 
 fc2_status batched_backward(int64_t C, const int64_t* offsets, const double* t, const double* x,
                             const double* sigma, const int* H, const double* fmin,

@@ -12,6 +12,8 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <chrono>
+#include <cstring>
 #include <map>
 #include <type_traits>
 #include <vector>
@@ -756,6 +758,7 @@ struct Batch {
     int64_t graphs = 0;  // chunk graphs launched
     int64_t launches = 0;
     int64_t stats[4] = {0, 0, 0, 0};
+    double phase_ms[7] = {0, 0, 0, 0, 0, 0, 0};  // host wall time of the call's phases
 
     void free_all() {
         release(t, s); release(x, s); release(sg, s); release(perm, s); release(tau, s);
@@ -987,6 +990,11 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     const bool fp64 = opt.prec == FC2_PREC_FP64;
     const size_t tsz = fp64 ? 8 : 4, csz = 2 * tsz;
     const int K = opt.top_k ? opt.top_k : 8;
+    auto now = [] { return std::chrono::steady_clock::now(); };
+    auto ms_since = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point z) {
+        return std::chrono::duration<double, std::milli>(z - a).count();
+    };
+    const auto t_entry = now();
     Batch b;
     if (opt.cuda_stream) b.s = (cudaStream_t)opt.cuda_stream;
     else {
@@ -1007,24 +1015,48 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     int64_t out_global = 0;
     int64_t curM = -1, curN = -1;
     int64_t c0 = 0;
-    while (c0 < C && st == FC2_OK) {
-        // ---- chunk: consecutive curves with the same N, within the memory budget
-        const int64_t N = Nc[c0];
-        const int64_t M = fc2_grid_size(N, oversample);
-        int64_t c1 = c0, S = 0, ntot = 0, nmax = 0, slot_samples = 0;
-        while (c1 < C && Nc[c1] == N && c1 - c0 < 2048) {
-            const int64_t n = offsets[c1 + 1] - offsets[c1];
-            const int64_t sl = (shared && c1 > c0) ? Hc[c1] : 3 * Hc[c1];
-            const size_t bytes = (size_t)(S + sl) * (size_t)M * csz * 2 + (size_t)(S + sl) * N * csz +
-                                 (size_t)(slot_samples + sl * n) * (4 + tsz + csz) +
-                                 (size_t)(ntot + n) * 80;
-            if (c1 > c0 && bytes > budget) break;
-            S += sl;
-            ntot += n;
-            nmax = std::max(nmax, n);
-            slot_samples += sl * n;
-            ++c1;
+    // ---- chunks: consecutive curves with the same N, within the memory budget,
+    // planned up front so that every buffer is allocated once, at the largest
+    // size any chunk needs
+    struct Chunk { int64_t c0, c1, S, ntot, nmax, slot_samples, out, N, M; };
+    std::vector<Chunk> chunks;
+    Chunk mx{0, 0, 0, 0, 0, 0, 0, 0, 0};
+    size_t mx_grid = 0, mx_spec = 0, mx_sort = 0, mx_tops = 0;
+    for (int64_t a = 0; a < C;) {
+        Chunk ch{a, a, 0, 0, 0, 0, 0, Nc[a], fc2_grid_size(Nc[a], oversample)};
+        while (ch.c1 < C && Nc[ch.c1] == ch.N && ch.c1 - a < 2048) {
+            const int64_t n = offsets[ch.c1 + 1] - offsets[ch.c1];
+            const int64_t sl = (shared && ch.c1 > a) ? Hc[ch.c1] : 3 * Hc[ch.c1];
+            const size_t bytes = (size_t)(ch.S + sl) * (size_t)ch.M * csz * 2 +
+                                 (size_t)(ch.S + sl) * ch.N * csz +
+                                 (size_t)(ch.slot_samples + sl * n) * (4 + tsz + csz) +
+                                 (size_t)(ch.ntot + n) * 80;
+            if (ch.c1 > a && bytes > budget) break;
+            ch.S += sl;
+            ch.ntot += n;
+            ch.nmax = std::max(ch.nmax, n);
+            ch.slot_samples += sl * n;
+            ch.out += (int64_t)Hc[ch.c1] * ch.N;
+            ++ch.c1;
         }
+        chunks.push_back(ch);
+        mx.S = std::max(mx.S, ch.S);
+        mx.ntot = std::max(mx.ntot, ch.ntot);
+        mx.slot_samples = std::max(mx.slot_samples, ch.slot_samples);
+        mx.out = std::max(mx.out, ch.out);
+        mx.c1 = std::max(mx.c1, ch.c1 - ch.c0);  // curves
+        mx_grid = std::max(mx_grid, (size_t)ch.S * ch.M * csz);
+        mx_spec = std::max(mx_spec, (size_t)ch.S * ch.N * csz);
+        mx_sort = std::max(mx_sort, sort_scratch_bytes(ch.nmax));
+        mx_tops = std::max(mx_tops, (size_t)(ch.c1 - ch.c0) * ((ch.N + BP_B - 1) / BP_B) * std::max(K, 1));
+        a = ch.c1;
+    }
+    const int64_t mx_nc = mx.c1, mx_nrec = mx_nc * K;
+    b.phase_ms[0] = ms_since(t_entry, now());
+    for (const Chunk& ch : chunks) {
+        if (st != FC2_OK) break;
+        c0 = ch.c0;
+        const int64_t c1 = ch.c1, S = ch.S, ntot = ch.ntot, nmax = ch.nmax, N = ch.N, M = ch.M;
         const int nc = (int)(c1 - c0);
         fc2_plan_s& p = b.cp;
         // ---- shared tables for this (N, M)
@@ -1055,59 +1087,62 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             curN = N;
         }
         // ---- buffers
+        const auto tpb = now();
         const int64_t base = offsets[c0];
         cudaError_t e = cudaSuccess;
         auto ok = [&](cudaError_t r) { if (e == cudaSuccess) e = r; return e == cudaSuccess; };
         if (opt.inputs_on_device) {
             b.t = (double*)(t + base); b.x = (double*)(x + base); b.sg = (double*)(sigma + base);
         } else {
-            ok(need(&b.t, &b.ct, ntot, s)) && ok(need(&b.x, &b.cx, ntot, s)) &&
-                ok(need(&b.sg, &b.csg, ntot, s)) &&
+            ok(need(&b.t, &b.ct, (size_t)mx.ntot, s)) && ok(need(&b.x, &b.cx, (size_t)mx.ntot, s)) &&
+                ok(need(&b.sg, &b.csg, (size_t)mx.ntot, s)) &&
                 ok(cudaMemcpyAsync(b.t, t + base, ntot * 8, cudaMemcpyHostToDevice, s)) &&
                 ok(cudaMemcpyAsync(b.x, x + base, ntot * 8, cudaMemcpyHostToDevice, s)) &&
                 ok(cudaMemcpyAsync(b.sg, sigma + base, ntot * 8, cudaMemcpyHostToDevice, s));
         }
         const int64_t nrec = (int64_t)nc * K;
-        int64_t out_chunk = 0;
-        for (int64_t c = c0; c < c1; ++c) out_chunk += (int64_t)Hc[c] * N;
-        const size_t sort_b = sort_scratch_bytes(nmax);
-        ok(need(&b.perm, &b.cperm, ntot, s)) && ok(need(&b.tau, &b.ctau, ntot, s)) &&
-            ok(need(&b.wq, &b.cwq, ntot, s)) && ok(need(&b.wp, &b.cwp, ntot, s)) &&
-            ok(need(&b.A, &b.cA, ntot, s)) && ok(need(&b.B, &b.cB, ntot, s)) &&
-            ok(need(&b.wq32, &b.cwq32, 2 * ntot, s)) && ok(need(&b.wp32, &b.cwp32, 2 * ntot, s)) &&
-            ok(need(&b.off, &b.coff, nc + 1, s)) && ok(need(&b.H, &b.cH, nc, s)) &&
-            ok(need(&b.slot0, &b.cslot0, nc, s)) && ok(need(&b.fmin, &b.cfmin, nc, s)) &&
-            ok(need(&b.qown, &b.cqown, nc, s)) && ok(need(&b.pslot0, &b.cpslot0, nc, s)) &&
-            ok(need(&b.df, &b.cdf, nc, s)) && ok(need(&b.scal, &b.cscal, (size_t)nc * SC_COUNT, s)) &&
-            ok(need(&b.out_off, &b.coo, nc, s)) && ok(need(&b.sq, &b.csq, nc, s)) &&
-            ok(need(&b.sp, &b.csp, nc, s)) && ok(need(&b.s1n, &b.cs1n, nc, s)) &&
-            ok(need(&b.chi0f, &b.cchi0f, nc, s)) && ok(need(&b.slot_cur, &b.cscur, S, s)) &&
-            ok(need(&b.slot_k, &b.csk, S, s)) && ok(need(&b.slot_kind, &b.cskind, S, s)) &&
-            ok(need(&b.slot_soff, &b.cssoff, S, s)) && ok(need(&b.slot_n, &b.csn, S, s)) &&
-            ok(need(&b.L, &b.cL, S, s)) && ok(need(&b.key, &b.ckey, slot_samples, s)) &&
-            ok(need(&b.dlt, &b.cdlt, slot_samples * tsz, s)) &&
-            ok(need(&b.cs, &b.ccs, slot_samples * csz, s)) &&
-            ok(need(&b.grid0, &b.cg0, (size_t)S * M * csz, s)) &&
-            ok(need(&b.grid1, &b.cg1, std::max((size_t)S * M * csz, sort_b + 4096), s)) &&
-            ok(need(&b.spec, &b.cspec, (size_t)S * N * csz, s)) &&
-            ok(need(&b.list, &b.cl1, (size_t)std::min<int64_t>(out_chunk, 1 << 24), s)) &&
-            ok(need(&b.list2, &b.cl2, (size_t)std::min<int64_t>(out_chunk, 1 << 22), s)) &&
-            ok(need(&b.list3, &b.cl3, (size_t)std::min<int64_t>(out_chunk, 1 << 20), s)) &&
-            ok(need(&b.list4, &b.cl4, (size_t)std::min<int64_t>(out_chunk, 1 << 20), s)) &&
+        const int64_t out_chunk = ch.out;
+        const size_t mxs = (size_t)mx.S, mxn = (size_t)mx.ntot, mxc = (size_t)mx_nc;
+        const size_t mxo = (size_t)mx.out, mxss = (size_t)mx.slot_samples;
+        ok(need(&b.perm, &b.cperm, mxn, s)) && ok(need(&b.tau, &b.ctau, mxn, s)) &&
+            ok(need(&b.wq, &b.cwq, mxn, s)) && ok(need(&b.wp, &b.cwp, mxn, s)) &&
+            ok(need(&b.A, &b.cA, mxn, s)) && ok(need(&b.B, &b.cB, mxn, s)) &&
+            ok(need(&b.wq32, &b.cwq32, 2 * mxn, s)) && ok(need(&b.wp32, &b.cwp32, 2 * mxn, s)) &&
+            ok(need(&b.off, &b.coff, mxc + 1, s)) && ok(need(&b.H, &b.cH, mxc, s)) &&
+            ok(need(&b.slot0, &b.cslot0, mxc, s)) && ok(need(&b.fmin, &b.cfmin, mxc, s)) &&
+            ok(need(&b.qown, &b.cqown, mxc, s)) && ok(need(&b.pslot0, &b.cpslot0, mxc, s)) &&
+            ok(need(&b.df, &b.cdf, mxc, s)) && ok(need(&b.scal, &b.cscal, mxc * SC_COUNT, s)) &&
+            ok(need(&b.out_off, &b.coo, mxc, s)) && ok(need(&b.sq, &b.csq, mxc, s)) &&
+            ok(need(&b.sp, &b.csp, mxc, s)) && ok(need(&b.s1n, &b.cs1n, mxc, s)) &&
+            ok(need(&b.chi0f, &b.cchi0f, mxc, s)) && ok(need(&b.slot_cur, &b.cscur, mxs, s)) &&
+            ok(need(&b.slot_k, &b.csk, mxs, s)) && ok(need(&b.slot_kind, &b.cskind, mxs, s)) &&
+            ok(need(&b.slot_soff, &b.cssoff, mxs, s)) && ok(need(&b.slot_n, &b.csn, mxs, s)) &&
+            ok(need(&b.L, &b.cL, mxs, s)) && ok(need(&b.key, &b.ckey, mxss, s)) &&
+            ok(need(&b.dlt, &b.cdlt, mxss * tsz, s)) &&
+            ok(need(&b.cs, &b.ccs, mxss * csz, s)) &&
+            ok(need(&b.grid0, &b.cg0, mx_grid, s)) &&
+            ok(need(&b.grid1, &b.cg1, std::max(mx_grid, mx_sort + 4096), s)) &&
+            ok(need(&b.spec, &b.cspec, mx_spec, s)) &&
+            ok(need(&b.list, &b.cl1, std::min<size_t>(mxo, 1 << 24), s)) &&
+            ok(need(&b.list2, &b.cl2, std::min<size_t>(mxo, 1 << 22), s)) &&
+            ok(need(&b.list3, &b.cl3, std::min<size_t>(mxo, 1 << 20), s)) &&
+            ok(need(&b.list4, &b.cl4, std::min<size_t>(mxo, 1 << 20), s)) &&
             ok(need(&b.dftab, &b.cdftab, 2 * 512 * 16, s)) &&
             ok(need(&b.qbase, &b.cqbase,
-                    std::max<size_t>({b.cl2, b.cl3, b.cl4, (size_t)std::max<int64_t>(nrec, 1)}), s)) &&
+                    std::max<size_t>({b.cl2, b.cl3, b.cl4, (size_t)std::max<int64_t>(mx_nrec, 1)}), s)) &&
             ok(need(&b.items, &b.citems, (size_t)BX_ITEMS, s)) &&
             ok(need(&b.part, &b.cpart, (size_t)BX_ITEMS * 6 * BHM, s)) &&
-            ok(need(&b.counts, &b.ccnt, 16, s)) && ok(need(&b.curves, &b.ccurves, nc, s)) &&
-            ok(need(&b.tops, &b.ctops, (size_t)nc * ((N + BP_B - 1) / BP_B) * std::max(K, 1), s)) &&
-            ok(need(&b.pent, &b.cpent, (size_t)std::max<int64_t>(nrec, 1), s)) &&
-            ok(need(&b.recs, &b.crecs, (size_t)std::max<int64_t>(nrec, 1), s));
+            ok(need(&b.counts, &b.ccnt, 16, s)) && ok(need(&b.curves, &b.ccurves, mxc, s)) &&
+            ok(need(&b.tops, &b.ctops, mx_tops, s)) &&
+            ok(need(&b.pent, &b.cpent, (size_t)std::max<int64_t>(mx_nrec, 1), s)) &&
+            ok(need(&b.recs, &b.crecs, (size_t)std::max<int64_t>(mx_nrec, 1), s));
         float* out = nullptr;
         if (dchi2 && out_dev) out = dchi2 + out_global;
-        else if (ok(need(&b.out, &b.cout, out_chunk, s))) out = b.out;
+        else if (ok(need(&b.out, &b.cout, (size_t)mx.out, s))) out = b.out;
         if (e != cudaSuccess) { st = map_cuda(e); break; }
         // ---- moments per curve, then host-side geometry
+        const auto tp0 = now();
+        b.phase_ms[1] += ms_since(tpb, tp0);
         std::vector<int64_t> offl(nc + 1);
         for (int c = 0; c <= nc; ++c) offl[c] = offsets[c0 + c] - base;
         ok(cudaMemcpyAsync(b.off, offl.data(), (nc + 1) * 8, cudaMemcpyHostToDevice, s));
@@ -1124,6 +1159,8 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         ok(cudaMemcpyAsync(scal.data(), b.scal, scal.size() * 8, cudaMemcpyDeviceToHost, s));
         ok(cudaMemcpyAsync(&status, b.counts + 8, 4, cudaMemcpyDeviceToHost, s));
         ok(cudaStreamSynchronize(s));
+        const auto tp1 = now();
+        b.phase_ms[2] += ms_since(tp0, tp1);
         if (e != cudaSuccess) { st = map_cuda(e); break; }
         if (status) { st = (fc2_status)status; break; }
         std::vector<int> Hv(nc), slot0(nc), scur, sk, skind, qownv(nc), pslotv(nc);
@@ -1226,12 +1263,16 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         const double tau_drop = opt.alias_tau > 0.0 ? opt.alias_tau : (fp64 ? 1e-9 : 1e-6);
         if (e == cudaSuccess && opt.autotune) e = autotune_fft(&p, s);
         if (e != cudaSuccess) { st = map_cuda(e); break; }
+        const auto tp2 = now();
+        b.phase_ms[3] += ms_since(tp1, tp2);
         e = launch_as_graph(b, [&]() {
             return fp64 ? chunk_launches<double>(b, nc, ntot, nmax, (int)S, hg, hoff, K, out, nrec,
                                                  tau_drop)
                         : chunk_launches<float>(b, nc, ntot, nmax, (int)S, hg, hoff, K, out, nrec,
                                                 tau_drop);
         });
+        const auto tp3 = now();
+        b.phase_ms[4] += ms_since(tp2, tp3);
         if (e != cudaSuccess) { st = map_cuda(e); break; }
         // ---- results (a list that overflowed its capacity leaves bins unrepaired)
         int32_t cnts[4] = {0, 0, 0, 0};  // re-solve, float, double-float, double lists
@@ -1241,6 +1282,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         if (peaks && K > 0)
             ok(cudaMemcpyAsync(peaks + c0 * K, b.recs, nrec * sizeof(fc2_best), cudaMemcpyDeviceToHost, s));
         ok(cudaStreamSynchronize(s));
+        b.phase_ms[5] += ms_since(tp3, now());
         if (e != cudaSuccess) { st = map_cuda(e); break; }
         if ((size_t)cnts[0] > b.cl1 || (size_t)cnts[1] > b.cl2 || (size_t)cnts[2] > b.cl3 ||
             (size_t)cnts[3] > b.cl4) {
@@ -1252,14 +1294,9 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         b.stats[2] += cnts[2];
         b.stats[3] += cnts[3];
         out_global += out_chunk;
-        c0 = c1;
     }
+    const auto t_loop_end = now();
     cudaStreamSynchronize(s);
-    if (launches_out) *launches_out = b.launches;
-    if (stats_out) {
-        for (int i = 0; i < 4; ++i) stats_out[i] = b.stats[i];
-        stats_out[4] = b.graphs;
-    }
     b.cp.d_key = nullptr; b.cp.d_dlt = nullptr; b.cp.d_cs = nullptr;
     b.cp.d_grid[0] = b.cp.d_grid[1] = nullptr; b.cp.d_spec = nullptr; b.cp.d_L = nullptr;
     b.cp.d_slot_soff = b.cp.d_slot_n = nullptr; b.cp.d_red = nullptr;
@@ -1267,6 +1304,13 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     b.free_all();
     cudaStreamSynchronize(s);
     if (b.own_stream) cudaStreamDestroy(s);
+    b.phase_ms[6] = ms_since(t_loop_end, now());
+    if (launches_out) *launches_out = b.launches;
+    if (stats_out) {
+        for (int i = 0; i < 4; ++i) stats_out[i] = b.stats[i];
+        stats_out[4] = b.graphs;
+        for (int i = 0; i < 7; ++i) std::memcpy(&stats_out[5 + i], &b.phase_ms[i], 8);
+    }
     return st;
 }
 
