@@ -738,6 +738,48 @@ __device__ __forceinline__ int64_t lower_bound_key(const int32_t* __restrict__ k
     return lo;
 }
 
+// Key ranges of every (grid, tile), found before spreading by one thread per
+// (grid, tile): for each sample set si of the grid (one, or two for a packed
+// grid) and each shift of the keys by -M, 0, +M, the lower bounds in the
+// set's sorted keys of a - w + 1 and a + TILE (a = tile start), i.e. the
+// samples whose windows meet the tile.  rng[((g ntile + tile) 2 + si) 6 + ..]
+// holds, in order, the bounds for the shifts -M (lo, hi), 0, +M.
+template <int TILE>
+__global__ void __launch_bounds__(128) k_tile_ranges(const int32_t* __restrict__ key,
+                                                     int64_t n_all, int64_t M, int w, int npk,
+                                                     int pH, int w_p,
+                                                     const int64_t* __restrict__ Lg,
+                                                     const int64_t* __restrict__ slot_soff,
+                                                     const int64_t* __restrict__ slot_n,
+                                                     int64_t ntile, int64_t* __restrict__ rng) {
+    const int g = blockIdx.y;
+    const int64_t tile = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tile >= ntile) return;
+    const int64_t a = tile * TILE;
+    if (a >= Lg[g]) return;
+    int t0 = g, nset = 1;
+    if (npk > 0) {
+        w = w_p;
+        if (g >= pH) {
+            t0 = pH + 2 * (g - pH);
+            nset = (t0 + 1 < 2 * pH) ? 2 : 1;
+        }
+    }
+    int64_t* out = rng + ((int64_t)g * ntile + tile) * 12;
+    for (int si = 0; si < nset; ++si) {
+        const int t = t0 + si;
+        const int64_t so = slot_soff ? slot_soff[t] : (int64_t)t * n_all;
+        const int64_t n = slot_n ? slot_n[t] : n_all;
+        const int32_t* kg = key + so;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const int64_t shv = (q >> 1) == 0 ? M : ((q >> 1) == 1 ? 0 : -M);
+            const int64_t v = (q & 1) ? a + TILE + shv : a - w + 1 + shv;
+            out[si * 6 + q] = lower_bound_key(kg, n, v);
+        }
+    }
+}
+
 template <typename T, int TILE, int NT, int CAP>
 __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
                                                const T* __restrict__ dlt,
@@ -747,15 +789,16 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
                                                const int64_t* __restrict__ Lg,
                                                cpx<T>* __restrict__ grid, int64_t gstride,
                                                const int64_t* __restrict__ slot_soff,
-                                               const int64_t* __restrict__ slot_n) {
+                                               const int64_t* __restrict__ slot_n,
+                                               const int64_t* __restrict__ rngtab) {
     constexpr int PER = TILE / NT;
     __shared__ int32_t sk[CAP];
     __shared__ T sd[CAP];
     __shared__ cpx<T> sc[CAP];
-    __shared__ int64_t rng[6];
     const int g = blockIdx.y;
     const int64_t a = (int64_t)blockIdx.x * TILE;
     if (a >= Lg[g]) return;
+    const int64_t* rt = rngtab + ((int64_t)g * gridDim.x + blockIdx.x) * 12;
     // sample sets of grid g: one, or (packed grids g >= H) two
     int t0 = g, nset = 1;
     if (npk > 0) {
@@ -773,39 +816,14 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
     for (int q = 0; q < PER; ++q) acc[q].init();
     for (int si = 0; si < nset; ++si) {
         const int t = t0 + si;
-        // samples of set t: [t n, (t + 1) n) or, for a batch, per-slot ranges
+        // samples of set t: from t n_all or, for a batch, from the slot's offset
         const int64_t so = slot_soff ? slot_soff[t] : (int64_t)t * n_all;
-        const int64_t n = slot_n ? slot_n[t] : n_all;
         const int32_t* kg = key + so;
         const T* dg = dlt + so;
         const cpx<T>* cg = cs + so;
-        if (threadIdx.x < 32) {
-            // ranges of keys (shifted by -M, 0, +M) whose windows meet the tile:
-            // six lower bounds at once, five lanes each; every round five probes
-            // split a group's interval [lo, hi) into six and one ballot keeps
-            // the part that holds the bound (log_6 n rounds of one load each)
-            const int lane = threadIdx.x, grp = lane / 5, sub = lane % 5;
-            const int q = grp < 6 ? grp : 5;
-            const int64_t shv = (q >> 1) == 0 ? M : ((q >> 1) == 1 ? 0 : -M);
-            const int64_t v = (q & 1) ? a + TILE + shv : a - w + 1 + shv;
-            int64_t lo = 0, hi = n;
-            while (__any_sync(0xffffffffu, grp < 6 && lo < hi)) {
-                const bool act = grp < 6 && lo < hi;
-                const int64_t len = hi - lo;
-                const int64_t pr = lo + (len * (sub + 1)) / 6;
-                const bool less = act && (int64_t)kg[pr] < v;
-                const unsigned m = __ballot_sync(0xffffffffu, less);
-                const int c = __popc((m >> (5 * q)) & 31u);
-                if (act) {
-                    const int64_t nlo = (c == 0) ? lo : lo + (len * c) / 6 + 1;
-                    const int64_t nhi = (c == 5) ? hi : lo + (len * (c + 1)) / 6;
-                    lo = nlo;
-                    hi = nhi;
-                }
-            }
-            if (grp < 6 && sub == 0) rng[grp] = lo;
-        }
-        __syncthreads();
+        int64_t rng[6];  // key ranges of the shifts -M, 0, +M (k_tile_ranges)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) rng[q] = rt[si * 6 + q];
         const int64_t c0 = rng[1] - rng[0], c1 = rng[3] - rng[2], c2 = rng[5] - rng[4];
         const int64_t total = c0 + c1 + c2;
         for (int64_t cb = 0; cb < total; cb += CAP) {
@@ -837,7 +855,6 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
             }
             __syncthreads();
         }
-        __syncthreads();  // rng is rewritten for the next set
     }
     cpx<T>* gg = grid + (int64_t)g * gstride + a;
 #pragma unroll
@@ -852,10 +869,17 @@ static cudaError_t spread_tiles(fc2_plan_s* p, cudaStream_t s) {
     int64_t Lmax = 0;
     for (auto& g : p->geom) Lmax = g.L > Lmax ? g.L : Lmax;
     int64_t tiles = (Lmax + TILE - 1) / TILE;
+    // the tile table (12 bounds per tile, at most 12 M / TILE bytes per grid)
+    // lives in the second grid buffer, which is free until the transform
+    int64_t* rngtab = reinterpret_cast<int64_t*>(p->d_grid[1]);
+    dim3 gt((unsigned)((tiles + 127) / 128), (unsigned)p->G);
+    k_tile_ranges<TILE><<<gt, 128, 0, s>>>(p->d_key, p->n, p->M, p->w, p->npk, p->H, p->w_p, p->d_L,
+                                           p->d_slot_soff, p->d_slot_n, tiles, rngtab);
     dim3 grid((unsigned)tiles, (unsigned)p->G);
     k_spread<T, TILE, NT, CAP><<<grid, NT, 0, s>>>(
         p->d_key, (const T*)p->d_dlt, (const cpx<T>*)p->d_cs, p->n, p->M, p->w, (T)p->beta,
-        p->npk, p->H, p->w_p, (T)p->beta_p, p->d_L, (cpx<T>*)p->d_grid[0], p->M, p->d_slot_soff, p->d_slot_n);
+        p->npk, p->H, p->w_p, (T)p->beta_p, p->d_L, (cpx<T>*)p->d_grid[0], p->M, p->d_slot_soff,
+        p->d_slot_n, rngtab);
     return cudaGetLastError();
 }
 
