@@ -166,13 +166,17 @@ __global__ void __launch_bounds__(128) k_bassemble(const cpx<TS>* __restrict__ s
 }
 
 constexpr double BX_EPS_DF = 1.5e-12;  // relative precision of the tier-2 (double-float) sums
+// relative pivot of the gridded equations below which an entry is taken as
+// nearly singular and starts at the double tier
+constexpr double BX_DMIN_T3 = 1e-7;
 
 // Double re-solve of listed (curve, bin) entries of the float path.  Entries
 // still too sensitive go on to the exact sums: to the float tier, straight to
 // the double-float tier when the float sums could not settle them either
 // (error estimate at the float sums' precision above the bar, or a small
 // relative pivot), or straight to the double tier when the coefficient norm
-// is beyond the double-float sums as well.
+// is beyond the double-float sums as well or the pivot is below what the
+// gridded equations resolve.
 template <int HM>
 __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__ spec,
                                                   const float* __restrict__ dec, int64_t N,
@@ -223,7 +227,7 @@ __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__
         if ((threadIdx.x & 31) == 0) {
             const int m = 2 * H + 1;
             if (!(est_err<double>(an2, m, eps) <= err_fix)) {
-                if (!(est_err<double>(an2, m, BX_EPS_DF) <= err_fix)) {
+                if (!(est_err<double>(an2, m, BX_EPS_DF) <= err_fix) || dmin < BX_DMIN_T3) {
                     const int32_t pos = atomicAdd(fcount3, 1);
                     if (pos < fcap3) flist3[pos] = rlist[b];
                 } else if (!(est_err<double>(an2, m, 2e-7 * sc[SC_RW]) <= err_fix) || dmin < 3e-3) {

@@ -176,6 +176,11 @@ __global__ void __launch_bounds__(128) k_assemble(const cpx<TS>* __restrict__ sp
     for (int h = 0; h < H; ++h) dchi2[(int64_t)h * sp.N + j] = to_double(out[h] * q.chi0);
 }
 
+// Relative pivot of the gridded equations (float spectra, entries good to
+// about 1e-7) below which a bin is taken as nearly singular and its exact
+// sums start at the double tier.
+constexpr double DMIN_T3 = 1e-7;
+
 // Double re-solve of float-path bins; bins still too sensitive go on to the
 // exact fix-up list.
 template <int H>
@@ -214,14 +219,13 @@ __global__ void __launch_bounds__(128) k_resolve(const cpx<float>* __restrict__ 
                 // small relative pivot (columns this solve drops come back with
                 // large coefficients in the exact solve) -- start at the
                 // double-float tier, and bins whose coefficient norm is beyond
-                // the double-float sums too start at the double tier.  A small
-                // pivot alone does not send a bin to the double tier: the
-                // gridded equations cannot resolve pivots near the double-float
-                // sums' precision.  Each tier checks its own result and passes
-                // bins on.
+                // the double-float sums too, or whose relative pivot is already
+                // below what these equations resolve (DMIN_T3), start at the
+                // double tier.  Each tier checks its own result and passes bins
+                // on.
                 const int m = 2 * H + 1;
                 int32_t *lst = flist, *cnt = fcount;
-                if (!(est_err<double>(an2, m, sp.eps_t2) <= sp.err_fix)) {
+                if (!(est_err<double>(an2, m, sp.eps_t2) <= sp.err_fix) || dmin < DMIN_T3) {
                     lst = flist3;
                     cnt = fcount3;
                 } else if (!(est_err<double>(an2, m, sp.eps_t1) <= sp.err_fix) || dmin < 3e-3) {
@@ -257,13 +261,17 @@ constexpr int EX_NT = 256;
 constexpr int EX_GRID = 4 * 152;
 constexpr int EX_MAX_CHUNKS = 64;
 
-// Chunks of the sample range for `count` bins: about two work items per CTA
-// of the EX_GRID-CTA grid, at least 16 samples per thread, at most
-// EX_MAX_CHUNKS chunks.  Evaluated identically on host and device, so kernels
-// that read the bin count from device memory derive the same geometry.
+// Chunks of the sample range of each bin (at least 16 samples per thread, at
+// most EX_MAX_CHUNKS).  While the bins do not outnumber the EX_GRID CTAs, the
+// chunk count is rounded down so that no CTA gets more than two items (a
+// third item on a few CTAs stretches the launch by one item time); with more
+// bins than CTAs, each bin is cut as finely as allowed, so that the
+// grid-stride loop hands every SM about the same share of small items.
+// Evaluated identically on host and device, so kernels that read the bin
+// count from device memory derive the same geometry.
 FC2_HD void exact_geometry(int64_t n, int64_t count, int64_t* chunk, int* nch) {
     if (count < 1) count = 1;
-    int64_t want = (2 * EX_GRID + count - 1) / count;
+    int64_t want = count <= EX_GRID ? (2 * EX_GRID) / count : EX_MAX_CHUNKS;
     if (want > EX_MAX_CHUNKS) want = EX_MAX_CHUNKS;
     int64_t c = (n + want - 1) / want;
     if (c < 16 * EX_NT) c = 16 * EX_NT;
