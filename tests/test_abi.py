@@ -126,3 +126,25 @@ def test_product_path_does_not_use_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "fc2_oracle" not in txt and "fc2o_" not in txt, f
+
+
+def test_batch_peak_records_layout_and_access():
+    """The structured record type matches fc2_best byte for byte, and the
+    batched peaks convert per curve, on access, to the single-curve dicts."""
+    from paper_0901_1913_gb300 import _fc2
+    assert _fc2.BEST_DTYPE.itemsize == ctypes.sizeof(_fc2.Best)
+    for name, *_ in _fc2.Best._fields_:
+        assert _fc2.BEST_DTYPE.fields[name][1] == getattr(_fc2.Best, name).offset, name
+    rec = np.zeros((3, 2), dtype=_fc2.BEST_DTYPE)
+    rec[1, 0]["j"], rec[1, 0]["f"], rec[1, 0]["dchi2"], rec[1, 0]["H"] = 7, 0.25, 3.5, 2
+    rec[1, 0]["A"][:6] = [1, 2, 3, 4, 5, 6]
+    # the same bytes read as the ctypes structure give the same dict
+    ref = _fc2.Best.from_buffer_copy(rec[1, 0].tobytes()).as_dict()
+    peaks = _fc2.BatchPeaks(rec)
+    assert len(peaks) == 3 and [len(p) for p in peaks] == [2, 2, 2]
+    got = peaks[1][0]
+    assert {k: got[k] for k in ("j", "f", "dchi2", "H", "flags")} == \
+        {k: ref[k] for k in ("j", "f", "dchi2", "H", "flags")}
+    np.testing.assert_array_equal(got["A"], ref["A"])
+    assert got["A"].tolist() == [1, 2, 3, 4, 5]  # 2H + 1 coefficients
+    assert [p[0]["j"] for p in peaks[0:3:2]] == [0, 0]
