@@ -51,7 +51,7 @@ typedef enum {
     FC2_ERR_CUDA = 2,          /* a CUDA runtime call failed */
     FC2_ERR_OOM = 3,           /* device allocation failed or the plan exceeds device memory */
     FC2_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up */
-    FC2_ERR_UNSUPPORTED = 5,   /* valid request this build does not implement */
+    FC2_ERR_UNSUPPORTED = 5,   /* valid request the library does not implement */
     FC2_ERR_NUMERIC = 6        /* non-finite intermediate (e.g. overflow in the solve) */
 } fc2_status;
 
