@@ -81,10 +81,16 @@ __global__ void k_bgather(const double* __restrict__ t, const double* __restrict
 
 // ----------------------------------------------------------- phase reduction
 // As the single-curve k_phase, per slot: the slot's curve, multiple k and
-// kind select the samples and the strengths.
+// kind select the samples and the strengths.  The band-centre modulation
+// e^{2 pi i k f_c tau}, f_c = f_min + (N/2) df, has the exact fixed-point
+// phase k (A + (N/2) B) mod 2^64 (A, B the sample's phases of f_min and df);
+// in the float path its phasor comes from the double-float tables on the
+// float pipes (well below float rounding), in the double path from sincospi.
 template <typename T>
 __global__ void k_bphase(const double* __restrict__ tau, const double* __restrict__ wq,
-                         const double* __restrict__ wp, const int64_t* __restrict__ off,
+                         const double* __restrict__ wp, const uint64_t* __restrict__ Aph,
+                         const uint64_t* __restrict__ Bph, const dfc* __restrict__ dftab,
+                         const int64_t* __restrict__ off,
                          const double* __restrict__ fmin, const double* __restrict__ df,
                          int64_t N, int64_t M, int w, const int* __restrict__ slot_cur,
                          const int* __restrict__ slot_k, const int* __restrict__ slot_kind,
@@ -104,11 +110,19 @@ __global__ void k_bphase(const double* __restrict__ tau, const double* __restric
     const double Xs = __dsub_rn(X, 0.5 * (double)w);
     const double fl = floor(Xs);
     const double de = __dsub_rn(Xs, fl);
-    const double q1 = __dmul_rn(__dmul_rn((double)k, fmin[c]), ts);
-    const double q2 = __dmul_rn((double)(N / 2), u);
-    const double th = __dadd_rn(__dsub_rn(q1, floor(q1)), __dsub_rn(q2, floor(q2)));
     double sn, cn;
-    sincospi(2.0 * th, &sn, &cn);
+    if constexpr (sizeof(T) == 4) {
+        const uint64_t kk = (uint64_t)k;
+        const uint64_t th = kk * Aph[a + s] + (uint64_t)(N / 2) * (kk * Bph[a + s]);
+        const dfc z = df_phasor(th, dftab, dftab + 256);
+        cn = (double)z.re.h + (double)z.re.l;
+        sn = (double)z.im.h + (double)z.im.l;
+    } else {
+        const double q1 = __dmul_rn(__dmul_rn((double)k, fmin[c]), ts);
+        const double q2 = __dmul_rn((double)(N / 2), u);
+        const double th = __dadd_rn(__dsub_rn(q1, floor(q1)), __dsub_rn(q2, floor(q2)));
+        sincospi(2.0 * th, &sn, &cn);
+    }
     const double amp = kind == 0 ? wq[a + s] : wp[a + s];
     const int64_t o = slot_soff[g] + s;
     key[o] = (int32_t)fl + 1;
@@ -829,7 +843,8 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
     if (e != cudaSuccess) return e;
     ++nl;
     dim3 gph((unsigned)((nmax + 255) / 256), (unsigned)S);
-    k_bphase<T><<<gph, 256, 0, s>>>(b.tau, b.wq, b.wp, b.off, b.fmin, b.df, N, p.M, p.w,
+    k_bphase<T><<<gph, 256, 0, s>>>(b.tau, b.wq, b.wp, b.A, b.B, (const dfc*)b.dftab, b.off,
+                                    b.fmin, b.df, N, p.M, p.w,
                                     b.slot_cur, b.slot_k, b.slot_kind, b.slot_soff, b.key,
                                     (T*)b.dlt, (cpx<T>*)b.cs);
     ++nl;
