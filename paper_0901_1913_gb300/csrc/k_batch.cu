@@ -269,8 +269,10 @@ __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__
 // k_bx_split numbers the items in entry order, k_bx_part sums each item with
 // one warp (lanes at stride 32, then a butterfly) into a row of partial sums,
 // and k_bexact adds an entry's rows in item order, solves and routes.  Entries
-// beyond the item capacity are summed whole by k_bexact.  Every order is
-// fixed, so results do not depend on scheduling.
+// beyond the item capacity are summed whole by k_bexact.  An entry's items and
+// their summation order depend only on its curve, so its result does not
+// depend on where the entry sits in the (atomically filled) list -- unless the
+// list overflows the item capacity, when which entries are summed whole does.
 // MODE 0 writes Delta chi^2 (float) and passes on to `next` the entries whose
 // error estimate from the coefficient norm, or whose smallest relative pivot,
 // is beyond what the tier's sums can vouch for.  MODE 1 writes coefficient
