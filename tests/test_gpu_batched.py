@@ -128,3 +128,42 @@ def test_batched_kernel_families_agree(fc2, oracle_mod, fft_kernel):
             _, _, chi0, _ = oracle_mod.moments(cur.x, cur.sigma)
             assert np.max(np.abs(out[blk] - ref[blk])) <= 2e-5 * chi0, (fft_kernel, N, c)
 
+
+
+def test_long_and_short_curves_in_one_batch(fc2, oracle_mod):
+    """A batch mixing a 2e5-sample curve (its exact-sum entries cut into the
+    most work items an entry may have) with short ones: every curve, and its
+    own one-curve plan, agree with the oracle on the first bins (periods
+    longer than the span, whose entries need the double tier), around the
+    yearly alias and on random bins.  (Near-alias bins are only bounds-checked:
+    there the batch and the one-curve plan may differ by more than the
+    tolerance and both be right.)"""
+    N = 1 << 14
+    curves = [synth.long_curve(n=200_000, N=N, H=4, T=3000.0, f_max=0.5),
+              synth.long_curve(seed=5, n=400, N=N, H=4, T=3000.0, f_max=0.5),
+              synth.long_curve(seed=6, n=3000, N=N, H=4, T=3000.0, f_max=0.5)]
+    offsets = np.concatenate([[0], np.cumsum([c.n for c in curves])]).astype(np.int64)
+    cat = lambda name: np.concatenate([getattr(c, name) for c in curves])
+    H = np.array([c.H for c in curves], dtype=np.int32)
+    fmin = np.array([c.f_min for c in curves])
+    df = np.array([c.df for c in curves])
+    Ns = np.full(len(curves), N, dtype=np.int64)
+    out, peaks, stats = fc2.execute_batched(offsets, cat("t"), cat("x"), cat("sigma"), H, fmin, df,
+                                            Ns, 2, "mixed", top_k=4)
+    assert stats["exact_double"] > 0  # the near-singular entries reached the double tier
+    pos = 0
+    for i, c in enumerate(curves):
+        block = out[pos:pos + c.H * N].reshape(c.H, N).astype(np.float64)
+        pos += c.H * N
+        d, _, _, chi0 = fc2.periodogram(c.t, c.x, c.sigma, c.H, c.f_min, c.df, N, 2, "mixed")
+        yearly = int(round((1.0 / 365.25 - c.f_min) / c.df))
+        bins = np.unique(np.concatenate([np.arange(0, 40), np.arange(yearly - 10, yearly + 11),
+                                         sample_bins(N, 40, i)]))
+        ref, piv = oracle_mod.dchi2_bins(c.t, c.x, c.sigma, c.H, c.f_min, c.df, bins,
+                                         with_pivots=True)
+        r = compare(block[:, bins].T, ref, piv, chi0)
+        assert r["ok"], (i, r)
+        r1 = compare(d[:, bins].T, ref, piv, chi0)
+        assert r1["ok"], (i, r1)
+    assert pos == out.size
+    assert len(peaks) == len(curves) and all(len(p) == 4 for p in peaks)
