@@ -739,11 +739,11 @@ __device__ __forceinline__ int64_t lower_bound_key(const int32_t* __restrict__ k
 }
 
 // Key ranges of every (grid, tile), found before spreading by one thread per
-// (grid, tile): for each sample set si of the grid (one, or two for a packed
-// grid) and each shift of the keys by -M, 0, +M, the lower bounds in the
-// set's sorted keys of a - w + 1 and a + TILE (a = tile start), i.e. the
-// samples whose windows meet the tile.  rng[((g ntile + tile) 2 + si) 6 + ..]
-// holds, in order, the bounds for the shifts -M (lo, hi), 0, +M.
+// (grid, tile, bound): for each sample set si of the grid (one, or two for a
+// packed grid) and each shift of the keys by -M, 0, +M, the lower bounds in
+// the set's sorted keys of a - w + 1 and a + TILE (a = tile start), i.e. the
+// samples whose windows meet the tile.  rng[((g ntile + tile) 2 + si) 6 + q]:
+// q = 0..5 the bounds for the shifts -M (lo, hi), 0, +M.
 template <int TILE>
 __global__ void __launch_bounds__(128) k_tile_ranges(const int32_t* __restrict__ key,
                                                      int64_t n_all, int64_t M, int w, int npk,
@@ -753,7 +753,9 @@ __global__ void __launch_bounds__(128) k_tile_ranges(const int32_t* __restrict__
                                                      const int64_t* __restrict__ slot_n,
                                                      int64_t ntile, int64_t* __restrict__ rng) {
     const int g = blockIdx.y;
-    const int64_t tile = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tile = idx / 12;
+    const int sq = (int)(idx - tile * 12), si = sq / 6, q = sq - si * 6;
     if (tile >= ntile) return;
     const int64_t a = tile * TILE;
     if (a >= Lg[g]) return;
@@ -765,19 +767,13 @@ __global__ void __launch_bounds__(128) k_tile_ranges(const int32_t* __restrict__
             nset = (t0 + 1 < 2 * pH) ? 2 : 1;
         }
     }
-    int64_t* out = rng + ((int64_t)g * ntile + tile) * 12;
-    for (int si = 0; si < nset; ++si) {
-        const int t = t0 + si;
-        const int64_t so = slot_soff ? slot_soff[t] : (int64_t)t * n_all;
-        const int64_t n = slot_n ? slot_n[t] : n_all;
-        const int32_t* kg = key + so;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            const int64_t shv = (q >> 1) == 0 ? M : ((q >> 1) == 1 ? 0 : -M);
-            const int64_t v = (q & 1) ? a + TILE + shv : a - w + 1 + shv;
-            out[si * 6 + q] = lower_bound_key(kg, n, v);
-        }
-    }
+    if (si >= nset) return;
+    const int t = t0 + si;
+    const int64_t so = slot_soff ? slot_soff[t] : (int64_t)t * n_all;
+    const int64_t n = slot_n ? slot_n[t] : n_all;
+    const int64_t shv = (q >> 1) == 0 ? M : ((q >> 1) == 1 ? 0 : -M);
+    const int64_t v = (q & 1) ? a + TILE + shv : a - w + 1 + shv;
+    rng[((int64_t)g * ntile + tile) * 12 + sq] = lower_bound_key(key + so, n, v);
 }
 
 template <typename T, int TILE, int NT, int CAP>
@@ -872,7 +868,7 @@ static cudaError_t spread_tiles(fc2_plan_s* p, cudaStream_t s) {
     // the tile table (12 bounds per tile, at most 12 M / TILE bytes per grid)
     // lives in the second grid buffer, which is free until the transform
     int64_t* rngtab = reinterpret_cast<int64_t*>(p->d_grid[1]);
-    dim3 gt((unsigned)((tiles + 127) / 128), (unsigned)p->G);
+    dim3 gt((unsigned)((tiles * 12 + 127) / 128), (unsigned)p->G);
     k_tile_ranges<TILE><<<gt, 128, 0, s>>>(p->d_key, p->n, p->M, p->w, p->npk, p->H, p->w_p, p->d_L,
                                            p->d_slot_soff, p->d_slot_n, tiles, rngtab);
     dim3 grid((unsigned)tiles, (unsigned)p->G);
