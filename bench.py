@@ -1,18 +1,26 @@
 #!/usr/bin/env python
 """Benchmark of the Fchi2 periodogram hot path on one GB300 per rank.
 
-Workload (the long single-curve case): n = 100,000 samples over 3000 d with a
-seasonal window and nightly cadence, an 8-harmonic sawtooth signal, H = 6,
-N = 2^22 trial frequencies up to 20 /d, grids oversampled 4x.  Inputs are
-seeded synthetic curves (seed 2 + rank); every grid is larger than L2.
+Headline workload (default): the batched survey -- 4096 light curves of
+n ~ lognormal(median 2000) samples in [50, 20000] over 1000 d with seasonal
+and nightly sampling, H in 2..6 harmonics, N = 2^18 trial frequencies up to
+12 /d per curve, 30% pure-noise curves, grids oversampled 2x.  Inputs are
+seeded synthetic curves; every chunk's grids (GBs) are larger than L2.
 
-One step = fc2_execute on resident inputs: phase reduction, spreading, FFTs,
-assembly and bordered Cholesky for all H' = 1..H, exact fix-up of sensitive
-bins, peaks and coefficients.  The metric counts one evaluation per
-(trial frequency, H').
+One step = fc2_execute_batched over the whole survey on device-resident
+inputs: per curve the moments, phase reduction, spreading, FFTs, assembly and
+bordered Cholesky for every H' = 1..H, the exact fix-up of sensitive bins,
+and the top-8 peaks with coefficients.  The metric counts one evaluation per
+(trial frequency, H').  Under torchrun each rank takes a contiguous range of
+a survey of 4096 x (ranks) curves (balanced by n_c + H_c N_c; no collective on
+the data path), so the work per GPU stays fixed.
+
+The same line carries sub-records of the long single curve (n = 10^5,
+N = 2^22, H = 6) and the large single curve (n ~ 10^6, N = 2^26, H = 8): mixed
+and FP64 rates, their ratio, stage times and oracle parity on sampled bins.
 
 --impl reference times the CPU oracle (direct sums + Householder least
-squares per bin) on a bounded sample of the same workload.
+squares per bin) on a bounded sample of the same survey.
 """
 from __future__ import annotations
 
@@ -32,8 +40,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Delta-chi2 evals/s (freq x H') at 1e-4*chi2_0, mixed vs FP64; % HBM peak"
 UNIT = "evals/s"
-WORKLOAD = "long single curve: n=100000, T=3000 d seasonal+nightly, sawtooth 8 harmonics, " \
-           "H=6, N=2^22 to 20/d, 4x oversampled grids"
+SURVEY = ("batched survey: 4096 curves per GPU, n ~ lognormal(median 2000) in [50, 20000], "
+          "seasonal/nightly sampling over 1000 d, H in 2..6, N=2^18 to 12/d, 30% nulls, "
+          "2x oversampled grids")
+LONG = ("long single curve: n=100000, T=3000 d seasonal+nightly, sawtooth 8 harmonics, "
+        "H=6, N=2^22 to 20/d, 4x oversampled grids")
+LARGE = ("large single curve: n~1e6 at 2-min cadence over 4 yr, H=8, N=2^26 to 24/d, "
+         "2x oversampled grids")
+# Algorithmic bytes per evaluation (mixed precision): each trial frequency needs
+# 3H float-complex spectrum values (Q at k = 1..2H, P at k = 1..H) written by the
+# transforms and read by the assembly (2 x 24 B per (f, H')), and one float
+# output per (f, H').
+B_ALG = 52.0
+B_FFT = 24.0    # the transforms' share: the kept spectra written
 
 
 def dist_init():
@@ -47,6 +66,8 @@ def dist_init():
             import torch
             if not torch.cuda.is_available():
                 backend = "gloo"
+            else:
+                torch.cuda.set_device(local)
         except Exception:
             backend = "gloo"
         dist.init_process_group(backend=backend)
@@ -74,6 +95,15 @@ def allreduce_max(ws, v):
     return float(t.item())
 
 
+def allgather(ws, obj):
+    if ws == 1:
+        return [obj]
+    import torch.distributed as dist
+    out = [None] * ws
+    dist.all_gather_object(out, obj)
+    return out
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -81,6 +111,20 @@ def load_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def profile_record(name):
+    """key=value lines of a committed profile summary, or {} when missing or
+    taken on other kernel sources than the ones built (its kernel_version)."""
+    try:
+        import importlib
+        ver = importlib.import_module("paper_0901_1913_gb300.build").sources_version()
+        with open(os.path.join(ROOT, "profiles", name)) as fh:
+            kv = dict(ln.strip().split("=", 1) for ln in fh
+                      if "=" in ln and not ln.startswith("#"))
+        return kv if kv.get("kernel_version") == ver else {}
+    except Exception:
+        return {}
 
 
 class ClockSampler:
@@ -162,207 +206,409 @@ def oracle_sample(c, bins, threads):
     return d, piv, time.perf_counter() - t0
 
 
-def sample_bins_for(c, n_random, seed, extra=()):
+def sample_bins_for(c, n_random, seed, extra=(), half=8):
     from tests.parity import sample_bins
     f0 = c.truth.get("f0", 1.0)
     cen = [int(round((f0 - c.f_min) / c.df)), int(round((2 * f0 - c.f_min) / c.df)),
            int(round((f0 / 2 - c.f_min) / c.df)), int(round((1.0 - c.f_min) / c.df))]
     cen += [int(j) for j in extra]
-    return sample_bins(c.N, n_random, seed, windows=cen, half=8)
+    return sample_bins(c.N, n_random, seed, windows=cen, half=half)
+
+
+def survey_for_rank(ws, rank):
+    """This rank's curves of a survey of 4096 x ws curves: (batch slice as a
+    synth.Batch-like namespace, (c_a, c_b))."""
+    from types import SimpleNamespace
+
+    from paper_0901_1913_gb300 import shard, synth
+    full = synth.survey_batch(C=4096 * ws)
+    cost = np.diff(full.offsets) + full.H.astype(np.float64) * full.N
+    ca, cb = shard.curve_partition(cost, ws)[rank]
+    off, (t, x, sg), (H, fm, df, N) = shard.curve_slice(full.offsets, (full.t, full.x, full.sigma),
+                                                        (full.H, full.f_min, full.df, full.N),
+                                                        (ca, cb))
+    b = SimpleNamespace(offsets=off, t=np.ascontiguousarray(t), x=np.ascontiguousarray(x),
+                        sigma=np.ascontiguousarray(sg), H=np.ascontiguousarray(H),
+                        f_min=np.ascontiguousarray(fm), df=np.ascontiguousarray(df),
+                        N=np.ascontiguousarray(N), oversample=full.oversample,
+                        truth=full.truth[ca:cb], C=cb - ca)
+    b.curve = lambda c: synth.Curve(b.t[off[c]:off[c + 1]], b.x[off[c]:off[c + 1]],
+                                    b.sigma[off[c]:off[c + 1]], int(b.H[c]), float(b.f_min[c]),
+                                    float(b.df[c]), int(b.N[c]), b.oversample, b.truth[c])
+    return b, (ca, cb)
 
 
 def run_reference(args):
+    """The oracle as it stands, timed on the host cores on a bounded sample of
+    the survey: each step evaluates ref_bins random trial frequencies (every
+    H') on each of 4 curves spread over the batch."""
     ws, rank, local = dist_init()
     if rank != 0:
         return
     from paper_0901_1913_gb300 import synth
-    c = synth.long_curve(seed=2)
+    b = synth.survey_batch()
     threads = os.cpu_count() or 1
-    per_step = max(threads, args.ref_bins)
+    picks = [0, b.C // 4, b.C // 2, 3 * b.C // 4]
     rng = np.random.default_rng(7)
-    times = []
+    times, evals = [], 0
     for it in range(args.warmup + args.steps):
-        bins = np.sort(rng.choice(c.N, size=per_step, replace=False))
-        _, _, dt = oracle_sample(c, bins, threads)
+        t0 = time.perf_counter()
+        ne = 0
+        for ci in picks:
+            c = b.curve(ci)
+            bins = np.sort(rng.choice(c.N, size=max(1, args.ref_bins), replace=False))
+            oracle_sample(c, bins, threads)
+            ne += bins.size * c.H
         if it >= args.warmup:
-            times.append(dt)
+            times.append(time.perf_counter() - t0)
+            evals += ne
     ms = 1e3 * sum(times) / len(times)
-    value = per_step * c.H / (ms / 1e3)
+    value = evals / sum(times)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (host)"},
+        "data": "synthetic", "config": {"workload": SURVEY, "l2": "n/a (host)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{per_step} random trial frequencies x H'=1..6 per step"},
+                         "sample": f"{args.ref_bins} random trial frequencies x H'=1..H_c on each "
+                                   f"of curves {picks} per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def run_gpu(args):
+def survey_parity(b, got_block, best_j, threads, seconds, n_curves=64, max_bins=1024):
+    """The oracle on n_curves curves spread over the batch: per curve up to
+    max_bins random trial frequencies plus +-8-bin windows at f0, 2 f0, f0/2,
+    1 /d and the GPU's best bin of row H, sized so the whole sample takes about
+    `seconds` on the host cores.  Returns (parity dict, cpu_baseline dict)."""
+    from oracle import oracle
+    from tests.parity import argmax_ok, compare
+    idx = np.unique(np.linspace(0, b.C - 1, n_curves).astype(int))
+    # oracle cost per bin ~ n_c H_c^3: probe it on one curve
+    c0 = b.curve(int(idx[0]))
+    probe = np.arange(0, c0.N, c0.N // (4 * threads))[:4 * threads]
+    _, _, dt = oracle_sample(c0, probe, threads)
+    per_unit = dt / (probe.size * c0.n * c0.H ** 3)
+    units = sum(b.curve(int(c)).n * int(b.H[c]) ** 3 for c in idx)
+    nb = int(max(16, min(max_bins, seconds / max(per_unit * units, 1e-12))))
+    errs, near, nbins, nev, t_or, arg_ok = [], 0, 0, 0, 0.0, 0
+    for c in idx:
+        cur = b.curve(int(c))
+        bins = sample_bins_for(cur, nb, int(c), extra=[best_j[c]])
+        d_or, piv, dt = oracle_sample(cur, bins, threads)
+        t_or += dt
+        blk = got_block(int(c))
+        _, _, chi0, _ = oracle.moments(cur.x, cur.sigma)
+        r = compare(blk[:, bins].T.astype(np.float64), d_or, piv, chi0)
+        errs.append(r)
+        near += r["n_near_alias"]
+        nbins += bins.size
+        nev += bins.size * cur.H
+        jo = int(bins[np.argmax(d_or[:, -1])])
+        arg_ok += int(argmax_ok(int(best_j[c]), jo, d_or[:, -1], chi0, bins))
+    parity = {"curves": int(idx.size), "bins": nbins, "evals": nev,
+              "random_bins_per_curve": nb,
+              "max_err_rel": max(e["max_err_rel"] for e in errs),
+              "near_alias_entries": near,
+              "argmax_ok": f"{arg_ok}/{idx.size}",
+              "ok": bool(all(e["ok"] for e in errs) and arg_ok == idx.size)}
+    cpu = {"value": nev / t_or, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{nbins} trial frequencies x H'=1..H_c on {idx.size} curves spread over the "
+                     f"batch ({nb} random per curve + windows at f0, 2f0, f0/2, 1/d and the "
+                     f"GPU's best bin)", "seconds": t_or}
+    return parity, cpu
+
+
+def single_curve_record(c, args, threads, n_random, half, mixed_steps, fp64_steps, windows):
+    """Mixed and FP64 rates of one curve (CUDA events on the plan's stream),
+    stage times, and oracle parity on sampled bins."""
+    import torch
+    from paper_0901_1913_gb300 import _fc2
+    from tests.parity import compare, sample_bins
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    out = torch.empty((c.H, c.N), dtype=torch.float64, device=dev)
+    res = {}
+    for prec, steps in (("mixed", mixed_steps), ("fp64", fp64_steps)):
+        with _fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, prec,
+                       stream=stream.cuda_stream, device=dev.index) as p:
+            p.execute(out)
+            torch.cuda.synchronize()
+            p.stage_timing(True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                p.execute(out, want_records=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            stage, nl, _ = p.stage_times()
+            p.stage_timing(False)
+            _, best, _, chi0 = p.execute(out)
+            res[prec] = dict(ms=e0.elapsed_time(e1) / steps, d=out.cpu().numpy(), best=best,
+                             chi0=chi0, stage=[round(float(v), 4) for v in stage],
+                             counts=list(p.counts), launches=nl)
+    evals = c.N * c.H
+    bins = sample_bins(c.N, n_random, 11, windows=list(windows) + [res["mixed"]["best"][-1]["j"]],
+                       half=half)
+    from oracle import oracle
+    t0 = time.perf_counter()
+    d_or, piv = oracle.dchi2_bins(c.t, c.x, c.sigma, c.H, c.f_min, c.df, bins, threads=threads,
+                                  with_pivots=True)
+    dt = time.perf_counter() - t0
+    chi0 = res["fp64"]["chi0"]
+    rm = compare(res["mixed"]["d"][:, bins].T, d_or, piv, chi0)
+    r6 = compare(res["fp64"]["d"][:, bins].T, d_or, piv, chi0)
+    names = ["spread", "fft", "assemble", "fixup", "peaks"]
+    return {
+        "n": c.n, "N": c.N, "H": c.H, "oversample": c.oversample,
+        "mixed": {"value": evals / (res["mixed"]["ms"] / 1e3), "ms_per_step": res["mixed"]["ms"],
+                  "steps": mixed_steps, "stage_ms": dict(zip(names, res["mixed"]["stage"])),
+                  "bins_resolved_double": res["mixed"]["counts"][0],
+                  "bins_exact_sums": res["mixed"]["counts"][1],
+                  "bins_through_tiers_2_3": res["mixed"]["counts"][2:4]},
+        "fp64": {"value": evals / (res["fp64"]["ms"] / 1e3), "ms_per_step": res["fp64"]["ms"],
+                 "steps": fp64_steps, "stage_ms": dict(zip(names, res["fp64"]["stage"]))},
+        "mixed_over_fp64": res["fp64"]["ms"] / res["mixed"]["ms"],
+        "parity": {"bins": int(bins.size), "mixed_max_err_rel": rm["max_err_rel"],
+                   "fp64_max_err_rel": r6["max_err_rel"], "near_alias_bins": rm["n_near_alias"],
+                   "ok": bool(rm["ok"] and r6["ok"])},
+        "oracle": {"value": bins.size * c.H / dt, "unit": UNIT, "cores": threads,
+                   "seconds": dt},
+    }
+
+
+def run_survey(args):
     ws, rank, local = dist_init()
     import torch
     from paper_0901_1913_gb300 import _fc2, synth
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    c = synth.long_curve(seed=2 + rank)
+    b, (ca, cb) = survey_for_rank(ws, rank)
+    evals = int(np.sum(b.H.astype(np.int64) * b.N))
+    K = 8
     stream = torch.cuda.Stream(device=dev)
-    evals = c.N * c.H
+    pos = np.concatenate([[0], np.cumsum(b.H.astype(np.int64) * b.N)])
 
-    def make_plan(prec, t=c.t, x=c.x, s=c.sigma):
-        return _fc2.Plan(t, x, s, c.H, c.f_min, c.df, c.N, c.oversample, prec,
-                         stream=stream.cuda_stream, device=local, fft_kernel=args.fft_kernel,
-                         fft_group=args.fft_group)
+    def call(t, x, s, out, prec="mixed", sub=None):
+        off, H, fm, df, N = b.offsets, b.H, b.f_min, b.df, b.N
+        if sub is not None:
+            off, H, fm, df, N = off[:sub + 1], H[:sub], fm[:sub], df[:sub], N[:sub]
+            t, x, s = t[:int(off[-1])], x[:int(off[-1])], s[:int(off[-1])]
+        return _fc2.execute_batched(off, t, x, s, H, fm, df, N, b.oversample, prec, top_k=K,
+                                    dchi2=out, stream=stream.cuda_stream, device=local)
 
-    out = torch.empty((c.H, c.N), dtype=torch.float64, device=dev)
+    # ---- end to end through the C ABI with host buffers; the process's first
+    # library call is the cold one (graph instantiation, pool growth, tables)
+    tp, xp, sp = (torch.from_numpy(v).pin_memory() for v in (b.t, b.x, b.sigma))
+    hout = torch.empty(evals, dtype=torch.float32).pin_memory()
+    barrier(ws)
+    t0 = time.perf_counter()
+    _, _, st_cold = call(tp, xp, sp, hout)
+    cold_ms = allreduce_max(ws, (time.perf_counter() - t0) * 1e3)
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        call(tp, xp, sp, hout)
+    e2e_s = allreduce_max(ws, (time.perf_counter() - t0) / e2e_steps)
+    del hout
 
-    def timed(plan, steps, warmup, sampler=None):
-        if sampler:
-            sampler.start()
-            time.sleep(0.3)  # the sampler is running before the timed region starts
-        for _ in range(warmup):
-            plan.execute(out, want_records=True)
-        barrier(ws)
-        torch.cuda.synchronize()
-        plan.stage_timing(True)
-        if sampler:
-            sampler.begin()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            plan.execute(out, want_records=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if sampler:
-            sampler.end()
-        clocks = sampler.stop() if sampler else None
-        barrier(ws)
-        ms = e0.elapsed_time(e1)
-        stage_ms, nl, fft_bytes = plan.stage_times()
-        plan.stage_timing(False)
-        return ms, stage_ms, nl, fft_bytes, clocks
-
-    # --- mixed (headline) ---
-    pm = make_plan("mixed")
+    # ---- device-resident inputs and output: the headline
+    td, xd, sd = (torch.from_numpy(v).to(dev) for v in (b.t, b.x, b.sigma))
+    out = torch.empty(evals, dtype=torch.float32, device=dev)
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    ms, stage_ms, nlaunch, fft_bytes, clocks = timed(pm, args.steps, args.warmup, sampler)
-    counts = pm.counts
-    ms_max = allreduce_max(ws, ms)
-    ms_step = ms_max / args.steps
-    value = ws * evals / (ms_step / 1e3)
-    dm = out.cpu().numpy()
-    _, best, peaks, chi0 = pm.execute(out)
-    pm.close()
-
-    # --- FP64 plain path, same workload ---
-    pf = make_plan("fp64")
-    f_steps = max(2, min(args.steps, args.fp64_steps))
-    ms64, stage64, _, fft_bytes64, _ = timed(pf, f_steps, max(1, min(args.warmup, 2)))
-    ms64_max = allreduce_max(ws, ms64)
-    d64 = out.cpu().numpy()
-    pf.close()
-    value64 = ws * evals / (ms64_max / f_steps / 1e3)
-
-    # --- end to end through the C ABI with host buffers ---
-    tp = torch.from_numpy(np.ascontiguousarray(c.t)).pin_memory()
-    xp = torch.from_numpy(np.ascontiguousarray(c.x)).pin_memory()
-    sp = torch.from_numpy(np.ascontiguousarray(c.sigma)).pin_memory()
-    hout = torch.empty((c.H, c.N), dtype=torch.float64).pin_memory()
-    e2e_steps = max(2, min(args.steps, args.e2e_steps))
-    for it in range(1 + e2e_steps):
-        if it == 1:
-            torch.cuda.synchronize()
-            barrier(ws)
-            t_e2e = time.perf_counter()
-        p = _fc2.Plan(tp, xp, sp, c.H, c.f_min, c.df, c.N, c.oversample, "mixed",
-                      stream=stream.cuda_stream, device=local, fft_kernel=args.fft_kernel,
-                      fft_group=args.fft_group)
-        p.execute(hout, want_records=True)
-        p.close()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    for _ in range(args.warmup):
+        call(td, xd, sd, out)
+    barrier(ws)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t_e2e) / e2e_steps
-    e2e_s = allreduce_max(ws, e2e_s)
-    rec_bytes = (c.H + 8) * _fc2.ctypes.sizeof(_fc2.Best) + 8
-    e2e = {"value": ws * evals / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(3 * c.n * 8), "d2h_bytes_per_step": int(c.H * c.N * 8 + rec_bytes),
-           "ms_per_step": e2e_s * 1e3, "includes": "plan create (H2D, moments, tables) + execute + D2H + destroy"}
+    _fc2.batch_timing(True)
+    if sampler:
+        sampler.begin()
+    stage_sum = dict.fromkeys(_fc2.BATCH_STAGES, 0.0)
+    fft_alg = 0.0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        _, peaks, stats = call(td, xd, sd, out)
+        for k, v in stats["stage_ms"].items():
+            stage_sum[k] += v
+        fft_alg += stats["fft_alg_bytes"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.end()
+    _fc2.batch_timing(False)
+    clocks = sampler.stop() if sampler else None
+    barrier(ws)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms_max = allreduce_max(ws, ms)
+    total_evals = sum(allgather(ws, evals))
+    value = total_evals / (ms_max / 1e3)
+    stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
+    fft_alg /= args.steps
+
+    # ---- FP64 on the first 256 curves (device-resident, CUDA events)
+    sub = min(256, b.C)
+    e64 = int(pos[sub])
+    out64 = torch.empty(e64, dtype=torch.float32, device=dev)
+    call(td, xd, sd, out64, "fp64", sub)
+    torch.cuda.synchronize()
+    f0e = torch.cuda.Event(enable_timing=True)
+    f1e = torch.cuda.Event(enable_timing=True)
+    f0e.record(stream)
+    for _ in range(2):
+        call(td, xd, sd, out64, "fp64", sub)
+    f1e.record(stream)
+    torch.cuda.synchronize()
+    ms64 = allreduce_max(ws, f0e.elapsed_time(f1e) / 2)
+    value64 = sum(allgather(ws, e64)) / (ms64 / 1e3)
+    del out64
+
+    # ---- the long curve split into bands over the ranks (records all-gathered)
+    band = None
+    if ws > 1 and not args.no_sub:
+        band = run_long_bands(ws, rank, local)
 
     if rank != 0:
         return
 
-    # --- roofline of the dominant kernel (the FFT passes) ---
     peak, peak_kind = load_peaks()
-    P = 2  # passes of the 2^24-point transforms at this size
-    fft_ms = stage_ms[1]
-    achieved = (fft_bytes / 1e9) / (fft_ms / 1e3) if fft_ms > 0 else 0.0
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "fft_pass_long_curve_traffic.txt")
-    try:
-        import importlib
-        ver = importlib.import_module("paper_0901_1913_gb300.build").kernel_version()
-        with open(tpath) as fh:
-            kv = dict(ln.strip().split("=", 1) for ln in fh if "=" in ln)
-        if kv.get("kernel_version") == ver and args.fft_kernel in ("default", "r64"):
-            traffic = float(kv["traffic_bytes_per_launch"])
-    except Exception:
-        traffic = None
-    kname = {"default": "k_fft_pass64", "r64": "k_fft_pass64", "r16": "k_fft_pass",
-             "bulk": "k_fft_pass_tma"}[args.fft_kernel]
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "kernel": f"{kname} (2 passes/step)",
-            "algorithmic_bytes_per_launch": fft_bytes / P, "launch_ms": fft_ms / P,
+    prof = profile_record("survey_traffic.txt")
+    traffic = float(prof["traffic_bytes_per_step"]) if "traffic_bytes_per_step" in prof else None
+    roof = {"bound": "hbm", "achieved": value * B_ALG / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": value * B_ALG / 1e9 / peak, "traffic": traffic,
+            "kernel": "the whole fc2_execute_batched step (every kernel of the survey pipeline)",
+            "algorithmic_bytes_per_eval": B_ALG,
+            "algorithmic_bytes_per_step": evals * B_ALG,
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
+    fft_ms = stage_ms["fft"]
+    dominant = {"name": "transform passes (k_fft_pass64<10,4> then k_fft_pass_tma<9>)",
+                "ms_per_step": fft_ms, "algorithmic_bytes_per_step": fft_alg,
+                "achieved": fft_alg / 1e9 / (fft_ms / 1e3) if fft_ms > 0 else None,
+                "frac": (fft_alg / 1e9 / (fft_ms / 1e3)) / peak if fft_ms > 0 else None,
+                "unit": "GB/s", "traffic_bytes_per_step": (float(prof["fft_traffic_bytes_per_step"])
+                                                        if "fft_traffic_bytes_per_step" in prof
+                                                        else None)}
+    dram_frac = float(prof["dram_frac_byte_weighted"]) if "dram_frac_byte_weighted" in prof else None
 
-    # --- CPU oracle on a bounded sample of the same curve: baseline + parity ---
-    cpu = None
-    parity = None
+    parity = cpu = None
     if not args.no_cpu and ws == 1:
+        best_j = np.array([int(pk[0]["j"]) if pk[0]["j"] >= 0 else 0
+                           for pk in (peaks[c] for c in range(b.C))])
+
+        def block(c):
+            return out[int(pos[c]):int(pos[c + 1])].cpu().numpy().reshape(int(b.H[c]), int(b.N[c]))
+        parity, cpu = survey_parity(b, block, best_j, os.cpu_count() or 1, args.cpu_seconds)
+
+    subrec = {}
+    if ws == 1 and not args.no_sub:
         threads = os.cpu_count() or 1
-        bj = [b["j"] for b in best] + [p["j"] for p in peaks if p["j"] >= 0]
-        probe = sample_bins_for(c, threads, 11)[:threads]
-        _, _, dt = oracle_sample(c, probe, threads)
-        per_bin = dt / len(probe) * threads
-        nbins = int(max(threads, min(20000, args.cpu_seconds * threads / max(per_bin, 1e-6))))
-        bins = sample_bins_for(c, max(0, nbins - 9 * 17), 13, extra=bj)
-        d_or, piv, dt = oracle_sample(c, bins, threads)
-        cpu = {"value": len(bins) * c.H / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{len(bins)} trial frequencies x H'=1..{c.H} (random + windows at f0, "
-                         f"2f0, f0/2, 1/d and the GPU's best bins)", "seconds": dt}
-        from tests.parity import argmax_ok, compare
-        rm = compare(dm[:, bins].T, d_or, piv, chi0)
-        r6 = compare(d64[:, bins].T, d_or, piv, chi0)
-        jo = int(bins[np.argmax(d_or[:, -1])])
-        parity = {"bins": len(bins), "mixed_max_err_rel": rm["max_err_rel"],
-                  "fp64_max_err_rel": r6["max_err_rel"], "near_alias_bins": rm["n_near_alias"],
-                  "ok": bool(rm["ok"] and r6["ok"]),
-                  "argmax_ok": bool(argmax_ok(best[-1]["j"], jo, d_or[:, -1], chi0, bins))}
+        c = synth.long_curve()
+        f0 = c.truth["f0"]
+        subrec["long_curve"] = dict(workload=LONG, **single_curve_record(
+            c, args, threads, 1024, 8, min(args.steps, 20), 3,
+            [round((k * f0 - c.f_min) / c.df) for k in (0.5, 1, 2)] + [round((1 - c.f_min) / c.df)]))
+        del c
+        c = synth.large_curve()
+        subrec["large_curve"] = dict(workload=LARGE, **single_curve_record(
+            c, args, threads, 48, 2, 3, 2,
+            [round((f * h - c.f_min) / c.df) for f in c.truth["fs"] for h in (1, 2)]))
+        del c
+    if band is not None:
+        subrec["long_curve_bands"] = band
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "mixed", "n": c.n, "N": c.N, "H": c.H,
-                   "oversample": c.oversample, "parallelism": f"{ws} independent curves",
-                   "l2": "inputs larger than L2 (18 grids x 128 MiB)",
-                   "fft_kernel": args.fft_kernel, "fft_group": args.fft_group},
+        "config": {"workload": SURVEY, "curves_per_gpu": b.C, "samples": int(b.offsets[-1]),
+                   "evals_per_step": evals, "N": int(b.N[0]), "H": "2..6",
+                   "oversample": int(b.oversample), "precision": "mixed",
+                   "parallelism": f"{ws} rank(s), contiguous curve ranges, no data-path collective",
+                   "l2": "inputs larger than L2 (each chunk's grids hold several GB)"},
         "roofline": roof,
+        "dominant_kernel": dominant,
+        "dram_frac": dram_frac,
         "cpu_baseline": cpu,
-        "e2e": e2e,
-        "gpu_launches": int(nlaunch * args.steps),
+        "e2e": {"value": total_evals / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(3 * 8 * int(b.offsets[-1])),
+                "d2h_bytes_per_step": int(4 * evals + b.C * K * _fc2.BEST_DTYPE.itemsize),
+                "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
+                "cold_first_call_ms": cold_ms,
+                "includes": "fc2_execute_batched from pinned host arrays (t, x, sigma) to pinned "
+                            "host Delta chi^2 and peak records; the cold call is the process's "
+                            "first library call"},
+        "gpu_launches": int(stats["launches"] * args.steps),
         "clocks": clocks,
-        "fp64": {"value": value64, "ms_per_step": ms64_max / f_steps, "steps": f_steps,
-                 "stage_ms": [round(v, 4) for v in stage64]},
-        "mixed_over_fp64": value / value64,
-        "stage_ms": {k: round(v, 4) for k, v in zip(["spread", "fft", "assemble", "fixup", "peaks"],
-                                                    stage_ms)},
-        "bins_resolved_double": counts[0], "bins_exact_sums": counts[1],
-        "bins_exact_double_float": counts[2], "bins_exact_double": counts[3],
-        "bins_routed_tiers": list(counts[4:7]),
+        "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()},
+        "batch_stats": {k: stats[k] for k in ("resolved", "exact", "exact_double_float",
+                                              "exact_double", "graphs")},
+        "fp64_first_256_curves": {"value": value64, "ms_per_step": ms64,
+                                  "evals_per_step": e64},
+        "mixed_over_fp64_batched": value / value64,
         "parity": parity,
+        **subrec,
     }
+    if "long_curve" in subrec:
+        line["mixed_over_fp64_single_curve"] = value / subrec["long_curve"]["fp64"]["value"]
+    print(json.dumps(line), flush=True)
+
+
+def run_long_bands(ws, rank, local):
+    """The long curve's trial range split into one band per rank (shard.run_band):
+    each rank transforms and solves its own band; the per-band records are
+    all-gathered and merged.  Timed by CUDA events on the plans' stream."""
+    import torch
+    from paper_0901_1913_gb300 import _fc2, shard, synth
+    c = synth.long_curve()
+    stream = torch.cuda.Stream(device=torch.device("cuda", local))
+
+    def make_plan(fm, nb, k):
+        return _fc2.Plan(c.t, c.x, c.sigma, c.H, fm, c.df, nb, c.oversample, "mixed", top_k=k,
+                         stream=stream.cuda_stream, device=local)
+
+    def gather(obj):
+        return allgather(ws, obj)
+
+    shard.run_band(make_plan, c.f_min, c.df, c.N, 8, rank, ws, gather)  # warm-up
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    band, _, best, peaks, _ = shard.run_band(make_plan, c.f_min, c.df, c.N, 8, rank, ws, gather)
+    torch.cuda.synchronize()
+    s = allreduce_max(ws, time.perf_counter() - t0)
+    return {"workload": LONG, "bands": ws, "value": c.N * c.H / s, "ms_per_step": s * 1e3,
+            "includes": "plan creation per band, execute, records all-gather and merge",
+            "best_H_j": int(best[-1]["j"]), "top_peak_j": int(peaks[0]["j"]) if peaks else -1}
+
+
+def run_long(args):
+    """The long single curve alone (--workload long): mixed rate with stage
+    times, FP64 rate, the transform's roofline, oracle parity."""
+    ws, rank, local = dist_init()
+    import torch
+    from paper_0901_1913_gb300 import synth
+    torch.cuda.set_device(local)
+    c = synth.long_curve(seed=2 + rank)
+    threads = os.cpu_count() or 1
+    f0 = c.truth["f0"]
+    rec = single_curve_record(c, args, threads, 1024, 8, args.steps, 3,
+                              [round((k * f0 - c.f_min) / c.df) for k in (0.5, 1, 2)] +
+                              [round((1 - c.f_min) / c.df)])
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": rec["mixed"]["value"], "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": rec["mixed"]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)",
+            "data": "synthetic", "config": {"workload": LONG}, **rec}
     print(json.dumps(line), flush=True)
 
 
@@ -569,8 +815,8 @@ def run_shared_field(args, line, threads):
 
 def run_workload(args):
     """The other synthetic workloads, one JSON line each (for the measurement
-    table; the default run is the long curve).  Oracle parity on a bounded
-    sample of bins or curves."""
+    table; the default run is the survey).  Oracle parity on a bounded sample
+    of bins or curves."""
     import torch
     from paper_0901_1913_gb300 import _fc2, synth
     from tests.parity import TOL, compare, sample_bins
@@ -690,16 +936,17 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fchi2", choices=["fchi2", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-bins", type=int, default=48)
-    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--ref-bins", type=int, default=128)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle (parity, cpu_baseline)")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the single-curve sub-records of the default run")
     ap.add_argument("--profile", action="store_true",
                     help="only run the mixed executes (for ncu); no benchmark line")
     ap.add_argument("--H", type=int, default=0, help="harmonics of the --profile run (default 6)")
-    ap.add_argument("--workload", default="long", choices=["long"] + sorted(WORKLOADS),
-                    help="long (default, the headline) or another synthetic workload")
+    ap.add_argument("--workload", default="survey", choices=["survey", "long"] + sorted(k for k in WORKLOADS if k != "survey"),
+                    help="survey (default, the headline) or another synthetic workload")
     ap.add_argument("--fft-kernel", default="default", choices=["default", "r64", "r16", "bulk"],
                     help="kernel family of the float transform passes")
     ap.add_argument("--fft-group", type=int, default=0,
@@ -707,14 +954,16 @@ def main():
     ap.add_argument("--curves", type=int, default=512,
                     help="curves of a --profile run of the survey or adjoint workload")
     args = ap.parse_args()
-    if args.profile:
-        run_profile(args)
-    elif args.workload != "long" and args.impl != "reference":
-        run_workload(args)
-    elif args.impl == "reference":
+    if args.impl == "reference":
         run_reference(args)
+    elif args.profile:
+        run_profile(args)
+    elif args.workload == "survey":
+        run_survey(args)
+    elif args.workload == "long":
+        run_long(args)
     else:
-        run_gpu(args)
+        run_workload(args)
 
 
 if __name__ == "__main__":

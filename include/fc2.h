@@ -295,8 +295,9 @@ fc2_status fc2_trim_device_memory(int device);
  *   1 <= nb <= 128.  Larger requests return FC2_ERR_INVALID_ARG.
  * Scratch: one file-scope device array of about 3.2 MB that every device that
  * loads the library holds until the process exits.  The first call on a device
- * looks up its device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls on a device share
+ * looks up its device address (cudaGetSymbolAddress) with that device current,
+ * and so does the first call after a cudaDeviceReset of that device; make
+ * those calls before any stream capture.  All calls on a device share
  * the array, so calls whose work overlaps on the GPU race; order them on one
  * stream.  Synchronous: returns after dchi2 is written.  Non-finite inputs or
  * sigma <= 0 give FC2_ERR_INVALID_ARG (detected on the device).

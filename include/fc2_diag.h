@@ -52,6 +52,32 @@ fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im);
 /* The time origin T0 the plan measures phases from (Sec. 3b); 0 on NULL. */
 double fc2_debug_t0(fc2_plan p);
 
+/* Fault injection for the tests of the bounded waits.  Every wait of the
+ * bulk-copy transform passes (fc2_options.fft_kernel 1 or 3, passes after the
+ * first of radix 2^8..2^12) on an mbarrier gives up after wait_cycles SM clock
+ * cycles (0 = the default, about two seconds); a CTA that gives up sets
+ * FC2_ERR_TIMEOUT, waits (again bounded) for its copies in flight and returns,
+ * and fc2_execute returns FC2_ERR_TIMEOUT.  drop_tile >= 0 names the tile of
+ * those passes whose barrier is armed but whose copy is never issued, so that
+ * its wait runs out; -1 issues every copy.  Both settings stay with the plan.
+ * FC2_ERR_INVALID_ARG on NULL, wait_cycles < 0 or drop_tile < -1. */
+fc2_status fc2_debug_fault(fc2_plan p, long long wait_cycles, int drop_tile);
+
+/* Fault injection for the tests of allocation failures: the k-th allocation
+ * from the library's device pool after this call (k >= 1) fails as if the
+ * device were out of memory, once; the caller sees FC2_ERR_OOM.  k <= 0
+ * disarms.  Process-wide. */
+void fc2_debug_fail_alloc(int64_t k);
+
+/* Allocations the library has requested from its device pools so far in this
+ * process (including those fc2_debug_fail_alloc made fail). */
+int64_t fc2_debug_alloc_count(void);
+
+/* Bytes of the library's device pool on `device` in use by live allocations,
+ * after waiting for all work on the device (0 if the library never allocated
+ * there, -1 on a CUDA error). */
+int64_t fc2_debug_pool_used(int device);
+
 /* Bins of the last execute that tier `tier` (2 or 3) handled, into out[0..cap).
  * Returns how many were copied, or -1 on a bad argument or a failed copy. */
 int64_t fc2_debug_tier_bins(fc2_plan p, int tier, int64_t* out, int64_t cap);
@@ -77,6 +103,19 @@ void fc2_debug_batch_counts(int64_t* out5);
  * layout and table uploads, graph capture / update and launch, the wait for
  * the chunk's kernels and results; release at the end.  No-op on NULL. */
 void fc2_debug_batch_phase_ms(double* out7);
+
+/* Stage timing of the batched path on (enable != 0) or off, for the process.
+ * While on, every chunk of fc2_execute_batched records CUDA events on its
+ * stream (inside the chunk's graph) between (0) gather, phase reduction and
+ * spreading, (1) FFT passes, (2) assembly, solve and double re-solve, (3) exact
+ * fix-up, (4) peaks and their records. */
+void fc2_debug_batch_timing(int enable);
+
+/* Device milliseconds of the five stages of the last fc2_execute_batched call
+ * with timing on, summed over its chunks (out6[0..4]), and the transforms'
+ * algorithmic bytes (out6[5]: the kept spectra written, 3 H_c N_c complex
+ * values per curve).  Zeros when timing was off.  No-op on NULL. */
+void fc2_debug_batch_stage_ms(double* out6);
 
 /* Stage timing of p on (enable != 0) or off; resets the accumulated times.
  * While on, each execute records CUDA events on the plan's stream around

@@ -154,6 +154,18 @@ def load():
         lib.fc2_debug_t0.restype = dbl
         lib.fc2_significance.argtypes = [_P, _P, _P, _P, _P]
         lib.fc2_significance.restype = i32
+        lib.fc2_debug_batch_timing.argtypes = [i32]
+        lib.fc2_debug_batch_timing.restype = None
+        lib.fc2_debug_batch_stage_ms.argtypes = [_P]
+        lib.fc2_debug_batch_stage_ms.restype = None
+        lib.fc2_debug_fault.argtypes = [_P, ctypes.c_longlong, i32]
+        lib.fc2_debug_fault.restype = i32
+        lib.fc2_debug_fail_alloc.argtypes = [i64]
+        lib.fc2_debug_fail_alloc.restype = None
+        lib.fc2_debug_alloc_count.argtypes = []
+        lib.fc2_debug_alloc_count.restype = i64
+        lib.fc2_debug_pool_used.argtypes = [i32]
+        lib.fc2_debug_pool_used.restype = i64
         _lib = lib
         return lib
 
@@ -317,6 +329,13 @@ class Plan:
     def t0(self):
         return float(load().fc2_debug_t0(self.h))
 
+    def debug_fault(self, wait_cycles=0, drop_tile=-1):
+        """Test-only fault injection (fc2_debug_fault): limit of the bulk-copy
+        transform's waits in SM cycles (0 = default) and a tile whose copy is
+        armed but never issued (-1 = none)."""
+        _check(load().fc2_debug_fault(self.h, int(wait_cycles), int(drop_tile)),
+               "fc2_debug_fault")
+
     def significance(self, log_p=None):
         """Significance of the last execute (fc2_significance): returns
         (log_p [H, N] or None, j_min [H], log_p_min [H], adj_scale [H]).
@@ -330,6 +349,14 @@ class Plan:
         _check(load().fc2_significance(self.h, _ptr(log_p), jmin.ctypes.data, lpmin.ctypes.data,
                                        adj.ctypes.data), "fc2_significance")
         return log_p, jmin, lpmin, adj
+
+
+def batch_timing(enable=True):
+    """Stage timing of the batched path on or off (fc2_debug_batch_timing)."""
+    load().fc2_debug_batch_timing(int(bool(enable)))
+
+
+BATCH_STAGES = ("spread", "fft", "assemble", "fixup", "peaks")
 
 
 def trim_device_memory(device=0):
@@ -379,13 +406,17 @@ def execute_batched(offsets, t, x, sigma, H, f_min, df, N, oversample=2, prec="m
     lib.fc2_debug_batch_counts(st.ctypes.data)
     ph = np.zeros(7)
     lib.fc2_debug_batch_phase_ms(ph.ctypes.data)
+    sm = np.zeros(6)
+    lib.fc2_debug_batch_stage_ms(sm.ctypes.data)
     return dchi2, BatchPeaks(peaks), dict(launches=int(lib.fc2_debug_batch_launches()),
                              resolved=int(st[0]), exact=int(st[1]),
                              exact_double_float=int(st[2]), exact_double=int(st[3]),
                              graphs=int(st[4]),
                              host_phase_ms=dict(zip(("setup", "alloc", "moments", "layout",
                                                      "graph", "wait", "release"),
-                                                    (float(v) for v in ph))))
+                                                    (float(v) for v in ph))),
+                             stage_ms=dict(zip(BATCH_STAGES, (float(v) for v in sm[:5]))),
+                             fft_alg_bytes=float(sm[5]))
 
 
 def _backward_argtypes(lib):

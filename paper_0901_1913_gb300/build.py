@@ -60,6 +60,23 @@ def build(verbose: bool = False) -> str:
 
 
 
+def sources_version() -> str:
+    """Short hash of every library source and public header; whole-pipeline
+    profiles record it so that stale counters are recognised after any kernel
+    changes."""
+    import hashlib
+    h = hashlib.sha1()
+    inc = os.path.join(HERE, "..", "include")
+    files = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC)
+                   if f.endswith((".cu", ".cuh", ".h", ".cpp")))
+    files += sorted(os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h"))
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
 def kernel_version() -> str:
     """Short hash of the transform sources; profiles record it so that stale
     counters are recognised after the kernel changes."""

@@ -1,6 +1,8 @@
 // fc2_api.cu -- the C ABI of libfc2: validation, plan lifetime, buffer
 // management and the order of kernel launches.  No kernel arithmetic here.
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstring>
 #include <math.h>
 #include <stdlib.h>
@@ -21,7 +23,7 @@ using namespace fc2;
 static int64_t g_last_batch_launches = 0;
 // re-solved, exact float / double-float / double, graphs; then the host
 // milliseconds of the call's seven phases (as doubles' bits)
-static int64_t g_last_batch_stats[12] = {0};
+static int64_t g_last_batch_stats[18] = {0};
 
 // Device memory comes from one stream-ordered pool per device owned by the
 // library.  Memory that a destroyed plan returns stays mapped in the pool
@@ -51,7 +53,20 @@ static cudaMemPool_t device_pool(int dev) {
     return pool;
 }
 
+// Fault injection for the tests (fc2_debug_fail_alloc): the k-th pool
+// allocation from now on fails as if the device were out of memory.
+static std::atomic<int64_t> g_fail_alloc_in{0};
+static std::atomic<int64_t> g_alloc_count{0};  // pool allocations so far (diagnostics)
+
 cudaError_t pool_alloc(void** ptr, size_t bytes, cudaStream_t s) {
+    g_alloc_count.fetch_add(1);
+    int64_t k = g_fail_alloc_in.load();
+    while (k > 0 && !g_fail_alloc_in.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 1) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -490,7 +505,21 @@ fc2_status fc2_execute(fc2_plan p, double* dchi2, fc2_best* best, fc2_best* peak
     }
     fc2_status st = run_pipeline(p);
     p->d_dchi2 = own;
-    if (st != FC2_OK) return st;
+    if (st != FC2_OK) {
+        // a kernel's own report (e.g. a bounded wait that gave up, after which
+        // later stages saw garbage) explains a failure better than its
+        // consequences; the word starts at zero again for the next execute
+        int status = 0;
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        if (cudaMemcpy(&status, p->d_status, 4, cudaMemcpyDeviceToHost) == cudaSuccess &&
+            status != 0) {
+            cudaMemset(p->d_status, 0, 4);
+            return (fc2_status)status;
+        }
+        cudaGetLastError();
+        return st;
+    }
     Guard g;
     const size_t bytes = (size_t)p->H * p->N * 8;
     if (dchi2 && !direct)
@@ -507,7 +536,13 @@ fc2_status fc2_execute(fc2_plan p, double* dchi2, fc2_best* best, fc2_best* peak
     if (g.e != cudaSuccess) return map_err(g.e);
     p->last_exact2_count = p->last_flag_count > 0 ? tiers[0] : 0;
     p->last_exact3_count = p->last_flag_count > 0 ? tiers[1] : 0;
-    if (status != 0) return (fc2_status)status;
+    if (status != 0) {
+        // a kernel reported a problem (e.g. a bounded wait that gave up): the
+        // word starts at zero again for the next execute of this plan
+        g.ok(cudaMemsetAsync(p->d_status, 0, 4, s));
+        g.ok(cudaStreamSynchronize(s));
+        return (fc2_status)status;
+    }
     p->executed = true;
     if (best) memcpy(best, recs.data(), sizeof(fc2_best) * p->H);
     if (peaks) memcpy(peaks, recs.data() + p->H, sizeof(fc2_best) * p->top_k);
@@ -667,6 +702,32 @@ fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im) {
 
 double fc2_debug_t0(fc2_plan p) { return p ? p->scal[SC_T0] : 0.0; }
 
+void fc2_debug_fail_alloc(int64_t k) { g_fail_alloc_in.store(k > 0 ? k : 0); }
+
+int64_t fc2_debug_alloc_count(void) { return g_alloc_count.load(); }
+
+int64_t fc2_debug_pool_used(int device) {
+    cudaMemPool_t pool = existing_pool(device);
+    if (!pool) return 0;
+    if (cudaSetDevice(device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    uint64_t used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return (int64_t)used;
+}
+
+fc2_status fc2_debug_fault(fc2_plan p, long long wait_cycles, int drop_tile) {
+    if (!p || wait_cycles < 0 || drop_tile < -1) return FC2_ERR_INVALID_ARG;
+    p->dbg_wait_cycles = wait_cycles;
+    p->dbg_drop_tile = drop_tile;
+    return FC2_OK;
+}
+
 /* Bins of the last execute that tier `tier` (2 or 3) of the exact fix-up
  * handled; returns how many were copied (at most cap), or -1. */
 int64_t fc2_debug_tier_bins(fc2_plan p, int tier, int64_t* out, int64_t cap) {
@@ -721,6 +782,13 @@ void fc2_debug_batch_counts(int64_t* out5) {
  * allocation and input uploads, moments and the wait for them, chunk layout and table uploads,
  * graph capture / update and launch, the wait for the chunk's kernels and
  * results; release of the buffers at the end. */
+void fc2_debug_batch_timing(int enable) { set_batch_timing(enable != 0); }
+
+void fc2_debug_batch_stage_ms(double* out6) {
+    if (out6)
+        for (int i = 0; i < 6; ++i) std::memcpy(&out6[i], &g_last_batch_stats[12 + i], 8);
+}
+
 void fc2_debug_batch_phase_ms(double* out7) {
     if (out7)
         for (int i = 0; i < 7; ++i) std::memcpy(&out7[i], &g_last_batch_stats[5 + i], 8);

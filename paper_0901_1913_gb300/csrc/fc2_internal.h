@@ -160,6 +160,11 @@ struct fc2_plan_s {
     int64_t stage_n = 0;
     int64_t launches = 0;      // kernels launched by the last execute
     double fft_bytes = 0;      // algorithmic bytes moved by the FFT passes per execute
+    // fault injection for the tests (fc2_debug_fault): limit of the bulk-copy
+    // transform's mbarrier waits in SM cycles (0 = default, about two seconds),
+    // and a tile whose copy that kernel arms but never issues (-1 = none)
+    long long dbg_wait_cycles = 0;
+    int dbg_drop_tile = -1;
 };
 
 namespace fc2 {
@@ -250,7 +255,8 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
                            const double* sigma, const int* H, const double* fmin,
                            const double* df, const int64_t* N, int oversample,
                            const fc2_options& opt, float* dchi2, fc2_best* peaks,
-                           int64_t* launches_out, int64_t* stats_out);  // stats_out[12]
+                           int64_t* launches_out, int64_t* stats_out);  // stats_out[18]
+void set_batch_timing(bool on);  // stage events in the batched path's chunk graphs
 
 fc2_status batched_backward(int64_t C, const int64_t* offsets, const double* t, const double* x,
                             const double* sigma, const int* H, const double* fmin,

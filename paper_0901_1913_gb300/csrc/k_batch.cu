@@ -779,6 +779,14 @@ struct Batch {
     int64_t launches = 0;
     int64_t stats[4] = {0, 0, 0, 0};
     double phase_ms[7] = {0, 0, 0, 0, 0, 0, 0};  // host wall time of the call's phases
+    // stage timing (fc2_debug_batch_timing): events recorded on the stream between
+    // the stages of every chunk (captured into the chunk's graph), device ms per
+    // stage summed over the chunks, and the transforms' algorithmic bytes (the
+    // kept spectra written: 3 H_c N_c complex values per curve)
+    bool timing = false;
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double stage_ms[5] = {0, 0, 0, 0, 0};
+    double fft_alg_bytes = 0;
 
     void free_all() {
         release(t, s); release(x, s); release(sg, s); release(perm, s); release(tau, s);
@@ -796,8 +804,15 @@ struct Batch {
         release(cp.d_twlo, s); release(cp.d_twhi, s); release(cp.d_twst, s); release(cp.d_dec, s);
         if (gexec) cudaGraphExecDestroy(gexec);
         gexec = nullptr;
+        for (auto& e : ev)
+            if (e) { cudaEventDestroy(e); e = nullptr; }
     }
 };
+
+// Process-wide switch of the batched path's stage timing (diagnostics).
+static bool g_batch_timing = false;
+void set_batch_timing(bool on) { g_batch_timing = on; }
+
 
 __global__ void k_set_count(int32_t* c, int32_t v) { *c = v; }
 
@@ -837,6 +852,10 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
     int64_t nl = 0;
     CurveTab ct{b.off, b.H, b.fmin, b.df, b.scal, b.slot0, b.out_off, b.sq, b.sp, b.s1n, b.chi0f,
                 b.qown, b.pslot0};
+    auto mark = [&](int i) {
+        if (b.timing) cudaEventRecord(b.ev[i], s);
+    };
+    mark(0);
     k_bgather<<<(unsigned)((ntot + 255) / 256), 256, 0, s>>>(
         b.t, b.x, b.sg, b.perm, ntot, b.off, nc, b.scal, b.fmin, b.df, b.tau, b.wq, b.wp, b.A, b.B,
         b.wq32, b.wp32);
@@ -854,8 +873,10 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
     if (e != cudaSuccess) return e;
     e = launch_spread(&p, s);
     if (e != cudaSuccess) return e;
+    mark(1);
     e = launch_fft(&p, s);
     if (e != cudaSuccess) return e;
+    mark(2);
     nl += 1 + (int64_t)p.passes.size();
     cudaMemsetAsync(b.counts, 0, 8 * sizeof(int32_t), s);
     k_set_count<<<1, 1, 0, s>>>(b.counts + 4, (int32_t)nrec);  // record count for the peaks
@@ -895,6 +916,7 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
                                                 (int64_t)b.cl4);
         ++nl;
     }
+    mark(3);
     // exact fix-up: float sums over list2 (escalating to list3), double-float
     // sums over list3 (escalating to list4), double sums over list4
     const dfc* tab = (const dfc*)b.dftab;
@@ -924,6 +946,7 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
     exact(I2{}, I0{}, b.list3, b.counts + 2, (int64_t)b.cl3, 1e-13, b.list4, b.counts + 3,
           (int64_t)b.cl4, nullptr);
     exact(I3{}, I0{}, b.list4, b.counts + 3, (int64_t)b.cl4, 1e-13, nullptr, nullptr, 0, nullptr);
+    mark(4);
     if (K > 0) {
         const int nblk = (int)((N + BP_B - 1) / BP_B);
         k_bpeaks1<<<dim3((unsigned)nblk, (unsigned)nc), BP_NT, 0, s>>>(out, N, ct, K, nblk, b.tops);
@@ -931,6 +954,7 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
         nl += 2;
         exact(I2{}, I1{}, b.pent, b.counts + 4, nrec, tau_drop, nullptr, nullptr, 0, b.recs);
     }
+    mark(5);
     b.launches += nl;
     return cudaGetLastError();
 }
@@ -1023,6 +1047,12 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         b.own_stream = true;
     }
     cudaStream_t s = b.s;
+    if (g_batch_timing) {
+        b.timing = true;
+        for (auto& ev : b.ev)
+            if (cudaEventCreate(&ev) != cudaSuccess) b.timing = false;
+        cudaGetLastError();
+    }
     cudaPointerAttributes at;
     bool out_dev = false;
     if (dchi2 && cudaPointerGetAttributes(&at, dchi2) == cudaSuccess && at.type == cudaMemoryTypeDevice)
@@ -1280,6 +1310,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         p.d_key = b.key; p.d_dlt = b.dlt; p.d_cs = b.cs;
         p.d_grid[0] = b.grid0; p.d_grid[1] = b.grid1; p.d_spec = b.spec;
         p.d_L = b.L; p.d_slot_soff = b.slot_soff; p.d_slot_n = b.slot_n;
+        p.d_status = b.counts + 8;  // status word of the chunk's kernels (bounded waits)
         p.h_slot_soff = ssoff; p.h_slot_n = sn;
         const double tau_drop = opt.alias_tau > 0.0 ? opt.alias_tau : (fp64 ? 1e-9 : 1e-6);
         if (e == cudaSuccess && opt.autotune) e = autotune_fft(&p, s);
@@ -1296,8 +1327,9 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         b.phase_ms[4] += ms_since(tp2, tp3);
         if (e != cudaSuccess) { st = map_cuda(e); break; }
         // ---- results (a list that overflowed its capacity leaves bins unrepaired)
-        int32_t cnts[4] = {0, 0, 0, 0};  // re-solve, float, double-float, double lists
-        ok(cudaMemcpyAsync(cnts, b.counts, 16, cudaMemcpyDeviceToHost, s));
+        // re-solve, float, double-float, double lists; [8] the status word
+        int32_t cnts[16] = {0};
+        ok(cudaMemcpyAsync(cnts, b.counts, 64, cudaMemcpyDeviceToHost, s));
         if (dchi2 && !out_dev)
             ok(cudaMemcpyAsync(dchi2 + out_global, out, out_chunk * sizeof(float), cudaMemcpyDeviceToHost, s));
         if (peaks && K > 0)
@@ -1305,6 +1337,15 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         ok(cudaStreamSynchronize(s));
         b.phase_ms[5] += ms_since(tp3, now());
         if (e != cudaSuccess) { st = map_cuda(e); break; }
+        if (cnts[8] != 0) { st = (fc2_status)cnts[8]; break; }
+        if (b.timing) {
+            for (int i = 0; i < 5; ++i) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, b.ev[i], b.ev[i + 1]) == cudaSuccess) b.stage_ms[i] += ms;
+                cudaGetLastError();
+            }
+            for (int c = 0; c < nc; ++c) b.fft_alg_bytes += 3.0 * Hv[c] * (double)N * (double)csz;
+        }
         if ((size_t)cnts[0] > b.cl1 || (size_t)cnts[1] > b.cl2 || (size_t)cnts[2] > b.cl3 ||
             (size_t)cnts[3] > b.cl4) {
             st = FC2_ERR_NUMERIC;
@@ -1320,7 +1361,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     cudaStreamSynchronize(s);
     b.cp.d_key = nullptr; b.cp.d_dlt = nullptr; b.cp.d_cs = nullptr;
     b.cp.d_grid[0] = b.cp.d_grid[1] = nullptr; b.cp.d_spec = nullptr; b.cp.d_L = nullptr;
-    b.cp.d_slot_soff = b.cp.d_slot_n = nullptr; b.cp.d_red = nullptr;
+    b.cp.d_slot_soff = b.cp.d_slot_n = nullptr; b.cp.d_red = nullptr; b.cp.d_status = nullptr;
     if (opt.inputs_on_device) { b.t = b.x = b.sg = nullptr; }
     b.free_all();
     cudaStreamSynchronize(s);
@@ -1331,6 +1372,8 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         for (int i = 0; i < 4; ++i) stats_out[i] = b.stats[i];
         stats_out[4] = b.graphs;
         for (int i = 0; i < 7; ++i) std::memcpy(&stats_out[5 + i], &b.phase_ms[i], 8);
+        for (int i = 0; i < 5; ++i) std::memcpy(&stats_out[12 + i], &b.stage_ms[i], 8);
+        std::memcpy(&stats_out[17], &b.fft_alg_bytes, 8);
     }
     return st;
 }

@@ -822,8 +822,9 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
 // and the last stage's results go from registers straight to global memory
 // where that fills whole 32-byte sectors (the last pass; a next pass of the
 // same radix), otherwise through the work buffer.  Every mbarrier wait is
-// bounded: a CTA that gives up sets FC2_ERR_TIMEOUT in *status, waits (again
-// bounded) for its other copy in flight and returns.
+// bounded (wait_cycles SM cycles): a CTA that gives up sets FC2_ERR_TIMEOUT in
+// *status, waits (again bounded) for each copy it still has in flight and
+// returns.
 constexpr int PT_NT = 512;
 constexpr int PT_LOGE = 13;
 constexpr long long PT_WAIT_CYCLES = 4000000000ll;  // about two seconds
@@ -861,11 +862,12 @@ FC2_D bool mbar_try_wait(uint64_t* m, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the completion of phase `parity` of *m.
-FC2_D bool mbar_wait_bounded(uint64_t* m, unsigned parity) {
+// Bounded wait for the completion of phase `parity` of *m (at most `cycles`
+// SM clock cycles).
+FC2_D bool mbar_wait_bounded(uint64_t* m, unsigned parity, long long cycles) {
     const long long t0 = clock64();
     while (!mbar_try_wait(m, parity))
-        if (clock64() - t0 > PT_WAIT_CYCLES) return false;
+        if (clock64() - t0 > cycles) return false;
     return true;
 }
 
@@ -883,7 +885,8 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
                                                         const cpx<float>* __restrict__ twlo,
                                                         const cpx<float>* __restrict__ twhi,
                                                         const cpx<float>* __restrict__ twst,
-                                                        int G, int* __restrict__ status) {
+                                                        int G, int* __restrict__ status,
+                                                        long long wait_cycles, int drop_tile) {
     using T = float;
     constexpr int R = 1 << LOGR, LOGJ = PT_LOGE - LOGR, J = 1 << LOGJ, E = 1 << PT_LOGE;
     constexpr int NT = PT_NT;
@@ -916,10 +919,13 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
     }
     __syncthreads();
     // thread 0: copy tile t into input buffer b (four 16 KB pieces, one mbarrier)
+    // (drop_tile >= 0, a fault-injection setting of the tests: that tile's
+    // barrier is armed but its copy is never issued, so its wait runs out)
     auto issue = [&](int t, int b) {
         const int gtl = t / tiles_x, bt = t - gtl * tiles_x, gt = a.g0 + gtl;
         const cpx<T>* src = in + (int64_t)gt * M + (int64_t)bt * E;
         mbar_expect_tx(&mbar[b], (unsigned)(E * sizeof(cpx<T>)));
+        if (t == drop_tile) return;
 #pragma unroll
         for (int c = 0; c < 4; ++c)
             bulk_g2s(ib + b * E + c * (E / 4), src + c * (E / 4),
@@ -941,12 +947,16 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
         const int bx = tile - gl * tiles_x;
         const int j0 = bx * J;
         if (bulk) {
-            const bool ok = mbar_wait_bounded(&mbar[buf], (unsigned)((it >> 1) & 1));
+            const bool ok = mbar_wait_bounded(&mbar[buf], (unsigned)((it >> 1) & 1), wait_cycles);
             if (!__syncthreads_and(ok)) {
-                // give up: report, wait for the other buffer's copy if one is in flight
+                // give up: report, then wait (again bounded) for every copy this CTA
+                // still has in flight -- the one just waited for and the next
+                // tile's into the other buffer -- so that none is left writing
+                // into the shared memory of a CTA that has exited
                 if (tid == 0 && status) atomicExch(status, (int)FC2_ERR_TIMEOUT);
+                mbar_wait_bounded(&mbar[buf], (unsigned)((it >> 1) & 1), wait_cycles);
                 if (tile + (int)gridDim.x < ntiles)
-                    mbar_wait_bounded(&mbar[buf ^ 1], (unsigned)(((it + 1) >> 1) & 1));
+                    mbar_wait_bounded(&mbar[buf ^ 1], (unsigned)(((it + 1) >> 1) & 1), wait_cycles);
                 return;
             }
         }
@@ -1272,6 +1282,51 @@ static int logj_of(const fc2_plan_s* p, int logR) {
     return FftCfg<T>::LOGE - logR;
 }
 
+// ------------------------------------------------------ per-device launch state
+// The SM count of the current device, and the dynamic shared-memory limit of a
+// kernel raised once per (device, kernel): cudaFuncSetAttribute acts on the
+// current device only, so a process that drives several devices needs it on
+// each.  Both are guarded by one mutex (plans may run on several host threads).
+static std::mutex g_launch_mu;
+static std::map<std::pair<int, const void*>, size_t> g_smem_raised;  // (device, kernel) -> bytes
+static std::map<int, int> g_sm_count;
+
+static int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    return dev;
+}
+
+static int device_sm_count() {
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    auto it = g_sm_count.find(dev);
+    if (it != g_sm_count.end()) return it->second;
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) {
+        cudaGetLastError();
+        nsm = 152;
+    }
+    g_sm_count[dev] = nsm;
+    return nsm;
+}
+
+static cudaError_t raise_smem_limit(const void* kern, size_t smem) {
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    const auto key = std::make_pair(dev, kern);
+    auto it = g_smem_raised.find(key);
+    if (it != g_smem_raised.end() && it->second >= smem) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    g_smem_raised[key] = smem;
+    return cudaSuccess;
+}
+
 template <typename T, int LOGR, int LOGJ, int NT>
 static cudaError_t run_pass(fc2_plan_s* p, const void* in, void* out, const PassArgs& a,
                             cudaStream_t s) {
@@ -1279,10 +1334,9 @@ static cudaError_t run_pass(fc2_plan_s* p, const void* in, void* out, const Pass
     const int64_t S = p->M >> LOGR;
     const size_t smem = (size_t)(phys(E - 1) + 1 + stage_tw_size(LOGR) + 1) * sizeof(cpx<T>);
     auto kern = k_fft_pass<T, LOGR, LOGJ, NT>;
-    static bool attr_done = false;  // per instantiation, once per process
-    if (!attr_done) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_done = true;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = raise_smem_limit((const void*)kern, smem);
+        if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)(S / J), (unsigned)a.ng);
     kern<<<grid, NT, smem, s>>>((const cpx<T>*)in, (cpx<T>*)out, a, p->d_L,
@@ -1298,19 +1352,12 @@ static cudaError_t run_pass64(fc2_plan_s* p, const void* in, void* out, const Pa
     const int64_t S = p->M >> LOGR;
     const size_t smem = (size_t)(E + 63 * (1 << (LOGR - 6))) * sizeof(cpx<float>);
     auto kern = k_fft_pass64<LOGR, LOGJ>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr_done = true;
+    {
+        const cudaError_t e = raise_smem_limit((const void*)kern, smem);
+        if (e != cudaSuccess) return e;
     }
     const int64_t ntiles = (S >> LOGJ) * (int64_t)a.ng;
-    static int nsm = 0;
-    if (!nsm) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (nsm <= 0) nsm = 152;
-    }
+    const int nsm = device_sm_count();
     const unsigned blocks = (unsigned)std::min<int64_t>(ntiles, (int64_t)nsm);
     kern<<<blocks, P64_NT, smem, s>>>((const cpx<float>*)in, (cpx<float>*)out, a, p->d_L,
                                    (const cpx<float>*)p->d_twlo, (const cpx<float>*)p->d_twhi,
@@ -1325,26 +1372,19 @@ static cudaError_t run_pass_tma(fc2_plan_s* p, const void* in, void* out, const 
     const int64_t S = p->M >> LOGR;
     constexpr size_t smem = pass_tma_smem<LOGR>();
     auto kern = k_fft_pass_tma<LOGR>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        const cudaError_t e = raise_smem_limit((const void*)kern, smem);
         if (e != cudaSuccess) return e;
-        attr_done = true;
     }
     const int64_t ntiles = (S >> LOGJ) * (int64_t)a.ng;
-    static int nsm = 0;
-    if (!nsm) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (nsm <= 0) nsm = 152;
-    }
+    const int nsm = device_sm_count();
     const unsigned blocks = (unsigned)std::min<int64_t>(ntiles, (int64_t)nsm);
     kern<<<blocks, PT_NT, smem, s>>>((const cpx<float>*)in, (cpx<float>*)out, a, p->d_L,
                                      (const cpx<float>*)p->d_twlo, (const cpx<float>*)p->d_twhi,
                                      (const cpx<float>*)p->d_twst + p->twst_off[LOGR], a.ng,
-                                     p->d_status);
+                                     p->d_status,
+                                     p->dbg_wait_cycles > 0 ? p->dbg_wait_cycles : PT_WAIT_CYCLES,
+                                     p->dbg_drop_tile);
     return cudaGetLastError();
 }
 

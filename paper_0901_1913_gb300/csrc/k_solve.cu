@@ -16,6 +16,8 @@
 // its relative pivot d_l / alpha_ll <= tau; dropped columns contribute nothing.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "fc2_common.cuh"
 #include "fc2_df.cuh"
 #include "fc2_internal.h"
@@ -1005,10 +1007,49 @@ constexpr int64_t NA_DOUBLES = NA_PART_OFF + NA_MAX_BINS * NA_MAX_CHUNKS * 6 * N
 
 static __device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
 
+// Device address of g_noalloc_scratch per device ordinal, with the unique ID
+// of the context it was looked up in: after cudaDeviceReset the device has a
+// new primary context and the address is looked up again.  Guarded by a mutex
+// (first calls may come from several host threads).
 struct NaScratchAddr {
-    double* ptr[64] = {nullptr};
+    double* ptr = nullptr;
+    unsigned long long ctx_id = 0;
 };
-NaScratchAddr g_na_addr;  // device address of g_noalloc_scratch, per device ordinal
+std::mutex g_na_mu;
+NaScratchAddr g_na_addr[64];
+
+// cuCtxGetCurrent / cuCtxGetId through the runtime's driver entry points
+// (no link against the driver library).
+typedef int (*NaCtxGetCurrent)(void** ctx);
+typedef int (*NaCtxGetId)(void* ctx, unsigned long long* id);
+NaCtxGetCurrent g_na_get_ctx = nullptr;
+NaCtxGetId g_na_get_id = nullptr;
+std::once_flag g_na_once;
+
+// Unique ID of the current context, or 0 if it cannot be read (the address is
+// then looked up again on every call).
+unsigned long long na_context_id() {
+    std::call_once(g_na_once, [] {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault,
+                                             &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+                cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            g_na_get_ctx = (NaCtxGetCurrent)f1;
+            g_na_get_id = (NaCtxGetId)f2;
+        }
+        cudaGetLastError();
+    });
+    if (!g_na_get_ctx || !g_na_get_id) return 0;
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_na_get_ctx(&ctx) != 0 || !ctx || g_na_get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 __global__ void __launch_bounds__(NA_NT) k_na_moments(const double* __restrict__ t,
                                                       const double* __restrict__ x,
@@ -1170,16 +1211,26 @@ extern "C" fc2_status fc2_dchi2_exact_noalloc(const double* t, const double* x,
     if (!(isfinite(f_min) && f_min >= 0.0) || !(isfinite(df) && df > 0.0)) return FC2_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return FC2_ERR_CUDA;
-    if (!g_na_addr.ptr[dev]) {
-        // first call on this device: device address of the scratch array
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return FC2_ERR_CUDA;
+    // makes the device's primary context current (a no-op when it already is)
+    if (cudaSetDevice(dev) != cudaSuccess) return FC2_ERR_CUDA;
+    double* scr = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_na_mu);
+        const unsigned long long id = na_context_id();
+        NaScratchAddr& a = g_na_addr[dev];
+        if (!a.ptr || id == 0 || id != a.ctx_id) {
+            // first call on this device (or in its current context): the device
+            // address of the scratch array
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return FC2_ERR_CUDA;
+            }
+            a.ptr = (double*)p;
+            a.ctx_id = id;
         }
-        g_na_addr.ptr[dev] = (double*)p;
+        scr = a.ptr;
     }
-    double* scr = g_na_addr.ptr[dev];
     cudaStream_t s = (cudaStream_t)cuda_stream;
     int64_t chunk = (n + NA_MAX_CHUNKS - 1) / NA_MAX_CHUNKS;
     if (chunk < 2048) chunk = 2048;

@@ -63,9 +63,10 @@ class Batch:
 
 
 def _rng(seed: int, *spawn_path: int) -> np.random.Generator:
-    ss = np.random.SeedSequence(seed)
-    for k in spawn_path:
-        ss = ss.spawn(k + 1)[k]
+    """Stream of the child at `spawn_path` of SeedSequence(seed): the child k of
+    a sequence has spawn key (parent key..., k), so it is built directly (the
+    same bytes as spawning k + 1 children and taking the last)."""
+    ss = np.random.SeedSequence(seed, spawn_key=tuple(int(k) for k in spawn_path))
     return np.random.Generator(np.random.PCG64(ss))
 
 
@@ -76,13 +77,9 @@ def lognormal_sigma(rng, n, median=0.05, s=0.4):
 def seasonal_night_times(rng, n, T, season_on=182.6, half_window=1.0 / 6.0):
     """Times on random nights inside the 'on' half of each year, each within an
     8-hour window centred on local midnight (t = d + 0.5 +- 1/6 d)."""
-    nights = []
-    d = 0
-    while d < T:
-        if (d % DAY_YEAR) < season_on:
-            nights.append(d)
-        d += 1
-    nights = np.asarray(nights, dtype=np.float64)
+    d = np.arange(int(math.ceil(T)), dtype=np.float64)  # whole days 0, 1, .. below T
+    d = d[d < T]
+    nights = d[np.fmod(d, DAY_YEAR) < season_on]
     pick = nights[rng.integers(0, nights.size, n)]
     t = pick + 0.5 + rng.uniform(-half_window, half_window, n)
     return np.sort(t)

@@ -396,6 +396,55 @@ def test_false_alarm_and_adjusted_hand_values(oracle_mod):
     np.testing.assert_allclose(s, [97.0 / 400.0, 95.0 / 300.0], rtol=1e-15)
 
 
+def test_adjusted_scale_is_unit_under_the_null(oracle_mod):
+    """Sec. 3d's adjusted Delta chi^2 divides by the best fit's residual chi^2
+    per degree of freedom.  Under a constant source with correct errors, the
+    residual chi^2 of the H'-harmonic fit at a fixed frequency is chi^2 with
+    n - 2H' - 1 degrees of freedom (n samples, 2H' + 1 parameters), so
+    1 / s_{H'} = (chi2_0 - Delta chi^2) / (n - 2H' - 1) has mean 1 and
+    variance 2 / (n - 2H' - 1).  With n = 20 a degree-of-freedom count off by
+    one moves the mean by 1/15 (about 11 standard errors here), and chi2_0 in
+    place of the residual by 4/15."""
+    rng = np.random.default_rng(4242)
+    n, R, H = 20, 4000, 2
+    t = np.sort(rng.uniform(0.0, 30.0, n))
+    sigma = rng.uniform(0.3, 2.0, n)
+    inv = np.empty((R, H))
+    for r in range(R):
+        x = 3.0 + sigma * rng.standard_normal(n)
+        d = oracle_mod.dchi2_freqs(t, x, sigma, H, [0.4123], threads=1)[0]
+        _, _, chi0, _ = oracle_mod.moments(x, sigma)
+        inv[r] = 1.0 / oracle_mod.adjusted_scale(d, chi0, n)
+    for h in range(H):
+        dof = n - 2 * (h + 1) - 1
+        se = math.sqrt(2.0 / dof / R)
+        assert abs(inv[:, h].mean() - 1.0) < 4.0 * se
+        # the spread is that of chi^2_dof / dof as well
+        assert abs(inv[:, h].var() - 2.0 / dof) < 0.25 * (2.0 / dof)
+
+
+def test_adjusted_scale_denominator_is_the_lstsq_residual(oracle_mod):
+    """The denominator chi2_0 - Delta chi^2_best is the residual chi^2 of the
+    best fit: numpy's least squares on the explicit weighted design
+    [1, sin 2 pi h f t, cos 2 pi h f t] at the best frequency, per H'."""
+    c = synth.tiny_curve(31, 60, T=25.0, H=3, N=300, f_min=0.02, df=0.01)
+    freqs = c.f_min + np.arange(c.N) * c.df
+    d = oracle_mod.dchi2_freqs(c.t, c.x, c.sigma, c.H, freqs)
+    _, _, chi0, _ = oracle_mod.moments(c.x, c.sigma)
+    best = d.max(axis=0)
+    s = oracle_mod.adjusted_scale(best, chi0, c.n)
+    sw = 1.0 / c.sigma
+    for h in range(1, c.H + 1):
+        f = freqs[np.argmax(d[:, h - 1])]
+        cols = [np.ones(c.n)]
+        for k in range(1, h + 1):
+            cols += [np.sin(2 * np.pi * k * f * c.t), np.cos(2 * np.pi * k * f * c.t)]
+        X = np.stack(cols, axis=1) * sw[:, None]
+        coef, *_ = np.linalg.lstsq(X, c.x * sw, rcond=None)
+        resid = float(np.sum((X @ coef - c.x * sw) ** 2))
+        np.testing.assert_allclose(s[h - 1], (c.n - 2 * h - 1) / resid, rtol=1e-9)
+
+
 # ------------------------------------------------------ the paper's gridding
 
 def test_paper_grid_times_on_and_off_cell_edges(oracle_mod):
