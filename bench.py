@@ -287,7 +287,7 @@ def survey_parity(b, got_block, best_j, threads, seconds, n_curves=64, max_bins=
     idx = np.unique(np.linspace(0, b.C - 1, n_curves).astype(int))
     # oracle cost per bin ~ n_c H_c^3: probe it on one curve
     c0 = b.curve(int(idx[0]))
-    probe = np.arange(0, c0.N, c0.N // (4 * threads))[:4 * threads]
+    probe = np.arange(0, c0.N, c0.N // (16 * threads))[:16 * threads]
     _, _, dt = oracle_sample(c0, probe, threads)
     per_unit = dt / (probe.size * c0.n * c0.H ** 3)
     units = sum(b.curve(int(c)).n * int(b.H[c]) ** 3 for c in idx)

@@ -13,10 +13,15 @@
  *   tier 1  float sine / cosine of the exact integer phases, compensated
  *           float sums;
  *   tier 2  double-float phasors and sums (about 48 significant bits);
- *   tier 3  double phasors and sums.
+ *   tier 3  double phasors and sums (the last tier of the FP64 path);
+ *   tier 4  double-float phasors evaluated directly for every harmonic
+ *           multiple from its exact integer phase, double-float products,
+ *           sums exact in 64-bit fixed point (the last tier of the mixed
+ *           path; on the float and integer pipes).
  * Each tier checks its own result (error estimate from the coefficient norm
  * and the smallest relative pivot of the bordered Cholesky factorisation) and
- * passes the bins it cannot vouch for to the next.
+ * passes the bins it cannot vouch for to the next; the last tier keeps what it
+ * finds.
  *
  * Conventions are those of fc2.h: plain C arrays, host pointers unless
  * stated, fc2_status returns, nothing throws across the ABI.  Calls that read
@@ -82,8 +87,12 @@ int64_t fc2_debug_pool_used(int device);
  * Returns how many were copied, or -1 on a bad argument or a failed copy. */
 int64_t fc2_debug_tier_bins(fc2_plan p, int tier, int64_t* out, int64_t cap);
 
+/* Last tier of the mixed path's exact fix-up, for the process: 4 (default)
+ * or 3 (double sums, as in the FP64 path).  Other values select 4. */
+void fc2_debug_last_tier(int tier);
+
 /* Delta chi^2 [H][nb] at bins[0..nb) from the exact sums of one tier
- * (1, 2 or 3), written to out (H * nb doubles).  Overwrites those bins of the
+ * (1, 2, 3 or 4), written to out (H * nb doubles).  Overwrites those bins of the
  * plan's device output.  FC2_ERR_INVALID_ARG for a bin outside [0, N), a bad
  * tier, or nb above N or above the plan's exact-round size. */
 fc2_status fc2_debug_exact_bins(fc2_plan p, const int64_t* bins, int64_t nb, int tier,

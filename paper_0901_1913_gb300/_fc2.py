@@ -160,6 +160,8 @@ def load():
         lib.fc2_debug_batch_stage_ms.restype = None
         lib.fc2_debug_fault.argtypes = [_P, ctypes.c_longlong, i32]
         lib.fc2_debug_fault.restype = i32
+        lib.fc2_debug_last_tier.argtypes = [i32]
+        lib.fc2_debug_last_tier.restype = None
         lib.fc2_debug_fail_alloc.argtypes = [i64]
         lib.fc2_debug_fail_alloc.restype = None
         lib.fc2_debug_alloc_count.argtypes = []
@@ -298,7 +300,8 @@ class Plan:
 
     def exact_bins(self, bins, tier):
         """Delta chi^2 [H, len(bins)] at the given bins from the exact sums of one
-        tier (1 float, 2 double-float, 3 double)."""
+        tier (1 float, 2 double-float, 3 double, 4 double-float terms with
+        sums exact in fixed point)."""
         b = np.ascontiguousarray(bins, dtype=np.int64)
         out = np.empty((self.H, b.size))
         _check(load().fc2_debug_exact_bins(self.h, b.ctypes.data, b.size, int(tier),
@@ -349,6 +352,12 @@ class Plan:
         _check(load().fc2_significance(self.h, _ptr(log_p), jmin.ctypes.data, lpmin.ctypes.data,
                                        adj.ctypes.data), "fc2_significance")
         return log_p, jmin, lpmin, adj
+
+
+def last_tier(tier=4):
+    """Last tier of the mixed path's exact fix-up for the process (4 default,
+    3 = double sums)."""
+    load().fc2_debug_last_tier(int(tier))
 
 
 def batch_timing(enable=True):

@@ -702,6 +702,8 @@ fc2_status fc2_debug_spectra(fc2_plan p, double* re, double* im) {
 
 double fc2_debug_t0(fc2_plan p) { return p ? p->scal[SC_T0] : 0.0; }
 
+void fc2_debug_last_tier(int tier) { set_last_fixup_tier(tier); }
+
 void fc2_debug_fail_alloc(int64_t k) { g_fail_alloc_in.store(k > 0 ? k : 0); }
 
 int64_t fc2_debug_alloc_count(void) { return g_alloc_count.load(); }
@@ -747,7 +749,7 @@ int64_t fc2_debug_tier_bins(fc2_plan p, int tier, int64_t* out, int64_t cap) {
  * those bins of the plan's internal output.  nb <= min(N, exact-round size). */
 fc2_status fc2_debug_exact_bins(fc2_plan p, const int64_t* bins, int64_t nb, int tier,
                                 double* out) {
-    if (!p || !bins || !out || nb < 1 || nb > p->N || nb > p->exact_cap || tier < 1 || tier > 3)
+    if (!p || !bins || !out || nb < 1 || nb > p->N || nb > p->exact_cap || tier < 1 || tier > 4)
         return FC2_ERR_INVALID_ARG;
     for (int64_t i = 0; i < nb; ++i)
         if (bins[i] < 0 || bins[i] >= p->N) return FC2_ERR_INVALID_ARG;

@@ -120,6 +120,84 @@ FC2_D double2 d_phasor(uint64_t u, const double2* t1, const double2* t2) {
     return make_double2(fma(pr, c, -pi * s), fma(pr, s, pi * c));
 }
 
+// ---------------------------------------------- sums exact in fixed point
+// The last precision tier of the exact fix-up keeps the float pipes' speed but
+// none of their accumulation error: each harmonic multiple's phasor is
+// evaluated directly from its exact integer phase k u (df_phasor, ~2^-46, no
+// chains of products), the products with the double-float weights are summed
+// in double-float over blocks of FX_BLOCK samples, and every block sum enters
+// a 64-bit integer accumulator at a fixed scale 2^s -- integer additions are
+// exact and associative, so the result does not depend on the order and the
+// only errors are the per-term ones (phasor, product, block, and the
+// conversion's rounding at 2^-s).
+constexpr int FX_BLOCK = 4;
+
+// Scale exponent s for sums of at most nterm terms of modulus <= vmax: the
+// scaled terms add up to less than 2^61 in modulus, and so does every partial
+// sum of the converted block pieces (each at most its terms' sum plus half a
+// unit of rounding), far inside the 64-bit range.  Clamped to the float
+// exponent range.
+FC2_D int fx_exponent(float vmax, int64_t nterm) {
+    const int ev = (vmax > 0.0f) ? ilogbf(vmax) + 1 : 0;  // vmax < 2^ev
+    int en = 0;
+    while ((1ll << en) < nterm) ++en;
+    int s = 61 - ev - en;
+    if (s > 126) s = 126;
+    if (s < -126) s = -126;
+    return s;
+}
+
+FC2_D void fx_flush(long long& acc, dfl& blk, float scale) {
+    acc += __float2ll_rn(blk.h * scale) + __float2ll_rn(blk.l * scale);
+    blk = dfl{0.f, 0.f};
+}
+
+// One lane's sums over samples i = i0 + start, + step, .. < i1 of multiple k:
+// acc[0..1] = sum w e^{2 pi i k u_i} (re, im) and, when with_p, acc[2..3] the
+// same with the weighted data; u_i = A_i + ju B_i (mod 2^64).  Weights as float
+// high parts at [i] and low parts at [ntot + i]; sq, sp = 2^s of each kind.
+FC2_D void fx_lane_sums(const uint64_t* __restrict__ Aph, const uint64_t* __restrict__ Bph,
+                        const float* __restrict__ wq32, const float* __restrict__ wp32,
+                        int64_t ntot, uint64_t ju, uint64_t k, int64_t i0, int64_t i1,
+                        int64_t start, int64_t step, bool with_p, const dfc* t1, const dfc* t2,
+                        float sq, float sp, long long acc[4]) {
+    dfl b0{0.f, 0.f}, b1{0.f, 0.f}, b2{0.f, 0.f}, b3{0.f, 0.f};
+    int cnt = 0;
+    for (int64_t i = i0 + start; i < i1; i += step) {
+        const uint64_t u = k * (Aph[i] + ju * Bph[i]);
+        const dfc z = df_phasor(u, t1, t2);
+        const dfl a{wq32[i], wq32[ntot + i]};
+        df_acc_mul(b0, a, z.re);
+        df_acc_mul(b1, a, z.im);
+        if (with_p) {
+            const dfl b{wp32[i], wp32[ntot + i]};
+            df_acc_mul(b2, b, z.re);
+            df_acc_mul(b3, b, z.im);
+        }
+        if (++cnt == FX_BLOCK) {
+            fx_flush(acc[0], b0, sq);
+            fx_flush(acc[1], b1, sq);
+            if (with_p) {
+                fx_flush(acc[2], b2, sp);
+                fx_flush(acc[3], b3, sp);
+            }
+            cnt = 0;
+        }
+    }
+    fx_flush(acc[0], b0, sq);
+    fx_flush(acc[1], b1, sq);
+    if (with_p) {
+        fx_flush(acc[2], b2, sp);
+        fx_flush(acc[3], b3, sp);
+    }
+}
+
+FC2_D float warp_max_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 // Every lane receives the warp's sum of (hi, lo) float pairs (butterfly of
 // error-free two-sums; two-sum is symmetric in its operands, so all lanes end
 // with the same bits).

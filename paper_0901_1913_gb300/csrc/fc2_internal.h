@@ -206,6 +206,9 @@ cudaError_t launch_fft(fc2_plan_s* p, cudaStream_t s);
 cudaError_t launch_assemble(fc2_plan_s* p, cudaStream_t s);
 cudaError_t launch_fixup(fc2_plan_s* p, int64_t n1, int64_t n2, int64_t n3, cudaStream_t s);
 cudaError_t launch_exact_bins(fc2_plan_s* p, int64_t nb, int tier, cudaStream_t s);
+// Last tier of the mixed path's exact fix-up (4 by default, 3 for diagnostics).
+void set_last_fixup_tier(int tier);
+int last_fixup_tier();
 // k_signif.cu: ln p(f) of the last execute (logp may be nullptr) and per row
 // the minimising bin, its ln p and the adjusted-Delta chi^2 factor (device arrays).
 cudaError_t launch_significance(fc2_plan_s* p, double* logp, int64_t* jmin, double* lpmin,

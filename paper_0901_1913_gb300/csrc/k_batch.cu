@@ -293,10 +293,10 @@ FC2_HD int bx_items_of(int64_t n) {
 // The phasor tables of tiers 2 and 3, staged in shared memory by every CTA.
 template <int TIER>
 struct BxTables {
-    dfc t2[TIER == 2 ? 512 : 1];
+    dfc t2[(TIER == 2 || TIER == 4) ? 512 : 1];
     double2 t3[TIER == 3 ? 512 : 1];
     FC2_D void load(const dfc* __restrict__ dftab) {
-        if constexpr (TIER == 2)
+        if constexpr (TIER == 2 || TIER == 4)
             for (int i = threadIdx.x; i < 512; i += blockDim.x) t2[i] = dftab[i];
         if constexpr (TIER == 3) {
             const double2* t64 = reinterpret_cast<const double2*>(dftab + 512);
@@ -369,6 +369,50 @@ FC2_D void bx_sums(const uint64_t* __restrict__ Aph, const uint64_t* __restrict_
         for (int v = 0; v < NV; ++v) {
             const float2 x = warp_allsum_pair(fa[v].h, fa[v].l);
             tot[v] = (double)x.x + (double)x.y;
+        }
+    } else if constexpr (TIER == 4) {
+        // lph lanes per harmonic multiple k = 1..2H (lane = (k - 1) lph + r),
+        // each over the samples i0 + r, + lph, ..; sums exact in fixed point
+        const int lph = 32 / (2 * H);
+        const int g = lane / lph, r = lane - g * lph;
+        float mq = 0.f, mp = 0.f;  // the item's largest weights set the scales
+        for (int64_t i = i0 + lane; i < i1; i += 32) {
+            mq = fmaxf(mq, fabsf(wq32[i]));
+            mp = fmaxf(mp, fabsf(wp32[i]));
+        }
+        mq = warp_max_f(mq);
+        mp = warp_max_f(mp);
+        // a harmonic's terms over the item (|w e^{..}| <= |w| (1 + 2^-23))
+        const int eq = fx_exponent(mq * 1.0000002f, i1 - i0 + 1);
+        const int ep = fx_exponent(mp * 1.0000002f, i1 - i0 + 1);
+        long long acc[4] = {0, 0, 0, 0};
+        if (g < 2 * H)
+            fx_lane_sums(Aph, Bph, wq32, wp32, ntot, ju, (uint64_t)(g + 1), i0, i1, r, lph,
+                         g < H, tb.t2, tb.t2 + 256, exp2f((float)eq), exp2f((float)ep), acc);
+        // group sums, exact: the group's first lane adds its lanes' values in order
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            long long s = acc[q];
+            for (int o = 1; o < lph; ++o) {
+                const long long y = __shfl_sync(0xffffffffu, acc[q], (lane + o) & 31);
+                if (r == 0) s += y;
+            }
+            acc[q] = s;
+        }
+        const double uq = ldexp(1.0, -eq), up = ldexp(1.0, -ep);
+#pragma unroll
+        for (int k = 0; k < 2 * HM; ++k) {
+            const int src = (k < 2 * H) ? k * lph : 0;
+            const double v0 = (double)__shfl_sync(0xffffffffu, acc[0], src) * uq;
+            const double v1 = (double)__shfl_sync(0xffffffffu, acc[1], src) * uq;
+            const double v2 = (double)__shfl_sync(0xffffffffu, acc[2], src) * up;
+            const double v3 = (double)__shfl_sync(0xffffffffu, acc[3], src) * up;
+            tot[2 * k] = (k < 2 * H) ? v0 : 0.0;
+            tot[2 * k + 1] = (k < 2 * H) ? v1 : 0.0;
+            if (k < HM) {
+                tot[4 * HM + 2 * k] = (k < H) ? v2 : 0.0;
+                tot[4 * HM + 2 * k + 1] = (k < H) ? v3 : 0.0;
+            }
         }
     } else {
 #pragma unroll
@@ -560,7 +604,7 @@ __global__ void __launch_bounds__(BX_NT) k_bexact(
         if constexpr (MODE == 0) {
             double o[HM], an2 = 0.0;
             const double dmin = warp_chol_solve<HM, true>(S, tau_drop, o, &an2, H);
-            const double eps = TIER == 1 ? 2e-7 * sc[SC_RW] : BX_EPS_DF;
+            const double eps = TIER == 1 ? 2e-7 * sc[SC_RW] : (TIER == 2 ? BX_EPS_DF : 1e-14);
             // sums cannot vouch for a pivot near their precision (their errors
             // can also make the coefficients look small): such entries go on
             if (lane == 0) {
@@ -783,6 +827,7 @@ struct Batch {
     // the stages of every chunk (captured into the chunk's graph), device ms per
     // stage summed over the chunks, and the transforms' algorithmic bytes (the
     // kept spectra written: 3 H_c N_c complex values per curve)
+    bool double_last = false;  // mixed path: double sums as the last fix-up tier (diagnostics)
     bool timing = false;
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     double stage_ms[5] = {0, 0, 0, 0, 0};
@@ -852,8 +897,10 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
     int64_t nl = 0;
     CurveTab ct{b.off, b.H, b.fmin, b.df, b.scal, b.slot0, b.out_off, b.sq, b.sp, b.s1n, b.chi0f,
                 b.qown, b.pslot0};
+    // (inside a stream capture only an external event record becomes a node of
+    // the graph; a plain record there would only order the capture)
     auto mark = [&](int i) {
-        if (b.timing) cudaEventRecord(b.ev[i], s);
+        if (b.timing) cudaEventRecordWithFlags(b.ev[i], s, cudaEventRecordExternal);
     };
     mark(0);
     k_bgather<<<(unsigned)((ntot + 255) / 256), 256, 0, s>>>(
@@ -941,11 +988,19 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
     using I1 = std::integral_constant<int, 1>;
     using I2 = std::integral_constant<int, 2>;
     using I3 = std::integral_constant<int, 3>;
+    using I4 = std::integral_constant<int, 4>;
     exact(I1{}, I0{}, b.list2, b.counts + 1, (int64_t)b.cl2, 1e-13, b.list3, b.counts + 2,
           (int64_t)b.cl3, nullptr);
     exact(I2{}, I0{}, b.list3, b.counts + 2, (int64_t)b.cl3, 1e-13, b.list4, b.counts + 3,
           (int64_t)b.cl4, nullptr);
-    exact(I3{}, I0{}, b.list4, b.counts + 3, (int64_t)b.cl4, 1e-13, nullptr, nullptr, 0, nullptr);
+    // the last tier: sums exact in fixed point on the float and integer pipes for
+    // the mixed path, double sums for the FP64 path
+    if (f32 && !b.double_last)
+        exact(I4{}, I0{}, b.list4, b.counts + 3, (int64_t)b.cl4, 1e-13, nullptr, nullptr, 0,
+              nullptr);
+    else
+        exact(I3{}, I0{}, b.list4, b.counts + 3, (int64_t)b.cl4, 1e-13, nullptr, nullptr, 0,
+              nullptr);
     mark(4);
     if (K > 0) {
         const int nblk = (int)((N + BP_B - 1) / BP_B);
@@ -1047,6 +1102,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         b.own_stream = true;
     }
     cudaStream_t s = b.s;
+    b.double_last = last_fixup_tier() == 3;
     if (g_batch_timing) {
         b.timing = true;
         for (auto& ev : b.ev)

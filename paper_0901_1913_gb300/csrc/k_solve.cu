@@ -16,6 +16,7 @@
 // its relative pivot d_l / alpha_ll <= tau; dropped columns contribute nothing.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <mutex>
 
 #include "fc2_common.cuh"
@@ -336,10 +337,12 @@ __global__ void __launch_bounds__(EX_NT) k_exact_partial(
     const int32_t* __restrict__ count_dev, int64_t count, int64_t base, int64_t cap, int H,
     double* __restrict__ part) {
     constexpr int NV = 6 * HM;
-    __shared__ double red[TIER == 3 ? EX_NT / 32 : 1][NV];
-    __shared__ float2 redf[TIER == 3 ? 1 : EX_NT / 32][NV];
-    __shared__ dfc stab[TIER == 2 ? 512 : 1];
+    constexpr bool DRED = (TIER == 3 || TIER == 4);  // per-warp partials in double
+    __shared__ double red[DRED ? EX_NT / 32 : 1][NV];
+    __shared__ float2 redf[DRED ? 1 : EX_NT / 32][NV];
+    __shared__ dfc stab[(TIER == 2 || TIER == 4) ? 512 : 1];
     __shared__ double2 stab64[TIER == 3 ? 512 : 1];
+    __shared__ float smax[2][EX_NT / 32];
     int64_t cnt = count_dev ? (int64_t)(*count_dev) - base : count;
     if (cnt > cap) cnt = cap;
     if (cnt <= 0) return;
@@ -348,7 +351,7 @@ __global__ void __launch_bounds__(EX_NT) k_exact_partial(
     exact_geometry(n, cnt, &chunk, &nch);
     const int64_t items = cnt * nch;
     const int lane = threadIdx.x & 31, wpi = threadIdx.x >> 5;
-    if constexpr (TIER == 2) {
+    if constexpr (TIER == 2 || TIER == 4) {
         for (int i = threadIdx.x; i < 512; i += EX_NT) stab[i] = dftab[i];
         __syncthreads();
     }
@@ -418,6 +421,61 @@ __global__ void __launch_bounds__(EX_NT) k_exact_partial(
                 const float2 x = warp_sum_pair(fa[v].h, fa[v].l);
                 if (lane == 0) redf[wpi][v] = x;
             }
+        } else if constexpr (TIER == 4) {
+            // lph lanes per harmonic multiple k (lane = (k - 1) lph + r); warp w
+            // takes samples i0 + r + lph (w + 8 q); sums exact in fixed point at
+            // scales set by the item's largest weights
+            float mq = 0.f, mp = 0.f;
+            for (int64_t i = i0 + threadIdx.x; i < i1; i += EX_NT) {
+                mq = fmaxf(mq, fabsf(wq32[i]));
+                mp = fmaxf(mp, fabsf(wp32[i]));
+            }
+            mq = warp_max_f(mq);
+            mp = warp_max_f(mp);
+            if (lane == 0) { smax[0][wpi] = mq; smax[1][wpi] = mp; }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < EX_NT / 32; ++q) {
+                mq = fmaxf(mq, smax[0][q]);
+                mp = fmaxf(mp, smax[1][q]);
+            }
+            const int eq = fx_exponent(mq * 1.0000002f, i1 - i0 + 1);
+            const int ep = fx_exponent(mp * 1.0000002f, i1 - i0 + 1);
+            const int lph = 32 / (2 * H);
+            const int g = lane / lph, r = lane - g * lph;
+            long long acc[4] = {0, 0, 0, 0};
+            if (g < 2 * H)
+                fx_lane_sums(Aph, Bph, wq32, wp32, n, ju, (uint64_t)(g + 1), i0, i1,
+                             r + (int64_t)lph * wpi, (int64_t)lph * (EX_NT / 32), g < H, stab,
+                             stab + 256, exp2f((float)eq), exp2f((float)ep), acc);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                long long sacc = acc[q];
+                for (int o = 1; o < lph; ++o) {
+                    const long long y = __shfl_sync(0xffffffffu, acc[q], (lane + o) & 31);
+                    if (r == 0) sacc += y;
+                }
+                acc[q] = sacc;
+            }
+            if (r == 0 && g < 2 * H) {
+                const double uq = ldexp(1.0, -eq), up = ldexp(1.0, -ep);
+                red[wpi][2 * g] = (double)acc[0] * uq;
+                red[wpi][2 * g + 1] = (double)acc[1] * uq;
+                if (g < H) {
+                    red[wpi][4 * HM + 2 * g] = (double)acc[2] * up;
+                    red[wpi][4 * HM + 2 * g + 1] = (double)acc[3] * up;
+                }
+            }
+            // values of multiples beyond 2H (and P beyond H) are never read
+            if (lane < NV) {
+                const int v = lane;
+                const bool used = (v < 4 * HM) ? (v / 2 < 2 * H) : ((v - 4 * HM) / 2 < H);
+                if (!used) red[wpi][v] = 0.0;
+            }
+            for (int v = lane + 32; v < NV; v += 32) {
+                const bool used = (v < 4 * HM) ? (v / 2 < 2 * H) : ((v - 4 * HM) / 2 < H);
+                if (!used) red[wpi][v] = 0.0;
+            }
         } else {
             double acc[NV];
 #pragma unroll
@@ -454,7 +512,7 @@ __global__ void __launch_bounds__(EX_NT) k_exact_partial(
         __syncthreads();
         if (threadIdx.x < NV) {
             double x = 0.0;
-            if constexpr (TIER == 3) {
+            if constexpr (DRED) {
 #pragma unroll
                 for (int q = 0; q < EX_NT / 32; ++q) x += red[q][threadIdx.x];
             } else {
@@ -824,6 +882,13 @@ static void launch_partial(fc2_plan_s* p, const int32_t* b32, const int64_t* b64
 constexpr double EPS_DF = 1.5e-12;
 constexpr double ERR_FIX = 2e-5;
 
+// Last tier of the mixed path's fix-up: 4 (double-float terms, sums exact in
+// fixed point; the default) or 3 (double; diagnostics).  The FP64 path always
+// ends in tier 3.
+static std::atomic<int> g_last_tier{4};
+void set_last_fixup_tier(int tier) { g_last_tier.store(tier == 3 ? 3 : 4); }
+int last_fixup_tier() { return g_last_tier.load(); }
+
 // Exact fix-up of the flagged bins in up to three tiers.  Bins start at the
 // tier the re-solve routed them to (lists 0, 2, 3 with n1, n2, n3 entries;
 // the double path routes everything to tier 1); a bin that a tier cannot
@@ -854,9 +919,11 @@ static cudaError_t fixup_h(fc2_plan_s* p, int64_t n1, int64_t n2, int64_t n3, cu
                                                  1e-13, EPS_DF, ERR_FIX, list3, cnt3, p->flag_cap,
                                                  p->d_dchi2, p->N);
     }
+    const bool fx_last = !p->fp64 && last_fixup_tier() == 4;
     for (int64_t base = 0; base < b3; base += cap) {
         const unsigned blocks = (unsigned)std::min(cap, b3 - base);
-        launch_partial<HH, 3>(p, list3, nullptr, cnt3, 0, base, cap, s);
+        if (fx_last) launch_partial<HH, 4>(p, list3, nullptr, cnt3, 0, base, cap, s);
+        else launch_partial<HH, 3>(p, list3, nullptr, cnt3, 0, base, cap, s);
         k_exact_dchi2<HH><<<blocks, 32, 0, s>>>(p->d_part, p->n, list3, cnt3, base, cap, p->d_scal,
                                                  1e-13, 0.0, ERR_FIX, nullptr, nullptr, 0,
                                                  p->d_dchi2, p->N);
@@ -872,6 +939,7 @@ static cudaError_t exact_bins_h(fc2_plan_s* p, int64_t nb, int tier, cudaStream_
     const unsigned blocks = (unsigned)nb;
     if (tier == 1) launch_partial<HH, 1>(p, list, nullptr, nullptr, nb, 0, nb, s);
     else if (tier == 2) launch_partial<HH, 2>(p, list, nullptr, nullptr, nb, 0, nb, s);
+    else if (tier == 4) launch_partial<HH, 4>(p, list, nullptr, nullptr, nb, 0, nb, s);
     else launch_partial<HH, 3>(p, list, nullptr, nullptr, nb, 0, nb, s);
     int32_t* cnt = p->d_flag_count + 3;
     const int32_t nb32 = (int32_t)nb;

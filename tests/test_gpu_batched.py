@@ -83,13 +83,18 @@ def test_batched_device_buffers_and_unsorted(fc2):
     assert np.max(np.abs(got - ref)) <= 1e-5 * scale
 
 
-@pytest.mark.parametrize("prec", ["mixed", "fp64"])
-def test_batched_degenerate_bins(fc2, oracle_mod, prec):
+@pytest.mark.parametrize("prec,last", [("mixed", 4), ("mixed", 3), ("fp64", 3)])
+def test_batched_degenerate_bins(fc2, oracle_mod, prec, last):
     """Bins that need the exact tiers (periods longer than the span, near the
-    daily aliases) through the batched fix-up, against the oracle."""
+    daily aliases) through the batched fix-up, against the oracle; the mixed
+    path with either last tier (sums exact in fixed point, or double)."""
     b = small_survey(C=8, N=1 << 14, seed=5)
-    out, _, stats = fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df, b.N,
-                                        2, prec)
+    fc2.last_tier(last)
+    try:
+        out, _, stats = fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df,
+                                            b.N, 2, prec)
+    finally:
+        fc2.last_tier(4)
     pos = 0
     for c in range(b.C):
         cur = b.curve(c)
