@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Delta-chi2 evals/s (freq x H') at 1e-4*chi2_0, mixed vs FP64; % HBM peak"
 UNIT = "evals/s"
-SURVEY = ("batched survey: 4096 curves per GPU, n ~ lognormal(median 2000) in [50, 20000], "
+SURVEY_BATCH = ("batched survey: 4096 curves per GPU, n ~ lognormal(median 2000) in [50, 20000], "
           "seasonal/nightly sampling over 1000 d, H in 2..6, N=2^18 to 12/d, 30% nulls, "
           "2x oversampled grids")
 LONG = ("long single curve: n=100000, T=3000 d seasonal+nightly, sawtooth 8 harmonics, "
@@ -268,7 +268,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": SURVEY, "l2": "n/a (host)"},
+        "data": "synthetic", "config": {"workload": SURVEY_BATCH, "l2": "n/a (host)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{args.ref_bins} random trial frequencies x H'=1..H_c on each "
                                    f"of curves {picks} per step"},
@@ -528,7 +528,7 @@ def run_survey(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64 (mixed)", "data": "synthetic",
-        "config": {"workload": SURVEY, "curves_per_gpu": b.C, "samples": int(b.offsets[-1]),
+        "config": {"workload": SURVEY_BATCH, "curves_per_gpu": b.C, "samples": int(b.offsets[-1]),
                    "evals_per_step": evals, "N": int(b.N[0]), "H": "2..6",
                    "oversample": int(b.oversample), "precision": "mixed",
                    "parallelism": f"{ws} rank(s), contiguous curve ranges, no data-path collective",

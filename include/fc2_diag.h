@@ -98,6 +98,33 @@ void fc2_debug_last_tier(int tier);
 fc2_status fc2_debug_exact_bins(fc2_plan p, const int64_t* bins, int64_t nb, int tier,
                                 double* out);
 
+/* Transform pass plans (host only, no GPU needed).  A plan is a list of
+ * radices 2^r1, 2^r2, .. (first pass first) whose exponents add up to logM.
+ *
+ * fc2_debug_fft_plan: the fixed planner's plan for 2^logM points in float
+ * (fp64 = 0) or double: radices into radices[0..P), returns P (-1 if it needs
+ * more than max_passes or logM is out of 1..40).
+ *
+ * fc2_debug_fft_candidates: the plans the autotuner times, as entries
+ * [P, r1, .., rP] one after another in radices[]; returns the entries'
+ * length (-1 if max_entries is too small).
+ *
+ * fc2_debug_fft_plan_check: with validate != 0, 1 when the plan breaks a
+ * precondition of the pass kernels for the given float kernel family
+ * (fc2_options.fft_kernel; every radix has a kernel, every pass's tiles fit
+ * the grid, and each next pass's tile width is at most the current radix);
+ * otherwise (or with validate = 0) the host replay of the kernels' index
+ * arithmetic for that plan -- the global loads of each pass's input, the
+ * stores toward the next pass on each kernel's store path, the shared tile
+ * slots those stores read, the inter-pass twiddle exponents -- over the
+ * first, last and spread tiles of every pass: 0 when all are in range, else
+ * 100 * (pass + 1) + the failing check, with info4 (may be NULL) = pass,
+ * check, tile, index.  -1 on bad arguments. */
+int fc2_debug_fft_plan(int logM, int fp64, int* radices, int max_passes);
+int fc2_debug_fft_candidates(int logM, int fp64, int* radices, int max_entries);
+int fc2_debug_fft_plan_check(int logM, int fp64, int fft_kernel, const int* radices, int P,
+                             int validate, int64_t* info4);
+
 /* Kernels launched by the last fc2_execute_batched call of this process. */
 int64_t fc2_debug_batch_launches(void);
 

@@ -259,6 +259,39 @@ packed:
 // elements keeps the strided butterfly writes free of bank conflicts).
 FC2_HD constexpr int phys(int e) { return e + (e >> 5); }
 
+// ------------------------------------------------ index arithmetic of the stores
+// Shared by the pass kernels and the host replay that checks a plan's index
+// ranges (fc2_debug_fft_plan_check).
+//
+// Element e of a tile on its way to the next pass (tile width 2^LOGJ, next
+// pass's tile width 2^LOGJn): jj = its column, k = its output row.
+struct TileElem {
+    int k, jj;
+};
+FC2_HD TileElem tile_elem(int e, int LOGJn, int LOGJ) {
+    const int kl = e & ((1 << LOGJn) - 1);
+    const int jj = (e >> LOGJn) & ((1 << LOGJ) - 1);
+    const int kb = e >> (LOGJn + LOGJ);
+    return TileElem{(kb << LOGJn) + kl, jj};
+}
+// Logical (Stockham autosort) index of output k of column j of a pass of radix
+// 2^LOGR after passes of radix product 2^logNs.
+FC2_HD int64_t stockham_out(int64_t j, int k, int logNs, int LOGR) {
+    return ((j >> logNs) << (logNs + LOGR)) + (j & ((1ll << logNs) - 1)) + ((int64_t)k << logNs);
+}
+// Where the next pass (radix 2^logRn, tile width 2^LOGJn, logSn = logM - logRn)
+// finds logical index i in its blocked layout: tile i mod Sn / Jn, row
+// i / Sn, column i mod Jn.
+FC2_HD int64_t blocked_pos(int64_t i, int logSn, int LOGJn, int logBlk) {
+    const int64_t jn = i & ((1ll << logSn) - 1), rn = i >> logSn;
+    return ((jn >> LOGJn) << logBlk) + (rn << LOGJn) + (jn & ((1ll << LOGJn) - 1));
+}
+// The same when the logical index is j R + kr (a first pass whose radix and
+// the next one's multiply to the grid length): row kr of column j.
+FC2_HD int64_t rowcol_pos(int kr, int64_t j, int LOGJn, int logBlk) {
+    return ((int64_t)(kr >> LOGJn) << logBlk) + (j << LOGJn) + (kr & ((1 << LOGJn) - 1));
+}
+
 // Stage decomposition of a length-2^LOGR DFT: the first stage takes LOGR % 4
 // bits (if nonzero), every other stage 4 bits (radix 16).
 FC2_HD constexpr int stage_bits(int LOGR, int DONE) {
@@ -483,29 +516,21 @@ __global__ void __launch_bounds__(NT, 2) k_fft_pass(const cpx<T>* __restrict__ i
     const int logNs = a.logNs;
     if (!a.last) {
         cpx<T>* gout = out + (int64_t)g * M;
-        const int LOGJn = a.logJn, Jn = 1 << a.logJn;
+        const int LOGJn = a.logJn;
         const int logBlk = a.logRn + a.logJn;  // Rn * Jn
         if (logNs == 0 && a.logM - a.logRn == LOGR) {
             // two-pass plan: logical output j R + k is column k, row j of the
             // next (last) pass
             for (int e = threadIdx.x; e < E; e += NT) {
-                const int kl = e & (Jn - 1);
-                const int jj = (e >> LOGJn) & (J - 1);
-                const int kb = e >> (LOGJn + LOGJ);
-                const int k = (kb << LOGJn) + kl;
-                gout[(kb << logBlk) + ((j0 + jj) << LOGJn) + kl] = s[phys(k * J + jj)];
+                const TileElem te = tile_elem(e, LOGJn, LOGJ);
+                gout[rowcol_pos(te.k, j0 + te.jj, LOGJn, logBlk)] = s[phys(te.k * J + te.jj)];
             }
         } else {
             const int logSn = a.logM - a.logRn;
             for (int e = threadIdx.x; e < E; e += NT) {
-                const int kl = e & (Jn - 1);
-                const int jj = (e >> LOGJn) & (J - 1);
-                const int kb = e >> (LOGJn + LOGJ);
-                const int k = (kb << LOGJn) + kl;
-                const int j = j0 + jj;
-                const int i = ((j >> logNs) << (logNs + LOGR)) + (j & ((1 << logNs) - 1)) + (k << logNs);
-                const int jn = i & ((1 << logSn) - 1), rn = i >> logSn;
-                gout[((jn >> LOGJn) << logBlk) + (rn << LOGJn) + (jn & (Jn - 1))] = s[phys(k * J + jj)];
+                const TileElem te = tile_elem(e, LOGJn, LOGJ);
+                const int64_t i = stockham_out(j0 + te.jj, te.k, logNs, LOGR);
+                gout[blocked_pos(i, logSn, LOGJn, logBlk)] = s[phys(te.k * J + te.jj)];
             }
         }
     } else {
@@ -547,14 +572,9 @@ FC2_D void store_tile_blocked(cpx<T>* __restrict__ gout, const cpx<T>* s, SIdx s
         return;
     }
     for (int e = tid; e < E; e += NT) {
-        const int kl = e & (Jn - 1);
-        const int jj = (e >> LOGJn) & (J - 1);
-        const int kb = e >> (LOGJn + LOGJ);
-        const int k = (kb << LOGJn) + kl;
-        const int j = j0 + jj;
-        const int i = ((j >> logNs) << (logNs + LOGR)) + (j & ((1 << logNs) - 1)) + (k << logNs);
-        const int jn = i & ((1 << logSn) - 1), rn = i >> logSn;
-        gout[((int64_t)(jn >> LOGJn) << logBlk) + (rn << LOGJn) + (jn & (Jn - 1))] = s[sidx(k * J + jj)];
+        const TileElem te = tile_elem(e, LOGJn, LOGJ);
+        const int64_t i = stockham_out(j0 + te.jj, te.k, logNs, LOGR);
+        gout[blocked_pos(i, logSn, LOGJn, logBlk)] = s[sidx(te.k * J + te.jj)];
     }
 }
 
@@ -714,7 +734,10 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
 #pragma unroll
                         for (int q = 1; q < 8; ++q) {
                             bl[q] = mul(bl[0], twiddle(twlo, twhi, a.tws, (int64_t)((64 * q * jm) << lts)));
-                            hi[q] = twiddle(twlo, twhi, a.tws, (int64_t)((512 * q * jm) << lts));
+                            // only the factors k >> 3 < QA / 8 of this radix: their
+                            // exponents stay below M (larger ones would not)
+                            if (8 * q < QA)
+                                hi[q] = twiddle(twlo, twhi, a.tws, (int64_t)((512 * q * jm) << lts));
                         }
 #pragma unroll
                         for (int k = 0; k < QA; ++k) {
@@ -786,14 +809,11 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
                 }
             } else if (same_radix) {
                 cpx<T>* gout = out + (int64_t)g * M;
-                const int LOGJn = a.logJn, Jn = 1 << a.logJn;
+                const int LOGJn = a.logJn;
                 const int logBlk = a.logRn + a.logJn;
-                const int col = (j0 + jj) << LOGJn;
 #pragma unroll
-                for (int k = 0; k < 64; ++k) {
-                    const int kr = pp + k * QA;
-                    gout[((kr >> LOGJn) << logBlk) + col + (kr & (Jn - 1))] = v[k];
-                }
+                for (int k = 0; k < 64; ++k)
+                    gout[rowcol_pos(pp + k * QA, j0 + jj, LOGJn, logBlk)] = v[k];
             } else {
 #pragma unroll
                 for (int k = 0; k < 64; ++k) s[swz<LOGJ>((pp + k * QA) * J + jj)] = v[k];
@@ -1068,14 +1088,11 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
             }
         } else if (same_radix) {
             cpx<T>* gout = out + (int64_t)g * M;
-            const int LOGJn = a.logJn, Jn = 1 << a.logJn;
+            const int LOGJn = a.logJn;
             const int logBlk = a.logRn + a.logJn;
-            const int col = (j0 + jj) << LOGJn;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const int kr = pp + k * NSL;
-                gout[((int64_t)(kr >> LOGJn) << logBlk) + col + (kr & (Jn - 1))] = v[k];
-            }
+            for (int k = 0; k < 16; ++k)
+                gout[rowcol_pos(pp + k * NSL, j0 + jj, LOGJn, logBlk)] = v[k];
         } else {
 #pragma unroll
             for (int k = 0; k < 16; ++k) wk[phys((pp + k * NSL) * J + jj)] = v[k];
@@ -1148,6 +1165,63 @@ void plan_fft_passes(fc2_plan_s* p) {
         p->passes.push_back({rs[i], Ns, 0});
         Ns <<= rs[i];
     }
+}
+
+// The fixed planner's radices for a grid of 2^logM points (first pass first).
+static std::vector<int> balanced_plan(int logM, bool fp64) {
+    const int maxr = fp64 ? FftCfg<double>::MAXR : FftCfg<float>::MAXR;
+    if (logM <= maxr) return {logM};
+    const int P = (logM + maxr - 1) / maxr;
+    std::vector<int> rs(P, logM / P);
+    for (int i = 0; i < logM % P; ++i) rs[i] += 1;
+    return rs;
+}
+
+// ------------------------------------------------------------ pass kernels
+// Which kernel runs a pass of radix 2^logR (as run_radix chooses), its tile
+// (2^loge elements, 2^logj columns) and threads.
+enum PassKernel { PK_SINGLE = 0, PK_R16 = 1, PK_R64 = 2, PK_BULK = 3 };
+struct PassShape {
+    int kind, loge, logj, nt;
+};
+static PassShape pass_shape(int logM, bool fp64, int family, int logR) {
+    if (logR == logM) {
+        const int nt = (1 << logR) / 16 < 32 ? 32 : (1 << logR) / 16;
+        return PassShape{PK_SINGLE, logR, 0, nt};
+    }
+    if (!fp64 && family == FFT_R64 && logR >= 10 && logR <= 12)
+        return PassShape{PK_R64, P64_LOGE, P64_LOGE - logR, P64_NT};
+    if (!fp64 && family != FFT_R16 && logR >= 8 && logR <= 12)
+        return PassShape{PK_BULK, PT_LOGE, PT_LOGE - logR, PT_NT};
+    const int loge = fp64 ? FftCfg<double>::LOGE : FftCfg<float>::LOGE;
+    return PassShape{PK_R16, loge, loge - logR, fp64 ? FftCfg<double>::NT : FftCfg<float>::NT};
+}
+
+// What the pass kernels assume of a plan (radices rs, first pass first):
+//  - the radices multiply to the grid length, each has a kernel (2^5..2^12 in
+//    float, 2^5..2^11 in double; a single pass at least 2^9);
+//  - every pass's tiles fit the grid (M / R columns hold at least one tile);
+//  - a non-last pass stores its tile's R outputs per column as rows of the
+//    next pass's tiles, Jn columns at a time: the next tile width Jn must not
+//    exceed R (otherwise a tile's store walks past its R rows -- out of its
+//    shared memory and out of the grid).
+static bool fft_plan_valid(int logM, bool fp64, int family, const std::vector<int>& rs) {
+    if (rs.empty()) return false;
+    int sum = 0;
+    for (int r : rs) sum += r;
+    if (sum != logM) return false;
+    const int maxr = fp64 ? FftCfg<double>::MAXR : FftCfg<float>::MAXR;
+    if (rs.size() == 1) return logM >= 9 && logM <= maxr;
+    for (size_t i = 0; i < rs.size(); ++i) {
+        if (rs[i] < 5 || rs[i] > maxr) return false;
+        const PassShape sh = pass_shape(logM, fp64, family, rs[i]);
+        if (sh.logj < 0 || logM - rs[i] < sh.logj) return false;
+        if (i + 1 < rs.size()) {
+            const PassShape nx = pass_shape(logM, fp64, family, rs[i + 1]);
+            if (nx.logj > rs[i]) return false;
+        }
+    }
+    return true;
 }
 
 // ------------------------------------------------------ transform autotuner
@@ -1235,6 +1309,7 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
         for (int fi = 0; fi < nfam && e == cudaSuccess; ++fi) {
             for (int grp : groups) {
                 const int fam = p->fp64 ? FFT_R16 : fams_f32[fi];
+                if (!fft_plan_valid(p->logM, p->fp64, fam, rs)) continue;
                 set_passes(p, rs);
                 p->fft_family = fam;
                 p->fft_group = grp;
@@ -1270,17 +1345,12 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
     return init_twiddles(p, s);
 }
 
-// Tile width (columns) of the pass with radix 2^logR: the radix-64 kernel's
-// tiles hold 2^P64_LOGE elements, the radix-16 kernel's 2^LOGE.
+// Tile width (columns) of the pass with radix 2^logR.
 template <typename T>
 static int logj_of(const fc2_plan_s* p, int logR) {
-    if (logR == p->logM) return 0;  // single pass: one column
-    if (sizeof(T) == 4 && p->fft_family == FFT_R64 && logR >= 10 && logR <= 12)
-        return P64_LOGE - logR;
-    if (sizeof(T) == 4 && p->fft_family != FFT_R16 && logR >= 8 && logR <= 12)
-        return PT_LOGE - logR;
-    return FftCfg<T>::LOGE - logR;
+    return pass_shape(p->logM, sizeof(T) == 8, p->fft_family, logR).logj;
 }
+
 
 // ------------------------------------------------------ per-device launch state
 // The SM count of the current device, and the dynamic shared-memory limit of a
@@ -1459,7 +1529,153 @@ static cudaError_t fft_impl(fc2_plan_s* p, cudaStream_t s) {
 }
 
 cudaError_t launch_fft(fc2_plan_s* p, cudaStream_t s) {
+    std::vector<int> rs;
+    for (const auto& ps : p->passes) rs.push_back(ps.logR);
+    if (!fft_plan_valid(p->logM, p->fp64, p->fft_family, rs)) return cudaErrorInvalidValue;
     return p->fp64 ? fft_impl<double>(p, s) : fft_impl<float>(p, s);
 }
 
+// ------------------------------------------------ host replay of a plan's indices
+// Every global and shared-memory index the pass kernels form for the plan's
+// tiles, replayed on the host with the kernels' own index functions: loads of
+// a pass's input, the stores toward the next pass on each kernel's store path
+// (rows of a same-radix or two-pass plan, the one-stride fast path, the
+// general blocked layout), the shared tile slots read by those stores, and the
+// inter-pass twiddle exponents.  Returns 0 when all of them are in range for
+// the tiles of every pass (all tiles up to 64 per pass, else the first and
+// last 16 and 32 spread between them -- the index functions are monotone
+// pieces in the tile number), else 100 * (pass + 1) + the failing check;
+// info[0..3] = pass, check, tile, index.
+static int replay_plan(int logM, bool fp64, int family, const std::vector<int>& rs,
+                       int64_t* info) {
+    const int64_t M = 1ll << logM;
+    const int P = (int)rs.size();
+    int logNs = 0;
+    auto fail = [&](int pi, int check, int64_t tile, int64_t idx) {
+        if (info) { info[0] = pi; info[1] = check; info[2] = tile; info[3] = idx; }
+        return 100 * (pi + 1) + check;
+    };
+    for (int pi = 0; pi < P; ++pi) {
+        const int LOGR = rs[pi];
+        const int64_t R = 1ll << LOGR, S = M >> LOGR;
+        const PassShape sh = pass_shape(logM, fp64, family, LOGR);
+        const int LOGJ = sh.logj, J = 1 << LOGJ;
+        const int64_t E = R << LOGJ;
+        const bool first = pi == 0, last = pi == P - 1;
+        const int logRn = last ? 0 : rs[pi + 1];
+        const int LOGJn = last ? 0 : pass_shape(logM, fp64, family, logRn).logj;
+        const int logBlk = logRn + LOGJn, logSn = logM - logRn;
+        const int64_t tiles = S >> LOGJ;
+        if (tiles < 1) return fail(pi, 1, 0, S);
+        std::vector<int64_t> pick;
+        if (tiles <= 64) {
+            for (int64_t t = 0; t < tiles; ++t) pick.push_back(t);
+        } else {
+            for (int64_t t = 0; t < 16; ++t) pick.push_back(t);
+            for (int64_t t = 16; t < tiles - 16; t += (tiles - 32) / 32 + 1) pick.push_back(t);
+            for (int64_t t = tiles - 16; t < tiles; ++t) pick.push_back(t);
+        }
+        const bool same_radix = (logNs == 0 && logM - logRn == LOGR);
+        for (int64_t bx : pick) {
+            const int64_t j0 = bx << LOGJ;
+            // loads: the first pass reads rows r < R of columns j0 .. j0 + J - 1;
+            // later passes read one contiguous tile of the blocked layout
+            const int64_t ld_max = first ? j0 + (J - 1) + (R - 1) * S : bx * E + E - 1;
+            if (ld_max >= M) return fail(pi, 2, bx, ld_max);
+            // inter-pass twiddle exponents (q < M keeps both table lookups in range)
+            if (!first) {
+                const int64_t jmax = (1ll << logNs) - 1;
+                const int lts = logM - logNs - LOGR;
+                int64_t qmax = 0;
+                if (sh.kind == PK_R64) {
+                    const int QA = 1 << (LOGR - 6);
+                    qmax = std::max<int64_t>((63 * jmax) << lts, (448 * jmax) << lts);
+                    if (QA > 8) qmax = std::max<int64_t>(qmax, ((512 * ((QA / 8) - 1)) * jmax) << lts);
+                } else {
+                    const int Q1 = 1 << stage_bits(LOGR, 0);
+                    qmax = std::max<int64_t>(((R / Q1 - 1) * jmax) << lts, ((R / Q1) * jmax) << lts);
+                }
+                if (qmax >= M) return fail(pi, 3, bx, qmax);
+            }
+            if (last) continue;  // the last pass's mode stores are range-checked
+            if ((sh.kind == PK_R64 || sh.kind == PK_BULK) && same_radix) {
+                for (int64_t kr = 0; kr < R; ++kr)
+                    for (int jj = 0; jj < J; ++jj) {
+                        const int64_t gi = rowcol_pos((int)kr, j0 + jj, LOGJn, logBlk);
+                        if (gi < 0 || gi >= M) return fail(pi, 4, bx, gi);
+                    }
+                continue;
+            }
+            const bool fast = (sh.kind == PK_R64 || sh.kind == PK_BULK) && logNs == 0 &&
+                              LOGR <= logSn && LOGJn <= LOGR && (((1 << LOGJn) << LOGJ) <= sh.nt);
+            if (fast) {
+                const int Jn = 1 << LOGJn, NT = sh.nt;
+                const int dkb = NT >> (LOGJn + LOGJ);
+                for (int tid = 0; tid < NT; ++tid) {
+                    const int kl = tid & (Jn - 1);
+                    const int jj = (tid >> LOGJn) & (J - 1);
+                    const int kb0 = tid >> (LOGJn + LOGJ);
+                    const int64_t i0 = (j0 + jj) << LOGR;
+                    const int64_t jb = i0 & ((1ll << logSn) - 1), rn = i0 >> logSn;
+                    const int e0 = (kb0 << (LOGJn + LOGJ)) + (kl << LOGJ) + jj;
+                    for (int64_t it = 0; it < E / NT; ++it) {
+                        const int64_t gi = (((jb >> LOGJn) + kb0 + it * dkb) << logBlk) +
+                                           (rn << LOGJn) + kl;
+                        const int64_t se = e0 + it * NT;
+                        if (gi < 0 || gi >= M) return fail(pi, 5, bx, gi);
+                        if (se < 0 || se >= E) return fail(pi, 6, bx, se);
+                    }
+                }
+                continue;
+            }
+            const bool rowcol = sh.kind == PK_R16 && same_radix;
+            for (int64_t e = 0; e < E; ++e) {
+                const TileElem te = tile_elem((int)e, LOGJn, LOGJ);
+                if (te.k >= R || te.jj >= J) return fail(pi, 7, bx, (int64_t)te.k * J + te.jj);
+                const int64_t gi = rowcol ? rowcol_pos(te.k, j0 + te.jj, LOGJn, logBlk)
+                                          : blocked_pos(stockham_out(j0 + te.jj, te.k, logNs, LOGR),
+                                                        logSn, LOGJn, logBlk);
+                if (gi < 0 || gi >= M) return fail(pi, 8, bx, gi);
+            }
+        }
+        logNs += LOGR;
+    }
+    return 0;
+}
+
 }  // namespace fc2
+
+extern "C" int fc2_debug_fft_plan(int logM, int fp64, int* radices, int max_passes) {
+    if (!radices || logM < 1 || logM > 40) return -1;
+    const std::vector<int> rs = fc2::balanced_plan(logM, fp64 != 0);
+    if ((int)rs.size() > max_passes) return -1;
+    for (size_t i = 0; i < rs.size(); ++i) radices[i] = rs[i];
+    return (int)rs.size();
+}
+
+extern "C" int fc2_debug_fft_candidates(int logM, int fp64, int* radices, int max_entries) {
+    if (!radices || logM < 1 || logM > 40) return -1;
+    const int maxr = fp64 ? fc2::FftCfg<double>::MAXR : fc2::FftCfg<float>::MAXR;
+    int n = 0;
+    for (const auto& rs : fc2::fft_candidates(logM, maxr)) {
+        if (n + (int)rs.size() + 1 > max_entries) return -1;
+        radices[n++] = (int)rs.size();
+        for (int r : rs) radices[n++] = r;
+    }
+    return n;
+}
+
+extern "C" int fc2_debug_fft_plan_check(int logM, int fp64, int fft_kernel, const int* radices,
+                                        int P, int validate, int64_t* info4) {
+    if (!radices || P < 1 || P > 8 || logM < 1 || logM > 40) return -1;
+    std::vector<int> rs(radices, radices + P);
+    int sum = 0;
+    for (int r : rs) {
+        if (r < 1 || r > 16) return -1;
+        sum += r;
+    }
+    if (sum != logM) return -1;
+    const int fam = fc2::fft_family_of(fft_kernel);
+    if (validate && !fc2::fft_plan_valid(logM, fp64 != 0, fam, rs)) return 1;
+    return fc2::replay_plan(logM, fp64 != 0, fam, rs, info4);
+}

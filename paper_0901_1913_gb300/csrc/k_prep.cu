@@ -865,8 +865,11 @@ static cudaError_t spread_tiles(fc2_plan_s* p, cudaStream_t s) {
     int64_t Lmax = 0;
     for (auto& g : p->geom) Lmax = g.L > Lmax ? g.L : Lmax;
     int64_t tiles = (Lmax + TILE - 1) / TILE;
-    // the tile table (12 bounds per tile, at most 12 M / TILE bytes per grid)
-    // lives in the second grid buffer, which is free until the transform
+    // the tile table (12 int64 bounds per tile: at most 96 M / TILE bytes per
+    // grid, against the M complex values of a grid) lives in the second grid
+    // buffer, which is free until the transform
+    static_assert(96 / TILE < 8, "the tile table must fit the second grid buffer");
+    if (tiles * 96 > p->M * (int64_t)sizeof(cpx<T>)) return cudaErrorInvalidValue;
     int64_t* rngtab = reinterpret_cast<int64_t*>(p->d_grid[1]);
     dim3 gt((unsigned)((tiles * 12 + 127) / 128), (unsigned)p->G);
     k_tile_ranges<TILE><<<gt, 128, 0, s>>>(p->d_key, p->n, p->M, p->w, p->npk, p->H, p->w_p, p->d_L,
