@@ -613,8 +613,9 @@ def run_long(args):
 
 
 def run_profile(args):
-    """Only `warmup + steps` mixed executes of the workload, optionally with
-    fewer harmonics (--H): the command profiled by ncu.  Prints one short line
+    """Only `warmup + steps` mixed executes of the workload (the survey, the
+    differentiation batch, the large curve, else the long curve, optionally with
+    fewer harmonics (--H)): the command profiled by ncu.  Prints one short line
     that is not a benchmark result."""
     import torch
     from paper_0901_1913_gb300 import _fc2, synth
@@ -628,7 +629,10 @@ def run_profile(args):
         print(json.dumps({"profile_run": True, "workload": args.workload, "curves": b.C,
                           "stats": stats}), flush=True)
         return
-    c = synth.long_curve(seed=2, H=args.H or 6)
+    if args.workload == "large":
+        c = synth.large_curve(N=args.N) if args.N else synth.large_curve()
+    else:
+        c = synth.long_curve(seed=2, H=args.H or 6)
     dev = torch.device("cuda", 0)
     out = torch.empty((c.H, c.N), dtype=torch.float64, device=dev)
     with _fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed",
@@ -945,6 +949,8 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="only run the mixed executes (for ncu); no benchmark line")
     ap.add_argument("--H", type=int, default=0, help="harmonics of the --profile run (default 6)")
+    ap.add_argument("--N", type=int, default=0,
+                    help="trial frequencies of a --profile run of the large curve (default 2^26)")
     ap.add_argument("--workload", default="survey", choices=["survey", "long"] + sorted(k for k in WORKLOADS if k != "survey"),
                     help="survey (default, the headline) or another synthetic workload")
     ap.add_argument("--fft-kernel", default="default", choices=["default", "r64", "r16", "bulk"],

@@ -614,8 +614,16 @@ struct PrunedDFT {
 // shared-memory wavefronts, plus the stage-B twiddles.  The kernel is
 // persistent: each CTA walks tiles with a stride of the grid size and asks L2
 // to prefetch its next tile while it computes the current one.
+// With 16-column tiles (LOGJ = 4) a row is one 128-byte bank row, and the
+// row's low four bits are XORed into the column instead: the stage-A writes
+// (rows pp QA + k, columns across a warp), the stage-B reads with columns
+// across a warp and those with 16 consecutive rows across a warp (the
+// row-first store below) then each take the minimum two wavefronts.
 template <int LOGJ>
-FC2_HD int swz(int e) { return e ^ (((e >> 7) & 7) << LOGJ); }
+FC2_HD int swz(int e) {
+    if constexpr (LOGJ == 4) return e ^ ((e >> 4) & 15);
+    else return e ^ (((e >> 7) & 7) << LOGJ);
+}
 
 FC2_D void prefetch_l2_bulk(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
@@ -773,7 +781,13 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
         const int logNs = a.logNs;
         const bool same_radix = (logNs == 0 && a.logM - a.logRn == LOGR);
         {
-            const int jj = threadIdx.x % J, pp = threadIdx.x / J;  // pp < QA
+            // a store of the next pass's rows from registers fills whole lines when
+            // a warp holds 16 consecutive rows of one column (the next pass's
+            // layout is row-contiguous within a column): row-first lanes for
+            // 16-column tiles; otherwise columns across the warp
+            const bool rows_first = (LOGJ == 4) && same_radix && !a.last;
+            const int jj = rows_first ? (int)(threadIdx.x >> 4) : (int)(threadIdx.x % J);
+            const int pp = rows_first ? (int)(threadIdx.x & 15) : (int)(threadIdx.x / J);  // pp < QA
             cpx<T> v[64];
 #pragma unroll
             for (int k = 0; k < 64; ++k) v[k] = s[swz<LOGJ>((pp + k * QA) * J + jj)];

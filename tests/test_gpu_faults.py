@@ -87,10 +87,12 @@ def test_batched_call_survives_each_failed_allocation():
 
 def test_bounded_wait_gives_up_and_reports_timeout(oracle_mod):
     from paper_0901_1913_gb300 import _fc2
-    # M = 2^18 (N = 2^16, 4x oversampled): two passes of radix 2^9; the second
-    # streams its tiles into shared memory with bulk copies on mbarriers
+    # M = 2^18 (N = 2^16, 4x oversampled): two passes of radix 2^9 with the
+    # bulk-copy kernel family; the second pass streams its tiles into shared
+    # memory with bulk copies on mbarriers
     c = synth.long_curve(n=3000, N=1 << 16)
-    with _fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed") as p:
+    with _fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed",
+                   fft_kernel="bulk") as p:
         d0, _, _, chi0 = p.execute()
         p.debug_fault(wait_cycles=2_000_000, drop_tile=0)   # ~1 ms per wait
         with pytest.raises(_fc2.Fc2Error) as ei:

@@ -109,23 +109,32 @@ def test_short_curve_full_periodogram(fc2, oracle_mod, prec):
     assert abs(best[2]["f"] - 1.37) < 2 * c.df
 
 
-def test_peaks_are_oracle_local_maxima(fc2, oracle_mod):
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_peaks_are_oracle_local_maxima(fc2, oracle_mod, prec):
+    """The top-K peak records against the oracle's full periodogram: each
+    record's bin is a local maximum of the oracle's Delta chi^2_H up to the
+    parity tolerance, its value is the oracle's, the list is in decreasing
+    order, and the oracle's K largest local maxima are the records' bins up to
+    near-ties (values within the tolerance)."""
     c = synth.short_curve()
-    d, best, peaks, chi0 = fc2.periodogram(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, 2, "fp64")
-    row = d[c.H - 1]
+    d, best, peaks, chi0 = fc2.periodogram(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, 2, prec)
+    ref = oracle_mod.periodogram(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N)
+    row = ref[:, c.H - 1]
+    tol = TOL * chi0
     js = [p["j"] for p in peaks]
     assert js[0] == best[c.H - 1]["j"]
-    vals = [row[j] for j in js]
+    vals = [p["dchi2"] for p in peaks]
     assert all(vals[i] >= vals[i + 1] for i in range(len(vals) - 1))
-    for j in js:
-        left = j == 0 or row[j] > row[j - 1]
-        right = j == c.N - 1 or row[j] >= row[j + 1]
-        assert left and right
-    # no local maximum above the K-th is missing
+    for p in peaks:
+        j = p["j"]
+        assert abs(p["dchi2"] - row[j]) <= tol
+        assert j == 0 or row[j] >= row[j - 1] - tol
+        assert j == c.N - 1 or row[j] >= row[j + 1] - tol
     lm = [(row[j], j) for j in range(c.N)
           if (j == 0 or row[j] > row[j - 1]) and (j == c.N - 1 or row[j] >= row[j + 1])]
     lm.sort(key=lambda v: (-v[0], v[1]))
-    assert [j for _, j in lm[:len(js)]] == js
+    for (v_or, j_or), p in zip(lm[:len(js)], peaks):
+        assert j_or == p["j"] or abs(v_or - row[p["j"]]) <= tol
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
@@ -193,7 +202,7 @@ def test_three_pass_transform(fc2, oracle_mod, prec, N, os_):
     assert r["ok"], r
 
 
-def test_autotuned_plan_matches_fixed_plan(fc2):
+def test_autotuned_plan_matches_fixed_plan(fc2, oracle_mod):
     """The autotuner only changes the transform's pass plan and kernel family:
     results agree with the fixed plan up to float rounding."""
     c = synth.long_curve(n=20000, N=1 << 18)
@@ -207,6 +216,12 @@ def test_autotuned_plan_matches_fixed_plan(fc2):
         assert np.max(np.abs(d - out[0][0])) <= 2e-5 * chi0
         assert best[-1]["j"] == out[0][1][-1]["j"]
     assert np.array_equal(out[1][0], out[2][0])
+    # the tuned plan's results against the oracle at the parity tolerance
+    bins = sample_bins(c.N, 200, 21, windows=[out[1][1][-1]["j"]], half=4)
+    ref, piv = oracle_mod.dchi2_bins(c.t, c.x, c.sigma, c.H, c.f_min, c.df, bins,
+                                     with_pivots=True)
+    r = compare(out[1][0][:, bins].T, ref, piv, out[1][2])
+    assert r["ok"], r
 
 
 def test_pool_reuse_and_trim(fc2):
