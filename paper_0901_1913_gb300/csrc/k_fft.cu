@@ -974,12 +974,33 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
     const int logNs = a.logNs;
     const bool same_radix = (logNs == 0 && a.logM - a.logRn == LOGR);
     int it = 0;
+    // Inter-pass twiddles of stage 1 (later passes): butterfly b of thread tid
+    // holds rows pp = (tid >> LOGJ) + b R/16 (+ k R/Q1) of column jj = tid mod J,
+    // so w^{pp jm 2^lts} = t0 * w^{b (R/16) jm 2^lts}: t0 is one lookup per thread
+    // and tile, the second factor (and the step w^{(R/Q1) jm 2^lts}) one lookup per
+    // (column, b) and tile, kept in shared memory -- instead of two lookups per
+    // butterfly.
+    constexpr int TW1 = PER1 + 1;
+    __shared__ cpx<T> tw1[J * TW1];
+    cpx<T> t0 = mk<T>(1.f, 0.f);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         const int buf = it & 1;
         const int gl = tile / tiles_x;
         const int g = a.g0 + gl;
         const int bx = tile - gl * tiles_x;
         const int j0 = bx * J;
+        if (bulk && logNs > 0) {
+            // read by the previous tile's stage 1, which every thread has left (its
+            // later stages passed barriers)
+            for (int q = tid; q < J * TW1; q += NT) {
+                const int cj = q / TW1, bb = q - cj * TW1;
+                const int jm = (j0 + cj) & nsg_mask;
+                const int64_t e = (bb < PER1) ? (int64_t)bb * (R / 16) * jm : (int64_t)(R / Q1) * jm;
+                tw1[q] = twiddle(twlo, twhi, a.tws, e << lts);
+            }
+            const int jm = (j0 + (tid & (J - 1))) & nsg_mask;
+            t0 = twiddle(twlo, twhi, a.tws, (int64_t)(((tid >> LOGJ) * jm)) << lts);
+        }
         if (bulk) {
             const bool ok = mbar_wait_bounded(&mbar[buf], (unsigned)((it >> 1) & 1), wait_cycles);
             if (!__syncthreads_and(ok)) {
@@ -1020,9 +1041,8 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
                     const int jm = (j0 + jj) & nsg_mask;
                     if (logNs > 0 && jm != 0) {
                         // w_M^{(pp + k R/Q1) jm 2^lts} = base * step^k, step^k = lo[k & 3] hi[k >> 2]
-                        const cpx<T> base = twiddle(twlo, twhi, a.tws, (int64_t)((pp * jm) << lts));
-                        const cpx<T> st1 =
-                            twiddle(twlo, twhi, a.tws, (int64_t)(((R / Q1) * jm) << lts));
+                        const cpx<T> base = mul(t0, tw1[jj * TW1 + b]);
+                        const cpx<T> st1 = tw1[jj * TW1 + PER1];
                         cpx<T> lo[4], hi[4];
                         lo[0] = mk<T>(1.f, 0.f);
                         lo[1] = st1;
