@@ -121,7 +121,7 @@ static void build_design(const double* t, const double* sw, int64_t n,
 static void householder_ls(double* D, int64_t n, int m, double* y,
                            double tau_r, int* rank, int* colmap,
                            double* diag, double* qty, double* minpiv) {
-    double orig[2 * 64 + 1];
+    double orig[2 * 64 + 9];  /* up to 2H + 1 harmonic and D + 1 <= 9 polynomial columns */
     for (int l = 0; l < m; ++l) {
         nsum_t s = {0, 0};
         const double* c = D + (int64_t)l * n;
@@ -256,6 +256,75 @@ int fc2o_dchi2_freqs(const double* t, const double* x, const double* sigma,
     }
     unprep(&P);
     return 0;
+}
+
+/* ------------------------------------------- trend fitted with the harmonics
+ * The polynomial detrending of Sec. 4 ("detrend the data with a polynomial
+ * fit ... removing variation out to t^3") read as a joint fit: the null model is
+ * the weighted least-squares polynomial of degree D in t, and the model at f is
+ * that polynomial plus the H' harmonics (Sec. 1, Eq. "eqtrunc"), all fitted
+ * together:  Delta chi^2_{H'}(f) = chi^2(poly) - chi^2(poly + H' harmonics).
+ * The polynomial columns use u = (t - t_c) / s, t_c and s the centre and
+ * half-width of the time span (a change of basis, the same span).  Householder
+ * QR on the weighted design [u^0 .. u^D, sin 1, cos 1, ..] with the polynomial
+ * columns first: Delta chi^2 = |projection onto the full span|^2 - |projection
+ * onto the polynomial span|^2; minpiv as in householder_ls, over all columns.
+ * chi2_0 (chi2_0[0], may be NULL): chi^2 of the polynomial alone. */
+int fc2o_dchi2_trend_freqs(const double* t, const double* x, const double* sigma,
+                           int64_t n, int H, int D, const double* freqs, int64_t nf,
+                           double tau_r, double* dchi2, double* minpiv, double* chi2_0) {
+    if (n < 1 || H < 1 || H > 64 || D < 0 || D > 8 || nf < 0 || !t || !x || !sigma || !dchi2)
+        return -1;
+    double lo = t[0], hi = t[0];
+    for (int64_t i = 1; i < n; ++i) { if (t[i] < lo) lo = t[i]; if (t[i] > hi) hi = t[i]; }
+    const double tc = 0.5 * (lo + hi), sc = (hi > lo) ? 0.5 * (hi - lo) : 1.0;
+    const int mmax = D + 1 + 2 * H;
+    double* Dm = (double*)malloc(sizeof(double) * (size_t)n * (size_t)mmax);
+    double* y = (double*)malloc(sizeof(double) * (size_t)n);
+    double* sw = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!Dm || !y || !sw) { free(Dm); free(y); free(sw); return -2; }
+    for (int64_t i = 0; i < n; ++i) sw[i] = 1.0 / sigma[i];
+    int rc = 0;
+    for (int64_t k = 0; k <= nf; ++k) {
+        /* k == nf: the polynomial alone (chi2_0) */
+        const int Hs = (k < nf) ? H : 0;
+        for (int Hp = (k < nf) ? 1 : 0; Hp <= Hs; ++Hp) {
+            const int m = D + 1 + 2 * Hp;
+            for (int64_t i = 0; i < n; ++i) {
+                const double u = (t[i] - tc) / sc;
+                double up = 1.0;
+                for (int q = 0; q <= D; ++q) { Dm[(int64_t)q * n + i] = sw[i] * up; up *= u; }
+                y[i] = sw[i] * x[i];
+            }
+            for (int h = 1; h <= Hp; ++h) {
+                double* Ds = Dm + (int64_t)(D + 2 * h - 1) * n;
+                double* Dc = Dm + (int64_t)(D + 2 * h) * n;
+                for (int64_t i = 0; i < n; ++i) {
+                    const double th = TWO_PI * phase_frac(h, freqs[k], t[i]);
+                    Ds[i] = sw[i] * sin(th);
+                    Dc[i] = sw[i] * cos(th);
+                }
+            }
+            int rank = 0, colmap[2 * 64 + 9];
+            double diag[2 * 64 + 9], qty[2 * 64 + 9], mp = 0.0;
+            householder_ls(Dm, n, m, y, tau_r, &rank, colmap, diag, qty, &mp);
+            double ss_all = 0.0, ss_poly = 0.0;
+            for (int q = 0; q < rank; ++q) {
+                ss_all += qty[q] * qty[q];
+                if (colmap[q] <= D) ss_poly += qty[q] * qty[q];
+            }
+            if (k < nf) {
+                dchi2[k * H + (Hp - 1)] = ss_all - ss_poly;
+                if (minpiv) minpiv[k * H + (Hp - 1)] = mp;
+            } else if (chi2_0) {
+                nsum_t yy = {0, 0};
+                for (int64_t i = 0; i < n; ++i) nadd(&yy, (sw[i] * x[i]) * (sw[i] * x[i]));
+                chi2_0[0] = nval(&yy) - ss_poly;
+            }
+        }
+    }
+    free(Dm); free(y); free(sw);
+    return rc;
 }
 
 /* Same, at the trial bins f_j = f_min + j * df for j in bins[nb]. */

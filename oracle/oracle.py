@@ -57,8 +57,11 @@ def _load():
             lib.fc2o_normal_eq.argtypes = [_D, _D, _D, i64, i32, dbl, _D, _D]
             lib.fc2o_grad.argtypes = [_D, _D, _D, i64, i32, dbl, dbl, _D, _D, _D, _D]
             lib.fc2o_refine.argtypes = [_D, _D, _D, i64, i32, dbl, dbl, dbl, dbl, _D, _D]
+            lib.fc2o_dchi2_trend_freqs.argtypes = [_D, _D, _D, i64, i32, i32, _D, i64, dbl, _D,
+                                                   _D, _D]
             for fn in ("fc2o_moments", "fc2o_dchi2_freqs", "fc2o_dchi2_bins", "fc2o_coeffs",
-                       "fc2o_trig_sums", "fc2o_normal_eq", "fc2o_grad", "fc2o_refine"):
+                       "fc2o_trig_sums", "fc2o_normal_eq", "fc2o_grad", "fc2o_refine",
+                       "fc2o_dchi2_trend_freqs"):
                 getattr(lib, fn).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -132,6 +135,48 @@ def freq_of(f_min, df, j):
 def dchi2_bins(t, x, sigma, H, f_min, df, bins, threads=None, tau_r=TAU_R, with_pivots=False):
     return dchi2_freqs(t, x, sigma, H, freq_of(f_min, df, np.asarray(bins, dtype=np.int64)),
                        threads=threads, tau_r=tau_r, with_pivots=with_pivots)
+
+
+def dchi2_trend_freqs(t, x, sigma, H, D, freqs, threads=None, tau_r=TAU_R, with_pivots=False):
+    """Trend fitted jointly with the harmonics (Sec. 4's polynomial detrending
+    read as a joint fit): Delta chi^2_{H'} = chi^2(degree-D polynomial) -
+    chi^2(polynomial + H' harmonics) at each frequency: ([len(freqs), H],
+    chi2 of the polynomial alone[, minimum relative pivots])."""
+    lib = _load()
+    t, x, sigma, freqs = _f64(t), _f64(x), _f64(sigma), _f64(np.atleast_1d(freqs))
+    nf = freqs.size
+    out = np.zeros((nf, H))
+    piv = np.zeros((nf, H))
+    chi0 = np.zeros(1)
+    nt = max(1, min(_threads(threads), nf))
+    chunks = np.array_split(np.arange(nf), nt)
+
+    def run(idx):
+        fr = np.ascontiguousarray(freqs[idx])
+        o = np.zeros((idx.size, H))
+        pv = np.zeros((idx.size, H))
+        c0 = np.zeros(1)
+        rc = lib.fc2o_dchi2_trend_freqs(_p(t), _p(x), _p(sigma), t.size, H, int(D), _p(fr),
+                                        idx.size, tau_r, _p(o), _p(pv), _p(c0))
+        out[idx] = o
+        piv[idx] = pv
+        return rc, c0[0]
+
+    if nt == 1:
+        res = [run(chunks[0])]
+    else:
+        with ThreadPoolExecutor(nt) as ex:
+            res = list(ex.map(run, chunks))
+    for rc, _ in res:
+        _check(rc, "dchi2_trend")
+    chi0[0] = res[0][1]
+    return (out, float(chi0[0]), piv) if with_pivots else (out, float(chi0[0]))
+
+
+def dchi2_trend_bins(t, x, sigma, H, D, f_min, df, bins, threads=None, tau_r=TAU_R,
+                     with_pivots=False):
+    return dchi2_trend_freqs(t, x, sigma, H, D, freq_of(f_min, df, np.asarray(bins, dtype=np.int64)),
+                             threads=threads, tau_r=tau_r, with_pivots=with_pivots)
 
 
 def coeffs(t, x, sigma, Hp, f, tau_r=TAU_R):

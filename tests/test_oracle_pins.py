@@ -528,3 +528,82 @@ def test_detrend_removes_polynomials_and_is_orthogonal(oracle_mod, degree):
     if degree == 0:
         _, xbar, _, _ = oracle_mod.moments(x, sigma)
         np.testing.assert_allclose(r, x - xbar, rtol=0, atol=1e-12 * np.abs(x).max())
+
+
+# ------------------------------------------- trend fitted with the harmonics
+
+def _lstsq_resid(X, y):
+    coef, *_ = np.linalg.lstsq(X, y, rcond=None)
+    return float(np.sum((X @ coef - y) ** 2))
+
+
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_joint_trend_fit_matches_lstsq(oracle_mod, D):
+    """Delta chi^2 of the joint fit (Sec. 4's detrending read as a polynomial of
+    degree D fitted together with the harmonics) equals the difference of two
+    numpy least-squares residuals on the explicit weighted designs
+    [u^0..u^D] and [u^0..u^D, sin 2 pi h f t, cos 2 pi h f t (h <= H')]."""
+    c = synth.tiny_curve(40 + D, 70, T=25.0, H=3, N=40, f_min=0.07, df=0.013)
+    freqs = c.f_min + np.arange(0, c.N, 7) * c.df
+    d, chi0 = oracle_mod.dchi2_trend_freqs(c.t, c.x, c.sigma, c.H, D, freqs)
+    sw = 1.0 / c.sigma
+    u = (c.t - 0.5 * (c.t.min() + c.t.max())) / (0.5 * (c.t.max() - c.t.min()))
+    P = np.vander(u, D + 1, increasing=True) * sw[:, None]
+    y = c.x * sw
+    r_poly = _lstsq_resid(P, y)
+    np.testing.assert_allclose(chi0, r_poly, rtol=1e-10)
+    for k, f in enumerate(freqs):
+        for Hp in range(1, c.H + 1):
+            cols = [P]
+            for h in range(1, Hp + 1):
+                th = 2 * np.pi * h * f * c.t
+                cols.append(np.stack([np.sin(th) * sw, np.cos(th) * sw], axis=1))
+            X = np.concatenate(cols, axis=1)
+            np.testing.assert_allclose(d[k, Hp - 1], r_poly - _lstsq_resid(X, y),
+                                       rtol=1e-8, atol=1e-9 * r_poly)
+
+
+def test_joint_trend_fit_degree_zero_is_the_plain_definition(oracle_mod):
+    c = synth.tiny_curve(51, 60, T=20.0, H=3, N=30, f_min=0.1, df=0.02)
+    freqs = c.f_min + np.arange(c.N) * c.df
+    d, chi0 = oracle_mod.dchi2_trend_freqs(c.t, c.x, c.sigma, c.H, 0, freqs)
+    ref = oracle_mod.dchi2_freqs(c.t, c.x, c.sigma, c.H, freqs)
+    _, _, chi0_ref, _ = oracle_mod.moments(c.x, c.sigma)
+    np.testing.assert_allclose(d, ref, rtol=1e-9, atol=1e-9 * chi0_ref)
+    np.testing.assert_allclose(chi0, chi0_ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("D", [1, 3])
+def test_joint_trend_fit_ignores_polynomials_and_bounds_subtract_first(oracle_mod, D):
+    """Adding any polynomial of degree <= D in t to the data leaves the joint
+    fit's Delta chi^2 unchanged; and the joint fit never falls below the
+    subtract-the-trend-first reading (same baseline, more freedom)."""
+    rng = np.random.default_rng(D)
+    c = synth.tiny_curve(60 + D, 90, T=40.0, H=2, N=60, f_min=0.04, df=0.011)
+    freqs = c.f_min + np.arange(c.N) * c.df
+    d, chi0 = oracle_mod.dchi2_trend_freqs(c.t, c.x, c.sigma, c.H, D, freqs)
+    tt = (c.t - c.t.mean()) / c.t.std()
+    poly = sum(rng.normal(0, 3.0) * tt ** k for k in range(D + 1))
+    d2, chi02 = oracle_mod.dchi2_trend_freqs(c.t, c.x + poly, c.sigma, c.H, D, freqs)
+    np.testing.assert_allclose(d2, d, rtol=1e-7, atol=1e-8 * chi0)
+    np.testing.assert_allclose(chi02, chi0, rtol=1e-8)
+    xd = oracle_mod.detrend(c.t, c.x, c.sigma, D)
+    d_first = oracle_mod.dchi2_freqs(c.t, xd, c.sigma, c.H, freqs)
+    assert np.all(d >= d_first - 1e-9 * chi0)
+    assert np.any(d > d_first + 1e-6 * chi0)
+
+
+def test_joint_trend_fit_noiseless_signal_is_fully_explained(oracle_mod):
+    """x = cubic trend + 2 harmonics of f0 (on the trial grid), no noise: at f0
+    the joint fit with H' >= 2 leaves no residual, Delta chi^2 = chi^2 of the
+    trend alone."""
+    rng = np.random.default_rng(9)
+    n, f0 = 120, 0.35
+    t = np.sort(rng.uniform(0, 60.0, n))
+    sigma = rng.uniform(0.5, 1.5, n)
+    tt = t / 60.0
+    x = 2.0 - 1.5 * tt + 0.7 * tt ** 2 + 0.4 * tt ** 3
+    x += 1.2 * np.sin(2 * np.pi * f0 * t + 0.3) + 0.5 * np.cos(4 * np.pi * f0 * t - 1.1)
+    d, chi0 = oracle_mod.dchi2_trend_freqs(t, x, sigma, 3, 3, [f0])
+    np.testing.assert_allclose(d[0, 1:], chi0, rtol=1e-9)
+    assert d[0, 0] < chi0 * (1 - 1e-3)
