@@ -131,6 +131,22 @@ typedef struct {
                                   or two, the data between passes largely stay in L2);
                                   0 = library default (all grids pass by pass); values
                                   below 0 are FC2_ERR_INVALID_ARG */
+    int trend_fit;             /* with detrend = D > 0: 0 = subtract the trend first (above);
+                                  1 = fit the trend together with the harmonics (Sec. 4's
+                                  polynomial detrending as one least-squares model): the null
+                                  model is the weighted least-squares polynomial of degree D
+                                  in u = (t - t_c) / s (t_c, s the centre and half-width of
+                                  the span), and Delta chi^2_{H'} = chi^2(polynomial) -
+                                  chi^2(polynomial + H' harmonics), all coefficients fitted
+                                  jointly.  Needs the D H extra transforms
+                                  sum w u^p e^{2 pi i k f t} (p = 1..D, k = 1..H); the
+                                  per-bin system is (2H + 1 + D)-square, its polynomial
+                                  block eliminated once.  chi2_0 (fc2_execute) is the
+                                  polynomial's chi^2; in records A[0] is the polynomial's
+                                  value at t_c plus xbar and A[2H'+1 .. 2H'+D] its higher
+                                  coefficients in u.  Single-curve plans only; no paper
+                                  gridding; fc2_backward returns FC2_ERR_UNSUPPORTED.
+                                  Values other than 0 and 1 are FC2_ERR_INVALID_ARG */
 } fc2_options;
 
 /* One selected frequency: bin index, frequency, Delta chi^2 and the
@@ -251,8 +267,10 @@ fc2_status fc2_backward_batched(int64_t C, const int64_t* offsets,
  *     (ties to the lowest j) and that value.  May be NULL.
  *   adj_scale [H] (host): s_{H'} = (n - 2H' - 1) / (chi2_0 - Delta chi^2_best),
  *     so that the adjusted Delta chi^2_adj = s_{H'} Delta chi^2 (Sec. 3d, the
- *     best fit's residual chi^2 per degree of freedom as the denominator);
- *     0 when n <= 2H' + 1 or the best fit leaves no residual.  May be NULL.
+ *     best fit's residual chi^2 per degree of freedom as the denominator;
+ *     with a jointly fitted trend of degree D the degrees of freedom are
+ *     n - 2H' - 1 - D and chi2_0 is the trend's chi^2); 0 when there are no
+ *     degrees of freedom left or the best fit leaves no residual.  May be NULL.
  * Returns FC2_ERR_INVALID_ARG if p is NULL or has not completed an execute.
  * Synchronous; runs on the plan's stream.
  */

@@ -29,7 +29,7 @@ class Options(ctypes.Structure):
                 ("outputs_on_device", ctypes.c_int), ("autotune", ctypes.c_int),
                 ("fft_kernel", ctypes.c_int), ("gridding", ctypes.c_int),
                 ("detrend", ctypes.c_int), ("shared_sampling", ctypes.c_int),
-                ("fft_group", ctypes.c_int)]
+                ("fft_group", ctypes.c_int), ("trend_fit", ctypes.c_int)]
 
 # fc2_options.gridding values
 GRIDDING = {"kernel": 0, "paper": 1}
@@ -197,7 +197,7 @@ def _is_dev(a):
 def make_options(prec="fp64", kernel_width=0, top_k=0, alias_tau=0.0, stream=None, device=0,
                  inputs_on_device=False, outputs_on_device=False, autotune=False,
                  fft_kernel="default", gridding="kernel", detrend=0, shared_sampling=False,
-                 fft_group=0):
+                 fft_group=0, trend_fit=False):
     o = Options()
     load().fc2_options_default(ctypes.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -214,6 +214,7 @@ def make_options(prec="fp64", kernel_width=0, top_k=0, alias_tau=0.0, stream=Non
     o.detrend = int(detrend)
     o.shared_sampling = int(bool(shared_sampling))
     o.fft_group = int(fft_group)
+    o.trend_fit = int(bool(trend_fit))
     return o
 
 
@@ -224,7 +225,7 @@ class Plan:
     def __init__(self, t, x, sigma, H, f_min, df, N, oversample=2, prec="fp64",
                  kernel_width=0, top_k=8, alias_tau=0.0, stream=None, device=0,
                  autotune=False, fft_kernel="default", gridding="kernel", detrend=0,
-                 fft_group=0):
+                 fft_group=0, trend_fit=False):
         lib = load()
         dev = _is_dev(t)
         if not dev:
@@ -237,7 +238,8 @@ class Plan:
         self.f_min, self.df = float(f_min), float(df)
         self.opt = make_options(prec, kernel_width, self.top_k, alias_tau, stream, device,
                                 autotune=autotune, fft_kernel=fft_kernel, gridding=gridding,
-                                detrend=detrend, fft_group=fft_group, inputs_on_device=dev)
+                                detrend=detrend, fft_group=fft_group, inputs_on_device=dev,
+                                trend_fit=trend_fit)
         h = _P()
         rc = lib.fc2_plan_create(_ptr(t), _ptr(x), _ptr(sigma), self.n, self.H, self.f_min,
                                  self.df, self.N, int(oversample), ctypes.byref(self.opt),

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfc2.so")
 SOURCES = ["fc2_api.cu", "k_prep.cu", "k_fft.cu", "k_solve.cu", "k_batch.cu", "k_adjoint.cu",
-           "k_signif.cu", "fc2_host.cpp"]
+           "k_signif.cu", "k_trend.cu", "fc2_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -118,7 +118,7 @@ void free_plan_memory(fc2_plan_s* p) {
     cudaStream_t s = p->stream;
     if (!p->borrowed) { dfree(p->d_t, s); dfree(p->d_x, s); dfree(p->d_sigma, s); }
     dfree(p->d_xdet, s);
-    dfree(p->d_scal, s); dfree(p->d_status, s); dfree(p->d_perm, s);
+    dfree(p->d_scal, s); dfree(p->d_status, s); dfree(p->d_perm, s); dfree(p->d_part_t, s);
     dfree(p->d_tau, s); dfree(p->d_wq, s); dfree(p->d_wp, s);
     dfree(p->d_key, s); dfree(p->d_dlt, s); dfree(p->d_cs, s);
     dfree(p->d_grid[0], s); dfree(p->d_grid[1], s); dfree(p->d_spec, s);
@@ -153,6 +153,9 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     if (opt.fft_group < 0) return FC2_ERR_INVALID_ARG;
     if (opt.gridding < 0 || opt.gridding > 1) return FC2_ERR_INVALID_ARG;
     if (opt.detrend < 0 || opt.detrend > 3) return FC2_ERR_INVALID_ARG;
+    if (opt.trend_fit < 0 || opt.trend_fit > 1) return FC2_ERR_INVALID_ARG;
+    if (opt.trend_fit == 1 && opt.detrend == 0) return FC2_ERR_INVALID_ARG;  // no trend to fit
+    if (opt.trend_fit == 1 && opt.gridding != 0) return FC2_ERR_UNSUPPORTED;
     if (H > 8) return FC2_ERR_UNSUPPORTED;
     int64_t M = fc2_grid_size(N, oversample);
     if (M == 0) return FC2_ERR_INVALID_ARG;
@@ -199,6 +202,9 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     p->paper = (opt.gridding == 1);
     p->s0 = s0;
     p->detrend = opt.detrend;
+    p->joint = (opt.trend_fit == 1);
+    p->D = p->joint ? opt.detrend : 0;
+    if (p->joint) p->G = 3 * H + p->D * H;  // the trend transforms w u^p e^{..}, p = 1..D
     if (p->paper) p->G = 1;
     p->w = opt.kernel_width ? opt.kernel_width : default_width(p->fp64, oversample);
     const double sig_eff = (double)M / (double)N;
@@ -213,7 +219,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         const double r = f_min / df;
         const double shd = floor(r + 0.5);
         const int64_t mmax = (int64_t)shd + N - 1;
-        if (!p->paper && !p->fp64 && !opt.kernel_width && shd >= 0.0 && shd < 1e15 &&
+        if (!p->paper && !p->fp64 && !p->joint && !opt.kernel_width && shd >= 0.0 && shd < 1e15 &&
             fabs(r - shd) <= 1e-9 * std::max(1.0, r) && 4 * std::max<int64_t>(mmax, 1) <= M) {
             p->packed = true;
             p->sh = (int64_t)shd;
@@ -235,7 +241,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     const size_t csz = 2 * tsz;
     const int G = p->G;
     const int NSRC = p->nsrc ? p->nsrc : G;  // sample sets
-    const size_t spec_rows = p->packed ? (size_t)2 * G : (size_t)3 * H;
+    const size_t spec_rows = p->packed ? (size_t)2 * G : (size_t)G;
     const size_t spec_bytes = p->paper ? (size_t)M * csz : spec_rows * N * csz;
     // memory estimate
     size_t need = 0;
@@ -291,6 +297,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         g.ok(dalloc(&p->d_best, (size_t)(H + p->top_k) * sizeof(fc2_best), s));
     p->flag_cap = N;
     p->exact_cap = std::max<int64_t>(2048, H + p->top_k);
+    if (p->joint) g.ok(dalloc(&p->d_part_t, trend_part_bytes(p->exact_cap, H, p->D), s));
     g.ok(dalloc(&p->d_part, exact_scratch_bytes(n, H, p->exact_cap), s)) &&
         g.ok(dalloc(&p->d_phA, (size_t)n * 8, s)) && g.ok(dalloc(&p->d_phB, (size_t)n * 8, s)) &&
         g.ok(dalloc(&p->d_wq32, (size_t)n * 8, s)) && g.ok(dalloc(&p->d_wp32, (size_t)n * 8, s)) &&
@@ -312,7 +319,24 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     fc2_status st = FC2_OK;
     if (g.e != cudaSuccess) st = map_err(g.e);
     else if (status != 0) st = (fc2_status)status;
-    if (st == FC2_OK && p->detrend > 0) {
+    double trend_sum[11] = {0};  // joint trend fit: sum w u^k (k <= 2D), sum w x u^p (p <= D)
+    if (st == FC2_OK && p->joint) {
+        void* scratch = nullptr;
+        int nblk = 0;
+        g.ok(pool_alloc(&scratch, trend_scratch_bytes(n), s));
+        if (g.e == cudaSuccess) {
+            g.ok(launch_trend_sums(p->d_t, p->d_x, p->d_sigma, n, p->D, p->d_scal,
+                                   (double*)scratch, &nblk, s));
+            std::vector<double> part((size_t)nblk * 11);
+            g.ok(cudaMemcpyAsync(part.data(), scratch, part.size() * 8, cudaMemcpyDeviceToHost, s));
+            cudaFreeAsync(scratch, s);
+            g.ok(cudaStreamSynchronize(s));
+            for (int b = 0; b < nblk; ++b)  // in block order
+                for (int v = 0; v < 11; ++v) trend_sum[v] += part[(size_t)b * 11 + v];
+        }
+        if (g.e != cudaSuccess) st = map_err(g.e);
+    }
+    if (st == FC2_OK && p->detrend > 0 && !p->joint) {
         // Polynomial detrending (Sec. 4), then the moments of the residuals.
         // A borrowed x is left untouched: the residuals go to a plan buffer.
         double* xo = p->d_x;
@@ -342,6 +366,51 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         // (the paper's gridding: T0 = min t, its "T0 <= all t_i").
         const double back =
             p->paper ? 0.0 : (0.5 * std::max(p->w, p->w_p) + 1.0) / ((double)M * df);
+        if (p->joint) {
+            // The trend's normal equations: G = sum w u^(p+q) / W (normalised, p, q <= D),
+            // beta_P = sum w (x - xbar) u^p.  G = L_G L_G^T once; the polynomial's
+            // own chi^2 is chi2_0 - |L_G^-1 beta_P|^2 / W, and y_P, normalised by
+            // sqrt(W chi2_poly), is what every bin's elimination needs.
+            const int D = p->D;
+            const double W = trend_sum[0], xbar = p->scal[SC_XBAR];
+            double Gm[4][4], L[4][4] = {{0}}, y[4];
+            for (int a = 0; a <= D; ++a)
+                for (int b = 0; b <= D; ++b) Gm[a][b] = trend_sum[a + b] / W;
+            for (int r = 0; r <= D && st == FC2_OK; ++r) {
+                for (int c = 0; c <= r; ++c) {
+                    double v = Gm[r][c];
+                    for (int k = 0; k < c; ++k) v -= L[r][k] * L[c][k];
+                    if (r == c) {
+                        if (!(v > 1e-14 * Gm[r][r])) { st = FC2_ERR_INVALID_ARG; break; }
+                        L[r][r] = sqrt(v);
+                    } else {
+                        L[r][c] = v / L[c][c];
+                    }
+                }
+            }
+            if (st == FC2_OK) {
+                double yy = 0.0;
+                for (int r = 0; r <= D; ++r) {
+                    double v = (trend_sum[2 * D + 1 + r] - xbar * trend_sum[r]) / sqrt(W);
+                    for (int k = 0; k < r; ++k) v -= L[r][k] * y[k];
+                    y[r] = v / L[r][r];
+                    yy += y[r] * y[r];
+                }
+                const double chi_poly = p->scal[SC_CHI0] - yy;
+                if (!(chi_poly > 0.0)) st = FC2_ERR_NUMERIC;  // the trend explains everything
+                p->jt_chi0 = chi_poly;
+                p->scal[SC_CHI0] = chi_poly;  // the null model's chi^2
+                for (int r = 0; r < 4; ++r) {
+                    for (int c = 0; c < 4; ++c) p->jt_LG[r * 4 + c] = (r <= D && c <= r) ? L[r][c] : 0.0;
+                    p->jt_yP[r] = (r <= D && chi_poly > 0.0) ? y[r] / sqrt(chi_poly) : 0.0;
+                }
+                // u = (t - t_c) / s over the span: relative to tau = t - T0 (after
+                // the shift below), u = (tau - jt_tc) jt_is
+                const double tc_abs = p->scal[SC_T0] + 0.5 * p->scal[SC_TAUMAX];
+                p->jt_is = p->scal[SC_TAUMAX] > 0.0 ? 2.0 / p->scal[SC_TAUMAX] : 1.0;
+                p->jt_tc = tc_abs - (p->scal[SC_T0] - back);
+            }
+        }
         p->scal[SC_T0] -= back;
         p->scal[SC_TAUMAX] += back;
         g.ok(cudaMemcpyAsync(p->d_scal, p->scal, sizeof(p->scal), cudaMemcpyHostToDevice, s));
@@ -366,7 +435,9 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         std::vector<int64_t> Ls(NSRC), Lh(G);
         for (int gi = 0; gi < NSRC; ++gi) {  // per sample set
             GridGeom& gg = p->geom[gi];
-            if (gi < 2 * H) { gg.k = gi + 1; gg.kind = 0; } else { gg.k = gi - 2 * H + 1; gg.kind = 1; }
+            if (gi < 2 * H) { gg.k = gi + 1; gg.kind = 0; }
+            else if (gi < 3 * H) { gg.k = gi - 2 * H + 1; gg.kind = 1; }
+            else { gg.k = (gi - 3 * H) % H + 1; gg.kind = 3; }  // the trend transforms
             if (p->packed) gg.kind = 2;
             const int wg = p->packed ? p->w_p : p->w;
             const double c = (double)gg.k * df;

@@ -160,6 +160,18 @@ struct fc2_plan_s {
     int64_t stage_n = 0;
     int64_t launches = 0;      // kernels launched by the last execute
     double fft_bytes = 0;      // algorithmic bytes moved by the FFT passes per execute
+    // trend fitted with the harmonics (fc2_options.trend_fit): degree D, the
+    // scaled time u = (tau - jt_tc) jt_is, the normalised polynomial Gram factor
+    // (lower triangle of chol(sum w u^(p+q) / W), row-major 4 x 4), the projected
+    // data y_P = L_G^-1 (sum w (x - xbar) u^p) / sqrt(W chi2_poly), chi2_poly,
+    // and the exact trend sums' partials [exact_cap][chunks][2 D H]
+    bool joint = false;
+    int D = 0;
+    double jt_tc = 0, jt_is = 1;
+    double jt_LG[16] = {0};
+    double jt_yP[4] = {0};
+    double jt_chi0 = 0;
+    double* d_part_t = nullptr;
     // fault injection for the tests (fc2_debug_fault): limit of the bulk-copy
     // transform's mbarrier waits in SM cycles (0 = default, about two seconds),
     // and a tile whose copy that kernel arms but never issues (-1 = none)
@@ -206,6 +218,20 @@ cudaError_t launch_fft(fc2_plan_s* p, cudaStream_t s);
 cudaError_t launch_assemble(fc2_plan_s* p, cudaStream_t s);
 cudaError_t launch_fixup(fc2_plan_s* p, int64_t n1, int64_t n2, int64_t n3, cudaStream_t s);
 cudaError_t launch_exact_bins(fc2_plan_s* p, int64_t nb, int tier, cudaStream_t s);
+// The double tier's partial sums for H harmonics (k_exact_partial<H, 3>).
+cudaError_t launch_exact_partial_tier3(fc2_plan_s* p, int H, const int32_t* b32,
+                                       const int64_t* b64, const int32_t* cnt_dev, int64_t cnt,
+                                       int64_t base, int64_t cap, cudaStream_t s);
+// k_trend.cu: the trend fitted with the harmonics (p->joint)
+cudaError_t launch_assemble_joint(fc2_plan_s* p, cudaStream_t s);
+cudaError_t launch_fixup_joint(fc2_plan_s* p, int64_t n3, cudaStream_t s);
+cudaError_t launch_records_joint(fc2_plan_s* p, const int64_t* rec_j, int nrec, int nch,
+                                 cudaStream_t s);
+size_t trend_part_bytes(int64_t cap, int H, int D);
+// k_prep.cu: block partial sums of w u^k (k <= 2D) and w x u^p (p <= D) of the
+// detrending (u on [-1, 1] over the span); nblk * 11 doubles into part
+cudaError_t launch_trend_sums(const double* t, const double* x, const double* sigma, int64_t n,
+                              int D, const double* scal, double* part, int* nblk, cudaStream_t s);
 // Last tier of the mixed path's exact fix-up (4 by default, 3 for diagnostics).
 void set_last_fixup_tier(int tier);
 int last_fixup_tier();

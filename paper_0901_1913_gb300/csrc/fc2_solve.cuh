@@ -237,6 +237,48 @@ FC2_D uint64_t frac_fx(double a, double b) {
     return hi + (uint64_t)lo;
 }
 
+// ------------------------------------------------------------ exact sums
+// Geometry of the exact sums' work items (bin, chunk of samples).
+constexpr int EX_NT = 256;
+constexpr int EX_GRID = 4 * 152;
+constexpr int EX_MAX_CHUNKS = 64;
+
+// Chunks of the sample range of each bin (at least 16 samples per thread, at
+// most EX_MAX_CHUNKS).  While the bins do not outnumber the EX_GRID CTAs, the
+// chunk count is rounded down so that no CTA gets more than two items (a
+// third item on a few CTAs stretches the launch by one item time); with more
+// bins than CTAs, each bin is cut as finely as allowed, so that the
+// grid-stride loop hands every SM about the same share of small items.
+// Evaluated identically on host and device, so kernels that read the bin
+// count from device memory derive the same geometry.
+FC2_HD void exact_geometry(int64_t n, int64_t count, int64_t* chunk, int* nch) {
+    if (count < 1) count = 1;
+    int64_t want = count <= EX_GRID ? (2 * EX_GRID) / count : EX_MAX_CHUNKS;
+    if (want > EX_MAX_CHUNKS) want = EX_MAX_CHUNKS;
+    int64_t c = (n + want - 1) / want;
+    if (c < 16 * EX_NT) c = 16 * EX_NT;
+    c = ((c + EX_NT - 1) / EX_NT) * EX_NT;
+    *chunk = c;
+    *nch = (int)((n + c - 1) / c);
+}
+
+
+// Warp w of the CTA owns record b: lanes add the chunk partials of values
+// v = lane, lane + 32, ... in chunk order into sh[], then every lane of the
+// warp can read the full sums.
+template <int HM>
+FC2_D void warp_sum_chunks(const double* __restrict__ part, int64_t b, int nch, double* sh) {
+    constexpr int NV = 6 * HM;
+    const int lane = threadIdx.x & 31;
+    for (int v = lane; v < NV; v += 32) {
+        double a = 0.0;
+        for (int c = 0; c < nch; ++c) a += part[((b * nch) + c) * NV + v];
+        sh[v] = a;
+    }
+    __syncwarp();
+}
+
+
 // Normalised system from exact sums acc = [Q_1..Q_2H (re, im) | P_1..P_H (re, im)]
 // laid out with stride 4 HM between the Q and P parts.
 template <int HM>

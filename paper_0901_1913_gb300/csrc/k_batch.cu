@@ -1066,6 +1066,8 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     if (opt.gridding == 1) return FC2_ERR_UNSUPPORTED;
     if (opt.detrend < 0 || opt.detrend > 3) return FC2_ERR_INVALID_ARG;
     if (opt.detrend != 0) return FC2_ERR_UNSUPPORTED;
+    if (opt.trend_fit < 0 || opt.trend_fit > 1) return FC2_ERR_INVALID_ARG;
+    if (opt.trend_fit != 0) return FC2_ERR_UNSUPPORTED;
     if (opt.shared_sampling < 0 || opt.shared_sampling > 1) return FC2_ERR_INVALID_ARG;
     const bool shared = opt.shared_sampling == 1;
     for (int64_t c = 0; c < C && shared; ++c)  // one sampling: same n, H and trial grid

@@ -336,6 +336,13 @@ __global__ void k_trend_apply(const double* __restrict__ t, const double* __rest
     xo[i] = x[i] - v;
 }
 
+cudaError_t launch_trend_sums(const double* t, const double* x, const double* sigma, int64_t n,
+                              int D, const double* scal, double* part, int* nblk, cudaStream_t s) {
+    *nblk = (int)((n + TR_NT - 1) / TR_NT);
+    k_trend_partial<<<*nblk, TR_NT, 0, s>>>(t, x, sigma, n, scal, D, part);
+    return cudaGetLastError();
+}
+
 size_t trend_scratch_bytes(int64_t n) {
     return (size_t)((n + TR_NT - 1) / TR_NT) * TR_NV * sizeof(double) + 64;
 }
@@ -529,16 +536,21 @@ cudaError_t launch_gather_sorted(const double* t, const double* x, const double*
 //   sum_i c_i e^{2 pi i theta_i} e^{2 pi i m u_i}.
 // All products and differences use explicit round-to-nearest intrinsics so no
 // contraction changes the reduced phase.
+// Transforms g >= 3H (the trend fitted with the harmonics) carry the strengths
+// w u^p e^{..} at multiple k: g = 3H + (p - 1) H + k - 1, u = (tau - tc) is.
 template <typename T>
 __global__ void k_phase(const double* __restrict__ tau, const double* __restrict__ wq,
                         const double* __restrict__ wp, int64_t n, int H, double f_min,
-                        double df, int64_t N, int64_t M, int w, int32_t* __restrict__ key,
-                        T* __restrict__ dlt, cpx<T>* __restrict__ cs) {
+                        double df, int64_t N, int64_t M, int w, double tc, double is,
+                        int32_t* __restrict__ key, T* __restrict__ dlt,
+                        cpx<T>* __restrict__ cs) {
     const int g = blockIdx.y;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    int k, kind;
-    if (g < 2 * H) { k = g + 1; kind = 0; } else { k = g - 2 * H + 1; kind = 1; }
+    int k, kind, pw = 0;
+    if (g < 2 * H) { k = g + 1; kind = 0; }
+    else if (g < 3 * H) { k = g - 2 * H + 1; kind = 1; }
+    else { pw = (g - 3 * H) / H + 1; k = (g - 3 * H) % H + 1; kind = 3; }
     const double ts = tau[s];
     const double c = __dmul_rn((double)k, df);
     const double p = __dmul_rn(c, ts);
@@ -553,7 +565,11 @@ __global__ void k_phase(const double* __restrict__ tau, const double* __restrict
     const double th = __dadd_rn(__dsub_rn(q1, floor(q1)), __dsub_rn(q2, floor(q2)));
     double sn, cn;
     sincospi(2.0 * th, &sn, &cn);
-    const double amp = kind == 0 ? wq[s] : wp[s];
+    double amp = kind == 1 ? wp[s] : wq[s];
+    if (kind == 3) {
+        const double u = (ts - tc) * is;
+        for (int q = 0; q < pw; ++q) amp *= u;
+    }
     const int64_t o = (int64_t)g * n + s;
     key[o] = kk;
     dlt[o] = (T)de;
@@ -568,16 +584,21 @@ __global__ void k_phase(const double* __restrict__ tau, const double* __restrict
 __global__ void k_phase_fx32(const uint64_t* __restrict__ A, const uint64_t* __restrict__ B,
                              const float* __restrict__ wq32, const float* __restrict__ wp32,
                              int64_t n, int H, int64_t N, int logM, int w, int npk, int w_p,
+                             const double* __restrict__ tau, double tc, double is,
                              int32_t* __restrict__ key, float* __restrict__ dlt,
                              cpx<float>* __restrict__ cs) {
     const int g = blockIdx.y;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    // g indexes sample sets: Q_{g+1}, P_{g-2H+1} unpacked; packed (npk > 0):
-    // set g is Q_{g+1}, carrying P_{g+1} as imaginary part when g < H and
-    // otherwise placed in the real (even g - H) or imaginary part of its grid
-    int k, kind;
-    if (g < 2 * H) { k = g + 1; kind = 0; } else { k = g - 2 * H + 1; kind = 1; }
+    // g indexes sample sets: Q_{g+1}, P_{g-2H+1} unpacked, then the trend
+    // transforms (w u^p at multiple k, g = 3H + (p - 1) H + k - 1); packed
+    // (npk > 0): set g is Q_{g+1}, carrying P_{g+1} as imaginary part when
+    // g < H and otherwise placed in the real (even g - H) or imaginary part of
+    // its grid
+    int k, kind, pw = 0;
+    if (g < 2 * H) { k = g + 1; kind = 0; }
+    else if (g < 3 * H) { k = g - 2 * H + 1; kind = 1; }
+    else { pw = (g - 3 * H) / H + 1; k = (g - 3 * H) % H + 1; kind = 3; }
     if (npk > 0) { kind = 2; w = w_p; }
     const uint64_t uk = (uint64_t)k * B[s];
     const int32_t cell = (int32_t)(uk >> (64 - logM));                 // floor(M u)
@@ -606,7 +627,11 @@ __global__ void k_phase_fx32(const uint64_t* __restrict__ A, const uint64_t* __r
     const uint64_t th = (uint64_t)k * A[s] + (uint64_t)(N / 2) * uk;
     float sn, cn;
     sincospif((float)(int32_t)(th >> 32) * 4.656612873077393e-10f, &sn, &cn);  // 2^-31
-    const float amp = kind == 0 ? wq32[s] : wp32[s];
+    float amp = kind == 1 ? wp32[s] : wq32[s];
+    if (kind == 3) {
+        const float u = (float)((tau[s] - tc) * is);
+        for (int q = 0; q < pw; ++q) amp *= u;
+    }
     cs[o] = mk<float>(amp * cn, amp * sn);
 }
 
@@ -677,12 +702,13 @@ static cudaError_t phase_impl(fc2_plan_s* p, cudaStream_t s) {
     dim3 grid((unsigned)((p->n + 255) / 256), (unsigned)nsrc);
     if constexpr (sizeof(T) == 4)
         k_phase_fx32<<<grid, 256, 0, s>>>(p->d_phA, p->d_phB, p->d_wq32, p->d_wp32, p->n, p->H,
-                                          p->N, p->logM, p->w, p->npk, p->w_p, p->d_key,
-                                          (float*)p->d_dlt, (cpx<float>*)p->d_cs);
+                                          p->N, p->logM, p->w, p->npk, p->w_p, p->d_tau,
+                                          p->jt_tc, p->jt_is, p->d_key, (float*)p->d_dlt,
+                                          (cpx<float>*)p->d_cs);
     else
         k_phase<T><<<grid, 256, 0, s>>>(p->d_tau, p->d_wq, p->d_wp, p->n, p->H, p->f_min, p->df,
-                                        p->N, p->M, p->w, p->d_key, (T*)p->d_dlt,
-                                        (cpx<T>*)p->d_cs);
+                                        p->N, p->M, p->w, p->jt_tc, p->jt_is, p->d_key,
+                                        (T*)p->d_dlt, (cpx<T>*)p->d_cs);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     for (int g = 0; g < nsrc; ++g)

@@ -106,8 +106,9 @@ __global__ void __launch_bounds__(SG_NT) k_logp1(const double* __restrict__ d, i
 // its ln p and the adjusted-Delta chi^2 factor of the row.
 __global__ void k_logp2(const Cand* __restrict__ bmin, int nblk, const double* __restrict__ d,
                         int64_t N, int H, double f0, const fc2_best* __restrict__ best,
-                        const double* __restrict__ scal, int64_t n, int64_t* __restrict__ jmin,
-                        double* __restrict__ lpmin, double* __restrict__ adj) {
+                        const double* __restrict__ scal, int64_t n, int extra,
+                        int64_t* __restrict__ jmin, double* __restrict__ lpmin,
+                        double* __restrict__ adj) {
     const int h = blockIdx.x;
     const int lane = threadIdx.x;
     if (h >= H) return;
@@ -123,7 +124,7 @@ __global__ void k_logp2(const Cand* __restrict__ bmin, int nblk, const double* _
     lpmin[h] = found ? log_p_of(d[(int64_t)h * N + jb], h + 1, log_fhat(f0, jb)) : 0.0;
     const double chi0 = scal[SC_CHI0];
     const double resid = chi0 - best[h].dchi2;
-    const double dof = (double)(n - 2 * (h + 1) - 1);
+    const double dof = (double)(n - 2 * (h + 1) - 1 - extra);  // extra: a jointly fitted trend
     adj[h] = (resid > 0.0 && dof > 0.0) ? dof / resid : 0.0;
 }
 
@@ -142,7 +143,7 @@ cudaError_t launch_significance(fc2_plan_s* p, double* logp, int64_t* jmin, doub
     if (e != cudaSuccess) return e;
     k_logp1<<<(unsigned)nblk, SG_NT, 0, s>>>(p->d_dchi2, N, H, f0, logp, bmin, nblk);
     k_logp2<<<(unsigned)H, 32, 0, s>>>(bmin, nblk, p->d_dchi2, N, H, f0, p->d_best, p->d_scal,
-                                       p->n, jmin, lpmin, adj);
+                                       p->n, p->joint ? p->D : 0, jmin, lpmin, adj);
     e = cudaGetLastError();
     cudaFreeAsync(bmin, s);
     return e;

@@ -260,29 +260,6 @@ __global__ void __launch_bounds__(128) k_resolve(const cpx<float>* __restrict__ 
 //    powers by multiplication) and double-float accumulation; worst-case
 //    error ~1e-12 * sum w, on the float pipes.
 //  - tier 3: everything in double (powers of e^{2 pi i f tau_i}).
-constexpr int EX_NT = 256;
-constexpr int EX_GRID = 4 * 152;
-constexpr int EX_MAX_CHUNKS = 64;
-
-// Chunks of the sample range of each bin (at least 16 samples per thread, at
-// most EX_MAX_CHUNKS).  While the bins do not outnumber the EX_GRID CTAs, the
-// chunk count is rounded down so that no CTA gets more than two items (a
-// third item on a few CTAs stretches the launch by one item time); with more
-// bins than CTAs, each bin is cut as finely as allowed, so that the
-// grid-stride loop hands every SM about the same share of small items.
-// Evaluated identically on host and device, so kernels that read the bin
-// count from device memory derive the same geometry.
-FC2_HD void exact_geometry(int64_t n, int64_t count, int64_t* chunk, int* nch) {
-    if (count < 1) count = 1;
-    int64_t want = count <= EX_GRID ? (2 * EX_GRID) / count : EX_MAX_CHUNKS;
-    if (want > EX_MAX_CHUNKS) want = EX_MAX_CHUNKS;
-    int64_t c = (n + want - 1) / want;
-    if (c < 16 * EX_NT) c = 16 * EX_NT;
-    c = ((c + EX_NT - 1) / EX_NT) * EX_NT;
-    *chunk = c;
-    *nch = (int)((n + c - 1) / c);
-}
-
 // Fixed-point phases: A_i = frac(f_min tau_i) 2^64 and B_i = frac(df tau_i) 2^64
 // (u64, from the exact double-double products), so that the phase of trial
 // bin j is A_i + j B_i modulo 2^64 -- an exact integer, as is k times it.
@@ -530,21 +507,6 @@ __global__ void __launch_bounds__(EX_NT) k_exact_partial(
         }
         __syncthreads();
     }
-}
-
-// Warp w of the CTA owns record b: lanes add the chunk partials of values
-// v = lane, lane + 32, ... in chunk order into sh[], then every lane of the
-// warp can read the full sums.
-template <int HM>
-FC2_D void warp_sum_chunks(const double* __restrict__ part, int64_t b, int nch, double* sh) {
-    constexpr int NV = 6 * HM;
-    const int lane = threadIdx.x & 31;
-    for (int v = lane; v < NV; v += 32) {
-        double a = 0.0;
-        for (int c = 0; c < nch; ++c) a += part[((b * nch) + c) * NV + v];
-        sh[v] = a;
-    }
-    __syncwarp();
 }
 
 // Final step of a fix-up round: solve from the exact sums; bins whose
@@ -865,6 +827,7 @@ static cudaError_t assemble_impl(fc2_plan_s* p, cudaStream_t s) {
 }
 
 cudaError_t launch_assemble(fc2_plan_s* p, cudaStream_t s) {
+    if (p->joint) return launch_assemble_joint(p, s);
     return p->fp64 ? assemble_impl<double>(p, s) : assemble_impl<float>(p, s);
 }
 
@@ -875,6 +838,23 @@ static void launch_partial(fc2_plan_s* p, const int32_t* b32, const int64_t* b64
     k_exact_partial<HH, TIER><<<EX_GRID, EX_NT, 0, s>>>(
         p->d_phA, p->d_phB, p->d_wq32, p->d_wp32, p->d_wq, p->d_wp, (const dfc*)p->d_dftab, p->n,
         b32, b64, cnt_dev, cnt, base, cap, p->H, p->d_part);
+}
+
+cudaError_t launch_exact_partial_tier3(fc2_plan_s* p, int H, const int32_t* b32,
+                                       const int64_t* b64, const int32_t* cnt_dev, int64_t cnt,
+                                       int64_t base, int64_t cap, cudaStream_t s) {
+    switch (H) {
+        case 1: launch_partial<1, 3>(p, b32, b64, cnt_dev, cnt, base, cap, s); break;
+        case 2: launch_partial<2, 3>(p, b32, b64, cnt_dev, cnt, base, cap, s); break;
+        case 3: launch_partial<3, 3>(p, b32, b64, cnt_dev, cnt, base, cap, s); break;
+        case 4: launch_partial<4, 3>(p, b32, b64, cnt_dev, cnt, base, cap, s); break;
+        case 5: launch_partial<5, 3>(p, b32, b64, cnt_dev, cnt, base, cap, s); break;
+        case 6: launch_partial<6, 3>(p, b32, b64, cnt_dev, cnt, base, cap, s); break;
+        case 7: launch_partial<7, 3>(p, b32, b64, cnt_dev, cnt, base, cap, s); break;
+        case 8: launch_partial<8, 3>(p, b32, b64, cnt_dev, cnt, base, cap, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // Worst-case relative error of the double-float sums: phasor powers up to
@@ -964,6 +944,7 @@ cudaError_t launch_exact_bins(fc2_plan_s* p, int64_t nb, int tier, cudaStream_t 
 }
 
 cudaError_t launch_fixup(fc2_plan_s* p, int64_t n1, int64_t n2, int64_t n3, cudaStream_t s) {
+    if (p->joint) return launch_fixup_joint(p, n3, s);  // every flagged bin: exact double sums
     switch (p->H) {
         case 1: return fixup_h<1>(p, n1, n2, n3, s);
         case 2: return fixup_h<2>(p, n1, n2, n3, s);
@@ -1003,6 +984,7 @@ cudaError_t launch_peaks(fc2_plan_s* p, cudaStream_t s) {
     int64_t chunk;
     int nch;
     exact_geometry(p->n, nrec, &chunk, &nch);
+    if (p->joint) return launch_records_joint(p, rec_j, nrec, nch, s);
 #define FC2_CO(HH)                                                                            \
     case HH:                                                                                  \
         launch_partial<HH, 1>(p, nullptr, rec_j, nullptr, nrec, 0, nrec, s);               \
