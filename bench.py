@@ -412,7 +412,7 @@ def run_survey(args):
     barrier(ws)
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        call(tp, xp, sp, hout)
+        _, _, st_e2e = call(tp, xp, sp, hout)
     e2e_s = allreduce_max(ws, (time.perf_counter() - t0) / e2e_steps)
     del hout
 
@@ -542,6 +542,8 @@ def run_survey(args):
                 "d2h_bytes_per_step": int(4 * evals + b.C * K * _fc2.BEST_DTYPE.itemsize),
                 "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
                 "cold_first_call_ms": cold_ms,
+                "host_phase_ms_last_call": {k: round(v, 2) for k, v in
+                                            st_e2e["host_phase_ms"].items()},
                 "includes": "fc2_execute_batched from pinned host arrays (t, x, sigma) to pinned "
                             "host Delta chi^2 and peak records; the cold call is the process's "
                             "first library call"},

@@ -807,6 +807,7 @@ struct Batch {
     char *dlt = nullptr, *cs = nullptr; size_t cdlt = 0, ccs = 0;
     char *grid0 = nullptr, *grid1 = nullptr, *spec = nullptr; size_t cg0 = 0, cg1 = 0, cspec = 0;
     float* out = nullptr; size_t cout = 0;
+    float* out2 = nullptr; size_t cout2 = 0;  // second host-bound output buffer
     int64_t *list = nullptr, *list2 = nullptr, *list3 = nullptr, *list4 = nullptr;
     size_t cl1 = 0, cl2 = 0, cl3 = 0, cl4 = 0;
     char* dftab = nullptr; size_t cdftab = 0;  // phasor tables of the exact sums
@@ -816,7 +817,18 @@ struct Batch {
     int* curves = nullptr; size_t ccurves = 0;
     Cand* tops = nullptr; size_t ctops = 0;
     int64_t* pent = nullptr; size_t cpent = 0;
-    fc2_best* recs = nullptr; size_t crecs = 0;
+    fc2_best* recs = nullptr; size_t crecs = 0;  // every curve's peak records [C][K]
+    fc2_best* recs_now = nullptr;  // the records of the chunk being launched
+    int32_t* cnt_hist = nullptr; size_t chist = 0;  // every chunk's counters, [chunk][16]
+    // mapped host memory for the per-chunk moments and status word
+    char* hmap = nullptr;
+    char* hmap_dev = nullptr;
+    // copy-out overlap: the host copies of chunk i run on their own stream while
+    // chunk i + 1 computes; chunks alternate between two output buffers, and a
+    // chunk waits for the copies of the chunk two before it (same buffers)
+    cudaStream_t cs2 = nullptr;
+    cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+    bool copied_pending[2] = {false, false};
     char* red = nullptr; size_t cred = 0;
     cudaGraphExec_t gexec = nullptr;
     int64_t graphs = 0;  // chunk graphs launched
@@ -842,15 +854,24 @@ struct Batch {
         release(s1n, s); release(chi0f, s); release(slot_cur, s); release(slot_k, s);
         release(slot_kind, s); release(slot_soff, s); release(slot_n, s); release(L, s);
         release(key, s); release(dlt, s); release(cs, s); release(grid0, s); release(grid1, s);
-        release(spec, s); release(out, s); release(list, s); release(list2, s); release(list3, s);
+        release(spec, s); release(out, s); release(out2, s); release(list, s); release(list2, s); release(list3, s);
         release(list4, s); release(dftab, s); release(qbase, s); release(items, s); release(part, s);
         release(counts, s); release(curves, s); release(tops, s); release(pent, s);
-        release(recs, s); release(red, s);
+        release(recs, s); release(cnt_hist, s); release(red, s);
         release(cp.d_twlo, s); release(cp.d_twhi, s); release(cp.d_twst, s); release(cp.d_dec, s);
         if (gexec) cudaGraphExecDestroy(gexec);
         gexec = nullptr;
         for (auto& e : ev)
             if (e) { cudaEventDestroy(e); e = nullptr; }
+        for (int i = 0; i < 2; ++i) {
+            if (ev_ready[i]) cudaEventDestroy(ev_ready[i]);
+            if (ev_copied[i]) cudaEventDestroy(ev_copied[i]);
+            ev_ready[i] = ev_copied[i] = nullptr;
+        }
+        if (cs2) cudaStreamDestroy(cs2);
+        cs2 = nullptr;
+        if (hmap) cudaFreeHost(hmap);
+        hmap = hmap_dev = nullptr;
     }
 };
 
@@ -860,6 +881,16 @@ void set_batch_timing(bool on) { g_batch_timing = on; }
 
 
 __global__ void k_set_count(int32_t* c, int32_t v) { *c = v; }
+
+// Word copy by a kernel: small results go to mapped host memory (and counters to
+// their history) without a copy-engine transfer, which would queue behind the
+// large host copy of the previous chunk's periodogram.
+__global__ void k_copy_words(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst,
+                             int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
 
 // Shared sampling: every curve of the chunk must have the first curve's times
 // and errors proportional to its errors (sigma_c = r_c sigma_0, so that their
@@ -1007,7 +1038,7 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
         k_bpeaks1<<<dim3((unsigned)nblk, (unsigned)nc), BP_NT, 0, s>>>(out, N, ct, K, nblk, b.tops);
         k_bpeaks2<<<(unsigned)nc, 256, 0, s>>>(b.tops, nblk, K, b.pent);
         nl += 2;
-        exact(I2{}, I1{}, b.pent, b.counts + 4, nrec, tau_drop, nullptr, nullptr, 0, b.recs);
+        exact(I2{}, I1{}, b.pent, b.counts + 4, nrec, tau_drop, nullptr, nullptr, 0, b.recs_now);
     }
     mark(5);
     b.launches += nl;
@@ -1162,7 +1193,39 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     }
     const int64_t mx_nc = mx.c1, mx_nrec = mx_nc * K;
     b.phase_ms[0] = ms_since(t_entry, now());
-    for (const Chunk& ch : chunks) {
+    // a host-bound periodogram is copied on a second stream (overlapping the next
+    // chunk); with stage timing on, every chunk is waited for instead, so that
+    // its stage events can be read before the next chunk records them again.
+    // Every curve's peak records stay on the device until the end.
+    const bool copy_out = !b.timing && dchi2 && !out_dev;
+    if (copy_out) {
+        bool good = cudaStreamCreateWithFlags(&b.cs2, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; i < 2 && good; ++i)
+            good = cudaEventCreateWithFlags(&b.ev_ready[i], cudaEventDisableTiming) == cudaSuccess &&
+                   cudaEventCreateWithFlags(&b.ev_copied[i], cudaEventDisableTiming) == cudaSuccess;
+        if (!good) {
+            cudaGetLastError();
+            b.free_all();
+            if (b.own_stream) cudaStreamDestroy(s);
+            return FC2_ERR_CUDA;
+        }
+    }
+    {
+        const size_t bytes = (size_t)mx_nc * SC_COUNT * 8 + 64;
+        if (cudaHostAlloc((void**)&b.hmap, bytes, cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer((void**)&b.hmap_dev, b.hmap, 0) != cudaSuccess) {
+            cudaGetLastError();
+            b.free_all();
+            if (b.own_stream) cudaStreamDestroy(s);
+            return FC2_ERR_OOM;
+        }
+    }
+    const size_t nchunks = chunks.size();
+    std::vector<int32_t> hist(nchunks * 16, 0);
+    size_t launched = 0;  // chunks whose graph was launched
+    for (size_t ci = 0; ci < nchunks; ++ci) {
+        const Chunk& ch = chunks[ci];
+        const int slot = (int)(ci & 1);
         if (st != FC2_OK) break;
         c0 = ch.c0;
         const int64_t c1 = ch.c1, S = ch.S, ntot = ch.ntot, nmax = ch.nmax, N = ch.N, M = ch.M;
@@ -1244,9 +1307,12 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             ok(need(&b.counts, &b.ccnt, 16, s)) && ok(need(&b.curves, &b.ccurves, mxc, s)) &&
             ok(need(&b.tops, &b.ctops, mx_tops, s)) &&
             ok(need(&b.pent, &b.cpent, (size_t)std::max<int64_t>(mx_nrec, 1), s)) &&
-            ok(need(&b.recs, &b.crecs, (size_t)std::max<int64_t>(mx_nrec, 1), s));
+            ok(need(&b.recs, &b.crecs, (size_t)std::max<int64_t>(C * K, 1), s)) &&
+            ok(need(&b.cnt_hist, &b.chist, nchunks * 16, s));
+        b.recs_now = b.recs + c0 * K;
         float* out = nullptr;
         if (dchi2 && out_dev) out = dchi2 + out_global;
+        else if (copy_out && slot) { if (ok(need(&b.out2, &b.cout2, (size_t)mx.out, s))) out = b.out2; }
         else if (ok(need(&b.out, &b.cout, (size_t)mx.out, s))) out = b.out;
         if (e != cudaSuccess) { st = map_cuda(e); break; }
         // ---- moments per curve, then host-side geometry
@@ -1265,9 +1331,17 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         ok(launch_moments(b.t, b.x, b.sg, b.off, nc, 0, b.scal, b.counts + 8, s));
         std::vector<double> scal((size_t)nc * SC_COUNT);
         int32_t status = 0;
-        ok(cudaMemcpyAsync(scal.data(), b.scal, scal.size() * 8, cudaMemcpyDeviceToHost, s));
-        ok(cudaMemcpyAsync(&status, b.counts + 8, 4, cudaMemcpyDeviceToHost, s));
+        const int64_t nsw = (int64_t)scal.size() * 2;  // 32-bit words of the moments
+        k_copy_words<<<(unsigned)std::min<int64_t>((nsw + 255) / 256, 1024), 256, 0, s>>>(
+            (const uint32_t*)b.scal, (uint32_t*)b.hmap_dev, nsw);
+        k_copy_words<<<1, 32, 0, s>>>((const uint32_t*)(b.counts + 8),
+                                      (uint32_t*)(b.hmap_dev + 8 * nsw / 2), 1);
+        ok(cudaGetLastError());
         ok(cudaStreamSynchronize(s));
+        if (e == cudaSuccess) {
+            std::memcpy(scal.data(), b.hmap, scal.size() * 8);
+            std::memcpy(&status, b.hmap + scal.size() * 8, 4);
+        }
         const auto tp1 = now();
         b.phase_ms[2] += ms_since(tp0, tp1);
         if (e != cudaSuccess) { st = map_cuda(e); break; }
@@ -1373,6 +1447,12 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         const double tau_drop = opt.alias_tau > 0.0 ? opt.alias_tau : (fp64 ? 1e-9 : 1e-6);
         if (e == cudaSuccess && opt.autotune) e = autotune_fft(&p, s);
         if (e != cudaSuccess) { st = map_cuda(e); break; }
+        // this chunk's buffers are the ones of the chunk two before it: its copies
+        // to the host must be done before the graph writes them again
+        if (e == cudaSuccess && copy_out && b.copied_pending[slot]) {
+            ok(cudaStreamWaitEvent(s, b.ev_copied[slot], 0));
+            b.copied_pending[slot] = false;
+        }
         const auto tp2 = now();
         b.phase_ms[3] += ms_since(tp1, tp2);
         e = launch_as_graph(b, [&]() {
@@ -1384,18 +1464,32 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         const auto tp3 = now();
         b.phase_ms[4] += ms_since(tp2, tp3);
         if (e != cudaSuccess) { st = map_cuda(e); break; }
-        // ---- results (a list that overflowed its capacity leaves bins unrepaired)
-        // re-solve, float, double-float, double lists; [8] the status word
-        int32_t cnts[16] = {0};
-        ok(cudaMemcpyAsync(cnts, b.counts, 64, cudaMemcpyDeviceToHost, s));
+        ++launched;
+        // ---- results: the chunk's counters kept on the device (read once at the
+        // end), its outputs copied to the host
+        k_copy_words<<<1, 32, 0, s>>>((const uint32_t*)b.counts, (uint32_t*)(b.cnt_hist + 16 * ci), 16);
+        ok(cudaGetLastError());
+        if (copy_out) {
+            ok(cudaEventRecord(b.ev_ready[slot], s));
+            ok(cudaStreamWaitEvent(b.cs2, b.ev_ready[slot], 0));
+            // in pieces, so that another transfer waits for one piece at most
+            const int64_t piece = (int64_t)64 << 20;  // floats
+            for (int64_t a = 0; a < out_chunk; a += piece)
+                ok(cudaMemcpyAsync(dchi2 + out_global + a, out + a,
+                                   std::min(piece, out_chunk - a) * sizeof(float),
+                                   cudaMemcpyDeviceToHost, b.cs2));
+            ok(cudaEventRecord(b.ev_copied[slot], b.cs2));
+            b.copied_pending[slot] = true;
+            b.phase_ms[5] += ms_since(tp3, now());
+            if (e != cudaSuccess) { st = map_cuda(e); break; }
+            out_global += out_chunk;
+            continue;
+        }
         if (dchi2 && !out_dev)
             ok(cudaMemcpyAsync(dchi2 + out_global, out, out_chunk * sizeof(float), cudaMemcpyDeviceToHost, s));
-        if (peaks && K > 0)
-            ok(cudaMemcpyAsync(peaks + c0 * K, b.recs, nrec * sizeof(fc2_best), cudaMemcpyDeviceToHost, s));
         ok(cudaStreamSynchronize(s));
         b.phase_ms[5] += ms_since(tp3, now());
         if (e != cudaSuccess) { st = map_cuda(e); break; }
-        if (cnts[8] != 0) { st = (fc2_status)cnts[8]; break; }
         if (b.timing) {
             for (int i = 0; i < 5; ++i) {
                 float ms = 0.f;
@@ -1404,19 +1498,50 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             }
             for (int c = 0; c < nc; ++c) b.fft_alg_bytes += 3.0 * Hv[c] * (double)N * (double)csz;
         }
+        // without the copy stream every chunk is checked before the next starts
+        int32_t cnts[16] = {0};
+        if (ok(cudaMemcpy(cnts, b.cnt_hist + 16 * ci, 64, cudaMemcpyDeviceToHost)))
+            std::memcpy(&hist[16 * ci], cnts, 64);
+        if (e != cudaSuccess) { st = map_cuda(e); break; }
+        if (cnts[8] != 0) { st = (fc2_status)cnts[8]; break; }
+        out_global += out_chunk;
+    }
+    const auto t_loop_end = now();
+    cudaStreamSynchronize(s);
+    if (b.cs2 && cudaStreamSynchronize(b.cs2) != cudaSuccess && st == FC2_OK) st = FC2_ERR_CUDA;
+    if (peaks && K > 0 && launched > 0 && st == FC2_OK) {
+        const int64_t ncur = (launched == nchunks) ? C : chunks[launched].c0;
+        if (cudaMemcpy(peaks, b.recs, (size_t)ncur * K * sizeof(fc2_best), cudaMemcpyDeviceToHost) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            st = FC2_ERR_CUDA;
+        }
+    }
+    // ---- every launched chunk's counters: the status word [8], then the list
+    // counts (re-solve, float, double-float, last tier; a list that overflowed
+    // its capacity leaves bins unrepaired)
+    if (launched > 0 && b.cnt_hist &&
+        cudaMemcpy(hist.data(), b.cnt_hist, launched * 64, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        if (st == FC2_OK) st = FC2_ERR_CUDA;
+        launched = 0;
+    }
+    for (size_t ci = 0; ci < launched; ++ci) {
+        const int32_t* cnts = &hist[16 * ci];
+        if (cnts[8] != 0) {
+            if (st == FC2_OK) st = (fc2_status)cnts[8];
+            break;
+        }
         if ((size_t)cnts[0] > b.cl1 || (size_t)cnts[1] > b.cl2 || (size_t)cnts[2] > b.cl3 ||
             (size_t)cnts[3] > b.cl4) {
-            st = FC2_ERR_NUMERIC;
+            if (st == FC2_OK) st = FC2_ERR_NUMERIC;
             break;
         }
         b.stats[0] += cnts[0];
         b.stats[1] += cnts[1];
         b.stats[2] += cnts[2];
         b.stats[3] += cnts[3];
-        out_global += out_chunk;
     }
-    const auto t_loop_end = now();
-    cudaStreamSynchronize(s);
     b.cp.d_key = nullptr; b.cp.d_dlt = nullptr; b.cp.d_cs = nullptr;
     b.cp.d_grid[0] = b.cp.d_grid[1] = nullptr; b.cp.d_spec = nullptr; b.cp.d_L = nullptr;
     b.cp.d_slot_soff = b.cp.d_slot_n = nullptr; b.cp.d_red = nullptr; b.cp.d_status = nullptr;
