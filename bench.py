@@ -392,13 +392,14 @@ def run_survey(args):
     stream = torch.cuda.Stream(device=dev)
     pos = np.concatenate([[0], np.cumsum(b.H.astype(np.int64) * b.N)])
 
-    def call(t, x, s, out, prec="mixed", sub=None):
+    def call(t, x, s, out, prec="mixed", sub=None, autotune="table"):
         off, H, fm, df, N = b.offsets, b.H, b.f_min, b.df, b.N
         if sub is not None:
             off, H, fm, df, N = off[:sub + 1], H[:sub], fm[:sub], df[:sub], N[:sub]
             t, x, s = t[:int(off[-1])], x[:int(off[-1])], s[:int(off[-1])]
         return _fc2.execute_batched(off, t, x, s, H, fm, df, N, b.oversample, prec, top_k=K,
-                                    dchi2=out, stream=stream.cuda_stream, device=local)
+                                    dchi2=out, stream=stream.cuda_stream, device=local,
+                                    autotune=autotune)
 
     # ---- end to end through the C ABI with host buffers; the process's first
     # library call is the cold one (graph instantiation, pool growth, tables)
@@ -408,6 +409,7 @@ def run_survey(args):
     t0 = time.perf_counter()
     _, _, st_cold = call(tp, xp, sp, hout)
     cold_ms = allreduce_max(ws, (time.perf_counter() - t0) * 1e3)
+    cold_cfg = st_cold["config"]
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
     barrier(ws)
     t0 = time.perf_counter()
@@ -453,6 +455,18 @@ def run_survey(args):
     value = total_evals / (ms_max / 1e3)
     stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
     fft_alg /= args.steps
+
+    # ---- the fixed default launch configuration, against the tuned one
+    call(td, xd, sd, out, autotune="fixed")
+    torch.cuda.synchronize()
+    x0e = torch.cuda.Event(enable_timing=True)
+    x1e = torch.cuda.Event(enable_timing=True)
+    x0e.record(stream)
+    for _ in range(2):
+        call(td, xd, sd, out, autotune="fixed")
+    x1e.record(stream)
+    torch.cuda.synchronize()
+    ms_fixed = allreduce_max(ws, x0e.elapsed_time(x1e) / 2)
 
     # ---- FP64 on the first 256 curves (device-resident, CUDA events)
     sub = min(256, b.C)
@@ -555,6 +569,13 @@ def run_survey(args):
         "fp64_first_256_curves": {"value": value64, "ms_per_step": ms64,
                                   "evals_per_step": e64},
         "mixed_over_fp64_batched": value / value64,
+        "autotune": {"choice": {k: v for k, v in stats["config"].items()
+                                if k not in ("configurations_timed", "tuning_ms")},
+                     "source_in_timed_steps": stats["config"]["source"],
+                     "tuned_in_first_call": {k: cold_cfg[k] for k in
+                                             ("source", "configurations_timed", "tuning_ms")},
+                     "ms_per_step_tuned": ms_max, "ms_per_step_fixed_default": ms_fixed,
+                     "fixed_over_tuned": ms_fixed / ms_max},
         "parity": parity,
         **subrec,
     }
@@ -942,7 +963,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fchi2", choices=["fchi2", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-bins", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle (parity, cpu_baseline)")

@@ -73,11 +73,29 @@ typedef struct {
     int device;                /* CUDA device ordinal */
     int inputs_on_device;      /* t, x, sigma are device pointers (borrowed, not copied) */
     int outputs_on_device;     /* dchi2 (and d_dx, d_dsigma) are device pointers */
-    int autotune;              /* 1 = time the candidate transform plans (radix per pass,
-                                  kernel family) on the plan's own buffers when it is
-                                  created and keep the fastest; the choice is cached per
-                                  device, size and precision for the process. 0 = the
-                                  fixed balanced plan */
+    int autotune;              /* fc2_plan_create: 1 = time the candidate transform plans
+                                  (radix per pass, kernel family) on the plan's own
+                                  buffers when it is created and keep the fastest; the
+                                  choice is cached per device, size and precision for
+                                  the process. 0 or -1 = the fixed balanced plan.
+                                  fc2_execute_batched: 0 (default) = the launch
+                                  configuration (transform plan and family, spreading
+                                  tile, assembly block, exact-sum work item) from the
+                                  tuning table, keyed by device, N, grid length,
+                                  oversampling, precision, kernel width, largest H of
+                                  the chunk and shared sampling; on a miss the chunk's
+                                  candidates are timed on the chunk itself (a second or
+                                  so for a full chunk) and the fastest is kept for the
+                                  process and appended to the cache file
+                                  $FC2_TUNE_CACHE (unset: ~/.cache/fc2-gb300/
+                                  batch_tune.txt or under $XDG_CACHE_HOME; "" or "off":
+                                  no file), which later processes read.  1 = tune
+                                  anew; -1 = the fixed default configuration.  A
+                                  transform family requested (fft_kernel != 0) also
+                                  fixes the configuration.  Every configuration meets
+                                  the same error bounds; float rounding depends on the
+                                  choice.  Values outside -1..1 are
+                                  FC2_ERR_INVALID_ARG */
     int fft_kernel;            /* kernel family of the float transform passes when autotune
                                   is 0: 0 = library default (= 1), 1 = two register stages
                                   of radix R/64 and 64 for radix 2^10..2^12 passes and

@@ -153,6 +153,27 @@ void fc2_debug_batch_timing(int enable);
  * values per curve).  Zeros when timing was off.  No-op on NULL. */
 void fc2_debug_batch_stage_ms(double* out6);
 
+/* Launch configuration of the last fc2_execute_batched call's last chunk
+ * (out12): [0] source (0 fixed, 1 tuning table or cache file, 2 tuned in the
+ * call), [1] transform family (0 radix-16 in shared memory, 1 two register
+ * stages, 2 bulk copies), [2] spreading tile (cells), [3] assembly block
+ * (threads), [4] samples per exact-sum work item, [5] transform passes,
+ * [6..9] their log2 radices, [10] configurations timed, [11] tuning
+ * milliseconds (host wall time; the bits of a double). */
+void fc2_debug_batch_config(int64_t* out12);
+
+/* Fixed configuration of batched calls that do not tune (autotune = -1, or a
+ * transform family requested): spreading tile 512 / 1024 / 2048 cells,
+ * assembly block 128 / 256 threads (float), exact-sum work item 1024 / 2048 /
+ * 4096 samples; 0, or a value the grid does not allow, keeps the default
+ * (1024 cells, or 128 below 4096-point grids; 128 threads; 2048 samples).
+ * Process-wide; for tests and diagnostics. */
+void fc2_debug_batch_force(int spread_tile, int asm_nt, int bx_ch);
+
+/* Empty this process's tuning table of the batched path; the cache file is
+ * read again at the next lookup. */
+void fc2_debug_batch_forget_tuning(void);
+
 /* Stage timing of p on (enable != 0) or off; resets the accumulated times.
  * While on, each execute records CUDA events on the plan's stream around
  * (0) phase reduction and spreading, (1) FFT passes, (2) assembly and solve,

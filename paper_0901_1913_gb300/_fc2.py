@@ -168,6 +168,12 @@ def load():
         lib.fc2_debug_alloc_count.restype = i64
         lib.fc2_debug_pool_used.argtypes = [i32]
         lib.fc2_debug_pool_used.restype = i64
+        lib.fc2_debug_batch_config.argtypes = [_P]
+        lib.fc2_debug_batch_config.restype = None
+        lib.fc2_debug_batch_force.argtypes = [i32, i32, i32]
+        lib.fc2_debug_batch_force.restype = None
+        lib.fc2_debug_batch_forget_tuning.argtypes = []
+        lib.fc2_debug_batch_forget_tuning.restype = None
         _lib = lib
         return lib
 
@@ -208,7 +214,7 @@ def make_options(prec="fp64", kernel_width=0, top_k=0, alias_tau=0.0, stream=Non
     o.device = int(device)
     o.inputs_on_device = int(bool(inputs_on_device))
     o.outputs_on_device = int(bool(outputs_on_device))
-    o.autotune = int(bool(autotune))
+    o.autotune = AUTOTUNE[autotune] if isinstance(autotune, str) else int(autotune)
     o.fft_kernel = FFT_KERNELS[fft_kernel] if isinstance(fft_kernel, str) else int(fft_kernel)
     o.gridding = GRIDDING[gridding] if isinstance(gridding, str) else int(gridding)
     o.detrend = int(detrend)
@@ -369,6 +375,38 @@ def batch_timing(enable=True):
 
 BATCH_STAGES = ("spread", "fft", "assemble", "fixup", "peaks")
 
+# fc2_options.autotune: single-curve plans tune with 1 (True) only; the batched
+# path tunes by default ("table": the tuning table or cache file, tuning on a
+# miss), "retune" tunes anew, "fixed" keeps the default configuration
+AUTOTUNE = {"fixed": -1, "table": 0, "retune": 1}
+FFT_FAMILY_NAMES = {0: "radix-16 stages in shared memory", 1: "two register stages",
+                    2: "radix-16 stages fed by bulk copies"}
+
+
+def batch_config():
+    """Launch configuration of the last batched call's last chunk
+    (fc2_debug_batch_config) as a dict."""
+    v = np.zeros(12, dtype=np.int64)
+    load().fc2_debug_batch_config(v.ctypes.data)
+    npass = int(v[5])
+    return dict(source=("fixed", "table", "tuned")[int(v[0])] if 0 <= v[0] <= 2 else int(v[0]),
+                fft_family=FFT_FAMILY_NAMES.get(int(v[1]), int(v[1])),
+                fft_log2_radices=[int(r) for r in v[6:6 + npass]],
+                spread_tile=int(v[2]), assemble_block=int(v[3]), exact_item_samples=int(v[4]),
+                configurations_timed=int(v[10]),
+                tuning_ms=float(v[11:12].view(np.float64)[0]))
+
+
+def batch_force(spread_tile=0, assemble_block=0, exact_item_samples=0):
+    """Fixed configuration of batched calls that do not tune (autotune
+    "fixed" or a transform family requested); zeros keep the defaults."""
+    load().fc2_debug_batch_force(int(spread_tile), int(assemble_block), int(exact_item_samples))
+
+
+def batch_forget_tuning():
+    """Empty the process's tuning table (the cache file is read again)."""
+    load().fc2_debug_batch_forget_tuning()
+
 
 def trim_device_memory(device=0):
     """Return the library's cached device memory on `device` to the system."""
@@ -427,7 +465,7 @@ def execute_batched(offsets, t, x, sigma, H, f_min, df, N, oversample=2, prec="m
                                                      "graph", "wait", "release"),
                                                     (float(v) for v in ph))),
                              stage_ms=dict(zip(BATCH_STAGES, (float(v) for v in sm[:5]))),
-                             fft_alg_bytes=float(sm[5]))
+                             fft_alg_bytes=float(sm[5]), config=batch_config())
 
 
 def _backward_argtypes(lib):

@@ -24,16 +24,34 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
+# Sources that embed the version of all sources (the batched path's tuning
+# cache file keys its entries by it): rebuilt whenever any source changes.
+VERSIONED = ("k_batch.cu",)
+
+
 def _compile(src: str, verbose: bool) -> str:
     path = os.path.join(CSRC, src)
     obj = os.path.join(BUILD, src + ".o")
     deps = [path] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
     inc = os.path.join(HERE, "..", "include")
     deps += [os.path.join(inc, h) for h in os.listdir(inc) if h.endswith(".h")]
-    if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
+    defs = []
+    stamp = None
+    if src in VERSIONED:
+        ver = sources_version()
+        defs = [f'-DFC2_SRC_VERSION="{ver}"']
+        stamp = obj + ".ver"
+    fresh = os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps)
+    if fresh and stamp is not None:
+        try:
+            with open(stamp) as fh:
+                fresh = fh.read().strip() == ver
+        except OSError:
+            fresh = False
+    if fresh:
         return obj
     cmd = [nvcc(), "-c", path, "-o", obj, "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-lineinfo", "--expt-relaxed-constexpr"] + ARCH
+           "-lineinfo", "--expt-relaxed-constexpr"] + defs + ARCH
     if verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -41,6 +59,9 @@ def _compile(src: str, verbose: bool) -> str:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
     if verbose:
         sys.stderr.write(r.stderr)
+    if stamp is not None:
+        with open(stamp, "w") as fh:
+            fh.write(ver)
     return obj
 
 

@@ -23,7 +23,7 @@ using namespace fc2;
 static int64_t g_last_batch_launches = 0;
 // re-solved, exact float / double-float / double, graphs; then the host
 // milliseconds of the call's seven phases (as doubles' bits)
-static int64_t g_last_batch_stats[18] = {0};
+static int64_t g_last_batch_stats[32] = {0};
 
 // Device memory comes from one stream-ordered pool per device owned by the
 // library.  Memory that a destroyed plan returns stays mapped in the pool
@@ -151,6 +151,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     if (opt.top_k < 0 || opt.top_k > 64 || opt.alias_tau < 0.0) return FC2_ERR_INVALID_ARG;
     if (opt.fft_kernel < 0 || opt.fft_kernel > 3) return FC2_ERR_INVALID_ARG;
     if (opt.fft_group < 0) return FC2_ERR_INVALID_ARG;
+    if (opt.autotune < -1 || opt.autotune > 1) return FC2_ERR_INVALID_ARG;
     if (opt.gridding < 0 || opt.gridding > 1) return FC2_ERR_INVALID_ARG;
     if (opt.detrend < 0 || opt.detrend > 3) return FC2_ERR_INVALID_ARG;
     if (opt.trend_fit < 0 || opt.trend_fit > 1) return FC2_ERR_INVALID_ARG;
@@ -427,9 +428,9 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
         // The occupied extent is rounded to whole first-pass rows, so that the
         // spread writes every cell the first pass reads.  With the autotuner the
         // first pass may have a radix as small as 2^8 (its candidates).
-        const int LOGR1 = opt.autotune ? std::min(p->passes[0].logR, 8) : p->passes[0].logR;
+        const int LOGR1 = opt.autotune > 0 ? std::min(p->passes[0].logR, 8) : p->passes[0].logR;
         const int64_t S1 = M >> LOGR1;
-        const int64_t tile = (M >= 4096) ? 1024 : 128;
+        const int64_t tile = spread_tile_of(M, p->spread_tile);
         const int64_t unit = std::max(S1, tile);
         p->geom.resize(NSRC);
         std::vector<int64_t> Ls(NSRC), Lh(G);
@@ -492,7 +493,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
             }
             p->fft_bytes = fb;
         }
-        if (opt.autotune) g.ok(autotune_fft(p, s));  // sets the pass plan and its tables
+        if (opt.autotune > 0) g.ok(autotune_fft(p, s));  // sets the pass plan and its tables
         else g.ok(init_twiddles(p, s));
         if (p->paper) g.ok(cudaStreamSynchronize(s));  // no deconvolution
         else g.ok(init_deconv(p, s));                   // synchronises
@@ -856,6 +857,30 @@ void fc2_debug_batch_counts(int64_t* out5) {
  * graph capture / update and launch, the wait for the chunk's kernels and
  * results; release of the buffers at the end. */
 void fc2_debug_batch_timing(int enable) { set_batch_timing(enable != 0); }
+
+/* Launch configuration of the last fc2_execute_batched call's last chunk
+ * (out12): [0] source (0 fixed, 1 tuning table, 2 tuned in the call),
+ * [1] transform family (0 radix-16 shared memory, 1 two register stages,
+ * 2 bulk copies), [2] spreading tile cells, [3] assembly block threads,
+ * [4] samples per exact-sum work item, [5] transform passes, [6..9] their
+ * log2 radices, [10] configurations timed, [11] tuning milliseconds (host
+ * wall time, as the bits of a double). */
+void fc2_debug_batch_config(int64_t* out12) {
+    if (out12)
+        for (int i = 0; i < 12; ++i) out12[i] = g_last_batch_stats[18 + i];
+}
+
+/* Fixed configuration for batched calls that do not tune (autotune -1 or a
+ * transform family requested): spreading tile 512 / 1024 / 2048 cells,
+ * assembly block 128 / 256 threads, work item 1024 / 2048 / 4096 samples;
+ * 0 (or a value the grid does not allow) keeps the default. */
+void fc2_debug_batch_force(int spread_tile, int asm_nt, int bx_ch) {
+    fc2::force_batch_config(spread_tile, asm_nt, bx_ch);
+}
+
+/* Forget the batched path's tuning table of this process (the cache file is
+ * read again at the next lookup). */
+void fc2_debug_batch_forget_tuning(void) { fc2::forget_batch_tuning(); }
 
 void fc2_debug_batch_stage_ms(double* out6) {
     if (out6)

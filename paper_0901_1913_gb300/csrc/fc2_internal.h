@@ -32,6 +32,16 @@ enum FftFamily {
     FFT_BULK = 2   // radix-16 stages fed by bulk asynchronous copies (k_fft_pass_tma), 2^8..2^12
 };
 
+// Cells per spreading tile: the default for the grid length (1024, or 128 below
+// 4096 points), or a requested width of 512, 1024 or 2048 when it is at most
+// half the grid (the tile's three key ranges must be disjoint).
+inline int spread_tile_of(int64_t M, int requested) {
+    if ((requested == 512 || requested == 1024 || requested == 2048) && 2 * (int64_t)requested <= M &&
+        M >= 4096)
+        return requested;
+    return M >= 4096 ? 1024 : 128;
+}
+
 // Family for fc2_options.fft_kernel (0 = library default).
 inline int fft_family_of(int fft_kernel) {
     return fft_kernel == 2 ? FFT_R16 : fft_kernel == 3 ? FFT_BULK : FFT_R64;
@@ -120,6 +130,7 @@ struct fc2_plan_s {
     int64_t tw64_off[16] = {0};
     int fft_family = fc2::FFT_R64;  // kernel family of the float passes (fc2::FftFamily)
     int fft_group = 0;         // grids taken through all passes together (0 = all)
+    int spread_tile = 0;       // cells per spreading tile (0 = default for M)
     double* d_dchi2 = nullptr; // [H][N]
     float* d_minpiv = nullptr; // unused slot kept for diagnostics
     int32_t* d_flag_list = nullptr;  // bins needing the exact fix-up
@@ -210,6 +221,16 @@ cudaError_t init_twiddles(fc2_plan_s* p, cudaStream_t s);
 cudaError_t init_deconv(fc2_plan_s* p, cudaStream_t s);
 void plan_fft_passes(fc2_plan_s* p);
 cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s);  // choose and set up the pass plan
+struct FftChoice {
+    std::vector<int> rs;  // log2 radix of each pass
+    int family;           // fc2::FftFamily
+};
+std::vector<FftChoice> fft_tune_candidates(int logM, bool fp64);
+bool fft_choice_valid(int logM, bool fp64, const FftChoice& c);
+cudaError_t set_fft_choice(fc2_plan_s* p, const FftChoice& c, cudaStream_t s);
+// k_batch.cu: the batched path's tuning table and fixed configuration
+void forget_batch_tuning();
+void force_batch_config(int spread_tile, int asm_nt, int bx_ch);
 cudaError_t pool_alloc(void** ptr, size_t bytes, cudaStream_t s);  // library device pool
 void drop_deconv_cache(int dev);  // k_fft.cu: cached deconvolution tables of a device
 cudaError_t launch_fft(fc2_plan_s* p, cudaStream_t s);

@@ -15,6 +15,10 @@
 #include <chrono>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <string>
+#include <sys/stat.h>
+#include <tuple>
 #include <type_traits>
 #include <vector>
 
@@ -40,6 +44,7 @@ struct CurveTab {
     const float* chi0f;     // [C] chi2_0
     const int* qown;        // [C] curve whose Q transforms (weights only) this curve reads
     const int* pslot0;      // [C] first P transform slot of the curve
+    int bx_ch;              // samples per exact-sum work item
 };
 
 // ------------------------------------------------------------------ gather
@@ -134,8 +139,8 @@ __global__ void k_bphase(const double* __restrict__ tau, const double* __restric
 // One thread per (trial frequency, curve) for the curves of one H; Delta
 // chi^2 written as float.  Bins whose estimated error is too large go to
 // `list` as (curve << 32 | j).
-template <typename TS, int H>
-__global__ void __launch_bounds__(128) k_bassemble(const cpx<TS>* __restrict__ spec,
+template <typename TS, int H, int NT>
+__global__ void __launch_bounds__(NT) k_bassemble(const cpx<TS>* __restrict__ spec,
                                                    const TS* __restrict__ dec, int64_t N,
                                                    const int* __restrict__ curves, CurveTab ct,
                                                    TS tau, TS eps, TS err_fix,
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__
 //   1: float sine / cosine, compensated float sums;
 //   2: double-float phasors, products and sums (about 48 bits);
 //   3: double phasors and sums.
-// An entry's samples are cut into work items of about BX_CH samples (at most
+// An entry's samples are cut into work items of about bx_ch samples (at most
 // BX_QMAX per entry) so that the long curves of a batch spread over all SMs:
 // k_bx_split numbers the items in entry order, k_bx_part sums each item with
 // one warp (lanes at stride 32, then a butterfly) into a row of partial sums,
@@ -280,13 +285,13 @@ __global__ void __launch_bounds__(128) k_bresolve(const cpx<float>* __restrict__
 // parts at [ntot + i].
 constexpr int BX_NT = 256;
 constexpr int BX_W = BX_NT / 32;
-constexpr int BX_CH = 2048;           // samples per work item
+constexpr int BX_CH = 2048;           // samples per work item by default (autotuned)
 constexpr int BX_QMAX = 64;           // work items per entry at most
 constexpr int BX_ITEMS = 1 << 18;     // work items per launch at most
 constexpr int BX_SPLIT_NT = 1024;     // threads of the (single-CTA) item numbering
 
-FC2_HD int bx_items_of(int64_t n) {
-    const int64_t q = (n + BX_CH - 1) / BX_CH;
+FC2_HD int bx_items_of(int64_t n, int ch) {
+    const int64_t q = (n + ch - 1) / ch;
     return (int)(q < 1 ? 1 : (q > BX_QMAX ? BX_QMAX : q));
 }
 
@@ -469,7 +474,7 @@ __global__ void __launch_bounds__(BX_SPLIT_NT) k_bx_split(CurveTab ct,
         const int64_t ent = list[e];
         if ((ent & 0xffffffffll) == 0xffffffffll) return 0;  // empty peak slot
         const int c = (int)(ent >> 32);
-        return bx_items_of(ct.off[c + 1] - ct.off[c]);
+        return bx_items_of(ct.off[c + 1] - ct.off[c], ct.bx_ch);
     };
     // item counts: at most (2^22 entries) x BX_QMAX in all, so int32 sums are exact
     int32_t v = 0;
@@ -534,7 +539,7 @@ __global__ void __launch_bounds__(BX_NT) k_bx_part(
         const int c = (int)(ent >> 32);
         const uint64_t ju = (uint64_t)(ent & 0xffffffffll);
         const int64_t a0 = ct.off[c], n = ct.off[c + 1] - a0;
-        const int nq = bx_items_of(n);
+        const int nq = bx_items_of(n, ct.bx_ch);
         const int64_t i0 = a0 + n * q / nq, i1 = a0 + n * (q + 1) / nq;
         double tot[NV];
         bx_sums<HM, TIER>(Aph, Bph, wq32, wp32, wq, wp, tb, ntot, ju, ct.H[c], i0, i1, lane, tot);
@@ -583,7 +588,7 @@ __global__ void __launch_bounds__(BX_NT) k_bexact(
         double tot[NV];
         const int qb = qbase[e];
         if (qb >= 0) {
-            const int nq = bx_items_of(a1 - a0);
+            const int nq = bx_items_of(a1 - a0, ct.bx_ch);
             double lo = 0.0, hi = 0.0;
             for (int q = 0; q < nq; ++q) {
                 const double* row = part + (int64_t)(qb + q) * NV;
@@ -779,6 +784,15 @@ constexpr int BHM = 8;  // harmonic capacity of the batched kernels
 
 }  // namespace
 
+// The launch configuration of a chunk: the transform plan and family, the
+// spreading tile, the assembly block and the exact-sum work item.
+struct BatchConfig {
+    FftChoice fft;
+    int spread_tile;
+    int asm_nt;
+    int bx_ch;
+};
+
 struct Batch {
     cudaStream_t s = nullptr;
     bool own_stream = false;
@@ -832,6 +846,16 @@ struct Batch {
     char* red = nullptr; size_t cred = 0;
     cudaGraphExec_t gexec = nullptr;
     int64_t graphs = 0;  // chunk graphs launched
+    // tuned launch parameters (besides the transform plan in cp): threads per
+    // assembly block and samples per exact-sum work item
+    int asm_nt = 128;
+    int bx_ch = BX_CH;
+    // the configuration of the last chunk, its source (0 fixed, 1 tuning table,
+    // 2 tuned in this call), the tuning time and the configurations timed
+    BatchConfig cfg{FftChoice{std::vector<int>(), 0}, 0, 0, 0};
+    int cfg_source = 0;
+    double tune_ms = 0;
+    int tune_timed = 0;
     int64_t launches = 0;
     int64_t stats[4] = {0, 0, 0, 0};
     double phase_ms[7] = {0, 0, 0, 0, 0, 0, 0};  // host wall time of the call's phases
@@ -927,11 +951,20 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
     const int64_t N = p.N;
     int64_t nl = 0;
     CurveTab ct{b.off, b.H, b.fmin, b.df, b.scal, b.slot0, b.out_off, b.sq, b.sp, b.s1n, b.chi0f,
-                b.qown, b.pslot0};
+                b.qown, b.pslot0, b.bx_ch};
     // (inside a stream capture only an external event record becomes a node of
     // the graph; a plain record there would only order the capture)
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    if (b.timing && cudaStreamIsCapturing(s, &capturing) != cudaSuccess) {
+        cudaGetLastError();
+        capturing = cudaStreamCaptureStatusNone;
+    }
     auto mark = [&](int i) {
-        if (b.timing) cudaEventRecordWithFlags(b.ev[i], s, cudaEventRecordExternal);
+        if (!b.timing) return;
+        if (capturing == cudaStreamCaptureStatusActive)
+            cudaEventRecordWithFlags(b.ev[i], s, cudaEventRecordExternal);
+        else
+            cudaEventRecord(b.ev[i], s);
     };
     mark(0);
     k_bgather<<<(unsigned)((ntot + 255) / 256), 256, 0, s>>>(
@@ -967,15 +1000,21 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
     for (size_t gi = 0; gi < hgroups.size(); ++gi) {
         const int Hh = hgroups[gi].empty() ? 0 : (int)gi + 1;
         if (!Hh) continue;
-        dim3 ga((unsigned)((N + 127) / 128), (unsigned)hgroups[gi].size());
+        // block of 128 threads, or 256 for float when the autotuner chose it
+        const int ant = (f32 && b.asm_nt == 256) ? 256 : 128;
+        dim3 ga((unsigned)((N + ant - 1) / ant), (unsigned)hgroups[gi].size());
         const int* cl = b.curves + hgroup_off[gi];
         const double eps = f32 ? eps_spec + 3e-7 : eps_spec;
 #define FC2_BASM(HH)                                                                          \
     case HH:                                                                                  \
-        k_bassemble<T, HH><<<ga, 128, 0, s>>>((const cpx<T>*)p.d_spec, (const T*)p.d_dec, N,  \
-                                              cl, ct, (T)tau_drop, (T)eps, (T)err_fix, out,   \
-                                              first_list,                                     \
-                                              first_cnt, first_cap);                          \
+        if (ant == 256)                                                                       \
+            k_bassemble<T, HH, 256><<<ga, 256, 0, s>>>(                                       \
+                (const cpx<T>*)p.d_spec, (const T*)p.d_dec, N, cl, ct, (T)tau_drop, (T)eps,   \
+                (T)err_fix, out, first_list, first_cnt, first_cap);                           \
+        else                                                                                  \
+            k_bassemble<T, HH, 128><<<ga, 128, 0, s>>>(                                       \
+                (const cpx<T>*)p.d_spec, (const T*)p.d_dec, N, cl, ct, (T)tau_drop, (T)eps,   \
+                (T)err_fix, out, first_list, first_cnt, first_cap);                           \
         break;
         switch (Hh) {
             FC2_BASM(1) FC2_BASM(2) FC2_BASM(3) FC2_BASM(4) FC2_BASM(5) FC2_BASM(6) FC2_BASM(7)
@@ -1081,6 +1120,250 @@ static cudaError_t launch_as_graph(Batch& b, F&& launches) {
     return e;
 }
 
+
+// ------------------------------------------------------------ batch autotuner
+// The batched path looks up the launch configuration by (device, N, M, oversampling, precision, kernel
+// width, largest H of the chunk, shared sampling); on a miss it times the
+// candidates on the chunk itself, one parameter after the other with the
+// others held (each candidate run twice after a warm-up, the best of the two
+// of the stage it affects), and keeps the fastest.  Choices are kept for the
+// process and, unless disabled, appended to a text file read at the first
+// lookup, so later processes skip the tuning.  Every candidate gives results
+// within the same error bounds; the rounding of the float stages depends on
+// the choice (radices, summation order within work items).
+
+struct BatchTuneKey {
+    std::string dev;
+    int64_t N, M;
+    int osmp, fp64, w, hmax, shared;
+    bool operator<(const BatchTuneKey& o) const {
+        return std::tie(dev, N, M, osmp, fp64, w, hmax, shared) <
+               std::tie(o.dev, o.N, o.M, o.osmp, o.fp64, o.w, o.hmax, o.shared);
+    }
+};
+
+static std::mutex g_btune_mu;
+static std::map<BatchTuneKey, BatchConfig> g_btune;
+static bool g_btune_loaded = false;
+
+#ifndef FC2_SRC_VERSION
+#define FC2_SRC_VERSION "unversioned"
+#endif
+
+// The cache file: $FC2_TUNE_CACHE ("" or "off": none), else
+// $XDG_CACHE_HOME/fc2-gb300/batch_tune.txt or ~/.cache/fc2-gb300/batch_tune.txt.
+static std::string tune_cache_path(bool make_dir) {
+    const char* env = getenv("FC2_TUNE_CACHE");
+    if (env) {
+        const std::string v(env);
+        if (v.empty() || v == "off") return std::string();
+        return v;
+    }
+    std::string base;
+    if (const char* x = getenv("XDG_CACHE_HOME")) base = x;
+    else if (const char* h = getenv("HOME")) base = std::string(h) + "/.cache";
+    else return std::string();
+    const std::string dir = base + "/fc2-gb300";
+    if (make_dir) {
+        mkdir(base.c_str(), 0755);
+        mkdir(dir.c_str(), 0755);
+    }
+    return dir + "/batch_tune.txt";
+}
+
+static std::string device_tag(int dev) {
+    static std::mutex mu;
+    static std::map<int, std::string> tags;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = tags.find(dev);
+    if (it != tags.end()) return it->second;
+    cudaDeviceProp pr;
+    if (cudaGetDeviceProperties(&pr, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    std::string name(pr.name);
+    for (char& c : name)
+        if (c == ' ' || c == '\t' || c == ':') c = '_';
+    return tags[dev] = name + "_" + std::to_string(pr.multiProcessorCount) + "sm";
+}
+
+static bool config_valid(const BatchTuneKey& k, const BatchConfig& c) {
+    int logM = 0;
+    while ((1ll << logM) < k.M) ++logM;
+    if (!fft_choice_valid(logM, k.fp64 != 0, c.fft)) return false;
+    if (spread_tile_of(k.M, c.spread_tile) != c.spread_tile) return false;
+    if (c.asm_nt != 128 && c.asm_nt != 256) return false;
+    if (c.bx_ch != 1024 && c.bx_ch != 2048 && c.bx_ch != 4096) return false;
+    return true;
+}
+
+// (under g_btune_mu) read the cache file once; lines of other sources or
+// malformed or invalid lines are skipped
+static void load_tune_cache() {
+    if (g_btune_loaded) return;
+    g_btune_loaded = true;
+    const std::string path = tune_cache_path(false);
+    if (path.empty()) return;
+    FILE* f = fopen(path.c_str(), "r");
+    if (!f) return;
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        char tag[32], ver[64], dev[160];
+        long long N, M;
+        int osmp, fp64, w, hmax, shared, np, r[4] = {0, 0, 0, 0}, fam, tile, ant, ch;
+        const int got = sscanf(line, "%31s %63s %159s %lld %lld %d %d %d %d %d : %d %d %d %d %d %d %d %d %d",
+                               tag, ver, dev, &N, &M, &osmp, &fp64, &w, &hmax, &shared, &np, &r[0],
+                               &r[1], &r[2], &r[3], &fam, &tile, &ant, &ch);
+        if (got != 19 || std::string(tag) != "fc2-batch-tune-1" ||
+            std::string(ver) != FC2_SRC_VERSION || np < 1 || np > 4)
+            continue;
+        BatchTuneKey k{dev, N, M, osmp, fp64, w, hmax, shared};
+        BatchConfig c{FftChoice{std::vector<int>(r, r + np), fam}, tile, ant, ch};
+        if (config_valid(k, c)) g_btune[k] = c;
+    }
+    fclose(f);
+}
+
+static void store_tune(const BatchTuneKey& k, const BatchConfig& c) {
+    std::lock_guard<std::mutex> lk(g_btune_mu);
+    g_btune[k] = c;
+    const std::string path = tune_cache_path(true);
+    if (path.empty()) return;
+    int r[4] = {0, 0, 0, 0};
+    const int np = (int)std::min<size_t>(c.fft.rs.size(), 4);
+    for (int i = 0; i < np; ++i) r[i] = c.fft.rs[i];
+    char line[512];
+    const int len = snprintf(line, sizeof line,
+                             "fc2-batch-tune-1 %s %s %lld %lld %d %d %d %d %d : %d %d %d %d %d %d %d %d %d\n",
+                             FC2_SRC_VERSION, k.dev.c_str(), (long long)k.N, (long long)k.M, k.osmp,
+                             k.fp64, k.w, k.hmax, k.shared, np, r[0], r[1], r[2], r[3], c.fft.family,
+                             c.spread_tile, c.asm_nt, c.bx_ch);
+    if (len <= 0 || len >= (int)sizeof line) return;
+    FILE* f = fopen(path.c_str(), "a");
+    if (!f) return;
+    fwrite(line, 1, (size_t)len, f);
+    fclose(f);
+}
+
+static bool lookup_tune(const BatchTuneKey& k, BatchConfig* c) {
+    std::lock_guard<std::mutex> lk(g_btune_mu);
+    load_tune_cache();
+    auto it = g_btune.find(k);
+    if (it == g_btune.end()) return false;
+    *c = it->second;
+    return true;
+}
+
+void forget_batch_tuning() {
+    std::lock_guard<std::mutex> lk(g_btune_mu);
+    g_btune.clear();
+    g_btune_loaded = false;
+}
+
+// A fixed configuration chosen for the next calls (diagnostics and tests:
+// every candidate must give the same results within the error bounds); zero
+// fields keep the defaults.
+static int g_force_tile = 0, g_force_asm = 0, g_force_ch = 0;
+void force_batch_config(int spread_tile, int asm_nt, int bx_ch) {
+    g_force_tile = spread_tile;
+    g_force_asm = asm_nt;
+    g_force_ch = bx_ch;
+}
+
+// Apply a configuration to the chunk plan and the batch.
+static cudaError_t apply_config(Batch& b, const BatchConfig& c) {
+    b.cp.spread_tile = c.spread_tile;
+    b.asm_nt = c.asm_nt;
+    b.bx_ch = c.bx_ch;
+    std::vector<int> cur;
+    for (const auto& ps : b.cp.passes) cur.push_back(ps.logR);
+    if (cur == c.fft.rs && b.cp.fft_family == c.fft.family && b.cp.fft_group == 0) return cudaSuccess;
+    return set_fft_choice(&b.cp, c.fft, b.s);
+}
+
+// Time the candidates on the chunk: run() launches the whole chunk (no graph);
+// the stage events give each stage's milliseconds.  *best starts at the
+// default configuration.
+template <typename Run>
+static cudaError_t tune_chunk(Batch& b, Run&& run, BatchConfig* best, int* timed) {
+    const bool had_timing = b.timing;
+    for (auto& ev : b.ev)
+        if (!ev && cudaEventCreate(&ev) != cudaSuccess) return cudaGetLastError();
+    b.timing = true;
+    cudaError_t e = cudaSuccess;
+    // stage milliseconds of configuration c: the better of two runs after a warm-up
+    auto measure = [&](const BatchConfig& c, int stage, float* ms) {
+        *ms = 1e30f;
+        if ((e = apply_config(b, c)) != cudaSuccess) return;
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+            if ((e = run()) != cudaSuccess) return;
+            if ((e = cudaStreamSynchronize(b.s)) != cudaSuccess) return;
+            float v = 0.f;
+            if ((e = cudaEventElapsedTime(&v, b.ev[stage], b.ev[stage + 1])) != cudaSuccess) return;
+            if (r > 0) *ms = std::min(*ms, v);
+        }
+        ++*timed;
+    };
+    const int logM = b.cp.logM;
+    const bool fp64 = b.cp.fp64;
+    // transforms: stage 1
+    float bestms = 1e30f;
+    BatchConfig cur = *best;
+    for (const auto& fc : fft_tune_candidates(logM, fp64)) {
+        BatchConfig c = cur;
+        c.fft = fc;
+        float ms;
+        measure(c, 1, &ms);
+        if (e != cudaSuccess) break;
+        if (ms < bestms) { bestms = ms; cur = c; }
+    }
+    // spreading tile: stage 0
+    if (e == cudaSuccess) {
+        bestms = 1e30f;
+        BatchConfig keep = cur;
+        for (int tile : {1024, 2048, 512}) {
+            if (spread_tile_of(b.cp.M, tile) != tile) continue;
+            BatchConfig c = keep;
+            c.spread_tile = tile;
+            float ms;
+            measure(c, 0, &ms);
+            if (e != cudaSuccess) break;
+            if (ms < bestms) { bestms = ms; cur = c; }
+        }
+    }
+    // assembly block: stage 2 (float only: FP64 keeps 128)
+    if (e == cudaSuccess && !fp64) {
+        bestms = 1e30f;
+        BatchConfig keep = cur;
+        for (int nt : {128, 256}) {
+            BatchConfig c = keep;
+            c.asm_nt = nt;
+            float ms;
+            measure(c, 2, &ms);
+            if (e != cudaSuccess) break;
+            if (ms < bestms) { bestms = ms; cur = c; }
+        }
+    }
+    // exact-sum work item: stage 3
+    if (e == cudaSuccess) {
+        bestms = 1e30f;
+        BatchConfig keep = cur;
+        for (int ch : {2048, 1024, 4096}) {
+            BatchConfig c = keep;
+            c.bx_ch = ch;
+            float ms;
+            measure(c, 3, &ms);
+            if (e != cudaSuccess) break;
+            if (ms < bestms) { bestms = ms; cur = c; }
+        }
+    }
+    b.timing = had_timing;
+    if (e != cudaSuccess) return e;
+    *best = cur;
+    return apply_config(b, cur);
+}
+
 fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, const double* x,
                            const double* sigma, const int* Hc, const double* fminc,
                            const double* dfc, const int64_t* Nc, int oversample,
@@ -1093,6 +1376,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     if (opt.prec != FC2_PREC_FP64 && opt.prec != FC2_PREC_MIXED) return FC2_ERR_INVALID_ARG;
     if (opt.top_k < 0 || opt.top_k > 64) return FC2_ERR_INVALID_ARG;
     if (opt.fft_kernel < 0 || opt.fft_kernel > 3) return FC2_ERR_INVALID_ARG;
+    if (opt.autotune < -1 || opt.autotune > 1) return FC2_ERR_INVALID_ARG;
     if (opt.gridding < 0 || opt.gridding > 1) return FC2_ERR_INVALID_ARG;
     if (opt.gridding == 1) return FC2_ERR_UNSUPPORTED;
     if (opt.detrend < 0 || opt.detrend > 3) return FC2_ERR_INVALID_ARG;
@@ -1220,6 +1504,9 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             return FC2_ERR_OOM;
         }
     }
+    // configuration: 0 fixed (autotune -1, or a transform family requested),
+    // 1 the tuning table with tuning on a miss (autotune 0), 2 tuning anew (1)
+    const int tune_mode = (opt.autotune < 0 || opt.fft_kernel != 0) ? 0 : (opt.autotune == 1 ? 2 : 1);
     const size_t nchunks = chunks.size();
     std::vector<int32_t> hist(nchunks * 16, 0);
     size_t launched = 0;  // chunks whose graph was launched
@@ -1352,11 +1639,39 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         std::vector<float> sqv(nc), spv(nc), s1v(nc), c0v(nc);
         std::vector<std::vector<int>> hg(BHM);
         bool unsorted = false;
-        const int LOGR1 = opt.autotune ? std::min(p.passes[0].logR, 8) : p.passes[0].logR;
-        const int64_t S1 = M >> LOGR1;
-        const int64_t tile = (M >= 4096) ? 1024 : 128;
-        const int64_t unit = std::max(S1, tile);
+        // ---- launch configuration: fixed, from the tuning table, or tuned on
+        // this chunk (then the occupied length of each grid is first rounded to
+        // suit every candidate, and again to the choice afterwards)
+        int hmax = 0;
+        for (int c = 0; c < nc; ++c) hmax = std::max(hmax, Hc[c0 + c]);
+        const BatchTuneKey tkey{device_tag(opt.device), N, M, oversample, fp64 ? 1 : 0, p.w, hmax,
+                                shared ? 1 : 0};
+        BatchConfig cfg{FftChoice{std::vector<int>(), p.fft_family}, spread_tile_of(M, 0), 128, BX_CH};
+        {
+            fc2_plan_s tmp;
+            tmp.logM = p.logM;
+            tmp.fp64 = p.fp64;
+            plan_fft_passes(&tmp);
+            for (const auto& ps : tmp.passes) cfg.fft.rs.push_back(ps.logR);
+        }
+        int source = 0;  // 0 fixed, 1 table, 2 tuned here
+        if (tune_mode == 0) {
+            cfg.spread_tile = spread_tile_of(M, g_force_tile);
+            if (g_force_asm == 256 && !fp64) cfg.asm_nt = 256;
+            if (g_force_ch == 1024 || g_force_ch == 4096) cfg.bx_ch = g_force_ch;
+        } else if (tune_mode == 1 && lookup_tune(tkey, &cfg)) {
+            source = 1;
+        } else {
+            source = 2;
+        }
+        int64_t unit = std::max(M >> cfg.fft.rs[0], (int64_t)cfg.spread_tile);
+        if (source == 2) {
+            for (const auto& fc : fft_tune_candidates(p.logM, fp64)) unit = std::max(unit, M >> fc.rs[0]);
+            for (int tile : {512, 1024, 2048}) unit = std::max(unit, (int64_t)spread_tile_of(M, tile));
+        }
+        if (e == cudaSuccess && source != 2) e = apply_config(b, cfg);
         int64_t acc_out = 0, acc_s = 0;
+        std::vector<double> cellsv;  // per grid: occupied cells, or -1 for a full grid
         p.geom.assign(S, GridGeom{});
         int gi = 0;
         for (int c = 0; c < nc; ++c) {
@@ -1393,16 +1708,26 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
                 gg.k = k; gg.kind = kind;
                 if (!(pmax < 1.0) || cells + p.w + 2.0 >= (double)M) {
                     gg.wraps = (pmax >= 1.0) ? 1 : 0;
-                    gg.L = M;
+                    cellsv.push_back(-1.0);
                 } else {
                     gg.wraps = 0;
-                    int64_t Lc = (int64_t)floor(cells) + p.w + 3;
-                    Lc = ((Lc + unit - 1) / unit) * unit;
-                    gg.L = std::min(Lc, M);
+                    cellsv.push_back(cells);
                 }
-                Lv.push_back(gg.L);
             }
         }
+        // occupied lengths: whole spreading tiles and whole first-pass rows
+        auto fill_L = [&](int64_t u) {
+            Lv.assign(S, M);
+            for (int64_t g = 0; g < S; ++g) {
+                if (cellsv[g] >= 0.0) {
+                    int64_t Lc = (int64_t)floor(cellsv[g]) + p.w + 3;
+                    Lc = ((Lc + u - 1) / u) * u;
+                    Lv[g] = std::min(Lc, M);
+                }
+                p.geom[g].L = Lv[g];
+            }
+        };
+        fill_L(unit);
         std::vector<int> curves_flat, hoff(BHM);
         for (int h = 0; h < BHM; ++h) {
             hoff[h] = (int)curves_flat.size();
@@ -1445,8 +1770,24 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         p.d_status = b.counts + 8;  // status word of the chunk's kernels (bounded waits)
         p.h_slot_soff = ssoff; p.h_slot_n = sn;
         const double tau_drop = opt.alias_tau > 0.0 ? opt.alias_tau : (fp64 ? 1e-9 : 1e-6);
-        if (e == cudaSuccess && opt.autotune) e = autotune_fft(&p, s);
+        if (e == cudaSuccess && source == 2) {
+            const auto tt0 = now();
+            e = tune_chunk(b, [&]() {
+                return fp64 ? chunk_launches<double>(b, nc, ntot, nmax, (int)S, hg, hoff, K, out, nrec,
+                                                     tau_drop)
+                            : chunk_launches<float>(b, nc, ntot, nmax, (int)S, hg, hoff, K, out, nrec,
+                                                    tau_drop);
+            }, &cfg, &b.tune_timed);
+            if (e == cudaSuccess) {
+                store_tune(tkey, cfg);
+                fill_L(std::max(M >> cfg.fft.rs[0], (int64_t)cfg.spread_tile));
+                ok(cudaMemcpyAsync(b.L, Lv.data(), S * 8, cudaMemcpyHostToDevice, s));
+            }
+            b.tune_ms += ms_since(tt0, now());
+        }
         if (e != cudaSuccess) { st = map_cuda(e); break; }
+        b.cfg = cfg;
+        b.cfg_source = std::max(b.cfg_source, source);
         // this chunk's buffers are the ones of the chunk two before it: its copies
         // to the host must be done before the graph writes them again
         if (e == cudaSuccess && copy_out && b.copied_pending[slot]) {
@@ -1557,6 +1898,16 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         for (int i = 0; i < 7; ++i) std::memcpy(&stats_out[5 + i], &b.phase_ms[i], 8);
         for (int i = 0; i < 5; ++i) std::memcpy(&stats_out[12 + i], &b.stage_ms[i], 8);
         std::memcpy(&stats_out[17], &b.fft_alg_bytes, 8);
+        stats_out[18] = b.cfg_source;
+        stats_out[19] = b.cfg.fft.family;
+        stats_out[20] = b.cfg.spread_tile;
+        stats_out[21] = b.cfg.asm_nt;
+        stats_out[22] = b.cfg.bx_ch;
+        stats_out[23] = (int64_t)b.cfg.fft.rs.size();
+        for (int i = 0; i < 4; ++i)
+            stats_out[24 + i] = i < (int)b.cfg.fft.rs.size() ? b.cfg.fft.rs[i] : 0;
+        stats_out[28] = b.tune_timed;
+        std::memcpy(&stats_out[29], &b.tune_ms, 8);
     }
     return st;
 }

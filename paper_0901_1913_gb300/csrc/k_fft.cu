@@ -1379,6 +1379,45 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
     return init_twiddles(p, s);
 }
 
+// The (pass plan, family) pairs the batched path's autotuner times: the same
+// plans as above with every float family (group 0: all grids pass by pass),
+// each checked by the plan validator.
+std::vector<FftChoice> fft_tune_candidates(int logM, bool fp64) {
+    std::vector<FftChoice> out;
+    const int maxr = fp64 ? FftCfg<double>::MAXR : FftCfg<float>::MAXR;
+    const int fams[3] = {FFT_R64, FFT_BULK, FFT_R16};
+    for (const auto& rs : fft_candidates(logM, maxr))
+        for (int fi = 0; fi < (fp64 ? 1 : 3); ++fi) {
+            const int fam = fp64 ? FFT_R16 : fams[fi];
+            if (fft_plan_valid(logM, fp64, fam, rs)) out.push_back(FftChoice{rs, fam});
+        }
+    return out;
+}
+
+bool fft_choice_valid(int logM, bool fp64, const FftChoice& c) {
+    int sum = 0;
+    for (int r : c.rs) {
+        if (r < 1 || r > 12) return false;
+        sum += r;
+    }
+    if (sum != logM || c.rs.empty()) return false;
+    if (c.family != FFT_R64 && c.family != FFT_BULK && c.family != FFT_R16) return false;
+    if (fp64 && c.family != FFT_R16) return false;
+    // only shapes the candidate list can hold
+    bool listed = false;
+    for (const auto& d : fft_tune_candidates(logM, fp64))
+        if (d.rs == c.rs && d.family == c.family) listed = true;
+    return listed;
+}
+
+cudaError_t set_fft_choice(fc2_plan_s* p, const FftChoice& c, cudaStream_t s) {
+    if (!fft_choice_valid(p->logM, p->fp64, c)) return cudaErrorInvalidValue;
+    set_passes(p, c.rs);
+    p->fft_family = c.family;
+    p->fft_group = 0;
+    return init_twiddles(p, s);
+}
+
 // Tile width (columns) of the pass with radix 2^logR.
 template <typename T>
 static int logj_of(const fc2_plan_s* p, int logR) {

@@ -910,9 +910,15 @@ static cudaError_t spread_tiles(fc2_plan_s* p, cudaStream_t s) {
 
 template <typename T>
 static cudaError_t spread_impl(fc2_plan_s* p, cudaStream_t s) {
-    // a tile must be at most half the grid so the three key ranges are disjoint
-    if (p->M >= 4096) return spread_tiles<T, 1024, 256, 2048>(p, s);
-    return spread_tiles<T, 128, 128, 1024>(p, s);
+    // a tile must be at most half the grid so the three key ranges are disjoint;
+    // the batched path may choose another tile width (its autotuner)
+    const int tile = spread_tile_of(p->M, p->spread_tile);
+    switch (tile) {
+        case 2048: return spread_tiles<T, 2048, 256, 2048>(p, s);
+        case 1024: return spread_tiles<T, 1024, 256, 2048>(p, s);
+        case 512: return spread_tiles<T, 512, 128, 2048>(p, s);
+        default: return spread_tiles<T, 128, 128, 1024>(p, s);
+    }
 }
 
 // ------------------------------------------------------- the paper's gridding

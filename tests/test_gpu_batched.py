@@ -207,3 +207,84 @@ def test_host_copies_overlap_chunks(fc2, oracle_mod):
         _, _, chi0, _ = oracle_mod.moments(x, s)
         r = compare(block[:, bins].T.astype(np.float64), ref, piv, chi0)
         assert r["ok"], (c, r)
+
+
+@pytest.mark.parametrize("tile,asm,item", [(512, 256, 1024), (2048, 128, 4096), (1024, 256, 2048)])
+def test_every_tuning_candidate_matches_oracle(fc2, oracle_mod, tile, asm, item):
+    """Each value the batched path's autotuner may pick for the spreading tile,
+    the assembly block and the exact-sum work item, forced as the fixed
+    configuration: sampled bins and the degenerate bins (periods longer than
+    the span, near 1/d) against the oracle."""
+    b = small_survey(C=8, N=1 << 14, seed=23)
+    fc2.batch_force(tile, asm, item)
+    try:
+        out, _, st = fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df, b.N,
+                                         2, "mixed", autotune="fixed")
+    finally:
+        fc2.batch_force(0, 0, 0)
+    cfg = st["config"]
+    assert (cfg["source"], cfg["spread_tile"], cfg["assemble_block"],
+            cfg["exact_item_samples"]) == ("fixed", tile, asm, item)
+    pos = 0
+    for c in range(b.C):
+        cur = b.curve(c)
+        block = out[pos:pos + cur.H * cur.N].reshape(cur.H, cur.N)
+        pos += cur.H * cur.N
+        if c % 2:
+            continue
+        one = int(round((1.0 - cur.f_min) / cur.df))
+        bins = np.unique(np.concatenate([np.arange(0, 24), np.arange(one - 8, one + 9),
+                                         sample_bins(cur.N, 60, c, windows=[], half=0)]))
+        ref, piv = oracle_mod.dchi2_bins(cur.t, cur.x, cur.sigma, cur.H, cur.f_min, cur.df, bins,
+                                         with_pivots=True)
+        _, _, chi0, _ = oracle_mod.moments(cur.x, cur.sigma)
+        r = compare(block[:, bins].T.astype(np.float64), ref, piv, chi0)
+        assert r["ok"], (c, tile, asm, item, r)
+
+
+def test_autotuner_table_and_cache_file(fc2, oracle_mod, tmp_path, monkeypatch):
+    """The batched path's autotuner: a call tunes on a miss (source "tuned"),
+    its choice is used by the next call of the same class (source "table",
+    the same bits), is written to the cache file with the sources' version, and
+    is read back from the file by a process that has forgotten it; the tuned
+    results match the oracle."""
+    import importlib
+    build = importlib.import_module("paper_0901_1913_gb300.build")
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("FC2_TUNE_CACHE", str(path))
+    fc2.batch_forget_tuning()
+    try:
+        b = small_survey(C=12, N=1 << 15, seed=29)
+        args = (b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df, b.N, 2, "mixed")
+        out1, _, st1 = fc2.execute_batched(*args)
+        c1 = st1["config"]
+        assert c1["source"] == "tuned" and c1["configurations_timed"] >= 5, c1
+        out2, _, st2 = fc2.execute_batched(*args)
+        assert st2["config"]["source"] == "table"
+        np.testing.assert_array_equal(out1, out2)
+        lines = path.read_text().split("\n")
+        assert lines[0].split()[:2] == ["fc2-batch-tune-1", build.sources_version()], lines[0]
+        fc2.batch_forget_tuning()
+        out3, _, st3 = fc2.execute_batched(*args)
+        c3 = st3["config"]
+        assert c3["source"] == "table"
+        for k in ("fft_family", "fft_log2_radices", "spread_tile", "assemble_block",
+                  "exact_item_samples"):
+            assert c3[k] == c1[k], k
+        np.testing.assert_array_equal(out1, out3)
+        # a forced re-tune runs the search again
+        _, _, st4 = fc2.execute_batched(*args, autotune="retune")
+        assert st4["config"]["source"] == "tuned"
+    finally:
+        fc2.batch_forget_tuning()
+    pos = 0
+    for c in range(0, b.C, 3):
+        cur = b.curve(c)
+        pos = int(np.sum(b.H[:c].astype(np.int64) * b.N[:c]))
+        block = out1[pos:pos + cur.H * cur.N].reshape(cur.H, cur.N)
+        bins = sample_bins(cur.N, 80, c, windows=[int(np.argmax(block[-1]))], half=3)
+        ref, piv = oracle_mod.dchi2_bins(cur.t, cur.x, cur.sigma, cur.H, cur.f_min, cur.df, bins,
+                                         with_pivots=True)
+        _, _, chi0, _ = oracle_mod.moments(cur.x, cur.sigma)
+        r = compare(block[:, bins].T.astype(np.float64), ref, piv, chi0)
+        assert r["ok"], (c, r)
