@@ -647,7 +647,8 @@ def run_profile(args):
         for _ in range(args.warmup + args.steps):
             _, _, stats = _fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df,
                                                b.N, b.oversample, "mixed", top_k=8,
-                                               fft_kernel=args.fft_kernel)
+                                               fft_kernel=args.fft_kernel,
+                                               autotune=args.autotune)
         torch.cuda.synchronize()
         print(json.dumps({"profile_run": True, "workload": args.workload, "curves": b.C,
                           "stats": stats}), flush=True)
@@ -964,6 +965,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fchi2", choices=["fchi2", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--autotune", default="table", choices=("table", "fixed", "retune"),
+                    help="batched launch configuration in --profile runs: the tuning table "
+                         "(tuning on a miss), the fixed default, or tuned anew")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-bins", type=int, default=128)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle (parity, cpu_baseline)")

@@ -650,24 +650,24 @@ __global__ void __launch_bounds__(BX_NT) k_bexact(
 
 // ------------------------------------------------------------------- peaks
 // Per curve: top-K local maxima of its Delta chi^2_H row (value > left,
-// >= right; edges one-sided), ordered by (value desc, j asc).  Stage 1 per
-// block of BP_B bins of one curve, stage 2 one block per curve.  Writes the
-// peak list as (curve << 32 | j) entries, empty slots as (curve << 32 | 0xffffffff).
+// >= right; edges one-sided), ordered by (value desc, j asc).  A threshold
+// first: every block of BP_B bins finds its best local maximum, and the K-th
+// best of those over the curve's blocks, theta, bounds the K-th best local
+// maximum from below (the K blocks whose best reaches theta hold K local maxima
+// at least as large).  Then only the blocks whose best reaches theta rank their
+// local maxima >= theta (the rest write empty lists), and one block per curve
+// merges the lists.  Writes the peak list as (curve << 32 | j) entries, empty
+// slots as (curve << 32 | 0xffffffff).
 constexpr int BP_NT = 256;
 constexpr int BP_PER = 16;
 constexpr int BP_B = BP_NT * BP_PER;
 constexpr int BP_NW = BP_NT / 32;
 constexpr int BP_KMAX = 64;
 
-__global__ void __launch_bounds__(BP_NT) k_bpeaks1(const float* __restrict__ out, int64_t N,
-                                                   CurveTab ct, int K, int nblk,
-                                                   Cand* __restrict__ tops) {
-    __shared__ Cand wtop[BP_NW][BP_KMAX];
-    const int c = blockIdx.y;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const float* row = out + ct.out_off[c] + (int64_t)(ct.H[c] - 1) * N;
-    const int64_t base = (int64_t)blockIdx.x * BP_B;
-    int64_t cv[BP_PER], cj[BP_PER];
+// Local maxima of the block's bins held by this thread (key, bin), empty as
+// (KEY_NONE, INT64_MAX).
+FC2_D void bp_local_maxima(const float* __restrict__ row, int64_t N, int64_t base, int lane, int w,
+                           int64_t* cv, int64_t* cj) {
 #pragma unroll
     for (int q = 0; q < BP_PER; ++q) {
         const int64_t jj = base + lane + (int64_t)(w * BP_PER + q) * 32;
@@ -680,6 +680,112 @@ __global__ void __launch_bounds__(BP_NT) k_bpeaks1(const float* __restrict__ out
             if (left && right) { cv[q] = x; cj[q] = jj; }
         }
     }
+}
+
+// Each block's best local maximum.
+__global__ void __launch_bounds__(BP_NT) k_bpeaks0(const float* __restrict__ out, int64_t N,
+                                                   CurveTab ct, int nblk,
+                                                   Cand* __restrict__ bbest) {
+    __shared__ Cand wb[BP_NW];
+    const int c = blockIdx.y;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float* row = out + ct.out_off[c] + (int64_t)(ct.H[c] - 1) * N;
+    // 32-bit order keys (okey's order for floats); neighbours from the adjacent
+    // lanes, the run's ends from memory; the running best in (value desc, j asc)
+    auto key32 = [](float f) -> int32_t {
+        const int32_t b = __float_as_int(f);
+        if ((b & 0x7fffffff) > 0x7f800000) return INT32_MIN;  // NaN: below everything
+        return b ^ ((b >> 31) & 0x7fffffff);
+    };
+    int32_t bv = INT32_MIN;
+    int64_t bj = INT64_MAX;
+    const int64_t base = (int64_t)blockIdx.x * BP_B;
+#pragma unroll 4
+    for (int q = 0; q < BP_PER; ++q) {
+        const int64_t j0 = base + (int64_t)(w * BP_PER + q) * 32;  // the warp's 32 bins
+        const int64_t jj = j0 + lane;
+        const int32_t x = jj < N ? key32(row[jj]) : INT32_MIN;
+        int32_t xl = __shfl_up_sync(0xffffffffu, x, 1);
+        int32_t xr = __shfl_down_sync(0xffffffffu, x, 1);
+        if (lane == 0 && jj > 0 && jj - 1 < N) xl = key32(row[jj - 1]);
+        if (lane == 31 && jj + 1 < N) xr = key32(row[jj + 1]);
+        const bool left = (jj == 0) || (x > xl);
+        const bool right = (jj == N - 1) || (x >= xr);
+        if (jj < N && left && right && (x > bv || (x == bv && jj < bj))) {
+            bv = x;
+            bj = jj;
+        }
+    }
+    int64_t v = (bv == INT32_MIN) ? KEY_NONE : (int64_t)bv, j = bj;
+    warp_best(v, j);
+    if (lane == 0) wb[w] = Cand{v, j};
+    __syncthreads();
+    if (w == 0) {
+        v = lane < BP_NW ? wb[lane].k : KEY_NONE;
+        j = lane < BP_NW ? wb[lane].j : INT64_MAX;
+        warp_best(v, j);
+        if (lane == 0) bbest[(int64_t)c * nblk + blockIdx.x] = Cand{v, j};
+    }
+}
+
+// theta[c]: the K-th best of curve c's block maxima, KEY_NONE when fewer than
+// K blocks have a local maximum (one 256-thread block per curve).
+__global__ void __launch_bounds__(256) k_bpeaks_theta(const Cand* __restrict__ bbest, int nblk,
+                                                      int K, int64_t* __restrict__ theta) {
+    __shared__ Cand ws[8];
+    const int c = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const Cand* bc = bbest + (int64_t)c * nblk;
+    int64_t pv = INT64_MAX, pj = -1, th = KEY_NONE;
+    for (int r = 0; r < K; ++r) {
+        int64_t v = KEY_NONE, j = INT64_MAX;
+        for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+            const Cand cd = bc[b];
+            if (cd.j != INT64_MAX && better(pv, pj, cd.k, cd.j) && better(cd.k, cd.j, v, j)) {
+                v = cd.k;
+                j = cd.j;
+            }
+        }
+        warp_best(v, j);
+        if (lane == 0) ws[w] = Cand{v, j};
+        __syncthreads();
+        v = lane < 8 ? ws[lane].k : KEY_NONE;
+        j = lane < 8 ? ws[lane].j : INT64_MAX;
+        warp_best(v, j);  // every warp: the round's winner
+        __syncthreads();  // ws is rewritten by the next round
+        if (j == INT64_MAX) {  // fewer than K blocks with a local maximum
+            th = KEY_NONE;
+            break;
+        }
+        th = v;
+        pv = v;
+        pj = j;
+    }
+    if (threadIdx.x == 0) theta[c] = th;
+}
+
+// The top-K local maxima >= theta of the blocks whose best reaches theta.
+__global__ void __launch_bounds__(BP_NT) k_bpeaks1(const float* __restrict__ out, int64_t N,
+                                                   CurveTab ct, int K, int nblk,
+                                                   const Cand* __restrict__ bbest,
+                                                   const int64_t* __restrict__ theta,
+                                                   Cand* __restrict__ tops) {
+    __shared__ Cand wtop[BP_NW][BP_KMAX];
+    const int c = blockIdx.y;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t th = theta[c];
+    const Cand bb = bbest[(int64_t)c * nblk + blockIdx.x];
+    Cand* tb = tops + ((int64_t)c * nblk + blockIdx.x) * K;
+    if (bb.j == INT64_MAX || bb.k < th) {
+        for (int r = threadIdx.x; r < K; r += blockDim.x) tb[r] = Cand{KEY_NONE, INT64_MAX};
+        return;
+    }
+    const float* row = out + ct.out_off[c] + (int64_t)(ct.H[c] - 1) * N;
+    int64_t cv[BP_PER], cj[BP_PER];
+    bp_local_maxima(row, N, (int64_t)blockIdx.x * BP_B, lane, w, cv, cj);
+#pragma unroll
+    for (int q = 0; q < BP_PER; ++q)
+        if (cv[q] < th) { cv[q] = KEY_NONE; cj[q] = INT64_MAX; }
     for (int r = 0; r < K; ++r) {
         int64_t v = KEY_NONE, j = INT64_MAX;
 #pragma unroll
@@ -701,7 +807,7 @@ __global__ void __launch_bounds__(BP_NT) k_bpeaks1(const float* __restrict__ out
             const int64_t mj = j;
             warp_best(v, j);
             if (lane < BP_NW && mj == j && j != INT64_MAX) ++head;
-            if (lane == 0) tops[((int64_t)c * nblk + blockIdx.x) * K + r] = Cand{v, j};
+            if (lane == 0) tb[r] = Cand{v, j};
         }
     }
 }
@@ -830,6 +936,8 @@ struct Batch {
     int32_t* counts = nullptr; size_t ccnt = 0;
     int* curves = nullptr; size_t ccurves = 0;
     Cand* tops = nullptr; size_t ctops = 0;
+    Cand* bbest = nullptr; size_t cbbest = 0;  // best local maximum of each peak block
+    int64_t* theta = nullptr; size_t ctheta = 0;  // per curve: the peak threshold
     int64_t* pent = nullptr; size_t cpent = 0;
     fc2_best* recs = nullptr; size_t crecs = 0;  // every curve's peak records [C][K]
     fc2_best* recs_now = nullptr;  // the records of the chunk being launched
@@ -880,7 +988,8 @@ struct Batch {
         release(key, s); release(dlt, s); release(cs, s); release(grid0, s); release(grid1, s);
         release(spec, s); release(out, s); release(out2, s); release(list, s); release(list2, s); release(list3, s);
         release(list4, s); release(dftab, s); release(qbase, s); release(items, s); release(part, s);
-        release(counts, s); release(curves, s); release(tops, s); release(pent, s);
+        release(counts, s); release(curves, s); release(tops, s); release(bbest, s);
+        release(theta, s); release(pent, s);
         release(recs, s); release(cnt_hist, s); release(red, s);
         release(cp.d_twlo, s); release(cp.d_twhi, s); release(cp.d_twst, s); release(cp.d_dec, s);
         if (gexec) cudaGraphExecDestroy(gexec);
@@ -1074,9 +1183,12 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
     mark(4);
     if (K > 0) {
         const int nblk = (int)((N + BP_B - 1) / BP_B);
-        k_bpeaks1<<<dim3((unsigned)nblk, (unsigned)nc), BP_NT, 0, s>>>(out, N, ct, K, nblk, b.tops);
+        k_bpeaks0<<<dim3((unsigned)nblk, (unsigned)nc), BP_NT, 0, s>>>(out, N, ct, nblk, b.bbest);
+        k_bpeaks_theta<<<(unsigned)nc, 256, 0, s>>>(b.bbest, nblk, K, b.theta);
+        k_bpeaks1<<<dim3((unsigned)nblk, (unsigned)nc), BP_NT, 0, s>>>(out, N, ct, K, nblk, b.bbest,
+                                                                        b.theta, b.tops);
         k_bpeaks2<<<(unsigned)nc, 256, 0, s>>>(b.tops, nblk, K, b.pent);
-        nl += 2;
+        nl += 4;
         exact(I2{}, I1{}, b.pent, b.counts + 4, nrec, tau_drop, nullptr, nullptr, 0, b.recs_now);
     }
     mark(5);
@@ -1593,6 +1705,8 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             ok(need(&b.part, &b.cpart, (size_t)BX_ITEMS * 6 * BHM, s)) &&
             ok(need(&b.counts, &b.ccnt, 16, s)) && ok(need(&b.curves, &b.ccurves, mxc, s)) &&
             ok(need(&b.tops, &b.ctops, mx_tops, s)) &&
+            ok(need(&b.bbest, &b.cbbest, std::max<size_t>(mx_tops / std::max(K, 1), 1), s)) &&
+            ok(need(&b.theta, &b.ctheta, mxc, s)) &&
             ok(need(&b.pent, &b.cpent, (size_t)std::max<int64_t>(mx_nrec, 1), s)) &&
             ok(need(&b.recs, &b.crecs, (size_t)std::max<int64_t>(C * K, 1), s)) &&
             ok(need(&b.cnt_hist, &b.chist, nchunks * 16, s));

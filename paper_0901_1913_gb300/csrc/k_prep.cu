@@ -814,9 +814,16 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
                                                const int64_t* __restrict__ slot_n,
                                                const int64_t* __restrict__ rngtab) {
     constexpr int PER = TILE / NT;
+    // cumulative key counts of the staged samples: cum[i] = samples with
+    // tile-relative key <= i - w (keys lie in [-w + 1, TILE)), so the samples of
+    // cell l (l - w + 1 <= key <= l, contiguous in sorted order) are
+    // [cum[l], cum[l + w]); PCUM consecutive entries per thread for the scan
+    constexpr int PCUM = (TILE + 32 + NT - 1) / NT;
     __shared__ int32_t sk[CAP];
     __shared__ T sd[CAP];
     __shared__ cpx<T> sc[CAP];
+    __shared__ int32_t cum[PCUM * NT];
+    __shared__ int32_t wtot[NT / 32];
     const int g = blockIdx.y;
     const int64_t a = (int64_t)blockIdx.x * TILE;
     if (a >= Lg[g]) return;
@@ -850,6 +857,8 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
         const int64_t total = c0 + c1 + c2;
         for (int64_t cb = 0; cb < total; cb += CAP) {
             const int cnt = (int)min((int64_t)CAP, total - cb);
+#pragma unroll
+            for (int i = 0; i < PCUM; ++i) cum[threadIdx.x * PCUM + i] = 0;
             for (int e = threadIdx.x; e < cnt; e += NT) {
                 int64_t v = cb + e;
                 int64_t src;
@@ -862,14 +871,38 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
                 sc[e] = cg[src];
             }
             __syncthreads();
+            // key histogram (exact counts), then an inclusive block scan
+            for (int e = threadIdx.x; e < cnt; e += NT) atomicAdd(&cum[sk[e] + w], 1);
+            __syncthreads();
+            {
+                int32_t run[PCUM];
+                int32_t t = 0;
+#pragma unroll
+                for (int i = 0; i < PCUM; ++i) {
+                    t += cum[threadIdx.x * PCUM + i];
+                    run[i] = t;
+                }
+                const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+                int32_t incl = t;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                if (lane == 31) wtot[wi] = incl;
+                __syncthreads();
+                int32_t before = incl - t;
+                for (int k = 0; k < wi; ++k) before += wtot[k];
+#pragma unroll
+                for (int i = 0; i < PCUM; ++i) cum[threadIdx.x * PCUM + i] = before + run[i];
+            }
+            __syncthreads();
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
                 const int l = threadIdx.x + q * NT;  // tile-relative cell
-                // samples with l - w + 1 <= key <= l, contiguous in sorted order
-                int lo = 0, hi = cnt;
-                while (lo < hi) { int mid = (lo + hi) >> 1; if (sk[mid] < l - w + 1) lo = mid + 1; else hi = mid; }
-                int e = lo;
-                for (; e < cnt && sk[e] <= l; ++e) {
+                // samples with l - w + 1 <= key <= l, in sorted order
+                const int e1 = cum[l + w];
+                for (int e = cum[l]; e < e1; ++e) {
                     T z = (T)(l - sk[e]) + (T)1 - sd[e] - hw;
                     T ph = es_kernel<T>(z, ihw, beta);
                     acc[q].add(sc[e].x * ph, sc[e].y * ph);
