@@ -320,9 +320,12 @@ def survey_parity(b, got_block, best_j, threads, seconds, n_curves=64, max_bins=
     return parity, cpu
 
 
-def single_curve_record(c, args, threads, n_random, half, mixed_steps, fp64_steps, windows):
+def single_curve_record(c, args, threads, n_random, half, mixed_steps, fp64_steps, windows,
+                        first_bins=0):
     """Mixed and FP64 rates of one curve (CUDA events on the plan's stream),
-    stage times, and oracle parity on sampled bins."""
+    stage times, and oracle parity on sampled bins (random ones, windows at the
+    given bins and the best one, and the first `first_bins` bins: periods
+    longer than the span, the exact fix-up's hardest cases)."""
     import torch
     from paper_0901_1913_gb300 import _fc2
     from tests.parity import compare, sample_bins
@@ -352,6 +355,7 @@ def single_curve_record(c, args, threads, n_random, half, mixed_steps, fp64_step
     evals = c.N * c.H
     bins = sample_bins(c.N, n_random, 11, windows=list(windows) + [res["mixed"]["best"][-1]["j"]],
                        half=half)
+    bins = np.union1d(bins, np.arange(min(first_bins, c.N), dtype=np.int64))
     from oracle import oracle
     t0 = time.perf_counter()
     d_or, piv = oracle.dchi2_bins(c.t, c.x, c.sigma, c.H, c.f_min, c.df, bins, threads=threads,
@@ -528,12 +532,14 @@ def run_survey(args):
         f0 = c.truth["f0"]
         subrec["long_curve"] = dict(workload=LONG, **single_curve_record(
             c, args, threads, 1024, 8, min(args.steps, 20), 3,
-            [round((k * f0 - c.f_min) / c.df) for k in (0.5, 1, 2)] + [round((1 - c.f_min) / c.df)]))
+            [round((k * f0 - c.f_min) / c.df) for k in (0.5, 1, 2)] + [round((1 - c.f_min) / c.df)],
+            first_bins=32))
         del c
         c = synth.large_curve()
         subrec["large_curve"] = dict(workload=LARGE, **single_curve_record(
-            c, args, threads, 48, 2, 3, 2,
-            [round((f * h - c.f_min) / c.df) for f in c.truth["fs"] for h in (1, 2)]))
+            c, args, threads, 192, 2, 3, 2,
+            [round((f * h - c.f_min) / c.df) for f in c.truth["fs"] for h in (1, 2)],
+            first_bins=32))
         del c
     if band is not None:
         subrec["long_curve_bands"] = band
