@@ -153,22 +153,31 @@ void fc2_debug_batch_timing(int enable);
  * values per curve).  Zeros when timing was off.  No-op on NULL. */
 void fc2_debug_batch_stage_ms(double* out6);
 
+/* e^{2 pi i u_k 2^-64} for n 64-bit phases (host array, n in 1..2^24) as the
+ * exact fix-up's double-float phasor evaluates it (table factors for the top
+ * 16 bits, a small rotation for the rest): out4[4k..4k+3] = (re high, re low,
+ * im high, im low), host floats.  For tests of its accuracy.
+ * FC2_ERR_INVALID_ARG for bad arguments, FC2_ERR_CUDA on a CUDA failure. */
+fc2_status fc2_debug_phasor(const uint64_t* u, int64_t n, float* out4);
+
 /* Launch configuration of the last fc2_execute_batched call's last chunk
  * (out12): [0] source (0 fixed, 1 tuning table or cache file, 2 tuned in the
  * call), [1] transform family (0 radix-16 in shared memory, 1 two register
  * stages, 2 bulk copies), [2] spreading tile (cells), [3] assembly block
  * (threads), [4] samples per exact-sum work item, [5] transform passes,
  * [6..9] their log2 radices, [10] configurations timed, [11] tuning
- * milliseconds (host wall time; the bits of a double). */
-void fc2_debug_batch_config(int64_t* out12);
+ * milliseconds (host wall time; the bits of a double), [12] grids taken
+ * through both transform passes at a time (0 = all grids pass by pass). */
+void fc2_debug_batch_config(int64_t* out13);
 
 /* Fixed configuration of batched calls that do not tune (autotune = -1, or a
  * transform family requested): spreading tile 512 / 1024 / 2048 cells,
  * assembly block 128 / 256 threads (float), exact-sum work item 1024 / 2048 /
- * 4096 samples; 0, or a value the grid does not allow, keeps the default
- * (1024 cells, or 128 below 4096-point grids; 128 threads; 2048 samples).
+ * 4096 samples, transform groups of 8 / 16 / 32 grids; 0, or a value the
+ * grid does not allow, keeps the default (1024 cells, or 128 below
+ * 4096-point grids; 128 threads; 2048 samples; all grids pass by pass).
  * Process-wide; for tests and diagnostics. */
-void fc2_debug_batch_force(int spread_tile, int asm_nt, int bx_ch);
+void fc2_debug_batch_force(int spread_tile, int asm_nt, int bx_ch, int fft_group);
 
 /* Empty this process's tuning table of the batched path; the cache file is
  * read again at the next lookup. */

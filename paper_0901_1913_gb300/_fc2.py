@@ -170,7 +170,7 @@ def load():
         lib.fc2_debug_pool_used.restype = i64
         lib.fc2_debug_batch_config.argtypes = [_P]
         lib.fc2_debug_batch_config.restype = None
-        lib.fc2_debug_batch_force.argtypes = [i32, i32, i32]
+        lib.fc2_debug_batch_force.argtypes = [i32, i32, i32, i32]
         lib.fc2_debug_batch_force.restype = None
         lib.fc2_debug_batch_forget_tuning.argtypes = []
         lib.fc2_debug_batch_forget_tuning.restype = None
@@ -386,21 +386,22 @@ FFT_FAMILY_NAMES = {0: "radix-16 stages in shared memory", 1: "two register stag
 def batch_config():
     """Launch configuration of the last batched call's last chunk
     (fc2_debug_batch_config) as a dict."""
-    v = np.zeros(12, dtype=np.int64)
+    v = np.zeros(13, dtype=np.int64)
     load().fc2_debug_batch_config(v.ctypes.data)
     npass = int(v[5])
     return dict(source=("fixed", "table", "tuned")[int(v[0])] if 0 <= v[0] <= 2 else int(v[0]),
                 fft_family=FFT_FAMILY_NAMES.get(int(v[1]), int(v[1])),
                 fft_log2_radices=[int(r) for r in v[6:6 + npass]],
                 spread_tile=int(v[2]), assemble_block=int(v[3]), exact_item_samples=int(v[4]),
-                configurations_timed=int(v[10]),
+                transform_group=int(v[12]), configurations_timed=int(v[10]),
                 tuning_ms=float(v[11:12].view(np.float64)[0]))
 
 
-def batch_force(spread_tile=0, assemble_block=0, exact_item_samples=0):
+def batch_force(spread_tile=0, assemble_block=0, exact_item_samples=0, transform_group=0):
     """Fixed configuration of batched calls that do not tune (autotune
     "fixed" or a transform family requested); zeros keep the defaults."""
-    load().fc2_debug_batch_force(int(spread_tile), int(assemble_block), int(exact_item_samples))
+    load().fc2_debug_batch_force(int(spread_tile), int(assemble_block), int(exact_item_samples),
+                                 int(transform_group))
 
 
 def batch_forget_tuning():

@@ -840,6 +840,14 @@ fc2_status fc2_debug_exact_bins(fc2_plan p, const int64_t* bins, int64_t nb, int
     return FC2_OK;
 }
 
+/* e^{2 pi i u_k 2^-64} for n 64-bit phases as the exact fix-up's double-float
+ * phasor computes it: out4[4k..4k+3] = (re hi, re lo, im hi, im lo).  For
+ * tests of its accuracy.  n in 1..2^24. */
+fc2_status fc2_debug_phasor(const uint64_t* u, int64_t n, float* out4) {
+    if (!u || !out4 || n < 1 || n > (1 << 24)) return FC2_ERR_INVALID_ARG;
+    return fc2::debug_phasor(u, n, out4) == cudaSuccess ? FC2_OK : FC2_ERR_CUDA;
+}
+
 /* Kernels launched by the last fc2_execute_batched call of this process. */
 int64_t fc2_debug_batch_launches(void) { return g_last_batch_launches; }
 
@@ -864,18 +872,19 @@ void fc2_debug_batch_timing(int enable) { set_batch_timing(enable != 0); }
  * 2 bulk copies), [2] spreading tile cells, [3] assembly block threads,
  * [4] samples per exact-sum work item, [5] transform passes, [6..9] their
  * log2 radices, [10] configurations timed, [11] tuning milliseconds (host
- * wall time, as the bits of a double). */
-void fc2_debug_batch_config(int64_t* out12) {
-    if (out12)
-        for (int i = 0; i < 12; ++i) out12[i] = g_last_batch_stats[18 + i];
+ * wall time, as the bits of a double), [12] grids per transform group (0 =
+ * all). */
+void fc2_debug_batch_config(int64_t* out13) {
+    if (out13)
+        for (int i = 0; i < 13; ++i) out13[i] = g_last_batch_stats[18 + i];
 }
 
 /* Fixed configuration for batched calls that do not tune (autotune -1 or a
  * transform family requested): spreading tile 512 / 1024 / 2048 cells,
  * assembly block 128 / 256 threads, work item 1024 / 2048 / 4096 samples;
  * 0 (or a value the grid does not allow) keeps the default. */
-void fc2_debug_batch_force(int spread_tile, int asm_nt, int bx_ch) {
-    fc2::force_batch_config(spread_tile, asm_nt, bx_ch);
+void fc2_debug_batch_force(int spread_tile, int asm_nt, int bx_ch, int fft_group) {
+    fc2::force_batch_config(spread_tile, asm_nt, bx_ch, fft_group);
 }
 
 /* Forget the batched path's tuning table of this process (the cache file is

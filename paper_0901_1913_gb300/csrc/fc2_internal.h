@@ -230,7 +230,7 @@ bool fft_choice_valid(int logM, bool fp64, const FftChoice& c);
 cudaError_t set_fft_choice(fc2_plan_s* p, const FftChoice& c, cudaStream_t s);
 // k_batch.cu: the batched path's tuning table and fixed configuration
 void forget_batch_tuning();
-void force_batch_config(int spread_tile, int asm_nt, int bx_ch);
+void force_batch_config(int spread_tile, int asm_nt, int bx_ch, int fft_group);
 cudaError_t pool_alloc(void** ptr, size_t bytes, cudaStream_t s);  // library device pool
 void drop_deconv_cache(int dev);  // k_fft.cu: cached deconvolution tables of a device
 cudaError_t launch_fft(fc2_plan_s* p, cudaStream_t s);
@@ -267,6 +267,7 @@ cudaError_t launch_phase_fx(fc2_plan_s* p, cudaStream_t s);
 // Phasor tables of the exact sums (512 double-float pairs, then 512 double2)
 // into tab (2 * 512 * 16 bytes).
 cudaError_t launch_init_dftab(void* tab, cudaStream_t s);
+cudaError_t debug_phasor(const uint64_t* u, int64_t n, float* out4);  // diagnostics
 
 // k_adjoint.cu: one entry = (curve << 32 | bin) of a curve table
 struct AdjTab {

@@ -897,6 +897,7 @@ struct BatchConfig {
     int spread_tile;
     int asm_nt;
     int bx_ch;
+    int fft_group = 0;  // grids taken through both passes at a time (0 = all)
 };
 
 struct Batch {
@@ -1307,6 +1308,7 @@ static bool config_valid(const BatchTuneKey& k, const BatchConfig& c) {
     if (spread_tile_of(k.M, c.spread_tile) != c.spread_tile) return false;
     if (c.asm_nt != 128 && c.asm_nt != 256) return false;
     if (c.bx_ch != 1024 && c.bx_ch != 2048 && c.bx_ch != 4096) return false;
+    if (c.fft_group != 0 && c.fft_group != 8 && c.fft_group != 16 && c.fft_group != 32) return false;
     return true;
 }
 
@@ -1323,15 +1325,15 @@ static void load_tune_cache() {
     while (fgets(line, sizeof line, f)) {
         char tag[32], ver[64], dev[160];
         long long N, M;
-        int osmp, fp64, w, hmax, shared, np, r[4] = {0, 0, 0, 0}, fam, tile, ant, ch;
-        const int got = sscanf(line, "%31s %63s %159s %lld %lld %d %d %d %d %d : %d %d %d %d %d %d %d %d %d",
+        int osmp, fp64, w, hmax, shared, np, r[4] = {0, 0, 0, 0}, fam, tile, ant, ch, grp;
+        const int got = sscanf(line, "%31s %63s %159s %lld %lld %d %d %d %d %d : %d %d %d %d %d %d %d %d %d %d",
                                tag, ver, dev, &N, &M, &osmp, &fp64, &w, &hmax, &shared, &np, &r[0],
-                               &r[1], &r[2], &r[3], &fam, &tile, &ant, &ch);
-        if (got != 19 || std::string(tag) != "fc2-batch-tune-1" ||
+                               &r[1], &r[2], &r[3], &fam, &tile, &ant, &ch, &grp);
+        if (got != 20 || std::string(tag) != "fc2-batch-tune-2" ||
             std::string(ver) != FC2_SRC_VERSION || np < 1 || np > 4)
             continue;
         BatchTuneKey k{dev, N, M, osmp, fp64, w, hmax, shared};
-        BatchConfig c{FftChoice{std::vector<int>(r, r + np), fam}, tile, ant, ch};
+        BatchConfig c{FftChoice{std::vector<int>(r, r + np), fam}, tile, ant, ch, grp};
         if (config_valid(k, c)) g_btune[k] = c;
     }
     fclose(f);
@@ -1347,10 +1349,10 @@ static void store_tune(const BatchTuneKey& k, const BatchConfig& c) {
     for (int i = 0; i < np; ++i) r[i] = c.fft.rs[i];
     char line[512];
     const int len = snprintf(line, sizeof line,
-                             "fc2-batch-tune-1 %s %s %lld %lld %d %d %d %d %d : %d %d %d %d %d %d %d %d %d\n",
+                             "fc2-batch-tune-2 %s %s %lld %lld %d %d %d %d %d : %d %d %d %d %d %d %d %d %d %d\n",
                              FC2_SRC_VERSION, k.dev.c_str(), (long long)k.N, (long long)k.M, k.osmp,
                              k.fp64, k.w, k.hmax, k.shared, np, r[0], r[1], r[2], r[3], c.fft.family,
-                             c.spread_tile, c.asm_nt, c.bx_ch);
+                             c.spread_tile, c.asm_nt, c.bx_ch, c.fft_group);
     if (len <= 0 || len >= (int)sizeof line) return;
     FILE* f = fopen(path.c_str(), "a");
     if (!f) return;
@@ -1376,11 +1378,12 @@ void forget_batch_tuning() {
 // A fixed configuration chosen for the next calls (diagnostics and tests:
 // every candidate must give the same results within the error bounds); zero
 // fields keep the defaults.
-static int g_force_tile = 0, g_force_asm = 0, g_force_ch = 0;
-void force_batch_config(int spread_tile, int asm_nt, int bx_ch) {
+static int g_force_tile = 0, g_force_asm = 0, g_force_ch = 0, g_force_grp = 0;
+void force_batch_config(int spread_tile, int asm_nt, int bx_ch, int fft_group) {
     g_force_tile = spread_tile;
     g_force_asm = asm_nt;
     g_force_ch = bx_ch;
+    g_force_grp = fft_group;
 }
 
 // Apply a configuration to the chunk plan and the batch.
@@ -1390,8 +1393,10 @@ static cudaError_t apply_config(Batch& b, const BatchConfig& c) {
     b.bx_ch = c.bx_ch;
     std::vector<int> cur;
     for (const auto& ps : b.cp.passes) cur.push_back(ps.logR);
-    if (cur == c.fft.rs && b.cp.fft_family == c.fft.family && b.cp.fft_group == 0) return cudaSuccess;
-    return set_fft_choice(&b.cp, c.fft, b.s);
+    cudaError_t e = cudaSuccess;
+    if (!(cur == c.fft.rs && b.cp.fft_family == c.fft.family)) e = set_fft_choice(&b.cp, c.fft, b.s);
+    b.cp.fft_group = c.fft_group;
+    return e;
 }
 
 // Time the candidates on the chunk: run() launches the whole chunk (no graph);
@@ -1773,6 +1778,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             cfg.spread_tile = spread_tile_of(M, g_force_tile);
             if (g_force_asm == 256 && !fp64) cfg.asm_nt = 256;
             if (g_force_ch == 1024 || g_force_ch == 4096) cfg.bx_ch = g_force_ch;
+            if (g_force_grp == 8 || g_force_grp == 16 || g_force_grp == 32) cfg.fft_group = g_force_grp;
         } else if (tune_mode == 1 && lookup_tune(tkey, &cfg)) {
             source = 1;
         } else {
@@ -2021,6 +2027,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         for (int i = 0; i < 4; ++i)
             stats_out[24 + i] = i < (int)b.cfg.fft.rs.size() ? b.cfg.fft.rs[i] : 0;
         stats_out[28] = b.tune_timed;
+        stats_out[30] = b.cfg.fft_group;
         std::memcpy(&stats_out[29], &b.tune_ms, 8);
     }
     return st;

@@ -1012,6 +1012,38 @@ cudaError_t launch_init_dftab(void* tab, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The double-float phasor of each phase (diagnostics: its accuracy test).
+__global__ void k_debug_phasor(const uint64_t* __restrict__ u, int64_t n,
+                               const dfc* __restrict__ tab, float* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const dfc z = df_phasor(u[i], tab, tab + 256);
+    out[4 * i] = z.re.h;
+    out[4 * i + 1] = z.re.l;
+    out[4 * i + 2] = z.im.h;
+    out[4 * i + 3] = z.im.l;
+}
+
+cudaError_t debug_phasor(const uint64_t* u, int64_t n, float* out4) {
+    void* d = nullptr;
+    const size_t tb = (size_t)512 * sizeof(dfc) + 512 * sizeof(double2);
+    const size_t bytes = tb + (size_t)n * 8 + (size_t)n * 16;
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e != cudaSuccess) return e;
+    char* base = (char*)d;
+    uint64_t* du = (uint64_t*)(base + tb);
+    float* dout = (float*)(base + tb + (size_t)n * 8);
+    e = launch_init_dftab(base, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(du, u, (size_t)n * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_debug_phasor<<<(unsigned)((n + 255) / 256), 256>>>(du, n, (const dfc*)base, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out4, dout, (size_t)n * 16, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e;
+}
+
 size_t exact_scratch_bytes(int64_t n, int H, int64_t cap) {
     (void)n;
     return (size_t)cap * EX_MAX_CHUNKS * 6 * H * sizeof(double);

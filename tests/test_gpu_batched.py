@@ -209,22 +209,23 @@ def test_host_copies_overlap_chunks(fc2, oracle_mod):
         assert r["ok"], (c, r)
 
 
-@pytest.mark.parametrize("tile,asm,item", [(512, 256, 1024), (2048, 128, 4096), (1024, 256, 2048)])
-def test_every_tuning_candidate_matches_oracle(fc2, oracle_mod, tile, asm, item):
+@pytest.mark.parametrize("tile,asm,item,grp", [(512, 256, 1024, 8), (2048, 128, 4096, 16),
+                                                (1024, 256, 2048, 32)])
+def test_every_tuning_candidate_matches_oracle(fc2, oracle_mod, tile, asm, item, grp):
     """Each value the batched path's autotuner may pick for the spreading tile,
-    the assembly block and the exact-sum work item, forced as the fixed
-    configuration: sampled bins and the degenerate bins (periods longer than
-    the span, near 1/d) against the oracle."""
+    the assembly block, the exact-sum work item and the transform group,
+    forced as the fixed configuration: sampled bins and the degenerate bins
+    (periods longer than the span, near 1/d) against the oracle."""
     b = small_survey(C=8, N=1 << 14, seed=23)
-    fc2.batch_force(tile, asm, item)
+    fc2.batch_force(tile, asm, item, grp)
     try:
         out, _, st = fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df, b.N,
                                          2, "mixed", autotune="fixed")
     finally:
-        fc2.batch_force(0, 0, 0)
+        fc2.batch_force(0, 0, 0, 0)
     cfg = st["config"]
-    assert (cfg["source"], cfg["spread_tile"], cfg["assemble_block"],
-            cfg["exact_item_samples"]) == ("fixed", tile, asm, item)
+    assert (cfg["source"], cfg["spread_tile"], cfg["assemble_block"], cfg["exact_item_samples"],
+            cfg["transform_group"]) == ("fixed", tile, asm, item, grp)
     pos = 0
     for c in range(b.C):
         cur = b.curve(c)
@@ -263,13 +264,13 @@ def test_autotuner_table_and_cache_file(fc2, oracle_mod, tmp_path, monkeypatch):
         assert st2["config"]["source"] == "table"
         np.testing.assert_array_equal(out1, out2)
         lines = path.read_text().split("\n")
-        assert lines[0].split()[:2] == ["fc2-batch-tune-1", build.sources_version()], lines[0]
+        assert lines[0].split()[:2] == ["fc2-batch-tune-2", build.sources_version()], lines[0]
         fc2.batch_forget_tuning()
         out3, _, st3 = fc2.execute_batched(*args)
         c3 = st3["config"]
         assert c3["source"] == "table"
         for k in ("fft_family", "fft_log2_radices", "spread_tile", "assemble_block",
-                  "exact_item_samples"):
+                  "exact_item_samples", "transform_group"):
             assert c3[k] == c1[k], k
         np.testing.assert_array_equal(out1, out3)
         # a forced re-tune runs the search again
