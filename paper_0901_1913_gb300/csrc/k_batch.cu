@@ -953,7 +953,22 @@ struct Batch {
     cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
     bool copied_pending[2] = {false, false};
     char* red = nullptr; size_t cred = 0;
-    cudaGraphExec_t gexec = nullptr;
+    // two executable graphs used by alternate chunks: a chunk's graph is updated
+    // only once the launch of the chunk two before it (same executable) is done
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    cudaEvent_t ev_graph[2] = {nullptr, nullptr};
+    bool graph_pending[2] = {false, false};
+    // the chunk being launched: its slices of the device inputs
+    const double *tc = nullptr, *xc = nullptr, *sgc = nullptr;
+    // every curve's moments (one launch for the whole call) and its offsets
+    double* scal_all = nullptr; size_t cscal_all = 0;
+    int64_t* goff = nullptr; size_t cgoff = 0;
+    // pinned staging of the chunk tables, two halves used by alternate chunks
+    // (a half is refilled once the copies of the chunk two before are done)
+    char* stage = nullptr;
+    size_t stage_half = 0;
+    cudaEvent_t ev_tab[2] = {nullptr, nullptr};
+    bool tab_pending[2] = {false, false};
     int64_t graphs = 0;  // chunk graphs launched
     // tuned launch parameters (besides the transform plan in cp): threads per
     // assembly block and samples per exact-sum work item
@@ -993,8 +1008,16 @@ struct Batch {
         release(theta, s); release(pent, s);
         release(recs, s); release(cnt_hist, s); release(red, s);
         release(cp.d_twlo, s); release(cp.d_twhi, s); release(cp.d_twst, s); release(cp.d_dec, s);
-        if (gexec) cudaGraphExecDestroy(gexec);
-        gexec = nullptr;
+        for (int i = 0; i < 2; ++i) {
+            if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
+            gexec[i] = nullptr;
+            if (ev_graph[i]) cudaEventDestroy(ev_graph[i]);
+            if (ev_tab[i]) cudaEventDestroy(ev_tab[i]);
+            ev_graph[i] = ev_tab[i] = nullptr;
+        }
+        release(scal_all, s); release(goff, s);
+        if (stage) cudaFreeHost(stage);
+        stage = nullptr;
         for (auto& e : ev)
             if (e) { cudaEventDestroy(e); e = nullptr; }
         for (int i = 0; i < 2; ++i) {
@@ -1078,7 +1101,7 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
     };
     mark(0);
     k_bgather<<<(unsigned)((ntot + 255) / 256), 256, 0, s>>>(
-        b.t, b.x, b.sg, b.perm, ntot, b.off, nc, b.scal, b.fmin, b.df, b.tau, b.wq, b.wp, b.A, b.B,
+        b.tc, b.xc, b.sgc, b.perm, ntot, b.off, nc, b.scal, b.fmin, b.df, b.tau, b.wq, b.wp, b.A, b.B,
         b.wq32, b.wp32);
     ++nl;
     cudaError_t e = launch_init_dftab(b.dftab, s);
@@ -1203,7 +1226,7 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
 // one is instantiated.  A stream that cannot be captured gets the launches
 // directly.
 template <typename F>
-static cudaError_t launch_as_graph(Batch& b, F&& launches) {
+static cudaError_t launch_as_graph(Batch& b, cudaGraphExec_t& gexec, F&& launches) {
     cudaStream_t s = b.s;
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
@@ -1217,17 +1240,17 @@ static cudaError_t launch_as_graph(Batch& b, F&& launches) {
         cudaGetLastError();
         return el != cudaSuccess ? el : (ec != cudaSuccess ? ec : cudaErrorUnknown);
     }
-    if (b.gexec) {
+    if (gexec) {
         cudaGraphExecUpdateResultInfo info;
-        if (cudaGraphExecUpdate(b.gexec, g, &info) != cudaSuccess) {
+        if (cudaGraphExecUpdate(gexec, g, &info) != cudaSuccess) {
             cudaGetLastError();
-            cudaGraphExecDestroy(b.gexec);
-            b.gexec = nullptr;
+            cudaGraphExecDestroy(gexec);
+            gexec = nullptr;
         }
     }
     cudaError_t e = cudaSuccess;
-    if (!b.gexec) e = cudaGraphInstantiate(&b.gexec, g, 0);
-    if (e == cudaSuccess) e = cudaGraphLaunch(b.gexec, s);
+    if (!gexec) e = cudaGraphInstantiate(&gexec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(gexec, s);
     cudaGraphDestroy(g);
     if (e == cudaSuccess) ++b.graphs;
     return e;
@@ -1529,6 +1552,39 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         return std::chrono::duration<double, std::milli>(z - a).count();
     };
     const auto t_entry = now();
+    // host inputs are copied to the device whole: a batch whose samples would
+    // take more than a quarter of the memory budget runs as two halves
+    if (!opt.inputs_on_device && C > 1) {
+        size_t fb = 0, tb = 0;
+        cudaMemGetInfo(&fb, &tb);
+        cudaGetLastError();
+        const size_t bud = std::min<size_t>(fb / 2, (size_t)48 << 30);
+        if ((size_t)(offsets[C] - offsets[0]) * 24 > bud / 4) {
+            const int64_t h = C / 2;
+            int64_t l1 = 0, l2 = 0, s1[32] = {0}, s2[32] = {0};
+            fc2_status r = batched_execute(h, offsets, t, x, sigma, Hc, fminc, dfc, Nc, oversample, opt,
+                                           dchi2, peaks, &l1, s1);
+            if (r != FC2_OK) return r;
+            int64_t o1 = 0;
+            for (int64_t c = 0; c < h; ++c) o1 += (int64_t)Hc[c] * Nc[c];
+            r = batched_execute(C - h, offsets + h, t, x, sigma, Hc + h, fminc + h, dfc + h, Nc + h,
+                                oversample, opt, dchi2 ? dchi2 + o1 : nullptr,
+                                peaks ? peaks + h * K : nullptr, &l2, s2);
+            if (launches_out) *launches_out = l1 + l2;
+            if (stats_out) {
+                for (int i = 0; i < 5; ++i) stats_out[i] = s1[i] + s2[i];
+                for (int i = 5; i < 18; ++i) {  // host phases, stage times, bytes: sums of doubles
+                    double a1, a2;
+                    std::memcpy(&a1, &s1[i], 8);
+                    std::memcpy(&a2, &s2[i], 8);
+                    a1 += a2;
+                    std::memcpy(&stats_out[i], &a1, 8);
+                }
+                for (int i = 18; i < 32; ++i) stats_out[i] = s2[i];
+            }
+            return r;
+        }
+    }
     Batch b;
     if (opt.cuda_stream) b.s = (cudaStream_t)opt.cuda_stream;
     else {
@@ -1599,11 +1655,17 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     // its stage events can be read before the next chunk records them again.
     // Every curve's peak records stay on the device until the end.
     const bool copy_out = !b.timing && dchi2 && !out_dev;
-    if (copy_out) {
-        bool good = cudaStreamCreateWithFlags(&b.cs2, cudaStreamNonBlocking) == cudaSuccess;
+    {
+        bool good = true;
+        if (copy_out) {
+            good = cudaStreamCreateWithFlags(&b.cs2, cudaStreamNonBlocking) == cudaSuccess;
+            for (int i = 0; i < 2 && good; ++i)
+                good = cudaEventCreateWithFlags(&b.ev_ready[i], cudaEventDisableTiming) == cudaSuccess &&
+                       cudaEventCreateWithFlags(&b.ev_copied[i], cudaEventDisableTiming) == cudaSuccess;
+        }
         for (int i = 0; i < 2 && good; ++i)
-            good = cudaEventCreateWithFlags(&b.ev_ready[i], cudaEventDisableTiming) == cudaSuccess &&
-                   cudaEventCreateWithFlags(&b.ev_copied[i], cudaEventDisableTiming) == cudaSuccess;
+            good = cudaEventCreateWithFlags(&b.ev_graph[i], cudaEventDisableTiming) == cudaSuccess &&
+                   cudaEventCreateWithFlags(&b.ev_tab[i], cudaEventDisableTiming) == cudaSuccess;
         if (!good) {
             cudaGetLastError();
             b.free_all();
@@ -1611,9 +1673,18 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             return FC2_ERR_CUDA;
         }
     }
+    // pinned staging of the chunk tables (two halves) and mapped memory for the
+    // moments of every curve and the status word
     {
-        const size_t bytes = (size_t)mx_nc * SC_COUNT * 8 + 64;
-        if (cudaHostAlloc((void**)&b.hmap, bytes, cudaHostAllocMapped) != cudaSuccess ||
+        size_t half = 0;
+        for (const Chunk& ch : chunks) {
+            const size_t nc = (size_t)(ch.c1 - ch.c0), S = (size_t)ch.S;
+            half = std::max(half, (nc + 1) * 8 + nc * SC_COUNT * 8 + nc * 72 + S * 44 + 16 * 64);
+        }
+        b.stage_half = (half + 255) & ~(size_t)255;
+        const size_t mbytes = (size_t)C * SC_COUNT * 8 + 64;
+        if (cudaHostAlloc((void**)&b.stage, 2 * b.stage_half, cudaHostAllocDefault) != cudaSuccess ||
+            cudaHostAlloc((void**)&b.hmap, mbytes, cudaHostAllocMapped) != cudaSuccess ||
             cudaHostGetDevicePointer((void**)&b.hmap_dev, b.hmap, 0) != cudaSuccess) {
             cudaGetLastError();
             b.free_all();
@@ -1627,6 +1698,57 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     const size_t nchunks = chunks.size();
     std::vector<int32_t> hist(nchunks * 16, 0);
     size_t launched = 0;  // chunks whose graph was launched
+    cudaError_t e = cudaSuccess;
+    auto ok = [&](cudaError_t r) { if (e == cudaSuccess) e = r; return e == cudaSuccess; };
+
+    // ---- inputs on the device (host inputs copied once), then the moments of
+    // every curve in one launch and one wait
+    const int64_t base0 = offsets[0], ntot_all = offsets[C] - base0;
+    const double *tall = t + base0, *xall = x + base0, *sgall = sigma + base0;
+    {
+        const auto tpa = now();
+        if (!opt.inputs_on_device) {
+            ok(need(&b.t, &b.ct, (size_t)ntot_all, s)) && ok(need(&b.x, &b.cx, (size_t)ntot_all, s)) &&
+                ok(need(&b.sg, &b.csg, (size_t)ntot_all, s)) &&
+                ok(cudaMemcpyAsync(b.t, t + base0, ntot_all * 8, cudaMemcpyHostToDevice, s)) &&
+                ok(cudaMemcpyAsync(b.x, x + base0, ntot_all * 8, cudaMemcpyHostToDevice, s)) &&
+                ok(cudaMemcpyAsync(b.sg, sigma + base0, ntot_all * 8, cudaMemcpyHostToDevice, s));
+            tall = b.t; xall = b.x; sgall = b.sg;
+        }
+        std::vector<int64_t> goffv(C + 1);
+        for (int64_t c = 0; c <= C; ++c) goffv[c] = offsets[c] - base0;
+        ok(need(&b.goff, &b.cgoff, (size_t)C + 1, s)) &&
+            ok(need(&b.scal_all, &b.cscal_all, (size_t)C * SC_COUNT, s)) &&
+            ok(need(&b.counts, &b.ccnt, 16, s)) &&
+            ok(cudaMemcpyAsync(b.goff, goffv.data(), (C + 1) * 8, cudaMemcpyHostToDevice, s)) &&
+            ok(cudaMemsetAsync(b.counts, 0, 16 * sizeof(int32_t), s));
+        if (shared && e == cudaSuccess)
+            for (const Chunk& ch : chunks) {
+                const int nc = (int)(ch.c1 - ch.c0);
+                if (nc < 2) continue;
+                const int64_t n0 = offsets[ch.c0 + 1] - offsets[ch.c0];
+                k_shared_check<<<dim3((unsigned)((n0 + 255) / 256), (unsigned)(nc - 1)), 256, 0, s>>>(
+                    tall, sgall, b.goff + ch.c0, nc, b.counts + 8);
+            }
+        ok(cudaGetLastError());
+        if (e == cudaSuccess) ok(launch_moments(tall, xall, sgall, b.goff, C, 0, b.scal_all, b.counts + 8, s));
+        const int64_t nsw = C * SC_COUNT * 2;  // 32-bit words of the moments
+        if (e == cudaSuccess) {
+            k_copy_words<<<(unsigned)std::min<int64_t>((nsw + 255) / 256, 4096), 256, 0, s>>>(
+                (const uint32_t*)b.scal_all, (uint32_t*)b.hmap_dev, nsw);
+            k_copy_words<<<1, 32, 0, s>>>((const uint32_t*)(b.counts + 8),
+                                          (uint32_t*)(b.hmap_dev + 4 * nsw), 1);
+            ok(cudaGetLastError());
+        }
+        ok(cudaStreamSynchronize(s));
+        int32_t status = 0;
+        if (e == cudaSuccess) std::memcpy(&status, b.hmap + 4 * nsw, 4);
+        if (e != cudaSuccess) st = map_cuda(e);
+        else if (status) st = (fc2_status)status;
+        b.phase_ms[2] += ms_since(tpa, now());
+    }
+    const double* scal_host = (const double*)b.hmap;
+
     for (size_t ci = 0; ci < nchunks; ++ci) {
         const Chunk& ch = chunks[ci];
         const int slot = (int)(ci & 1);
@@ -1650,32 +1772,22 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             p.fft_family = fft_family_of(opt.fft_kernel);
             release(p.d_twlo, s); release(p.d_twhi, s); release(p.d_twst, s); release(p.d_dec, s);
             const int sh = (p.logM + 1) / 2;
-            cudaError_t e = pool_alloc((void**)&p.d_twlo, (size_t)(1ll << sh) * csz, s);
-            if (e == cudaSuccess) e = pool_alloc((void**)&p.d_twhi, (size_t)(M >> sh) * csz, s);
-            if (e == cudaSuccess) e = pool_alloc((void**)&p.d_twst, (size_t)(8 * 4096 + 256) * csz, s);
-            if (e == cudaSuccess) e = pool_alloc((void**)&p.d_dec, (size_t)N * tsz, s);
-            if (e == cudaSuccess) e = need(&b.red, &b.cred, 8192, s);
+            cudaError_t ea = pool_alloc((void**)&p.d_twlo, (size_t)(1ll << sh) * csz, s);
+            if (ea == cudaSuccess) ea = pool_alloc((void**)&p.d_twhi, (size_t)(M >> sh) * csz, s);
+            if (ea == cudaSuccess) ea = pool_alloc((void**)&p.d_twst, (size_t)(8 * 4096 + 256) * csz, s);
+            if (ea == cudaSuccess) ea = pool_alloc((void**)&p.d_dec, (size_t)N * tsz, s);
+            if (ea == cudaSuccess) ea = need(&b.red, &b.cred, 8192, s);
             p.d_red = b.red;
-            if (e == cudaSuccess) e = init_twiddles(&p, s);
-            if (e == cudaSuccess) e = init_deconv(&p, s);
-            if (e != cudaSuccess) { st = map_cuda(e); break; }
+            if (ea == cudaSuccess) ea = init_twiddles(&p, s);
+            if (ea == cudaSuccess) ea = init_deconv(&p, s);
+            if (ea != cudaSuccess) { st = map_cuda(ea); break; }
             curM = M;
             curN = N;
         }
-        // ---- buffers
+        // ---- buffers (allocated by the first chunk at the largest size any needs)
         const auto tpb = now();
-        const int64_t base = offsets[c0];
-        cudaError_t e = cudaSuccess;
-        auto ok = [&](cudaError_t r) { if (e == cudaSuccess) e = r; return e == cudaSuccess; };
-        if (opt.inputs_on_device) {
-            b.t = (double*)(t + base); b.x = (double*)(x + base); b.sg = (double*)(sigma + base);
-        } else {
-            ok(need(&b.t, &b.ct, (size_t)mx.ntot, s)) && ok(need(&b.x, &b.cx, (size_t)mx.ntot, s)) &&
-                ok(need(&b.sg, &b.csg, (size_t)mx.ntot, s)) &&
-                ok(cudaMemcpyAsync(b.t, t + base, ntot * 8, cudaMemcpyHostToDevice, s)) &&
-                ok(cudaMemcpyAsync(b.x, x + base, ntot * 8, cudaMemcpyHostToDevice, s)) &&
-                ok(cudaMemcpyAsync(b.sg, sigma + base, ntot * 8, cudaMemcpyHostToDevice, s));
-        }
+        const int64_t base = offsets[c0] - base0;
+        b.tc = tall + base; b.xc = xall + base; b.sgc = sgall + base;
         const int64_t nrec = (int64_t)nc * K;
         const int64_t out_chunk = ch.out;
         const size_t mxs = (size_t)mx.S, mxn = (size_t)mx.ntot, mxc = (size_t)mx_nc;
@@ -1708,7 +1820,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
                     std::max<size_t>({b.cl2, b.cl3, b.cl4, (size_t)std::max<int64_t>(mx_nrec, 1)}), s)) &&
             ok(need(&b.items, &b.citems, (size_t)BX_ITEMS, s)) &&
             ok(need(&b.part, &b.cpart, (size_t)BX_ITEMS * 6 * BHM, s)) &&
-            ok(need(&b.counts, &b.ccnt, 16, s)) && ok(need(&b.curves, &b.ccurves, mxc, s)) &&
+            ok(need(&b.curves, &b.ccurves, mxc, s)) &&
             ok(need(&b.tops, &b.ctops, mx_tops, s)) &&
             ok(need(&b.bbest, &b.cbbest, std::max<size_t>(mx_tops / std::max(K, 1), 1), s)) &&
             ok(need(&b.theta, &b.ctheta, mxc, s)) &&
@@ -1721,37 +1833,12 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         else if (copy_out && slot) { if (ok(need(&b.out2, &b.cout2, (size_t)mx.out, s))) out = b.out2; }
         else if (ok(need(&b.out, &b.cout, (size_t)mx.out, s))) out = b.out;
         if (e != cudaSuccess) { st = map_cuda(e); break; }
-        // ---- moments per curve, then host-side geometry
-        const auto tp0 = now();
-        b.phase_ms[1] += ms_since(tpb, tp0);
-        std::vector<int64_t> offl(nc + 1);
-        for (int c = 0; c <= nc; ++c) offl[c] = offsets[c0 + c] - base;
-        ok(cudaMemcpyAsync(b.off, offl.data(), (nc + 1) * 8, cudaMemcpyHostToDevice, s));
-        ok(cudaMemsetAsync(b.counts, 0, 16 * sizeof(int32_t), s));
-        if (shared && nc > 1) {
-            const int64_t n0 = offl[1] - offl[0];
-            k_shared_check<<<dim3((unsigned)((n0 + 255) / 256), (unsigned)(nc - 1)), 256, 0, s>>>(
-                b.t, b.sg, b.off, nc, b.counts + 8);
-            ok(cudaGetLastError());
-        }
-        ok(launch_moments(b.t, b.x, b.sg, b.off, nc, 0, b.scal, b.counts + 8, s));
-        std::vector<double> scal((size_t)nc * SC_COUNT);
-        int32_t status = 0;
-        const int64_t nsw = (int64_t)scal.size() * 2;  // 32-bit words of the moments
-        k_copy_words<<<(unsigned)std::min<int64_t>((nsw + 255) / 256, 1024), 256, 0, s>>>(
-            (const uint32_t*)b.scal, (uint32_t*)b.hmap_dev, nsw);
-        k_copy_words<<<1, 32, 0, s>>>((const uint32_t*)(b.counts + 8),
-                                      (uint32_t*)(b.hmap_dev + 8 * nsw / 2), 1);
-        ok(cudaGetLastError());
-        ok(cudaStreamSynchronize(s));
-        if (e == cudaSuccess) {
-            std::memcpy(scal.data(), b.hmap, scal.size() * 8);
-            std::memcpy(&status, b.hmap + scal.size() * 8, 4);
-        }
         const auto tp1 = now();
-        b.phase_ms[2] += ms_since(tp0, tp1);
-        if (e != cudaSuccess) { st = map_cuda(e); break; }
-        if (status) { st = (fc2_status)status; break; }
+        b.phase_ms[1] += ms_since(tpb, tp1);
+        // ---- host-side layout from the curves' moments
+        std::vector<int64_t> offl(nc + 1);
+        for (int c = 0; c <= nc; ++c) offl[c] = offsets[c0 + c] - offsets[c0];
+        std::vector<double> scal(scal_host + (size_t)c0 * SC_COUNT, scal_host + (size_t)c1 * SC_COUNT);
         std::vector<int> Hv(nc), slot0(nc), scur, sk, skind, qownv(nc), pslotv(nc);
         std::vector<double> fminv(nc), dfv(nc);
         std::vector<int64_t> oo(nc), ssoff, sn, Lv;
@@ -1853,32 +1940,52 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             hoff[h] = (int)curves_flat.size();
             curves_flat.insert(curves_flat.end(), hg[h].begin(), hg[h].end());
         }
-        ok(cudaMemcpyAsync(b.scal, scal.data(), scal.size() * 8, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.H, Hv.data(), nc * 4, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.slot0, slot0.data(), nc * 4, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.qown, qownv.data(), nc * 4, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.pslot0, pslotv.data(), nc * 4, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.fmin, fminv.data(), nc * 8, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.df, dfv.data(), nc * 8, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.out_off, oo.data(), nc * 8, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.sq, sqv.data(), nc * 4, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.sp, spv.data(), nc * 4, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.s1n, s1v.data(), nc * 4, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.chi0f, c0v.data(), nc * 4, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.slot_cur, scur.data(), S * 4, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.slot_k, sk.data(), S * 4, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.slot_kind, skind.data(), S * 4, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.slot_soff, ssoff.data(), S * 8, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.slot_n, sn.data(), S * 8, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.L, Lv.data(), S * 8, cudaMemcpyHostToDevice, s));
-        ok(cudaMemcpyAsync(b.curves, curves_flat.data(), nc * 4, cudaMemcpyHostToDevice, s));
+        // ---- the tables, through this chunk's half of the pinned staging (free
+        // once the copies of the chunk two before are done), in stream order
+        // after the previous chunk's launches
+        if (b.tab_pending[slot]) {
+            ok(cudaEventSynchronize(b.ev_tab[slot]));
+            b.tab_pending[slot] = false;
+        }
+        char* stg = b.stage + (size_t)slot * b.stage_half;
+        size_t sused = 0;
+        auto put = [&](void* dst, const void* src, size_t bytes) {
+            if (bytes == 0 || e != cudaSuccess) return;
+            if (sused + bytes > b.stage_half) { e = cudaErrorInvalidValue; return; }
+            std::memcpy(stg + sused, src, bytes);
+            ok(cudaMemcpyAsync(dst, stg + sused, bytes, cudaMemcpyHostToDevice, s));
+            sused += (bytes + 15) & ~(size_t)15;
+        };
+        put(b.off, offl.data(), (nc + 1) * 8);
+        put(b.scal, scal.data(), scal.size() * 8);
+        put(b.H, Hv.data(), nc * 4);
+        put(b.slot0, slot0.data(), nc * 4);
+        put(b.qown, qownv.data(), nc * 4);
+        put(b.pslot0, pslotv.data(), nc * 4);
+        put(b.fmin, fminv.data(), nc * 8);
+        put(b.df, dfv.data(), nc * 8);
+        put(b.out_off, oo.data(), nc * 8);
+        put(b.sq, sqv.data(), nc * 4);
+        put(b.sp, spv.data(), nc * 4);
+        put(b.s1n, s1v.data(), nc * 4);
+        put(b.chi0f, c0v.data(), nc * 4);
+        put(b.slot_cur, scur.data(), S * 4);
+        put(b.slot_k, sk.data(), S * 4);
+        put(b.slot_kind, skind.data(), S * 4);
+        put(b.slot_soff, ssoff.data(), S * 8);
+        put(b.slot_n, sn.data(), S * 8);
+        put(b.L, Lv.data(), S * 8);
+        put(b.curves, curves_flat.data(), nc * 4);
+        ok(cudaEventRecord(b.ev_tab[slot], s));
+        b.tab_pending[slot] = true;
+        ok(cudaMemsetAsync(b.counts, 0, 16 * sizeof(int32_t), s));
         // time order within each curve
         k_iota_plus<<<(unsigned)((ntot + 255) / 256), 256, 0, s>>>(b.perm, ntot, 0);
         if (unsorted)
             for (int c = 0; c < nc; ++c)
                 if (scal[(size_t)c * SC_COUNT + SC_SORTED] == 0.0) {
                     const int64_t n = offl[c + 1] - offl[c];
-                    ok(sort_by_time(b.t + offl[c], n, b.perm + offl[c], b.grid1, b.cg1, s));
+                    ok(sort_by_time(b.tc + offl[c], n, b.perm + offl[c], b.grid1, b.cg1, s));
                     k_add_base<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(b.perm + offl[c], n, offl[c]);
                 }
         // chunk plan fields for the shared launchers
@@ -1901,7 +2008,10 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             if (e == cudaSuccess) {
                 store_tune(tkey, cfg);
                 fill_L(std::max(M >> cfg.fft.rs[0], (int64_t)cfg.spread_tile));
-                ok(cudaMemcpyAsync(b.L, Lv.data(), S * 8, cudaMemcpyHostToDevice, s));
+                // (the tuning runs waited for every copy of this half)
+                put(b.L, Lv.data(), S * 8);
+                ok(cudaMemsetAsync(b.counts, 0, 16 * sizeof(int32_t), s));
+                ok(cudaEventRecord(b.ev_tab[slot], s));
             }
             b.tune_ms += ms_since(tt0, now());
         }
@@ -1914,18 +2024,26 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             ok(cudaStreamWaitEvent(s, b.ev_copied[slot], 0));
             b.copied_pending[slot] = false;
         }
+        // the executable graph of the chunk two before must have finished
+        if (b.graph_pending[slot]) {
+            ok(cudaEventSynchronize(b.ev_graph[slot]));
+            b.graph_pending[slot] = false;
+        }
         const auto tp2 = now();
         b.phase_ms[3] += ms_since(tp1, tp2);
-        e = launch_as_graph(b, [&]() {
-            return fp64 ? chunk_launches<double>(b, nc, ntot, nmax, (int)S, hg, hoff, K, out, nrec,
-                                                 tau_drop)
-                        : chunk_launches<float>(b, nc, ntot, nmax, (int)S, hg, hoff, K, out, nrec,
-                                                tau_drop);
-        });
+        if (e == cudaSuccess)
+            e = launch_as_graph(b, b.gexec[slot], [&]() {
+                return fp64 ? chunk_launches<double>(b, nc, ntot, nmax, (int)S, hg, hoff, K, out, nrec,
+                                                     tau_drop)
+                            : chunk_launches<float>(b, nc, ntot, nmax, (int)S, hg, hoff, K, out, nrec,
+                                                    tau_drop);
+            });
         const auto tp3 = now();
         b.phase_ms[4] += ms_since(tp2, tp3);
         if (e != cudaSuccess) { st = map_cuda(e); break; }
         ++launched;
+        ok(cudaEventRecord(b.ev_graph[slot], s));
+        b.graph_pending[slot] = true;
         // ---- results: the chunk's counters kept on the device (read once at the
         // end), its outputs copied to the host
         k_copy_words<<<1, 32, 0, s>>>((const uint32_t*)b.counts, (uint32_t*)(b.cnt_hist + 16 * ci), 16);
@@ -1941,17 +2059,13 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
                                    cudaMemcpyDeviceToHost, b.cs2));
             ok(cudaEventRecord(b.ev_copied[slot], b.cs2));
             b.copied_pending[slot] = true;
-            b.phase_ms[5] += ms_since(tp3, now());
-            if (e != cudaSuccess) { st = map_cuda(e); break; }
-            out_global += out_chunk;
-            continue;
+        } else if (dchi2 && !out_dev) {
+            ok(cudaMemcpyAsync(dchi2 + out_global, out, out_chunk * sizeof(float), cudaMemcpyDeviceToHost,
+                               s));
         }
-        if (dchi2 && !out_dev)
-            ok(cudaMemcpyAsync(dchi2 + out_global, out, out_chunk * sizeof(float), cudaMemcpyDeviceToHost, s));
-        ok(cudaStreamSynchronize(s));
-        b.phase_ms[5] += ms_since(tp3, now());
-        if (e != cudaSuccess) { st = map_cuda(e); break; }
         if (b.timing) {
+            // stage events are re-recorded by the next chunk: read them now
+            ok(cudaStreamSynchronize(s));
             for (int i = 0; i < 5; ++i) {
                 float ms = 0.f;
                 if (cudaEventElapsedTime(&ms, b.ev[i], b.ev[i + 1]) == cudaSuccess) b.stage_ms[i] += ms;
@@ -1959,12 +2073,8 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             }
             for (int c = 0; c < nc; ++c) b.fft_alg_bytes += 3.0 * Hv[c] * (double)N * (double)csz;
         }
-        // without the copy stream every chunk is checked before the next starts
-        int32_t cnts[16] = {0};
-        if (ok(cudaMemcpy(cnts, b.cnt_hist + 16 * ci, 64, cudaMemcpyDeviceToHost)))
-            std::memcpy(&hist[16 * ci], cnts, 64);
+        b.phase_ms[5] += ms_since(tp3, now());
         if (e != cudaSuccess) { st = map_cuda(e); break; }
-        if (cnts[8] != 0) { st = (fc2_status)cnts[8]; break; }
         out_global += out_chunk;
     }
     const auto t_loop_end = now();

@@ -146,3 +146,38 @@ def test_double_float_phasor_accuracy(fc2):
     err = max(np.max(np.abs(o[:, 0] + o[:, 1] - ref_re)), np.max(np.abs(o[:, 2] + o[:, 3] - ref_im)))
     print("phasor max abs error", float(err), "= 2^%.1f" % np.log2(float(err)))
     assert err <= 2.0 ** -45
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_exact_aliases_at_30_min_cadence(fc2, oracle_mod, prec):
+    """The large curve's 30-minute-cadence variant (n ~ 6.7e4 over 4 years,
+    H = 8): every time is a whole number of 1/48 d (up to the rounding of the
+    times), so sin(2 pi h f t) vanishes on all samples wherever 2 h f / 48 is
+    an integer -- f = 3 /d for h = 8, f = 6 /d for h = 4, ... -- and cosines
+    equal the constant where it is even: the design matrix is rank-deficient
+    there (the rank-drop rule must engage).  Those bins (on the
+    trial grid: f_min = df = 24 / 2^22) with windows around them, the first
+    bins and random bins, against the oracle."""
+    c = synth.large_curve(cadence_min=30.0, N=1 << 22)
+    # aliases f = 24 m / h that fall on a trial frequency (j + 1) df = j' 24 / 2^22
+    alias_f = sorted({24.0 * m / h for h in range(1, 9) for m in range(1, 9)
+                      if 24.0 * m / h <= 23.9 and (m << 22) % h == 0})
+    centres = [int(round(f / c.df)) - 1 for f in alias_f]
+    assert len(centres) == 7  # 3, 6, .., 21 /d
+    assert all(abs((j + 1) * c.df - f) < 1e-9 for j, f in zip(centres, alias_f))
+    with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, prec) as p:
+        d, _, _, chi0 = p.execute()
+        counts = p.counts
+    bins = sample_bins(c.N, 60, 13, windows=centres, half=2)
+    bins = np.unique(np.concatenate([bins, np.arange(0, 16)]))
+    ref, piv = oracle_mod.dchi2_bins(c.t, c.x, c.sigma, c.H, c.f_min, c.df, bins,
+                                     with_pivots=True)
+    # some of them are rank decisions for the oracle too (at f = 12 /d the
+    # fourth and eighth cosines equal the constant on every sample; a sine
+    # that vanishes is a near-zero column, which a pivot relative to the
+    # column's own norm does not flag)
+    at = np.searchsorted(bins, centres)
+    assert np.any(piv[at, -1] < 1e-8), piv[at, -1]
+    r = compare(d[:, bins].T, ref, piv, chi0)
+    print(prec, counts, r)
+    assert r["ok"], r
