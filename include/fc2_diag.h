@@ -179,6 +179,14 @@ void fc2_debug_batch_config(int64_t* out13);
  * Process-wide; for tests and diagnostics. */
 void fc2_debug_batch_force(int spread_tile, int asm_nt, int bx_ch, int fft_group);
 
+/* Fixed transform plan of batched calls that do not tune (as
+ * fc2_debug_batch_force): log2 radices rs[0..n), n <= 4, first pass first,
+ * and the float kernel family (0 radix-16 stages in shared memory, 1 two
+ * register stages, 2 bulk copies).  It is used only for grids whose length it
+ * fits and where it is one of the autotuner's candidates; n = 0 clears it.
+ * Process-wide; for tests. */
+void fc2_debug_batch_force_plan(const int* rs, int n, int family);
+
 /* Empty this process's tuning table of the batched path; the cache file is
  * read again at the next lookup. */
 void fc2_debug_batch_forget_tuning(void);

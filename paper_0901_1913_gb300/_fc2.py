@@ -172,6 +172,8 @@ def load():
         lib.fc2_debug_batch_config.restype = None
         lib.fc2_debug_batch_force.argtypes = [i32, i32, i32, i32]
         lib.fc2_debug_batch_force.restype = None
+        lib.fc2_debug_batch_force_plan.argtypes = [_P, i32, i32]
+        lib.fc2_debug_batch_force_plan.restype = None
         lib.fc2_debug_batch_forget_tuning.argtypes = []
         lib.fc2_debug_batch_forget_tuning.restype = None
         _lib = lib
@@ -402,6 +404,14 @@ def batch_force(spread_tile=0, assemble_block=0, exact_item_samples=0, transform
     "fixed" or a transform family requested); zeros keep the defaults."""
     load().fc2_debug_batch_force(int(spread_tile), int(assemble_block), int(exact_item_samples),
                                  int(transform_group))
+
+
+def batch_force_plan(radices=(), family=1):
+    """Fixed transform plan (log2 radices, first pass first) and float kernel
+    family (0 radix-16 shared memory, 1 register stages, 2 bulk copies) of
+    batched calls that do not tune; () clears it."""
+    r = np.ascontiguousarray(radices, dtype=np.int32)
+    load().fc2_debug_batch_force_plan(r.ctypes.data if r.size else None, int(r.size), int(family))
 
 
 def batch_forget_tuning():

@@ -887,6 +887,15 @@ void fc2_debug_batch_force(int spread_tile, int asm_nt, int bx_ch, int fft_group
     fc2::force_batch_config(spread_tile, asm_nt, bx_ch, fft_group);
 }
 
+/* Fixed transform plan for batched calls that do not tune: log2 radices
+ * rs[0..n) and kernel family (0 radix-16 shared memory, 1 register stages,
+ * 2 bulk copies); used only when it is one of the tuner's candidates for the
+ * grid length; n = 0 clears it. */
+void fc2_debug_batch_force_plan(const int* rs, int n, int family) {
+    if (n < 0 || n > 4 || (n > 0 && !rs)) return;
+    fc2::force_batch_plan(rs, n, family);
+}
+
 /* Forget the batched path's tuning table of this process (the cache file is
  * read again at the next lookup). */
 void fc2_debug_batch_forget_tuning(void) { fc2::forget_batch_tuning(); }

@@ -231,6 +231,7 @@ cudaError_t set_fft_choice(fc2_plan_s* p, const FftChoice& c, cudaStream_t s);
 // k_batch.cu: the batched path's tuning table and fixed configuration
 void forget_batch_tuning();
 void force_batch_config(int spread_tile, int asm_nt, int bx_ch, int fft_group);
+void force_batch_plan(const int* rs, int n, int family);
 cudaError_t pool_alloc(void** ptr, size_t bytes, cudaStream_t s);  // library device pool
 void drop_deconv_cache(int dev);  // k_fft.cu: cached deconvolution tables of a device
 cudaError_t launch_fft(fc2_plan_s* p, cudaStream_t s);

@@ -1402,6 +1402,12 @@ void forget_batch_tuning() {
 // every candidate must give the same results within the error bounds); zero
 // fields keep the defaults.
 static int g_force_tile = 0, g_force_asm = 0, g_force_ch = 0, g_force_grp = 0;
+static std::vector<int> g_force_rs;  // forced transform plan (empty: none)
+static int g_force_fam = -1;
+void force_batch_plan(const int* rs, int n, int family) {
+    g_force_rs.assign(rs, rs + (n > 0 ? n : 0));
+    g_force_fam = family;
+}
 void force_batch_config(int spread_tile, int asm_nt, int bx_ch, int fft_group) {
     g_force_tile = spread_tile;
     g_force_asm = asm_nt;
@@ -1866,6 +1872,10 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
             if (g_force_asm == 256 && !fp64) cfg.asm_nt = 256;
             if (g_force_ch == 1024 || g_force_ch == 4096) cfg.bx_ch = g_force_ch;
             if (g_force_grp == 8 || g_force_grp == 16 || g_force_grp == 32) cfg.fft_group = g_force_grp;
+            if (!g_force_rs.empty()) {
+                const FftChoice fc{g_force_rs, g_force_fam};
+                if (fft_choice_valid(p.logM, fp64, fc)) cfg.fft = fc;
+            }
         } else if (tune_mode == 1 && lookup_tune(tkey, &cfg)) {
             source = 1;
         } else {

@@ -1260,8 +1260,9 @@ static bool fft_plan_valid(int logM, bool fp64, int family, const std::vector<in
 
 // ------------------------------------------------------ transform autotuner
 // Candidate pass plans for a length-2^logM transform: the balanced split into
-// the fewest passes (the fixed planner's choice) and, when every radix stays
-// at 2^8 or above, the balanced split into one pass more; float plans are
+// the fewest passes (the fixed planner's choice), for two passes of unequal
+// radix also the smaller radix first, and, when every radix stays at 2^8 or
+// above, the balanced split into one pass more; float plans are
 // tried with both kernel families.  Only pass shapes the fixed planner also
 // produces for some length are searched: a wider search (unbalanced splits,
 // small radices in three-pass plans) is not covered by the tests.  Each
@@ -1289,7 +1290,10 @@ static std::vector<std::vector<int>> fft_candidates(int logM, int maxr) {
         return out;
     }
     const int P = (logM + maxr - 1) / maxr;
-    out.push_back(balanced_split(logM, P));
+    const std::vector<int> bal = balanced_split(logM, P);
+    out.push_back(bal);
+    // the same two radices in the other order (the smaller first)
+    if (P == 2 && bal[0] != bal[1] && bal[1] >= 8) out.push_back({bal[1], bal[0]});
     const std::vector<int> more = balanced_split(logM, P + 1);
     if (more.back() >= 8) out.push_back(more);
     return out;

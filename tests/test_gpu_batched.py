@@ -289,3 +289,34 @@ def test_autotuner_table_and_cache_file(fc2, oracle_mod, tmp_path, monkeypatch):
         _, _, chi0, _ = oracle_mod.moments(cur.x, cur.sigma)
         r = compare(block[:, bins].T.astype(np.float64), ref, piv, chi0)
         assert r["ok"], (c, r)
+
+
+@pytest.mark.parametrize("family", [1, 2, 0])
+def test_reversed_two_pass_plan_matches_oracle(fc2, oracle_mod, family):
+    """The autotuner's other two-pass plan for the survey's 2^19-point grids:
+    radix 2^9 first, then 2^10 (the fixed plan takes 2^10 first), forced with
+    each float kernel family: the same Delta chi^2 as the fixed plan up to
+    float rounding, and sampled bins against the oracle."""
+    b = small_survey(C=6, N=1 << 18, seed=31)
+    args = (b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df, b.N, 2, "mixed")
+    ref, _, _ = fc2.execute_batched(*args, autotune="fixed")
+    fc2.batch_force_plan((9, 10), family)
+    try:
+        out, _, st = fc2.execute_batched(*args, autotune="fixed")
+    finally:
+        fc2.batch_force_plan(())
+    assert st["config"]["fft_log2_radices"] == [9, 10], st["config"]
+    pos = 0
+    for c in range(b.C):
+        cur = b.curve(c)
+        block = out[pos:pos + cur.H * cur.N].reshape(cur.H, cur.N)
+        rblock = ref[pos:pos + cur.H * cur.N].reshape(cur.H, cur.N)
+        pos += cur.H * cur.N
+        _, _, chi0, _ = oracle_mod.moments(cur.x, cur.sigma)
+        assert np.max(np.abs(block - rblock)) <= 2e-5 * chi0, (family, c)
+        bins = sample_bins(cur.N, 60, c, windows=[int(np.argmax(block[-1]))], half=3)
+        bins = np.unique(np.concatenate([bins, np.arange(0, 8)]))
+        oref, piv = oracle_mod.dchi2_bins(cur.t, cur.x, cur.sigma, cur.H, cur.f_min, cur.df, bins,
+                                          with_pivots=True)
+        r = compare(block[:, bins].T.astype(np.float64), oref, piv, chi0)
+        assert r["ok"], (family, c, r)
