@@ -905,6 +905,22 @@ FC2_D bool mbar_wait_bounded(uint64_t* m, unsigned parity, long long cycles) {
     return true;
 }
 
+// The 16-point transform of SmallDFT<T, 16> where only outputs 0..3 and
+// 12..15 are wanted (a last pass that keeps the centred half of the modes):
+// the same operations for those outputs, the other eight not formed.
+template <typename T>
+FC2_D void dft16_centred(cpx<T>* v) {
+    cpx<T> e[8], o[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { e[i] = v[2 * i]; o[i] = v[2 * i + 1]; }
+    SmallDFT<T, 8>::run(e);
+    SmallDFT<T, 8>::run(o);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = add(e[k], k == 0 ? o[0] : mul(o[k], root16<T>(k)));
+#pragma unroll
+    for (int k = 4; k < 8; ++k) v[k + 8] = sub(e[k], k == 4 ? mul_i(o[4]) : mul(o[k], root16<T>(k)));
+}
+
 template <int LOGR>
 constexpr size_t pass_tma_smem() {
     return (size_t)(2 * (1 << PT_LOGE) + phys((1 << PT_LOGE) - 1) + 1 + stage_tw_size(LOGR)) *
@@ -1093,13 +1109,25 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
         for (int k = 0; k < 16; ++k) v[k] = wk[phys((pp + k * NSL) * J + jj)];
 #pragma unroll
         for (int k = 1; k < 16; ++k) v[k] = mul(v[k], st[TOFF_L + (k - 1) * NSL + pp]);
-        SmallDFT<T, 16>::run(v);
+        // a last pass keeping the centred half of the modes (N = M / 2) only
+        // needs elements k < 4 (o < M / 4) and k >= 12 (o >= 3 M / 4): the
+        // last stage's step is M / 16
+        const bool centred = a.last && g >= a.npk && 2 * a.N == M && 2 * a.hN == a.N &&
+                             16 * (NSL << logNs) == M;
+        if (centred) dft16_centred(v);
+        else SmallDFT<T, 16>::run(v);
         __syncthreads();  // every thread has read the work buffer
         // output row of element k: pp + k NSL
         if (a.last) {
             const int o0 = j0 + jj + (pp << logNs);
             const int step = NSL << logNs;
-            if (g < a.npk) {
+            if (centred) {
+                cpx<T>* spec = out + (int64_t)(a.npk + g) * a.N;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) spec[o0 + k * step + a.hN] = v[k];
+#pragma unroll
+                for (int k = 12; k < 16; ++k) spec[o0 + k * step - (M - a.hN)] = v[k];
+            } else if (g < a.npk) {
                 cpx<T>* plus = out + (int64_t)(2 * g) * a.N;
                 cpx<T>* minus = plus + a.N;
 #pragma unroll
