@@ -35,7 +35,7 @@ class Options(ctypes.Structure):
 GRIDDING = {"kernel": 0, "paper": 1}
 
 # fc2_options.fft_kernel values
-FFT_KERNELS = {"default": 0, "r64": 1, "r16": 2, "bulk": 3}
+FFT_KERNELS = {"default": 0, "r64": 1, "r16": 2, "bulk": 3, "r32": 4}
 
 
 class Best(ctypes.Structure):
@@ -382,7 +382,8 @@ BATCH_STAGES = ("spread", "fft", "assemble", "fixup", "peaks")
 # miss), "retune" tunes anew, "fixed" keeps the default configuration
 AUTOTUNE = {"fixed": -1, "table": 0, "retune": 1}
 FFT_FAMILY_NAMES = {0: "radix-16 stages in shared memory", 1: "two register stages",
-                    2: "radix-16 stages fed by bulk copies"}
+                    2: "radix-16 stages fed by bulk copies",
+                    3: "two register stages of radix 32 (512 threads)"}
 
 
 def batch_config():

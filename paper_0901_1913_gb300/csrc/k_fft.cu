@@ -630,11 +630,13 @@ FC2_D void prefetch_l2_bulk(const void* p, unsigned bytes) {
 }
 FC2_D void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
 
+// Stage-B twiddles of the register passes: entry (k - 1) QA + pm = w_R^{k pm},
+// k = 1 .. RB - 1, pm < QA = R / RB (RB = 2^LRB).
 template <typename T>
-__global__ void k_init_tw64(cpx<T>* tw, int LOGR) {
-    const int QA = 1 << (LOGR - 6);
+__global__ void k_init_tw64(cpx<T>* tw, int LOGR, int LRB) {
+    const int QA = 1 << (LOGR - LRB);
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 63 * QA) return;
+    if (i >= ((1 << LRB) - 1) * QA) return;
     const int k = i / QA + 1, pm = i % QA;
     double sn, cn;
     sincospi(2.0 * (double)(k * pm) / (double)(1 << LOGR), &sn, &cn);
@@ -643,20 +645,24 @@ __global__ void k_init_tw64(cpx<T>* tw, int LOGR) {
 
 constexpr int P64_NT = 256;                 // threads of a radix-64 pass CTA (one CTA per SM)
 constexpr int P64_LOGE = 14;                // log2 of its tile: 64 elements per thread
+constexpr int P32_NT = 512;                 // threads of the radix-32 variant (same tile)
 
-template <int LOGR, int LOGJ>
-__global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __restrict__ in,
-                                                       cpx<float>* __restrict__ out, PassArgs a,
-                                                       const int64_t* __restrict__ Lg,
-                                                       const cpx<float>* __restrict__ twlo,
-                                                       const cpx<float>* __restrict__ twhi,
-                                                       const cpx<float>* __restrict__ tw64,
-                                                       int G) {
+// The pass body for a stage-B radix RB (64: 256 threads of 64 elements; 32:
+// 512 threads of 32 elements -- the same tile with twice the warps and half
+// the registers per thread).
+template <int RB, int LOGR, int LOGJ>
+FC2_D void regpass_body(const cpx<float>* __restrict__ in, cpx<float>* __restrict__ out,
+                        const PassArgs& a, const int64_t* __restrict__ Lg,
+                        const cpx<float>* __restrict__ twlo, const cpx<float>* __restrict__ twhi,
+                        const cpx<float>* __restrict__ tw64, int G) {
     using T = float;
-    constexpr int R = 1 << LOGR, J = 1 << LOGJ, E = R * J, NT = P64_NT;
-    constexpr int QAB = LOGR - 6, QA = 1 << QAB;
-    constexpr int PERA = 64 / QA;  // stage-A butterflies per thread
-    static_assert(E == 64 * NT, "tile must be 64 elements per thread");
+    constexpr int LRB = RB == 64 ? 6 : 5;
+    constexpr int R = 1 << LOGR, J = 1 << LOGJ, E = R * J, NT = RB == 64 ? P64_NT : P32_NT;
+    constexpr int QAB = LOGR - LRB, QA = 1 << QAB;
+    constexpr int PERA = RB / QA;  // stage-A butterflies per thread
+    static_assert(RB == 64 || RB == 32, "stage-B radix 64 or 32");
+    static_assert(E == RB * NT, "tile must be RB elements per thread");
+    static_assert(PERA * NT == RB * J, "stage-A butterflies must divide evenly");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* s = reinterpret_cast<cpx<T>*>(smem_raw);
     cpx<T>* st = s + E;
@@ -666,7 +672,7 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
     const int ntiles = tiles_x * G;
     const int nsg_mask = (1 << a.logNs) - 1;
     const int lts = a.logM - a.logNs - LOGR;
-    for (int i = threadIdx.x; i < 63 * QA; i += NT) cp_elem(&st[i], &tw64[i]);
+    for (int i = threadIdx.x; i < (RB - 1) * QA; i += NT) cp_elem(&st[i], &tw64[i]);
     cp_async_wait_all();
     auto rows_of = [&](int g) {
         int rows = R;
@@ -701,21 +707,21 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
             }
         }
         const int rows = rows_of(g);
-        // ---- stage A: radix QA, rows pp + k 64 -> rows pp QA + k.  In the first
+        // ---- stage A: radix QA, rows pp + k RB -> rows pp QA + k.  In the first
         // pass only rows < `rows` hold samples, so only the leading
-        // ceil(rows / 64) inputs of each stage-A transform can be nonzero: a
+        // ceil(rows / RB) inputs of each stage-A transform can be nonzero: a
         // pruned transform (PrunedDFT) skips the zeros.
         auto stage_a = [&](auto mz_tag) {
             constexpr int MZ = decltype(mz_tag)::value;
 #pragma unroll
             for (int b = 0; b < PERA; ++b) {
                 const int bi = threadIdx.x + b * NT;
-                const int jj = bi % J, pp = bi / J;  // pp < 64
+                const int jj = bi % J, pp = bi / J;  // pp < RB
                 cpx<T> v[QA];
                 if constexpr (MZ < QA) {
 #pragma unroll
                     for (int k = 0; k < MZ; ++k) {
-                        const int r = pp + k * 64;
+                        const int r = pp + k * RB;
                         v[k] = (r < rows) ? gin[j0 + jj + r * S] : mk<T>(0.f, 0.f);
                     }
                     PrunedDFT<T, QA, MZ>::run(v);
@@ -723,17 +729,17 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
                     if (a.first) {
 #pragma unroll
                         for (int k = 0; k < QA; ++k) {
-                            const int r = pp + k * 64;
+                            const int r = pp + k * RB;
                             v[k] = (r < rows) ? gin[j0 + jj + r * S] : mk<T>(0.f, 0.f);
                         }
                     } else {
                         const cpx<T>* src = gin + (int64_t)bx * E;
 #pragma unroll
-                        for (int k = 0; k < QA; ++k) v[k] = src[(pp + k * 64) * J + jj];
+                        for (int k = 0; k < QA; ++k) v[k] = src[(pp + k * RB) * J + jj];
                     }
                     const int jm = (j0 + jj) & nsg_mask;
                     if (a.logNs > 0 && jm != 0) {
-                        // w_M^{(pp + 64 k) jm 2^lts} = base * step^k, step^k = lo[k & 7] hi[k >> 3];
+                        // w_M^{(pp + RB k) jm 2^lts} = base * step^k, step^k = lo[k & 7] hi[k >> 3];
                         // every factor is a table lookup (no chains of products)
                         // (base lo[q] formed once per q: the same products as per k)
                         cpx<T> bl[8], hi[8];
@@ -741,11 +747,11 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
                         hi[0] = mk<T>(1.f, 0.f);
 #pragma unroll
                         for (int q = 1; q < 8; ++q) {
-                            bl[q] = mul(bl[0], twiddle(twlo, twhi, a.tws, (int64_t)((64 * q * jm) << lts)));
+                            bl[q] = mul(bl[0], twiddle(twlo, twhi, a.tws, (int64_t)((RB * q * jm) << lts)));
                             // only the factors k >> 3 < QA / 8 of this radix: their
                             // exponents stay below M (larger ones would not)
                             if (8 * q < QA)
-                                hi[q] = twiddle(twlo, twhi, a.tws, (int64_t)((512 * q * jm) << lts));
+                                hi[q] = twiddle(twlo, twhi, a.tws, (int64_t)((8 * RB * q * jm) << lts));
                         }
 #pragma unroll
                         for (int k = 0; k < QA; ++k) {
@@ -762,7 +768,7 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
         };
         int mz = QA;
         if (a.first) {
-            const int kz = (rows + 63) >> 6;
+            const int kz = (rows + RB - 1) >> LRB;
             mz = 1;
             while (mz < kz && mz < QA) mz <<= 1;
         }
@@ -774,7 +780,7 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
         else if (mz == 16) stage_a(std::integral_constant<int, (QA > 16 ? 16 : QA)>{});
         else stage_a(std::integral_constant<int, (QA > 32 ? 32 : QA)>{});
         __syncthreads();
-        // ---- stage B: radix 64, rows pp + k QA.  Where a warp's stores from
+        // ---- stage B: radix RB, rows pp + k QA.  Where a warp's stores from
         // registers hit the same 32-byte sectors as a smem-staged store would
         // (the last pass, and a next pass of the same radix), the results go
         // straight to global memory; otherwise they are staged in place.
@@ -786,16 +792,16 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
             // layout is row-contiguous within a column): row-first lanes for
             // 16-column tiles; otherwise columns across the warp
             const bool rows_first = (LOGJ == 4) && same_radix && !a.last;
-            const int jj = rows_first ? (int)(threadIdx.x >> 4) : (int)(threadIdx.x % J);
-            const int pp = rows_first ? (int)(threadIdx.x & 15) : (int)(threadIdx.x / J);  // pp < QA
-            cpx<T> v[64];
+            const int jj = rows_first ? (int)(threadIdx.x >> QAB) : (int)(threadIdx.x % J);
+            const int pp = rows_first ? (int)(threadIdx.x & (QA - 1)) : (int)(threadIdx.x / J);  // pp < QA
+            cpx<T> v[RB];
 #pragma unroll
-            for (int k = 0; k < 64; ++k) v[k] = s[swz<LOGJ>((pp + k * QA) * J + jj)];
+            for (int k = 0; k < RB; ++k) v[k] = s[swz<LOGJ>((pp + k * QA) * J + jj)];
             if constexpr (QA > 1) {
 #pragma unroll
-                for (int k = 1; k < 64; ++k) v[k] = mul(v[k], st[(k - 1) * QA + pp]);
+                for (int k = 1; k < RB; ++k) v[k] = mul(v[k], st[(k - 1) * QA + pp]);
             }
-            SmallDFT<T, 64>::run(v);
+            SmallDFT<T, RB>::run(v);
             if (a.last) {
                 // output index o of element k grows by QA Ns per k; mode m = o or o - M
                 const int o0 = j0 + jj + (pp << logNs);
@@ -804,7 +810,7 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
                     cpx<T>* plus = out + (int64_t)(2 * g) * a.N;
                     cpx<T>* minus = plus + a.N;
 #pragma unroll
-                    for (int k = 0; k < 64; ++k) {
+                    for (int k = 0; k < RB; ++k) {
                         const int o = o0 + k * step;
                         const int jp = o - a.sh;                    // mode +(sh + jp)
                         const int jm = ((M - o) & (M - 1)) - a.sh;  // mode -(sh + jm)
@@ -815,7 +821,7 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
                     cpx<T>* spec = out + (int64_t)(a.npk + g) * a.N;
                     const int lo_end = a.N - a.hN, hi_start = M - a.hN;
 #pragma unroll
-                    for (int k = 0; k < 64; ++k) {
+                    for (int k = 0; k < RB; ++k) {
                         const int o = o0 + k * step;
                         if (o < lo_end) spec[o + a.hN] = v[k];
                         else if (o >= hi_start) spec[o - hi_start] = v[k];
@@ -826,11 +832,11 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
                 const int LOGJn = a.logJn;
                 const int logBlk = a.logRn + a.logJn;
 #pragma unroll
-                for (int k = 0; k < 64; ++k)
+                for (int k = 0; k < RB; ++k)
                     gout[rowcol_pos(pp + k * QA, j0 + jj, LOGJn, logBlk)] = v[k];
             } else {
 #pragma unroll
-                for (int k = 0; k < 64; ++k) s[swz<LOGJ>((pp + k * QA) * J + jj)] = v[k];
+                for (int k = 0; k < RB; ++k) s[swz<LOGJ>((pp + k * QA) * J + jj)] = v[k];
             }
         }
         if (!a.last && !same_radix) {
@@ -841,6 +847,28 @@ __global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __re
         }
         __syncthreads();  // the tile buffer is reused by the next iteration
     }
+}
+
+template <int LOGR, int LOGJ>
+__global__ void __launch_bounds__(P64_NT, 1) k_fft_pass64(const cpx<float>* __restrict__ in,
+                                                       cpx<float>* __restrict__ out, PassArgs a,
+                                                       const int64_t* __restrict__ Lg,
+                                                       const cpx<float>* __restrict__ twlo,
+                                                       const cpx<float>* __restrict__ twhi,
+                                                       const cpx<float>* __restrict__ tw64,
+                                                       int G) {
+    regpass_body<64, LOGR, LOGJ>(in, out, a, Lg, twlo, twhi, tw64, G);
+}
+
+template <int LOGR, int LOGJ>
+__global__ void __launch_bounds__(P32_NT, 1) k_fft_pass32(const cpx<float>* __restrict__ in,
+                                                       cpx<float>* __restrict__ out, PassArgs a,
+                                                       const int64_t* __restrict__ Lg,
+                                                       const cpx<float>* __restrict__ twlo,
+                                                       const cpx<float>* __restrict__ twhi,
+                                                       const cpx<float>* __restrict__ tw32,
+                                                       int G) {
+    regpass_body<32, LOGR, LOGJ>(in, out, a, Lg, twlo, twhi, tw32, G);
 }
 
 // ------------------------------------------- radix-16 pass fed by bulk copies
@@ -1187,13 +1215,15 @@ cudaError_t init_twiddles(fc2_plan_s* p, cudaStream_t s) {
         }
         off += n + 16;
     }
-    // tables of the two-stage radix-64 float kernel (stage-B twiddles)
+    // tables of the two-stage register float kernels (stage-B twiddles; radix
+    // 32 for the radix-32 family's 2^10 passes, else 64)
     for (auto& ps : p->passes) {
         if (p->fp64 || ps.logR < 10 || ps.logR > 12 || p->tw64_off[ps.logR] != 0) continue;
         p->tw64_off[ps.logR] = off;
-        const int n = 63 * (1 << (ps.logR - 6));
+        const int lrb = (p->fft_family == FFT_R32 && ps.logR == 10) ? 5 : 6;
+        const int n = ((1 << lrb) - 1) * (1 << (ps.logR - lrb));
         k_init_tw64<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((cpx<float>*)p->d_twst + off,
-                                                                      ps.logR);
+                                                                      ps.logR, lrb);
         off += n + 16;
     }
     if (p->fp64)
@@ -1242,7 +1272,7 @@ static std::vector<int> balanced_plan(int logM, bool fp64) {
 // ------------------------------------------------------------ pass kernels
 // Which kernel runs a pass of radix 2^logR (as run_radix chooses), its tile
 // (2^loge elements, 2^logj columns) and threads.
-enum PassKernel { PK_SINGLE = 0, PK_R16 = 1, PK_R64 = 2, PK_BULK = 3 };
+enum PassKernel { PK_SINGLE = 0, PK_R16 = 1, PK_R64 = 2, PK_BULK = 3, PK_R32 = 4 };
 struct PassShape {
     int kind, loge, logj, nt;
 };
@@ -1253,6 +1283,8 @@ static PassShape pass_shape(int logM, bool fp64, int family, int logR) {
     }
     if (!fp64 && family == FFT_R64 && logR >= 10 && logR <= 12)
         return PassShape{PK_R64, P64_LOGE, P64_LOGE - logR, P64_NT};
+    if (!fp64 && family == FFT_R32 && logR == 10)
+        return PassShape{PK_R32, P64_LOGE, P64_LOGE - logR, P32_NT};
     if (!fp64 && family != FFT_R16 && logR >= 8 && logR <= 12)
         return PassShape{PK_BULK, PT_LOGE, PT_LOGE - logR, PT_NT};
     const int loge = fp64 ? FftCfg<double>::LOGE : FftCfg<float>::LOGE;
@@ -1366,8 +1398,8 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
     std::vector<int> best_rs = cands.front();
     int best_fam = FFT_R64, best_grp = 0;
     cudaError_t e = cudaSuccess;
-    const int fams_f32[3] = {FFT_BULK, FFT_R64, FFT_R16};
-    const int nfam = p->fp64 ? 1 : 3;
+    const int fams_f32[4] = {FFT_BULK, FFT_R64, FFT_R32, FFT_R16};
+    const int nfam = p->fp64 ? 1 : 4;
     std::vector<int> groups{0};
     if (p->G > 1) groups.push_back(1);
     if (p->G > 2) groups.push_back(2);
@@ -1417,9 +1449,9 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
 std::vector<FftChoice> fft_tune_candidates(int logM, bool fp64) {
     std::vector<FftChoice> out;
     const int maxr = fp64 ? FftCfg<double>::MAXR : FftCfg<float>::MAXR;
-    const int fams[3] = {FFT_R64, FFT_BULK, FFT_R16};
+    const int fams[4] = {FFT_R64, FFT_R32, FFT_BULK, FFT_R16};
     for (const auto& rs : fft_candidates(logM, maxr))
-        for (int fi = 0; fi < (fp64 ? 1 : 3); ++fi) {
+        for (int fi = 0; fi < (fp64 ? 1 : 4); ++fi) {
             const int fam = fp64 ? FFT_R16 : fams[fi];
             if (fft_plan_valid(logM, fp64, fam, rs)) out.push_back(FftChoice{rs, fam});
         }
@@ -1433,7 +1465,8 @@ bool fft_choice_valid(int logM, bool fp64, const FftChoice& c) {
         sum += r;
     }
     if (sum != logM || c.rs.empty()) return false;
-    if (c.family != FFT_R64 && c.family != FFT_BULK && c.family != FFT_R16) return false;
+    if (c.family != FFT_R64 && c.family != FFT_R32 && c.family != FFT_BULK && c.family != FFT_R16)
+        return false;
     if (fp64 && c.family != FFT_R16) return false;
     // only shapes the candidate list can hold
     bool listed = false;
@@ -1520,23 +1553,32 @@ static cudaError_t run_pass(fc2_plan_s* p, const void* in, void* out, const Pass
     return cudaGetLastError();
 }
 
-template <int LOGR>
+template <int RB, int LOGR>
 static cudaError_t run_pass64(fc2_plan_s* p, const void* in, void* out, const PassArgs& a,
                               cudaStream_t s) {
     constexpr int LOGJ = P64_LOGE - LOGR, E = 1 << P64_LOGE;
+    constexpr int NT = RB == 64 ? P64_NT : P32_NT;
     const int64_t S = p->M >> LOGR;
-    const size_t smem = (size_t)(E + 63 * (1 << (LOGR - 6))) * sizeof(cpx<float>);
-    auto kern = k_fft_pass64<LOGR, LOGJ>;
+    const size_t smem = (size_t)(E + (RB - 1) * ((1 << LOGR) / RB)) * sizeof(cpx<float>);
+    const void* kfn;
+    if constexpr (RB == 64) kfn = (const void*)k_fft_pass64<LOGR, LOGJ>;
+    else kfn = (const void*)k_fft_pass32<LOGR, LOGJ>;
     {
-        const cudaError_t e = raise_smem_limit((const void*)kern, smem);
+        const cudaError_t e = raise_smem_limit(kfn, smem);
         if (e != cudaSuccess) return e;
     }
     const int64_t ntiles = (S >> LOGJ) * (int64_t)a.ng;
     const int nsm = device_sm_count();
     const unsigned blocks = (unsigned)std::min<int64_t>(ntiles, (int64_t)nsm);
-    kern<<<blocks, P64_NT, smem, s>>>((const cpx<float>*)in, (cpx<float>*)out, a, p->d_L,
-                                   (const cpx<float>*)p->d_twlo, (const cpx<float>*)p->d_twhi,
-                                   (const cpx<float>*)p->d_twst + p->tw64_off[LOGR], a.ng);
+    const cpx<float>* tw = (const cpx<float>*)p->d_twst + p->tw64_off[LOGR];
+    if constexpr (RB == 64)
+        k_fft_pass64<LOGR, LOGJ><<<blocks, NT, smem, s>>>((const cpx<float>*)in, (cpx<float>*)out, a,
+                                                          p->d_L, (const cpx<float>*)p->d_twlo,
+                                                          (const cpx<float>*)p->d_twhi, tw, a.ng);
+    else
+        k_fft_pass32<LOGR, LOGJ><<<blocks, NT, smem, s>>>((const cpx<float>*)in, (cpx<float>*)out, a,
+                                                          p->d_L, (const cpx<float>*)p->d_twlo,
+                                                          (const cpx<float>*)p->d_twhi, tw, a.ng);
     return cudaGetLastError();
 }
 
@@ -1567,7 +1609,9 @@ template <typename T, int LOGR>
 static cudaError_t run_radix(fc2_plan_s* p, const void* in, void* out, const PassArgs& a,
                              cudaStream_t s) {
     if constexpr (sizeof(T) == 4 && LOGR >= 10 && LOGR <= 12) {
-        if (LOGR != p->logM && p->fft_family == FFT_R64) return run_pass64<LOGR>(p, in, out, a, s);
+        if (LOGR != p->logM && p->fft_family == FFT_R64) return run_pass64<64, LOGR>(p, in, out, a, s);
+        if constexpr (LOGR == 10)
+            if (LOGR != p->logM && p->fft_family == FFT_R32) return run_pass64<32, LOGR>(p, in, out, a, s);
     }
     if constexpr (sizeof(T) == 4 && LOGR >= 8 && LOGR <= 12) {
         if (LOGR != p->logM && p->fft_family != FFT_R16) return run_pass_tma<LOGR>(p, in, out, a, s);
@@ -1692,10 +1736,11 @@ static int replay_plan(int logM, bool fp64, int family, const std::vector<int>& 
                 const int64_t jmax = (1ll << logNs) - 1;
                 const int lts = logM - logNs - LOGR;
                 int64_t qmax = 0;
-                if (sh.kind == PK_R64) {
-                    const int QA = 1 << (LOGR - 6);
-                    qmax = std::max<int64_t>((63 * jmax) << lts, (448 * jmax) << lts);
-                    if (QA > 8) qmax = std::max<int64_t>(qmax, ((512 * ((QA / 8) - 1)) * jmax) << lts);
+                if (sh.kind == PK_R64 || sh.kind == PK_R32) {
+                    const int RB = sh.kind == PK_R64 ? 64 : 32, QA = (1 << LOGR) / RB;
+                    qmax = std::max<int64_t>(((RB - 1) * jmax) << lts, ((7 * RB) * jmax) << lts);
+                    if (QA > 8)
+                        qmax = std::max<int64_t>(qmax, ((8 * RB * ((QA / 8) - 1)) * jmax) << lts);
                 } else {
                     const int Q1 = 1 << stage_bits(LOGR, 0);
                     qmax = std::max<int64_t>(((R / Q1 - 1) * jmax) << lts, ((R / Q1) * jmax) << lts);
@@ -1703,7 +1748,7 @@ static int replay_plan(int logM, bool fp64, int family, const std::vector<int>& 
                 if (qmax >= M) return fail(pi, 3, bx, qmax);
             }
             if (last) continue;  // the last pass's mode stores are range-checked
-            if ((sh.kind == PK_R64 || sh.kind == PK_BULK) && same_radix) {
+            if ((sh.kind == PK_R64 || sh.kind == PK_R32 || sh.kind == PK_BULK) && same_radix) {
                 for (int64_t kr = 0; kr < R; ++kr)
                     for (int jj = 0; jj < J; ++jj) {
                         const int64_t gi = rowcol_pos((int)kr, j0 + jj, LOGJn, logBlk);
@@ -1711,7 +1756,8 @@ static int replay_plan(int logM, bool fp64, int family, const std::vector<int>& 
                     }
                 continue;
             }
-            const bool fast = (sh.kind == PK_R64 || sh.kind == PK_BULK) && logNs == 0 &&
+            const bool fast = (sh.kind == PK_R64 || sh.kind == PK_R32 || sh.kind == PK_BULK) &&
+                              logNs == 0 &&
                               LOGR <= logSn && LOGJn <= LOGR && (((1 << LOGJn) << LOGJ) <= sh.nt);
             if (fast) {
                 const int Jn = 1 << LOGJn, NT = sh.nt;
