@@ -992,7 +992,7 @@ def main():
                     help="trial frequencies of a --profile run of the large curve (default 2^26)")
     ap.add_argument("--workload", default="survey", choices=["survey", "long"] + sorted(k for k in WORKLOADS if k != "survey"),
                     help="survey (default, the headline) or another synthetic workload")
-    ap.add_argument("--fft-kernel", default="default", choices=["default", "r64", "r16", "bulk", "r32"],
+    ap.add_argument("--fft-kernel", default="default", choices=["default", "r64", "r16", "bulk", "r32", "r32x"],
                     help="kernel family of the float transform passes")
     ap.add_argument("--fft-group", type=int, default=0,
                     help="grids taken through all transform passes together (0 = all)")

@@ -103,9 +103,10 @@ typedef struct {
                                   shared memory, 3 = radix-16 stages fed by bulk
                                   asynchronous copies (radix 2^8..2^12 passes), 4 = two
                                   register stages of radix 32 and 32 with 512 threads
-                                  (2^10 passes; family 3's kernel for the others).  Passes
-                                  a family does not cover use family 2.  FP64 ignores it;
-                                  values outside 0..4 are FC2_ERR_INVALID_ARG */
+                                  (2^10 passes; family 3's kernel for the others), 5 = the
+                                  same for 2^9 (16 x 32) and 2^10 passes.  Passes a family
+                                  does not cover use family 2.  FP64 ignores it; values
+                                  outside 0..5 are FC2_ERR_INVALID_ARG */
     int gridding;              /* 0 = spreading kernel of width kernel_width with its
                                   Fourier transform divided out, one transform per
                                   harmonic multiple (default; meets 1e-4 chi2_0).

@@ -35,7 +35,7 @@ class Options(ctypes.Structure):
 GRIDDING = {"kernel": 0, "paper": 1}
 
 # fc2_options.fft_kernel values
-FFT_KERNELS = {"default": 0, "r64": 1, "r16": 2, "bulk": 3, "r32": 4}
+FFT_KERNELS = {"default": 0, "r64": 1, "r16": 2, "bulk": 3, "r32": 4, "r32x": 5}
 
 
 class Best(ctypes.Structure):
@@ -383,7 +383,8 @@ BATCH_STAGES = ("spread", "fft", "assemble", "fixup", "peaks")
 AUTOTUNE = {"fixed": -1, "table": 0, "retune": 1}
 FFT_FAMILY_NAMES = {0: "radix-16 stages in shared memory", 1: "two register stages",
                     2: "radix-16 stages fed by bulk copies",
-                    3: "two register stages of radix 32 (512 threads)"}
+                    3: "two register stages of radix 32 (512 threads)",
+                    4: "two register stages of radix 32 (512 threads), also 2^9 passes"}
 
 
 def batch_config():

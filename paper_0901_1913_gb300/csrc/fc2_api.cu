@@ -149,7 +149,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     if (opt.kernel_width != 0 && (opt.kernel_width < 2 || opt.kernel_width > 16))
         return FC2_ERR_INVALID_ARG;
     if (opt.top_k < 0 || opt.top_k > 64 || opt.alias_tau < 0.0) return FC2_ERR_INVALID_ARG;
-    if (opt.fft_kernel < 0 || opt.fft_kernel > 4) return FC2_ERR_INVALID_ARG;
+    if (opt.fft_kernel < 0 || opt.fft_kernel > 5) return FC2_ERR_INVALID_ARG;
     if (opt.fft_group < 0) return FC2_ERR_INVALID_ARG;
     if (opt.autotune < -1 || opt.autotune > 1) return FC2_ERR_INVALID_ARG;
     if (opt.gridding < 0 || opt.gridding > 1) return FC2_ERR_INVALID_ARG;

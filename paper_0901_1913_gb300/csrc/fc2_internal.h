@@ -30,8 +30,10 @@ enum FftFamily {
     FFT_R64 = 1,   // two register stages of radix R/64 and 64 (k_fft_pass64) for radix
                    // 2^10..2^12, FFT_BULK's kernel for 2^8 and 2^9
     FFT_BULK = 2,  // radix-16 stages fed by bulk asynchronous copies (k_fft_pass_tma), 2^8..2^12
-    FFT_R32 = 3    // two register stages of radix 32 and 32 (k_fft_pass32, 512 threads) for
+    FFT_R32 = 3,   // two register stages of radix 32 and 32 (k_fft_pass32, 512 threads) for
                    // radix 2^10; FFT_BULK's kernel for 2^8, 2^9, 2^11 and 2^12
+    FFT_R32X = 4   // k_fft_pass32 for radix 2^9 (16 x 32) and 2^10; FFT_BULK's kernel for
+                   // 2^8, 2^11 and 2^12
 };
 
 // Cells per spreading tile: the default for the grid length (1024, or 128 below
@@ -46,7 +48,11 @@ inline int spread_tile_of(int64_t M, int requested) {
 
 // Family for fc2_options.fft_kernel (0 = library default).
 inline int fft_family_of(int fft_kernel) {
-    return fft_kernel == 2 ? FFT_R16 : fft_kernel == 3 ? FFT_BULK : fft_kernel == 4 ? FFT_R32 : FFT_R64;
+    return fft_kernel == 2   ? FFT_R16
+           : fft_kernel == 3 ? FFT_BULK
+           : fft_kernel == 4 ? FFT_R32
+           : fft_kernel == 5 ? FFT_R32X
+                             : FFT_R64;
 }
 
 struct GridGeom {

@@ -1194,6 +1194,11 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
     }
 }
 
+// Whether a float pass of radix 2^logR runs on the radix-32 register kernel.
+static bool r32_pass(int family, int logR) {
+    return (family == FFT_R32 && logR == 10) || (family == FFT_R32X && (logR == 9 || logR == 10));
+}
+
 cudaError_t init_twiddles(fc2_plan_s* p, cudaStream_t s) {
     int sh = (p->logM + 1) / 2;
     int64_t nlo = 1ll << sh, nhi = p->M >> sh;
@@ -1218,9 +1223,12 @@ cudaError_t init_twiddles(fc2_plan_s* p, cudaStream_t s) {
     // tables of the two-stage register float kernels (stage-B twiddles; radix
     // 32 for the radix-32 family's 2^10 passes, else 64)
     for (auto& ps : p->passes) {
-        if (p->fp64 || ps.logR < 10 || ps.logR > 12 || p->tw64_off[ps.logR] != 0) continue;
+        if (p->fp64 || p->tw64_off[ps.logR] != 0) continue;
+        if (!((ps.logR >= 10 && ps.logR <= 12 && p->fft_family == FFT_R64) ||
+              r32_pass(p->fft_family, ps.logR)))
+            continue;
         p->tw64_off[ps.logR] = off;
-        const int lrb = (p->fft_family == FFT_R32 && ps.logR == 10) ? 5 : 6;
+        const int lrb = r32_pass(p->fft_family, ps.logR) ? 5 : 6;
         const int n = ((1 << lrb) - 1) * (1 << (ps.logR - lrb));
         k_init_tw64<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>((cpx<float>*)p->d_twst + off,
                                                                       ps.logR, lrb);
@@ -1283,7 +1291,7 @@ static PassShape pass_shape(int logM, bool fp64, int family, int logR) {
     }
     if (!fp64 && family == FFT_R64 && logR >= 10 && logR <= 12)
         return PassShape{PK_R64, P64_LOGE, P64_LOGE - logR, P64_NT};
-    if (!fp64 && family == FFT_R32 && logR == 10)
+    if (!fp64 && r32_pass(family, logR))
         return PassShape{PK_R32, P64_LOGE, P64_LOGE - logR, P32_NT};
     if (!fp64 && family != FFT_R16 && logR >= 8 && logR <= 12)
         return PassShape{PK_BULK, PT_LOGE, PT_LOGE - logR, PT_NT};
@@ -1398,8 +1406,8 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
     std::vector<int> best_rs = cands.front();
     int best_fam = FFT_R64, best_grp = 0;
     cudaError_t e = cudaSuccess;
-    const int fams_f32[4] = {FFT_BULK, FFT_R64, FFT_R32, FFT_R16};
-    const int nfam = p->fp64 ? 1 : 4;
+    const int fams_f32[5] = {FFT_BULK, FFT_R64, FFT_R32, FFT_R32X, FFT_R16};
+    const int nfam = p->fp64 ? 1 : 5;
     std::vector<int> groups{0};
     if (p->G > 1) groups.push_back(1);
     if (p->G > 2) groups.push_back(2);
@@ -1449,9 +1457,9 @@ cudaError_t autotune_fft(fc2_plan_s* p, cudaStream_t s) {
 std::vector<FftChoice> fft_tune_candidates(int logM, bool fp64) {
     std::vector<FftChoice> out;
     const int maxr = fp64 ? FftCfg<double>::MAXR : FftCfg<float>::MAXR;
-    const int fams[4] = {FFT_R64, FFT_R32, FFT_BULK, FFT_R16};
+    const int fams[5] = {FFT_R64, FFT_R32, FFT_R32X, FFT_BULK, FFT_R16};
     for (const auto& rs : fft_candidates(logM, maxr))
-        for (int fi = 0; fi < (fp64 ? 1 : 4); ++fi) {
+        for (int fi = 0; fi < (fp64 ? 1 : 5); ++fi) {
             const int fam = fp64 ? FFT_R16 : fams[fi];
             if (fft_plan_valid(logM, fp64, fam, rs)) out.push_back(FftChoice{rs, fam});
         }
@@ -1465,7 +1473,8 @@ bool fft_choice_valid(int logM, bool fp64, const FftChoice& c) {
         sum += r;
     }
     if (sum != logM || c.rs.empty()) return false;
-    if (c.family != FFT_R64 && c.family != FFT_R32 && c.family != FFT_BULK && c.family != FFT_R16)
+    if (c.family != FFT_R64 && c.family != FFT_R32 && c.family != FFT_R32X && c.family != FFT_BULK &&
+        c.family != FFT_R16)
         return false;
     if (fp64 && c.family != FFT_R16) return false;
     // only shapes the candidate list can hold
@@ -1610,8 +1619,9 @@ static cudaError_t run_radix(fc2_plan_s* p, const void* in, void* out, const Pas
                              cudaStream_t s) {
     if constexpr (sizeof(T) == 4 && LOGR >= 10 && LOGR <= 12) {
         if (LOGR != p->logM && p->fft_family == FFT_R64) return run_pass64<64, LOGR>(p, in, out, a, s);
-        if constexpr (LOGR == 10)
-            if (LOGR != p->logM && p->fft_family == FFT_R32) return run_pass64<32, LOGR>(p, in, out, a, s);
+    }
+    if constexpr (sizeof(T) == 4 && (LOGR == 9 || LOGR == 10)) {
+        if (LOGR != p->logM && r32_pass(p->fft_family, LOGR)) return run_pass64<32, LOGR>(p, in, out, a, s);
     }
     if constexpr (sizeof(T) == 4 && LOGR >= 8 && LOGR <= 12) {
         if (LOGR != p->logM && p->fft_family != FFT_R16) return run_pass_tma<LOGR>(p, in, out, a, s);

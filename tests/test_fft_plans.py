@@ -61,7 +61,7 @@ def test_every_library_plan_replays_in_range(lib, fp64):
     for logM in range(9, 29):
         for rs in library_plans(lib, logM, fp64):
             assert sum(rs) == logM
-            for kern in (1, 2, 3, 4):
+            for kern in (1, 2, 3, 4, 5):
                 rc, info = check(lib, logM, fp64, kern, rs)
                 assert rc == 0, (logM, fp64, kern, rs, rc, info)
 
@@ -87,7 +87,7 @@ def test_validity_implies_in_range_for_all_splits(lib, fp64):
             for rs in itertools.product(range(5, 13), repeat=P):
                 if sum(rs) != logM:
                     continue
-                for kern in (1, 2, 3, 4):
+                for kern in (1, 2, 3, 4, 5):
                     rc_v, _ = check(lib, logM, fp64, kern, rs)
                     rc_r, info = check(lib, logM, fp64, kern, rs, validate=False)
                     if rc_v == 0:

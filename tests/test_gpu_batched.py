@@ -114,7 +114,7 @@ def test_batched_degenerate_bins(fc2, oracle_mod, prec, last):
     print(prec, stats)
 
 
-@pytest.mark.parametrize("fft_kernel", ["r64", "r16", "bulk", "r32"])
+@pytest.mark.parametrize("fft_kernel", ["r64", "r16", "bulk", "r32", "r32x"])
 def test_batched_kernel_families_agree(fc2, oracle_mod, fft_kernel):
     """The batch's transforms (2^14-point grids, passes (7, 7), and 2^19-point
     ones, passes (10, 9)) give the same Delta chi^2 with every float kernel
@@ -291,7 +291,7 @@ def test_autotuner_table_and_cache_file(fc2, oracle_mod, tmp_path, monkeypatch):
         assert r["ok"], (c, r)
 
 
-@pytest.mark.parametrize("family", [1, 2, 0, 3])
+@pytest.mark.parametrize("family", [1, 2, 0, 3, 4])
 def test_reversed_two_pass_plan_matches_oracle(fc2, oracle_mod, family):
     """The autotuner's other two-pass plan for the survey's 2^19-point grids:
     radix 2^9 first, then 2^10 (the fixed plan takes 2^10 first), forced with

@@ -60,7 +60,8 @@ def test_packed_spectra_match_direct_sums(fc2, oracle_mod):
 
 
 @pytest.mark.parametrize("fft_kernel,fft_group", [("r64", 0), ("r16", 0), ("bulk", 0),
-                                                  ("r32", 0), ("r64", 1), ("bulk", 2)])
+                                                  ("r32", 0), ("r32x", 0), ("r64", 1),
+                                                  ("bulk", 2)])
 @pytest.mark.parametrize("logN,oversample", [(14, 4), (19, 4), (22, 4), (19, 2)])
 def test_fft_kernel_families_match_direct_sums(fc2, oracle_mod, fft_kernel, fft_group, logN,
                                                oversample):
