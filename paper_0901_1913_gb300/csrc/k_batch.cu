@@ -107,22 +107,34 @@ __global__ void k_bphase(const double* __restrict__ tau, const double* __restric
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const int k = slot_k[g], kind = slot_kind[g];
-    const double ts = tau[a + s];
-    const double cc = __dmul_rn((double)k, df[c]);
-    const double p = __dmul_rn(cc, ts);
-    const double u = __dsub_rn(p, floor(p));
-    const double X = __dmul_rn((double)M, u);
-    const double Xs = __dsub_rn(X, 0.5 * (double)w);
-    const double fl = floor(Xs);
-    const double de = __dsub_rn(Xs, fl);
     double sn, cn;
+    int64_t fl;
+    T de;
     if constexpr (sizeof(T) == 4) {
+        // the cell position from the exact fixed-point phase B = frac(df tau) 2^64:
+        // X - w/2 = M frac(k df tau) - w/2 in fixed point with 63 - log2 M
+        // fraction bits (integer arithmetic, no double instruction)
         const uint64_t kk = (uint64_t)k;
-        const uint64_t th = kk * Aph[a + s] + (uint64_t)(N / 2) * (kk * Bph[a + s]);
+        const uint64_t kb = kk * Bph[a + s];  // frac(k df tau) 2^64
+        const int fb = 63 - (63 - __clzll((long long)M));
+        const int64_t xs = (int64_t)(kb >> 1) - ((int64_t)w << (fb - 1));
+        fl = xs >> fb;  // floor
+        const uint64_t fr = (uint64_t)xs & ((1ull << fb) - 1);
+        de = __fmul_rn(__ull2float_rn(fr), __int_as_float((127 - fb) << 23));  // fr 2^-fb
+        const uint64_t th = kk * Aph[a + s] + (uint64_t)(N / 2) * kb;
         const dfc z = df_phasor(th, dftab, dftab + 256);
         cn = (double)z.re.h + (double)z.re.l;
         sn = (double)z.im.h + (double)z.im.l;
     } else {
+        const double ts = tau[a + s];
+        const double cc = __dmul_rn((double)k, df[c]);
+        const double p = __dmul_rn(cc, ts);
+        const double u = __dsub_rn(p, floor(p));
+        const double X = __dmul_rn((double)M, u);
+        const double Xs = __dsub_rn(X, 0.5 * (double)w);
+        const double flo = floor(Xs);
+        fl = (int64_t)flo;
+        de = (T)__dsub_rn(Xs, flo);
         const double q1 = __dmul_rn(__dmul_rn((double)k, fmin[c]), ts);
         const double q2 = __dmul_rn((double)(N / 2), u);
         const double th = __dadd_rn(__dsub_rn(q1, floor(q1)), __dsub_rn(q2, floor(q2)));
@@ -131,7 +143,7 @@ __global__ void k_bphase(const double* __restrict__ tau, const double* __restric
     const double amp = kind == 0 ? wq[a + s] : wp[a + s];
     const int64_t o = slot_soff[g] + s;
     key[o] = (int32_t)fl + 1;
-    dlt[o] = (T)de;
+    dlt[o] = de;
     cs[o] = mk<T>((T)(amp * cn), (T)(amp * sn));
 }
 
