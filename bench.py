@@ -513,7 +513,9 @@ def run_survey(args):
             "algorithmic_bytes_per_step": evals * B_ALG,
             "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"}
     fft_ms = stage_ms["fft"]
-    dominant = {"name": "transform passes (k_fft_pass64<10,4> then k_fft_pass_tma<9>)",
+    cfg = stats["config"]
+    dominant = {"name": "transform passes (log2 radices %s, %s)" % (
+                    " x ".join(str(r) for r in cfg["fft_log2_radices"]), cfg["fft_family"]),
                 "ms_per_step": fft_ms, "algorithmic_bytes_per_step": fft_alg,
                 "achieved": fft_alg / 1e9 / (fft_ms / 1e3) if fft_ms > 0 else None,
                 "frac": (fft_alg / 1e9 / (fft_ms / 1e3)) / peak if fft_ms > 0 else None,
