@@ -320,3 +320,35 @@ def test_reversed_two_pass_plan_matches_oracle(fc2, oracle_mod, family):
                                           with_pivots=True)
         r = compare(block[:, bins].T.astype(np.float64), oref, piv, chi0)
         assert r["ok"], (family, c, r)
+
+
+def test_batched_peaks_are_oracle_local_maxima(fc2, oracle_mod):
+    """The batched top-K records (block maxima, the K-th-best threshold, then
+    the ranking of the blocks that reach it) against the oracle's full
+    periodogram of each checked curve: every record is a local maximum of the
+    oracle's Delta chi^2_H with its value, in decreasing order, and the
+    oracle's K largest local maxima are the records' bins up to near-ties."""
+    b = small_survey(C=8, N=1 << 13, seed=37)
+    K = 6
+    _, peaks, _ = fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df, b.N, 2,
+                                      "mixed", top_k=K)
+    for c in range(0, b.C, 2):
+        cur = b.curve(c)
+        ref = oracle_mod.periodogram(cur.t, cur.x, cur.sigma, cur.H, cur.f_min, cur.df, cur.N)
+        row = ref[:, cur.H - 1]
+        _, _, chi0, _ = oracle_mod.moments(cur.x, cur.sigma)
+        tol = TOL * chi0
+        recs = [p for p in peaks[c] if p["j"] >= 0]
+        assert len(recs) == K
+        vals = [p["dchi2"] for p in recs]
+        assert all(vals[i] >= vals[i + 1] for i in range(K - 1))
+        for p in recs:
+            j = int(p["j"])
+            assert abs(p["dchi2"] - row[j]) <= tol, (c, j)
+            assert j == 0 or row[j] >= row[j - 1] - tol
+            assert j == cur.N - 1 or row[j] >= row[j + 1] - tol
+        lm = [(row[j], j) for j in range(cur.N)
+              if (j == 0 or row[j] > row[j - 1]) and (j == cur.N - 1 or row[j] >= row[j + 1])]
+        lm.sort(key=lambda v: (-v[0], v[1]))
+        for (v_or, j_or), p in zip(lm[:K], recs):
+            assert j_or == p["j"] or abs(v_or - row[int(p["j"])]) <= tol, (c, j_or, p["j"])
