@@ -474,6 +474,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
             p->geom[0].L = L;
             p->geom[0].wraps = (L == M) ? 1 : 0;
         }
+        p->h_L = Lh;
         g.ok(cudaMemcpyAsync(p->d_L, Lh.data(), G * 8, cudaMemcpyHostToDevice, s));
         // Algorithmic bytes of the transform: each pass reads its input once
         // (the first pass only the rows that hold samples) and writes its output

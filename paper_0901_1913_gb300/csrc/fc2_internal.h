@@ -160,6 +160,7 @@ struct fc2_plan_s {
     fc2_best* d_best = nullptr;  // [H + top_k]
 
     std::vector<fc2::GridGeom> geom;  // per source (sample set)
+    std::vector<int64_t> h_L;         // occupied extent of each grid (d_L's host copy)
     std::vector<fc2::FftPass> passes;
     int64_t last_flag_count = 0;
     bool executed = false;     // the device output holds a completed execute

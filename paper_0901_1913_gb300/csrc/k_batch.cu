@@ -1955,6 +1955,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
                 }
                 p.geom[g].L = Lv[g];
             }
+            p.h_L = Lv;
         };
         fill_L(unit);
         std::vector<int> curves_flat, hoff(BHM);

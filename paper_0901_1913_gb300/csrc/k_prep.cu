@@ -770,21 +770,64 @@ __device__ __forceinline__ int64_t lower_bound_key(const int32_t* __restrict__ k
 // the set's sorted keys of a - w + 1 and a + TILE (a = tile start), i.e. the
 // samples whose windows meet the tile.  rng[((g ntile + tile) 2 + si) 6 + q]:
 // q = 0..5 the bounds for the shifts -M (lo, hi), 0, +M.
+// The occupied tiles of every grid as one list: tfirst[g] = first list entry
+// of grid g (its tiles cover [0, L_g)), tfirst[G] = the entry count (one CTA,
+// a block scan over the grids); then tgrid[t] = the grid of entry t
+// (k_tile_fill, a search of tfirst per entry).
+template <int TILE>
+__global__ void __launch_bounds__(1024) k_tile_list(const int64_t* __restrict__ Lg, int G,
+                                                    int64_t* __restrict__ tfirst) {
+    __shared__ int64_t wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, wi = tid >> 5;
+    const int per = (G + 1023) / 1024;
+    const int g0 = tid * per, g1 = min(G, g0 + per);
+    int64_t v = 0;
+    for (int g = g0; g < g1; ++g) v += (Lg[g] + TILE - 1) / TILE;
+    int64_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wi] = incl;
+    __syncthreads();
+    int64_t base = incl - v;
+    for (int k = 0; k < wi; ++k) base += wsum[k];
+    for (int g = g0; g < g1; ++g) {
+        tfirst[g] = base;
+        base += (Lg[g] + TILE - 1) / TILE;
+    }
+    if (g0 < G && g1 == G) tfirst[G] = base;
+}
+
+__global__ void k_tile_fill(const int64_t* __restrict__ tfirst, int G, int64_t ntile,
+                            int32_t* __restrict__ tgrid) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntile) return;
+    int lo = 0, hi = G;  // the last g with tfirst[g] <= t
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (tfirst[mid] <= t) lo = mid; else hi = mid;
+    }
+    tgrid[t] = lo;
+}
+
 template <int TILE>
 __global__ void __launch_bounds__(128) k_tile_ranges(const int32_t* __restrict__ key,
                                                      int64_t n_all, int64_t M, int w, int npk,
                                                      int pH, int w_p,
-                                                     const int64_t* __restrict__ Lg,
+                                                     const int64_t* __restrict__ tfirst,
+                                                     const int32_t* __restrict__ tgrid,
                                                      const int64_t* __restrict__ slot_soff,
                                                      const int64_t* __restrict__ slot_n,
                                                      int64_t ntile, int64_t* __restrict__ rng) {
-    const int g = blockIdx.y;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t tile = idx / 12;
-    const int sq = (int)(idx - tile * 12), si = sq / 6, q = sq - si * 6;
-    if (tile >= ntile) return;
+    const int64_t et = idx / 12;  // list entry
+    const int sq = (int)(idx - et * 12), si = sq / 6, q = sq - si * 6;
+    if (et >= ntile) return;
+    const int g = tgrid[et];
+    const int64_t tile = et - tfirst[g];
     const int64_t a = tile * TILE;
-    if (a >= Lg[g]) return;
     int t0 = g, nset = 1;
     if (npk > 0) {
         w = w_p;
@@ -799,7 +842,7 @@ __global__ void __launch_bounds__(128) k_tile_ranges(const int32_t* __restrict__
     const int64_t n = slot_n ? slot_n[t] : n_all;
     const int64_t shv = (q >> 1) == 0 ? M : ((q >> 1) == 1 ? 0 : -M);
     const int64_t v = (q & 1) ? a + TILE + shv : a - w + 1 + shv;
-    rng[((int64_t)g * ntile + tile) * 12 + sq] = lower_bound_key(key + so, n, v);
+    rng[et * 12 + sq] = lower_bound_key(key + so, n, v);
 }
 
 template <typename T, int TILE, int NT, int CAP>
@@ -808,7 +851,8 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
                                                const cpx<T>* __restrict__ cs, int64_t n_all,
                                                int64_t M, int w, T beta, int npk, int pH,
                                                int w_p, T beta_p,
-                                               const int64_t* __restrict__ Lg,
+                                               const int64_t* __restrict__ tfirst,
+                                               const int32_t* __restrict__ tgrid,
                                                cpx<T>* __restrict__ grid, int64_t gstride,
                                                const int64_t* __restrict__ slot_soff,
                                                const int64_t* __restrict__ slot_n,
@@ -824,10 +868,10 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
     __shared__ cpx<T> sc[CAP];
     __shared__ int32_t cum[PCUM * NT];
     __shared__ int32_t wtot[NT / 32];
-    const int g = blockIdx.y;
-    const int64_t a = (int64_t)blockIdx.x * TILE;
-    if (a >= Lg[g]) return;
-    const int64_t* rt = rngtab + ((int64_t)g * gridDim.x + blockIdx.x) * 12;
+    const int64_t et = blockIdx.x;  // list entry: an occupied tile
+    const int g = tgrid[et];
+    const int64_t a = (et - tfirst[g]) * TILE;
+    const int64_t* rt = rngtab + et * 12;
     // sample sets of grid g: one, or (packed grids g >= H) two
     int t0 = g, nset = 1;
     if (npk > 0) {
@@ -921,23 +965,34 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
 
 template <typename T, int TILE, int NT, int CAP>
 static cudaError_t spread_tiles(fc2_plan_s* p, cudaStream_t s) {
-    int64_t Lmax = 0;
-    for (auto& g : p->geom) Lmax = g.L > Lmax ? g.L : Lmax;
-    int64_t tiles = (Lmax + TILE - 1) / TILE;
-    // the tile table (12 int64 bounds per tile: at most 96 M / TILE bytes per
-    // grid, against the M complex values of a grid) lives in the second grid
+    // only the occupied tiles are launched: the list of (grid, tile) entries
+    // covering [0, L_g) of every grid, built on the device from the same L the
+    // host counts here
+    int64_t tiles = 0;
+    if ((int)p->h_L.size() != p->G) return cudaErrorInvalidValue;
+    for (int64_t L : p->h_L) {
+        if (L < 1 || L > p->M) return cudaErrorInvalidValue;
+        tiles += (L + TILE - 1) / TILE;
+    }
+    if (tiles < 1 || tiles > INT32_MAX) return cudaErrorInvalidValue;
+    // the tile table (12 int64 bounds per entry, at most 96 M / TILE bytes per
+    // grid), the list's grid starts and entries live in the second grid
     // buffer, which is free until the transform
     static_assert(96 / TILE < 8, "the tile table must fit the second grid buffer");
-    if (tiles * 96 > p->M * (int64_t)sizeof(cpx<T>)) return cudaErrorInvalidValue;
+    const size_t need = (size_t)tiles * 96 + (size_t)(p->G + 1) * 8 + (size_t)tiles * 4;
+    if (need > (size_t)p->G * (size_t)p->M * sizeof(cpx<T>)) return cudaErrorInvalidValue;
     int64_t* rngtab = reinterpret_cast<int64_t*>(p->d_grid[1]);
-    dim3 gt((unsigned)((tiles * 12 + 127) / 128), (unsigned)p->G);
-    k_tile_ranges<TILE><<<gt, 128, 0, s>>>(p->d_key, p->n, p->M, p->w, p->npk, p->H, p->w_p, p->d_L,
-                                           p->d_slot_soff, p->d_slot_n, tiles, rngtab);
-    dim3 grid((unsigned)tiles, (unsigned)p->G);
-    k_spread<T, TILE, NT, CAP><<<grid, NT, 0, s>>>(
+    int64_t* tfirst = rngtab + tiles * 12;
+    int32_t* tgrid = reinterpret_cast<int32_t*>(tfirst + p->G + 1);
+    k_tile_list<TILE><<<1, 1024, 0, s>>>(p->d_L, p->G, tfirst);
+    k_tile_fill<<<(unsigned)((tiles + 255) / 256), 256, 0, s>>>(tfirst, p->G, tiles, tgrid);
+    const unsigned gt = (unsigned)((tiles * 12 + 127) / 128);
+    k_tile_ranges<TILE><<<gt, 128, 0, s>>>(p->d_key, p->n, p->M, p->w, p->npk, p->H, p->w_p, tfirst,
+                                           tgrid, p->d_slot_soff, p->d_slot_n, tiles, rngtab);
+    k_spread<T, TILE, NT, CAP><<<(unsigned)tiles, NT, 0, s>>>(
         p->d_key, (const T*)p->d_dlt, (const cpx<T>*)p->d_cs, p->n, p->M, p->w, (T)p->beta,
-        p->npk, p->H, p->w_p, (T)p->beta_p, p->d_L, (cpx<T>*)p->d_grid[0], p->M, p->d_slot_soff,
-        p->d_slot_n, rngtab);
+        p->npk, p->H, p->w_p, (T)p->beta_p, tfirst, tgrid, (cpx<T>*)p->d_grid[0], p->M,
+        p->d_slot_soff, p->d_slot_n, rngtab);
     return cudaGetLastError();
 }
 
