@@ -156,7 +156,7 @@ FC2_D double2 d_phasor(uint64_t u, const double2* t1, const double2* t2) {
 // exact and associative, so the result does not depend on the order and the
 // only errors are the per-term ones (phasor, product, block, and the
 // conversion's rounding at 2^-s).
-constexpr int FX_BLOCK = 4;
+constexpr int FX_BLOCK = 8;
 
 // Scale exponent s for sums of at most nterm terms of modulus <= vmax: the
 // scaled terms add up to less than 2^61 in modulus, and so does every partial
