@@ -670,7 +670,7 @@ def run_profile(args):
     if args.workload == "large":
         c = synth.large_curve(N=args.N) if args.N else synth.large_curve()
     else:
-        c = synth.long_curve(seed=2, H=args.H or 6)
+        c = synth.long_curve(seed=2, H=args.H or 6, **({"N": args.N} if args.N else {}))
     dev = torch.device("cuda", 0)
     out = torch.empty((c.H, c.N), dtype=torch.float64, device=dev)
     with _fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, c.oversample, "mixed",
