@@ -902,6 +902,64 @@ constexpr int BHM = 8;  // harmonic capacity of the batched kernels
 
 }  // namespace
 
+// Pinned host buffers of the batched calls (the chunk tables' staging and the
+// mapped moments), kept for the process: pinning host memory costs
+// milliseconds per call on this platform.  A call takes a free pair large
+// enough or allocates one, and returns it at the end; concurrent calls get
+// different pairs.
+struct PinnedPair {
+    char* stage = nullptr;
+    size_t stage_bytes = 0;
+    char* map = nullptr;
+    size_t map_bytes = 0;
+};
+static std::mutex g_pin_mu;
+static std::vector<PinnedPair> g_pin_free;
+
+static bool pinned_acquire(size_t stage_bytes, size_t map_bytes, PinnedPair* out) {
+    {
+        std::lock_guard<std::mutex> lk(g_pin_mu);
+        for (size_t i = 0; i < g_pin_free.size(); ++i)
+            if (g_pin_free[i].stage_bytes >= stage_bytes && g_pin_free[i].map_bytes >= map_bytes) {
+                *out = g_pin_free[i];
+                g_pin_free.erase(g_pin_free.begin() + (long)i);
+                return true;
+            }
+    }
+    PinnedPair p;
+    p.stage_bytes = stage_bytes;
+    p.map_bytes = map_bytes;
+    if (cudaHostAlloc((void**)&p.stage, stage_bytes, cudaHostAllocPortable) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cudaHostAlloc((void**)&p.map, map_bytes, cudaHostAllocMapped | cudaHostAllocPortable) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(p.stage);
+        return false;
+    }
+    *out = p;
+    return true;
+}
+
+static void pinned_release(const PinnedPair& p) {
+    if (!p.stage && !p.map) return;
+    std::lock_guard<std::mutex> lk(g_pin_mu);
+    g_pin_free.push_back(p);
+    // keep a few pairs; free the smallest beyond that
+    while (g_pin_free.size() > 4) {
+        size_t k = 0;
+        for (size_t i = 1; i < g_pin_free.size(); ++i)
+            if (g_pin_free[i].stage_bytes + g_pin_free[i].map_bytes <
+                g_pin_free[k].stage_bytes + g_pin_free[k].map_bytes)
+                k = i;
+        cudaFreeHost(g_pin_free[k].stage);
+        cudaFreeHost(g_pin_free[k].map);
+        g_pin_free.erase(g_pin_free.begin() + (long)k);
+    }
+}
+
 // The launch configuration of a chunk: the transform plan and family, the
 // spreading tile, the assembly block and the exact-sum work item.
 struct BatchConfig {
@@ -977,6 +1035,7 @@ struct Batch {
     int64_t* goff = nullptr; size_t cgoff = 0;
     // pinned staging of the chunk tables, two halves used by alternate chunks
     // (a half is refilled once the copies of the chunk two before are done)
+    PinnedPair pins;  // the staging and mapped buffers (returned to the cache at the end)
     char* stage = nullptr;
     size_t stage_half = 0;
     cudaEvent_t ev_tab[2] = {nullptr, nullptr};
@@ -1028,7 +1087,8 @@ struct Batch {
             ev_graph[i] = ev_tab[i] = nullptr;
         }
         release(scal_all, s); release(goff, s);
-        if (stage) cudaFreeHost(stage);
+        pinned_release(pins);
+        pins = PinnedPair();
         stage = nullptr;
         for (auto& e : ev)
             if (e) { cudaEventDestroy(e); e = nullptr; }
@@ -1039,7 +1099,6 @@ struct Batch {
         }
         if (cs2) cudaStreamDestroy(cs2);
         cs2 = nullptr;
-        if (hmap) cudaFreeHost(hmap);
         hmap = hmap_dev = nullptr;
     }
 };
@@ -1673,6 +1732,7 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     // its stage events can be read before the next chunk records them again.
     // Every curve's peak records stay on the device until the end.
     const bool copy_out = !b.timing && dchi2 && !out_dev;
+    const auto tsetup = now();
     {
         bool good = true;
         if (copy_out) {
@@ -1701,15 +1761,20 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
         }
         b.stage_half = (half + 255) & ~(size_t)255;
         const size_t mbytes = (size_t)C * SC_COUNT * 8 + 64;
-        if (cudaHostAlloc((void**)&b.stage, 2 * b.stage_half, cudaHostAllocDefault) != cudaSuccess ||
-            cudaHostAlloc((void**)&b.hmap, mbytes, cudaHostAllocMapped) != cudaSuccess ||
-            cudaHostGetDevicePointer((void**)&b.hmap_dev, b.hmap, 0) != cudaSuccess) {
+        bool got = pinned_acquire(2 * b.stage_half, mbytes, &b.pins);
+        if (got) {
+            b.stage = b.pins.stage;
+            b.hmap = b.pins.map;
+            got = cudaHostGetDevicePointer((void**)&b.hmap_dev, b.hmap, 0) == cudaSuccess;
+        }
+        if (!got) {
             cudaGetLastError();
             b.free_all();
             if (b.own_stream) cudaStreamDestroy(s);
             return FC2_ERR_OOM;
         }
     }
+    b.phase_ms[1] += ms_since(tsetup, now());  // streams, events, pinned buffers
     // configuration: 0 fixed (autotune -1, or a transform family requested),
     // 1 the tuning table with tuning on a miss (autotune 0), 2 tuning anew (1)
     const int tune_mode = (opt.autotune < 0 || opt.fft_kernel != 0) ? 0 : (opt.autotune == 1 ? 2 : 1);
