@@ -352,3 +352,36 @@ def test_batched_peaks_are_oracle_local_maxima(fc2, oracle_mod):
         lm.sort(key=lambda v: (-v[0], v[1]))
         for (v_or, j_or), p in zip(lm[:K], recs):
             assert j_or == p["j"] or abs(v_or - row[int(p["j"])]) <= tol, (c, j_or, p["j"])
+
+
+def test_concurrent_batched_calls_from_two_threads(fc2):
+    """Two host threads running batched calls at the same time (each on its
+    own stream, through the process-wide tuning table, pinned-buffer cache,
+    table caches and device pool) give the same bits as the calls run one
+    after the other."""
+    import threading
+    cases = [small_survey(C=6, N=1 << 13, seed=41), small_survey(C=9, N=1 << 14, seed=43)]
+    ref = [fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df, b.N, 2,
+                               "mixed", top_k=4)[:2] for b in cases]
+    got = [None, None]
+    errs = []
+
+    def run(i):
+        try:
+            b = cases[i]
+            for _ in range(3):
+                got[i] = fc2.execute_batched(b.offsets, b.t, b.x, b.sigma, b.H, b.f_min, b.df,
+                                             b.N, 2, "mixed", top_k=4)[:2]
+        except Exception as e:  # noqa: BLE001 - reported below
+            errs.append(e)
+
+    th = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    for (o_ref, p_ref), (o, p) in zip(ref, got):
+        np.testing.assert_array_equal(o, o_ref)
+        np.testing.assert_array_equal(p.records["j"], p_ref.records["j"])
+        np.testing.assert_array_equal(p.records["dchi2"], p_ref.records["dchi2"])
