@@ -191,6 +191,14 @@ void fc2_debug_batch_force_plan(const int* rs, int n, int family);
  * read again at the next lookup. */
 void fc2_debug_batch_forget_tuning(void);
 
+/* on != 0: every spreading tile goes to the general kernel (running sums of
+ * all of a tile's cells kept across sample batches and sample sets), also the
+ * tiles of one sample set that fit one staging batch, which by default the
+ * single-batch kernel computes cell by cell.  Both sum each cell's samples in
+ * the same order with the same arithmetic.  0 restores the default.
+ * Process-wide; for tests. */
+void fc2_debug_spread_force_general(int on);
+
 /* Stage timing of p on (enable != 0) or off; resets the accumulated times.
  * While on, each execute records CUDA events on the plan's stream around
  * (0) phase reduction and spreading, (1) FFT passes, (2) assembly and solve,

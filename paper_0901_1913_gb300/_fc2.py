@@ -176,6 +176,8 @@ def load():
         lib.fc2_debug_batch_force_plan.restype = None
         lib.fc2_debug_batch_forget_tuning.argtypes = []
         lib.fc2_debug_batch_forget_tuning.restype = None
+        lib.fc2_debug_spread_force_general.argtypes = [i32]
+        lib.fc2_debug_spread_force_general.restype = None
         _lib = lib
         return lib
 
@@ -419,6 +421,13 @@ def batch_force_plan(radices=(), family=1):
 def batch_forget_tuning():
     """Empty the process's tuning table (the cache file is read again)."""
     load().fc2_debug_batch_forget_tuning()
+
+
+def spread_force_general(on=True):
+    """Send every spreading tile to the general kernel (True) or restore the
+    default, where tiles of one sample set that fit one staging batch go to
+    the single-batch kernel (False)."""
+    load().fc2_debug_spread_force_general(int(bool(on)))
 
 
 def trim_device_memory(device=0):

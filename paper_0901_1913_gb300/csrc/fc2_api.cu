@@ -900,6 +900,7 @@ void fc2_debug_batch_force_plan(const int* rs, int n, int family) {
 /* Forget the batched path's tuning table of this process (the cache file is
  * read again at the next lookup). */
 void fc2_debug_batch_forget_tuning(void) { fc2::forget_batch_tuning(); }
+void fc2_debug_spread_force_general(int on) { fc2::force_spread_general(on); }
 
 void fc2_debug_batch_stage_ms(double* out6) {
     if (out6)

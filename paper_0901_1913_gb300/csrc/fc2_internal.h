@@ -217,6 +217,8 @@ cudaError_t launch_gather_sorted(const double* t, const double* x, const double*
 cudaError_t launch_phase(fc2_plan_s* p, cudaStream_t s);
 cudaError_t sort_wrapping_keys(fc2_plan_s* p, cudaStream_t s);
 cudaError_t launch_spread(fc2_plan_s* p, cudaStream_t s);
+void force_spread_general(int on);  // every tile to the general spreading kernel (tests)
+int device_sm_count();
 // The paper's nearest-lower-cell binning into grid 0 (paper gridding).
 cudaError_t launch_bin(fc2_plan_s* p, cudaStream_t s);
 // Polynomial detrending of x (degree D <= 3) into xo; scal holds T0 and max tau.

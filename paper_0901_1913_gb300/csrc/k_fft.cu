@@ -1517,7 +1517,8 @@ static int current_device() {
     return dev;
 }
 
-static int device_sm_count() {
+// SMs of the current device (queried once per device).
+int device_sm_count() {
     const int dev = current_device();
     std::lock_guard<std::mutex> lk(g_launch_mu);
     auto it = g_sm_count.find(dev);

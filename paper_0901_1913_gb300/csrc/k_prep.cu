@@ -856,7 +856,9 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
                                                cpx<T>* __restrict__ grid, int64_t gstride,
                                                const int64_t* __restrict__ slot_soff,
                                                const int64_t* __restrict__ slot_n,
-                                               const int64_t* __restrict__ rngtab) {
+                                               const int64_t* __restrict__ rngtab,
+                                               const int32_t* __restrict__ tlist,
+                                               const int32_t* __restrict__ tlist_count) {
     constexpr int PER = TILE / NT;
     // cumulative key counts of the staged samples: cum[i] = samples with
     // tile-relative key <= i - w (keys lie in [-w + 1, TILE)), so the samples of
@@ -868,7 +870,11 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
     __shared__ cpx<T> sc[CAP];
     __shared__ int32_t cum[PCUM * NT];
     __shared__ int32_t wtot[NT / 32];
-    const int64_t et = blockIdx.x;  // list entry: an occupied tile
+    // every occupied tile (one per CTA), or the tiles listed by the single-batch
+    // kernel (CTAs walk the list)
+    const int64_t nlist = tlist ? (int64_t)*tlist_count : 1;
+    for (int64_t li = tlist ? blockIdx.x : 0; li < nlist; li += gridDim.x) {
+    const int64_t et = tlist ? (int64_t)tlist[li] : (int64_t)blockIdx.x;
     const int g = tgrid[et];
     const int64_t a = (et - tfirst[g]) * TILE;
     const int64_t* rt = rngtab + et * 12;
@@ -961,9 +967,112 @@ __global__ void __launch_bounds__(NT) k_spread(const int32_t* __restrict__ key,
         const int l = threadIdx.x + q * NT;
         gg[l] = acc[q].val();
     }
+    }
 }
 
+// The same sums for a tile of one sample set whose samples fit one staging
+// batch (all tiles of an unpacked grid but the densest): each cell is summed
+// and stored in turn, so a thread holds one running sum instead of one per
+// cell, and with fewer registers and a smaller staging buffer more CTAs fit
+// an SM (the kernel waits mostly on its loads and barriers).  Other tiles are
+// appended to `tlist` for the general kernel.  A cell's samples and their
+// order, and the arithmetic, are the general kernel's.
 template <typename T, int TILE, int NT, int CAP>
+__global__ void __launch_bounds__(NT, 2048 / NT) k_spread1(const int32_t* __restrict__ key,
+                                                           const T* __restrict__ dlt,
+                                                           const cpx<T>* __restrict__ cs,
+                                                           int64_t n_all, int64_t M, int w, T beta,
+                                                           const int64_t* __restrict__ tfirst,
+                                                           const int32_t* __restrict__ tgrid,
+                                                           cpx<T>* __restrict__ grid,
+                                                           int64_t gstride,
+                                                           const int64_t* __restrict__ slot_soff,
+                                                           const int64_t* __restrict__ rngtab,
+                                                           int32_t* __restrict__ tlist,
+                                                           int32_t* __restrict__ tlist_count) {
+    constexpr int PER = TILE / NT;
+    constexpr int PCUM = (TILE + 32 + NT - 1) / NT;
+    __shared__ int32_t sk[CAP];
+    __shared__ T sd[CAP];
+    __shared__ cpx<T> sc[CAP];
+    __shared__ int32_t cum[PCUM * NT];
+    __shared__ int32_t wtot[NT / 32];
+    const int64_t et = blockIdx.x;
+    const int g = tgrid[et];
+    const int64_t a = (et - tfirst[g]) * TILE;
+    const int64_t* rt = rngtab + et * 12;
+    int64_t rng[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) rng[q] = rt[q];
+    const int64_t c0 = rng[1] - rng[0], c1 = rng[3] - rng[2], c2 = rng[5] - rng[4];
+    const int64_t total = c0 + c1 + c2;
+    if (total > CAP) {
+        if (threadIdx.x == 0) tlist[atomicAdd(tlist_count, 1)] = (int32_t)et;
+        return;
+    }
+    const int cnt = (int)total;
+    const int64_t so = slot_soff ? slot_soff[g] : (int64_t)g * n_all;
+    const int32_t* kg = key + so;
+    const T* dg = dlt + so;
+    const cpx<T>* cg = cs + so;
+#pragma unroll
+    for (int i = 0; i < PCUM; ++i) cum[threadIdx.x * PCUM + i] = 0;
+    for (int e = threadIdx.x; e < cnt; e += NT) {
+        int64_t src, shv;
+        if (e < c0) { src = rng[0] + e; shv = -M; }
+        else if (e < c0 + c1) { src = rng[2] + (e - c0); shv = 0; }
+        else { src = rng[4] + (e - c0 - c1); shv = M; }
+        sk[e] = (int32_t)((int64_t)kg[src] + shv - a);
+        sd[e] = dg[src];
+        sc[e] = cg[src];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += NT) atomicAdd(&cum[sk[e] + w], 1);
+    __syncthreads();
+    {
+        int32_t run[PCUM];
+        int32_t t = 0;
+#pragma unroll
+        for (int i = 0; i < PCUM; ++i) {
+            t += cum[threadIdx.x * PCUM + i];
+            run[i] = t;
+        }
+        const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+        int32_t incl = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wtot[wi] = incl;
+        __syncthreads();
+        int32_t before = incl - t;
+        for (int k = 0; k < wi; ++k) before += wtot[k];
+#pragma unroll
+        for (int i = 0; i < PCUM; ++i) cum[threadIdx.x * PCUM + i] = before + run[i];
+    }
+    __syncthreads();
+    const T ihw = (T)2 / (T)w;
+    const T hw = (T)0.5 * (T)w;
+    cpx<T>* gg = grid + (int64_t)g * gstride + a;
+    for (int q = 0; q < PER; ++q) {
+        const int l = threadIdx.x + q * NT;
+        Acc<T> acc;
+        acc.init();
+        const int e1 = cum[l + w];
+        for (int e = cum[l]; e < e1; ++e) {
+            T z = (T)(l - sk[e]) + (T)1 - sd[e] - hw;
+            T ph = es_kernel<T>(z, ihw, beta);
+            acc.add(sc[e].x * ph, sc[e].y * ph);
+        }
+        gg[l] = acc.val();
+    }
+}
+
+// Tests may send every tile to the general kernel (a comparison of the two).
+static int g_spread_general_only = 0;
+
+template <typename T, int TILE, int NT, int CAP, int CAP1>
 static cudaError_t spread_tiles(fc2_plan_s* p, cudaStream_t s) {
     // only the occupied tiles are launched: the list of (grid, tile) entries
     // covering [0, L_g) of every grid, built on the device from the same L the
@@ -979,7 +1088,7 @@ static cudaError_t spread_tiles(fc2_plan_s* p, cudaStream_t s) {
     // grid), the list's grid starts and entries live in the second grid
     // buffer, which is free until the transform
     static_assert(96 / TILE < 8, "the tile table must fit the second grid buffer");
-    const size_t need = (size_t)tiles * 96 + (size_t)(p->G + 1) * 8 + (size_t)tiles * 4;
+    const size_t need = (size_t)tiles * 96 + (size_t)(p->G + 1) * 8 + (size_t)tiles * 8 + 16;
     if (need > (size_t)p->G * (size_t)p->M * sizeof(cpx<T>)) return cudaErrorInvalidValue;
     int64_t* rngtab = reinterpret_cast<int64_t*>(p->d_grid[1]);
     int64_t* tfirst = rngtab + tiles * 12;
@@ -989,10 +1098,27 @@ static cudaError_t spread_tiles(fc2_plan_s* p, cudaStream_t s) {
     const unsigned gt = (unsigned)((tiles * 12 + 127) / 128);
     k_tile_ranges<TILE><<<gt, 128, 0, s>>>(p->d_key, p->n, p->M, p->w, p->npk, p->H, p->w_p, tfirst,
                                            tgrid, p->d_slot_soff, p->d_slot_n, tiles, rngtab);
+    if (p->npk == 0 && !g_spread_general_only) {
+        // one sample set per grid: tiles that fit one batch in the single-batch
+        // kernel, the rest listed (after the tile grids) for the general kernel
+        int32_t* tlist = tgrid + tiles;
+        int32_t* tcount = tlist + tiles;
+        cudaError_t e = cudaMemsetAsync(tcount, 0, sizeof(int32_t), s);
+        if (e != cudaSuccess) return e;
+        k_spread1<T, TILE, NT, CAP1><<<(unsigned)tiles, NT, 0, s>>>(
+            p->d_key, (const T*)p->d_dlt, (const cpx<T>*)p->d_cs, p->n, p->M, p->w, (T)p->beta,
+            tfirst, tgrid, (cpx<T>*)p->d_grid[0], p->M, p->d_slot_soff, rngtab, tlist, tcount);
+        const unsigned gb = (unsigned)std::min<int64_t>(tiles, (int64_t)device_sm_count() * 2);
+        k_spread<T, TILE, NT, CAP><<<gb, NT, 0, s>>>(
+            p->d_key, (const T*)p->d_dlt, (const cpx<T>*)p->d_cs, p->n, p->M, p->w, (T)p->beta,
+            p->npk, p->H, p->w_p, (T)p->beta_p, tfirst, tgrid, (cpx<T>*)p->d_grid[0], p->M,
+            p->d_slot_soff, p->d_slot_n, rngtab, tlist, tcount);
+        return cudaGetLastError();
+    }
     k_spread<T, TILE, NT, CAP><<<(unsigned)tiles, NT, 0, s>>>(
         p->d_key, (const T*)p->d_dlt, (const cpx<T>*)p->d_cs, p->n, p->M, p->w, (T)p->beta,
         p->npk, p->H, p->w_p, (T)p->beta_p, tfirst, tgrid, (cpx<T>*)p->d_grid[0], p->M,
-        p->d_slot_soff, p->d_slot_n, rngtab);
+        p->d_slot_soff, p->d_slot_n, rngtab, nullptr, nullptr);
     return cudaGetLastError();
 }
 
@@ -1002,10 +1128,10 @@ static cudaError_t spread_impl(fc2_plan_s* p, cudaStream_t s) {
     // the batched path may choose another tile width (its autotuner)
     const int tile = spread_tile_of(p->M, p->spread_tile);
     switch (tile) {
-        case 2048: return spread_tiles<T, 2048, 256, 2048>(p, s);
-        case 1024: return spread_tiles<T, 1024, 256, 2048>(p, s);
-        case 512: return spread_tiles<T, 512, 128, 2048>(p, s);
-        default: return spread_tiles<T, 128, 128, 1024>(p, s);
+        case 2048: return spread_tiles<T, 2048, 256, 2048, 1024>(p, s);
+        case 1024: return spread_tiles<T, 1024, 256, 2048, 1024>(p, s);
+        case 512: return spread_tiles<T, 512, 128, 2048, 512>(p, s);
+        default: return spread_tiles<T, 128, 128, 1024, 256>(p, s);
     }
 }
 
@@ -1058,5 +1184,7 @@ cudaError_t launch_bin(fc2_plan_s* p, cudaStream_t s) {
 cudaError_t launch_spread(fc2_plan_s* p, cudaStream_t s) {
     return p->fp64 ? spread_impl<double>(p, s) : spread_impl<float>(p, s);
 }
+
+void force_spread_general(int on) { g_spread_general_only = on ? 1 : 0; }
 
 }  // namespace fc2
