@@ -1593,6 +1593,8 @@ fc2_status batched_execute(int64_t C, const int64_t* offsets, const double* t, c
     if (opt.prec != FC2_PREC_FP64 && opt.prec != FC2_PREC_MIXED) return FC2_ERR_INVALID_ARG;
     if (opt.top_k < 0 || opt.top_k > 64) return FC2_ERR_INVALID_ARG;
     if (opt.fft_kernel < 0 || opt.fft_kernel > 5) return FC2_ERR_INVALID_ARG;
+    if (opt.kernel_width != 0 && (opt.kernel_width < 2 || opt.kernel_width > 16))
+        return FC2_ERR_INVALID_ARG;  // (the spreading kernels' key tables assume w <= 32)
     if (opt.autotune < -1 || opt.autotune > 1) return FC2_ERR_INVALID_ARG;
     if (opt.gridding < 0 || opt.gridding > 1) return FC2_ERR_INVALID_ARG;
     if (opt.gridding == 1) return FC2_ERR_UNSUPPORTED;

@@ -108,6 +108,24 @@ def test_validation_rejects_bad_arguments(lib, field, value):
     assert not h.value
 
 
+@pytest.mark.parametrize("kw", [dict(kernel_width=1), dict(kernel_width=17),
+                                dict(kernel_width=40), dict(top_k=65), dict(oversample=1)])
+def test_batched_validation_rejects_bad_options(lib, kw):
+    """The batched entry point validates its options on the host before any
+    device call (a spreading width beyond 16 cells would overrun the
+    spreading kernels' key tables)."""
+    from paper_0901_1913_gb300 import _fc2
+    t = np.linspace(0, 10, 50)
+    x = np.sin(t)
+    s = np.full(50, 0.1)
+    args = dict(oversample=2)
+    args.update(kw)
+    with pytest.raises(_fc2.Fc2Error) as ei:
+        _fc2.execute_batched(np.array([0, 50]), t, x, s, np.array([3]), np.array([0.1]),
+                             np.array([0.01]), np.array([100]), prec="mixed", **args)
+    assert ei.value.code == _fc2.FC2_ERR_INVALID_ARG
+
+
 def test_null_pointers_rejected(lib):
     from paper_0901_1913_gb300 import _fc2
     h = ctypes.c_void_p()
