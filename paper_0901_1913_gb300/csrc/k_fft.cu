@@ -949,6 +949,12 @@ FC2_D void dft16_centred(cpx<T>* v) {
     for (int k = 4; k < 8; ++k) v[k + 8] = sub(e[k], k == 4 ? mul_i(o[4]) : mul(o[k], root16<T>(k)));
 }
 
+// First-stage radix bits of the bulk-copy pass: radix 32 for 2^9 passes (two
+// stages, 32 x 16: the first with half the threads, one butterfly of 32
+// each), else as the other shared-memory stages (2^9 would otherwise take
+// 2 x 16 x 16, one more pass through shared memory).
+FC2_HD constexpr int bulk_stage1_bits(int LOGR) { return LOGR == 9 ? 5 : stage_bits(LOGR, 0); }
+
 template <int LOGR>
 constexpr size_t pass_tma_smem() {
     return (size_t)(2 * (1 << PT_LOGE) + phys((1 << PT_LOGE) - 1) + 1 + stage_tw_size(LOGR)) *
@@ -972,11 +978,15 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
     constexpr int NWK = phys(E - 1) + 1;
     static_assert(LOGR >= 8 && LOGR <= 12, "radix 2^8..2^12");
     // stage 1 (radix Q1), middle stages of radix 16, last stage of radix 16
-    constexpr int QB1 = stage_bits(LOGR, 0), Q1 = 1 << QB1;
-    constexpr int PER1 = ((R / Q1) * J) / NT;
+    constexpr int QB1 = bulk_stage1_bits(LOGR), Q1 = 1 << QB1;
+    constexpr int NB1 = (R / Q1) * J;                      // stage-1 butterflies
+    constexpr bool HALF1 = NB1 < NT;                       // threads tid >= NB1 idle in stage 1
+    constexpr int PER1 = HALF1 ? 1 : NB1 / NT;
     constexpr int DL = LOGR - 4, NSL = 1 << DL;            // last stage: Ns = R / 16
     constexpr int TOFF_L = NST - 15 * NSL;                 // its twiddle table
-    static_assert(PER1 * NT == (R / Q1) * J, "stage-1 butterflies must divide evenly");
+    static_assert(HALF1 ? (NT % NB1 == 0 && Q1 == 32) : PER1 * NT == NB1,
+                  "stage-1 butterflies must divide evenly");
+    static_assert(Q1 <= 32, "stage-1 radix");
     static_assert(NSL * J == NT, "one last-stage butterfly per thread");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* ib = reinterpret_cast<cpx<T>*>(smem_raw);  // [2][E] input buffers
@@ -1024,7 +1034,11 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
     // and tile, the second factor (and the step w^{(R/Q1) jm 2^lts}) one lookup per
     // (column, b) and tile, kept in shared memory -- instead of two lookups per
     // butterfly.
-    constexpr int TW1 = PER1 + 1;
+    // (a radix-32 stage 1: per column the powers step^q, q = 1, 2, 3, 4, 8,
+    // 12, 16 of step = w^{(R/Q1) jm 2^lts}, each a table lookup; element k's
+    // factor is t0 step^(k mod 4) step^(4 ((k >> 2) mod 4)) step^(16 (k >> 4)),
+    // three products of looked-up values)
+    constexpr int TW1 = HALF1 ? 7 : PER1 + 1;
     __shared__ cpx<T> tw1[J * TW1];
     cpx<T> t0 = mk<T>(1.f, 0.f);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
@@ -1039,7 +1053,9 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
             for (int q = tid; q < J * TW1; q += NT) {
                 const int cj = q / TW1, bb = q - cj * TW1;
                 const int jm = (j0 + cj) & nsg_mask;
-                const int64_t e = (bb < PER1) ? (int64_t)bb * (R / 16) * jm : (int64_t)(R / Q1) * jm;
+                int64_t e;
+                if constexpr (HALF1) e = (int64_t)(R / Q1) * jm * (bb < 3 ? bb + 1 : 4 * (bb - 2));
+                else e = (bb < PER1) ? (int64_t)bb * (R / 16) * jm : (int64_t)(R / Q1) * jm;
                 tw1[q] = twiddle(twlo, twhi, a.tws, e << lts);
             }
             const int jm = (j0 + (tid & (J - 1))) & nsg_mask;
@@ -1071,6 +1087,7 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
 #pragma unroll
             for (int b = 0; b < PER1; ++b) {
                 const int bi = tid + b * NT;
+                if (HALF1 && bi >= NB1) break;
                 const int jj = bi & (J - 1), pp = bi >> LOGJ;
                 cpx<T> v[Q1];
                 if (!bulk) {
@@ -1083,7 +1100,23 @@ __global__ void __launch_bounds__(PT_NT, 1) k_fft_pass_tma(const cpx<float>* __r
 #pragma unroll
                     for (int k = 0; k < Q1; ++k) v[k] = src[(pp + k * (R / Q1)) * J + jj];
                     const int jm = (j0 + jj) & nsg_mask;
-                    if (logNs > 0 && jm != 0) {
+                    if constexpr (HALF1) {
+                        if (logNs > 0 && jm != 0) {
+                            // w_M^{(pp + k R/Q1) jm 2^lts} = t0 step^(k & 3) step^(k & 12) step^(k & 16)
+                            const cpx<T>* sq = tw1 + jj * TW1;  // step^1, 2, 3, 4, 8, 12, 16
+                            cpx<T> lo[4];
+                            lo[0] = t0;
+#pragma unroll
+                            for (int q = 1; q < 4; ++q) lo[q] = mul(t0, sq[q - 1]);
+#pragma unroll
+                            for (int k = 0; k < Q1; ++k) {
+                                cpx<T> w = lo[k & 3];
+                                if (((k >> 2) & 3) != 0) w = mul(w, sq[2 + ((k >> 2) & 3)]);
+                                if ((k >> 4) != 0) w = mul(w, sq[6]);
+                                v[k] = mul(v[k], w);
+                            }
+                        }
+                    } else if (logNs > 0 && jm != 0) {
                         // w_M^{(pp + k R/Q1) jm 2^lts} = base * step^k, step^k = lo[k & 3] hi[k >> 2]
                         const cpx<T> base = mul(t0, tw1[jj * TW1 + b]);
                         const cpx<T> st1 = tw1[jj * TW1 + PER1];
@@ -1752,6 +1785,9 @@ static int replay_plan(int logM, bool fp64, int family, const std::vector<int>& 
                     qmax = std::max<int64_t>(((RB - 1) * jmax) << lts, ((7 * RB) * jmax) << lts);
                     if (QA > 8)
                         qmax = std::max<int64_t>(qmax, ((8 * RB * ((QA / 8) - 1)) * jmax) << lts);
+                } else if (sh.kind == PK_BULK && bulk_stage1_bits(LOGR) == 5) {
+                    // radix-32 stage 1: t0 up to (R/16 - 1) jm, steps (R/32) jm x 1, 4, 16
+                    qmax = std::max<int64_t>(((R / 16 - 1) * jmax) << lts, ((R / 32) * 16 * jmax) << lts);
                 } else {
                     const int Q1 = 1 << stage_bits(LOGR, 0);
                     qmax = std::max<int64_t>(((R / Q1 - 1) * jmax) << lts, ((R / Q1) * jmax) << lts);

@@ -62,12 +62,12 @@ def test_packed_spectra_match_direct_sums(fc2, oracle_mod):
 @pytest.mark.parametrize("fft_kernel,fft_group", [("r64", 0), ("r16", 0), ("bulk", 0),
                                                   ("r32", 0), ("r32x", 0), ("r64", 1),
                                                   ("bulk", 2)])
-@pytest.mark.parametrize("logN,oversample", [(14, 4), (19, 4), (22, 4), (19, 2)])
+@pytest.mark.parametrize("logN,oversample", [(14, 4), (19, 4), (22, 4), (19, 2), (18, 2)])
 def test_fft_kernel_families_match_direct_sums(fc2, oracle_mod, fft_kernel, fft_group, logN,
                                                oversample):
     """Every float transform kernel family, on pass plans (8, 8), (11, 10) and
-    (12, 12) with packed grids and (10, 10) with unpacked ones, gives spectra
-    equal to the direct sums of Eq. eqPQ."""
+    (12, 12) with packed grids and (10, 10) and (10, 9) with unpacked ones,
+    gives spectra equal to the direct sums of Eq. eqPQ."""
     c = synth.long_curve(n=3000, N=1 << logN)
     with fc2.Plan(c.t, c.x, c.sigma, c.H, c.f_min, c.df, c.N, oversample, "mixed",
                   fft_kernel=fft_kernel, fft_group=fft_group) as p:
