@@ -160,6 +160,11 @@ void fc2_debug_batch_stage_ms(double* out6);
  * FC2_ERR_INVALID_ARG for bad arguments, FC2_ERR_CUDA on a CUDA failure. */
 fc2_status fc2_debug_phasor(const uint64_t* u, int64_t n, float* out4);
 
+/* The same for the phasor of the fix-up's last tier (sums exact in fixed
+ * point): one double-float table entry e^{2 pi i m / 65536} for the top 16
+ * bits, then the same small rotation.  Same arguments and errors. */
+fc2_status fc2_debug_phasor16(const uint64_t* u, int64_t n, float* out4);
+
 /* Launch configuration of the last fc2_execute_batched call's last chunk
  * (out12): [0] source (0 fixed, 1 tuning table or cache file, 2 tuned in the
  * call), [1] transform family (0 radix-16 in shared memory, 1 two register

@@ -302,7 +302,7 @@ fc2_status fc2_plan_create(const double* t, const double* x, const double* sigma
     g.ok(dalloc(&p->d_part, exact_scratch_bytes(n, H, p->exact_cap), s)) &&
         g.ok(dalloc(&p->d_phA, (size_t)n * 8, s)) && g.ok(dalloc(&p->d_phB, (size_t)n * 8, s)) &&
         g.ok(dalloc(&p->d_wq32, (size_t)n * 8, s)) && g.ok(dalloc(&p->d_wp32, (size_t)n * 8, s)) &&
-        g.ok(dalloc(&p->d_dftab, 2 * 512 * 16, s));
+        g.ok(dalloc(&p->d_dftab, DFTAB_BYTES, s));
     if (g.e != cudaSuccess) {
         fc2_status st = map_err(g.e);
         free_plan_memory(p);
@@ -846,7 +846,14 @@ fc2_status fc2_debug_exact_bins(fc2_plan p, const int64_t* bins, int64_t nb, int
  * tests of its accuracy.  n in 1..2^24. */
 fc2_status fc2_debug_phasor(const uint64_t* u, int64_t n, float* out4) {
     if (!u || !out4 || n < 1 || n > (1 << 24)) return FC2_ERR_INVALID_ARG;
-    return fc2::debug_phasor(u, n, out4) == cudaSuccess ? FC2_OK : FC2_ERR_CUDA;
+    return fc2::debug_phasor(u, n, 0, out4) == cudaSuccess ? FC2_OK : FC2_ERR_CUDA;
+}
+
+/* The last tier's phasor (one 65536-entry table, then the small rotation),
+ * as fc2_debug_phasor. */
+fc2_status fc2_debug_phasor16(const uint64_t* u, int64_t n, float* out4) {
+    if (!u || !out4 || n < 1 || n > (1 << 24)) return FC2_ERR_INVALID_ARG;
+    return fc2::debug_phasor(u, n, 1, out4) == cudaSuccess ? FC2_OK : FC2_ERR_CUDA;
 }
 
 /* Kernels launched by the last fc2_execute_batched call of this process. */

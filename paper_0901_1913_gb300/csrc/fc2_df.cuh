@@ -133,6 +133,23 @@ FC2_D dfc df_phasor(uint64_t u, const dfc* t1, const dfc* t2) {
     return dfc_rot_small(dfc_mul(t1[a], t2[b]), eps, s);
 }
 
+// e^{2 pi i u 2^-64} for a 64-bit phase u, to ~2^-46, from one table of
+// 65536 double-float entries e^{2 pi i m / 65536} (t16[m], m = the top 16 bits;
+// 1 MB, read through the caches) and the same small rotation by the remaining
+// 48 bits as df_phasor: the product of two table factors (df_phasor's
+// dfc_mul) is not needed.
+FC2_D dfc df_phasor16(uint64_t u, const dfc* __restrict__ t16) {
+    const int m = (int)(u >> 48);
+    const uint64_t r = u & ((1ull << 48) - 1);
+    const float rh = (float)(uint32_t)(r >> 24), rl = (float)(uint32_t)(r & 0xffffffu);
+    const dfl d = df_two_sum(rh * 9.094947017729282e-13f, rl * 5.421010862427522e-20f);  // 2^-40, 2^-64
+    const dfl th = df_mul(d, dfl{6.28318548202514648f, -1.74845553146951525e-07f});  // 2 pi
+    const float eps = -0.5f * th.h * th.h;
+    const float t3 = th.h * th.h * th.h * (1.0f / 6.0f);
+    const dfl s = df_fast_sum(th.h, th.l - t3);
+    return dfc_rot_small(t16[m], eps, s);
+}
+
 // e^{2 pi i u 2^-64} in double from the same split as df_phasor: two table
 // factors times 1 - theta^2/2 + i (theta - theta^3/6), theta < 1e-4 (the
 // dropped terms are below 4e-18).
@@ -149,8 +166,8 @@ FC2_D double2 d_phasor(uint64_t u, const double2* t1, const double2* t2) {
 // ---------------------------------------------- sums exact in fixed point
 // The last precision tier of the exact fix-up keeps the float pipes' speed but
 // none of their accumulation error: each harmonic multiple's phasor is
-// evaluated directly from its exact integer phase k u (df_phasor, ~2^-46, no
-// chains of products), the products with the double-float weights are summed
+// evaluated directly from its exact integer phase k u (df_phasor or
+// df_phasor16, ~2^-46, no chains of products), the products with the double-float weights are summed
 // in double-float over blocks of FX_BLOCK samples, and every block sum enters
 // a 64-bit integer accumulator at a fixed scale 2^s -- integer additions are
 // exact and associative, so the result does not depend on the order and the
@@ -178,20 +195,23 @@ FC2_D void fx_flush(long long& acc, dfl& blk, float scale) {
     blk = dfl{0.f, 0.f};
 }
 
-// One lane's sums over samples i = i0 + start, + step, .. < i1 of multiple k:
+// One lane's sums over samples i = i0 + start, + step, .. < i1 of multiple k
+// (phasors by df_phasor16 from the table t1 when T16, else by df_phasor from
+// the tables t1, t2; the two differ by float rounding, both ~2^-46):
 // acc[0..1] = sum w e^{2 pi i k u_i} (re, im) and, when with_p, acc[2..3] the
 // same with the weighted data; u_i = A_i + ju B_i (mod 2^64).  Weights as float
 // high parts at [i] and low parts at [ntot + i]; sq, sp = 2^s of each kind.
+template <bool T16>
 FC2_D void fx_lane_sums(const uint64_t* __restrict__ Aph, const uint64_t* __restrict__ Bph,
                         const float* __restrict__ wq32, const float* __restrict__ wp32,
                         int64_t ntot, uint64_t ju, uint64_t k, int64_t i0, int64_t i1,
-                        int64_t start, int64_t step, bool with_p, const dfc* t1, const dfc* t2,
-                        float sq, float sp, long long acc[4]) {
+                        int64_t start, int64_t step, bool with_p, const dfc* __restrict__ t1,
+                        const dfc* __restrict__ t2, float sq, float sp, long long acc[4]) {
     dfl b0{0.f, 0.f}, b1{0.f, 0.f}, b2{0.f, 0.f}, b3{0.f, 0.f};
     int cnt = 0;
     for (int64_t i = i0 + start; i < i1; i += step) {
         const uint64_t u = k * (Aph[i] + ju * Bph[i]);
-        const dfc z = df_phasor(u, t1, t2);
+        const dfc z = T16 ? df_phasor16(u, t1) : df_phasor(u, t1, t2);
         const dfl a{wq32[i], wq32[ntot + i]};
         df_acc_mul(b0, a, z.re);
         df_acc_mul(b1, a, z.im);

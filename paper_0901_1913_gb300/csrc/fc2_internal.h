@@ -24,6 +24,14 @@ enum ScalarSlot {
     SC_COUNT = 8
 };
 
+// Phasor tables of the exact sums (one device allocation): 512 double-float
+// entries (e^{2 pi i a / 256}, then e^{2 pi i b / 65536}), the same 512 in
+// double, then (single-curve plans) the 65536 double-float entries
+// e^{2 pi i m / 65536} of the last tier's phasors, at DFTAB_T16 (16-byte
+// units); a batch keeps the first two (2 * 512 * 16 bytes).
+constexpr int DFTAB_T16 = 1024;
+constexpr size_t DFTAB_BYTES = (size_t)(DFTAB_T16 + 65536) * 16;
+
 // Float transform kernel families (double passes always use FFT_R16).
 enum FftFamily {
     FFT_R16 = 0,   // radix-16 stages in shared memory (k_fft_pass)
@@ -278,8 +286,8 @@ size_t exact_scratch_bytes(int64_t n, int H, int64_t cap);
 cudaError_t launch_phase_fx(fc2_plan_s* p, cudaStream_t s);
 // Phasor tables of the exact sums (512 double-float pairs, then 512 double2)
 // into tab (2 * 512 * 16 bytes).
-cudaError_t launch_init_dftab(void* tab, cudaStream_t s);
-cudaError_t debug_phasor(const uint64_t* u, int64_t n, float* out4);  // diagnostics
+cudaError_t launch_init_dftab(void* tab, bool with16, cudaStream_t s);  // with16: also DFTAB_T16's table
+cudaError_t debug_phasor(const uint64_t* u, int64_t n, int table16, float* out4);  // diagnostics
 
 // k_adjoint.cu: one entry = (curve << 32 | bin) of a curve table
 struct AdjTab {

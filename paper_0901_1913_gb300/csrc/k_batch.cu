@@ -404,8 +404,8 @@ FC2_D void bx_sums(const uint64_t* __restrict__ Aph, const uint64_t* __restrict_
         const int ep = fx_exponent(mp * 1.0000002f, i1 - i0 + 1);
         long long acc[4] = {0, 0, 0, 0};
         if (g < 2 * H)
-            fx_lane_sums(Aph, Bph, wq32, wp32, ntot, ju, (uint64_t)(g + 1), i0, i1, r, lph,
-                         g < H, tb.t2, tb.t2 + 256, exp2f((float)eq), exp2f((float)ep), acc);
+            fx_lane_sums<false>(Aph, Bph, wq32, wp32, ntot, ju, (uint64_t)(g + 1), i0, i1, r, lph,
+                                g < H, tb.t2, tb.t2 + 256, exp2f((float)eq), exp2f((float)ep), acc);
         // group sums, exact: the group's first lane adds its lanes' values in order
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -1175,7 +1175,7 @@ static cudaError_t chunk_launches(Batch& b, int nc, int64_t ntot, int64_t nmax, 
         b.tc, b.xc, b.sgc, b.perm, ntot, b.off, nc, b.scal, b.fmin, b.df, b.tau, b.wq, b.wp, b.A, b.B,
         b.wq32, b.wp32);
     ++nl;
-    cudaError_t e = launch_init_dftab(b.dftab, s);
+    cudaError_t e = launch_init_dftab(b.dftab, false, s);
     if (e != cudaSuccess) return e;
     ++nl;
     dim3 gph((unsigned)((nmax + 255) / 256), (unsigned)S);

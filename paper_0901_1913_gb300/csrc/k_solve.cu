@@ -280,16 +280,23 @@ __global__ void k_phase_fx(const double* __restrict__ tau, const double* __restr
 
 // Tables e^{2 pi i a / 256} (entries 0..255) and e^{2 pi i b / 65536}
 // (entries 256..511): double-float for df_phasor (tier 2), then the same in
-// double (tier 3).
-__global__ void k_init_dftab(dfc* __restrict__ tab, double2* __restrict__ tab64) {
+// double (tier 3); then e^{2 pi i m / 65536}, m < 65536, double-float, for
+// df_phasor16 (the last tier) at DFTAB_T16.
+__global__ void k_init_dftab(dfc* __restrict__ tab, int with16) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 512) return;
-    const double x = (i < 256) ? (double)i / 128.0 : (double)(i - 256) / 32768.0;
+    if (i >= (with16 ? 512 + 65536 : 512)) return;
     double sn, cn;
-    sincospi(x, &sn, &cn);
-    tab[i] = dfc{df_from_double(cn), df_from_double(sn)};
-    tab64[i] = make_double2(cn, sn);
+    if (i < 512) {
+        const double x = (i < 256) ? (double)i / 128.0 : (double)(i - 256) / 32768.0;
+        sincospi(x, &sn, &cn);
+        tab[i] = dfc{df_from_double(cn), df_from_double(sn)};
+        reinterpret_cast<double2*>(tab + 512)[i] = make_double2(cn, sn);
+    } else {
+        sincospi((double)(i - 512) / 32768.0, &sn, &cn);
+        tab[DFTAB_T16 + (i - 512)] = dfc{df_from_double(cn), df_from_double(sn)};
+    }
 }
+constexpr unsigned DFTAB_INIT_BLOCKS = (512 + 65536 + 255) / 256;
 
 // Lane 0 receives the warp's sum of (hi, lo) float pairs, added with
 // error-free two-sums (all on the float pipes).
@@ -317,7 +324,7 @@ __global__ void __launch_bounds__(EX_NT) k_exact_partial(
     constexpr bool DRED = (TIER == 3 || TIER == 4);  // per-warp partials in double
     __shared__ double red[DRED ? EX_NT / 32 : 1][NV];
     __shared__ float2 redf[DRED ? 1 : EX_NT / 32][NV];
-    __shared__ dfc stab[(TIER == 2 || TIER == 4) ? 512 : 1];
+    __shared__ dfc stab[TIER == 2 ? 512 : 1];
     __shared__ double2 stab64[TIER == 3 ? 512 : 1];
     __shared__ float smax[2][EX_NT / 32];
     int64_t cnt = count_dev ? (int64_t)(*count_dev) - base : count;
@@ -328,7 +335,7 @@ __global__ void __launch_bounds__(EX_NT) k_exact_partial(
     exact_geometry(n, cnt, &chunk, &nch);
     const int64_t items = cnt * nch;
     const int lane = threadIdx.x & 31, wpi = threadIdx.x >> 5;
-    if constexpr (TIER == 2 || TIER == 4) {
+    if constexpr (TIER == 2) {
         for (int i = threadIdx.x; i < 512; i += EX_NT) stab[i] = dftab[i];
         __syncthreads();
     }
@@ -422,9 +429,10 @@ __global__ void __launch_bounds__(EX_NT) k_exact_partial(
             const int g = lane / lph, r = lane - g * lph;
             long long acc[4] = {0, 0, 0, 0};
             if (g < 2 * H)
-                fx_lane_sums(Aph, Bph, wq32, wp32, n, ju, (uint64_t)(g + 1), i0, i1,
-                             r + (int64_t)lph * wpi, (int64_t)lph * (EX_NT / 32), g < H, stab,
-                             stab + 256, exp2f((float)eq), exp2f((float)ep), acc);
+                fx_lane_sums<true>(Aph, Bph, wq32, wp32, n, ju, (uint64_t)(g + 1), i0, i1,
+                                   r + (int64_t)lph * wpi, (int64_t)lph * (EX_NT / 32), g < H,
+                                   dftab + DFTAB_T16, nullptr, exp2f((float)eq),
+                                   exp2f((float)ep), acc);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 long long sacc = acc[q];
@@ -1003,40 +1011,42 @@ cudaError_t launch_phase_fx(fc2_plan_s* p, cudaStream_t s) {
     k_phase_fx<<<(unsigned)((p->n + 255) / 256), 256, 0, s>>>(p->d_tau, p->d_wq, p->d_wp, p->n,
                                                              p->f_min, p->df, p->d_phA, p->d_phB,
                                                              p->d_wq32, p->d_wp32);
-    k_init_dftab<<<2, 256, 0, s>>>((dfc*)p->d_dftab, (double2*)((dfc*)p->d_dftab + 512));
+    k_init_dftab<<<DFTAB_INIT_BLOCKS, 256, 0, s>>>((dfc*)p->d_dftab, 1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_dftab(void* tab, cudaStream_t s) {
-    k_init_dftab<<<2, 256, 0, s>>>((dfc*)tab, (double2*)((dfc*)tab + 512));
+cudaError_t launch_init_dftab(void* tab, bool with16, cudaStream_t s) {
+    if (with16) k_init_dftab<<<DFTAB_INIT_BLOCKS, 256, 0, s>>>((dfc*)tab, 1);
+    else k_init_dftab<<<2, 256, 0, s>>>((dfc*)tab, 0);
     return cudaGetLastError();
 }
 
-// The double-float phasor of each phase (diagnostics: its accuracy test).
+// The double-float phasor of each phase (diagnostics: its accuracy test), from
+// the two 256-entry tables (df_phasor) or the 65536-entry one (df_phasor16).
 __global__ void k_debug_phasor(const uint64_t* __restrict__ u, int64_t n,
-                               const dfc* __restrict__ tab, float* __restrict__ out) {
+                               const dfc* __restrict__ tab, int table16, float* __restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const dfc z = df_phasor(u[i], tab, tab + 256);
+    const dfc z = table16 ? df_phasor16(u[i], tab + DFTAB_T16) : df_phasor(u[i], tab, tab + 256);
     out[4 * i] = z.re.h;
     out[4 * i + 1] = z.re.l;
     out[4 * i + 2] = z.im.h;
     out[4 * i + 3] = z.im.l;
 }
 
-cudaError_t debug_phasor(const uint64_t* u, int64_t n, float* out4) {
+cudaError_t debug_phasor(const uint64_t* u, int64_t n, int table16, float* out4) {
     void* d = nullptr;
-    const size_t tb = (size_t)512 * sizeof(dfc) + 512 * sizeof(double2);
+    const size_t tb = DFTAB_BYTES;
     const size_t bytes = tb + (size_t)n * 8 + (size_t)n * 16;
     cudaError_t e = cudaMalloc(&d, bytes);
     if (e != cudaSuccess) return e;
     char* base = (char*)d;
     uint64_t* du = (uint64_t*)(base + tb);
     float* dout = (float*)(base + tb + (size_t)n * 8);
-    e = launch_init_dftab(base, 0);
+    e = launch_init_dftab(base, true, 0);
     if (e == cudaSuccess) e = cudaMemcpy(du, u, (size_t)n * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        k_debug_phasor<<<(unsigned)((n + 255) / 256), 256>>>(du, n, (const dfc*)base, dout);
+        k_debug_phasor<<<(unsigned)((n + 255) / 256), 256>>>(du, n, (const dfc*)base, table16, dout);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(out4, dout, (size_t)n * 16, cudaMemcpyDeviceToHost);

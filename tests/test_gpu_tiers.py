@@ -121,11 +121,13 @@ def test_large_curve_full_size(fc2, oracle_mod):
     assert counts[1] > 100 and r["ok"], r
 
 
-def test_double_float_phasor_accuracy(fc2):
-    """The exact fix-up's double-float phasor e^{2 pi i u 2^-64} (table factors
-    for the top 16 bits, then a small rotation by the rest) against the same
-    exact phase evaluated in long double: random phases over the whole 64-bit
-    range plus the table and rotation boundaries, within 2^-45 absolute."""
+@pytest.mark.parametrize("fn", ["fc2_debug_phasor", "fc2_debug_phasor16"])
+def test_double_float_phasor_accuracy(fc2, fn):
+    """The exact fix-up's double-float phasors e^{2 pi i u 2^-64} (two table
+    factors for the top 16 bits, or one entry of the 65536-entry table of the
+    last tier, then a small rotation by the rest) against the same exact phase
+    evaluated in long double: random phases over the whole 64-bit range plus
+    the table and rotation boundaries, within 2^-45 absolute."""
     import ctypes
     lib = fc2.load()
     rng = np.random.default_rng(5)
@@ -134,8 +136,8 @@ def test_double_float_phasor_accuracy(fc2):
     u = np.concatenate([np.array(edges, dtype=np.uint64),
                         rng.integers(0, 2**64, size=50000, dtype=np.uint64, endpoint=False)])
     out = np.zeros(4 * u.size, dtype=np.float32)
-    rc = lib.fc2_debug_phasor(ctypes.c_void_p(u.ctypes.data), ctypes.c_int64(u.size),
-                              ctypes.c_void_p(out.ctypes.data))
+    rc = getattr(lib, fn)(ctypes.c_void_p(u.ctypes.data), ctypes.c_int64(u.size),
+                          ctypes.c_void_p(out.ctypes.data))
     assert rc == 0
     ld = np.longdouble
     two_pi = ld("6.283185307179586476925286766559005768394338798750211641949889184615632812572")
@@ -144,7 +146,7 @@ def test_double_float_phasor_accuracy(fc2):
     ref_re, ref_im = np.cos(two_pi * frac), np.sin(two_pi * frac)
     o = out.reshape(-1, 4).astype(ld)
     err = max(np.max(np.abs(o[:, 0] + o[:, 1] - ref_re)), np.max(np.abs(o[:, 2] + o[:, 3] - ref_im)))
-    print("phasor max abs error", float(err), "= 2^%.1f" % np.log2(float(err)))
+    print(fn, "max abs error", float(err), "= 2^%.1f" % np.log2(float(err)))
     assert err <= 2.0 ** -45
 
 
