@@ -418,6 +418,31 @@ class PinnedHost:
             self._ptr = ctypes.c_void_p()
 
 
+def host_link_probe(hbuf, dev, stream):
+    """GB/s of one 2 GB copy each way between a device buffer and the pinned
+    host buffer `hbuf` (float32), timed with CUDA events: the host link's
+    state when the end-to-end steps ran (the link is shared with the
+    machine's other GPUs and jobs)."""
+    import torch
+    n = min(hbuf.numel(), 512 << 20)
+    d = torch.empty(n, dtype=torch.float32, device=dev)
+    out = {}
+    for name in ("d2h", "h2d"):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            if name == "d2h":
+                hbuf[:n].copy_(d, non_blocking=True)
+            else:
+                d.copy_(hbuf[:n], non_blocking=True)
+            e1.record(stream)
+        stream.synchronize()
+        out[name] = round(4 * n / (e0.elapsed_time(e1) / 1e3) / 1e9, 1)
+    del d
+    return out
+
+
 def run_survey(args):
     ws, rank, local = dist_init()
     import torch
@@ -457,6 +482,7 @@ def run_survey(args):
     for _ in range(e2e_steps):
         _, _, st_e2e = call(tp, xp, sp, hout)
     e2e_s = allreduce_max(ws, (time.perf_counter() - t0) / e2e_steps)
+    link = host_link_probe(hout, dev, stream)
     del hout
     hbuf.close()
 
@@ -607,6 +633,7 @@ def run_survey(args):
                 "h2d_bytes_per_step": int(3 * 8 * int(b.offsets[-1])),
                 "d2h_bytes_per_step": int(4 * evals + b.C * K * _fc2.BEST_DTYPE.itemsize),
                 "ms_per_step": e2e_s * 1e3, "steps": e2e_steps,
+                "host_link_gbs_after": link,
                 "cold_first_call_ms": cold_ms,
                 "host_phase_ms_last_call": {k: round(v, 2) for k, v in
                                             st_e2e["host_phase_ms"].items()},
